@@ -1,0 +1,254 @@
+"""FP64 CPU oracle for GBEM (Wu & Li, arXiv 2203.11733).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The product path never
+imports this module, and this module imports nothing from the product.
+
+It implements, plainly and slowly, every step of the extraction:
+
+* ``mesh_boxes``      -- the boundary partition into rectangles I_j of a set of
+                         cuboid conductors (Sec. 3.1, before Eq. "myequation";
+                         Sec. 3.3: every conductor is a union of cuboids).
+* ``entries`` / ``assemble`` -- the Galerkin matrix of Eq. "matrix",
+                         a_ij = (1/(4 pi |I_i||I_j|)) int int 1/|x-y|, computed
+                         in ``gbem_oracle.c`` (see its header for the method).
+* ``capacitance``     -- the right-hand sides b of Eq. "lineareq1" (f0 = 1 on
+                         the main net, 0 elsewhere, Sec. 3.1), the solve A X = b
+                         by Cholesky (Sec. 3.2: A is symmetric positive
+                         definite, Theorem 1) and the charge of Eq.
+                         "electriccharge", Q_n = eps * sum_{I_j on net n} X_j.
+
+Units: lengths in micrometres, so A is in 1/um and X in um; the capacitance in
+farads is eps0 * eps_r * 1e-6 * X.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gbem_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+EPS0 = 8.8541878128e-12  # F/m, CODATA 2018
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, strict IEEE arithmetic)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+        P = ctypes.c_void_p
+        lib.orc_rect_potential.restype = d
+        lib.orc_rect_potential.argtypes = [ctypes.c_int, P, P]
+        lib.orc_pair_integral.restype = d
+        lib.orc_pair_integral.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P]
+        lib.orc_entries.restype = ctypes.c_int
+        lib.orc_entries.argtypes = [ctypes.c_int, P, P, i64, P, P, P, ctypes.c_int]
+        lib.orc_assemble.restype = ctypes.c_int
+        lib.orc_assemble.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int]
+        lib.orc_gl_nodes.restype = ctypes.c_int
+        lib.orc_gl_nodes.argtypes = [ctypes.c_int, P, P]
+        lib.orc_max_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+# --------------------------------------------------------------------------
+# Boundary partition (Sec. 3.1 and Sec. 3.3)
+# --------------------------------------------------------------------------
+
+def divide(lo: float, hi: float, h: float, ratio: float = 1.0, h_min: float = 0.0) -> list[float]:
+    """Nodes of a 1-D division of [lo, hi].
+
+    Uniform (ratio <= 1): n = ceil(L/h) equal cells.  Edge-graded: cells of
+    h_min, h_min*ratio, ... grow from both ends while they stay below h; the
+    middle is split into equal cells no longer than h.
+    """
+    L = hi - lo
+    if ratio <= 1.0 or h_min <= 0.0 or h_min >= h:
+        n = max(1, math.ceil(L / h - 1e-9))
+        return [lo + (L * k) / n for k in range(n)] + [hi]
+    sizes = []
+    s = h_min
+    while s < h:
+        sizes.append(s)
+        s = s * ratio
+    m = len(sizes)
+    while m > 0 and 2.0 * sum(sizes[:m]) > L:
+        m -= 1
+    if m == 0:
+        n = max(1, math.ceil(L / h - 1e-9))
+        return [lo + (L * k) / n for k in range(n)] + [hi]
+    left = [lo]
+    acc = lo
+    for k in range(m):
+        acc = acc + sizes[k]
+        left.append(acc)
+    right = [hi]
+    acc = hi
+    for k in range(m):
+        acc = acc - sizes[k]
+        right.append(acc)
+    right.reverse()
+    xl, xr = left[-1], right[0]
+    M = xr - xl
+    nodes = left[:-1]
+    if M > 1e-12 * L:
+        nmid = max(1, math.ceil(M / h - 1e-9))
+        nodes += [xl + (M * k) / nmid for k in range(nmid)]
+    nodes += right
+    return nodes
+
+
+def mesh_boxes(boxes, h: float, ratio: float = 1.0, h_min: float = 0.0):
+    """Panels of the surfaces of disjoint cuboids.
+
+    ``boxes``: iterable of (lo[3], hi[3], conductor).  Returns (axis int32[n],
+    geo float64[n,5] = (c, lo0, hi0, lo1, hi1), cond int32[n]).  Every face of
+    a box is cut on the tensor grid of the 1-D divisions of its two edges.
+    """
+    axis, geo, cond = [], [], []
+    for lo, hi, c in boxes:
+        for k in range(3):
+            p, q = [a for a in range(3) if a != k]
+            np_ = divide(lo[p], hi[p], h, ratio, h_min)
+            nq = divide(lo[q], hi[q], h, ratio, h_min)
+            for plane in (lo[k], hi[k]):
+                for a in range(len(np_) - 1):
+                    for b in range(len(nq) - 1):
+                        axis.append(k)
+                        geo.append((plane, np_[a], np_[a + 1], nq[b], nq[b + 1]))
+                        cond.append(c)
+    return (np.asarray(axis, dtype=np.int32), np.asarray(geo, dtype=np.float64).reshape(-1, 5),
+            np.asarray(cond, dtype=np.int32))
+
+
+def areas(geo: np.ndarray) -> np.ndarray:
+    return (geo[:, 2] - geo[:, 1]) * (geo[:, 4] - geo[:, 3])
+
+
+# --------------------------------------------------------------------------
+# Matrix entries (Sec. 3.4, Eq. "matrix")
+# --------------------------------------------------------------------------
+
+def rect_potential(axis: int, geo, x) -> float:
+    """int over the panel of 1/|x - y| dy (the inner integral)."""
+    g = np.ascontiguousarray(geo, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_load().orc_rect_potential(int(axis), _ptr(g), _ptr(xx)))
+
+
+def pair_integral(axis_i: int, geo_i, axis_j: int, geo_j, method: int = 0):
+    """int_{I_i} int_{I_j} 1/|x-y| (no 1/(4 pi), no area factors).
+
+    method 0 chooses 4-D Gauss-Legendre for well separated pairs and the
+    split-outer quadrature otherwise; method 1 always splits.  Returns
+    (value, number of quadratures that did not meet their convergence test).
+    """
+    gi = np.ascontiguousarray(geo_i, dtype=np.float64)
+    gj = np.ascontiguousarray(geo_j, dtype=np.float64)
+    nf = ctypes.c_int(0)
+    v = _load().orc_pair_integral(int(axis_i), _ptr(gi), int(axis_j), _ptr(gj), int(method),
+                                  ctypes.byref(nf))
+    return float(v), int(nf.value)
+
+
+def entries(axis, geo, I, J, nthreads: int = 0):
+    """a_ij for the index pairs (I[t], J[t])."""
+    axis = np.ascontiguousarray(axis, dtype=np.int32)
+    geo = np.ascontiguousarray(geo, dtype=np.float64)
+    I = np.ascontiguousarray(I, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    out = np.empty(len(I), dtype=np.float64)
+    nf = _load().orc_entries(len(axis), _ptr(axis), _ptr(geo), len(I), _ptr(I), _ptr(J), _ptr(out),
+                             int(nthreads))
+    if nf:
+        raise RuntimeError(f"oracle: {nf} quadratures did not converge")
+    return out
+
+
+def assemble(axis, geo, nthreads: int = 0) -> np.ndarray:
+    """The full symmetric N x N matrix A of Eq. "matrix"."""
+    axis = np.ascontiguousarray(axis, dtype=np.int32)
+    geo = np.ascontiguousarray(geo, dtype=np.float64)
+    n = len(axis)
+    A = np.empty((n, n), dtype=np.float64)
+    nf = _load().orc_assemble(n, _ptr(axis), _ptr(geo), _ptr(A), int(nthreads))
+    if nf:
+        raise RuntimeError(f"oracle: {nf} quadratures did not converge")
+    return A
+
+
+# --------------------------------------------------------------------------
+# Solve and charge (Eqs. "lineareq1" and "electriccharge")
+# --------------------------------------------------------------------------
+
+def rhs(cond: np.ndarray):
+    """b for every main net: column k is 1 on the panels of conductor k.
+
+    Returns (B float64[N, n_c], conductor ids in column order)."""
+    ids = np.unique(cond)
+    B = (cond[:, None] == ids[None, :]).astype(np.float64)
+    return B, ids
+
+
+def solve(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """X = A^{-1} B by Cholesky (A is symmetric positive definite)."""
+    import scipy.linalg as sla
+    c = sla.cho_factor(A, lower=True, check_finite=True)
+    return sla.cho_solve(c, B)
+
+
+def capacitance_from_matrix(A: np.ndarray, cond: np.ndarray, eps_r: float) -> np.ndarray:
+    """Maxwell capacitance matrix in farads: C[m, k] = charge on conductor m
+    when conductor k is at 1 V and every other conductor at 0 V."""
+    B, _ = rhs(cond)
+    X = solve(A, B)
+    return EPS0 * eps_r * 1e-6 * (B.T @ X)
+
+
+def capacitance(axis, geo, cond, eps_r: float, nthreads: int = 0) -> np.ndarray:
+    A = assemble(axis, geo, nthreads)
+    return capacitance_from_matrix(A, np.asarray(cond), eps_r)
+
+
+def gauss_legendre(n: int):
+    x = np.empty(n)
+    w = np.empty(n)
+    if _load().orc_gl_nodes(int(n), _ptr(x), _ptr(w)) != 0:
+        raise ValueError(n)
+    return x, w
