@@ -1,0 +1,215 @@
+/*
+ * gbem.h -- C ABI of the GB300 Galerkin boundary element capacitance library.
+ *
+ * The library implements the single-dielectric method of Wu & Li, "GBEM:
+ * Galerkin Boundary Element Method for 3-D Capacitance Extraction"
+ * (arXiv 2203.11733), Sec. 3:
+ *
+ *   boundary partition    dOmega = U_j I_j into axis-aligned rectangles
+ *                         (Sec. 3.1 before Eq. "myequation"; Sec. 3.3: every
+ *                         conductor is built from cuboids)        -> gbem_mesh
+ *   Galerkin matrix       a_ij = 1/(4 pi |I_i||I_j|) int_Ii int_Ij 1/|x-y|
+ *                         (Eq. "matrix", Sec. 3.4)                -> gbem_assemble
+ *   Cholesky factor       A is symmetric positive definite (Sec. 3.2,
+ *                         Theorem 1), so A = L L^T                -> gbem_factor
+ *   solve                 A X = b, b_i = mean of f0 over I_i with f0 = 1 on the
+ *                         main net and 0 elsewhere (Eq. "lineareq1")
+ *                                                                 -> gbem_solve
+ *   charge                Q_n = eps * sum_{I_j on net n} X_j
+ *                         (Eq. "electriccharge")                  -> gbem_capacitance
+ *
+ * Units: lengths in micrometres; A in 1/um; X in um; capacitances in farads,
+ * C = eps0 * eps_r * 1e-6 * X (eps0 = 8.8541878128e-12 F/m).  The kernel
+ * 1/(4 pi |x-y|) is the paper's u* (Sec. 2.1, Eq. "representation"); the
+ * permittivity enters only at the charge step, as in Eq. "electriccharge".
+ * Conductors sit in free space (no grounded enclosure unless the caller adds
+ * one as an extra conductor held at 0 V).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a gbem_status; on failure the context keeps a message
+ *    readable through gbem_last_error().  No C++ exception crosses the ABI.
+ *  - Device memory for handles comes from the allocator passed to
+ *    gbem_create() (cudaMalloc/cudaFree when none is given); handles own it
+ *    and release it in their *_destroy call.  Host arrays passed in are read
+ *    during the call only and stay owned by the caller; so do device arrays
+ *    passed to gbem_solve().
+ *  - gbem_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  gbem_assemble, gbem_factor and gbem_solve only enqueue work on
+ *    it; gbem_capacitance, gbem_matrix_download and gbem_matrix_status wait
+ *    for that stream.
+ *  - A context and its handles are not thread safe; use one context per
+ *    worker thread.
+ *  - Matrix layout: N x N column-major, lower triangle significant, padded
+ *    internally to a multiple of 128 with the identity.
+ */
+#ifndef GBEM_H
+#define GBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBEM_OK = 0,
+    GBEM_ERR_ARG = -1,      /* invalid argument (null pointer, size, id) */
+    GBEM_ERR_OOM = -2,      /* allocator refused, or HBM budget exceeded */
+    GBEM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    GBEM_ERR_NOT_SPD = -4,  /* Cholesky met a non-positive pivot */
+    GBEM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    GBEM_ERR_NOCONV = -6,   /* iterative refinement missed its tolerance */
+    GBEM_ERR_MESH = -7,     /* malformed geometry: empty, degenerate or
+                               overlapping boxes, zero-area panel */
+    GBEM_ERR_STATE = -8,    /* call out of order (e.g. solve before factor) */
+    GBEM_ERR_NODEV = -9     /* context has no device (created with device -1) */
+} gbem_status;
+
+typedef enum {
+    GBEM_FP64 = 0,  /* every step in FP64 */
+    GBEM_MIXED = 1  /* FP32 far-field quadrature and FP32 factor; FP64 near
+                       field, FP64 residual and iterative refinement */
+} gbem_precision;
+
+typedef void* gbem_stream;
+
+/* A conductor cuboid (Sec. 3.3): lo < hi componentwise, in um. */
+typedef struct {
+    double lo[3];
+    double hi[3];
+    int32_t conductor;
+} gbem_box;
+
+/* Boundary partition.  Each box edge of length L is divided either uniformly
+ * into ceil(L/h) cells (ratio <= 1) or, when ratio > 1 and 0 < h_min < h,
+ * with cells h_min, h_min*ratio, ... growing from both ends while below h
+ * and the rest split into equal cells no longer than h. */
+typedef struct {
+    double h;
+    double ratio;
+    double h_min;
+} gbem_mesh_params;
+
+/* Tunables.  Zero fields keep the defaults shown. */
+typedef struct {
+    double q_near_fp64;   /* gap / largest edge below which a pair uses the
+                             closed form in FP64 mode (12) */
+    double q_near_mixed;  /* same in mixed mode (0.5) */
+    double ir_tol;        /* relative residual target of refinement (1e-12) */
+    int ir_max_iter;      /* refinement iterations at most (10) */
+    int nb;               /* Cholesky block size: 64 */
+} gbem_tuning;
+
+typedef void* (*gbem_alloc_fn)(size_t bytes, gbem_stream stream, void* user);
+typedef void (*gbem_free_fn)(void* ptr, size_t bytes, gbem_stream stream, void* user);
+
+typedef struct gbem_ctx_s gbem_ctx;
+typedef struct gbem_mesh_s gbem_mesh_t;
+typedef struct gbem_matrix_s gbem_matrix_t;
+
+/* Create a context on CUDA device `device` (or -1 for a host-only context
+ * that can mesh but not compute).  hbm_budget caps the bytes the context may
+ * hold at once (0 = no cap).  alloc/free may be NULL (cudaMalloc/cudaFree). */
+gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget,
+                        gbem_alloc_fn alloc, gbem_free_fn free_fn, void* user);
+void gbem_destroy(gbem_ctx* ctx);
+const char* gbem_last_error(const gbem_ctx* ctx);
+gbem_status gbem_set_tuning(gbem_ctx* ctx, const gbem_tuning* t);
+/* Bytes currently held by the context's handles. */
+size_t gbem_bytes_in_use(const gbem_ctx* ctx);
+
+/* Mesh the surfaces of `nbox` disjoint cuboids (Sec. 3.1, Sec. 3.3).
+ * Boxes with the same conductor id form one conductor; boxes may not
+ * overlap or touch.  Panels are ordered by conductor (ids ascending), then
+ * by the Morton code of the panel centre.  Uploads panel geometry to the
+ * device when the context has one. */
+gbem_status gbem_mesh(gbem_ctx* ctx, const gbem_box* boxes, int nbox,
+                      const gbem_mesh_params* params, gbem_mesh_t** out);
+
+/* Build a mesh from an explicit panel list, kept in the given order.
+ * axis[i] in {0,1,2} is the panel's normal axis; geo[5*i..5*i+4] =
+ * {c, lo0, hi0, lo1, hi1}: the plane coordinate and the extents along the two
+ * other axes in increasing axis order; cond[i] the conductor id. */
+gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis,
+                                  const double* geo, const int32_t* cond,
+                                  gbem_mesh_t** out);
+
+/* Panel count and conductor count of a mesh. */
+gbem_status gbem_mesh_info(const gbem_mesh_t* mesh, int* n_panels, int* n_cond);
+
+/* Host copies of the panels in mesh order (arrays of n_panels, 5*n_panels,
+ * n_panels) and the sorted conductor ids (array of n_cond); any pointer may
+ * be NULL. */
+gbem_status gbem_mesh_panels(const gbem_mesh_t* mesh, int8_t* axis, double* geo,
+                             int32_t* cond, int32_t* cond_ids);
+void gbem_mesh_destroy(gbem_mesh_t* mesh);
+
+/* Assemble the Galerkin matrix (Eq. "matrix") on `stream`.  Pairs whose gap
+ * is below q_near times their largest edge use exact 4-D corner sums of
+ * closed-form antiderivatives in FP64; the others use a tensor Gauss-Legendre
+ * rule whose order follows the gap (FP64, or FP32 in mixed mode). */
+gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream stream,
+                          gbem_matrix_t** out);
+
+/* Cholesky factorisation A = L L^T (Sec. 3.2), blocked, on `stream`.  FP64
+ * mode factors an FP64 copy; mixed mode factors the FP32 copy (diagonal
+ * blocks in FP64 arithmetic).  A non-positive pivot is recorded and reported
+ * by the next waiting call as GBEM_ERR_NOT_SPD. */
+gbem_status gbem_factor(gbem_matrix_t* mat, gbem_stream stream);
+
+/* Solve A X = B for nrhs right-hand sides on `stream`.  B_dev and X_dev are
+ * device arrays, column-major with leading dimensions ldb, ldx >= N, and may
+ * alias.  Mixed mode runs FP64 iterative refinement until the relative
+ * residual max_k |B_k - A X_k|_inf / |B_k|_inf is below ir_tol; if ir_iters
+ * is not NULL the call waits for the stream and stores the iterations used. */
+gbem_status gbem_solve(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ldb,
+                       double* X_dev, int ldx, int* ir_iters, gbem_stream stream);
+
+/* Maxwell capacitance matrix in farads, n_c x n_c row-major into C_host:
+ * C[m][k] = charge on conductor m with conductor k at 1 V and the others at
+ * 0 V (Eqs. "lineareq1", "electriccharge"), rows and columns in ascending
+ * conductor id.  Factors the matrix first if needed.  resid_out (may be
+ * NULL) receives the final relative residual.  Waits for the stream. */
+gbem_status gbem_capacitance(gbem_mesh_t* mesh, gbem_matrix_t* mat, double eps_r,
+                             double* C_host, double* resid_out, gbem_stream stream);
+
+/* Copy the assembled matrix A (both triangles filled) to host memory,
+ * N x N column-major.  Waits for the matrix's last stream. */
+gbem_status gbem_matrix_download(gbem_matrix_t* mat, double* host);
+
+/* Wait for the matrix's last stream and report a recorded device-side error
+ * (GBEM_ERR_NOT_SPD from the factorisation), else GBEM_OK. */
+gbem_status gbem_matrix_status(gbem_matrix_t* mat);
+
+/* Tracing.  With timing enabled, every call records CUDA events on its
+ * stream around each phase; gbem_get_stats waits for those events and adds
+ * their elapsed times.  launches counts every kernel launched by the library
+ * in this process (all contexts).  reset != 0 clears the counters after
+ * reading. */
+enum {
+    GBEM_PHASE_MESH = 0,      /* panel upload */
+    GBEM_PHASE_ASSEMBLE = 1,  /* gbem_assemble kernels */
+    GBEM_PHASE_FACTOR = 2,    /* Cholesky */
+    GBEM_PHASE_SOLVE = 3,     /* triangular solves, residuals, refinement */
+    GBEM_PHASE_REDUCE = 4,    /* right-hand sides and charge reduction */
+    GBEM_NPHASE = 5
+};
+typedef struct {
+    double ms[GBEM_NPHASE];
+    long long calls[GBEM_NPHASE];
+    long long launches;
+} gbem_stats;
+gbem_status gbem_set_timing(gbem_ctx* ctx, int enable);
+gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset);
+
+/* Matrix order N and the number of panel pairs by class: pairs evaluated by
+ * closed form, and by Gauss-Legendre order 1..6 (counts[0] closed form,
+ * counts[n] order n; array of 7).  Waits for the assembly stream. */
+gbem_status gbem_matrix_info(gbem_matrix_t* mat, int* n, long long* counts);
+void gbem_matrix_destroy(gbem_matrix_t* mat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBEM_H */

@@ -23,8 +23,10 @@
  *     touches I_j uses tanh-sinh (double exponential) quadrature with levels
  *     refined until two levels agree, every other piece uses adaptive tensor
  *     Gauss-Legendre (orders 8 and 16 compared, 2x2 subdivision otherwise),
- *   - pairs whose gap is at least three times the larger panel diagonal use a
- *     direct 4-D tensor Gauss-Legendre rule of orders 8 and 10, compared.
+ *   - pairs whose gap is at least the larger panel diagonal use a direct 4-D
+ *     tensor Gauss-Legendre rule (orders 8 and 10 compared beyond three
+ *     diagonals, 12 and 16 below), which avoids the cancellation of the
+ *     corner formula when the inner panel is small against the distance.
  * Gauss-Legendre nodes are computed here by Newton's method on the Legendre
  * recurrence.
  *
@@ -389,10 +391,16 @@ static double orc_pair(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
 {
     double g = orc_gap(Pi, Pj);
     double dmax = fmax(orc_diag(Pi), orc_diag(Pj));
+    /* Separated pairs: direct 4-D rule, two orders compared.  The agreement
+     * test allows for the rounding of a sum of up to 16^4 terms. */
     if (g >= 3.0 * dmax) {
         double i8 = orc_pair_gl4(Pi, Pj, 8);
         double i10 = orc_pair_gl4(Pi, Pj, 10);
-        if (fabs(i10 - i8) <= 1e-15 * fabs(i10)) return i10;
+        if (fabs(i10 - i8) <= 5e-14 * fabs(i10)) return i10;
+    } else if (g >= dmax) {
+        double i12 = orc_pair_gl4(Pi, Pj, 12);
+        double i16 = orc_pair_gl4(Pi, Pj, 16);
+        if (fabs(i16 - i12) <= 5e-14 * fabs(i16)) return i16;
     }
     return orc_pair_split(Pi, Pj, nfail);
 }

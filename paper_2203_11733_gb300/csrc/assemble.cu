@@ -1,0 +1,596 @@
+// Assembly of the Galerkin single-layer matrix (Wu & Li, Sec. 3.4):
+//
+//   a_ij = 1/(4 pi |I_i| |I_j|) int_{I_i} int_{I_j} 1/|x - y| dy dx
+//
+// One CTA owns one 32x32 tile of the lower triangle.  Every pair of the tile
+// is classified by q = gap / (largest edge of the two panels):
+//
+//  * near pairs (q below a threshold) are evaluated exactly, in FP64, as a
+//    16-term corner sum of a closed-form antiderivative of 1/r.  Parallel
+//    panels use F(u,v,w) with d^4F/du^2dv^2 = 1/r (it covers the paper's
+//    coplanar case of Eqs. "int1"/"int2" and the offset case for which the
+//    paper falls back to 1-D quadrature, Eq. "int3"); perpendicular panels
+//    use H(u,v,w) with d^4H/du^2dvdw = 1/r (a closed form of the reduction in
+//    Eqs. "int4"/"int5").  Touching and self pairs are the same formula with
+//    the 0*log(0) limits taken as 0.
+//  * far pairs use an n x n tensor Gauss-Legendre rule on each panel (n^4
+//    kernel evaluations), n the smallest order whose calibrated error bound
+//    at this q is below the mode's tolerance: FP64 in FP64 mode, FP32 with
+//    an FP64 outer sum in mixed mode.
+//
+// Near pairs are gathered into a per-tile shared-memory list during the
+// classification pass and evaluated afterwards by full warps, so the scarce
+// FP64 pipe never runs a closed form with most lanes of a warp idle.
+#include <cstdio>
+
+#include "gbem_internal.h"
+
+namespace {
+
+__constant__ double c_glx[GBEM_GL_MAX + 1][GBEM_GL_MAX];
+__constant__ double c_glw[GBEM_GL_MAX + 1][GBEM_GL_MAX];
+__constant__ float c_glxf[GBEM_GL_MAX + 1][GBEM_GL_MAX];
+__constant__ float c_glwf[GBEM_GL_MAX + 1][GBEM_GL_MAX];
+
+// Smallest gap ratio q at which the n-point rule is used (index n), per mode.
+// FP64 mode targets 1e-11 relative error per entry, mixed mode 3e-7.
+__constant__ float c_qmin[2][GBEM_GL_MAX + 1] = {
+    {3.0e38f, 3.0e38f, 200.0f, 24.0f, 6.0f, 3.0f, 2.0f},
+    {3.0e38f, 700.0f, 16.0f, 3.0f, 1.5f, 1.0f, 0.5f},
+};
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ far field
+
+// 1/sqrt(x) in FP64: single-precision estimate refined by one Newton step
+// y <- y + y (1 - x y^2) / 2 (relative error about 1.5 e0^2 < 1e-13).
+__device__ __forceinline__ double rsq64(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    double e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+
+// Parallel panels: offsets of the centres (dp, dq) in-plane and w along the
+// normal; half extents ai, bi (panel i) and aj, bj (panel j).
+template <int N>
+__device__ double far64_par(double dp, double dq, double w, double ai, double bi, double aj,
+                            double bj)
+{
+    double Q[N * N], WQ[N * N];
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+            double t = dq + c_glx[N][b] * bi - c_glx[N][d] * bj;
+            Q[b * N + d] = fma(t, t, w * w);
+            WQ[b * N + d] = c_glw[N][b] * c_glw[N][d];
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double t = dp + c_glx[N][a] * ai - c_glx[N][c] * aj;
+            double p = t * t;
+            double si = 0.0;
+#pragma unroll
+            for (int k = 0; k < N * N; ++k) si = fma(WQ[k], rsq64(p + Q[k]), si);
+            s = fma(c_glw[N][a] * c_glw[N][c], si, s);
+        }
+    return s;
+}
+
+// Perpendicular panels: shared axis offset ds with half extents si, sj; the
+// offset of panel i's centre from panel j's plane dv (half extent ti of i
+// along j's normal), and of panel i's plane from panel j's centre dw (half
+// extent tj of j along i's normal).
+template <int N>
+__device__ double far64_orth(double ds, double si, double sj, double dv, double ti, double dw,
+                             double tj)
+{
+    double VW[N * N], WVW[N * N];
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+            double tv = dv + c_glx[N][b] * ti;
+            double tw = dw - c_glx[N][d] * tj;
+            VW[b * N + d] = fma(tv, tv, tw * tw);
+            WVW[b * N + d] = c_glw[N][b] * c_glw[N][d];
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double t = ds + c_glx[N][a] * si - c_glx[N][c] * sj;
+            double p = t * t;
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < N * N; ++k) acc = fma(WVW[k], rsq64(p + VW[k]), acc);
+            s = fma(c_glw[N][a] * c_glw[N][c], acc, s);
+        }
+    return s;
+}
+
+template <int N>
+__device__ double far32_par(float dp, float dq, float w, float ai, float bi, float aj, float bj)
+{
+    float Q[N * N], WQ[N * N];
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+            float t = dq + c_glxf[N][b] * bi - c_glxf[N][d] * bj;
+            Q[b * N + d] = fmaf(t, t, w * w);
+            WQ[b * N + d] = c_glwf[N][b] * c_glwf[N][d];
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            float t = dp + c_glxf[N][a] * ai - c_glxf[N][c] * aj;
+            float p = t * t;
+            float si = 0.0f;
+#pragma unroll
+            for (int k = 0; k < N * N; ++k) si = fmaf(WQ[k], rsqrtf(p + Q[k]), si);
+            s += (double)(c_glwf[N][a] * c_glwf[N][c] * si);
+        }
+    return s;
+}
+
+template <int N>
+__device__ double far32_orth(float ds, float si, float sj, float dv, float ti, float dw, float tj)
+{
+    float VW[N * N], WVW[N * N];
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+            float tv = dv + c_glxf[N][b] * ti;
+            float tw = dw - c_glxf[N][d] * tj;
+            VW[b * N + d] = fmaf(tv, tv, tw * tw);
+            WVW[b * N + d] = c_glwf[N][b] * c_glwf[N][d];
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            float t = ds + c_glxf[N][a] * si - c_glxf[N][c] * sj;
+            float p = t * t;
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < N * N; ++k) acc = fmaf(WVW[k], rsqrtf(p + VW[k]), acc);
+            s += (double)(c_glwf[N][a] * c_glwf[N][c] * acc);
+        }
+    return s;
+}
+
+// ------------------------------------------------------------------ near field
+
+// coef * ln(t + rho) with rho = sqrt(t^2 + r2); 0 * ln 0 -> 0; the t < 0 branch
+// uses ln(t + rho) = ln(r2 / (rho - t)) to avoid cancellation.
+__device__ __forceinline__ double xlog(double coef, double t, double r2, double rho)
+{
+    if (coef == 0.0) return 0.0;
+    return (t >= 0.0) ? coef * log(t + rho) : coef * log(r2 / (rho - t));
+}
+
+// F(u,v,w) = v/2 (u^2-w^2) ln(v+rho) + u/2 (v^2-w^2) ln(u+rho)
+//            - (u^2+v^2-2w^2) rho/6 - u v w atan(u v/(w rho))
+__device__ double F_par(double u, double v, double w)
+{
+    double u2 = u * u, v2 = v * v, w2 = w * w;
+    double rho = sqrt(u2 + v2 + w2);
+    double r = xlog(0.5 * v * (u2 - w2), v, u2 + w2, rho) + xlog(0.5 * u * (v2 - w2), u, v2 + w2, rho) -
+               (u2 + v2 - 2.0 * w2) * rho * (1.0 / 6.0);
+    double uvw = u * v * w;
+    if (uvw != 0.0) r -= uvw * atan(u * v / (w * rho));
+    return r;
+}
+
+// H(u,v,w) = u v w ln(u+rho) + w(3u^2-w^2)/6 ln(v+rho) + v(3u^2-v^2)/6 ln(w+rho)
+//            - v w rho/3 - u w^2/2 atan(uv/(w rho)) - u v^2/2 atan(uw/(v rho))
+//            - u^3/6 atan(vw/(u rho))
+__device__ double H_orth(double u, double v, double w)
+{
+    double u2 = u * u, v2 = v * v, w2 = w * w;
+    double rho = sqrt(u2 + v2 + w2);
+    double r = xlog(u * v * w, u, v2 + w2, rho) +
+               xlog(w * (3.0 * u2 - w2) * (1.0 / 6.0), v, u2 + w2, rho) +
+               xlog(v * (3.0 * u2 - v2) * (1.0 / 6.0), w, u2 + v2, rho) - v * w * rho * (1.0 / 3.0);
+    if (u * w != 0.0 && v != 0.0) r -= 0.5 * u * w2 * atan(u * v / (w * rho));
+    if (u * v != 0.0 && w != 0.0) r -= 0.5 * u * v2 * atan(u * w / (v * rho));
+    if (u != 0.0 && v * w != 0.0) r -= (u * u2 * (1.0 / 6.0)) * atan(v * w / (u * rho));
+    return r;
+}
+
+// ------------------------------------------------------------------ tile kernel
+
+struct TileGeo {
+    // FP64 geometry: plane c, extents on the two in-plane axes
+    double c[2 * GBEM_TILE], lo0[2 * GBEM_TILE], hi0[2 * GBEM_TILE], lo1[2 * GBEM_TILE],
+        hi1[2 * GBEM_TILE];
+    // FP32 copies for classification: box extents per global axis
+    float blo[3][2 * GBEM_TILE], bhi[3][2 * GBEM_TILE];
+    // centres as float hi + lo pairs (mixed far field) and half extents
+    float chi[3][2 * GBEM_TILE], clo[3][2 * GBEM_TILE];
+    float half[3][2 * GBEM_TILE];  // half extent along each global axis (0 on the normal)
+    float lmax[2 * GBEM_TILE];
+    float area[2 * GBEM_TILE];
+    int axis[2 * GBEM_TILE];
+    int valid[2 * GBEM_TILE];
+};
+
+__device__ __forceinline__ int ax_p(int k) { return k == 0 ? 1 : 0; }
+__device__ __forceinline__ int ax_q(int k) { return k == 2 ? 1 : 2; }
+
+// Exact near-field entry for slots s (row) and t (column) of the tile.
+__device__ double near_entry(const TileGeo& G, int s, int t)
+{
+    int ki = G.axis[s], kj = G.axis[t];
+    double I = 0.0;
+    if (ki == kj) {
+        double a[2] = {G.lo0[s], G.hi0[s]}, ap[2] = {G.lo0[t], G.hi0[t]};
+        double b[2] = {G.lo1[s], G.hi1[s]}, bp[2] = {G.lo1[t], G.hi1[t]};
+        double w = G.c[s] - G.c[t];
+#pragma unroll
+        for (int al = 0; al < 2; ++al)
+#pragma unroll
+            for (int be = 0; be < 2; ++be)
+#pragma unroll
+                for (int ga = 0; ga < 2; ++ga)
+#pragma unroll
+                    for (int de = 0; de < 2; ++de) {
+                        double f = F_par(a[al] - ap[be], b[ga] - bp[de], w);
+                        I += ((al + be + ga + de) & 1) ? -f : f;
+                    }
+    } else {
+        int sh = 3 - ki - kj;
+        // extents of panel i along the shared axis (p) and along kj (q)
+        bool i_sh_first = (ax_p(ki) == sh);
+        double p[2] = {i_sh_first ? G.lo0[s] : G.lo1[s], i_sh_first ? G.hi0[s] : G.hi1[s]};
+        double q[2] = {i_sh_first ? G.lo1[s] : G.lo0[s], i_sh_first ? G.hi1[s] : G.hi0[s]};
+        bool j_sh_first = (ax_p(kj) == sh);
+        double r[2] = {j_sh_first ? G.lo0[t] : G.lo1[t], j_sh_first ? G.hi0[t] : G.hi1[t]};
+        double tt[2] = {j_sh_first ? G.lo1[t] : G.lo0[t], j_sh_first ? G.hi1[t] : G.hi0[t]};
+        double ci = G.c[s], cj = G.c[t];
+#pragma unroll
+        for (int al = 0; al < 2; ++al)
+#pragma unroll
+            for (int be = 0; be < 2; ++be)
+#pragma unroll
+                for (int ga = 0; ga < 2; ++ga)
+#pragma unroll
+                    for (int de = 0; de < 2; ++de) {
+                        double hv = H_orth(p[al] - r[be], q[ga] - cj, ci - tt[de]);
+                        I += ((al + be + ga + de) & 1) ? -hv : hv;
+                    }
+    }
+    double ai = (G.hi0[s] - G.lo0[s]) * (G.hi1[s] - G.lo1[s]);
+    double aj = (G.hi0[t] - G.lo0[t]) * (G.hi1[t] - G.lo1[t]);
+    return I / (4.0 * kPi * ai * aj);
+}
+
+template <bool MIXED>
+__device__ double far_entry(const TileGeo& G, int s, int t, int n)
+{
+    int ki = G.axis[s], kj = G.axis[t];
+    double sum = 0.0;
+    if (!MIXED) {
+        // centre offsets in FP64
+        double ci[3], cj[3];
+        ci[ki] = G.c[s];
+        ci[ax_p(ki)] = 0.5 * (G.lo0[s] + G.hi0[s]);
+        ci[ax_q(ki)] = 0.5 * (G.lo1[s] + G.hi1[s]);
+        cj[kj] = G.c[t];
+        cj[ax_p(kj)] = 0.5 * (G.lo0[t] + G.hi0[t]);
+        cj[ax_q(kj)] = 0.5 * (G.lo1[t] + G.hi1[t]);
+        double d[3] = {ci[0] - cj[0], ci[1] - cj[1], ci[2] - cj[2]};
+        if (ki == kj) {
+            int p = ax_p(ki), q = ax_q(ki);
+            double ai = 0.5 * (G.hi0[s] - G.lo0[s]), bi = 0.5 * (G.hi1[s] - G.lo1[s]);
+            double aj = 0.5 * (G.hi0[t] - G.lo0[t]), bj = 0.5 * (G.hi1[t] - G.lo1[t]);
+            switch (n) {
+            case 1: sum = 4.0 * rsq64(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
+            case 2: sum = far64_par<2>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 3: sum = far64_par<3>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 4: sum = far64_par<4>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 5: sum = far64_par<5>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            default: sum = far64_par<6>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            }
+        } else {
+            int sh = 3 - ki - kj;
+            // half extents of i along the shared axis and along kj, of j along
+            // the shared axis and along ki
+            bool i_first = (ax_p(ki) == sh), j_first = (ax_p(kj) == sh);
+            double hs_i = i_first ? 0.5 * (G.hi0[s] - G.lo0[s]) : 0.5 * (G.hi1[s] - G.lo1[s]);
+            double hv_i = i_first ? 0.5 * (G.hi1[s] - G.lo1[s]) : 0.5 * (G.hi0[s] - G.lo0[s]);
+            double hs_j = j_first ? 0.5 * (G.hi0[t] - G.lo0[t]) : 0.5 * (G.hi1[t] - G.lo1[t]);
+            double hw_j = j_first ? 0.5 * (G.hi1[t] - G.lo1[t]) : 0.5 * (G.hi0[t] - G.lo0[t]);
+            switch (n) {
+            case 1: sum = 4.0 * rsq64(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
+            case 2: sum = far64_orth<2>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 3: sum = far64_orth<3>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 4: sum = far64_orth<4>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 5: sum = far64_orth<5>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            default: sum = far64_orth<6>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            }
+        }
+    } else {
+        // centre offsets from float (hi, lo) pairs: error about 1 ulp of |d|
+        float d[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) d[e] = (G.chi[e][s] - G.chi[e][t]) + (G.clo[e][s] - G.clo[e][t]);
+        if (ki == kj) {
+            int p = ax_p(ki), q = ax_q(ki);
+            float ai = G.half[p][s], bi = G.half[q][s], aj = G.half[p][t], bj = G.half[q][t];
+            switch (n) {
+            case 1: sum = 4.0 * (double)rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
+            case 2: sum = far32_par<2>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 3: sum = far32_par<3>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 4: sum = far32_par<4>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            case 5: sum = far32_par<5>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            default: sum = far32_par<6>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
+            }
+        } else {
+            int sh = 3 - ki - kj;
+            float hs_i = G.half[sh][s], hs_j = G.half[sh][t];
+            float hv_i = G.half[kj][s], hw_j = G.half[ki][t];
+            switch (n) {
+            case 1: sum = 4.0 * (double)rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
+            case 2: sum = far32_orth<2>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 3: sum = far32_orth<3>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 4: sum = far32_orth<4>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            case 5: sum = far32_orth<5>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            default: sum = far32_orth<6>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
+            }
+        }
+    }
+    // I = (prod of half extents) * sum and |I_i||I_j| = 16 * (same product):
+    // a_ij = sum / (64 pi)
+    return sum * (1.0 / (64.0 * kPi));
+}
+
+constexpr int kThreads = 256;
+constexpr int kPairs = GBEM_TILE * GBEM_TILE;
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, float q_near,
+                                                           double* __restrict__ A64,
+                                                           float* __restrict__ A32,
+                                                           unsigned long long* __restrict__ counts)
+{
+    __shared__ TileGeo G;
+    __shared__ unsigned short nlist[kPairs];
+    __shared__ int n_par, n_orth;
+    __shared__ int cnt[GBEM_GL_MAX + 1];
+
+    // lower-triangular tile coordinates (TI >= TJ) from the linear block index
+    long long b = blockIdx.x;
+    int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
+    while ((long long)TI * (TI + 1) / 2 > b) --TI;
+    int TJ = (int)(b - (long long)TI * (TI + 1) / 2);
+    const int n = g.n;
+    const int tid = threadIdx.x;
+
+    if (tid < 2 * GBEM_TILE) {
+        int slot = tid;
+        int idx = (slot < GBEM_TILE) ? TI * GBEM_TILE + slot : TJ * GBEM_TILE + (slot - GBEM_TILE);
+        int ok = idx < n;
+        G.valid[slot] = ok;
+        if (ok) {
+            int k = g.axis[idx];
+            double c = g.c[idx], l0 = g.lo0[idx], h0 = g.hi0[idx], l1 = g.lo1[idx], h1 = g.hi1[idx];
+            G.axis[slot] = k;
+            G.c[slot] = c;
+            G.lo0[slot] = l0;
+            G.hi0[slot] = h0;
+            G.lo1[slot] = l1;
+            G.hi1[slot] = h1;
+            int p = ax_p(k), q = ax_q(k);
+            double ctr[3], lo[3], hi[3];
+            ctr[k] = c;
+            lo[k] = c;
+            hi[k] = c;
+            ctr[p] = 0.5 * (l0 + h0);
+            lo[p] = l0;
+            hi[p] = h0;
+            ctr[q] = 0.5 * (l1 + h1);
+            lo[q] = l1;
+            hi[q] = h1;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                float chi = (float)ctr[e];
+                G.chi[e][slot] = chi;
+                G.clo[e][slot] = (float)(ctr[e] - (double)chi);
+                G.blo[e][slot] = (float)lo[e];
+                G.bhi[e][slot] = (float)hi[e];
+                G.half[e][slot] = (float)(0.5 * (hi[e] - lo[e]));
+            }
+            G.lmax[slot] = (float)fmax(h0 - l0, h1 - l1);
+            G.area[slot] = (float)((h0 - l0) * (h1 - l1));
+        }
+    }
+    if (tid == 0) {
+        n_par = 0;
+        n_orth = 0;
+    }
+    if (tid <= GBEM_GL_MAX) cnt[tid] = 0;
+    __syncthreads();
+
+    const int mode = MIXED ? 1 : 0;
+    // pass 1: classify; evaluate far pairs, queue near pairs
+    for (int e = tid; e < kPairs; e += kThreads) {
+        int ii = e & (GBEM_TILE - 1), jj = e >> 5;
+        int s = ii, t = GBEM_TILE + jj;
+        if (!G.valid[s] || !G.valid[t]) continue;
+        if (TI == TJ && ii < jj) continue;
+        float g2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float gd = fmaxf(0.0f, fmaxf(G.blo[d][t] - G.bhi[d][s], G.blo[d][s] - G.bhi[d][t]));
+            g2 = fmaf(gd, gd, g2);
+        }
+        float L = fmaxf(G.lmax[s], G.lmax[t]);
+        float gap = sqrtf(g2);
+        float q = gap / L;
+        // The closed form loses about eps * R^4 / (|I_i| |I_j|) to cancellation
+        // between its 16 corner terms (R: largest corner distance); keep it
+        // below 2e-12 relative, else use quadrature when an order fits.
+        float R = gap + G.lmax[s] + G.lmax[t];
+        bool cf_ok = (q < q_near) && (R * R * R * R <= 1.8e4f * G.area[s] * G.area[t]);
+        int order = 0;
+        if (MIXED ? (q >= q_near) : !cf_ok) {
+#pragma unroll
+            for (int m = GBEM_GL_MAX; m >= 1; --m)
+                if (q >= c_qmin[mode][m]) order = m;
+        }
+        if (order == 0) {
+            if (G.axis[s] == G.axis[t]) {
+                int slot = atomicAdd(&n_par, 1);
+                nlist[slot] = (unsigned short)e;
+            } else {
+                int slot = atomicAdd(&n_orth, 1);
+                nlist[kPairs - 1 - slot] = (unsigned short)e;
+            }
+            continue;
+        }
+        double v = far_entry<MIXED>(G, s, t, order);
+        size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
+        A64[i + j * (size_t)np] = v;
+        if (MIXED) A32[i + j * (size_t)np] = (float)v;
+        atomicAdd(&cnt[order], 1);
+    }
+    __syncthreads();
+    // pass 2: near pairs, parallel ones first then perpendicular ones
+    const int tot = n_par + n_orth;
+    for (int x = tid; x < tot; x += kThreads) {
+        int e = (x < n_par) ? nlist[x] : nlist[kPairs - 1 - (x - n_par)];
+        int ii = e & (GBEM_TILE - 1), jj = e >> 5;
+        double v = near_entry(G, ii, GBEM_TILE + jj);
+        size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
+        A64[i + j * (size_t)np] = v;
+        if (MIXED) A32[i + j * (size_t)np] = (float)v;
+    }
+    if (tid == 0) cnt[0] = tot;
+    __syncthreads();
+    if (tid <= GBEM_GL_MAX && cnt[tid]) atomicAdd(&counts[tid], (unsigned long long)cnt[tid]);
+}
+
+// Identity in the padding rows (lower part): A[r][c] = (r == c) for r >= n.
+__global__ void pad_identity(double* A64, float* A32, int n, int np)
+{
+    long long total = (long long)(np - n) * np;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int r = n + (int)(e % (np - n));
+        int c = (int)(e / (np - n));
+        if (c > r) continue;
+        double v = (r == c) ? 1.0 : 0.0;
+        A64[r + (size_t)c * np] = v;
+        if (A32) A32[r + (size_t)c * np] = (float)v;
+    }
+}
+
+__global__ void copy_lower(const double* __restrict__ A, double* __restrict__ L, int np)
+{
+    size_t total = (size_t)np * np;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t r = e % np, c = e / np;
+        if (r >= c) L[e] = A[e];
+    }
+}
+
+// Gauss-Legendre nodes on [-1,1] from Newton's method on the three-term
+// Legendre recurrence (host side, computed once per process).
+void gl_nodes(int n, double* x, double* w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) {
+                // one more evaluation at the converged root for the weight
+                p0 = 1.0;
+                p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = pk;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                break;
+            }
+        }
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+cudaError_t gl_upload()
+{
+    double hx[GBEM_GL_MAX + 1][GBEM_GL_MAX] = {}, hw[GBEM_GL_MAX + 1][GBEM_GL_MAX] = {};
+    float fx[GBEM_GL_MAX + 1][GBEM_GL_MAX] = {}, fw[GBEM_GL_MAX + 1][GBEM_GL_MAX] = {};
+    hx[1][0] = 0.0;
+    hw[1][0] = 2.0;
+    for (int n = 2; n <= GBEM_GL_MAX; ++n) gl_nodes(n, hx[n], hw[n]);
+    for (int n = 1; n <= GBEM_GL_MAX; ++n)
+        for (int i = 0; i < n; ++i) {
+            fx[n][i] = (float)hx[n][i];
+            fw[n][i] = (float)hw[n][i];
+        }
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(c_glx, hx, sizeof(hx))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_glw, hw, sizeof(hw))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_glxf, fx, sizeof(fx))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_glwf, fw, sizeof(fw));
+}
+
+cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
+                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s)
+{
+    if (g.n <= 0) return cudaSuccess;
+    long long nt = (g.n + GBEM_TILE - 1) / GBEM_TILE;
+    long long tiles = nt * (nt + 1) / 2;
+    if (prec == GBEM_MIXED)
+        assemble_tiles<true><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, A32, counts);
+    else
+        assemble_tiles<false><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, nullptr,
+                                                                   counts);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s)
+{
+    if (np == n) return cudaSuccess;
+    pad_identity<<<256, 256, 0, s>>>(A64, A32, n, np);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_lower(const double* A, double* L, int np, cudaStream_t s)
+{
+    copy_lower<<<1024, 256, 0, s>>>(A, L, np);
+    count_launch();
+    return cudaGetLastError();
+}

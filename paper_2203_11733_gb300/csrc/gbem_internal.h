@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libgbem.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gbem.h"
+
+// Matrices are padded to a multiple of this with the identity.
+constexpr int GBEM_PAD = 128;
+// Assembly tile edge (panels).
+constexpr int GBEM_TILE = 32;
+// Largest Gauss-Legendre order used by the far-field rule.
+constexpr int GBEM_GL_MAX = 6;
+
+struct gbem_ctx_s {
+    int device = -1;
+    int num_sms = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    gbem_alloc_fn alloc = nullptr;
+    gbem_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    std::string err;
+    gbem_tuning tune{};
+    bool gl_uploaded = false;
+    // tracing
+    bool timing = false;
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double ms[GBEM_NPHASE] = {};
+    long long calls[GBEM_NPHASE] = {};
+};
+
+// Kernels launched by the library in this process.
+extern std::atomic<long long> g_gbem_launches;
+inline void count_launch(long long k = 1) { g_gbem_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Device view of a mesh: structure of arrays, one entry per panel.
+struct DevPanels {
+    const double* c = nullptr;    // plane coordinate
+    const double* lo0 = nullptr;  // extents on the first in-plane axis
+    const double* hi0 = nullptr;
+    const double* lo1 = nullptr;  // extents on the second in-plane axis
+    const double* hi1 = nullptr;
+    const int8_t* axis = nullptr; // normal axis
+    const int32_t* cond = nullptr;// conductor index 0..n_c-1
+    int n = 0;
+};
+
+struct gbem_mesh_s {
+    gbem_ctx* ctx = nullptr;
+    int n = 0;
+    int n_cond = 0;
+    std::vector<int8_t> axis;
+    std::vector<double> geo;        // 5 per panel
+    std::vector<int32_t> cond;      // conductor index (0..n_c-1)
+    std::vector<int32_t> cond_ids;  // conductor index -> caller's id
+    void* dbuf = nullptr;
+    size_t dbytes = 0;
+    DevPanels dev;
+};
+
+struct gbem_matrix_s {
+    gbem_ctx* ctx = nullptr;
+    gbem_mesh_t* mesh = nullptr;
+    int n = 0;
+    int np = 0;                 // padded order
+    int nb = 64;                // factor block
+    gbem_precision prec = GBEM_FP64;
+    double* A64 = nullptr;      // np x np col-major, lower triangle
+    float* A32 = nullptr;       // mixed: FP32 copy, factored in place
+    double* L64 = nullptr;      // FP64 mode: the factor
+    void* Linv = nullptr;       // inverses of the diagonal blocks (T)
+    int* dflags = nullptr;      // [0] not-SPD pivot, [1] IR done, [2] IR iters, [3] spare
+    unsigned long long* dcounts = nullptr; // pair class counts (8)
+    double* dnorm = nullptr;    // IR: [0] residual, [1..] scratch
+    // solve work buffers (np x cap_rhs)
+    int cap_rhs = 0;
+    double* X = nullptr;
+    double* R = nullptr;
+    double* B = nullptr;
+    void* W = nullptr;          // T: triangular-solve work
+    bool factored = false;
+    cudaStream_t last = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+};
+
+// ---- context helpers (api.cpp)
+gbem_status ctx_fail(gbem_ctx* ctx, gbem_status st, const std::string& msg);
+void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s);
+void ctx_free(gbem_ctx* ctx, void* p, size_t bytes, cudaStream_t s);
+
+// ---- mesher (mesh.cpp)
+gbem_status mesh_build_boxes(const gbem_box* boxes, int nbox, const gbem_mesh_params* p,
+                             std::vector<int8_t>& axis, std::vector<double>& geo,
+                             std::vector<int32_t>& cond_raw, std::string& err);
+void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond);
+void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<double>& nodes);
+
+// ---- kernels (assemble.cu, factor.cu, solve.cu)
+cudaError_t gl_upload();
+cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
+                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s);
+cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
+cudaError_t launch_copy_lower(const double* A, double* L, int np, cudaStream_t s);
+cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s);
+cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, cudaStream_t s);
+cudaError_t launch_trsv_f64(const double* L, const double* Linv, int np, int nb, double* W, int nrhs,
+                            cudaStream_t s);
+cudaError_t launch_trsv_f32(const float* L, const float* Linv, int np, int nb, float* W, int nrhs,
+                            cudaStream_t s);
+cudaError_t launch_pack_rhs(const double* B, int ldb, int n, int np, int nrhs, double* Bp,
+                            cudaStream_t s);
+cudaError_t launch_unpack(const double* Xp, int np, int n, int nrhs, double* X, int ldx,
+                          cudaStream_t s);
+cudaError_t launch_ir_begin(const double* Bp, int np, int nrhs, double* X, double* R, double* norm,
+                            int* flags, cudaStream_t s);
+cudaError_t launch_to_f32(const double* R, int np, int nrhs, float* W, const int* done,
+                          cudaStream_t s);
+cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, const int* done,
+                           cudaStream_t s);
+cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, int nb, float* W,
+                                    int nrhs, const int* done, cudaStream_t s);
+cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,
+                            double* R, const int* done, cudaStream_t s);
+cudaError_t launch_ir_check(const double* R, const double* Bp, int np, int nrhs, double* norm,
+                            double tol, int* flags, cudaStream_t s);
+cudaError_t launch_indicator_rhs(const int32_t* cond, int n, int np, int n_cond, double* Bp,
+                                 cudaStream_t s);
+cudaError_t launch_capacitance(const int32_t* cond, int n, int np, int n_cond, const double* X,
+                               double scale, double* C, cudaStream_t s);

@@ -1,0 +1,197 @@
+// Boundary partition of cuboid conductors into axis-aligned rectangular
+// panels (Wu & Li, Sec. 3.1: dOmega = U_j I_j; Sec. 3.3: every conductor is
+// built from cuboids, so every panel is an axis-aligned rectangle).
+//
+// Each box edge is divided on its own; a face is cut on the tensor grid of
+// its two edge divisions.  Panels are then ordered by conductor and, inside a
+// conductor, by the Morton code of the panel centre, so that a tile of
+// consecutive panels is spatially compact (near pairs gather close to the
+// diagonal of the matrix, and far tiles see similar distances).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gbem_internal.h"
+
+void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<double>& nodes)
+{
+    nodes.clear();
+    const double L = hi - lo;
+    const double h = p->h;
+    auto uniform = [&]() {
+        int n = std::max(1, (int)std::ceil(L / h - 1e-9));
+        for (int k = 0; k < n; ++k) nodes.push_back(lo + (L * k) / n);
+        nodes.push_back(hi);
+    };
+    if (p->ratio <= 1.0 || p->h_min <= 0.0 || p->h_min >= h) {
+        uniform();
+        return;
+    }
+    std::vector<double> sizes;
+    for (double s = p->h_min; s < h; s = s * p->ratio) sizes.push_back(s);
+    int m = (int)sizes.size();
+    while (m > 0) {
+        double tot = 0.0;
+        for (int k = 0; k < m; ++k) tot += sizes[k];
+        if (2.0 * tot <= L) break;
+        --m;
+    }
+    if (m == 0) {
+        uniform();
+        return;
+    }
+    std::vector<double> left{lo}, right{hi};
+    double acc = lo;
+    for (int k = 0; k < m; ++k) {
+        acc = acc + sizes[k];
+        left.push_back(acc);
+    }
+    acc = hi;
+    for (int k = 0; k < m; ++k) {
+        acc = acc - sizes[k];
+        right.push_back(acc);
+    }
+    std::reverse(right.begin(), right.end());
+    const double xl = left.back(), xr = right.front();
+    const double M = xr - xl;
+    nodes.assign(left.begin(), left.end() - 1);
+    if (M > 1e-12 * L) {
+        int nmid = std::max(1, (int)std::ceil(M / h - 1e-9));
+        for (int k = 0; k < nmid; ++k) nodes.push_back(xl + (M * k) / nmid);
+    }
+    nodes.insert(nodes.end(), right.begin(), right.end());
+}
+
+gbem_status mesh_build_boxes(const gbem_box* boxes, int nbox, const gbem_mesh_params* p,
+                             std::vector<int8_t>& axis, std::vector<double>& geo,
+                             std::vector<int32_t>& cond_raw, std::string& err)
+{
+    if (nbox <= 0 || !boxes || !p) {
+        err = "gbem_mesh: no boxes";
+        return GBEM_ERR_ARG;
+    }
+    if (!(p->h > 0.0) || !std::isfinite(p->h)) {
+        err = "gbem_mesh: h must be positive";
+        return GBEM_ERR_ARG;
+    }
+    for (int b = 0; b < nbox; ++b)
+        for (int d = 0; d < 3; ++d)
+            if (!(boxes[b].hi[d] > boxes[b].lo[d]) || !std::isfinite(boxes[b].lo[d]) ||
+                !std::isfinite(boxes[b].hi[d])) {
+                err = "gbem_mesh: box " + std::to_string(b) + " is empty or not finite";
+                return GBEM_ERR_MESH;
+            }
+    // boxes may neither overlap nor touch: touching faces would be interior
+    for (int a = 0; a < nbox; ++a)
+        for (int b = a + 1; b < nbox; ++b) {
+            bool sep = false;
+            for (int d = 0; d < 3; ++d)
+                if (boxes[a].hi[d] < boxes[b].lo[d] || boxes[b].hi[d] < boxes[a].lo[d]) sep = true;
+            if (!sep) {
+                err = "gbem_mesh: boxes " + std::to_string(a) + " and " + std::to_string(b) +
+                      " overlap or touch";
+                return GBEM_ERR_MESH;
+            }
+        }
+    // estimate size first so that a runaway h is refused before allocating
+    double est = 0.0;
+    std::vector<double> n0, n1;
+    for (int b = 0; b < nbox; ++b)
+        for (int k = 0; k < 3; ++k) {
+            int pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+            mesh_divide(boxes[b].lo[pa], boxes[b].hi[pa], p, n0);
+            mesh_divide(boxes[b].lo[qa], boxes[b].hi[qa], p, n1);
+            est += 2.0 * (double)(n0.size() - 1) * (double)(n1.size() - 1);
+        }
+    if (est > 2.0e6) {
+        err = "gbem_mesh: more than 2e6 panels requested";
+        return GBEM_ERR_ARG;
+    }
+    axis.clear();
+    geo.clear();
+    cond_raw.clear();
+    for (int b = 0; b < nbox; ++b) {
+        const gbem_box& B = boxes[b];
+        for (int k = 0; k < 3; ++k) {
+            int pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+            mesh_divide(B.lo[pa], B.hi[pa], p, n0);
+            mesh_divide(B.lo[qa], B.hi[qa], p, n1);
+            for (int side = 0; side < 2; ++side) {
+                double plane = side ? B.hi[k] : B.lo[k];
+                for (size_t a = 0; a + 1 < n0.size(); ++a)
+                    for (size_t c = 0; c + 1 < n1.size(); ++c) {
+                        axis.push_back((int8_t)k);
+                        geo.push_back(plane);
+                        geo.push_back(n0[a]);
+                        geo.push_back(n0[a + 1]);
+                        geo.push_back(n1[c]);
+                        geo.push_back(n1[c + 1]);
+                        cond_raw.push_back(B.conductor);
+                    }
+            }
+        }
+    }
+    return GBEM_OK;
+}
+
+static uint64_t spread3(uint64_t x)
+{
+    x &= 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+// Reorder panels by conductor index, then by Morton code of the centre.
+void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond)
+{
+    const size_t n = axis.size();
+    if (n == 0) return;
+    std::vector<double> ctr(3 * n);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = 0; i < n; ++i) {
+        int k = axis[i], pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+        const double* g = &geo[5 * i];
+        ctr[3 * i + k] = g[0];
+        ctr[3 * i + pa] = 0.5 * (g[1] + g[2]);
+        ctr[3 * i + qa] = 0.5 * (g[3] + g[4]);
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], ctr[3 * i + d]);
+            hi[d] = std::max(hi[d], ctr[3 * i + d]);
+        }
+    }
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    std::vector<uint64_t> code(n);
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t m = 0;
+        for (int d = 0; d < 3; ++d) {
+            double t = (ctr[3 * i + d] - lo[d]) / ext;
+            uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+            m |= spread3(q) << d;
+        }
+        code[i] = m;
+    }
+    std::vector<size_t> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        if (cond[a] != cond[b]) return cond[a] < cond[b];
+        return code[a] < code[b];
+    });
+    std::vector<int8_t> ax2(n);
+    std::vector<double> g2(5 * n);
+    std::vector<int32_t> c2(n);
+    for (size_t t = 0; t < n; ++t) {
+        ax2[t] = axis[idx[t]];
+        c2[t] = cond[idx[t]];
+        for (int e = 0; e < 5; ++e) g2[5 * t + e] = geo[5 * idx[t] + e];
+    }
+    axis.swap(ax2);
+    geo.swap(g2);
+    cond.swap(c2);
+}

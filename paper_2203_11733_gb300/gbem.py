@@ -1,0 +1,336 @@
+"""Python binding of libgbem (include/gbem.h): argument marshalling only.
+
+Every step of the extraction runs in the library's CUDA kernels; this module
+converts Python/numpy/torch arguments to plain pointers and sizes and raises
+on error statuses.  Device memory for handles comes from PyTorch's caching
+allocator through the ABI's allocator callback.  There is no CPU fallback:
+if ``libgbem.so`` has not been built, importing the library fails loudly.
+
+Names follow the C ABI: ``gbem_create``, ``gbem_mesh``, ``gbem_assemble``,
+``gbem_factor``, ``gbem_solve``, ``gbem_capacitance`` ...; the classes below
+are small conveniences over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GBEM_OK = 0
+STATUS = {
+    0: "GBEM_OK", -1: "GBEM_ERR_ARG", -2: "GBEM_ERR_OOM", -3: "GBEM_ERR_CUDA",
+    -4: "GBEM_ERR_NOT_SPD", -5: "GBEM_ERR_TIMEOUT", -6: "GBEM_ERR_NOCONV", -7: "GBEM_ERR_MESH",
+    -8: "GBEM_ERR_STATE", -9: "GBEM_ERR_NODEV",
+}
+GBEM_FP64 = 0
+GBEM_MIXED = 1
+EPS0 = 8.8541878128e-12
+
+
+class GbemError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("conductor", ctypes.c_int32)]
+
+
+class _MeshParams(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("ratio", ctypes.c_double), ("h_min", ctypes.c_double)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("q_near_fp64", ctypes.c_double), ("q_near_mixed", ctypes.c_double),
+                ("ir_tol", ctypes.c_double), ("ir_max_iter", ctypes.c_int), ("nb", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+# symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "gbem_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ALLOC_FN, FREE_FN, _P]),
+    "gbem_destroy": (None, [_P]),
+    "gbem_last_error": (ctypes.c_char_p, [_P]),
+    "gbem_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_Tuning)]),
+    "gbem_bytes_in_use": (ctypes.c_size_t, [_P]),
+    "gbem_mesh": (ctypes.c_int, [_P, ctypes.POINTER(_Box), ctypes.c_int, ctypes.POINTER(_MeshParams),
+                                 ctypes.POINTER(_P)]),
+    "gbem_mesh_from_panels": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(_P)]),
+    "gbem_mesh_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "gbem_mesh_panels": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gbem_mesh_destroy": (None, [_P]),
+    "gbem_assemble": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "gbem_factor": (ctypes.c_int, [_P, _P]),
+    "gbem_solve": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int), _P]),
+    "gbem_capacitance": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "gbem_matrix_download": (ctypes.c_int, [_P, _P]),
+    "gbem_matrix_status": (ctypes.c_int, [_P]),
+    "gbem_matrix_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
+    "gbem_matrix_destroy": (None, [_P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libgbem.so (raises if it is missing and building is not asked for)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(
+                    f"libgbem.so not built ({path}); run __graft_entry__.build() or "
+                    "python paper_2203_11733_gb300/build.py")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (or device=-1: host-only, meshing
+    only).  ``torch_alloc`` routes device memory through PyTorch's caching
+    allocator; otherwise the library uses cudaMalloc."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, torch_alloc: bool = True):
+        self.lib = load()
+        self.device = device
+        self._cb = None
+        alloc, free = ALLOC_FN(), FREE_FN()
+        if device >= 0 and torch_alloc:
+            import torch
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+                except Exception:   # refusal is reported through a NULL pointer
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            alloc, free = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._cb = (alloc, free)
+        h = ctypes.c_void_p()
+        st = self.lib.gbem_create(ctypes.byref(h), int(device), int(hbm_budget), alloc, free, None)
+        if st != GBEM_OK:
+            raise GbemError(st, "gbem_create failed")
+        self.h = h
+
+    def check(self, st: int):
+        if st != GBEM_OK:
+            msg = self.lib.gbem_last_error(self.h)
+            raise GbemError(st, msg.decode() if msg else "")
+
+    def set_tuning(self, q_near_fp64=0.0, q_near_mixed=0.0, ir_tol=0.0, ir_max_iter=0, nb=0):
+        t = _Tuning(q_near_fp64, q_near_mixed, ir_tol, ir_max_iter, nb)
+        self.check(self.lib.gbem_set_tuning(self.h, ctypes.byref(t)))
+
+    def bytes_in_use(self) -> int:
+        return int(self.lib.gbem_bytes_in_use(self.h))
+
+    def mesh(self, boxes, params) -> "Mesh":
+        return gbem_mesh(self, boxes, params)
+
+    def mesh_from_panels(self, axis, geo, cond) -> "Mesh":
+        return gbem_mesh_from_panels(self, axis, geo, cond)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.h = ctx, handle
+        n, nc = ctypes.c_int(), ctypes.c_int()
+        ctx.check(ctx.lib.gbem_mesh_info(handle, ctypes.byref(n), ctypes.byref(nc)))
+        self.n, self.n_cond = n.value, nc.value
+
+    def panels(self):
+        """(axis int8[n], geo float64[n,5], cond int32[n], conductor ids int32[n_c])"""
+        axis = np.empty(self.n, np.int8)
+        geo = np.empty((self.n, 5), np.float64)
+        cond = np.empty(self.n, np.int32)
+        ids = np.empty(self.n_cond, np.int32)
+        self.ctx.check(self.ctx.lib.gbem_mesh_panels(self.h, _ptr(axis), _ptr(geo), _ptr(cond), _ptr(ids)))
+        return axis, geo, cond, ids
+
+    def assemble(self, precision=GBEM_FP64, stream=None) -> "Matrix":
+        return gbem_assemble(self, precision, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.gbem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    def __init__(self, mesh: Mesh, handle, precision):
+        self.mesh, self.ctx, self.h, self.precision = mesh, mesh.ctx, handle, precision
+        self.n = mesh.n
+
+    def factor(self, stream=None):
+        gbem_factor(self, stream)
+
+    def solve(self, B, X=None, stream=None):
+        return gbem_solve(self, B, X, stream)
+
+    def capacitance(self, eps_r: float, stream=None):
+        return gbem_capacitance(self.mesh, self, eps_r, stream)
+
+    def download(self) -> np.ndarray:
+        A = np.empty((self.n, self.n), np.float64, order="F")
+        self.ctx.check(self.ctx.lib.gbem_matrix_download(self.h, _ptr(A)))
+        return A
+
+    def status(self):
+        self.ctx.check(self.ctx.lib.gbem_matrix_status(self.h))
+
+    def info(self):
+        n = ctypes.c_int()
+        counts = np.zeros(7, np.int64)
+        self.ctx.check(self.ctx.lib.gbem_matrix_info(self.h, ctypes.byref(n), _ptr(counts)))
+        return n.value, counts
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.gbem_matrix_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- ABI-named calls
+
+def gbem_create(device: int = 0, hbm_budget: int = 0, torch_alloc: bool = True) -> Context:
+    return Context(device, hbm_budget, torch_alloc)
+
+
+def gbem_mesh(ctx: Context, boxes, params) -> Mesh:
+    arr = (_Box * len(boxes))()
+    for i, (lo, hi, c) in enumerate(boxes):
+        arr[i].lo[:] = [float(v) for v in lo]
+        arr[i].hi[:] = [float(v) for v in hi]
+        arr[i].conductor = int(c)
+    p = _MeshParams(float(params["h"]), float(params.get("ratio", 1.0)), float(params.get("h_min", 0.0)))
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.gbem_mesh(ctx.h, arr, len(boxes), ctypes.byref(p), ctypes.byref(h)))
+    return Mesh(ctx, h)
+
+
+def gbem_mesh_from_panels(ctx: Context, axis, geo, cond) -> Mesh:
+    axis = np.ascontiguousarray(axis, dtype=np.int8)
+    geo = np.ascontiguousarray(geo, dtype=np.float64).reshape(-1, 5)
+    cond = np.ascontiguousarray(cond, dtype=np.int32)
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.gbem_mesh_from_panels(ctx.h, len(axis), _ptr(axis), _ptr(geo), _ptr(cond),
+                                            ctypes.byref(h)))
+    return Mesh(ctx, h)
+
+
+def gbem_assemble(mesh: Mesh, precision=GBEM_FP64, stream=None) -> Matrix:
+    h = ctypes.c_void_p()
+    ctx = mesh.ctx
+    ctx.check(ctx.lib.gbem_assemble(mesh.h, int(precision), _stream_handle(stream), ctypes.byref(h)))
+    return Matrix(mesh, h, precision)
+
+
+def gbem_factor(mat: Matrix, stream=None):
+    mat.ctx.check(mat.ctx.lib.gbem_factor(mat.h, _stream_handle(stream)))
+
+
+def gbem_solve(mat: Matrix, B, X=None, stream=None):
+    """Solve A X = B on device; B, X are torch float64 CUDA tensors of shape
+    (N, nrhs) in column-major layout (i.e. B.t() contiguous) or (N,).
+    Returns (X, refinement iterations)."""
+    import torch
+    if B.dim() == 1:
+        B = B[:, None]
+    Bc = B.t().contiguous()          # (nrhs, N) row-major == (N, nrhs) column-major
+    n, nrhs = B.shape
+    Xc = torch.empty_like(Bc) if X is None else X.t()
+    it = ctypes.c_int(0)
+    mat.ctx.check(mat.ctx.lib.gbem_solve(mat.h, ctypes.c_void_p(Bc.data_ptr()), nrhs, n,
+                                         ctypes.c_void_p(Xc.data_ptr()), n, ctypes.byref(it),
+                                         _stream_handle(stream)))
+    return Xc.t(), it.value
+
+
+def gbem_capacitance(mesh: Mesh, mat: Matrix, eps_r: float, stream=None, want_residual: bool = True):
+    """Maxwell capacitance matrix in farads (n_c x n_c, ascending conductor
+    ids) and the final relative residual."""
+    C = np.empty((mesh.n_cond, mesh.n_cond), np.float64)
+    r = ctypes.c_double(0.0)
+    mesh.ctx.check(mesh.ctx.lib.gbem_capacitance(mesh.h, mat.h, float(eps_r), _ptr(C),
+                                                 ctypes.byref(r) if want_residual else None,
+                                                 _stream_handle(stream)))
+    return C, r.value
+
+
+def extract(ctx: Context, boxes, params, eps_r: float, precision=GBEM_FP64, stream=None):
+    """Mesh, assemble, factor, solve and reduce: one full extraction."""
+    mesh = gbem_mesh(ctx, boxes, params)
+    try:
+        mat = gbem_assemble(mesh, precision, stream)
+        try:
+            return gbem_capacitance(mesh, mat, eps_r, stream)
+        finally:
+            mat.close()
+    finally:
+        mesh.close()
