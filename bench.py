@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=200000)
+    ap.add_argument("--profile", default=None, choices=["mixed", "fp64"],
+                    help="one warm-up and one extraction in that precision, nothing else "
+                         "(for ncu captures)")
     return ap.parse_args()
 
 
@@ -214,6 +217,18 @@ def run_ours(args):
         C, _ = gbem.gbem_capacitance(mesh, mat, eps_r, stream, want_residual=False)
         mat.close()
         return C
+
+    if args.profile:
+        prec = gbem.GBEM_MIXED if args.profile == "mixed" else gbem.GBEM_FP64
+        step(prec)
+        torch.cuda.synchronize()
+        C = step(prec)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": args.profile, "n_panels": n, "C": C.tolist()}))
+        mesh.close()
+        ctx.close()
+        return
 
     def timed(fn, k, flush_between=True):
         """k steps timed with CUDA events on the launching stream, L2 flushed
