@@ -12,9 +12,11 @@ are small conveniences over them.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -55,6 +57,17 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 _lib = None
 _lock = threading.Lock()
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # release handles while the allocator (PyTorch) is still alive
+    for c in list(_live_contexts):
+        try:
+            c.close()
+        except Exception:
+            pass
 
 # symbol -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -134,6 +147,8 @@ class Context:
         self.lib = load()
         self.device = device
         self._cb = None
+        self.h = None
+        self._children = weakref.WeakSet()
         alloc, free = ALLOC_FN(), FREE_FN()
         if device >= 0 and torch_alloc:
             import torch
@@ -154,6 +169,7 @@ class Context:
         if st != GBEM_OK:
             raise GbemError(st, "gbem_create failed")
         self.h = h
+        _live_contexts.add(self)
 
     def check(self, st: int):
         if st != GBEM_OK:
@@ -174,7 +190,14 @@ class Context:
         return gbem_mesh_from_panels(self, axis, geo, cond)
 
     def close(self):
+        """Destroy the context; matrices and meshes made from it go first."""
         if getattr(self, "h", None):
+            kids = list(self._children)
+            for k in kids:
+                if isinstance(k, Matrix):
+                    k.close()
+            for k in kids:
+                k.close()
             self.lib.gbem_destroy(self.h)
             self.h = None
 
@@ -188,6 +211,7 @@ class Context:
 class Mesh:
     def __init__(self, ctx: Context, handle):
         self.ctx, self.h = ctx, handle
+        ctx._children.add(self)
         n, nc = ctypes.c_int(), ctypes.c_int()
         ctx.check(ctx.lib.gbem_mesh_info(handle, ctypes.byref(n), ctypes.byref(nc)))
         self.n, self.n_cond = n.value, nc.value
@@ -206,7 +230,8 @@ class Mesh:
 
     def close(self):
         if getattr(self, "h", None):
-            self.ctx.lib.gbem_mesh_destroy(self.h)
+            if self.ctx.h is not None:
+                self.ctx.lib.gbem_mesh_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -220,6 +245,7 @@ class Matrix:
     def __init__(self, mesh: Mesh, handle, precision):
         self.mesh, self.ctx, self.h, self.precision = mesh, mesh.ctx, handle, precision
         self.n = mesh.n
+        mesh.ctx._children.add(self)
 
     def factor(self, stream=None):
         gbem_factor(self, stream)
@@ -246,7 +272,8 @@ class Matrix:
 
     def close(self):
         if getattr(self, "h", None):
-            self.ctx.lib.gbem_matrix_destroy(self.h)
+            if self.ctx.h is not None:
+                self.ctx.lib.gbem_matrix_destroy(self.h)
             self.h = None
 
     def __del__(self):
