@@ -113,6 +113,7 @@ typedef struct gbem_matrix_s gbem_matrix_t;
  * hold at once (0 = no cap).  alloc/free may be NULL (cudaMalloc/cudaFree). */
 gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget,
                         gbem_alloc_fn alloc, gbem_free_fn free_fn, void* user);
+/* Destroy a context.  Its meshes and matrices must be destroyed first. */
 void gbem_destroy(gbem_ctx* ctx);
 const char* gbem_last_error(const gbem_ctx* ctx);
 gbem_status gbem_set_tuning(gbem_ctx* ctx, const gbem_tuning* t);
@@ -165,6 +166,25 @@ gbem_status gbem_factor(gbem_matrix_t* mat, gbem_stream stream);
  * is not NULL the call waits for the stream and stores the iterations used. */
 gbem_status gbem_solve(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ldb,
                        double* X_dev, int ldx, int* ir_iters, gbem_stream stream);
+
+/* Size in bytes of the fixed device scratch used by gbem_solve_noalloc. */
+#define GBEM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* gbem_solve without any device allocation.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory at solve time -- a
+ * serving worker that reserved its HBM budget up front, an application whose
+ * device memory belongs to its own pool and forbids library cudaMalloc calls,
+ * or a latency-critical loop that must not risk the device synchronisation
+ * cudaMalloc/cudaFree can cause.  Arguments and results are those of
+ * gbem_solve (the matrix must be factored).  The work buffers live in one
+ * file-scope device array of GBEM_NOALLOC_SCRATCH_BYTES that every GPU using
+ * the library holds until the process exits; a call needing more
+ * (5 * 8 * padded N * nrhs bytes plus 256) fails with GBEM_ERR_ARG.  The first
+ * call on a device looks up the array's device address (call it once before
+ * any stream capture).  All calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller. */
+gbem_status gbem_solve_noalloc(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ldb,
+                               double* X_dev, int ldx, int* ir_iters, gbem_stream stream);
 
 /* Maxwell capacitance matrix in farads, n_c x n_c row-major into C_host:
  * C[m][k] = charge on conductor m with conductor k at 1 V and the others at
