@@ -179,10 +179,12 @@ gbem_status gbem_solve(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ld
  * gbem_solve (the matrix must be factored).  The work buffers live in one
  * file-scope device array of GBEM_NOALLOC_SCRATCH_BYTES that every GPU using
  * the library holds until the process exits; a call needing more
- * (5 * 8 * padded N * nrhs bytes plus 256) fails with GBEM_ERR_ARG.  The first
- * call on a device looks up the array's device address (call it once before
- * any stream capture).  All calls share the array: calls that overlap on the
- * GPU race and must be serialised by the caller. */
+ * (5 * 8 * padded N * nrhs bytes plus 256 plus 4 bytes per 64 rows, each term
+ * rounded up to 256) fails with GBEM_ERR_ARG.  The first call on a device
+ * looks up the array's device address (call it once before any stream
+ * capture).  The call waits for its stream before returning.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by the
+ * caller. */
 gbem_status gbem_solve_noalloc(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ldb,
                                double* X_dev, int ldx, int* ir_iters, gbem_stream stream);
 

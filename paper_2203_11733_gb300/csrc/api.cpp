@@ -162,7 +162,9 @@ gbem_status solve_padded(gbem_matrix_t* m, int nrhs, cudaStream_t s, int* iters,
         if (!cuda_ok(ctx, cudaMemcpyAsync(W, m->B, sizeof(double) * np * nrhs, cudaMemcpyDeviceToDevice, s),
                      "solve copy"))
             return GBEM_ERR_CUDA;
-        if (!cuda_ok(ctx, launch_trsv_f64(m->L64, static_cast<const double*>(m->Linv), np, m->nb, W, nrhs, s),
+        if (!cuda_ok(ctx,
+                     launch_trsv_f64(m->L64, static_cast<const double*>(m->Linv), np, m->nb, W, nrhs, m->dsync,
+                                     m->dflags + 3, s),
                      "trsv"))
             return GBEM_ERR_CUDA;
         if (!cuda_ok(ctx, cudaMemcpyAsync(m->X, W, sizeof(double) * np * nrhs, cudaMemcpyDeviceToDevice, s),
@@ -195,7 +197,8 @@ gbem_status solve_padded(gbem_matrix_t* m, int nrhs, cudaStream_t s, int* iters,
     int host_flags[3] = {0, 0, 0};
     for (int it = 0; it < maxit; ++it) {
         if (!cuda_ok(ctx, launch_to_f32(m->R, np, nrhs, W, done, s), "to_f32") ||
-            !cuda_ok(ctx, launch_trsv_f32_guarded(Lf, Li, np, m->nb, W, nrhs, done, s), "trsv") ||
+            !cuda_ok(ctx, launch_trsv_f32_guarded(Lf, Li, np, m->nb, W, nrhs, m->dsync, m->dflags + 3, done, s),
+                     "trsv") ||
             !cuda_ok(ctx, launch_add_f32(W, np, nrhs, m->X, done, s), "add") ||
             !cuda_ok(ctx, launch_residual(m->A64, np, m->B, m->X, nrhs, m->R, done, s), "residual") ||
             !cuda_ok(ctx, launch_ir_check(m->R, m->B, np, nrhs, m->dnorm, ctx->tune.ir_tol, m->dflags, s),
@@ -505,6 +508,11 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
     const size_t np = (size_t)m->np;
     const size_t nblk = np / m->nb;
     PhaseTimer pt(ctx, GBEM_PHASE_FACTOR, s);
+    if (!m->dsync) {
+        m->dsync = mat_alloc<unsigned>(m, nblk, s);
+        if (!m->dsync) return GBEM_ERR_OOM;
+        if (!cuda_ok(ctx, cudaMemsetAsync(m->dsync, 0, nblk * sizeof(unsigned), s), "memset")) return GBEM_ERR_CUDA;
+    }
     if (m->prec == GBEM_FP64) {
         if (!m->L64) m->L64 = mat_alloc<double>(m, np * np, s);
         if (!m->Linv) m->Linv = mat_alloc<double>(m, nblk * m->nb * m->nb, s);
@@ -589,6 +597,7 @@ gbem_status gbem_capacitance(gbem_mesh_t* mesh, gbem_matrix_t* m, double eps_r, 
     if (resid_out) *resid_out = resid;
     m->last = s;
     if (flags[0]) return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "Cholesky met a non-positive pivot");
+    if (flags[3]) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
     return solve_st;
 }
 
@@ -620,6 +629,7 @@ gbem_status gbem_matrix_status(gbem_matrix_t* m)
         !cuda_ok(ctx, cudaMemcpy(flags, m->dflags, sizeof(flags), cudaMemcpyDeviceToHost), "d2h"))
         return GBEM_ERR_CUDA;
     if (flags[0]) return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "Cholesky met a non-positive pivot");
+    if (flags[3]) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
     return GBEM_OK;
 }
 

@@ -22,6 +22,7 @@
 // classification pass and evaluated afterwards by full warps, so the scarce
 // FP64 pipe never runs a closed form with most lanes of a warp idle.
 #include <cstdio>
+#include <type_traits>
 
 #include "gbem_internal.h"
 
@@ -45,128 +46,81 @@ constexpr double kPi = 3.14159265358979323846;
 
 // 1/sqrt(x) in FP64: single-precision estimate refined by one Newton step
 // y <- y + y (1 - x y^2) / 2 (relative error about 1.5 e0^2 < 1e-13).
-__device__ __forceinline__ double rsq64(double x)
+__device__ __forceinline__ double rsq(double x)
 {
     double y = (double)rsqrtf((float)x);
     double e = fma(-x * y, y, 1.0);
     return fma(0.5 * y, e, y);
 }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// Parallel panels: offsets of the centres (dp, dq) in-plane and w along the
-// normal; half extents ai, bi (panel i) and aj, bj (panel j).
-template <int N>
-__device__ double far64_par(double dp, double dq, double w, double ai, double bi, double aj,
-                            double bj)
+template <typename T> __device__ __forceinline__ T glx(int n, int i);
+template <typename T> __device__ __forceinline__ T glw(int n, int i);
+template <> __device__ __forceinline__ double glx<double>(int n, int i) { return c_glx[n][i]; }
+template <> __device__ __forceinline__ double glw<double>(int n, int i) { return c_glw[n][i]; }
+template <> __device__ __forceinline__ float glx<float>(int n, int i) { return c_glxf[n][i]; }
+template <> __device__ __forceinline__ float glw<float>(int n, int i) { return c_glwf[n][i]; }
+
+// Tensor Gauss-Legendre sum of 1/r over N x N nodes on each panel, without
+// the half-extent Jacobians (a_ij = sum / (64 pi)).
+//
+// Parallel panels: centre offsets (dp, dq) in-plane and w along the normal;
+// half extents ai, bi (panel i) and aj, bj (panel j).  The outer loop runs
+// over node pairs along p, the inner (unrolled) one over node pairs along q.
+template <typename T, int N>
+__device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
 {
-    double Q[N * N], WQ[N * N];
+    T Q[N * N], WQ[N * N];
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int d = 0; d < N; ++d) {
-            double t = dq + c_glx[N][b] * bi - c_glx[N][d] * bj;
-            Q[b * N + d] = fma(t, t, w * w);
-            WQ[b * N + d] = c_glw[N][b] * c_glw[N][d];
+            T t = dq + glx<T>(N, b) * bi - glx<T>(N, d) * bj;
+            Q[b * N + d] = t * t + w * w;
+            WQ[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
     double s = 0.0;
+#pragma unroll 1
+    for (int ac = 0; ac < N * N; ++ac) {
+        const int a = ac / N, c = ac % N;
+        T t = dp + glx<T>(N, a) * ai - glx<T>(N, c) * aj;
+        T p = t * t;
+        T si = T(0);
 #pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            double t = dp + c_glx[N][a] * ai - c_glx[N][c] * aj;
-            double p = t * t;
-            double si = 0.0;
-#pragma unroll
-            for (int k = 0; k < N * N; ++k) si = fma(WQ[k], rsq64(p + Q[k]), si);
-            s = fma(c_glw[N][a] * c_glw[N][c], si, s);
-        }
+        for (int k = 0; k < N * N; ++k) si += WQ[k] * rsq(p + Q[k]);
+        s += (double)(glw<T>(N, a) * glw<T>(N, c) * si);
+    }
     return s;
 }
 
-// Perpendicular panels: shared axis offset ds with half extents si, sj; the
-// offset of panel i's centre from panel j's plane dv (half extent ti of i
-// along j's normal), and of panel i's plane from panel j's centre dw (half
+// Perpendicular panels: shared-axis offset ds with half extents si, sj; the
+// offset dv of panel i's centre from panel j's plane (half extent ti of i
+// along j's normal) and dw of panel i's plane from panel j's centre (half
 // extent tj of j along i's normal).
-template <int N>
-__device__ double far64_orth(double ds, double si, double sj, double dv, double ti, double dw,
-                             double tj)
+template <typename T, int N>
+__device__ __noinline__ double far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj)
 {
-    double VW[N * N], WVW[N * N];
+    T VW[N * N], WVW[N * N];
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int d = 0; d < N; ++d) {
-            double tv = dv + c_glx[N][b] * ti;
-            double tw = dw - c_glx[N][d] * tj;
-            VW[b * N + d] = fma(tv, tv, tw * tw);
-            WVW[b * N + d] = c_glw[N][b] * c_glw[N][d];
+            T tv = dv + glx<T>(N, b) * ti;
+            T tw = dw - glx<T>(N, d) * tj;
+            VW[b * N + d] = tv * tv + tw * tw;
+            WVW[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
     double s = 0.0;
+#pragma unroll 1
+    for (int ac = 0; ac < N * N; ++ac) {
+        const int a = ac / N, c = ac % N;
+        T t = ds + glx<T>(N, a) * si - glx<T>(N, c) * sj;
+        T p = t * t;
+        T acc = T(0);
 #pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            double t = ds + c_glx[N][a] * si - c_glx[N][c] * sj;
-            double p = t * t;
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < N * N; ++k) acc = fma(WVW[k], rsq64(p + VW[k]), acc);
-            s = fma(c_glw[N][a] * c_glw[N][c], acc, s);
-        }
-    return s;
-}
-
-template <int N>
-__device__ double far32_par(float dp, float dq, float w, float ai, float bi, float aj, float bj)
-{
-    float Q[N * N], WQ[N * N];
-#pragma unroll
-    for (int b = 0; b < N; ++b)
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-            float t = dq + c_glxf[N][b] * bi - c_glxf[N][d] * bj;
-            Q[b * N + d] = fmaf(t, t, w * w);
-            WQ[b * N + d] = c_glwf[N][b] * c_glwf[N][d];
-        }
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            float t = dp + c_glxf[N][a] * ai - c_glxf[N][c] * aj;
-            float p = t * t;
-            float si = 0.0f;
-#pragma unroll
-            for (int k = 0; k < N * N; ++k) si = fmaf(WQ[k], rsqrtf(p + Q[k]), si);
-            s += (double)(c_glwf[N][a] * c_glwf[N][c] * si);
-        }
-    return s;
-}
-
-template <int N>
-__device__ double far32_orth(float ds, float si, float sj, float dv, float ti, float dw, float tj)
-{
-    float VW[N * N], WVW[N * N];
-#pragma unroll
-    for (int b = 0; b < N; ++b)
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-            float tv = dv + c_glxf[N][b] * ti;
-            float tw = dw - c_glxf[N][d] * tj;
-            VW[b * N + d] = fmaf(tv, tv, tw * tw);
-            WVW[b * N + d] = c_glwf[N][b] * c_glwf[N][d];
-        }
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            float t = ds + c_glxf[N][a] * si - c_glxf[N][c] * sj;
-            float p = t * t;
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < N * N; ++k) acc = fmaf(WVW[k], rsqrtf(p + VW[k]), acc);
-            s += (double)(c_glwf[N][a] * c_glwf[N][c] * acc);
-        }
+        for (int k = 0; k < N * N; ++k) acc += WVW[k] * rsq(p + VW[k]);
+        s += (double)(glw<T>(N, a) * glw<T>(N, c) * acc);
+    }
     return s;
 }
 
@@ -182,7 +136,7 @@ __device__ __forceinline__ double xlog(double coef, double t, double r2, double 
 
 // F(u,v,w) = v/2 (u^2-w^2) ln(v+rho) + u/2 (v^2-w^2) ln(u+rho)
 //            - (u^2+v^2-2w^2) rho/6 - u v w atan(u v/(w rho))
-__device__ double F_par(double u, double v, double w)
+__device__ __noinline__ double F_par(double u, double v, double w)
 {
     double u2 = u * u, v2 = v * v, w2 = w * w;
     double rho = sqrt(u2 + v2 + w2);
@@ -196,7 +150,7 @@ __device__ double F_par(double u, double v, double w)
 // H(u,v,w) = u v w ln(u+rho) + w(3u^2-w^2)/6 ln(v+rho) + v(3u^2-v^2)/6 ln(w+rho)
 //            - v w rho/3 - u w^2/2 atan(uv/(w rho)) - u v^2/2 atan(uw/(v rho))
 //            - u^3/6 atan(vw/(u rho))
-__device__ double H_orth(double u, double v, double w)
+__device__ __noinline__ double H_orth(double u, double v, double w)
 {
     double u2 = u * u, v2 = v * v, w2 = w * w;
     double rho = sqrt(u2 + v2 + w2);
@@ -229,60 +183,59 @@ struct TileGeo {
 __device__ __forceinline__ int ax_p(int k) { return k == 0 ? 1 : 0; }
 __device__ __forceinline__ int ax_q(int k) { return k == 2 ? 1 : 2; }
 
-// Exact near-field entry for slots s (row) and t (column) of the tile.
-__device__ double near_entry(const TileGeo& G, int s, int t)
+// Exact entry of parallel panels: 16-corner sum of F.
+__device__ double near_par(const TileGeo& G, int s, int t)
 {
-    int ki = G.axis[s], kj = G.axis[t];
+    const double w = G.c[s] - G.c[t];
     double I = 0.0;
-    if (ki == kj) {
-        double a[2] = {G.lo0[s], G.hi0[s]}, ap[2] = {G.lo0[t], G.hi0[t]};
-        double b[2] = {G.lo1[s], G.hi1[s]}, bp[2] = {G.lo1[t], G.hi1[t]};
-        double w = G.c[s] - G.c[t];
-#pragma unroll
-        for (int al = 0; al < 2; ++al)
-#pragma unroll
-            for (int be = 0; be < 2; ++be)
-#pragma unroll
-                for (int ga = 0; ga < 2; ++ga)
-#pragma unroll
-                    for (int de = 0; de < 2; ++de) {
-                        double f = F_par(a[al] - ap[be], b[ga] - bp[de], w);
-                        I += ((al + be + ga + de) & 1) ? -f : f;
-                    }
-    } else {
-        int sh = 3 - ki - kj;
-        // extents of panel i along the shared axis (p) and along kj (q)
-        bool i_sh_first = (ax_p(ki) == sh);
-        double p[2] = {i_sh_first ? G.lo0[s] : G.lo1[s], i_sh_first ? G.hi0[s] : G.hi1[s]};
-        double q[2] = {i_sh_first ? G.lo1[s] : G.lo0[s], i_sh_first ? G.hi1[s] : G.hi0[s]};
-        bool j_sh_first = (ax_p(kj) == sh);
-        double r[2] = {j_sh_first ? G.lo0[t] : G.lo1[t], j_sh_first ? G.hi0[t] : G.hi1[t]};
-        double tt[2] = {j_sh_first ? G.lo1[t] : G.lo0[t], j_sh_first ? G.hi1[t] : G.hi0[t]};
-        double ci = G.c[s], cj = G.c[t];
-#pragma unroll
-        for (int al = 0; al < 2; ++al)
-#pragma unroll
-            for (int be = 0; be < 2; ++be)
-#pragma unroll
-                for (int ga = 0; ga < 2; ++ga)
-#pragma unroll
-                    for (int de = 0; de < 2; ++de) {
-                        double hv = H_orth(p[al] - r[be], q[ga] - cj, ci - tt[de]);
-                        I += ((al + be + ga + de) & 1) ? -hv : hv;
-                    }
+#pragma unroll 1
+    for (int k = 0; k < 16; ++k) {
+        const int al = k & 1, be = (k >> 1) & 1, ga = (k >> 2) & 1, de = (k >> 3) & 1;
+        double u = (al ? G.hi0[s] : G.lo0[s]) - (be ? G.hi0[t] : G.lo0[t]);
+        double v = (ga ? G.hi1[s] : G.lo1[s]) - (de ? G.hi1[t] : G.lo1[t]);
+        double f = F_par(u, v, w);
+        I += ((al + be + ga + de) & 1) ? -f : f;
     }
-    double ai = (G.hi0[s] - G.lo0[s]) * (G.hi1[s] - G.lo1[s]);
-    double aj = (G.hi0[t] - G.lo0[t]) * (G.hi1[t] - G.lo1[t]);
-    return I / (4.0 * kPi * ai * aj);
+    return I;
 }
 
-template <bool MIXED>
-__device__ double far_entry(const TileGeo& G, int s, int t, int n)
+// Exact entry of perpendicular panels: 16-corner sum of H.  Panel i spans the
+// shared axis (p) and j's normal axis (q); panel j spans the shared axis (r)
+// and i's normal axis (t).
+__device__ double near_orth(const TileGeo& G, int s, int t)
 {
-    int ki = G.axis[s], kj = G.axis[t];
-    double sum = 0.0;
-    if (!MIXED) {
-        // centre offsets in FP64
+    const int ki = G.axis[s], kj = G.axis[t];
+    const int sh = 3 - ki - kj;
+    const bool i_first = (ax_p(ki) == sh), j_first = (ax_p(kj) == sh);
+    const double p0 = i_first ? G.lo0[s] : G.lo1[s], p1 = i_first ? G.hi0[s] : G.hi1[s];
+    const double q0 = i_first ? G.lo1[s] : G.lo0[s], q1 = i_first ? G.hi1[s] : G.hi0[s];
+    const double r0 = j_first ? G.lo0[t] : G.lo1[t], r1 = j_first ? G.hi0[t] : G.hi1[t];
+    const double t0 = j_first ? G.lo1[t] : G.lo0[t], t1 = j_first ? G.hi1[t] : G.hi0[t];
+    const double ci = G.c[s], cj = G.c[t];
+    double I = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < 16; ++k) {
+        const int al = k & 1, be = (k >> 1) & 1, ga = (k >> 2) & 1, de = (k >> 3) & 1;
+        double hv = H_orth((al ? p1 : p0) - (be ? r1 : r0), (ga ? q1 : q0) - cj, ci - (de ? t1 : t0));
+        I += ((al + be + ga + de) & 1) ? -hv : hv;
+    }
+    return I;
+}
+
+__device__ __forceinline__ double near_scale(const TileGeo& G, int s, int t)
+{
+    double ai = (G.hi0[s] - G.lo0[s]) * (G.hi1[s] - G.lo1[s]);
+    double aj = (G.hi0[t] - G.lo0[t]) * (G.hi1[t] - G.lo1[t]);
+    return 1.0 / (4.0 * kPi * ai * aj);
+}
+
+// Far entry of order N for the pair (s, t), T the arithmetic type.
+template <typename T, int N>
+__device__ double far_entry(const TileGeo& G, int s, int t)
+{
+    const int ki = G.axis[s], kj = G.axis[t];
+    T d[3];
+    if constexpr (sizeof(T) == 8) {
         double ci[3], cj[3];
         ci[ki] = G.c[s];
         ci[ax_p(ki)] = 0.5 * (G.lo0[s] + G.hi0[s]);
@@ -290,74 +243,72 @@ __device__ double far_entry(const TileGeo& G, int s, int t, int n)
         cj[kj] = G.c[t];
         cj[ax_p(kj)] = 0.5 * (G.lo0[t] + G.hi0[t]);
         cj[ax_q(kj)] = 0.5 * (G.lo1[t] + G.hi1[t]);
-        double d[3] = {ci[0] - cj[0], ci[1] - cj[1], ci[2] - cj[2]};
-        if (ki == kj) {
-            int p = ax_p(ki), q = ax_q(ki);
-            double ai = 0.5 * (G.hi0[s] - G.lo0[s]), bi = 0.5 * (G.hi1[s] - G.lo1[s]);
-            double aj = 0.5 * (G.hi0[t] - G.lo0[t]), bj = 0.5 * (G.hi1[t] - G.lo1[t]);
-            switch (n) {
-            case 1: sum = 4.0 * rsq64(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
-            case 2: sum = far64_par<2>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 3: sum = far64_par<3>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 4: sum = far64_par<4>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 5: sum = far64_par<5>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            default: sum = far64_par<6>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            }
-        } else {
-            int sh = 3 - ki - kj;
-            // half extents of i along the shared axis and along kj, of j along
-            // the shared axis and along ki
-            bool i_first = (ax_p(ki) == sh), j_first = (ax_p(kj) == sh);
-            double hs_i = i_first ? 0.5 * (G.hi0[s] - G.lo0[s]) : 0.5 * (G.hi1[s] - G.lo1[s]);
-            double hv_i = i_first ? 0.5 * (G.hi1[s] - G.lo1[s]) : 0.5 * (G.hi0[s] - G.lo0[s]);
-            double hs_j = j_first ? 0.5 * (G.hi0[t] - G.lo0[t]) : 0.5 * (G.hi1[t] - G.lo1[t]);
-            double hw_j = j_first ? 0.5 * (G.hi1[t] - G.lo1[t]) : 0.5 * (G.hi0[t] - G.lo0[t]);
-            switch (n) {
-            case 1: sum = 4.0 * rsq64(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
-            case 2: sum = far64_orth<2>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 3: sum = far64_orth<3>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 4: sum = far64_orth<4>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 5: sum = far64_orth<5>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            default: sum = far64_orth<6>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            }
-        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) d[e] = ci[e] - cj[e];
     } else {
         // centre offsets from float (hi, lo) pairs: error about 1 ulp of |d|
-        float d[3];
 #pragma unroll
         for (int e = 0; e < 3; ++e) d[e] = (G.chi[e][s] - G.chi[e][t]) + (G.clo[e][s] - G.clo[e][t]);
-        if (ki == kj) {
-            int p = ax_p(ki), q = ax_q(ki);
-            float ai = G.half[p][s], bi = G.half[q][s], aj = G.half[p][t], bj = G.half[q][t];
-            switch (n) {
-            case 1: sum = 4.0 * (double)rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
-            case 2: sum = far32_par<2>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 3: sum = far32_par<3>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 4: sum = far32_par<4>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            case 5: sum = far32_par<5>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            default: sum = far32_par<6>(d[p], d[q], d[ki], ai, bi, aj, bj); break;
-            }
-        } else {
-            int sh = 3 - ki - kj;
-            float hs_i = G.half[sh][s], hs_j = G.half[sh][t];
-            float hv_i = G.half[kj][s], hw_j = G.half[ki][t];
-            switch (n) {
-            case 1: sum = 4.0 * (double)rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]); break;
-            case 2: sum = far32_orth<2>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 3: sum = far32_orth<3>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 4: sum = far32_orth<4>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            case 5: sum = far32_orth<5>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            default: sum = far32_orth<6>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j); break;
-            }
-        }
     }
-    // I = (prod of half extents) * sum and |I_i||I_j| = 16 * (same product):
-    // a_ij = sum / (64 pi)
+    double sum;
+    if (ki == kj) {
+        const int p = ax_p(ki), q = ax_q(ki);
+        T ai, bi, aj, bj;
+        if constexpr (sizeof(T) == 8) {
+            ai = 0.5 * (G.hi0[s] - G.lo0[s]);
+            bi = 0.5 * (G.hi1[s] - G.lo1[s]);
+            aj = 0.5 * (G.hi0[t] - G.lo0[t]);
+            bj = 0.5 * (G.hi1[t] - G.lo1[t]);
+        } else {
+            ai = G.half[p][s];
+            bi = G.half[q][s];
+            aj = G.half[p][t];
+            bj = G.half[q][t];
+        }
+        if constexpr (N == 1) sum = 4.0 * (double)rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        else sum = far_par<T, N>(d[p], d[q], d[ki], ai, bi, aj, bj);
+    } else {
+        const int sh = 3 - ki - kj;
+        T hs_i, hv_i, hs_j, hw_j;
+        if constexpr (sizeof(T) == 8) {
+            const bool i_first = (ax_p(ki) == sh), j_first = (ax_p(kj) == sh);
+            hs_i = i_first ? 0.5 * (G.hi0[s] - G.lo0[s]) : 0.5 * (G.hi1[s] - G.lo1[s]);
+            hv_i = i_first ? 0.5 * (G.hi1[s] - G.lo1[s]) : 0.5 * (G.hi0[s] - G.lo0[s]);
+            hs_j = j_first ? 0.5 * (G.hi0[t] - G.lo0[t]) : 0.5 * (G.hi1[t] - G.lo1[t]);
+            hw_j = j_first ? 0.5 * (G.hi1[t] - G.lo1[t]) : 0.5 * (G.hi0[t] - G.lo0[t]);
+        } else {
+            hs_i = G.half[sh][s];
+            hs_j = G.half[sh][t];
+            hv_i = G.half[kj][s];
+            hw_j = G.half[ki][t];
+        }
+        if constexpr (N == 1) sum = 4.0 * (double)rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        else sum = far_orth<T, N>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j);
+    }
+    // I = (product of half extents) * sum and |I_i||I_j| = 16 * (same product)
     return sum * (1.0 / (64.0 * kPi));
 }
 
 constexpr int kThreads = 256;
 constexpr int kPairs = GBEM_TILE * GBEM_TILE;
+// Pair classes: 0 near parallel, 1 near perpendicular, 2 + 2 (n - 1) + o for
+// a far pair of order n = 1..6 (o = 1 if perpendicular).
+constexpr int kClasses = 2 + 2 * GBEM_GL_MAX;
+
+template <typename T>
+__device__ double eval_class(const TileGeo& G, int cls, int s, int t)
+{
+    switch (cls) {
+    case 0: return near_par(G, s, t) * near_scale(G, s, t);
+    case 1: return near_orth(G, s, t) * near_scale(G, s, t);
+    case 2: case 3: return far_entry<T, 1>(G, s, t);
+    case 4: case 5: return far_entry<T, 2>(G, s, t);
+    case 6: case 7: return far_entry<T, 3>(G, s, t);
+    case 8: case 9: return far_entry<T, 4>(G, s, t);
+    case 10: case 11: return far_entry<T, 5>(G, s, t);
+    default: return far_entry<T, 6>(G, s, t);
+    }
+}
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, float q_near,
@@ -365,19 +316,27 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, 
                                                            float* __restrict__ A32,
                                                            unsigned long long* __restrict__ counts)
 {
+    using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ TileGeo G;
-    __shared__ unsigned short nlist[kPairs];
-    __shared__ int n_par, n_orth;
-    __shared__ int cnt[GBEM_GL_MAX + 1];
+    __shared__ unsigned short list[kPairs];
+    __shared__ unsigned char cls_of[kPairs];
+    __shared__ int cls_cnt[kClasses], cls_off[kClasses + 1];
+    __shared__ int tile_ij[2];
 
-    // lower-triangular tile coordinates (TI >= TJ) from the linear block index
-    long long b = blockIdx.x;
-    int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
-    while ((long long)TI * (TI + 1) / 2 > b) --TI;
-    int TJ = (int)(b - (long long)TI * (TI + 1) / 2);
-    const int n = g.n;
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        // lower-triangular tile coordinates (TI >= TJ) from the linear block index
+        long long b = blockIdx.x;
+        int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
+        while ((long long)TI * (TI + 1) / 2 > b) --TI;
+        tile_ij[0] = TI;
+        tile_ij[1] = (int)(b - (long long)TI * (TI + 1) / 2);
+    }
+    if (tid < kClasses) cls_cnt[tid] = 0;
+    __syncthreads();
+    const int TI = tile_ij[0], TJ = tile_ij[1];
+    const int n = g.n;
 
     if (tid < 2 * GBEM_TILE) {
         int slot = tid;
@@ -417,70 +376,87 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, 
             G.area[slot] = (float)((h0 - l0) * (h1 - l1));
         }
     }
-    if (tid == 0) {
-        n_par = 0;
-        n_orth = 0;
-    }
-    if (tid <= GBEM_GL_MAX) cnt[tid] = 0;
     __syncthreads();
 
+    // 1. classify every pair; count the classes
+    constexpr int kPer = kPairs / kThreads;
+    int my_cls[kPer], my_rank[kPer];
     const int mode = MIXED ? 1 : 0;
-    // pass 1: classify; evaluate far pairs, queue near pairs
-    for (int e = tid; e < kPairs; e += kThreads) {
-        int ii = e & (GBEM_TILE - 1), jj = e >> 5;
-        int s = ii, t = GBEM_TILE + jj;
-        if (!G.valid[s] || !G.valid[t]) continue;
-        if (TI == TJ && ii < jj) continue;
-        float g2 = 0.0f;
+    const unsigned lane = tid & 31;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            float gd = fmaxf(0.0f, fmaxf(G.blo[d][t] - G.bhi[d][s], G.blo[d][s] - G.bhi[d][t]));
-            g2 = fmaf(gd, gd, g2);
-        }
-        float L = fmaxf(G.lmax[s], G.lmax[t]);
-        float gap = sqrtf(g2);
-        float q = gap / L;
-        // The closed form loses about eps * R^4 / (|I_i| |I_j|) to cancellation
-        // between its 16 corner terms (R: largest corner distance); keep it
-        // below 2e-12 relative, else use quadrature when an order fits.
-        float R = gap + G.lmax[s] + G.lmax[t];
-        bool cf_ok = (q < q_near) && (R * R * R * R <= 1.8e4f * G.area[s] * G.area[t]);
-        int order = 0;
-        if (MIXED ? (q >= q_near) : !cf_ok) {
+    for (int r = 0; r < kPer; ++r) {
+        const int e = tid + r * kThreads;
+        const int ii = e & (GBEM_TILE - 1), jj = e >> 5;
+        const int s = ii, t = GBEM_TILE + jj;
+        int cls = -1;
+        if (G.valid[s] && G.valid[t] && !(TI == TJ && ii < jj)) {
+            float g2 = 0.0f;
 #pragma unroll
-            for (int m = GBEM_GL_MAX; m >= 1; --m)
-                if (q >= c_qmin[mode][m]) order = m;
-        }
-        if (order == 0) {
-            if (G.axis[s] == G.axis[t]) {
-                int slot = atomicAdd(&n_par, 1);
-                nlist[slot] = (unsigned short)e;
-            } else {
-                int slot = atomicAdd(&n_orth, 1);
-                nlist[kPairs - 1 - slot] = (unsigned short)e;
+            for (int d = 0; d < 3; ++d) {
+                float gd = fmaxf(0.0f, fmaxf(G.blo[d][t] - G.bhi[d][s], G.blo[d][s] - G.bhi[d][t]));
+                g2 = fmaf(gd, gd, g2);
             }
-            continue;
+            const float L = fmaxf(G.lmax[s], G.lmax[t]);
+            const float gap = sqrtf(g2);
+            const float q = gap / L;
+            // The closed form loses about eps * R^4 / (|I_i| |I_j|) to cancellation
+            // between its 16 corner terms (R: largest corner distance); keep it
+            // below 2e-12 relative, else use quadrature when an order fits.
+            const float R = gap + G.lmax[s] + G.lmax[t];
+            const bool cf_ok = (q < q_near) && (R * R * R * R <= 1.8e4f * G.area[s] * G.area[t]);
+            int order = 0;
+            if (MIXED ? (q >= q_near) : !cf_ok) {
+#pragma unroll
+                for (int m = GBEM_GL_MAX; m >= 1; --m)
+                    if (q >= c_qmin[mode][m]) order = m;
+            }
+            const int orth = G.axis[s] != G.axis[t];
+            cls = order == 0 ? orth : 2 + 2 * (order - 1) + orth;
         }
-        double v = far_entry<MIXED>(G, s, t, order);
-        size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
-        A64[i + j * (size_t)np] = v;
-        if (MIXED) A32[i + j * (size_t)np] = (float)v;
-        atomicAdd(&cnt[order], 1);
+        // warp-aggregated rank within the class
+        const unsigned peers = __match_any_sync(0xffffffffu, cls);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (cls >= 0 && (int)lane == leader) base = atomicAdd(&cls_cnt[cls], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        my_cls[r] = cls;
+        my_rank[r] = base + __popc(peers & ((1u << lane) - 1u));
+        if (cls >= 0) cls_of[e] = (unsigned char)cls;
     }
     __syncthreads();
-    // pass 2: near pairs, parallel ones first then perpendicular ones
-    const int tot = n_par + n_orth;
-    for (int x = tid; x < tot; x += kThreads) {
-        int e = (x < n_par) ? nlist[x] : nlist[kPairs - 1 - (x - n_par)];
-        int ii = e & (GBEM_TILE - 1), jj = e >> 5;
-        double v = near_entry(G, ii, GBEM_TILE + jj);
-        size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
+    // 2. class offsets: near classes first, then far classes by falling order
+    if (tid == 0) {
+        int acc = 0;
+        cls_off[0] = 0;
+        cls_off[1] = acc += cls_cnt[0];
+        acc += cls_cnt[1];
+        for (int c = kClasses - 1; c >= 2; --c) {
+            cls_off[c] = acc;
+            acc += cls_cnt[c];
+        }
+        cls_off[kClasses] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPer; ++r)
+        if (my_cls[r] >= 0) list[cls_off[my_cls[r]] + my_rank[r]] = (unsigned short)(tid + r * kThreads);
+    __syncthreads();
+    // 3. evaluate in class order: every warp runs one code path but at class
+    //    boundaries
+    const int total = cls_off[kClasses];
+    for (int x = tid; x < total; x += kThreads) {
+        const int e = list[x];
+        const int ii = e & (GBEM_TILE - 1), jj = e >> 5;
+        const double v = eval_class<T>(G, cls_of[e], ii, GBEM_TILE + jj);
+        const size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
         A64[i + j * (size_t)np] = v;
         if (MIXED) A32[i + j * (size_t)np] = (float)v;
     }
-    if (tid == 0) cnt[0] = tot;
-    __syncthreads();
-    if (tid <= GBEM_GL_MAX && cnt[tid]) atomicAdd(&counts[tid], (unsigned long long)cnt[tid]);
+    // class counts: near pairs, then far pairs by order
+    if (tid < kClasses) {
+        int order = tid < 2 ? 0 : 1 + (tid - 2) / 2;
+        if (cls_cnt[tid]) atomicAdd(&counts[order], (unsigned long long)cls_cnt[tid]);
+    }
 }
 
 // Identity in the padding rows (lower part): A[r][c] = (r == c) for r >= n.

@@ -20,58 +20,121 @@ namespace {
 
 constexpr int NB = 64;
 
+// Cholesky of one 64x64 diagonal block and the inverse of its factor.  Each
+// of the 256 threads keeps a fixed 4x4 sub-block of the matrix in registers;
+// step j publishes the current column j through shared memory (double
+// buffered), and every thread applies the rank-1 update -a_rj a_cj / a_jj to
+// its entries right of column j: one barrier per column.  Column j is scaled
+// by 1/sqrt(a_jj) at the end.  The inverse L^-1 is then formed the same way,
+// by forward elimination of the identity.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_diag(T* __restrict__ L, int ld, int k0,
                                                   T* __restrict__ Linv, int* __restrict__ info)
 {
     extern __shared__ unsigned char smem_raw[];
-    T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
-    T(*inv)[NB + 1] = a + NB;
+    T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);   // the factor, for the inverse
+    __shared__ T col[2][NB];
+    __shared__ T piv[NB];
     const int tid = threadIdx.x;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e % NB, c = e / NB;
-        a[r][c] = (r >= c) ? L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] : T(0);
-    }
-    __syncthreads();
+    const int r0 = (tid & 15) * 4, c0 = (tid >> 4) * 4;   // this thread's 4x4 sub-block
+    T x[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = r0 + u, c = c0 + v;
+            x[u][v] = (r >= c) ? L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] : T(0);
+        }
     for (int j = 0; j < NB; ++j) {
-        if (tid == 0) {
-            T d = a[j][j];
-            if (!(d > T(0))) {
-                info[0] = 1;
-                d = T(1);
+        const int b = j & 1;
+        // owners of column j publish it (rows >= j)
+        if (c0 <= j && j < c0 + 4) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (c0 + v == j)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) col[b][r0 + u] = x[u][v];
+        }
+        __syncthreads();
+        T d = col[b][j];
+        if (tid == 0) piv[j] = d;
+        if (!(d > T(0))) d = T(1);
+        const T rd = T(1) / d;
+        if (c0 + 3 > j) {
+            T cr[4], cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                cr[u] = col[b][r0 + u];
+                cc[u] = col[b][c0 + u] * rd;
             }
-            a[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        T djj = a[j][j];
-        for (int r = j + 1 + tid; r < NB; r += blockDim.x) a[r][j] /= djj;
-        __syncthreads();
-        // rank-1 update of the trailing lower triangle
-        const int m = NB - 1 - j;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            int r = j + 1 + e % m, c = j + 1 + e / m;
-            if (r >= c) a[r][c] -= a[r][j] * a[c][j];
-        }
-        __syncthreads();
-    }
-    // inverse of the lower-triangular factor, one column per thread
-    if (tid < NB) {
-        const int c = tid;
-        for (int r = 0; r < c; ++r) inv[r][c] = T(0);
-        inv[c][c] = T(1) / a[c][c];
-        for (int r = c + 1; r < NB; ++r) {
-            T s = T(0);
-            for (int k = c; k < r; ++k) s += a[r][k] * inv[k][c];
-            inv[r][c] = -s / a[r][r];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (c0 + v > j && r0 + u >= c0 + v) x[u][v] -= cr[u] * cc[v];
         }
     }
     __syncthreads();
-    T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e % NB, c = e / NB;
-        if (r >= c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = a[r][c];
-        Lb[e] = inv[r][c];
+    if (tid < NB) {
+        T d = piv[tid];
+        if (!(d > T(0))) {
+            info[0] = 1;
+            d = T(1);
+        }
+        piv[tid] = sqrt(d);
     }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = r0 + u, c = c0 + v;
+            T val = (r > c) ? x[u][v] / piv[c] : (r == c ? piv[c] : T(0));
+            a[r][c] = val;
+            if (r >= c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = val;
+        }
+    __syncthreads();
+    // X = L^-1 by forward elimination of the identity: after row j of X is
+    // final (divided by l_jj), rows i > j subtract l_ij X_j.
+    T y[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) y[u][v] = (r0 + u == c0 + v) ? T(1) : T(0);
+    __shared__ T rowj[2][NB];
+    for (int j = 0; j < NB; ++j) {
+        const int b = j & 1;
+        const T rl = T(1) / a[j][j];
+        // owners of row j finalise it and publish it
+        if (r0 <= j && j < r0 + 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (r0 + u == j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        y[u][v] *= rl;
+                        rowj[b][c0 + v] = y[u][v];
+                    }
+        }
+        __syncthreads();
+        if (r0 + 3 > j) {
+            T lr[4], xr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lr[u] = a[r0 + u][j];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xr[v] = rowj[b][c0 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (r0 + u > j) y[u][v] -= lr[u] * xr[v];
+        }
+    }
+    T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Lb[(r0 + u) + (size_t)(c0 + v) * NB] = y[u][v];
 }
 
 // L_ik = A_ik Linv_kk^T for the row block starting at k0 + NB * (1 + blockIdx.x)
@@ -162,7 +225,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, cudaStream_t s)
     const size_t smem = 2 * NB * (NB + 1) * sizeof(T);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
+                                  (int)(NB * (NB + 1) * sizeof(T)))) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
@@ -172,7 +235,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, cudaStream_t s)
         return e;
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * NB;
-        potrf_diag<T><<<1, 256, smem, s>>>(L, np, k0, Linv, info);
+        potrf_diag<T><<<1, 256, NB * (NB + 1) * sizeof(T), s>>>(L, np, k0, Linv, info);
         count_launch();
         const int m = nblk - k - 1;
         if (m > 0) {

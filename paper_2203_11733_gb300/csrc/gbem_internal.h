@@ -79,7 +79,8 @@ struct gbem_matrix_s {
     float* A32 = nullptr;       // mixed: FP32 copy, factored in place
     double* L64 = nullptr;      // FP64 mode: the factor
     void* Linv = nullptr;       // inverses of the diagonal blocks (T)
-    int* dflags = nullptr;      // [0] not-SPD pivot, [1] IR done, [2] IR iters, [3] spare
+    int* dflags = nullptr;      // [0] not-SPD pivot, [1] IR done, [2] IR iters, [3] wait timeout
+    unsigned* dsync = nullptr;  // one flag per 64-row block for the persistent solves
     unsigned long long* dcounts = nullptr; // pair class counts (8)
     double* dnorm = nullptr;    // IR: [0] residual, [1..] scratch
     // solve work buffers (np x cap_rhs)
@@ -113,10 +114,11 @@ cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
 cudaError_t launch_copy_lower(const double* A, double* L, int np, cudaStream_t s);
 cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s);
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, cudaStream_t s);
+// W (np x nrhs, followed by np x nrhs of work space) := A^-1 W with the
+// factor L and its diagonal-block inverses; sync: np/64 flags, status: word
+// that receives GBEM_ERR_TIMEOUT if a bounded device wait gives up.
 cudaError_t launch_trsv_f64(const double* L, const double* Linv, int np, int nb, double* W, int nrhs,
-                            cudaStream_t s);
-cudaError_t launch_trsv_f32(const float* L, const float* Linv, int np, int nb, float* W, int nrhs,
-                            cudaStream_t s);
+                            unsigned* sync, int* status, cudaStream_t s);
 cudaError_t launch_pack_rhs(const double* B, int ldb, int n, int np, int nrhs, double* Bp,
                             cudaStream_t s);
 cudaError_t launch_unpack(const double* Xp, int np, int n, int nrhs, double* X, int ldx,
@@ -128,7 +130,7 @@ cudaError_t launch_to_f32(const double* R, int np, int nrhs, float* W, const int
 cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, const int* done,
                            cudaStream_t s);
 cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, int nb, float* W,
-                                    int nrhs, const int* done, cudaStream_t s);
+                                    int nrhs, unsigned* sync, int* status, const int* done, cudaStream_t s);
 cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,
                             double* R, const int* done, cudaStream_t s);
 cudaError_t launch_ir_check(const double* R, const double* Bp, int np, int nrhs, double* norm,

@@ -3,134 +3,256 @@
 // and the charge on each conductor (Eq. "electriccharge").
 //
 // Triangular solves are blocked by the factor's 64-wide diagonal blocks and
-// use their stored inverses: the forward sweep takes, for k = 0..nblk-1,
-//     Y_k = Linv_kk W_k,   W_i -= L_ik Y_k (i > k)
-// and the backward sweep, for k = nblk-1..0,
-//     X_k = Linv_kk^T Y_k, Y_i -= L_ki^T X_k (i < k).
-// One launch per block step; every CTA recomputes the small diagonal product
-// itself so that no CTA waits on another.
+// use their stored inverses.  Forward sweep, block rows b = 0..nblk-1:
+//     Y_b = Linv_bb (W_b - sum_{j<b} L_bj Y_j)
+// backward sweep, b = nblk-1..0:
+//     X_b = Linv_bb^T (Y_b - sum_{j>b} L_jb^T X_j).
+// Each sweep is one persistent cooperative launch: CTA c owns block rows
+// c, c + G, ... and consumes the solved blocks of other CTAs as their flags
+// appear.  All CTAs are co-resident (cooperative launch), so every wait ends;
+// each wait is also bounded and reports GBEM_ERR_TIMEOUT through a status word
+// instead of spinning forever.
+#include <atomic>
+
 #include "gbem_internal.h"
 
 namespace {
 
 constexpr int NB = 64;
-constexpr int MAXR = 16;   // right-hand sides per pass
+constexpr int MAXR = 16;          // right-hand sides per pass
+constexpr long long kSpinLimit = 1LL << 22;   // ~0.5 s of polling at 100 ns
 
-// Forward step k: rows of block k and the rows below.
-template <typename T>
-__global__ void __launch_bounds__(256) trsv_fwd_step(const T* __restrict__ L, const T* __restrict__ Linv,
-                                                     int np, int k, T* __restrict__ W,
-                                                     T* __restrict__ Y, int nrhs, const int* done)
+std::atomic<unsigned> g_epoch{1};
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p)
 {
-    if (done && *done) return;
-    __shared__ T w[NB][MAXR];
-    __shared__ T y[NB][MAXR];
-    const int tid = threadIdx.x;
-    const int k0 = k * NB;
-    const T* Lb = Linv + (size_t)k * NB * NB;
-    for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
-        const int nr = min(MAXR, nrhs - r0);
-        for (int e = tid; e < NB * nr; e += blockDim.x) {
-            int r = e % NB, c = e / NB;
-            w[r][c] = W[(size_t)(k0 + r) + (size_t)(r0 + c) * np];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * nr; e += blockDim.x) {
-            int r = e % NB, c = e / NB;
-            T s = T(0);
-            for (int t = 0; t <= r; ++t) s += Lb[r + (size_t)t * NB] * w[t][c];
-            y[r][c] = s;
-        }
-        __syncthreads();
-        if (blockIdx.x == 0)
-            for (int e = tid; e < NB * nr; e += blockDim.x) {
-                int r = e % NB, c = e / NB;
-                Y[(size_t)(k0 + r) + (size_t)(r0 + c) * np] = y[r][c];
-            }
-        // rows below, one row per thread
-        for (int row = k0 + NB + blockIdx.x * blockDim.x + tid; row < np;
-             row += gridDim.x * blockDim.x) {
-            T acc[MAXR];
-#pragma unroll
-            for (int c = 0; c < MAXR; ++c) acc[c] = T(0);
-            for (int t = 0; t < NB; ++t) {
-                T l = L[(size_t)row + (size_t)(k0 + t) * np];
-#pragma unroll
-                for (int c = 0; c < MAXR; ++c) acc[c] += l * y[t][c];
-            }
-            for (int c = 0; c < nr; ++c) W[(size_t)row + (size_t)(r0 + c) * np] -= acc[c];
-        }
-        __syncthreads();
-    }
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Backward step k: X_k = Linv_kk^T Y_k written into W; rows above updated in Y.
-template <typename T>
-__global__ void __launch_bounds__(256) trsv_bwd_step(const T* __restrict__ L, const T* __restrict__ Linv,
-                                                     int np, int k, T* __restrict__ Y,
-                                                     T* __restrict__ W, int nrhs, const int* done)
+__device__ __forceinline__ void store_release(unsigned* p, unsigned v)
 {
-    if (done && *done) return;
-    __shared__ T yk[NB][MAXR];
-    __shared__ T x[NB][MAXR];
-    const int tid = threadIdx.x;
-    const int k0 = k * NB;
-    const T* Lb = Linv + (size_t)k * NB * NB;
-    for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
-        const int nr = min(MAXR, nrhs - r0);
-        for (int e = tid; e < NB * nr; e += blockDim.x) {
-            int r = e % NB, c = e / NB;
-            yk[r][c] = Y[(size_t)(k0 + r) + (size_t)(r0 + c) * np];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * nr; e += blockDim.x) {
-            int r = e % NB, c = e / NB;
-            T s = T(0);
-            for (int t = r; t < NB; ++t) s += Lb[t + (size_t)r * NB] * yk[t][c];
-            x[r][c] = s;
-        }
-        __syncthreads();
-        if (blockIdx.x == 0)
-            for (int e = tid; e < NB * nr; e += blockDim.x) {
-                int r = e % NB, c = e / NB;
-                W[(size_t)(k0 + r) + (size_t)(r0 + c) * np] = x[r][c];
-            }
-        // rows above: Y_i -= (L_ki)^T X_k, i.e. for row `row` < k0:
-        // sum_t L[k0 + t][row] * x[t]  (column `row` of L, rows k0..k0+63)
-        for (int row = blockIdx.x * blockDim.x + tid; row < k0; row += gridDim.x * blockDim.x) {
-            T acc[MAXR];
-#pragma unroll
-            for (int c = 0; c < MAXR; ++c) acc[c] = T(0);
-            const T* col = L + (size_t)row * np + k0;
-            for (int t = 0; t < NB; ++t) {
-                T l = col[t];
-#pragma unroll
-                for (int c = 0; c < MAXR; ++c) acc[c] += l * x[t][c];
-            }
-            for (int c = 0; c < nr; ++c) Y[(size_t)row + (size_t)(r0 + c) * np] -= acc[c];
-        }
-        __syncthreads();
-    }
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename T>
-cudaError_t trsv(const T* L, const T* Linv, int np, T* W, T* Y, int nrhs, const int* done,
-                 cudaStream_t s)
+// Thread 0 waits until flag == epoch (bounded); the CTA then proceeds
+// together.  Returns false if the wait gave up (status set).
+__device__ bool wait_flag(const unsigned* flag, unsigned epoch, int* status, int* s_ok)
 {
+    if (threadIdx.x == 0) {
+        long long spins = 0;
+        int ok = 1;
+        while (load_acquire(flag) != epoch) {
+            if (++spins > kSpinLimit || atomicAdd(status, 0) != 0) {
+                atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <typename T, int R>
+struct SweepSmem {
+    T iv[NB][NB + 1];      // diagonal-block inverse
+    T v[NB][R];            // solved block of another row (Y_j or X_j)
+    T part[4][NB][R];      // partial sums of the four column quarters
+    T w[NB][R];            // right-hand side block of this row, then the result
+    int ok;
+};
+
+// Forward sweep on right-hand-side columns [0, nr) of W (np x nrhs, col-major).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) trsv_fwd(const T* __restrict__ L, const T* __restrict__ Linv, int np,
+                                                const T* __restrict__ W, T* __restrict__ Y, int nr,
+                                                unsigned* sync, unsigned epoch, int* status, const int* done)
+{
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    SweepSmem<T, R>& S = *reinterpret_cast<SweepSmem<T, R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;   // row of the block, column quarter
     const int nblk = np / NB;
-    for (int k = 0; k < nblk; ++k) {
-        int rows = np - (k + 1) * NB;
-        int grid = max(1, min(1024, (rows + 255) / 256));
-        trsv_fwd_step<T><<<grid, 256, 0, s>>>(L, Linv, np, k, W, Y, nrhs, done);
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int b0 = b * NB;
+        T acc[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) acc[c] = T(0);
+        for (int j = 0; j < b; ++j) {
+            if (!wait_flag(sync + j, epoch, status, &S.ok)) return;
+            const int j0 = j * NB;
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                S.v[t][c] = (c < nr) ? __ldcg(Y + (size_t)(j0 + t) + (size_t)c * np) : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int tt = 0; tt < NB / 4; ++tt) {
+                const int t = q * (NB / 4) + tt;
+                const T l = L[(size_t)(b0 + r) + (size_t)(j0 + t) * np];
+#pragma unroll
+                for (int c = 0; c < R; ++c) acc[c] += l * S.v[t][c];
+            }
+            __syncthreads();
+        }
+        // w = W_b - sum of the four partial sums; Y_b = Linv_bb w
+        for (int e = tid; e < NB * NB; e += blockDim.x)
+            S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+#pragma unroll
+        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            T rhs = (c < nr) ? W[(size_t)(b0 + t) + (size_t)c * np] : T(0);
+            S.w[t][c] = rhs - (((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c]);
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            if (c >= nr) continue;
+            T sum = T(0);
+            for (int k = 0; k <= t; ++k) sum += S.iv[t][k] * S.w[k][c];
+            Y[(size_t)(b0 + t) + (size_t)c * np] = sum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            store_release(sync + b, epoch);
+        }
+    }
+}
+
+// Backward sweep: X = L^-T Y, written into W; block rows in falling order.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) trsv_bwd(const T* __restrict__ L, const T* __restrict__ Linv, int np,
+                                                const T* __restrict__ Y, T* __restrict__ X, int nr,
+                                                unsigned* sync, unsigned epoch, int* status, const int* done)
+{
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    SweepSmem<T, R>& S = *reinterpret_cast<SweepSmem<T, R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;
+    const int nblk = np / NB;
+    for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
+        const int b0 = b * NB;
+        T acc[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) acc[c] = T(0);
+        for (int j = nblk - 1; j > b; --j) {
+            if (!wait_flag(sync + j, epoch, status, &S.ok)) return;
+            const int j0 = j * NB;
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                S.v[t][c] = (c < nr) ? __ldcg(X + (size_t)(j0 + t) + (size_t)c * np) : T(0);
+            }
+            __syncthreads();
+            // row r of L_jb^T is column (b0 + r) of L, rows j0..j0+63
+            const T* col = L + (size_t)(b0 + r) * np + j0 + q * (NB / 4);
+#pragma unroll
+            for (int tt = 0; tt < NB / 4; ++tt) {
+                const T l = col[tt];
+#pragma unroll
+                for (int c = 0; c < R; ++c) acc[c] += l * S.v[q * (NB / 4) + tt][c];
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < NB * NB; e += blockDim.x)
+            S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+#pragma unroll
+        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            T rhs = (c < nr) ? Y[(size_t)(b0 + t) + (size_t)c * np] : T(0);
+            S.w[t][c] = rhs - (((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c]);
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            if (c >= nr) continue;
+            T sum = T(0);
+            for (int k = t; k < NB; ++k) sum += S.iv[k][t] * S.w[k][c];
+            X[(size_t)(b0 + t) + (size_t)c * np] = sum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            store_release(sync + b, epoch);
+        }
+    }
+}
+
+template <typename K>
+int coop_grid(K kernel, size_t smem, int nblk)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return std::max(1, std::min(nblk, std::max(1, per) * sms));
+}
+
+template <typename T, int R>
+cudaError_t sweep_pair(const T* L, const T* Linv, int np, T* W, T* Y, int nr, unsigned* sync, int* status,
+                       const int* done, cudaStream_t s)
+{
+    const size_t smem = sizeof(SweepSmem<T, R>);
+    const int nblk = np / NB;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(trsv_fwd<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(trsv_bwd<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    unsigned e1 = g_epoch.fetch_add(2);
+    unsigned e2 = e1 + 1;
+    {
+        const T* Wc = W;
+        int grid = coop_grid(trsv_fwd<T, R>, smem, nblk);
+        void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Wc, (void*)&Y, (void*)&nr,
+                        (void*)&sync, (void*)&e1, (void*)&status, (void*)&done};
+        if ((e = cudaLaunchCooperativeKernel((void*)trsv_fwd<T, R>, grid, 256, args, smem, s)) != cudaSuccess)
+            return e;
         count_launch();
     }
-    for (int k = nblk - 1; k >= 0; --k) {
-        int rows = k * NB;
-        int grid = max(1, min(1024, (rows + 255) / 256));
-        trsv_bwd_step<T><<<grid, 256, 0, s>>>(L, Linv, np, k, Y, W, nrhs, done);
+    {
+        const T* Yc = Y;
+        int grid = coop_grid(trsv_bwd<T, R>, smem, nblk);
+        void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Yc, (void*)&W, (void*)&nr,
+                        (void*)&sync, (void*)&e2, (void*)&status, (void*)&done};
+        if ((e = cudaLaunchCooperativeKernel((void*)trsv_bwd<T, R>, grid, 256, args, smem, s)) != cudaSuccess)
+            return e;
         count_launch();
     }
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+// W (np x nrhs) := L^-T L^-1 W, with Y (same size) as work; sync holds one
+// flag per 64-row block.
+template <typename T>
+cudaError_t trsv(const T* L, const T* Linv, int np, T* W, T* Y, int nrhs, unsigned* sync, int* status,
+                 const int* done, cudaStream_t s)
+{
+    for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
+        const int nr = std::min(MAXR, nrhs - c0);
+        T* Wc = W + (size_t)c0 * np;
+        T* Yc = Y + (size_t)c0 * np;
+        cudaError_t e;
+        if (nr <= 4) e = sweep_pair<T, 4>(L, Linv, np, Wc, Yc, nr, sync, status, done, s);
+        else if (nr <= 8) e = sweep_pair<T, 8>(L, Linv, np, Wc, Yc, nr, sync, status, done, s);
+        else e = sweep_pair<T, 16>(L, Linv, np, Wc, Yc, nr, sync, status, done, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 __global__ void pack_rhs(const double* __restrict__ B, int ldb, int n, int np, int nrhs,
@@ -189,53 +311,71 @@ __global__ void add_f32(const float* __restrict__ W, size_t total, double* __res
         X[e] += (double)W[e];
 }
 
-// R = B - A X with A symmetric, only its lower triangle stored.  CTA owns 32
-// rows and walks every 32-column block in order (deterministic sums): lower
-// blocks are read directly, blocks above the diagonal through the transpose.
-constexpr int RT = 32;
+// R = B - A X with A symmetric, only its lower triangle stored.  A CTA owns 16
+// rows and walks the 64-column blocks in order; blocks left of the diagonal
+// are read directly, blocks right of it through the transpose (coalesced in
+// both cases).  16 column groups per CTA and a fixed-order final sum keep the
+// result independent of scheduling; small row blocks spread the FP64 work
+// over every SM.
+constexpr int RT = 16;
+constexpr int CT = 64;
+template <int RR>
 __global__ void __launch_bounds__(256) residual(const double* __restrict__ A, int np,
                                                 const double* __restrict__ Bp,
                                                 const double* __restrict__ X, int nrhs,
                                                 double* __restrict__ R, const int* done)
 {
     if (done && *done) return;
-    __shared__ double a[RT][RT + 1];
-    __shared__ double xs[RT][MAXR];
-    __shared__ double part[8][RT][MAXR];
+    __shared__ double a[RT][CT + 1];
+    __shared__ double xs[CT][RR + 1];
+    __shared__ double part[8][RT][RR];
     const int tid = threadIdx.x;
     const int i0 = blockIdx.x * RT;
-    const int ri = tid % RT, grp = tid / RT;  // 8 column groups
-    for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
-        const int nr = min(MAXR, nrhs - c0);
-        double acc[MAXR];
+    const int ri = tid % RT, grp = tid / RT;  // 16 column groups
+    for (int c0 = 0; c0 < nrhs; c0 += RR) {
+        const int nr = min(RR, nrhs - c0);
+        double acc[RR];
 #pragma unroll
-        for (int c = 0; c < MAXR; ++c) acc[c] = 0.0;
-        for (int j0 = 0; j0 < np; j0 += RT) {
+        for (int c = 0; c < RR; ++c) acc[c] = 0.0;
+        for (int j0 = 0; j0 < np; j0 += CT) {
             __syncthreads();
-            // tile a[r][c] = A(i0 + r, j0 + c)
-            for (int e = tid; e < RT * RT; e += blockDim.x) {
-                int r = e % RT, c = e / RT;
-                double v;
-                if (j0 < i0) v = A[(size_t)(i0 + r) + (size_t)(j0 + c) * np];
-                else if (j0 > i0) v = A[(size_t)(j0 + r) + (size_t)(i0 + c) * np];
-                else v = A[(size_t)(i0 + max(r, c)) + (size_t)(i0 + min(r, c)) * np];
-                if (j0 > i0) a[c][r] = v;
-                else a[r][c] = v;
+            // a[r][c] = A(i0 + r, j0 + c)
+            if (j0 + CT <= i0) {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int r = e % RT, c = e / RT;
+                    a[r][c] = A[(size_t)(i0 + r) + (size_t)(j0 + c) * np];
+                }
+            } else if (j0 >= i0 + RT) {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int c = e % CT, r = e / CT;
+                    a[r][c] = A[(size_t)(j0 + c) + (size_t)(i0 + r) * np];
+                }
+            } else {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int r = e % RT, c = e / RT;
+                    int gi = i0 + r, gj = j0 + c;
+                    a[r][c] = A[(size_t)max(gi, gj) + (size_t)min(gi, gj) * np];
+                }
             }
-            for (int e = tid; e < RT * nr; e += blockDim.x) {
-                int r = e % RT, c = e / RT;
-                xs[r][c] = X[(size_t)(j0 + r) + (size_t)(c0 + c) * np];
+            for (int e = tid; e < CT * RR; e += blockDim.x) {
+                int r = e % CT, c = e / CT;
+                xs[r][c] = (c < nr) ? X[(size_t)(j0 + r) + (size_t)(c0 + c) * np] : 0.0;
             }
             __syncthreads();
-            for (int jj = grp; jj < RT; jj += 8) {
-                double av = a[ri][jj];
 #pragma unroll
-                for (int c = 0; c < MAXR; ++c)
-                    if (c < nr) acc[c] = fma(av, xs[jj][c], acc[c]);
+            for (int q = 0; q < CT / 16; ++q) {
+                const int jj = grp + 16 * q;
+                const double av = a[ri][jj];
+#pragma unroll
+                for (int c = 0; c < RR; ++c) acc[c] = fma(av, xs[jj][c], acc[c]);
             }
         }
+        // the two column groups of a warp first, then 8 partial sums
 #pragma unroll
-        for (int c = 0; c < MAXR; ++c) part[grp][ri][c] = acc[c];
+        for (int c = 0; c < RR; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+        if ((grp & 1) == 0)
+#pragma unroll
+            for (int c = 0; c < RR; ++c) part[grp >> 1][ri][c] = acc[c];
         __syncthreads();
         for (int e = tid; e < RT * nr; e += blockDim.x) {
             int r = e % RT, c = e / RT;
@@ -244,6 +384,7 @@ __global__ void __launch_bounds__(256) residual(const double* __restrict__ A, in
             size_t idx = (size_t)(i0 + r) + (size_t)(c0 + c) * np;
             R[idx] = Bp[idx] - s;
         }
+        __syncthreads();
     }
 }
 
@@ -326,25 +467,18 @@ static int grid_for(size_t total)
 }  // namespace
 
 cudaError_t launch_trsv_f64(const double* L, const double* Linv, int np, int nb, double* W, int nrhs,
-                            cudaStream_t s)
+                            unsigned* sync, int* status, cudaStream_t s)
 {
     if (nb != NB || nrhs <= 0) return cudaErrorInvalidValue;
     // Y shares the tail of W's allocation: W holds 2 * np * nrhs entries
-    return trsv<double>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, nullptr, s);
-}
-
-cudaError_t launch_trsv_f32(const float* L, const float* Linv, int np, int nb, float* W, int nrhs,
-                            cudaStream_t s)
-{
-    if (nb != NB || nrhs <= 0) return cudaErrorInvalidValue;
-    return trsv<float>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, nullptr, s);
+    return trsv<double>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, sync, status, nullptr, s);
 }
 
 cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, int nb, float* W,
-                                    int nrhs, const int* done, cudaStream_t s)
+                                    int nrhs, unsigned* sync, int* status, const int* done, cudaStream_t s)
 {
     if (nb != NB || nrhs <= 0) return cudaErrorInvalidValue;
-    return trsv<float>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, done, s);
+    return trsv<float>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, sync, status, done, s);
 }
 
 cudaError_t launch_pack_rhs(const double* B, int ldb, int n, int np, int nrhs, double* Bp,
@@ -392,9 +526,17 @@ cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, const in
 cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,
                             double* R, const int* done, cudaStream_t s)
 {
-    if (np % RT) return cudaErrorInvalidValue;
-    residual<<<np / RT, 256, 0, s>>>(A, np, Bp, X, nrhs, R, done);
-    count_launch();
+    if (np % CT) return cudaErrorInvalidValue;
+    for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
+        const int nr = std::min(MAXR, nrhs - c0);
+        const double* Bc = Bp + (size_t)c0 * np;
+        const double* Xc = X + (size_t)c0 * np;
+        double* Rc = R + (size_t)c0 * np;
+        if (nr <= 4) residual<4><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        else if (nr <= 8) residual<8><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        else residual<16><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

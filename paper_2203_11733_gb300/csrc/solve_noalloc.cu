@@ -59,7 +59,9 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
     if (!m->factored) return ctx_fail(ctx, GBEM_ERR_STATE, "solve before factor");
     const size_t np = (size_t)m->np;
     const size_t vec = align256(np * nrhs * sizeof(double));
-    const size_t need = 5 * vec + 256;   // B, X, R, W (two halves), flags and norm
+    const size_t nblk = np / 64;
+    const size_t need = 5 * vec + 256 + align256(nblk * sizeof(unsigned));   // B, X, R, W (two halves),
+                                                                             // flags and norm, block flags
     if (need > kScratchBytes)
         return ctx_fail(ctx, GBEM_ERR_ARG,
                         "gbem_solve_noalloc: needs " + std::to_string(need) + " bytes of scratch (padded N " +
@@ -86,6 +88,9 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
     void* W = base + 3 * vec;                       // 2 np nrhs entries of the solve type
     int* flags = reinterpret_cast<int*>(base + 5 * vec);
     double* norm = reinterpret_cast<double*>(base + 5 * vec + 64);
+    // block flags of the persistent solves: compared against a fresh epoch on
+    // every sweep, so their old contents never need clearing
+    unsigned* sync = reinterpret_cast<unsigned*>(base + 5 * vec + 256);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int n = m->n, npi = m->np;
 
@@ -99,8 +104,8 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
         double* Wd = static_cast<double*>(W);
         if ((e = cudaMemcpyAsync(Wd, Bp, sizeof(double) * np * nrhs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return fail(e, "copy");
-        if ((e = launch_trsv_f64(m->L64, static_cast<const double*>(m->Linv), npi, m->nb, Wd, nrhs, s)) !=
-            cudaSuccess)
+        if ((e = launch_trsv_f64(m->L64, static_cast<const double*>(m->Linv), npi, m->nb, Wd, nrhs, sync,
+                                 flags + 3, s)) != cudaSuccess)
             return fail(e, "trsv");
         if ((e = launch_unpack(Wd, npi, n, nrhs, X_dev, ldx, s)) != cudaSuccess) return fail(e, "unpack");
     } else {
@@ -111,8 +116,8 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
         const int maxit = ctx->tune.ir_max_iter > 0 ? ctx->tune.ir_max_iter : 10;
         for (int it = 0; it < maxit && !host_flags[1]; ++it) {
             if ((e = launch_to_f32(R, npi, nrhs, Wf, done, s)) != cudaSuccess ||
-                (e = launch_trsv_f32_guarded(m->A32, static_cast<const float*>(m->Linv), npi, m->nb, Wf, nrhs, done,
-                                             s)) != cudaSuccess ||
+                (e = launch_trsv_f32_guarded(m->A32, static_cast<const float*>(m->Linv), npi, m->nb, Wf, nrhs,
+                                             sync, flags + 3, done, s)) != cudaSuccess ||
                 (e = launch_add_f32(Wf, npi, nrhs, X, done, s)) != cudaSuccess ||
                 (e = launch_residual(m->A64, npi, Bp, X, nrhs, R, done, s)) != cudaSuccess ||
                 (e = launch_ir_check(R, Bp, npi, nrhs, norm, ctx->tune.ir_tol, flags, s)) != cudaSuccess)
@@ -129,9 +134,12 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
             return ctx_fail(ctx, GBEM_ERR_NOCONV, "gbem_solve_noalloc: refinement missed its tolerance");
         }
     }
-    if (ir_iters) {
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "sync");
-        *ir_iters = iters;
-    }
+    // the status words live in the shared scratch, so read them before returning
+    int fl[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(fl, flags, sizeof(fl), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(e, "sync");
+    if (ir_iters) *ir_iters = iters;
+    if (fl[3]) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "gbem_solve_noalloc: a bounded device wait gave up");
     return GBEM_OK;
 }
