@@ -524,8 +524,10 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
     } else {
         if (m->factored) return ctx_fail(ctx, GBEM_ERR_STATE, "mixed factor is in place; assemble again");
         if (!m->Linv) m->Linv = mat_alloc<float>(m, nblk * m->nb * m->nb, s);
-        if (!m->Linv) return GBEM_ERR_OOM;
-        if (!cuda_ok(ctx, launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, s),
+        if (!m->split) m->split = mat_alloc<unsigned char>(m, cholesky_f32_split_bytes(m->np), s);
+        if (!m->Linv || !m->split) return GBEM_ERR_OOM;
+        if (!cuda_ok(ctx,
+                     launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, m->split, s),
                      "cholesky"))
             return GBEM_ERR_CUDA;
     }

@@ -15,6 +15,7 @@
 // non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
 // factorisation completes without NaNs; the host reports GBEM_ERR_NOT_SPD.
 #include "gbem_internal.h"
+#include "tc_syrk.cuh"
 
 namespace {
 
@@ -218,11 +219,66 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
         }
 }
 
+// The 64-wide leading column strip of the trailing matrix (used when the
+// trailing order is an odd number of 64-blocks): tiles (t0 + 64 b, t0).
 template <typename T>
-cudaError_t cholesky(T* L, int np, T* Linv, int* info, cudaStream_t s)
+__global__ void __launch_bounds__(256) syrk_strip(T* __restrict__ L, int ld, int k0)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T* sa = reinterpret_cast<T*>(smem_raw);
+    T* sb = sa + NB * (NB + 1);
+    const int t0 = k0 + NB;
+    const int rI = t0 + NB * blockIdx.x, rJ = t0;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        int r = e % NB, c = e / NB;
+        sa[r * (NB + 1) + c] = L[(size_t)(rI + r) + (size_t)(k0 + c) * ld];
+        sb[r * (NB + 1) + c] = L[(size_t)(rJ + r) + (size_t)(k0 + c) * ld];
+    }
+    __syncthreads();
+    const int tr = (tid % 16) * 4, tc = (tid / 16) * 4;
+    T acc[4][4] = {};
+    for (int t = 0; t < NB; ++t) {
+        T x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = sa[(tr + u) * (NB + 1) + t];
+            y[u] = sb[(tc + u) * (NB + 1) + t];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) L[(size_t)(rI + tr + u) + (size_t)(rJ + tc + v) * ld] -= acc[u][v];
+}
+
+// Tensor-core trailing update of the lower 128 x 128 tiles of [r0, np)^2
+// (FP32 storage, 3xTF32 arithmetic) from the split panel; a bounded wait that
+// gives up sets status[0] = GBEM_ERR_TIMEOUT.
+__global__ void __launch_bounds__(256) syrk_tc(float* __restrict__ L, int ld, int r0,
+                                               const unsigned char* __restrict__ hi,
+                                               const unsigned char* __restrict__ lo, int* status)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    long long b = blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
+    while ((long long)I * (I + 1) / 2 > b) --I;
+    const int J = (int)(b - (long long)I * (I + 1) / 2);
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem) && threadIdx.x == 0)
+        atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+}
+
+template <typename T>
+cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s)
 {
     const int nblk = np / NB;
     const size_t smem = 2 * NB * (NB + 1) * sizeof(T);
+    constexpr bool kTensor = sizeof(T) == 4;   // FP32 storage: trailing update on tcgen05
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(NB * (NB + 1) * sizeof(T)))) != cudaSuccess)
@@ -233,14 +289,41 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, cudaStream_t s)
     if ((e = cudaFuncSetAttribute(syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(syrk_strip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    if (kTensor &&
+        (e = cudaFuncSetAttribute(syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
+            cudaSuccess)
+        return e;
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * NB;
         potrf_diag<T><<<1, 256, NB * (NB + 1) * sizeof(T), s>>>(L, np, k0, Linv, info);
         count_launch();
-        const int m = nblk - k - 1;
-        if (m > 0) {
-            trsm_panel<T><<<m, 256, smem, s>>>(L, np, k0, Linv);
-            count_launch();
+        const int m = nblk - k - 1;   // trailing order in 64-blocks
+        if (m <= 0) continue;
+        trsm_panel<T><<<m, 256, smem, s>>>(L, np, k0, Linv);
+        count_launch();
+        if (kTensor) {
+            int r0 = k0 + NB;
+            if (m & 1) {
+                syrk_strip<T><<<m, 256, smem, s>>>(L, np, k0);
+                count_launch();
+                r0 += NB;
+            }
+            const long long nt = (np - r0) / tc::TM;
+            if (nt > 0) {
+                unsigned char* hi = split;
+                unsigned char* lo = split + (size_t)nt * tc::OPER_BYTES;
+                const long long elems = (long long)(np - r0) * tc::TK;
+                const int sgrid = (int)std::min<long long>(4096, (elems + 255) / 256);
+                tc::split_panel<<<sgrid, 256, 0, s>>>(reinterpret_cast<const float*>(L), np, k0, r0, np, hi, lo);
+                count_launch();
+                syrk_tc<<<(unsigned)(nt * (nt + 1) / 2), 256, tc::SMEM_BYTES, s>>>(reinterpret_cast<float*>(L), np,
+                                                                                     r0, hi, lo, info + 3);
+                count_launch();
+            }
+        } else {
             long long tiles = (long long)m * (m + 1) / 2;
             syrk_update<T><<<(unsigned)tiles, 256, smem, s>>>(L, np, k0);
             count_launch();
@@ -254,11 +337,14 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, cudaStream_t s)
 cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s)
 {
     if (nb != NB || np % NB) return cudaErrorInvalidValue;
-    return cholesky<double>(L, np, Linv, info, s);
+    return cholesky<double>(L, np, Linv, info, nullptr, s);
 }
 
-cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, cudaStream_t s)
+size_t cholesky_f32_split_bytes(int np) { return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES; }
+
+cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
+                                cudaStream_t s)
 {
-    if (nb != NB || np % NB) return cudaErrorInvalidValue;
-    return cholesky<float>(L, np, Linv, info, s);
+    if (nb != NB || np % tc::TM || !split) return cudaErrorInvalidValue;
+    return cholesky<float>(L, np, Linv, info, split, s);
 }

@@ -79,6 +79,7 @@ struct gbem_matrix_s {
     float* A32 = nullptr;       // mixed: FP32 copy, factored in place
     double* L64 = nullptr;      // FP64 mode: the factor
     void* Linv = nullptr;       // inverses of the diagonal blocks (T)
+    unsigned char* split = nullptr;  // mixed: hi/lo copies of one panel for the tensor-core update
     int* dflags = nullptr;      // [0] not-SPD pivot, [1] IR done, [2] IR iters, [3] wait timeout
     unsigned* dsync = nullptr;  // one flag per 64-row block for the persistent solves
     unsigned long long* dcounts = nullptr; // pair class counts (8)
@@ -113,7 +114,11 @@ cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, dou
 cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
 cudaError_t launch_copy_lower(const double* A, double* L, int np, cudaStream_t s);
 cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s);
-cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, cudaStream_t s);
+// The FP32 factor's tensor-core update needs `split` work space of
+// cholesky_f32_split_bytes(np) bytes (the hi/lo copies of one panel).
+size_t cholesky_f32_split_bytes(int np);
+cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
+                                cudaStream_t s);
 // W (np x nrhs, followed by np x nrhs of work space) := A^-1 W with the
 // factor L and its diagonal-block inverses; sync: np/64 flags, status: word
 // that receives GBEM_ERR_TIMEOUT if a bounded device wait gives up.

@@ -1,0 +1,249 @@
+// Tensor-core (tcgen05, kind::tf32) trailing update of the blocked Cholesky:
+//
+//     C[I, J] -= A_I A_J^T        (A_I, A_J: 128 x 64 row blocks of the panel)
+//
+// in 3xTF32 arithmetic: every fp32 operand is split as a = a_hi + a_lo with
+// a_hi = tf32(a) (round to nearest) and a_lo = a - a_hi, and the product is
+// accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi, which keeps
+// the error of the update near FP32 rounding.
+//
+// The panel columns [k0, k0 + 64) are split once per elimination step by
+// split_panel into hi and lo copies laid out, per 128-row block, exactly as
+// the tensor core reads them from shared memory: the canonical K-major layout
+// without swizzle, 8-row x 16-byte core matrices consecutive along K (leading
+// byte offset 128 B, 16 of them for the 64 panel columns) and then along M/N
+// (stride byte offset 2048 B).  A 128-row block of one part is 32 KB of
+// contiguous bytes.
+//
+// One CTA (8 warps) owns one 128 x 128 tile:
+//   1. warp 0 allocates 128 TMEM columns (the FP32 accumulator, one lane per
+//      tile row);
+//   2. one thread bulk-copies the hi/lo blocks of rows I and J into shared
+//      memory (cp.async.bulk, completing on an mbarrier; diagonal tiles copy
+//      one pair);
+//   3. after the bounded wait, one thread issues 8 K-steps x 3 tcgen05.mma
+//      (M = N = 128, K = 8) and commits them to a second mbarrier;
+//   4. every warp waits (bounded), reads 32 accumulator lanes x 64 columns
+//      with tcgen05.ld and subtracts them from C in global memory;
+//   5. warp 0 frees the TMEM columns.
+#pragma once
+
+#include <cstdint>
+
+namespace tc {
+
+constexpr int TM = 128;       // tile rows (MMA M) and columns (MMA N)
+constexpr int TK = 64;        // panel width (sum over K)
+constexpr int OPER_BYTES = TM * TK * 4;                 // one operand part (hi or lo)
+constexpr int SMEM_BYTES = 4 * OPER_BYTES + 256;        // A_hi, A_lo, B_hi, B_lo, barrier + TMEM slot
+constexpr long long kWaitLimit = 1LL << 20;             // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Byte offset of element (row r, k) of a 128 x 64 fp32 operand in the K-major,
+// no-swizzle core-matrix layout.
+__device__ __forceinline__ uint32_t kmajor_offset(int r, int k)
+{
+    return (uint32_t)((k >> 2) * 128 + (r >> 3) * (TK / 4) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits
+// 0-13, leading byte offset >> 4 in bits 16-29, stride byte offset >> 4 in
+// bits 32-45, descriptor version 1 in bits 46-47, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(((TK / 4) * 128) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D fp32 (bits 4-5 = 1), A and B tf32
+// (bits 7-9 = 2, bits 10-12 = 2), both K-major, N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc()
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Load 16 consecutive fp32 accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi/lo split of panel rows [r0, np) x columns [k0, k0 + 64) of the
+// column-major L into the block layout above (one thread per element).
+__global__ void split_panel(const float* __restrict__ L, int ld, int k0, int r0, int np,
+                            unsigned char* __restrict__ hi, unsigned char* __restrict__ lo)
+{
+    const long long total = (long long)(np - r0) * TK;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % (np - r0)), k = (int)(e / (np - r0));
+        const float x = L[(size_t)(r0 + r) + (size_t)(k0 + k) * ld];
+        const float h = to_tf32(x);
+        const size_t off = (size_t)(r / TM) * OPER_BYTES + kmajor_offset(r % TM, k);
+        *reinterpret_cast<float*>(hi + off) = h;
+        *reinterpret_cast<float*>(lo + off) = x - h;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait on phase 0 of an mbarrier.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar)
+{
+    long long spins = 0;
+    while (!mbar_try_wait(bar, 0))
+        if (++spins > kWaitLimit) return false;
+    return true;
+}
+
+// C[rI + .., rJ + ..] -= A_I A_J^T for one 128 x 128 tile.  I and J index the
+// 128-row blocks of the split panel (rows rI = r0 + 128 I, rJ = r0 + 128 J).
+// 256 threads.  Returns false if a bounded wait gave up.
+__device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
+                          const unsigned char* __restrict__ lo, int I, int J, unsigned char* smem)
+{
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + OPER_BYTES;
+    unsigned char* b_hi = (I == J) ? a_hi : smem + 2 * OPER_BYTES;
+    unsigned char* b_lo = (I == J) ? a_lo : smem + 3 * OPER_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * OPER_BYTES);   // [0] operands, [1] MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * OPER_BYTES + 64);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        mbar_init(bar_ld, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint32_t parts = (I == J) ? 2 : 4;
+        mbar_expect_tx(bar_ld, parts * OPER_BYTES);
+        bulk_g2s(smem_u32(a_hi), hi + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
+        bulk_g2s(smem_u32(a_lo), lo + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
+        if (I != J) {
+            bulk_g2s(smem_u32(b_hi), hi + (size_t)J * OPER_BYTES, OPER_BYTES, bar_ld);
+            bulk_g2s(smem_u32(b_lo), lo + (size_t)J * OPER_BYTES, OPER_BYTES, bar_ld);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    bool ok = true;
+    if (tid == 0) {
+        ok = mbar_wait_bounded(bar_ld);
+        if (ok) {
+            const uint32_t idesc = make_idesc();
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+            for (int ks = 0; ks < TK / 8; ++ks) {
+                const uint32_t off = ks * 256;   // 8 tf32 = two core matrices along K
+                mma_tf32(tmem, make_desc(ah + off), make_desc(bh + off), idesc, ks > 0);
+                mma_tf32(tmem, make_desc(ah + off), make_desc(bl + off), idesc, 1);
+                mma_tf32(tmem, make_desc(al + off), make_desc(bh + off), idesc, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar_mma)
+                         : "memory");
+        }
+    }
+    // every thread learns whether the operand wait succeeded
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (ok) ok = mbar_wait_bounded(bar_mma);
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
+        const int q = warp & 3, half = warp >> 2;
+        const int row = q * 32 + (tid & 31);
+        float* crow = L + (size_t)(rI + row);
+#pragma unroll 1
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+            float v[16], c[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) c[i] = crow[(size_t)(rJ + c0 + i) * ld];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) crow[(size_t)(rJ + c0 + i) * ld] = c[i] - v[i];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM) : "memory");
+    }
+    return ok;
+}
+
+}  // namespace tc
