@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=200000)
+    ap.add_argument("--workload", default="crossing_bus_2x2", choices=["crossing_bus_2x2", "batch512", "serving"],
+                    help="crossing_bus_2x2: the headline line; batch512 / serving: the batched and served forms")
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--profile", default=None, choices=["mixed", "fp64"],
                     help="one warm-up and one extraction in that precision, nothing else "
                          "(for ncu captures)")
@@ -385,10 +388,106 @@ def roofline(stats, steps, n, nc, ctx, mesh, lib):
     return out
 
 
+def run_batch(args):
+    """512 independent 2-6 bar structures (N log-uniform in [200, 3000]):
+    one graph launch for the whole batch, against one-at-a-time extractions
+    (mixed and FP64) of the same structures on the same GPU."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem, workloads as W
+    B.build()
+    structs = W.batch_small_structures(seed=4242 + rank, count=args.batch_count)
+    ctx = gbem.Context(local)
+    meshes = [ctx.mesh(b, p) for b, p in structs]
+    ns = np.array([m.n for m in meshes])
+    t0 = time.perf_counter()
+    batch = gbem.Batch(ctx, meshes)
+    t_create = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        Cs, res = batch.run(W.EPS_R_SIO2, stream)
+    ctx.lib.gbem_get_stats.argtypes = [ctypes_void(), ctypes_void(), ctypes_int()]
+    gbem_stats(ctx, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Cs, res = batch.run(W.EPS_R_SIO2, stream)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    st = gbem_stats(ctx, reset=True)
+    ms_batch = total / args.steps
+    # one at a time, same structures, same GPU
+    def one_at_a_time(prec, idx):
+        t = 0.0
+        out = []
+        for i in idx:
+            m = meshes[i]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mat = gbem.gbem_assemble(m, prec, stream)
+            C, _ = gbem.gbem_capacitance(m, mat, W.EPS_R_SIO2, stream, want_residual=False)
+            e1.record(stream)
+            e1.synchronize()
+            mat.close()
+            t += e0.elapsed_time(e1)
+            out.append(C)
+        return t, out
+    idx = list(range(len(meshes)))
+    one_at_a_time(gbem.GBEM_MIXED, idx[:4])
+    t_mixed, C_mixed = one_at_a_time(gbem.GBEM_MIXED, idx)
+    sub = idx[::8]                      # FP64 one at a time on every 8th structure (time bound)
+    t64, C64 = one_at_a_time(gbem.GBEM_FP64, sub)
+    err_vs_fp64 = max(float(np.max(np.abs(Cs[i] - C)) / np.max(np.abs(C))) for i, C in zip(sub, C64))
+    err_vs_single = max(float(np.max(np.abs(Cs[i] - C)) / np.max(np.abs(C))) for i, C in zip(idx, C_mixed))
+    n_ext = len(meshes)
+    line = {
+        "metric": "extractions/s", "value": world * n_ext / (ms_batch * 1e-3), "unit": "extractions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+        "data": "synthetic",
+        "config": {"workload": f"batch{n_ext}: 2-6 parallel/crossing bars, N log-uniform [200,3000]",
+                   "n_structures": n_ext, "n_panels_total": int(ns.sum()), "n_min": int(ns.min()),
+                   "n_max": int(ns.max()), "refinement_passes": 3, "graph_kernels_per_launch": int(st["launches"] / args.steps)},
+        "pairs_per_s": world * float((ns * (ns + 1) / 2).sum()) / (ms_batch * 1e-3),
+        "one_at_a_time_mixed": {"extractions_per_s": n_ext / (t_mixed * 1e-3), "ms_total": t_mixed},
+        "one_at_a_time_fp64": {"extractions_per_s": len(sub) / (t64 * 1e-3), "structures": len(sub)},
+        "batch_over_single_mixed": t_mixed / ms_batch,
+        "batch_over_single_fp64": (t64 / len(sub) * n_ext) / ms_batch,
+        "cap_rel_err_vs_fp64_gpu": err_vs_fp64, "cap_rel_err_vs_single_mixed": err_vs_single,
+        "max_residual": float(np.max(res)), "batch_create_s": t_create, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    ctx.close()
+
+
+def ctypes_void():
+    import ctypes
+    return ctypes.c_void_p
+
+
+def ctypes_int():
+    import ctypes
+    return ctypes.c_int
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch512":
+        run_batch(args)
     else:
         run_ours(args)
 

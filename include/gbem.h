@@ -225,6 +225,31 @@ typedef struct {
 gbem_status gbem_set_timing(gbem_ctx* ctx, int enable);
 gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset);
 
+/* Batched extraction: many independent structures (meshes of one context)
+ * assembled, factored and solved together in mixed precision.  The whole
+ * pipeline -- batched assembly over every tile of every structure, the
+ * batched Cholesky (one launch per elimination step for all structures),
+ * `iters` FP64 refinement passes, residuals and capacitances -- is captured
+ * once into a CUDA graph on the batch's own stream and replayed by each
+ * gbem_batch_run (one graph launch).  The meshes' panel data are copied at
+ * creation; the meshes may be destroyed afterwards.  iters 0 selects 3.
+ * Every structure has at most 16 conductors. */
+typedef struct gbem_batch_s gbem_batch_t;
+gbem_status gbem_batch_create(gbem_ctx* ctx, int count, gbem_mesh_t* const* meshes, int iters,
+                              gbem_batch_t** out);
+/* Run the batch after work already enqueued on `stream`, and wait for it.
+ * C_host receives the capacitance matrices back to back (structure b's
+ * n_c(b) x n_c(b) row-major block at the offset reported by
+ * gbem_batch_info); resid_host (may be NULL) the final relative residual of
+ * each structure. */
+gbem_status gbem_batch_run(gbem_batch_t* batch, double eps_r, double* C_host, double* resid_host,
+                           gbem_stream stream);
+/* count structures; c_total = total length of C_host; c_offset (array of
+ * count, may be NULL) = offset of each structure's block. */
+gbem_status gbem_batch_info(const gbem_batch_t* batch, int* count, long long* c_total,
+                            long long* c_offset);
+void gbem_batch_destroy(gbem_batch_t* batch);
+
 /* Matrix order N and the number of panel pairs by class: pairs evaluated by
  * closed form, and by Gauss-Legendre order 1..6 (counts[0] closed form,
  * counts[n] order n; array of 7).  Waits for the assembly stream. */

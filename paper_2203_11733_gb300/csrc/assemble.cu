@@ -310,11 +310,11 @@ __device__ double eval_class(const TileGeo& G, int cls, int s, int t)
     }
 }
 
+// One 32 x 32 lower tile (linear index b over the lower triangle of tiles).
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, float q_near,
-                                                           double* __restrict__ A64,
-                                                           float* __restrict__ A32,
-                                                           unsigned long long* __restrict__ counts)
+__device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_near, double* __restrict__ A64,
+                                          float* __restrict__ A32, unsigned long long* __restrict__ counts,
+                                          long long b)
 {
     using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ TileGeo G;
@@ -325,8 +325,7 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, 
 
     const int tid = threadIdx.x;
     if (tid == 0) {
-        // lower-triangular tile coordinates (TI >= TJ) from the linear block index
-        long long b = blockIdx.x;
+        // lower-triangular tile coordinates (TI >= TJ) from the linear tile index
         int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
         while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
         while ((long long)TI * (TI + 1) / 2 > b) --TI;
@@ -453,9 +452,60 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, 
         if (MIXED) A32[i + j * (size_t)np] = (float)v;
     }
     // class counts: near pairs, then far pairs by order
-    if (tid < kClasses) {
+    if (tid < kClasses && counts) {
         int order = tid < 2 ? 0 : 1 + (tid - 2) / 2;
         if (cls_cnt[tid]) atomicAdd(&counts[order], (unsigned long long)cls_cnt[tid]);
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, float q_near,
+                                                           double* __restrict__ A64,
+                                                           float* __restrict__ A32,
+                                                           unsigned long long* __restrict__ counts)
+{
+    tile_body<MIXED>(g, np, q_near, A64, A32, counts, blockIdx.x);
+}
+
+// Batched assembly: CTA index -> (structure, tile) through the prefix sums of
+// the structures' tile counts.
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads) assemble_batched(BatchView v, float q_near)
+{
+    __shared__ int sb;
+    if (threadIdx.x == 0) sb = batch_find(v.tile_prefix, v.nb, (long long)blockIdx.x);
+    __syncthreads();
+    const int b = sb;
+    const long long po = v.poff[b];
+    DevPanels g;
+    g.c = v.c + po;
+    g.lo0 = v.lo0 + po;
+    g.hi0 = v.hi0 + po;
+    g.lo1 = v.lo1 + po;
+    g.hi1 = v.hi1 + po;
+    g.axis = v.axis + po;
+    g.cond = v.cond + po;
+    g.n = v.n[b];
+    tile_body<MIXED>(g, v.np[b], q_near, v.A64 + v.moff[b], MIXED ? v.A32 + v.moff[b] : nullptr, nullptr,
+                     (long long)blockIdx.x - v.tile_prefix[b]);
+}
+
+// Identity padding of every structure of a batch (rows n..np-1, lower part).
+__global__ void pad_batched(BatchView v)
+{
+    const int b = blockIdx.y;
+    const int n = v.n[b], np = v.np[b];
+    double* A64 = v.A64 + v.moff[b];
+    float* A32 = v.A32 ? v.A32 + v.moff[b] : nullptr;
+    long long total = (long long)(np - n) * np;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int r = n + (int)(e % (np - n));
+        int c = (int)(e / (np - n));
+        if (c > r) continue;
+        double val = (r == c) ? 1.0 : 0.0;
+        A64[r + (size_t)c * np] = val;
+        if (A32) A32[r + (size_t)c * np] = (float)val;
     }
 }
 
@@ -552,6 +602,20 @@ cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, dou
     else
         assemble_tiles<false><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, nullptr,
                                                                    counts);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_batched(const BatchView& v, long long tiles, gbem_precision prec, double q_near,
+                                    cudaStream_t s)
+{
+    if (tiles <= 0) return cudaSuccess;
+    pad_batched<<<dim3(64, v.nb), 256, 0, s>>>(v);
+    count_launch();
+    if (prec == GBEM_MIXED)
+        assemble_batched<true><<<(unsigned)tiles, kThreads, 0, s>>>(v, (float)q_near);
+    else
+        assemble_batched<false><<<(unsigned)tiles, kThreads, 0, s>>>(v, (float)q_near);
     count_launch();
     return cudaGetLastError();
 }

@@ -29,8 +29,8 @@ constexpr int NB = 64;
 // by 1/sqrt(a_jj) at the end.  The inverse L^-1 is then formed the same way,
 // by forward elimination of the identity.
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_diag(T* __restrict__ L, int ld, int k0,
-                                                  T* __restrict__ Linv, int* __restrict__ info)
+__device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
+                                           int* __restrict__ info)
 {
     extern __shared__ unsigned char smem_raw[];
     T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);   // the factor, for the inverse
@@ -138,16 +138,22 @@ __global__ void __launch_bounds__(256) potrf_diag(T* __restrict__ L, int ld, int
         for (int v = 0; v < 4; ++v) Lb[(r0 + u) + (size_t)(c0 + v) * NB] = y[u][v];
 }
 
-// L_ik = A_ik Linv_kk^T for the row block starting at k0 + NB * (1 + blockIdx.x)
 template <typename T>
-__global__ void __launch_bounds__(256) trsm_panel(T* __restrict__ L, int ld, int k0,
-                                                  const T* __restrict__ Linv)
+__global__ void __launch_bounds__(256) potrf_diag(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
+                                                  int* __restrict__ info)
+{
+    potrf_body<T>(L, ld, k0, Linv, info);
+}
+
+// L_ik = A_ik Linv_kk^T for the row block starting at k0 + NB * (1 + i)
+template <typename T>
+__device__ __forceinline__ void trsm_body(T* __restrict__ L, int ld, int k0, const T* __restrict__ Linv, int i)
 {
     extern __shared__ unsigned char smem_raw[];
     T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
     T(*iv)[NB + 1] = a + NB;
     const int tid = threadIdx.x;
-    const int r0 = k0 + NB * (1 + blockIdx.x);
+    const int r0 = k0 + NB * (1 + i);
     const T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         int r = e % NB, c = e / NB;
@@ -176,14 +182,19 @@ __global__ void __launch_bounds__(256) trsm_panel(T* __restrict__ L, int ld, int
         for (int v = 0; v < 4; ++v) L[(size_t)(r0 + tr + u) + (size_t)(k0 + tc + v) * ld] = acc[u][v];
 }
 
-// A_IJ -= L_Ik L_Jk^T for the lower tiles (I >= J) of the trailing matrix.
 template <typename T>
-__global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, int k0)
+__global__ void __launch_bounds__(256) trsm_panel(T* __restrict__ L, int ld, int k0, const T* __restrict__ Linv)
+{
+    trsm_body<T>(L, ld, k0, Linv, blockIdx.x);
+}
+
+// A_IJ -= L_Ik L_Jk^T for the lower tile b (I >= J) of the trailing matrix.
+template <typename T>
+__device__ __forceinline__ void syrk_body(T* __restrict__ L, int ld, int k0, long long b)
 {
     extern __shared__ unsigned char smem_raw[];
     T* sa = reinterpret_cast<T*>(smem_raw);   // [NB][NB+1]  rows of block I
     T* sb = sa + NB * (NB + 1);               // [NB][NB+1]  rows of block J
-    long long b = blockIdx.x;
     int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
@@ -217,6 +228,12 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
             size_t idx = (size_t)(rI + tr + u) + (size_t)(rJ + tc + v) * ld;
             L[idx] -= acc[u][v];
         }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, int k0)
+{
+    syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
 // The 64-wide leading column strip of the trailing matrix (used when the
@@ -332,6 +349,36 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
     return cudaGetLastError();
 }
 
+// ---- batched factorisation: elimination step k of every structure of a
+// batch at once (FP32 storage).  steps[k * (nb + 1) ..] holds, per step, the
+// prefix sums over structures of their panel blocks below the diagonal
+// (trsm) and, at offset nsteps * (nb + 1), of their trailing tiles (syrk).
+__global__ void __launch_bounds__(256) potrf_batched(BatchView v, int k)
+{
+    const int b = blockIdx.x;
+    const int np = v.np[b];
+    if (k * NB >= np) return;
+    potrf_body<float>(v.A32 + v.moff[b], np, k * NB, v.Linv + v.ioff[b], v.flags + 4 * b);
+}
+
+__global__ void __launch_bounds__(256) trsm_batched(BatchView v, int k, const long long* __restrict__ prefix)
+{
+    __shared__ int sb;
+    if (threadIdx.x == 0) sb = batch_find(prefix, v.nb, (long long)blockIdx.x);
+    __syncthreads();
+    const int b = sb;
+    trsm_body<float>(v.A32 + v.moff[b], v.np[b], k * NB, v.Linv + v.ioff[b], (int)(blockIdx.x - prefix[b]));
+}
+
+__global__ void __launch_bounds__(256) syrk_batched(BatchView v, int k, const long long* __restrict__ prefix)
+{
+    __shared__ int sb;
+    if (threadIdx.x == 0) sb = batch_find(prefix, v.nb, (long long)blockIdx.x);
+    __syncthreads();
+    const int b = sb;
+    syrk_body<float>(v.A32 + v.moff[b], v.np[b], k * NB, (long long)blockIdx.x - prefix[b]);
+}
+
 }  // namespace
 
 cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s)
@@ -347,4 +394,34 @@ cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info
 {
     if (nb != NB || np % tc::TM || !split) return cudaErrorInvalidValue;
     return cholesky<float>(L, np, Linv, info, split, s);
+}
+
+cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long long* steps_dev,
+                                    const long long* steps_host, cudaStream_t s)
+{
+    const size_t smem = 2 * NB * (NB + 1) * sizeof(float);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(potrf_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(NB * (NB + 1) * sizeof(float)))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(trsm_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(syrk_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    const int nb1 = v.nb + 1;
+    for (int k = 0; k < nsteps; ++k) {
+        potrf_batched<<<v.nb, 256, NB * (NB + 1) * sizeof(float), s>>>(v, k);
+        count_launch();
+        const long long ntrsm = steps_host[(size_t)k * nb1 + v.nb];
+        const long long nsyrk = steps_host[(size_t)(nsteps + k) * nb1 + v.nb];
+        if (ntrsm > 0) {
+            trsm_batched<<<(unsigned)ntrsm, 256, smem, s>>>(v, k, steps_dev + (size_t)k * nb1);
+            count_launch();
+        }
+        if (nsyrk > 0) {
+            syrk_batched<<<(unsigned)nsyrk, 256, smem, s>>>(v, k, steps_dev + (size_t)(nsteps + k) * nb1);
+            count_launch();
+        }
+    }
+    return cudaGetLastError();
 }

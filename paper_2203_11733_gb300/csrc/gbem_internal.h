@@ -55,6 +55,45 @@ struct DevPanels {
     int n = 0;
 };
 
+// Device view of a batch of independent structures (pooled buffers; every
+// per-structure array has nb entries, prefix arrays nb + 1).
+struct BatchView {
+    int nb = 0;
+    const int* n = nullptr;           // panels
+    const int* np = nullptr;          // padded order (multiple of 128)
+    const int* nc = nullptr;          // conductors
+    const long long* poff = nullptr;  // panel offset in the panel pools
+    const long long* moff = nullptr;  // matrix offset (elements) in A64 / A32
+    const long long* voff = nullptr;  // vector offset (elements) in B, X, R, W, Y (np x nc)
+    const long long* ioff = nullptr;  // inverse-block offset (elements) in Linv (np/64 * 4096)
+    const long long* coff = nullptr;  // capacitance offset (nc x nc) in C
+    const long long* tile_prefix = nullptr;   // assembly tiles
+    const long long* rows_prefix = nullptr;   // 16-row blocks (residual)
+    const double *c = nullptr, *lo0 = nullptr, *hi0 = nullptr, *lo1 = nullptr, *hi1 = nullptr;
+    const int8_t* axis = nullptr;
+    const int32_t* cond = nullptr;
+    double* A64 = nullptr;
+    float* A32 = nullptr;
+    float* Linv = nullptr;
+    double *B = nullptr, *X = nullptr, *R = nullptr;
+    float *W = nullptr, *Y = nullptr;
+    int* flags = nullptr;             // 4 per structure: [0] not SPD, [3] wait timeout
+    double* C = nullptr;
+    double* resid = nullptr;          // per structure: final relative residual
+};
+
+// Structure owning global index x given prefix sums p[0..nb] (p[0] = 0).
+__host__ __device__ inline int batch_find(const long long* p, int nb, long long x)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (p[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 struct gbem_mesh_s {
     gbem_ctx* ctx = nullptr;
     int n = 0;
@@ -112,6 +151,17 @@ cudaError_t gl_upload();
 cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
                             double* A64, float* A32, unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
+cudaError_t launch_assemble_batched(const BatchView& v, long long tiles, gbem_precision prec, double q_near,
+                                    cudaStream_t s);
+cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long long* steps_dev,
+                                    const long long* steps_host, cudaStream_t s);
+// Batched solve: begin (right-hand sides, X = 0, R = B), then per refinement
+// iteration W = f32(R), W = A32^-1 W, X += W, R = B - A64 X; finish writes the
+// residual and the capacitance matrix of every structure.
+cudaError_t launch_batch_begin(const BatchView& v, cudaStream_t s);
+cudaError_t launch_batch_iteration(const BatchView& v, size_t vec_total, long long row_blocks, int max_nc,
+                                   cudaStream_t s);
+cudaError_t launch_batch_finish(const BatchView& v, double scale, cudaStream_t s);
 cudaError_t launch_copy_lower(const double* A, double* L, int np, cudaStream_t s);
 cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* info, cudaStream_t s);
 // The FP32 factor's tensor-core update needs `split` work space of

@@ -320,17 +320,15 @@ __global__ void add_f32(const float* __restrict__ W, size_t total, double* __res
 constexpr int RT = 16;
 constexpr int CT = 64;
 template <int RR>
-__global__ void __launch_bounds__(256) residual(const double* __restrict__ A, int np,
-                                                const double* __restrict__ Bp,
-                                                const double* __restrict__ X, int nrhs,
-                                                double* __restrict__ R, const int* done)
+__device__ __forceinline__ void residual_body(const double* __restrict__ A, int np, const double* __restrict__ Bp,
+                                              const double* __restrict__ X, int nrhs, double* __restrict__ R,
+                                              int blk)
 {
-    if (done && *done) return;
     __shared__ double a[RT][CT + 1];
     __shared__ double xs[CT][RR + 1];
     __shared__ double part[8][RT][RR];
     const int tid = threadIdx.x;
-    const int i0 = blockIdx.x * RT;
+    const int i0 = blk * RT;
     const int ri = tid % RT, grp = tid / RT;  // 16 column groups
     for (int c0 = 0; c0 < nrhs; c0 += RR) {
         const int nr = min(RR, nrhs - c0);
@@ -386,6 +384,15 @@ __global__ void __launch_bounds__(256) residual(const double* __restrict__ A, in
         }
         __syncthreads();
     }
+}
+
+template <int RR>
+__global__ void __launch_bounds__(256) residual(const double* __restrict__ A, int np, const double* __restrict__ Bp,
+                                                const double* __restrict__ X, int nrhs, double* __restrict__ R,
+                                                const int* done)
+{
+    if (done && *done) return;
+    residual_body<RR>(A, np, Bp, X, nrhs, R, blockIdx.x);
 }
 
 // max_k |R_k|_inf / |B_k|_inf -> norm[0]; converged -> flags[1] = 1, else
@@ -462,6 +469,157 @@ static int grid_for(size_t total)
 {
     size_t g = (total + 255) / 256;
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+// ------------------------------------------------------------------ batches
+
+// Right-hand sides (indicator of each conductor), X = 0, R = B, per structure.
+__global__ void batch_begin(BatchView v)
+{
+    const int b = blockIdx.y;
+    const int n = v.n[b], np = v.np[b], nc = v.nc[b];
+    const int32_t* cond = v.cond + v.poff[b];
+    const long long o = v.voff[b];
+    const size_t total = (size_t)np * nc;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % np), k = (int)(e / np);
+        const double bv = (r < n && cond[r] == k) ? 1.0 : 0.0;
+        v.B[o + e] = bv;
+        v.R[o + e] = bv;
+        v.X[o + e] = 0.0;
+    }
+}
+
+__global__ void batch_to_f32(const double* __restrict__ R, float* __restrict__ W, size_t total)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        W[e] = (float)R[e];
+}
+
+__global__ void batch_add(const float* __restrict__ W, double* __restrict__ X, size_t total)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        X[e] += (double)W[e];
+}
+
+// W := L^-T L^-1 W for one structure per CTA: the block sweeps of the
+// persistent solve, run by a single CTA so no CTA waits on another.
+template <int R>
+__global__ void __launch_bounds__(256) trsv_batched(BatchView v)
+{
+    const int b = blockIdx.x;
+    const int np = v.np[b], nr = v.nc[b], nblk = np / NB;
+    const float* __restrict__ L = v.A32 + v.moff[b];
+    const float* __restrict__ Linv = v.Linv + v.ioff[b];
+    float* W = v.W + v.voff[b];
+    float* Y = v.Y + v.voff[b];
+    __shared__ float iv[NB][NB + 1];
+    __shared__ float sv[NB][R];
+    __shared__ float part[4][NB][R];
+    __shared__ float sw[NB][R];
+    const int tid = threadIdx.x, r = tid & (NB - 1), q = tid >> 6;
+    for (int dir = 0; dir < 2; ++dir) {
+        const float* src = dir == 0 ? W : Y;   // right-hand side of this sweep
+        float* dst = dir == 0 ? Y : W;          // its solution
+        for (int s = 0; s < nblk; ++s) {
+            const int bk = dir == 0 ? s : nblk - 1 - s;
+            const int b0 = bk * NB;
+            float acc[R];
+#pragma unroll
+            for (int c = 0; c < R; ++c) acc[c] = 0.f;
+            for (int t2 = 0; t2 < s; ++t2) {
+                const int j = dir == 0 ? t2 : nblk - 1 - t2;
+                const int j0 = j * NB;
+                for (int e = tid; e < NB * R; e += blockDim.x) {
+                    const int t = e % NB, c = e / NB;
+                    sv[t][c] = (c < nr) ? dst[(size_t)(j0 + t) + (size_t)c * np] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int tt = 0; tt < NB / 4; ++tt) {
+                    const int t = q * (NB / 4) + tt;
+                    // forward: L[b0 + r][j0 + t]; backward: L[j0 + t][b0 + r]
+                    const float l = dir == 0 ? L[(size_t)(b0 + r) + (size_t)(j0 + t) * np]
+                                             : L[(size_t)(j0 + t) + (size_t)(b0 + r) * np];
+#pragma unroll
+                    for (int c = 0; c < R; ++c) acc[c] += l * sv[t][c];
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < NB * NB; e += blockDim.x) iv[e % NB][e / NB] = Linv[(size_t)bk * NB * NB + e];
+#pragma unroll
+            for (int c = 0; c < R; ++c) part[q][r][c] = acc[c];
+            __syncthreads();
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                const float rhs = (c < nr) ? src[(size_t)(b0 + t) + (size_t)c * np] : 0.f;
+                sw[t][c] = rhs - (((part[0][t][c] + part[1][t][c]) + part[2][t][c]) + part[3][t][c]);
+            }
+            __syncthreads();
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                if (c >= nr) continue;
+                float sum = 0.f;
+                if (dir == 0)
+                    for (int k = 0; k <= t; ++k) sum += iv[t][k] * sw[k][c];
+                else
+                    for (int k = t; k < NB; ++k) sum += iv[k][t] * sw[k][c];
+                dst[(size_t)(b0 + t) + (size_t)c * np] = sum;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// R = B - A X over every 16-row block of every structure.
+template <int RR>
+__global__ void __launch_bounds__(256) residual_batched(BatchView v)
+{
+    __shared__ int sb;
+    if (threadIdx.x == 0) sb = batch_find(v.rows_prefix, v.nb, (long long)blockIdx.x);
+    __syncthreads();
+    const int b = sb;
+    const long long o = v.voff[b];
+    residual_body<RR>(v.A64 + v.moff[b], v.np[b], v.B + o, v.X + o, v.nc[b], v.R + o,
+                      (int)(blockIdx.x - v.rows_prefix[b]));
+}
+
+// Final relative residual and capacitance of each structure (one CTA each).
+__global__ void batch_finish(BatchView v, double scale)
+{
+    const int b = blockIdx.x;
+    const int n = v.n[b], np = v.np[b], nc = v.nc[b];
+    const long long o = v.voff[b];
+    const int32_t* cond = v.cond + v.poff[b];
+    __shared__ double red[256];
+    double worst = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        double m = 0.0;
+        for (int r = threadIdx.x; r < np; r += blockDim.x) m = fmax(m, fabs(v.R[o + r + (size_t)c * np]));
+        red[threadIdx.x] = m;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+            __syncthreads();
+        }
+        worst = fmax(worst, red[0]);   // |B_c|_inf = 1 for an indicator right-hand side
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) v.resid[b] = worst;
+    for (int mk = 0; mk < nc * nc; ++mk) {
+        const int m = mk / nc, k = mk % nc;
+        double sum = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (cond[i] == m) sum += v.X[o + i + (size_t)k * np];
+        red[threadIdx.x] = sum;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) v.C[v.coff[b] + mk] = scale * red[0];
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -560,6 +718,39 @@ cudaError_t launch_capacitance(const int32_t* cond, int n, int np, int n_cond, c
                                double scale, double* C, cudaStream_t s)
 {
     capacitance<<<n_cond * n_cond, 256, 0, s>>>(cond, n, np, n_cond, X, scale, C);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_begin(const BatchView& v, cudaStream_t s)
+{
+    batch_begin<<<dim3(64, v.nb), 256, 0, s>>>(v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iteration(const BatchView& v, size_t vec_total, long long row_blocks, int max_nc,
+                                   cudaStream_t s)
+{
+    const int g = (int)std::min<size_t>(8192, (vec_total + 255) / 256);
+    batch_to_f32<<<g, 256, 0, s>>>(v.R, v.W, vec_total);
+    count_launch();
+    if (max_nc <= 4) trsv_batched<4><<<v.nb, 256, 0, s>>>(v);
+    else if (max_nc <= 8) trsv_batched<8><<<v.nb, 256, 0, s>>>(v);
+    else trsv_batched<16><<<v.nb, 256, 0, s>>>(v);
+    count_launch();
+    batch_add<<<g, 256, 0, s>>>(v.W, v.X, vec_total);
+    count_launch();
+    if (max_nc <= 4) residual_batched<4><<<(unsigned)row_blocks, 256, 0, s>>>(v);
+    else if (max_nc <= 8) residual_batched<8><<<(unsigned)row_blocks, 256, 0, s>>>(v);
+    else residual_batched<16><<<(unsigned)row_blocks, 256, 0, s>>>(v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finish(const BatchView& v, double scale, cudaStream_t s)
+{
+    batch_finish<<<v.nb, 256, 0, s>>>(v, scale);
     count_launch();
     return cudaGetLastError();
 }

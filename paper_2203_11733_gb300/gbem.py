@@ -92,6 +92,10 @@ _SIGS = {
     "gbem_matrix_status": (ctypes.c_int, [_P]),
     "gbem_matrix_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "gbem_matrix_destroy": (None, [_P]),
+    "gbem_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "gbem_batch_run": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
+    "gbem_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong), _P]),
+    "gbem_batch_destroy": (None, [_P]),
 }
 
 
@@ -194,7 +198,7 @@ class Context:
         if getattr(self, "h", None):
             kids = list(self._children)
             for k in kids:
-                if isinstance(k, Matrix):
+                if isinstance(k, (Matrix, Batch)):
                     k.close()
             for k in kids:
                 k.close()
@@ -274,6 +278,47 @@ class Matrix:
         if getattr(self, "h", None):
             if self.ctx.h is not None:
                 self.ctx.lib.gbem_matrix_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched extraction of independent structures (one CUDA graph)."""
+
+    def __init__(self, ctx: Context, meshes, iters: int = 0):
+        self.ctx, self.meshes = ctx, list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
+                                                      for m in self.meshes])
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.gbem_batch_create(ctx.h, len(self.meshes), ctypes.cast(arr, ctypes.c_void_p), int(iters),
+                                            ctypes.byref(h)))
+        self.h = h
+        ctx._children.add(self)
+        cnt, tot = ctypes.c_int(), ctypes.c_longlong()
+        self.c_offset = np.zeros(len(self.meshes), np.int64)
+        ctx.check(ctx.lib.gbem_batch_info(h, ctypes.byref(cnt), ctypes.byref(tot), _ptr(self.c_offset)))
+        self.c_total = tot.value
+
+    def run(self, eps_r: float, stream=None):
+        """List of capacitance matrices (farads) and the residual of each."""
+        C = np.empty(self.c_total, np.float64)
+        res = np.empty(len(self.meshes), np.float64)
+        self.ctx.check(self.ctx.lib.gbem_batch_run(self.h, float(eps_r), _ptr(C), _ptr(res), _stream_handle(stream)))
+        out = []
+        for b, m in enumerate(self.meshes):
+            o = int(self.c_offset[b])
+            out.append(C[o:o + m.n_cond * m.n_cond].reshape(m.n_cond, m.n_cond))
+        return out, res
+
+    def close(self):
+        if getattr(self, "h", None):
+            if self.ctx.h is not None:
+                self.ctx.lib.gbem_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
