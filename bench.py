@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default="crossing_bus_2x2", choices=["crossing_bus_2x2", "batch512", "serving"],
                     help="crossing_bus_2x2: the headline line; batch512 / serving: the batched and served forms")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-count", type=int, default=120)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--profile", default=None, choices=["mixed", "fp64"],
                     help="one warm-up and one extraction in that precision, nothing else "
                          "(for ncu captures)")
@@ -472,6 +475,96 @@ def run_batch(args):
     ctx.close()
 
 
+def run_serving(args):
+    """Poisson stream of 2-15 conductor bus extractions (N log-uniform in
+    [500, 30000]) through the continuous-batching server, at 0.8x the
+    capacity measured on a burst; against one-at-a-time FP64 and mixed loops
+    on the first requests."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem, workloads as W
+    B.build()
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def run_stream(reqs, rate_scale=None):
+        srv = gbem.Server(local, hbm_budget=budget, slots=args.serve_slots)
+        got = {}
+        t0 = time.perf_counter()
+        for k, (t_arr, boxes, params) in enumerate(reqs):
+            if rate_scale is not None:
+                while time.perf_counter() - t0 < t_arr * rate_scale:
+                    for info, C in srv.poll(wait_ms=1):
+                        got[info["id"]] = (info, C)
+            srv.submit(k, boxes, params, W.EPS_R_SIO2)
+        while len(got) < len(reqs):
+            for info, C in srv.poll(wait_ms=20):
+                got[info["id"]] = (info, C)
+        stats = srv.stats()
+        srv.close()
+        return got, stats
+
+    # capacity: a burst of requests submitted at once
+    cal = W.serving_requests(seed=2024 + rank, count=24, rate_per_s=1.0)
+    got, _ = run_stream(cal)
+    t_first = min(i["submit_s"] for i, _ in got.values())
+    t_last = max(i["done_s"] for i, _ in got.values())
+    capacity = len(cal) / (t_last - t_first)
+    rate = 0.8 * capacity
+    reqs = W.serving_requests(seed=777 + rank, count=args.serve_count, rate_per_s=1.0)
+    # the generator's arrival times are for rate 1/s: scale them to `rate`
+    clocks = ClockSampler(local)
+    clocks.start()
+    got, stats = run_stream(reqs, rate_scale=1.0 / rate)
+    clk = clocks.stop()
+    infos = [got[k][0] for k in range(len(reqs))]
+    lat = np.array([i["done_s"] - i["submit_s"] for i in infos]) * 1e3
+    wait = np.array([i["start_s"] - i["submit_s"] for i in infos]) * 1e3
+    span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
+    ok = all(i["status"] == 0 for i in infos)
+    ns = np.array([i["n_panels"] for i in infos])
+    # one at a time on the same GPU: the first requests, FP64 then mixed
+    ctx = gbem.Context(local)
+    def loop(prec, k_max, t_cap):
+        t = []
+        Cs = []
+        for k in range(k_max):
+            _, boxes, params = reqs[k]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C, _ = gbem.extract(ctx, boxes, params, W.EPS_R_SIO2, precision=prec)
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+            Cs.append(C)
+            if sum(t) > t_cap:
+                break
+        return np.array(t), Cs
+    t64, C64 = loop(gbem.GBEM_FP64, 8, 40.0)
+    tmx, Cmx = loop(gbem.GBEM_MIXED, len(t64), 1e9)
+    err = max(float(np.max(np.abs(got[k][1] - C64[k])) / np.max(np.abs(C64[k]))) for k in range(len(C64)))
+    ctx.close()
+    line = {
+        "metric": "extractions/s", "value": world * len(reqs) / span, "unit": "extractions/s", "n_gpus": world,
+        "steps": len(reqs), "warmup": len(cal), "ms_per_step": 1e3 * span / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {len(reqs)} 2-15 conductor buses, N log-uniform [500,30000]",
+                   "rate_per_s": rate, "capacity_per_s": capacity, "slots": args.serve_slots,
+                   "hbm_budget_gb": args.serve_budget_gb, "n_max": int(ns.max()), "n_median": int(np.median(ns))},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "queue_wait_p50_ms": float(np.percentile(wait, 50)),
+        "queue_wait_p99_ms": float(np.percentile(wait, 99)), "all_ok": ok,
+        "peak_reserved_gb": stats["peak_reserved"] / (1 << 30),
+        "one_at_a_time_fp64": {"requests": len(t64), "extractions_per_s": len(t64) / float(t64.sum()),
+                               "p50_ms": float(np.percentile(t64, 50) * 1e3)},
+        "one_at_a_time_mixed": {"requests": len(tmx), "extractions_per_s": len(tmx) / float(tmx.sum())},
+        "cap_rel_err_vs_fp64_gpu": err, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def ctypes_void():
     import ctypes
     return ctypes.c_void_p
@@ -488,6 +581,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch512":
         run_batch(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

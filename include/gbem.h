@@ -250,6 +250,44 @@ gbem_status gbem_batch_info(const gbem_batch_t* batch, int* count, long long* c_
                             long long* c_offset);
 void gbem_batch_destroy(gbem_batch_t* batch);
 
+/* Extraction server (continuous batching).  Requests are meshed on the host
+ * when submitted, so their device footprint is known; they wait in a
+ * first-in first-out queue and are admitted by `slots` worker threads (each
+ * with its own context and stream) whenever a worker is free and the request
+ * fits in hbm_budget bytes next to the requests already running.  Admitted
+ * requests run concurrently and overlap on the device; geometry, matrix,
+ * factor and right-hand sides stay on the device for the request's life.  A
+ * request larger than the whole budget completes with GBEM_ERR_OOM.  The
+ * paper has no serving layer; every extraction follows Sec. 3 as above. */
+typedef struct gbem_server_s gbem_server_t;
+typedef struct {
+    long long id;       /* the caller's request id */
+    int status;         /* gbem_status of the extraction */
+    int n_panels;
+    int n_cond;
+    double residual;    /* final relative residual of the solve */
+    double submit_s;    /* seconds since server creation: submitted, */
+    double start_s;     /* admitted, */
+    double done_s;      /* completed */
+    long long c_offset; /* offset of this result's n_cond x n_cond C in the poll buffer */
+} gbem_result_info;
+gbem_status gbem_server_create(int device, size_t hbm_budget, int slots, gbem_precision prec,
+                               gbem_server_t** out);
+/* Queue one extraction (boxes and mesh parameters as for gbem_mesh).
+ * bytes_needed (may be NULL) receives the device bytes it will hold. */
+gbem_status gbem_server_submit(gbem_server_t* srv, long long id, const gbem_box* boxes, int nbox,
+                               const gbem_mesh_params* params, double eps_r, size_t* bytes_needed);
+/* Move up to max_results completed results into infos (and their capacitance
+ * matrices, back to back, into C of c_capacity doubles).  With wait_ms > 0 and
+ * nothing completed, wait up to wait_ms for a completion. */
+gbem_status gbem_server_poll(gbem_server_t* srv, gbem_result_info* infos, double* C, long long c_capacity,
+                             int max_results, int* count, int wait_ms);
+gbem_status gbem_server_stats(gbem_server_t* srv, int* queued, int* running, size_t* reserved,
+                              size_t* peak_reserved);
+/* Stop the workers (each finishes the request it is running; queued requests
+ * are dropped) and release everything. */
+void gbem_server_destroy(gbem_server_t* srv);
+
 /* Matrix order N and the number of panel pairs by class: pairs evaluated by
  * closed form, and by Gauss-Legendre order 1..6 (counts[0] closed form,
  * counts[n] order n; array of 7).  Waits for the assembly stream. */

@@ -52,6 +52,12 @@ class _Tuning(ctypes.Structure):
                 ("ir_tol", ctypes.c_double), ("ir_max_iter", ctypes.c_int), ("nb", ctypes.c_int)]
 
 
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("n_panels", ctypes.c_int),
+                ("n_cond", ctypes.c_int), ("residual", ctypes.c_double), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("c_offset", ctypes.c_longlong)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -96,6 +102,16 @@ _SIGS = {
     "gbem_batch_run": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "gbem_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong), _P]),
     "gbem_batch_destroy": (None, [_P]),
+    "gbem_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_P)]),
+    "gbem_server_submit": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(_Box), ctypes.c_int,
+                                          ctypes.POINTER(_MeshParams), ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "gbem_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(ResultInfo), _P, ctypes.c_longlong, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "gbem_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "gbem_server_destroy": (None, [_P]),
 }
 
 
@@ -319,6 +335,71 @@ class Batch:
         if getattr(self, "h", None):
             if self.ctx.h is not None:
                 self.ctx.lib.gbem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _boxes(boxes):
+    arr = (_Box * len(boxes))()
+    for i, (lo, hi, c) in enumerate(boxes):
+        arr[i].lo[:] = [float(v) for v in lo]
+        arr[i].hi[:] = [float(v) for v in hi]
+        arr[i].conductor = int(c)
+    return arr
+
+
+class Server:
+    """Extraction server with continuous batching (gbem_server_*)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 64 << 30, slots: int = 4, precision=GBEM_MIXED):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.gbem_server_create(int(device), int(hbm_budget), int(slots), int(precision), ctypes.byref(h))
+        if st != GBEM_OK:
+            raise GbemError(st, "gbem_server_create failed")
+        self.h = h
+
+    def submit(self, rid: int, boxes, params, eps_r: float) -> int:
+        arr = _boxes(boxes)
+        p = _MeshParams(float(params["h"]), float(params.get("ratio", 1.0)), float(params.get("h_min", 0.0)))
+        need = ctypes.c_size_t(0)
+        st = self.lib.gbem_server_submit(self.h, int(rid), arr, len(boxes), ctypes.byref(p), float(eps_r),
+                                         ctypes.byref(need))
+        if st != GBEM_OK:
+            raise GbemError(st, "gbem_server_submit failed")
+        return need.value
+
+    def poll(self, wait_ms: int = 0, max_results: int = 256):
+        """List of (info dict, C) for completed requests."""
+        infos = (ResultInfo * max_results)()
+        C = np.empty(max_results * 256, np.float64)
+        cnt = ctypes.c_int(0)
+        st = self.lib.gbem_server_poll(self.h, infos, _ptr(C), len(C), max_results, ctypes.byref(cnt), int(wait_ms))
+        if st != GBEM_OK:
+            raise GbemError(st, "gbem_server_poll failed")
+        out = []
+        for k in range(cnt.value):
+            i = infos[k]
+            info = {f: getattr(i, f) for f, _ in ResultInfo._fields_}
+            n = i.n_cond
+            Ck = C[i.c_offset:i.c_offset + n * n].reshape(n, n).copy() if n else None
+            out.append((info, Ck))
+        return out
+
+    def stats(self):
+        q, r = ctypes.c_int(), ctypes.c_int()
+        res, peak = ctypes.c_size_t(), ctypes.c_size_t()
+        self.lib.gbem_server_stats(self.h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(res), ctypes.byref(peak))
+        return {"queued": q.value, "running": r.value, "reserved": res.value, "peak_reserved": peak.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbem_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
