@@ -61,6 +61,28 @@ template <> __device__ __forceinline__ double glw<double>(int n, int i) { return
 template <> __device__ __forceinline__ float glx<float>(int n, int i) { return c_glxf[n][i]; }
 template <> __device__ __forceinline__ float glw<float>(int n, int i) { return c_glwf[n][i]; }
 
+// Outer sum of the quadrature: plain FP64 in FP64 mode; in mixed mode a
+// compensated (Kahan) FP32 sum, which keeps FP64 instructions -- about 70x
+// dearer than FP32 ones here -- out of the far field.
+template <typename T>
+struct OuterSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct OuterSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+
 // Tensor Gauss-Legendre sum of 1/r over N x N nodes on each panel, without
 // the half-extent Jacobians (a_ij = sum / (64 pi)).
 //
@@ -79,7 +101,7 @@ __device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
             Q[b * N + d] = t * t + w * w;
             WQ[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
-    double s = 0.0;
+    OuterSum<T> s;
 #pragma unroll 1
     for (int ac = 0; ac < N * N; ++ac) {
         const int a = ac / N, c = ac % N;
@@ -88,9 +110,9 @@ __device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
         T si = T(0);
 #pragma unroll
         for (int k = 0; k < N * N; ++k) si += WQ[k] * rsq(p + Q[k]);
-        s += (double)(glw<T>(N, a) * glw<T>(N, c) * si);
+        s.add(glw<T>(N, a) * glw<T>(N, c) * si);
     }
-    return s;
+    return s.value();
 }
 
 // Perpendicular panels: shared-axis offset ds with half extents si, sj; the
@@ -110,7 +132,7 @@ __device__ __noinline__ double far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj
             VW[b * N + d] = tv * tv + tw * tw;
             WVW[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
-    double s = 0.0;
+    OuterSum<T> s;
 #pragma unroll 1
     for (int ac = 0; ac < N * N; ++ac) {
         const int a = ac / N, c = ac % N;
@@ -119,9 +141,9 @@ __device__ __noinline__ double far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < N * N; ++k) acc += WVW[k] * rsq(p + VW[k]);
-        s += (double)(glw<T>(N, a) * glw<T>(N, c) * acc);
+        s.add(glw<T>(N, a) * glw<T>(N, c) * acc);
     }
-    return s;
+    return s.value();
 }
 
 // ------------------------------------------------------------------ near field

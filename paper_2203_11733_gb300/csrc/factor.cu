@@ -21,121 +21,107 @@ namespace {
 
 constexpr int NB = 64;
 
-// Cholesky of one 64x64 diagonal block and the inverse of its factor.  Each
-// of the 256 threads keeps a fixed 4x4 sub-block of the matrix in registers;
-// step j publishes the current column j through shared memory (double
-// buffered), and every thread applies the rank-1 update -a_rj a_cj / a_jj to
-// its entries right of column j: one barrier per column.  Column j is scaled
-// by 1/sqrt(a_jj) at the end.  The inverse L^-1 is then formed the same way,
-// by forward elimination of the identity.
+// Cholesky of one 64x64 diagonal block fused with the inverse of its factor.
+// Each of the 256 threads keeps a fixed 4x4 sub-block of the matrix A and of
+// X = L^-1 (started as the identity) in registers.  Step j publishes, through
+// double-buffered shared memory, the current column j of A (unscaled) and
+// row j of X; then every thread
+//   - subtracts a_rj a_cj / a_jj from its entries of A right of column j,
+//   - finalises X_j = X_j / l_jj and subtracts l_ij X_j from its rows i > j
+//     of X (l_ij = a_ij / sqrt(a_jj): forward elimination of the identity).
+// One barrier per column.  Column j of L is a_.j / sqrt(a_jj) at the end.
+// A non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
+// factorisation completes without NaNs.
+template <typename T>
+struct PotrfSmem {
+    T col[2][NB];
+    T rowx[2][NB];
+    T piv[NB];
+};
+
+__device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
+__device__ __forceinline__ double rsqrt_t(double d) { return 1.0 / sqrt(d); }
+
 template <typename T>
 __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
                                            int* __restrict__ info)
 {
     extern __shared__ unsigned char smem_raw[];
-    T(*a)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);   // the factor, for the inverse
-    __shared__ T col[2][NB];
-    __shared__ T piv[NB];
+    PotrfSmem<T>& S = *reinterpret_cast<PotrfSmem<T>*>(smem_raw);
     const int tid = threadIdx.x;
     const int r0 = (tid & 15) * 4, c0 = (tid >> 4) * 4;   // this thread's 4x4 sub-block
-    T x[4][4];
+    T x[4][4], y[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int r = r0 + u, c = c0 + v;
             x[u][v] = (r >= c) ? L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] : T(0);
+            y[u][v] = (r == c) ? T(1) : T(0);
         }
     for (int j = 0; j < NB; ++j) {
         const int b = j & 1;
-        // owners of column j publish it (rows >= j)
         if (c0 <= j && j < c0 + 4) {
 #pragma unroll
             for (int v = 0; v < 4; ++v)
                 if (c0 + v == j)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) col[b][r0 + u] = x[u][v];
+                    for (int u = 0; u < 4; ++u) S.col[b][r0 + u] = x[u][v];
+        }
+        if (r0 <= j && j < r0 + 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (r0 + u == j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) S.rowx[b][c0 + v] = y[u][v];
         }
         __syncthreads();
-        T d = col[b][j];
-        if (tid == 0) piv[j] = d;
+        T d = S.col[b][j];
+        if (tid == 0) S.piv[j] = d;
         if (!(d > T(0))) d = T(1);
-        const T rd = T(1) / d;
-        if (c0 + 3 > j) {
-            T cr[4], cc[4];
+        const T rs = rsqrt_t(d);          // 1 / l_jj
+        const T rd = rs * rs;             // 1 / a_jj
+        if (r0 + 3 < j) continue;   // rows above j: nothing left to update
+        T cr[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                cr[u] = col[b][r0 + u];
-                cc[u] = col[b][c0 + u] * rd;
-            }
+        for (int u = 0; u < 4; ++u) cr[u] = S.col[b][r0 + u];
+        if (c0 + 3 > j) {            // entries of A right of column j
+            T cc[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cc[v] = S.col[b][c0 + v] * rd;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
                     if (c0 + v > j && r0 + u >= c0 + v) x[u][v] -= cr[u] * cc[v];
         }
-    }
-    __syncthreads();
-    if (tid < NB) {
-        T d = piv[tid];
-        if (!(d > T(0))) {
-            info[0] = 1;
-            d = T(1);
+        T xj[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) xj[v] = S.rowx[b][c0 + v] * rs;   // final row j of X
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const T l = cr[u] * rs;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (r0 + u > j) y[u][v] -= l * xj[v];
+                else if (r0 + u == j) y[u][v] = xj[v];
+            }
         }
-        piv[tid] = sqrt(d);
     }
     __syncthreads();
+    if (tid < NB && !(S.piv[tid] > T(0))) info[0] = 1;
+    T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int r = r0 + u, c = c0 + v;
-            T val = (r > c) ? x[u][v] / piv[c] : (r == c ? piv[c] : T(0));
-            a[r][c] = val;
-            if (r >= c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = val;
+            T p = S.piv[c];
+            if (!(p > T(0))) p = T(1);
+            if (r > c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = x[u][v] * rsqrt_t(p);
+            else if (r == c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = p * rsqrt_t(p);
+            Lb[r + (size_t)c * NB] = y[u][v];
         }
-    __syncthreads();
-    // X = L^-1 by forward elimination of the identity: after row j of X is
-    // final (divided by l_jj), rows i > j subtract l_ij X_j.
-    T y[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) y[u][v] = (r0 + u == c0 + v) ? T(1) : T(0);
-    __shared__ T rowj[2][NB];
-    for (int j = 0; j < NB; ++j) {
-        const int b = j & 1;
-        const T rl = T(1) / a[j][j];
-        // owners of row j finalise it and publish it
-        if (r0 <= j && j < r0 + 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (r0 + u == j)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        y[u][v] *= rl;
-                        rowj[b][c0 + v] = y[u][v];
-                    }
-        }
-        __syncthreads();
-        if (r0 + 3 > j) {
-            T lr[4], xr[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) lr[u] = a[r0 + u][j];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) xr[v] = rowj[b][c0 + v];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (r0 + u > j) y[u][v] -= lr[u] * xr[v];
-        }
-    }
-    T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) Lb[(r0 + u) + (size_t)(c0 + v) * NB] = y[u][v];
 }
 
 template <typename T>
@@ -236,16 +222,17 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-// The 64-wide leading column strip of the trailing matrix (used when the
-// trailing order is an odd number of 64-blocks): tiles (t0 + 64 b, t0).
+// The leading column strip of the trailing matrix, gridDim.y 64-wide column
+// blocks wide: tiles (t0 + 64 I, t0 + 64 J) with I >= J, t0 = k0 + 64.
 template <typename T>
 __global__ void __launch_bounds__(256) syrk_strip(T* __restrict__ L, int ld, int k0)
 {
+    if (blockIdx.x < blockIdx.y) return;
     extern __shared__ unsigned char smem_raw[];
     T* sa = reinterpret_cast<T*>(smem_raw);
     T* sb = sa + NB * (NB + 1);
     const int t0 = k0 + NB;
-    const int rI = t0 + NB * blockIdx.x, rJ = t0;
+    const int rI = t0 + NB * blockIdx.x, rJ = t0 + NB * blockIdx.y;
     const int tid = threadIdx.x;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         int r = e % NB, c = e / NB;
@@ -290,6 +277,29 @@ __global__ void __launch_bounds__(256) syrk_tc(float* __restrict__ L, int ld, in
         atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
 }
 
+// One launch of the FP32 factorisation step: CTA 0 factors the next
+// diagonal block (k0n, already brought up to date by the strip kernel) while
+// the other CTAs apply the current panel to the tensor-core region [r0, np)^2,
+// which does not touch that block.  The diagonal factorisation is thereby
+// hidden behind the trailing update.
+__global__ void __launch_bounds__(256) step_fused(float* __restrict__ L, int ld, int k0n, float* __restrict__ Linv,
+                                                  int* __restrict__ info, int r0, const unsigned char* __restrict__ hi,
+                                                  const unsigned char* __restrict__ lo)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    if (blockIdx.x == 0) {
+        potrf_body<float>(L, ld, k0n, Linv, info);
+        return;
+    }
+    long long b = blockIdx.x - 1;
+    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
+    while ((long long)I * (I + 1) / 2 > b) --I;
+    const int J = (int)(b - (long long)I * (I + 1) / 2);
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem) && threadIdx.x == 0)
+        atomicCAS(info + 3, 0, (int)GBEM_ERR_TIMEOUT);
+}
+
 template <typename T>
 cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s)
 {
@@ -298,7 +308,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
     constexpr bool kTensor = sizeof(T) == 4;   // FP32 storage: trailing update on tcgen05
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(NB * (NB + 1) * sizeof(T)))) != cudaSuccess)
+                                  (int)sizeof(PotrfSmem<T>))) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
@@ -313,38 +323,53 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         (e = cudaFuncSetAttribute(syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
             cudaSuccess)
         return e;
+    if (kTensor) {
+        if ((e = cudaFuncSetAttribute(step_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
+            cudaSuccess)
+            return e;
+        // block 0 is factored alone; every later diagonal block is factored
+        // inside the fused launch of the previous step
+        potrf_diag<T><<<1, 256, sizeof(PotrfSmem<T>), s>>>(L, np, 0, Linv, info);
+        count_launch();
+        for (int k = 0; k + 1 < nblk; ++k) {
+            const int k0 = k * NB;
+            const int m = nblk - k - 1;   // trailing order in 64-blocks
+            trsm_panel<T><<<m, 256, smem, s>>>(L, np, k0, Linv);
+            count_launch();
+            // strip: one or two column blocks, leaving an even number of
+            // blocks (whole 128-tiles) for the tensor cores
+            const int sw = ((m - 1) & 1) ? 2 : 1;
+            syrk_strip<T><<<dim3(m, sw), 256, smem, s>>>(L, np, k0);
+            count_launch();
+            const int r0 = k0 + NB + NB * sw;
+            const long long nt = (np - r0) / tc::TM;
+            // one split buffer suffices: the next step's split follows this
+            // step's fused launch in stream order
+            unsigned char* hi = split;
+            unsigned char* lo = split + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
+            if (nt > 0) {
+                const long long elems = (long long)(np - r0) * tc::TK;
+                const int sgrid = (int)std::min<long long>(4096, (elems + 255) / 256);
+                tc::split_panel<<<sgrid, 256, 0, s>>>(reinterpret_cast<const float*>(L), np, k0, r0, np, hi, lo);
+                count_launch();
+            }
+            step_fused<<<(unsigned)(1 + nt * (nt + 1) / 2), 256, tc::SMEM_BYTES, s>>>(
+                reinterpret_cast<float*>(L), np, k0 + NB, reinterpret_cast<float*>(Linv), info, r0, hi, lo);
+            count_launch();
+        }
+        return cudaGetLastError();
+    }
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * NB;
-        potrf_diag<T><<<1, 256, NB * (NB + 1) * sizeof(T), s>>>(L, np, k0, Linv, info);
+        potrf_diag<T><<<1, 256, sizeof(PotrfSmem<T>), s>>>(L, np, k0, Linv, info);
         count_launch();
         const int m = nblk - k - 1;   // trailing order in 64-blocks
         if (m <= 0) continue;
         trsm_panel<T><<<m, 256, smem, s>>>(L, np, k0, Linv);
         count_launch();
-        if (kTensor) {
-            int r0 = k0 + NB;
-            if (m & 1) {
-                syrk_strip<T><<<m, 256, smem, s>>>(L, np, k0);
-                count_launch();
-                r0 += NB;
-            }
-            const long long nt = (np - r0) / tc::TM;
-            if (nt > 0) {
-                unsigned char* hi = split;
-                unsigned char* lo = split + (size_t)nt * tc::OPER_BYTES;
-                const long long elems = (long long)(np - r0) * tc::TK;
-                const int sgrid = (int)std::min<long long>(4096, (elems + 255) / 256);
-                tc::split_panel<<<sgrid, 256, 0, s>>>(reinterpret_cast<const float*>(L), np, k0, r0, np, hi, lo);
-                count_launch();
-                syrk_tc<<<(unsigned)(nt * (nt + 1) / 2), 256, tc::SMEM_BYTES, s>>>(reinterpret_cast<float*>(L), np,
-                                                                                     r0, hi, lo, info + 3);
-                count_launch();
-            }
-        } else {
-            long long tiles = (long long)m * (m + 1) / 2;
-            syrk_update<T><<<(unsigned)tiles, 256, smem, s>>>(L, np, k0);
-            count_launch();
-        }
+        long long tiles = (long long)m * (m + 1) / 2;
+        syrk_update<T><<<(unsigned)tiles, 256, smem, s>>>(L, np, k0);
+        count_launch();
     }
     return cudaGetLastError();
 }
@@ -402,7 +427,7 @@ cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long l
     const size_t smem = 2 * NB * (NB + 1) * sizeof(float);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(potrf_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(NB * (NB + 1) * sizeof(float)))) != cudaSuccess ||
+                                  (int)sizeof(PotrfSmem<float>))) != cudaSuccess ||
         (e = cudaFuncSetAttribute(trsm_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(syrk_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -410,7 +435,7 @@ cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long l
         return e;
     const int nb1 = v.nb + 1;
     for (int k = 0; k < nsteps; ++k) {
-        potrf_batched<<<v.nb, 256, NB * (NB + 1) * sizeof(float), s>>>(v, k);
+        potrf_batched<<<v.nb, 256, sizeof(PotrfSmem<float>), s>>>(v, k);
         count_launch();
         const long long ntrsm = steps_host[(size_t)k * nb1 + v.nb];
         const long long nsyrk = steps_host[(size_t)(nsteps + k) * nb1 + v.nb];

@@ -20,7 +20,7 @@ namespace {
 
 constexpr int NB = 64;
 constexpr int MAXR = 16;          // right-hand sides per pass
-constexpr long long kSpinLimit = 1LL << 22;   // ~0.5 s of polling at 100 ns
+constexpr long long kSpinLimit = 1LL << 24;   // ~1 s of polling at 32 ns
 
 std::atomic<unsigned> g_epoch{1};
 
@@ -49,7 +49,7 @@ __device__ bool wait_flag(const unsigned* flag, unsigned epoch, int* status, int
                 ok = 0;
                 break;
             }
-            __nanosleep(100);
+            __nanosleep(32);
         }
         *s_ok = ok;
     }
@@ -67,6 +67,10 @@ struct SweepSmem {
 };
 
 // Forward sweep on right-hand-side columns [0, nr) of W (np x nrhs, col-major).
+// Per block row, everything that does not depend on other blocks -- the
+// diagonal-block inverse, the right-hand side and the next L tile -- is
+// loaded before the CTA waits, so only the solved block crosses the critical
+// path.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) trsv_fwd(const T* __restrict__ L, const T* __restrict__ Linv, int np,
                                                 const T* __restrict__ W, T* __restrict__ Y, int nr,
@@ -78,12 +82,28 @@ __global__ void __launch_bounds__(256) trsv_fwd(const T* __restrict__ L, const T
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;   // row of the block, column quarter
     const int nblk = np / NB;
+    constexpr int QW = NB / 4;
     for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int b0 = b * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+        T rhs[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) rhs[c] = (q == 0 && c < nr) ? W[(size_t)(b0 + r) + (size_t)c * np] : T(0);
         T acc[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) acc[c] = T(0);
+        T lnext[QW];
+        if (b > 0)
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lnext[tt] = L[(size_t)(b0 + r) + (size_t)(q * QW + tt) * np];
         for (int j = 0; j < b; ++j) {
+            T lcur[QW];
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
+            if (j + 1 < b)
+#pragma unroll
+                for (int tt = 0; tt < QW; ++tt)
+                    lnext[tt] = L[(size_t)(b0 + r) + (size_t)((j + 1) * NB + q * QW + tt) * np];
             if (!wait_flag(sync + j, epoch, status, &S.ok)) return;
             const int j0 = j * NB;
             for (int e = tid; e < NB * R; e += blockDim.x) {
@@ -92,24 +112,23 @@ __global__ void __launch_bounds__(256) trsv_fwd(const T* __restrict__ L, const T
             }
             __syncthreads();
 #pragma unroll
-            for (int tt = 0; tt < NB / 4; ++tt) {
-                const int t = q * (NB / 4) + tt;
-                const T l = L[(size_t)(b0 + r) + (size_t)(j0 + t) * np];
+            for (int tt = 0; tt < QW; ++tt) {
+                const int t = q * QW + tt;
 #pragma unroll
-                for (int c = 0; c < R; ++c) acc[c] += l * S.v[t][c];
+                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[t][c];
             }
             __syncthreads();
         }
         // w = W_b - sum of the four partial sums; Y_b = Linv_bb w
-        for (int e = tid; e < NB * NB; e += blockDim.x)
-            S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
 #pragma unroll
         for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        if (q == 0)
+#pragma unroll
+            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
         __syncthreads();
         for (int e = tid; e < NB * R; e += blockDim.x) {
             const int t = e % NB, c = e / NB;
-            T rhs = (c < nr) ? W[(size_t)(b0 + t) + (size_t)c * np] : T(0);
-            S.w[t][c] = rhs - (((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c]);
+            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
         }
         __syncthreads();
         for (int e = tid; e < NB * R; e += blockDim.x) {
@@ -139,12 +158,29 @@ __global__ void __launch_bounds__(256) trsv_bwd(const T* __restrict__ L, const T
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;
     const int nblk = np / NB;
+    constexpr int QW = NB / 4;
     for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
         const int b0 = b * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+        T rhs[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) rhs[c] = (q == 0 && c < nr) ? Y[(size_t)(b0 + r) + (size_t)c * np] : T(0);
         T acc[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) acc[c] = T(0);
+        // row r of L_jb^T is column (b0 + r) of L, rows j0 + q * 16 ..
+        const T* col = L + (size_t)(b0 + r) * np + q * QW;
+        T lnext[QW];
+        if (b < nblk - 1)
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(nblk - 1) * NB + tt];
         for (int j = nblk - 1; j > b; --j) {
+            T lcur[QW];
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
+            if (j - 1 > b)
+#pragma unroll
+                for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(j - 1) * NB + tt];
             if (!wait_flag(sync + j, epoch, status, &S.ok)) return;
             const int j0 = j * NB;
             for (int e = tid; e < NB * R; e += blockDim.x) {
@@ -152,25 +188,22 @@ __global__ void __launch_bounds__(256) trsv_bwd(const T* __restrict__ L, const T
                 S.v[t][c] = (c < nr) ? __ldcg(X + (size_t)(j0 + t) + (size_t)c * np) : T(0);
             }
             __syncthreads();
-            // row r of L_jb^T is column (b0 + r) of L, rows j0..j0+63
-            const T* col = L + (size_t)(b0 + r) * np + j0 + q * (NB / 4);
 #pragma unroll
-            for (int tt = 0; tt < NB / 4; ++tt) {
-                const T l = col[tt];
+            for (int tt = 0; tt < QW; ++tt) {
 #pragma unroll
-                for (int c = 0; c < R; ++c) acc[c] += l * S.v[q * (NB / 4) + tt][c];
+                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[q * QW + tt][c];
             }
             __syncthreads();
         }
-        for (int e = tid; e < NB * NB; e += blockDim.x)
-            S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
 #pragma unroll
         for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        if (q == 0)
+#pragma unroll
+            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
         __syncthreads();
         for (int e = tid; e < NB * R; e += blockDim.x) {
             const int t = e % NB, c = e / NB;
-            T rhs = (c < nr) ? Y[(size_t)(b0 + t) + (size_t)c * np] : T(0);
-            S.w[t][c] = rhs - (((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c]);
+            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
         }
         __syncthreads();
         for (int e = tid; e < NB * R; e += blockDim.x) {
