@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--profile", default=None, choices=["mixed", "fp64"],
                     help="one warm-up and one extraction in that precision, nothing else "
                          "(for ncu captures)")
+    ap.add_argument("--profile-workload", default="crossing_bus_2x2",
+                    choices=["crossing_bus_2x2", "two_bars", "bus_3layer_5x5x5"],
+                    help="structure of the --profile run (two_bars: a small case for pass counts)")
     return ap.parse_args()
 
 
@@ -203,7 +206,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     lib = gbem.load()
-    boxes, params = getattr(W, WORKLOAD)()
+    boxes, params = getattr(W, args.profile_workload if args.profile else WORKLOAD)()
     eps_r = W.EPS_R_SIO2
     ctx = gbem.Context(local)
     stream = torch.cuda.Stream()
@@ -260,26 +263,34 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(gbem.GBEM_MIXED)
     barrier()
-    ctx.lib.gbem_set_timing(ctx.h, 1)
-    stats = gbem_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 1)
+    stats = gbem.get_stats(ctx, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     ms_total, C_mixed = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
     clk = clocks.stop()
     barrier()
-    stats = gbem_stats(ctx, reset=True)
-    ctx.lib.gbem_set_timing(ctx.h, 0)
+    stats = gbem.get_stats(ctx, reset=True)
     ms_step = ms_total / args.steps
     value = world * pairs * args.steps / (ms_total * 1e-3)
+
+    # ---- the same steps again with an event pair around every launch of the
+    # traced kernels (kept out of the headline timing: the events cost time)
+    gbem.set_timing(ctx, 2)
+    gbem.get_kernel_stats(ctx, reset=True)
+    ms_traced, _ = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
+    kst = gbem.get_kernel_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 0)
+    gbem.get_stats(ctx, reset=True)
 
     # ---- FP64 path on the same GPU
     step(gbem.GBEM_FP64)
     barrier()
-    ctx.lib.gbem_set_timing(ctx.h, 1)
-    gbem_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 1)
+    gbem.get_stats(ctx, reset=True)
     ms64, C_fp64 = timed(lambda: step(gbem.GBEM_FP64), args.fp64_steps)
-    stats64 = gbem_stats(ctx, reset=True)
-    ctx.lib.gbem_set_timing(ctx.h, 0)
+    stats64 = gbem.get_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 0)
     ms64_step = ms64 / args.fp64_steps
 
     # ---- end to end: host boxes -> mesh + upload -> ... -> C on the host
@@ -301,7 +312,7 @@ def run_ours(args):
         err_mixed = float(np.max(np.abs(C_mixed - C_ref)) / scale)
         err_fp64 = float(np.max(np.abs(C_fp64 - C_ref)) / scale)
 
-    roof = roofline(stats, args.steps, n, nc, ctx, mesh, lib)
+    roof, kern = roofline(kst, args.steps, ms_traced / args.steps)
     line = None
     if rank == 0:
         cpu = None
@@ -328,6 +339,7 @@ def run_ours(args):
                     "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": int(stats["launches"]),
             "roofline": roof,
+            "kernels": kern,
             "clocks": clk,
         }
         if cpu is not None:
@@ -342,53 +354,70 @@ def run_ours(args):
 PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
 
 
-def gbem_stats(ctx, reset=False):
-    import ctypes
+KERNEL_NAMES = {
+    "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
+    "panel": "panel_step: panel products, strip update and hi/lo split (cooperative)",
+    "update": "step_fused: diagonal factor+inverse in CTA 0, tcgen05 3xTF32 trailing update in the rest",
+    "sweep": "trsv_fwd/trsv_bwd: persistent cooperative triangular sweeps",
+    "residual": "residual: FP64 R = B - A X over the lower triangle",
+}
+FP64_PEAK_TF = 1.25   # nominal GB300 FP64 (non-tensor) rate
 
-    class Stats(ctypes.Structure):
-        _fields_ = [("ms", ctypes.c_double * 5), ("calls", ctypes.c_longlong * 5), ("launches", ctypes.c_longlong)]
-    s = Stats()
-    ctx.lib.gbem_get_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
-    ctx.check(ctx.lib.gbem_get_stats(ctx.h, ctypes.byref(s), 1 if reset else 0))
-    return {"ms": list(s.ms), "calls": list(s.calls), "launches": s.launches}
+
+def traffic_per_launch(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (dram__bytes_read.sum + dram__bytes_write.sum over one factorisation's
+    launches, divided by their number), or None."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{WORKLOAD}_mixed.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(parts) >= 3 and parts[0] == kernel:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
 
 
-def roofline(stats, steps, n, nc, ctx, mesh, lib):
-    """Roofline of the dominant phase.  The factorisation is one dense
-    contraction chain: N^3/3 algorithmic flops per extraction in FP32 (SIMT,
-    'alu'); assembly counts far-field kernel evaluations."""
+def roofline(kst, steps, ms_traced_step):
+    """Roofline of the kernel with the largest device time in the traced
+    pass.  achieved = its algorithmic bytes (or flops) per launch, as the
+    library reports them for every launch, over its average CUDA-event
+    launch duration on the launching stream."""
     peaks = {}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         peaks = json.load(open(p))
-    ms = dict(zip(PHASES, stats["ms"]))
-    dom = max(ms, key=lambda k: ms[k])
-    np_ = (n + 127) // 128 * 128
-    sm_count, max_mhz = 152, float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tf = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
-    out = {"phase": dom}
-    if dom == "factor":
-        flops = np_ ** 3 / 3.0
-        t = ms["factor"] / steps * 1e-3
-        out.update({"kernel": "cholesky (potrf_diag + trsm_panel + syrk_update, FP32)", "bound": "alu",
-                    "achieved": flops / t / 1e12, "peak": fp32_peak_tf, "unit": "TFLOP/s",
-                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (nominal unit count)",
-                    "traffic": None})
-    elif dom == "assemble":
-        t = ms["assemble"] / steps * 1e-3
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        bytes_ = n * n / 2 * (8 + 4)
-        out.update({"kernel": "assemble_tiles (mixed)", "bound": "hbm", "achieved": bytes_ / t / 1e9,
-                    "peak": hbm, "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                    "traffic": None})
+    kern = {}
+    for k, d in kst.items():
+        if d["launches"] == 0:
+            continue
+        t = d["ms"] / d["launches"] * 1e-3
+        kern[k] = {"ms_per_step": d["ms"] / steps, "launches_per_step": d["launches"] / steps,
+                   "us_per_launch": t * 1e6,
+                   "gb_per_s": d["bytes"] / d["launches"] / t / 1e9,
+                   "tflop_per_s": d["flops"] / d["launches"] / t / 1e12}
+    kern["traced_ms_per_step"] = ms_traced_step
+    names = [k for k in kst if kst[k]["launches"] > 0]
+    dom = max(names, key=lambda k: kst[k]["ms"])
+    d = kst[dom]
+    t = d["ms"] / d["launches"] * 1e-3
+    out = {"kernel": KERNEL_NAMES[dom], "share_of_traced_step": d["ms"] / steps / ms_traced_step,
+           "launches_per_step": d["launches"] / steps, "us_per_launch": t * 1e6}
+    if dom == "residual":
+        out.update({"bound": "alu", "achieved": d["flops"] / d["launches"] / t / 1e12, "peak": FP64_PEAK_TF,
+                    "unit": "TFLOP/s", "peak_source": "nominal FP64 rate (no measured FP64 peak)",
+                    "work_per_launch": d["flops"] / d["launches"], "traffic": None})
     else:
-        t = ms[dom] / steps * 1e-3
-        bytes_ = np_ * np_ * 8
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        out.update({"kernel": dom, "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s",
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs", "traffic": None})
+        src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+        out.update({"bound": "hbm", "achieved": d["bytes"] / d["launches"] / t / 1e9, "peak": hbm,
+                    "unit": "GB/s", "peak_source": src, "work_per_launch": d["bytes"] / d["launches"],
+                    "traffic": traffic_per_launch(dom)})
     out["frac"] = out["achieved"] / out["peak"]
-    return out
+    return out, kern
 
 
 def run_batch(args):
@@ -412,8 +441,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         Cs, res = batch.run(W.EPS_R_SIO2, stream)
-    ctx.lib.gbem_get_stats.argtypes = [ctypes_void(), ctypes_void(), ctypes_int()]
-    gbem_stats(ctx, reset=True)
+    gbem.get_stats(ctx, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     total = 0.0
@@ -426,7 +454,7 @@ def run_batch(args):
         e1.synchronize()
         total += e0.elapsed_time(e1)
     clk = clocks.stop()
-    st = gbem_stats(ctx, reset=True)
+    st = gbem.get_stats(ctx, reset=True)
     ms_batch = total / args.steps
     # one at a time, same structures, same GPU
     def one_at_a_time(prec, idx):
@@ -563,16 +591,6 @@ def run_serving(args):
     }
     if rank == 0:
         print(json.dumps(line))
-
-
-def ctypes_void():
-    import ctypes
-    return ctypes.c_void_p
-
-
-def ctypes_int():
-    import ctypes
-    return ctypes.c_int
 
 
 def main():

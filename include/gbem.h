@@ -204,8 +204,8 @@ gbem_status gbem_matrix_download(gbem_matrix_t* mat, double* host);
  * (GBEM_ERR_NOT_SPD from the factorisation), else GBEM_OK. */
 gbem_status gbem_matrix_status(gbem_matrix_t* mat);
 
-/* Tracing.  With timing enabled, every call records CUDA events on its
- * stream around each phase; gbem_get_stats waits for those events and adds
+/* Tracing.  With timing enabled (level 1 or 2), every call records CUDA
+ * events on its stream around each phase; gbem_get_stats waits for those events and adds
  * their elapsed times.  launches counts every kernel launched by the library
  * in this process (all contexts).  reset != 0 clears the counters after
  * reading. */
@@ -224,6 +224,31 @@ typedef struct {
 } gbem_stats;
 gbem_status gbem_set_timing(gbem_ctx* ctx, int enable);
 gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset);
+
+/* Kernel-level tracing.  With gbem_set_timing(ctx, 2) the library also
+ * records a CUDA event pair, on the launch stream, around every launch of
+ * the kernels below, and adds the algorithmic work that launch was given:
+ * bytes that must cross HBM at least once and useful flops (the
+ * contraction's 2mnk, not the 3x of the split-precision tensor products).
+ * gbem_get_kernel_stats waits for the events and returns per kernel the
+ * summed device time, the number of launches, bytes and flops.  reset != 0
+ * clears the sums after reading.  The events cost a few microseconds per
+ * launch, so time the workload itself with level 1 or 0. */
+enum {
+    GBEM_KERNEL_ASSEMBLE = 0,  /* one CTA per 32 x 32 tile: Galerkin entries */
+    GBEM_KERNEL_PANEL = 1,     /* FP32 factor: panel products, strip update, hi/lo split */
+    GBEM_KERNEL_UPDATE = 2,    /* FP32 factor: diagonal block + tensor-core trailing update */
+    GBEM_KERNEL_SWEEP = 3,     /* persistent forward/backward triangular sweeps */
+    GBEM_KERNEL_RESIDUAL = 4,  /* FP64 residual R = B - A X */
+    GBEM_NKERNEL = 5
+};
+typedef struct {
+    double ms[GBEM_NKERNEL];
+    long long launches[GBEM_NKERNEL];
+    double bytes[GBEM_NKERNEL];
+    double flops[GBEM_NKERNEL];
+} gbem_kernel_stats;
+gbem_status gbem_get_kernel_stats(gbem_ctx* ctx, gbem_kernel_stats* out, int reset);
 
 /* Batched extraction: many independent structures (meshes of one context)
  * assembled, factored and solved together in mixed precision.  The whole

@@ -43,6 +43,40 @@ struct PhaseTimer {
     }
 };
 
+}  // namespace
+
+thread_local KernelTrace* g_trace = nullptr;
+
+cudaEvent_t trace_begin(cudaStream_t s)
+{
+    if (!g_trace) return nullptr;
+    cudaEvent_t a = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a;
+}
+
+void trace_end(int kind, cudaEvent_t a, cudaStream_t s, double bytes, double flops)
+{
+    if (!g_trace || !a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess) {
+        g_trace->recs.push_back({kind, a, b, bytes, flops});
+        return;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+}
+
+TraceScope::TraceScope(gbem_ctx* ctx) : prev(g_trace) { g_trace = (ctx && ctx->ktiming) ? &ctx->ktrace : nullptr; }
+TraceScope::~TraceScope() { g_trace = prev; }
+
+namespace {
+
 gbem_tuning default_tuning()
 {
     gbem_tuning t{};
@@ -329,9 +363,41 @@ size_t gbem_bytes_in_use(const gbem_ctx* ctx) { return ctx ? ctx->in_use : 0; }
 
 gbem_status gbem_set_timing(gbem_ctx* ctx, int enable)
 {
-    if (!ctx) return GBEM_ERR_ARG;
+    if (!ctx || enable < 0 || enable > 2) return GBEM_ERR_ARG;
     ctx->timing = enable != 0;
+    ctx->ktiming = enable == 2;
     return GBEM_OK;
+}
+
+gbem_status gbem_get_kernel_stats(gbem_ctx* ctx, gbem_kernel_stats* out, int reset)
+{
+    if (!ctx || !out) return GBEM_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    gbem_status st = GBEM_OK;
+    KernelTrace& T = ctx->ktrace;
+    for (auto& r : T.recs) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            T.ms[r.kind] += ms;
+            T.launches[r.kind] += 1;
+            T.bytes[r.kind] += r.bytes;
+            T.flops[r.kind] += r.flops;
+        } else {
+            cudaGetLastError();
+            st = ctx_fail(ctx, GBEM_ERR_CUDA, "event timing failed");
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    T.recs.clear();
+    for (int k = 0; k < GBEM_NKERNEL; ++k) {
+        out->ms[k] = T.ms[k];
+        out->launches[k] = T.launches[k];
+        out->bytes[k] = T.bytes[k];
+        out->flops[k] = T.flops[k];
+        if (reset) T.ms[k] = T.bytes[k] = T.flops[k] = 0.0, T.launches[k] = 0;
+    }
+    return st;
 }
 
 gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset)
@@ -462,6 +528,7 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
     if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
     if (prec != GBEM_FP64 && prec != GBEM_MIXED) return ctx_fail(ctx, GBEM_ERR_ARG, "bad precision");
     DeviceGuard g(ctx->device);
+    TraceScope ts(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     gbem_matrix_t* m = new (std::nothrow) gbem_matrix_t();
     if (!m) return GBEM_ERR_OOM;
@@ -504,6 +571,7 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
     if (!m) return GBEM_ERR_ARG;
     gbem_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
+    TraceScope ts(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t np = (size_t)m->np;
     const size_t nblk = np / m->nb;
@@ -544,6 +612,7 @@ gbem_status gbem_solve(gbem_matrix_t* m, const double* B_dev, int nrhs, int ldb,
     if (ldb < m->n || ldx < m->n) return ctx_fail(ctx, GBEM_ERR_ARG, "leading dimension below N");
     if (!m->factored) return ctx_fail(ctx, GBEM_ERR_STATE, "solve before factor");
     DeviceGuard g(ctx->device);
+    TraceScope ts(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     gbem_status st = ensure_solve_buffers(m, nrhs, s);
     if (st != GBEM_OK) return st;
@@ -567,6 +636,7 @@ gbem_status gbem_capacitance(gbem_mesh_t* mesh, gbem_matrix_t* m, double eps_r, 
     gbem_ctx* ctx = m->ctx;
     if (m->mesh != mesh) return ctx_fail(ctx, GBEM_ERR_ARG, "matrix was assembled from another mesh");
     DeviceGuard g(ctx->device);
+    TraceScope ts(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     gbem_status st;
     if (!m->factored && (st = gbem_factor(m, stream)) != GBEM_OK) return st;

@@ -619,12 +619,16 @@ cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, dou
     if (g.n <= 0) return cudaSuccess;
     long long nt = (g.n + GBEM_TILE - 1) / GBEM_TILE;
     long long tiles = nt * (nt + 1) / 2;
+    cudaEvent_t ev = trace_begin(s);
     if (prec == GBEM_MIXED)
         assemble_tiles<true><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, A32, counts);
     else
         assemble_tiles<false><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, nullptr,
                                                                    counts);
     count_launch();
+    // algorithmic bytes: the lower entries written (FP64, plus FP32 in mixed mode) and the panels read
+    const double entries = (double)g.n * (g.n + 1) / 2;
+    trace_end(GBEM_KERNEL_ASSEMBLE, ev, s, entries * (prec == GBEM_MIXED ? 12.0 : 8.0) + 45.0 * g.n, 0.0);
     return cudaGetLastError();
 }
 

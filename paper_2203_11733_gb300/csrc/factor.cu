@@ -3,17 +3,26 @@
 // the single-layer operator is elliptic, hence Cholesky).
 //
 // The matrix is np x np column-major (np a multiple of the block size nb = 64,
-// padding rows carry the identity), lower triangle significant.  For each
-// block column k:
-//   1. potrf_diag:  L_kk = chol(A_kk) in shared memory, and Linv_kk = L_kk^-1
-//                   (kept for the triangular solves);
+// padding rows carry the identity), lower triangle significant.
+//
+// FP64 storage, for each block column k:
+//   1. potrf_diag:  L_kk = chol(A_kk) and Linv_kk = L_kk^-1 (kept for the
+//                   panel products and the triangular solves);
 //   2. trsm_panel:  L_ik = A_ik Linv_kk^T for the blocks below;
 //   3. syrk_update: A_ij -= L_ik L_jk^T on the lower tiles of the trailing
 //                   matrix.
-// T is the storage and arithmetic type: double in FP64 mode, float in mixed
-// mode (whose FP64 refinement restores the solution's accuracy).  A
-// non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
+// FP32 storage (mixed mode, whose FP64 refinement restores the solution's
+// accuracy), two launches per block column k:
+//   1. panel_step:  L_ik for every block below, the update of the next one or
+//                   two block columns (the strip), and the TF32 hi/lo split
+//                   of the panel;
+//   2. step_fused:  CTA 0 factors and inverts diagonal block k+1 while the
+//                   other CTAs apply the panel to the rest of the trailing
+//                   matrix on the tensor cores (tc_syrk.cuh).
+// A non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
 // factorisation completes without NaNs; the host reports GBEM_ERR_NOT_SPD.
+#include <algorithm>
+
 #include "gbem_internal.h"
 #include "tc_syrk.cuh"
 
@@ -21,26 +30,97 @@ namespace {
 
 constexpr int NB = 64;
 
-// Cholesky of one 64x64 diagonal block fused with the inverse of its factor.
-// Each of the 256 threads keeps a fixed 4x4 sub-block of the matrix A and of
-// X = L^-1 (started as the identity) in registers.  Step j publishes, through
-// double-buffered shared memory, the current column j of A (unscaled) and
-// row j of X; then every thread
-//   - subtracts a_rj a_cj / a_jj from its entries of A right of column j,
-//   - finalises X_j = X_j / l_jj and subtracts l_ij X_j from its rows i > j
-//     of X (l_ij = a_ij / sqrt(a_jj): forward elimination of the identity).
-// One barrier per column.  Column j of L is a_.j / sqrt(a_jj) at the end.
+// Cholesky of one 64x64 diagonal block and the inverse X = L^-1 of its factor
+// (kept for the panel products and the triangular solves), in 16 steps of 4
+// columns with one barrier each.
+//
+// The 136 threads below index 136 each own one 4x4 block (R, C), R >= C, of
+// the lower triangle, in registers.  At step s:
+//   1. the owners of column block s publish it through double-buffered
+//      shared memory;
+//   2. every thread with R >= s factors the 4x4 pivot block
+//      P_ss = L_ss L_ss^T itself and solves its own rows against it, which
+//      gives its block L_Rs;
+//   3. threads right of column block s apply the rank-4 update
+//      A_RC -= L_Rs L_Cs^T; the owners store L_Rs, and from then on their
+//      registers accumulate block (R, s) of X;
+//   4. X follows by block forward substitution one step behind the factor:
+//      threads with C < s <= R subtract L_R,s-1 X_s-1,C (X_s-1,C was
+//      published at step s-1), and the threads of row block s finish
+//      X_sC = L_ss^-1 (I_sC - sum_J L_sJ X_JC) and publish it.
 // A non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
 // factorisation completes without NaNs.
 template <typename T>
 struct PotrfSmem {
-    T col[2][NB];
-    T rowx[2][NB];
-    T piv[NB];
+    T pan[2][NB][4];   // column block s of the reduced matrix, pan[b][r][w]
+    T xr[2][4][NB];    // row block s of X, xr[b][w][c]
 };
 
 __device__ __forceinline__ float rsqrt_t(float d) { return rsqrtf(d); }
 __device__ __forceinline__ double rsqrt_t(double d) { return 1.0 / sqrt(d); }
+
+// barrier 1 over warps 0-4 (the threads that own a block of the triangle)
+__device__ __forceinline__ void bar_factor() { asm volatile("bar.sync 1, 160;" ::: "memory"); }
+
+// four consecutive elements (16- or 32-byte aligned)
+__device__ __forceinline__ void load4(const float* p, float v[4])
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d)
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+// P = Ld Ld^T for a 4x4 block (lower entries of p); dv[w] = 1 / Ld[w][w].
+template <typename T>
+__device__ __forceinline__ void chol4(const T p[4][4], T Ld[4][4], T dv[4], bool& bad)
+{
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        T d = p[w][w];
+#pragma unroll
+        for (int q = 0; q < w; ++q) d -= Ld[w][q] * Ld[w][q];
+        if (!(d > T(0))) {
+            bad = true;
+            d = T(1);
+        }
+        const T rs = rsqrt_t(d);
+        dv[w] = rs;
+        Ld[w][w] = d * rs;
+#pragma unroll
+        for (int i = w + 1; i < 4; ++i) {
+            T a = p[i][w];
+#pragma unroll
+            for (int q = 0; q < w; ++q) a -= Ld[i][q] * Ld[w][q];
+            Ld[i][w] = a * rs;
+        }
+    }
+}
+
+// l = a Ld^-T: the row of L whose row of the reduced matrix is a.
+template <typename T>
+__device__ __forceinline__ void solve_row(const T a[4], const T Ld[4][4], const T dv[4], T l[4])
+{
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        T x = a[w];
+#pragma unroll
+        for (int q = 0; q < w; ++q) x -= l[q] * Ld[w][q];
+        l[w] = x * dv[w];
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
@@ -49,79 +129,132 @@ __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T*
     extern __shared__ unsigned char smem_raw[];
     PotrfSmem<T>& S = *reinterpret_cast<PotrfSmem<T>*>(smem_raw);
     const int tid = threadIdx.x;
-    const int r0 = (tid & 15) * 4, c0 = (tid >> 4) * 4;   // this thread's 4x4 sub-block
-    T x[4][4], y[4][4];
+    if (tid >= 160) return;
+    // triangular thread map: tid -> (R, C), R >= C, column blocks in order
+    const bool act = tid < 136;
+    int C = 0, R = act ? tid : 0;
+    while (R >= 16 - C) {
+        R -= 16 - C;
+        ++C;
+    }
+    R += C;
+    const int r0 = 4 * R, c0 = 4 * C;
+    T z[4][4], lr[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+        T col[4] = {T(0), T(0), T(0), T(0)};
+        if (act) load4(L + (size_t)(k0 + r0) + (size_t)(k0 + c0 + v) * ld, col);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int r = r0 + u, c = c0 + v;
-            x[u][v] = (r >= c) ? L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] : T(0);
-            y[u][v] = (r == c) ? T(1) : T(0);
+        for (int u = 0; u < 4; ++u) {
+            z[u][v] = col[u];
+            lr[u][v] = T(0);
         }
-    for (int j = 0; j < NB; ++j) {
-        const int b = j & 1;
-        if (c0 <= j && j < c0 + 4) {
+    }
+    bool bad = false;
+#pragma unroll 1
+    for (int s = 0; s < 16; ++s) {
+        const int b = s & 1;
+        if (act && C == s) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-                if (c0 + v == j)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) S.col[b][r0 + u] = x[u][v];
+            for (int u = 0; u < 4; ++u) store4(&S.pan[b][r0 + u][0], z[u][0], z[u][1], z[u][2], z[u][3]);
         }
-        if (r0 <= j && j < r0 + 4) {
+        bar_factor();
+        if (!act || R < s) continue;
+        T p[4][4], Ld[4][4], dv[4], nr[4][4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) load4(&S.pan[b][4 * s + w][0], p[w]);
+        chol4(p, Ld, dv, bad);
+        if (R == s) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (r0 + u == j)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) S.rowx[b][c0 + v] = y[u][v];
+                for (int w = 0; w < 4; ++w) nr[u][w] = Ld[u][w];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                T a[4];
+                load4(&S.pan[b][r0 + u][0], a);
+                solve_row(a, Ld, dv, nr[u]);
+            }
         }
-        __syncthreads();
-        T d = S.col[b][j];
-        if (tid == 0) S.piv[j] = d;
-        if (!(d > T(0))) d = T(1);
-        const T rs = rsqrt_t(d);          // 1 / l_jj
-        const T rd = rs * rs;             // 1 / a_jj
-        if (r0 + 3 < j) continue;   // rows above j: nothing left to update
-        T cr[4];
+        if (C == s) {
+            // the block of L is final: store it and start the block of X
 #pragma unroll
-        for (int u = 0; u < 4; ++u) cr[u] = S.col[b][r0 + u];
-        if (c0 + 3 > j) {            // entries of A right of column j
-            T cc[4];
+            for (int v = 0; v < 4; ++v) {
+                T* dst = L + (size_t)(k0 + r0) + (size_t)(k0 + c0 + v) * ld;
+                if (R > C) store4(dst, nr[0][v], nr[1][v], nr[2][v], nr[3][v]);
+                else {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) cc[v] = S.col[b][c0 + v] * rd;
+                    for (int u = v; u < 4; ++u) dst[u] = nr[u][v];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) z[u][v] = (R == C && u == v) ? T(1) : T(0);
+            }
+            if (R == C && bad) info[0] = 1;
+        } else {
+            T P[4][4], Q[4][4];   // z -= P Q^T
+            if (C > s) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    T a[4];
+                    load4(&S.pan[b][c0 + v][0], a);
+                    solve_row(a, Ld, dv, Q[v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) P[u][w] = nr[u][w];
+            } else {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    T x[4];
+                    load4(&S.xr[b ^ 1][w][c0], x);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) Q[v][w] = x[v];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) P[u][w] = lr[u][w];
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    if (c0 + v > j && r0 + u >= c0 + v) x[u][v] -= cr[u] * cc[v];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) z[u][v] -= P[u][w] * Q[v][w];
         }
-        T xj[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) xj[v] = S.rowx[b][c0 + v] * rs;   // final row j of X
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const T l = cr[u] * rs;
+        if (R == s) {
+            // finish row block s of X: z = L_ss^-1 z, column by column
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                if (r0 + u > j) y[u][v] -= l * xj[v];
-                else if (r0 + u == j) y[u][v] = xj[v];
+                T col[4] = {z[0][v], z[1][v], z[2][v], z[3][v]}, x[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    T t = col[w];
+#pragma unroll
+                    for (int q = 0; q < w; ++q) t -= Ld[w][q] * x[q];
+                    x[w] = t * dv[w];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) z[u][v] = x[u];
             }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) store4(&S.xr[b][w][c0], z[w][0], z[w][1], z[w][2], z[w][3]);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) lr[u][w] = nr[u][w];
     }
-    __syncthreads();
-    if (tid < NB && !(S.piv[tid] > T(0))) info[0] = 1;
+    if (!act) return;
+    // X: this block and zeros in its mirror above the diagonal
     T* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int r = r0 + u, c = c0 + v;
-            T p = S.piv[c];
-            if (!(p > T(0))) p = T(1);
-            if (r > c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = x[u][v] * rsqrt_t(p);
-            else if (r == c) L[(size_t)(k0 + r) + (size_t)(k0 + c) * ld] = p * rsqrt_t(p);
-            Lb[r + (size_t)c * NB] = y[u][v];
-        }
+    for (int v = 0; v < 4; ++v) {
+        store4(Lb + r0 + (size_t)(c0 + v) * NB, z[0][v], z[1][v], z[2][v], z[3][v]);
+        if (R > C) store4(Lb + c0 + (size_t)(r0 + v) * NB, T(0), T(0), T(0), T(0));
+    }
 }
 
 template <typename T>
@@ -222,63 +355,161 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-// The leading column strip of the trailing matrix, gridDim.y 64-wide column
-// blocks wide: tiles (t0 + 64 I, t0 + 64 J) with I >= J, t0 = k0 + 64.
-template <typename T>
-__global__ void __launch_bounds__(256) syrk_strip(T* __restrict__ L, int ld, int k0)
+constexpr long long kPanelSpinLimit = 1LL << 24;   // ~1 s of polling at 32 ns
+
+__device__ __forceinline__ unsigned panel_load_acquire(const unsigned* p)
 {
-    if (blockIdx.x < blockIdx.y) return;
-    extern __shared__ unsigned char smem_raw[];
-    T* sa = reinterpret_cast<T*>(smem_raw);
-    T* sb = sa + NB * (NB + 1);
-    const int t0 = k0 + NB;
-    const int rI = t0 + NB * blockIdx.x, rJ = t0 + NB * blockIdx.y;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e % NB, c = e / NB;
-        sa[r * (NB + 1) + c] = L[(size_t)(rI + r) + (size_t)(k0 + c) * ld];
-        sb[r * (NB + 1) + c] = L[(size_t)(rJ + r) + (size_t)(k0 + c) * ld];
-    }
-    __syncthreads();
-    const int tr = (tid % 16) * 4, tc = (tid / 16) * 4;
-    T acc[4][4] = {};
-    for (int t = 0; t < NB; ++t) {
-        T x[4], y[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            x[u] = sa[(tr + u) * (NB + 1) + t];
-            y[u] = sb[(tc + u) * (NB + 1) + t];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) L[(size_t)(rI + tr + u) + (size_t)(rJ + tc + v) * ld] -= acc[u][v];
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Tensor-core trailing update of the lower 128 x 128 tiles of [r0, np)^2
-// (FP32 storage, 3xTF32 arithmetic) from the split panel; a bounded wait that
-// gives up sets status[0] = GBEM_ERR_TIMEOUT.
-__global__ void __launch_bounds__(256) syrk_tc(float* __restrict__ L, int ld, int r0,
-                                               const unsigned char* __restrict__ hi,
-                                               const unsigned char* __restrict__ lo, int* status)
+__device__ __forceinline__ void panel_store_release(unsigned* p, unsigned v)
 {
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    long long b = blockIdx.x;
-    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
-    while ((long long)I * (I + 1) / 2 > b) --I;
-    const int J = (int)(b - (long long)I * (I + 1) / 2);
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem) && threadIdx.x == 0)
-        atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+
+// Panel step k of the FP32 factorisation: one persistent cooperative launch
+// over the row blocks i = k+1 .. nblk-1 below the diagonal block.  Per row
+// block:
+//   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
+//      so the sum over t stops at the output column);
+//   2. the CTA that owns one of the sw strip blocks c = k+1 .. k+sw
+//      publishes its L_ck with a release flag (token k + 1);
+//   3. row blocks at or below r0 write the TF32 hi/lo split of L_ik in the
+//      tensor-core operand layout;
+//   4. A_ic -= L_ik L_ck^T for the strip blocks c <= i, after acquiring the
+//      flag of L_ck (a bounded wait: one that gives up sets status to
+//      GBEM_ERR_TIMEOUT and the CTA goes on with whatever it read).
+// The owners of the strip blocks take them as their first row block and wait
+// for nothing before publishing, so no wait can form a cycle; the cooperative
+// launch makes every CTA resident.
+__global__ void __launch_bounds__(256) panel_step(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv,
+                                                  int nblk, int sw, int r0, unsigned char* __restrict__ hi,
+                                                  unsigned char* __restrict__ lo, unsigned* __restrict__ flags,
+                                                  unsigned token, int* __restrict__ status)
+{
+    // Blocks are stored transposed (t-major, rows padded to 68 floats) so
+    // that a thread's four rows or columns at one t are one 16-byte load.
+    constexpr int P = NB + 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*ivT)[P] = reinterpret_cast<float(*)[P]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
+    float(*aT)[P] = ivT + NB;                                   // aT[t][r] = A_ik, then L_ik
+    float(*lcT)[P] = aT + NB;                                   // lcT[s * 64 + t][c] = L_ck[c][t]
+    const int tid = threadIdx.x;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const int k0 = k * NB, m = nblk - k - 1;
+    const float* Lb = Linv + (size_t)k * NB * NB;
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {   // Linv_kk column-major: e*4 = c + 64 t
+        const float4 q = reinterpret_cast<const float4*>(Lb)[e];
+        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = q;
+    }
+    unsigned have = 0;   // bit s: L_ck of strip block s is in shared memory
+    for (int idx = blockIdx.x; idx < m; idx += gridDim.x) {
+        const int i = k + 1 + idx, rI = i * NB;
+        __syncthreads();   // the previous row block is done with aT
+        for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+            const int t = e >> 4, r = (e & 15) * 4;
+            *reinterpret_cast<float4*>(&aT[t][r]) =
+                *reinterpret_cast<const float4*>(L + (size_t)(rI + r) + (size_t)(k0 + t) * ld);
+        }
+        __syncthreads();
+        float acc[4][4] = {};
+        for (int t = 0; t < tc + 4; ++t) {   // Linv_kk is lower triangular
+            const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+            const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+        }
+        __syncthreads();   // every thread is done reading A_ik
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+            *reinterpret_cast<float4*>(&aT[tc + v][tr]) = q;
+            *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(k0 + tc + v) * ld) = q;
+        }
+        if (idx < sw) {
+            __syncthreads();   // the whole block is stored
+            if (tid == 0) {
+                __threadfence();
+                panel_store_release(flags + idx, token);
+            }
+        }
+        if (rI >= r0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rr = rI - r0 + tr + u;
+                const size_t off = (size_t)(rr / tc::TM) * tc::OPER_BYTES + tc::kmajor_offset(rr % tc::TM, tc);
+                float h[4], l[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    h[v] = tc::to_tf32(acc[u][v]);
+                    l[v] = acc[u][v] - h[v];
+                }
+                *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        __syncthreads();   // aT holds L_ik
+        for (int sidx = 0; sidx < sw; ++sidx) {
+            const int c = k + 1 + sidx;
+            if (c > i) break;
+            const float(*bT)[P] = aT;
+            if (c != i) {
+                if (!((have >> sidx) & 1u)) {
+                    if (tid == 0) {
+                        long long spins = 0;
+                        while (panel_load_acquire(flags + sidx) < token) {
+                            if (++spins > kPanelSpinLimit || atomicAdd(status, 0) != 0) {
+                                atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                    }
+                    __syncthreads();
+                    float(*dst)[P] = lcT + sidx * NB;
+                    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+                        const int t = e >> 4, r = (e & 15) * 4;
+                        *reinterpret_cast<float4*>(&dst[t][r]) =
+                            __ldcg(reinterpret_cast<const float4*>(L + (size_t)(c * NB + r) + (size_t)(k0 + t) * ld));
+                    }
+                    __syncthreads();
+                    have |= 1u << sidx;
+                }
+                bT = lcT + sidx * NB;
+            }
+            float acc2[4][4] = {};
+            for (int t = 0; t < NB; ++t) {
+                const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+                const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
+                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float4* p = reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(c * NB + tc + v) * ld);
+                float4 o = *p;
+                o.x -= acc2[0][v];
+                o.y -= acc2[1][v];
+                o.z -= acc2[2][v];
+                o.w -= acc2[3][v];
+                *p = o;
+            }
+        }
+    }
+}
+
+constexpr size_t kPanelSmem = 4 * NB * (NB + 4) * sizeof(float);
 
 // One launch of the FP32 factorisation step: CTA 0 factors the next
-// diagonal block (k0n, already brought up to date by the strip kernel) while
+// diagonal block (k0n, already brought up to date by the panel kernel) while
 // the other CTAs apply the current panel to the tensor-core region [r0, np)^2,
 // which does not touch that block.  The diagonal factorisation is thereby
 // hidden behind the trailing update.
@@ -310,55 +541,76 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
     if ((e = cudaFuncSetAttribute(potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(PotrfSmem<T>))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(syrk_strip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
-    if (kTensor &&
-        (e = cudaFuncSetAttribute(syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
-            cudaSuccess)
-        return e;
-    if (kTensor) {
+    if constexpr (kTensor) {
         if ((e = cudaFuncSetAttribute(step_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
-            cudaSuccess)
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(panel_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem)) !=
+                cudaSuccess)
             return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_step, 256, kPanelSmem)) != cudaSuccess)
+            return e;
+        const int resident = std::max(1, per) * sms;
+        unsigned char* hi = split;
+        unsigned char* lo = split + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
+        unsigned* flags = reinterpret_cast<unsigned*>(lo + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES);
+        if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
         // block 0 is factored alone; every later diagonal block is factored
         // inside the fused launch of the previous step
         potrf_diag<T><<<1, 256, sizeof(PotrfSmem<T>), s>>>(L, np, 0, Linv, info);
         count_launch();
+        float* Lf = reinterpret_cast<float*>(L);
+        const float* Linvf = reinterpret_cast<const float*>(Linv);
+        int* status = info + 3;
         for (int k = 0; k + 1 < nblk; ++k) {
             const int k0 = k * NB;
-            const int m = nblk - k - 1;   // trailing order in 64-blocks
-            trsm_panel<T><<<m, 256, smem, s>>>(L, np, k0, Linv);
-            count_launch();
-            // strip: one or two column blocks, leaving an even number of
+            const int m = nblk - k - 1;   // row blocks below the diagonal
+            // strip of one or two column blocks, leaving an even number of
             // blocks (whole 128-tiles) for the tensor cores
-            const int sw = ((m - 1) & 1) ? 2 : 1;
-            syrk_strip<T><<<dim3(m, sw), 256, smem, s>>>(L, np, k0);
+            int sw = ((m - 1) & 1) ? 2 : 1;
+            int r0 = k0 + NB + NB * sw;
+            int kk = k, ld = np;
+            unsigned token = (unsigned)k + 1;
+            void* args[] = {&Lf, &ld, &kk, &Linvf, (void*)&nblk, &sw, &r0, &hi, &lo, &flags, &token, &status};
+            const int grid = std::min(m, resident);
+            cudaEvent_t ev = trace_begin(s);
+            if ((e = cudaLaunchCooperativeKernel((const void*)panel_step, dim3(grid), dim3(256), args, kPanelSmem, s)) !=
+                cudaSuccess)
+                return e;
             count_launch();
-            const int r0 = k0 + NB + NB * sw;
-            const long long nt = (np - r0) / tc::TM;
-            // one split buffer suffices: the next step's split follows this
-            // step's fused launch in stream order
-            unsigned char* hi = split;
-            unsigned char* lo = split + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
-            if (nt > 0) {
-                const long long elems = (long long)(np - r0) * tc::TK;
-                const int sgrid = (int)std::min<long long>(4096, (elems + 255) / 256);
-                tc::split_panel<<<sgrid, 256, 0, s>>>(reinterpret_cast<const float*>(L), np, k0, r0, np, hi, lo);
-                count_launch();
+            {
+                // per row block: A_ik read, L_ik written, its hi/lo split
+                // written (below r0), the strip blocks read and written
+                const double blk = 4.0 * NB * NB;
+                const double strips = (double)m * sw - (sw - 1);
+                const double split_rows = (double)(np - r0);
+                trace_end(GBEM_KERNEL_PANEL, ev, s, 2.0 * m * blk + blk + 8.0 * split_rows * NB + 2.0 * strips * blk,
+                          (double)m * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB);
             }
+            const long long nt = (np - r0) / tc::TM;
+            ev = trace_begin(s);
             step_fused<<<(unsigned)(1 + nt * (nt + 1) / 2), 256, tc::SMEM_BYTES, s>>>(
-                reinterpret_cast<float*>(L), np, k0 + NB, reinterpret_cast<float*>(Linv), info, r0, hi, lo);
+                Lf, np, k0 + NB, reinterpret_cast<float*>(Linv), info, r0, hi, lo);
             count_launch();
+            {
+                // every lower 128-tile of [r0, np)^2 read and written once, the
+                // hi/lo panel read once; the diagonal block read, its factor
+                // and inverse written
+                const double tiles = (double)nt * (nt + 1) / 2;
+                const double tb = 4.0 * tc::TM * tc::TM;
+                trace_end(GBEM_KERNEL_UPDATE, ev, s, 2.0 * tiles * tb + 8.0 * (np - r0) * NB + 3.0 * 4.0 * NB * NB,
+                          tiles * 2.0 * tc::TM * tc::TM * tc::TK + 2.0 * NB * NB * NB / 3.0);
+            }
         }
         return cudaGetLastError();
     }
+    if ((e = cudaFuncSetAttribute(trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * NB;
         potrf_diag<T><<<1, 256, sizeof(PotrfSmem<T>), s>>>(L, np, k0, Linv, info);
@@ -412,7 +664,7 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
     return cholesky<double>(L, np, Linv, info, nullptr, s);
 }
 
-size_t cholesky_f32_split_bytes(int np) { return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES; }
+size_t cholesky_f32_split_bytes(int np) { return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 256; }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
                                 cudaStream_t s)

@@ -17,6 +17,26 @@ constexpr int GBEM_TILE = 32;
 // Largest Gauss-Legendre order used by the far-field rule.
 constexpr int GBEM_GL_MAX = 6;
 
+// Kernel-level tracing (gbem_set_timing level 2).  The entry points install
+// their context's trace for the calling thread (TraceScope); launchers wrap
+// their main kernels in trace_begin / trace_end, which do nothing when no
+// trace is installed.
+struct KernelTrace {
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    std::vector<Rec> recs;
+    double ms[GBEM_NKERNEL] = {};
+    double bytes[GBEM_NKERNEL] = {};
+    double flops[GBEM_NKERNEL] = {};
+    long long launches[GBEM_NKERNEL] = {};
+};
+extern thread_local KernelTrace* g_trace;
+cudaEvent_t trace_begin(cudaStream_t s);
+void trace_end(int kind, cudaEvent_t a, cudaStream_t s, double bytes, double flops);
+
 struct gbem_ctx_s {
     int device = -1;
     int num_sms = 0;
@@ -30,6 +50,8 @@ struct gbem_ctx_s {
     bool gl_uploaded = false;
     // tracing
     bool timing = false;
+    bool ktiming = false;
+    KernelTrace ktrace;
     struct Pending {
         int phase;
         cudaEvent_t a, b;
@@ -135,6 +157,11 @@ struct gbem_matrix_s {
 };
 
 // ---- context helpers (api.cpp)
+struct TraceScope {
+    KernelTrace* prev;
+    explicit TraceScope(gbem_ctx* ctx);
+    ~TraceScope();
+};
 gbem_status ctx_fail(gbem_ctx* ctx, gbem_status st, const std::string& msg);
 void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s);
 void ctx_free(gbem_ctx* ctx, void* p, size_t bytes, cudaStream_t s);

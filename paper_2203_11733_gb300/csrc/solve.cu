@@ -248,23 +248,32 @@ cudaError_t sweep_pair(const T* L, const T* Linv, int np, T* W, T* Y, int nr, un
         return e;
     unsigned e1 = g_epoch.fetch_add(2);
     unsigned e2 = e1 + 1;
+    // one sweep reads the lower triangle of L and the diagonal-block
+    // inverses once and the right-hand sides twice
+    const double sweep_bytes =
+        sizeof(T) * ((double)np * (np + NB) / 2 + (double)np * NB + 3.0 * np * nr);
+    const double sweep_flops = (double)np * np * nr;
     {
         const T* Wc = W;
         int grid = coop_grid(trsv_fwd<T, R>, smem, nblk);
         void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Wc, (void*)&Y, (void*)&nr,
                         (void*)&sync, (void*)&e1, (void*)&status, (void*)&done};
+        cudaEvent_t ev = trace_begin(s);
         if ((e = cudaLaunchCooperativeKernel((void*)trsv_fwd<T, R>, grid, 256, args, smem, s)) != cudaSuccess)
             return e;
         count_launch();
+        trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
     }
     {
         const T* Yc = Y;
         int grid = coop_grid(trsv_bwd<T, R>, smem, nblk);
         void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Yc, (void*)&W, (void*)&nr,
                         (void*)&sync, (void*)&e2, (void*)&status, (void*)&done};
+        cudaEvent_t ev = trace_begin(s);
         if ((e = cudaLaunchCooperativeKernel((void*)trsv_bwd<T, R>, grid, 256, args, smem, s)) != cudaSuccess)
             return e;
         count_launch();
+        trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
     }
     return cudaSuccess;
 }
@@ -723,10 +732,15 @@ cudaError_t launch_residual(const double* A, int np, const double* Bp, const dou
         const double* Bc = Bp + (size_t)c0 * np;
         const double* Xc = X + (size_t)c0 * np;
         double* Rc = R + (size_t)c0 * np;
+        cudaEvent_t ev = trace_begin(s);
         if (nr <= 4) residual<4><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
         else if (nr <= 8) residual<8><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
         else residual<16><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
         count_launch();
+        // the lower triangle of A64 once, B and X read and R written; each
+        // lower entry serves two products per right-hand side
+        trace_end(GBEM_KERNEL_RESIDUAL, ev, s, 8.0 * ((double)np * (np + CT) / 2 + 3.0 * np * nr),
+                  2.0 * (double)np * np * nr);
     }
     return cudaGetLastError();
 }

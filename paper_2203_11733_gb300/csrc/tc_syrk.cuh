@@ -7,8 +7,8 @@
 // accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi, which keeps
 // the error of the update near FP32 rounding.
 //
-// The panel columns [k0, k0 + 64) are split once per elimination step by
-// split_panel into hi and lo copies laid out, per 128-row block, exactly as
+// The panel columns [k0, k0 + 64) are split once per elimination step (by
+// the panel kernel, as it produces them) into hi and lo copies laid out, per 128-row block, exactly as
 // the tensor core reads them from shared memory: the canonical K-major layout
 // without swizzle, 8-row x 16-byte core matrices consecutive along K (leading
 // byte offset 128 B, 16 of them for the 64 panel columns) and then along M/N
@@ -119,23 +119,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// hi/lo split of panel rows [r0, np) x columns [k0, k0 + 64) of the
-// column-major L into the block layout above (one thread per element).
-__global__ void split_panel(const float* __restrict__ L, int ld, int k0, int r0, int np,
-                            unsigned char* __restrict__ hi, unsigned char* __restrict__ lo)
-{
-    const long long total = (long long)(np - r0) * TK;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e % (np - r0)), k = (int)(e / (np - r0));
-        const float x = L[(size_t)(r0 + r) + (size_t)(k0 + k) * ld];
-        const float h = to_tf32(x);
-        const size_t off = (size_t)(r / TM) * OPER_BYTES + kmajor_offset(r % TM, k);
-        *reinterpret_cast<float*>(hi + off) = h;
-        *reinterpret_cast<float*>(lo + off) = x - h;
-    }
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)

@@ -98,6 +98,9 @@ _SIGS = {
     "gbem_matrix_status": (ctypes.c_int, [_P]),
     "gbem_matrix_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "gbem_matrix_destroy": (None, [_P]),
+    "gbem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gbem_get_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "gbem_get_kernel_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "gbem_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P)]),
     "gbem_batch_run": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "gbem_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong), _P]),
@@ -113,6 +116,39 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "gbem_server_destroy": (None, [_P]),
 }
+
+
+class Stats(ctypes.Structure):
+    """gbem_stats: per-phase device time and calls, kernels launched."""
+    _fields_ = [("ms", ctypes.c_double * 5), ("calls", ctypes.c_longlong * 5), ("launches", ctypes.c_longlong)]
+
+
+KERNELS = ["assemble", "panel", "update", "sweep", "residual"]
+
+
+class KernelStats(ctypes.Structure):
+    """gbem_kernel_stats: per traced kernel, device time, launches and the
+    algorithmic bytes and flops of those launches."""
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_longlong * 5),
+                ("bytes", ctypes.c_double * 5), ("flops", ctypes.c_double * 5)]
+
+
+def set_timing(ctx, level: int):
+    """0 off, 1 phase events, 2 phase and per-kernel events."""
+    ctx.check(ctx.lib.gbem_set_timing(ctx.h, int(level)))
+
+
+def get_stats(ctx, reset: bool = False) -> dict:
+    s = Stats()
+    ctx.check(ctx.lib.gbem_get_stats(ctx.h, ctypes.byref(s), 1 if reset else 0))
+    return {"ms": list(s.ms), "calls": list(s.calls), "launches": s.launches}
+
+
+def get_kernel_stats(ctx, reset: bool = False) -> dict:
+    s = KernelStats()
+    ctx.check(ctx.lib.gbem_get_kernel_stats(ctx.h, ctypes.byref(s), 1 if reset else 0))
+    return {k: {"ms": s.ms[i], "launches": s.launches[i], "bytes": s.bytes[i], "flops": s.flops[i]}
+            for i, k in enumerate(KERNELS)}
 
 
 def library_path() -> str:
