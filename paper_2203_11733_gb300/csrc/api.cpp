@@ -176,9 +176,10 @@ gbem_status ensure_solve_buffers(gbem_matrix_t* m, int nrhs, cudaStream_t s)
     m->X = mat_alloc<double>(m, np * nrhs, s);
     m->R = mat_alloc<double>(m, np * nrhs, s);
     m->B = mat_alloc<double>(m, np * nrhs, s);
-    size_t esz = (m->prec == GBEM_MIXED) ? sizeof(float) : sizeof(double);
-    m->W = (esz == 4) ? (void*)mat_alloc<float>(m, 2 * np * nrhs, s)
-                      : (void*)mat_alloc<double>(m, 2 * np * nrhs, s);
+    // W: FP64 mode, solve vectors and work (2 x np x nrhs doubles); mixed
+    // mode, FP32 solve vectors and work, then X as float pairs (4 x np x nrhs
+    // floats): the same bytes
+    m->W = mat_alloc<double>(m, 2 * np * nrhs, s);
     if (!m->X || !m->R || !m->B || !m->W) return GBEM_ERR_OOM;
     m->cap_rhs = nrhs;
     return GBEM_OK;
@@ -222,6 +223,7 @@ gbem_status solve_padded(gbem_matrix_t* m, int nrhs, cudaStream_t s, int* iters,
     }
     // mixed: X = 0, R = B; repeat { W = f32(R); W = L^-T L^-1 W; X += W; R = B - A X }
     float* W = static_cast<float*>(m->W);
+    float2* Xdf = reinterpret_cast<float2*>(W + 2 * (size_t)np * nrhs);
     const float* Lf = m->A32;
     const float* Li = static_cast<const float*>(m->Linv);
     int* done = m->dflags + 1;
@@ -233,12 +235,16 @@ gbem_status solve_padded(gbem_matrix_t* m, int nrhs, cudaStream_t s, int* iters,
         if (!cuda_ok(ctx, launch_to_f32(m->R, np, nrhs, W, done, s), "to_f32") ||
             !cuda_ok(ctx, launch_trsv_f32_guarded(Lf, Li, np, m->nb, W, nrhs, m->dsync, m->dflags + 3, done, s),
                      "trsv") ||
-            !cuda_ok(ctx, launch_add_f32(W, np, nrhs, m->X, done, s), "add") ||
-            !cuda_ok(ctx, launch_residual(m->A64, np, m->B, m->X, nrhs, m->R, done, s), "residual") ||
+            !cuda_ok(ctx, launch_add_f32(W, np, nrhs, m->X, Xdf, done, s), "add") ||
+            !cuda_ok(ctx, launch_residual_df(reinterpret_cast<const float2*>(m->A64), np, m->B, Xdf, nrhs, m->R, done, s),
+                     "residual") ||
             !cuda_ok(ctx, launch_ir_check(m->R, m->B, np, nrhs, m->dnorm, ctx->tune.ir_tol, m->dflags, s),
                      "ir check"))
             return GBEM_ERR_CUDA;
-        // read the flags back: stop once converged
+        // read the flags back: stop once converged.  The first two
+        // iterations go out together (a converged iteration leaves the next
+        // one's kernels without work), saving one host round trip.
+        if (it == 0 && maxit > 1) continue;
         if (!cuda_ok(ctx, cudaMemcpyAsync(host_flags, m->dflags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s),
                      "d2h") ||
             !cuda_ok(ctx, cudaStreamSynchronize(s), "sync"))
@@ -686,6 +692,14 @@ gbem_status gbem_matrix_download(gbem_matrix_t* m, double* host)
                               cudaMemcpyDeviceToHost),
                  "download"))
         return GBEM_ERR_CUDA;
+    if (m->prec == GBEM_MIXED) {
+        // mixed-mode storage holds float pairs: the entry is hi + lo
+        for (size_t e = 0; e < (size_t)n * n; ++e) {
+            float p[2];
+            std::memcpy(p, host + e, sizeof(p));
+            host[e] = (double)p[0] + (double)p[1];
+        }
+    }
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < j; ++i) host[i + (size_t)j * n] = host[j + (size_t)i * n];
     return GBEM_OK;

@@ -470,8 +470,15 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
         const int ii = e & (GBEM_TILE - 1), jj = e >> 5;
         const double v = eval_class<T>(G, cls_of[e], ii, GBEM_TILE + jj);
         const size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
-        A64[i + j * (size_t)np] = v;
-        if (MIXED) A32[i + j * (size_t)np] = (float)v;
+        if (MIXED) {
+            // FP64 entry kept as an unevaluated float pair (hi + lo) for the
+            // compensated FP32 residual; hi is also the factor's copy
+            const float h = __double2float_rn(v);
+            reinterpret_cast<float2*>(A64)[i + j * (size_t)np] = make_float2(h, __double2float_rn(v - (double)h));
+            A32[i + j * (size_t)np] = h;
+        } else {
+            A64[i + j * (size_t)np] = v;
+        }
     }
     // class counts: near pairs, then far pairs by order
     if (tid < kClasses && counts) {
@@ -512,26 +519,28 @@ __global__ void __launch_bounds__(kThreads) assemble_batched(BatchView v, float 
                      (long long)blockIdx.x - v.tile_prefix[b]);
 }
 
-// Identity padding of every structure of a batch (rows n..np-1, lower part).
+// Identity padding of every structure of a batch (rows n..np-1, lower part;
+// batches are mixed: float pairs in the FP64 storage and the FP32 copy).
 __global__ void pad_batched(BatchView v)
 {
     const int b = blockIdx.y;
     const int n = v.n[b], np = v.np[b];
     double* A64 = v.A64 + v.moff[b];
-    float* A32 = v.A32 ? v.A32 + v.moff[b] : nullptr;
+    float* A32 = v.A32 + v.moff[b];
     long long total = (long long)(np - n) * np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         int r = n + (int)(e % (np - n));
         int c = (int)(e / (np - n));
         if (c > r) continue;
-        double val = (r == c) ? 1.0 : 0.0;
-        A64[r + (size_t)c * np] = val;
-        if (A32) A32[r + (size_t)c * np] = (float)val;
+        const float val = (r == c) ? 1.0f : 0.0f;
+        reinterpret_cast<float2*>(A64)[r + (size_t)c * np] = make_float2(val, 0.0f);
+        A32[r + (size_t)c * np] = val;
     }
 }
 
 // Identity in the padding rows (lower part): A[r][c] = (r == c) for r >= n.
+// With an FP32 copy (mixed mode) the FP64 storage holds float pairs.
 __global__ void pad_identity(double* A64, float* A32, int n, int np)
 {
     long long total = (long long)(np - n) * np;
@@ -540,9 +549,13 @@ __global__ void pad_identity(double* A64, float* A32, int n, int np)
         int r = n + (int)(e % (np - n));
         int c = (int)(e / (np - n));
         if (c > r) continue;
-        double v = (r == c) ? 1.0 : 0.0;
-        A64[r + (size_t)c * np] = v;
-        if (A32) A32[r + (size_t)c * np] = (float)v;
+        const double v = (r == c) ? 1.0 : 0.0;
+        if (A32) {
+            reinterpret_cast<float2*>(A64)[r + (size_t)c * np] = make_float2((float)v, 0.0f);
+            A32[r + (size_t)c * np] = (float)v;
+        } else {
+            A64[r + (size_t)c * np] = v;
+        }
     }
 }
 
@@ -636,12 +649,10 @@ cudaError_t launch_assemble_batched(const BatchView& v, long long tiles, gbem_pr
                                     cudaStream_t s)
 {
     if (tiles <= 0) return cudaSuccess;
+    if (prec != GBEM_MIXED) return cudaErrorInvalidValue;   // batches are mixed precision
     pad_batched<<<dim3(64, v.nb), 256, 0, s>>>(v);
     count_launch();
-    if (prec == GBEM_MIXED)
-        assemble_batched<true><<<(unsigned)tiles, kThreads, 0, s>>>(v, (float)q_near);
-    else
-        assemble_batched<false><<<(unsigned)tiles, kThreads, 0, s>>>(v, (float)q_near);
+    assemble_batched<true><<<(unsigned)tiles, kThreads, 0, s>>>(v, (float)q_near);
     count_launch();
     return cudaGetLastError();
 }

@@ -122,7 +122,7 @@ gbem_status gbem_batch_create(gbem_ctx* ctx, int count, gbem_mesh_t* const* mesh
     const size_t o_A64 = take(sizeof(double) * (size_t)M), o_A32 = take(sizeof(float) * (size_t)M);
     const size_t o_Linv = take(sizeof(float) * (size_t)I);
     const size_t o_B = take(8 * (size_t)V), o_X = take(8 * (size_t)V), o_R = take(8 * (size_t)V),
-                 o_W = take(4 * (size_t)V), o_Y = take(4 * (size_t)V);
+                 o_W = take(4 * (size_t)V), o_Y = take(4 * (size_t)V), o_Xdf = take(8 * (size_t)V);
     const size_t o_flags = take(sizeof(int) * 4 * (size_t)nb), o_C = take(8 * (size_t)C), o_res = take(8 * (size_t)nb);
     B->bytes = off;
     B->buf = ctx_alloc(ctx, B->bytes, nullptr);
@@ -196,6 +196,7 @@ gbem_status gbem_batch_create(gbem_ctx* ctx, int count, gbem_mesh_t* const* mesh
     v.R = reinterpret_cast<double*>(d + o_R);
     v.W = reinterpret_cast<float*>(d + o_W);
     v.Y = reinterpret_cast<float*>(d + o_Y);
+    v.Xdf = reinterpret_cast<float2*>(d + o_Xdf);
     v.flags = reinterpret_cast<int*>(d + o_flags);
     v.C = reinterpret_cast<double*>(d + o_C);
     v.resid = reinterpret_cast<double*>(d + o_res);

@@ -123,13 +123,12 @@ __device__ __forceinline__ void solve_row(const T a[4], const T Ld[4][4], const 
 }
 
 template <typename T>
-__device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
+__device__ __forceinline__ void potrf_work(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
                                            int* __restrict__ info)
 {
     extern __shared__ unsigned char smem_raw[];
     PotrfSmem<T>& S = *reinterpret_cast<PotrfSmem<T>*>(smem_raw);
     const int tid = threadIdx.x;
-    if (tid >= 160) return;
     // triangular thread map: tid -> (R, C), R >= C, column blocks in order
     const bool act = tid < 136;
     int C = 0, R = act ? tid : 0;
@@ -257,6 +256,76 @@ __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T*
     }
 }
 
+// Warps 0-4 factor; the other threads of the CTA pass through.
+template <typename T>
+__device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
+                                           int* __restrict__ info)
+{
+    if (threadIdx.x < 160) potrf_work<T>(L, ld, k0, Linv, info);
+}
+
+// Programmatic dependent launch: wait for the previous kernel of the stream
+// (a no-op when launched without the attribute), and let the next one be
+// scheduled early; it waits in turn before touching memory.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr int PT = NB + 4;   // padded row of a t-major 64 x 64 block in shared memory
+
+// L_ck = A_ck Linv_kk^T for the ns row blocks c = k+1 .. k+ns below diagonal
+// block k (k0 = 64 k), which its CTA has just factored.  Stored t-major,
+// lsT[s * 4096 + t * 64 + r] = L_ck[r][t], for the strip update of the next
+// panel step.  All 256 threads; shared memory: two t-major blocks.
+__device__ void strip_rows(const float* __restrict__ L, int ld, int k0, const float* __restrict__ Linv,
+                           float* __restrict__ lsT, int ns)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
+    float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_ck[r][t]
+    const int tid = threadIdx.x;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const float* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
+    __syncthreads();   // the factorisation is done with shared memory, its stores are issued
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x)
+        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = __ldcg(reinterpret_cast<const float4*>(Lb) + e);
+    for (int sidx = 0; sidx < ns; ++sidx) {
+        const int rc = k0 + NB * (1 + sidx);
+        if (sidx) __syncthreads();
+        for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+            const int t = e >> 4, r = (e & 15) * 4;
+            *reinterpret_cast<float4*>(&aT[t][r]) =
+                *reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld);
+        }
+        __syncthreads();
+        float acc[4][4] = {};
+        for (int t = 0; t < tc + 4; ++t) {   // Linv_kk is lower triangular
+            const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+            const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+        }
+        float* dst = lsT + (size_t)sidx * NB * NB;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            *reinterpret_cast<float4*>(dst + (size_t)(tc + v) * NB + tr) =
+                make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+    }
+}
+
+constexpr size_t kStripSmem = 2 * NB * PT * sizeof(float);
+
+// The first diagonal block of the FP32 factorisation and the strip rows of
+// panel step 0.
+__global__ void __launch_bounds__(256) potrf_first(float* __restrict__ L, int ld, float* __restrict__ Linv,
+                                                   int* __restrict__ info, float* __restrict__ lsT, int ns)
+{
+    potrf_body<float>(L, ld, 0, Linv, info);
+    if (ns > 0) strip_rows(L, ld, 0, Linv, lsT, ns);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_diag(T* __restrict__ L, int ld, int k0, T* __restrict__ Linv,
                                                   int* __restrict__ info)
@@ -355,171 +424,128 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-constexpr long long kPanelSpinLimit = 1LL << 24;   // ~1 s of polling at 32 ns
-
-__device__ __forceinline__ unsigned panel_load_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void panel_store_release(unsigned* p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Panel step k of the FP32 factorisation: one persistent cooperative launch
-// over the row blocks i = k+1 .. nblk-1 below the diagonal block.  Per row
-// block:
+// Panel step k of the FP32 factorisation, one CTA per row block
+// i = k + 1 + blockIdx.x below diagonal block k:
 //   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
 //      so the sum over t stops at the output column);
-//   2. the CTA that owns one of the sw strip blocks c = k+1 .. k+sw
-//      publishes its L_ck with a release flag (token k + 1);
-//   3. row blocks at or below r0 write the TF32 hi/lo split of L_ik in the
+//   2. row blocks at or below r0 write the TF32 hi/lo split of L_ik in the
 //      tensor-core operand layout;
-//   4. A_ic -= L_ik L_ck^T for the strip blocks c <= i, after acquiring the
-//      flag of L_ck (a bounded wait: one that gives up sets status to
-//      GBEM_ERR_TIMEOUT and the CTA goes on with whatever it read).
-// The owners of the strip blocks take them as their first row block and wait
-// for nothing before publishing, so no wait can form a cycle; the cooperative
-// launch makes every CTA resident.
+//   3. A_ic -= L_ik L_ck^T for the sw strip blocks c = k+1 .. k+sw, c <= i,
+//      with L_ck (lsT, t-major) computed by the CTA that factored block k.
+// The strip targets are read at the start, so their latency overlaps the
+// panel product.
 __global__ void __launch_bounds__(256) panel_step(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv,
-                                                  int nblk, int sw, int r0, unsigned char* __restrict__ hi,
-                                                  unsigned char* __restrict__ lo, unsigned* __restrict__ flags,
-                                                  unsigned token, int* __restrict__ status)
+                                                  int sw, int r0, unsigned char* __restrict__ hi,
+                                                  unsigned char* __restrict__ lo, const float* __restrict__ lsT)
 {
-    // Blocks are stored transposed (t-major, rows padded to 68 floats) so
-    // that a thread's four rows or columns at one t are one 16-byte load.
-    constexpr int P = NB + 4;
+    pdl_wait();
+    pdl_trigger();
+    // Blocks are stored t-major (rows padded to 68 floats) so that a
+    // thread's four rows or columns at one t are one 16-byte load.
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float(*ivT)[P] = reinterpret_cast<float(*)[P]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
-    float(*aT)[P] = ivT + NB;                                   // aT[t][r] = A_ik, then L_ik
-    float(*lcT)[P] = aT + NB;                                   // lcT[s * 64 + t][c] = L_ck[c][t]
+    float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
+    float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_ik, then L_ik
+    float(*lcT)[PT] = aT + NB;                                    // lcT[s * 64 + t][c] = L_ck[c][t]
     const int tid = threadIdx.x;
     const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
-    const int k0 = k * NB, m = nblk - k - 1;
+    const int k0 = k * NB;
+    const int i = k + 1 + blockIdx.x, rI = i * NB;
+    const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
+    float4 tgt[2][4];
+#pragma unroll
+    for (int sidx = 0; sidx < 2; ++sidx)
+        if (sidx < nstrip)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                tgt[sidx][v] = *reinterpret_cast<const float4*>(L + (size_t)(rI + tr) +
+                                                                (size_t)((k + 1 + sidx) * NB + tc + v) * ld);
     const float* Lb = Linv + (size_t)k * NB * NB;
-    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {   // Linv_kk column-major: e*4 = c + 64 t
-        const float4 q = reinterpret_cast<const float4*>(Lb)[e];
-        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = q;
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {   // Linv_kk column-major: 4e = c + 64 t
+        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(Lb)[e];
+        const int t = e >> 4, r = (e & 15) * 4;
+        *reinterpret_cast<float4*>(&aT[t][r]) =
+            *reinterpret_cast<const float4*>(L + (size_t)(rI + r) + (size_t)(k0 + t) * ld);
     }
-    unsigned have = 0;   // bit s: L_ck of strip block s is in shared memory
-    for (int idx = blockIdx.x; idx < m; idx += gridDim.x) {
-        const int i = k + 1 + idx, rI = i * NB;
-        __syncthreads();   // the previous row block is done with aT
-        for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
-            const int t = e >> 4, r = (e & 15) * 4;
-            *reinterpret_cast<float4*>(&aT[t][r]) =
-                *reinterpret_cast<const float4*>(L + (size_t)(rI + r) + (size_t)(k0 + t) * ld);
+    for (int e = tid; e < nstrip * NB * NB / 4; e += blockDim.x)
+        *reinterpret_cast<float4*>(&lcT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(lsT)[e];
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int t = 0; t < tc + 4; ++t) {
+        const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+        const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+    }
+    __syncthreads();   // every thread is done reading A_ik
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+        *reinterpret_cast<float4*>(&aT[tc + v][tr]) = q;
+        *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(k0 + tc + v) * ld) = q;
+    }
+    if (rI >= r0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int rr = rI - r0 + tr + u;
+            const size_t off = (size_t)(rr / tc::TM) * tc::OPER_BYTES + tc::kmajor_offset(rr % tc::TM, tc);
+            float h[4], l[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                h[v] = tc::to_tf32(acc[u][v]);
+                l[v] = acc[u][v] - h[v];
+            }
+            *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
         }
-        __syncthreads();
-        float acc[4][4] = {};
-        for (int t = 0; t < tc + 4; ++t) {   // Linv_kk is lower triangular
+    }
+    __syncthreads();   // aT holds L_ik
+#pragma unroll
+    for (int sidx = 0; sidx < 2; ++sidx) {
+        if (sidx >= nstrip) break;
+        const float(*bT)[PT] = lcT + sidx * NB;
+        float acc2[4][4] = {};
+        for (int t = 0; t < NB; ++t) {
             const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
-            const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+            const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
             const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+                for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
         }
-        __syncthreads();   // every thread is done reading A_ik
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
-            *reinterpret_cast<float4*>(&aT[tc + v][tr]) = q;
-            *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(k0 + tc + v) * ld) = q;
-        }
-        if (idx < sw) {
-            __syncthreads();   // the whole block is stored
-            if (tid == 0) {
-                __threadfence();
-                panel_store_release(flags + idx, token);
-            }
-        }
-        if (rI >= r0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int rr = rI - r0 + tr + u;
-                const size_t off = (size_t)(rr / tc::TM) * tc::OPER_BYTES + tc::kmajor_offset(rr % tc::TM, tc);
-                float h[4], l[4];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    h[v] = tc::to_tf32(acc[u][v]);
-                    l[v] = acc[u][v] - h[v];
-                }
-                *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-            }
-        }
-        __syncthreads();   // aT holds L_ik
-        for (int sidx = 0; sidx < sw; ++sidx) {
-            const int c = k + 1 + sidx;
-            if (c > i) break;
-            const float(*bT)[P] = aT;
-            if (c != i) {
-                if (!((have >> sidx) & 1u)) {
-                    if (tid == 0) {
-                        long long spins = 0;
-                        while (panel_load_acquire(flags + sidx) < token) {
-                            if (++spins > kPanelSpinLimit || atomicAdd(status, 0) != 0) {
-                                atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
-                                break;
-                            }
-                            __nanosleep(32);
-                        }
-                    }
-                    __syncthreads();
-                    float(*dst)[P] = lcT + sidx * NB;
-                    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
-                        const int t = e >> 4, r = (e & 15) * 4;
-                        *reinterpret_cast<float4*>(&dst[t][r]) =
-                            __ldcg(reinterpret_cast<const float4*>(L + (size_t)(c * NB + r) + (size_t)(k0 + t) * ld));
-                    }
-                    __syncthreads();
-                    have |= 1u << sidx;
-                }
-                bT = lcT + sidx * NB;
-            }
-            float acc2[4][4] = {};
-            for (int t = 0; t < NB; ++t) {
-                const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
-                const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
-                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                float4* p = reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(c * NB + tc + v) * ld);
-                float4 o = *p;
-                o.x -= acc2[0][v];
-                o.y -= acc2[1][v];
-                o.z -= acc2[2][v];
-                o.w -= acc2[3][v];
-                *p = o;
-            }
+            float4 o = tgt[sidx][v];
+            o.x -= acc2[0][v];
+            o.y -= acc2[1][v];
+            o.z -= acc2[2][v];
+            o.w -= acc2[3][v];
+            *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld) = o;
         }
     }
 }
 
-constexpr size_t kPanelSmem = 4 * NB * (NB + 4) * sizeof(float);
+constexpr size_t kPanelSmem = 4 * NB * PT * sizeof(float);
 
 // One launch of the FP32 factorisation step: CTA 0 factors the next
-// diagonal block (k0n, already brought up to date by the panel kernel) while
-// the other CTAs apply the current panel to the tensor-core region [r0, np)^2,
-// which does not touch that block.  The diagonal factorisation is thereby
-// hidden behind the trailing update.
+// diagonal block (k0n, already brought up to date by the panel kernel) and
+// computes the ns strip rows of the next panel step, while the other CTAs
+// apply the current panel to the tensor-core region [r0, np)^2, which touches
+// neither.  The diagonal factorisation is thereby hidden behind the trailing
+// update.
 __global__ void __launch_bounds__(256) step_fused(float* __restrict__ L, int ld, int k0n, float* __restrict__ Linv,
                                                   int* __restrict__ info, int r0, const unsigned char* __restrict__ hi,
-                                                  const unsigned char* __restrict__ lo)
+                                                  const unsigned char* __restrict__ lo, float* __restrict__ lsT, int ns)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    pdl_wait();
+    pdl_trigger();
     if (blockIdx.x == 0) {
         potrf_body<float>(L, ld, k0n, Linv, info);
+        if (ns > 0) strip_rows(L, ld, k0n, Linv, lsT, ns);
         return;
     }
     long long b = blockIdx.x - 1;
@@ -545,39 +571,43 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         if ((e = cudaFuncSetAttribute(step_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(panel_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(potrf_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
                 cudaSuccess)
             return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_step, 256, kPanelSmem)) != cudaSuccess)
-            return e;
-        const int resident = std::max(1, per) * sms;
         unsigned char* hi = split;
         unsigned char* lo = split + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
-        unsigned* flags = reinterpret_cast<unsigned*>(lo + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES);
-        if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+        float* lsT = reinterpret_cast<float*>(lo + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES);
+        float* Lf = reinterpret_cast<float*>(L);
+        float* Linvf = reinterpret_cast<float*>(Linv);
+        // strip width of panel step k: one or two column blocks, leaving an
+        // even number of blocks (whole 128-tiles) for the tensor cores
+        auto strip_width = [nblk](int k) {
+            const int m = nblk - k - 1;
+            return m <= 0 ? 0 : (((m - 1) & 1) ? 2 : 1);
+        };
         // block 0 is factored alone; every later diagonal block is factored
         // inside the fused launch of the previous step
-        potrf_diag<T><<<1, 256, sizeof(PotrfSmem<T>), s>>>(L, np, 0, Linv, info);
+        potrf_first<<<1, 256, kStripSmem, s>>>(Lf, np, Linvf, info, lsT, strip_width(0));
         count_launch();
-        float* Lf = reinterpret_cast<float*>(L);
-        const float* Linvf = reinterpret_cast<const float*>(Linv);
-        int* status = info + 3;
+        cudaLaunchAttribute pdl[1];
+        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        pdl[0].val.programmaticStreamSerializationAllowed = 1;
         for (int k = 0; k + 1 < nblk; ++k) {
             const int k0 = k * NB;
             const int m = nblk - k - 1;   // row blocks below the diagonal
-            // strip of one or two column blocks, leaving an even number of
-            // blocks (whole 128-tiles) for the tensor cores
-            int sw = ((m - 1) & 1) ? 2 : 1;
-            int r0 = k0 + NB + NB * sw;
-            int kk = k, ld = np;
-            unsigned token = (unsigned)k + 1;
-            void* args[] = {&Lf, &ld, &kk, &Linvf, (void*)&nblk, &sw, &r0, &hi, &lo, &flags, &token, &status};
-            const int grid = std::min(m, resident);
+            const int sw = strip_width(k);
+            const int r0 = k0 + NB + NB * sw;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(m);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = kPanelSmem;
+            cfg.stream = s;
+            cfg.attrs = pdl;
+            cfg.numAttrs = 1;
             cudaEvent_t ev = trace_begin(s);
-            if ((e = cudaLaunchCooperativeKernel((const void*)panel_step, dim3(grid), dim3(256), args, kPanelSmem, s)) !=
-                cudaSuccess)
+            if ((e = cudaLaunchKernelEx(&cfg, panel_step, Lf, np, k, (const float*)Linvf, sw, r0, hi, lo,
+                                        (const float*)lsT)) != cudaSuccess)
                 return e;
             count_launch();
             {
@@ -590,9 +620,12 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                           (double)m * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB);
             }
             const long long nt = (np - r0) / tc::TM;
+            cfg.gridDim = dim3((unsigned)(1 + nt * (nt + 1) / 2));
+            cfg.dynamicSmemBytes = tc::SMEM_BYTES;
             ev = trace_begin(s);
-            step_fused<<<(unsigned)(1 + nt * (nt + 1) / 2), 256, tc::SMEM_BYTES, s>>>(
-                Lf, np, k0 + NB, reinterpret_cast<float*>(Linv), info, r0, hi, lo);
+            if ((e = cudaLaunchKernelEx(&cfg, step_fused, Lf, np, k0 + NB, Linvf, info, r0, (const unsigned char*)hi,
+                                        (const unsigned char*)lo, lsT, strip_width(k + 1))) != cudaSuccess)
+                return e;
             count_launch();
             {
                 // every lower 128-tile of [r0, np)^2 read and written once, the
@@ -664,7 +697,10 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
     return cholesky<double>(L, np, Linv, info, nullptr, s);
 }
 
-size_t cholesky_f32_split_bytes(int np) { return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 256; }
+size_t cholesky_f32_split_bytes(int np)
+{
+    return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 2 * NB * NB * sizeof(float);   // + strip rows
+}
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
                                 cudaStream_t s)

@@ -94,11 +94,12 @@ struct BatchView {
     const double *c = nullptr, *lo0 = nullptr, *hi0 = nullptr, *lo1 = nullptr, *hi1 = nullptr;
     const int8_t* axis = nullptr;
     const int32_t* cond = nullptr;
-    double* A64 = nullptr;
+    double* A64 = nullptr;            // float pairs (hi, lo) per entry: batches are mixed
     float* A32 = nullptr;
     float* Linv = nullptr;
     double *B = nullptr, *X = nullptr, *R = nullptr;
     float *W = nullptr, *Y = nullptr;
+    float2* Xdf = nullptr;            // X as float pairs for the compensated residual
     int* flags = nullptr;             // 4 per structure: [0] not SPD, [3] wait timeout
     double* C = nullptr;
     double* resid = nullptr;          // per structure: final relative residual
@@ -136,7 +137,8 @@ struct gbem_matrix_s {
     int np = 0;                 // padded order
     int nb = 64;                // factor block
     gbem_precision prec = GBEM_FP64;
-    double* A64 = nullptr;      // np x np col-major, lower triangle
+    double* A64 = nullptr;      // np x np col-major, lower triangle: FP64 entries, or in
+                                // mixed mode float pairs (hi, lo) with hi + lo the FP64 entry
     float* A32 = nullptr;       // mixed: FP32 copy, factored in place
     double* L64 = nullptr;      // FP64 mode: the factor
     void* Linv = nullptr;       // inverses of the diagonal blocks (T)
@@ -209,12 +211,17 @@ cudaError_t launch_ir_begin(const double* Bp, int np, int nrhs, double* X, doubl
                             int* flags, cudaStream_t s);
 cudaError_t launch_to_f32(const double* R, int np, int nrhs, float* W, const int* done,
                           cudaStream_t s);
-cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, const int* done,
+// X += W; with Xdf, also X as float pairs for launch_residual_df.
+cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, float2* Xdf, const int* done,
                            cudaStream_t s);
 cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, int nb, float* W,
                                     int nrhs, unsigned* sync, int* status, const int* done, cudaStream_t s);
 cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,
                             double* R, const int* done, cudaStream_t s);
+// R = B - A X with A and X stored as float pairs (mixed mode's FP64 storage),
+// in compensated FP32 arithmetic.
+cudaError_t launch_residual_df(const float2* A, int np, const double* Bp, const float2* Xdf, int nrhs,
+                               double* R, const int* done, cudaStream_t s);
 cudaError_t launch_ir_check(const double* R, const double* Bp, int np, int nrhs, double* norm,
                             double tol, int* flags, cudaStream_t s);
 cudaError_t launch_indicator_rhs(const int32_t* cond, int n, int np, int n_cond, double* Bp,

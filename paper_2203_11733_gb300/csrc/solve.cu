@@ -344,13 +344,24 @@ __global__ void to_f32(const double* __restrict__ R, size_t total, float* __rest
         W[e] = (float)R[e];
 }
 
+// X += W, and X as an unevaluated float pair (hi + lo) for the compensated
+// residual when Xdf is given.
+__device__ __forceinline__ float2 split_df(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 __global__ void add_f32(const float* __restrict__ W, size_t total, double* __restrict__ X,
-                        const int* done)
+                        float2* __restrict__ Xdf, const int* done)
 {
     if (*done) return;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x)
-        X[e] += (double)W[e];
+         e += (size_t)gridDim.x * blockDim.x) {
+        const double x = X[e] + (double)W[e];
+        X[e] = x;
+        if (Xdf) Xdf[e] = split_df(x);
+    }
 }
 
 // R = B - A X with A symmetric, only its lower triangle stored.  A CTA owns 16
@@ -428,6 +439,147 @@ __device__ __forceinline__ void residual_body(const double* __restrict__ A, int 
     }
 }
 
+// The same product with A and X stored as unevaluated float pairs
+// (a = a.x + a.y, |a.y| <= ulp(a.x) / 2) and compensated FP32 arithmetic
+// throughout (double-float: Dekker's product via FMA and Knuth's two-sum):
+//   a x = a.x x.x + e + (a.x x.y + a.y x.x),  e = fma(a.x, x.x, -a.x x.x) exact,
+// summed into (s, c) with s + p = s' + err exactly.  The dropped a.y x.y term
+// and the FP32 rounding of the tail sums leave a relative error of a few
+// 2^-48 per partial sum, far below the refinement tolerance.  The explicit
+// _rn intrinsics keep the compiler from contracting the exact steps.
+__device__ __forceinline__ void df_acc(float& s, float& c, float2 a, float2 x)
+{
+    const float p = __fmul_rn(a.x, x.x);
+    const float e = __fmaf_rn(a.x, x.x, -p);
+    const float t = __fmaf_rn(a.x, x.y, __fmul_rn(a.y, x.x));
+    const float sn = __fadd_rn(s, p);
+    const float bb = __fsub_rn(sn, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bb)), __fsub_rn(p, bb));
+    s = sn;
+    c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, t)));
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The 64-column blocks of A and X stream through a STAGES-deep cp.async
+// ring, so a CTA keeps several blocks of loads in flight while it computes.
+template <int RR>
+struct DfRes {
+    static constexpr int STAGES = RR <= 8 ? 3 : 2;
+    struct Ring {
+        float2 a[STAGES][RT][CT + 1];
+        float2 xs[STAGES][CT][RR + 1];
+    };
+    static constexpr size_t BYTES =
+        sizeof(Ring) > sizeof(double) * 8 * RT * RR ? sizeof(Ring) : sizeof(double) * 8 * RT * RR;
+};
+
+template <int RR>
+__device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, int np, const double* __restrict__ Bp,
+                                                 const float2* __restrict__ X, int nrhs, double* __restrict__ R,
+                                                 int blk)
+{
+    constexpr int S = DfRes<RR>::STAGES;
+    __shared__ __align__(16) unsigned char smem[DfRes<RR>::BYTES];
+    auto& ring = *reinterpret_cast<typename DfRes<RR>::Ring*>(smem);
+    auto part = reinterpret_cast<double(*)[RT][RR]>(smem);   // after the ring is drained
+    const int tid = threadIdx.x;
+    const int i0 = blk * RT;
+    const int ri = tid % RT, grp = tid / RT;  // 16 column groups
+    const int nblk = np / CT;
+    for (int c0 = 0; c0 < nrhs; c0 += RR) {
+        const int nr = min(RR, nrhs - c0);
+        __syncthreads();   // the previous pass is done reading its partial sums
+        for (int e = tid; e < S * CT * RR; e += blockDim.x) {   // unused columns read as zero
+            const int st = e / (CT * RR), r = (e / RR) % CT, c = e % RR;
+            if (c >= nr) ring.xs[st][r][c] = make_float2(0.0f, 0.0f);
+        }
+        auto issue = [&](int jb) {
+            const int st = jb % S, j0 = jb * CT;
+            if (j0 + CT <= i0) {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int r = e % RT, c = e / RT;
+                    cp_async8(&ring.a[st][r][c], A + (size_t)(i0 + r) + (size_t)(j0 + c) * np);
+                }
+            } else if (j0 >= i0 + RT) {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int c = e % CT, r = e / CT;
+                    cp_async8(&ring.a[st][r][c], A + (size_t)(j0 + c) + (size_t)(i0 + r) * np);
+                }
+            } else {
+                for (int e = tid; e < RT * CT; e += blockDim.x) {
+                    int r = e % RT, c = e / RT;
+                    int gi = i0 + r, gj = j0 + c;
+                    cp_async8(&ring.a[st][r][c], A + (size_t)max(gi, gj) + (size_t)min(gi, gj) * np);
+                }
+            }
+            for (int e = tid; e < CT * nr; e += blockDim.x) {
+                int r = e % CT, c = e / CT;
+                cp_async8(&ring.xs[st][r][c], X + (size_t)(j0 + r) + (size_t)(c0 + c) * np);
+            }
+        };
+        __syncthreads();   // zeros written
+#pragma unroll
+        for (int q = 0; q < S - 1; ++q) {
+            if (q < nblk) issue(q);
+            cp_async_commit();
+        }
+        float sh[RR], sl[RR];
+#pragma unroll
+        for (int c = 0; c < RR; ++c) sh[c] = sl[c] = 0.0f;
+        for (int jb = 0; jb < nblk; ++jb) {
+            if (jb + S - 1 < nblk) issue(jb + S - 1);
+            cp_async_commit();
+            cp_async_wait<S - 1>();   // block jb has landed (this thread's copies)
+            __syncthreads();          // ... and every thread's
+            const int st = jb % S;
+#pragma unroll
+            for (int q = 0; q < CT / 16; ++q) {
+                const int jj = grp + 16 * q;
+                const float2 av = ring.a[st][ri][jj];
+#pragma unroll
+                for (int c = 0; c < RR; ++c) df_acc(sh[c], sl[c], av, ring.xs[st][jj][c]);
+            }
+            __syncthreads();          // the stage is free for the copy issued next
+        }
+        cp_async_wait<0>();
+        double acc[RR];
+#pragma unroll
+        for (int c = 0; c < RR; ++c) {
+            acc[c] = (double)sh[c] + (double)sl[c];
+            acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+        }
+        __syncthreads();
+        if ((grp & 1) == 0)
+#pragma unroll
+            for (int c = 0; c < RR; ++c) part[grp >> 1][ri][c] = acc[c];
+        __syncthreads();
+        for (int e = tid; e < RT * nr; e += blockDim.x) {
+            int r = e % RT, c = e / RT;
+            double sum = 0.0;
+            for (int g = 0; g < 8; ++g) sum += part[g][r][c];
+            size_t idx = (size_t)(i0 + r) + (size_t)(c0 + c) * np;
+            R[idx] = Bp[idx] - sum;
+        }
+    }
+}
+
+template <int RR>
+__global__ void __launch_bounds__(256) residual_df(const float2* __restrict__ A, int np,
+                                                   const double* __restrict__ Bp, const float2* __restrict__ X,
+                                                   int nrhs, double* __restrict__ R, const int* done)
+{
+    if (done && *done) return;
+    residual_df_body<RR>(A, np, Bp, X, nrhs, R, blockIdx.x);
+}
+
 template <int RR>
 __global__ void __launch_bounds__(256) residual(const double* __restrict__ A, int np, const double* __restrict__ Bp,
                                                 const double* __restrict__ X, int nrhs, double* __restrict__ R,
@@ -439,36 +591,51 @@ __global__ void __launch_bounds__(256) residual(const double* __restrict__ A, in
 
 // max_k |R_k|_inf / |B_k|_inf -> norm[0]; converged -> flags[1] = 1, else
 // flags[2] += 1 (iterations taken).
-__global__ void ir_check(const double* __restrict__ R, const double* __restrict__ Bp, int np,
-                         int nrhs, double* norm, double tol, int* flags)
+__device__ __forceinline__ double block_max_1024(double v, double* red)
 {
-    __shared__ double red[256];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = red[threadIdx.x & 31];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+// One CTA of 1024 threads; each thread keeps eight loads in flight.
+__global__ void __launch_bounds__(1024) ir_check(const double* __restrict__ R, const double* __restrict__ Bp,
+                                                 int np, int nrhs, double* norm, double tol, int* flags)
+{
+    __shared__ double red[32];
     if (flags[1]) return;
     double worst = 0.0;
     for (int c = 0; c < nrhs; ++c) {
+        const double* Rc = R + (size_t)c * np;
+        const double* Bc = Bp + (size_t)c * np;
         double mr = 0.0, mb = 0.0;
-        for (int r = threadIdx.x; r < np; r += blockDim.x) {
-            mr = fmax(mr, fabs(R[(size_t)r + (size_t)c * np]));
-            mb = fmax(mb, fabs(Bp[(size_t)r + (size_t)c * np]));
+        int r = threadIdx.x;
+        for (; r + 3 * 1024 < np; r += 4 * 1024) {
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = Rc[r + q * 1024];
+                b[q] = Bc[r + q * 1024];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                mr = fmax(mr, fabs(a[q]));
+                mb = fmax(mb, fabs(b[q]));
+            }
         }
-        red[threadIdx.x] = mr;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-            __syncthreads();
+        for (; r < np; r += 1024) {
+            mr = fmax(mr, fabs(Rc[r]));
+            mb = fmax(mb, fabs(Bc[r]));
         }
-        mr = red[0];
-        __syncthreads();
-        red[threadIdx.x] = mb;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-            __syncthreads();
-        }
-        mb = red[0];
-        __syncthreads();
-        double rel = (mb > 0.0) ? mr / mb : mr;
-        worst = fmax(worst, rel);
+        mr = block_max_1024(mr, red);
+        mb = block_max_1024(mb, red);
+        worst = fmax(worst, (mb > 0.0) ? mr / mb : mr);
     }
     if (threadIdx.x == 0) {
         norm[0] = worst;
@@ -538,10 +705,14 @@ __global__ void batch_to_f32(const double* __restrict__ R, float* __restrict__ W
         W[e] = (float)R[e];
 }
 
-__global__ void batch_add(const float* __restrict__ W, double* __restrict__ X, size_t total)
+__global__ void batch_add(const float* __restrict__ W, double* __restrict__ X, float2* __restrict__ Xdf,
+                          size_t total)
 {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-        X[e] += (double)W[e];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const double x = X[e] + (double)W[e];
+        X[e] = x;
+        Xdf[e] = split_df(x);
+    }
 }
 
 // W := L^-T L^-1 W for one structure per CTA: the block sweeps of the
@@ -622,8 +793,8 @@ __global__ void __launch_bounds__(256) residual_batched(BatchView v)
     __syncthreads();
     const int b = sb;
     const long long o = v.voff[b];
-    residual_body<RR>(v.A64 + v.moff[b], v.np[b], v.B + o, v.X + o, v.nc[b], v.R + o,
-                      (int)(blockIdx.x - v.rows_prefix[b]));
+    residual_df_body<RR>(reinterpret_cast<const float2*>(v.A64) + v.moff[b], v.np[b], v.B + o, v.Xdf + o, v.nc[b],
+                         v.R + o, (int)(blockIdx.x - v.rows_prefix[b]));
 }
 
 // Final relative residual and capacitance of each structure (one CTA each).
@@ -714,11 +885,11 @@ cudaError_t launch_to_f32(const double* R, int np, int nrhs, float* W, const int
     return cudaGetLastError();
 }
 
-cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, const int* done,
+cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, float2* Xdf, const int* done,
                            cudaStream_t s)
 {
     size_t total = (size_t)np * nrhs;
-    add_f32<<<grid_for(total), 256, 0, s>>>(W, total, X, done);
+    add_f32<<<grid_for(total), 256, 0, s>>>(W, total, X, Xdf, done);
     count_launch();
     return cudaGetLastError();
 }
@@ -745,10 +916,32 @@ cudaError_t launch_residual(const double* A, int np, const double* Bp, const dou
     return cudaGetLastError();
 }
 
+cudaError_t launch_residual_df(const float2* A, int np, const double* Bp, const float2* Xdf, int nrhs,
+                               double* R, const int* done, cudaStream_t s)
+{
+    if (np % CT) return cudaErrorInvalidValue;
+    for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
+        const int nr = std::min(MAXR, nrhs - c0);
+        const double* Bc = Bp + (size_t)c0 * np;
+        const float2* Xc = Xdf + (size_t)c0 * np;
+        double* Rc = R + (size_t)c0 * np;
+        cudaEvent_t ev = trace_begin(s);
+        if (nr <= 4) residual_df<4><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        else if (nr <= 8) residual_df<8><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        else residual_df<16><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        count_launch();
+        // the lower triangle of A (float pairs) once, B and X read and R
+        // written; each lower entry serves two products per right-hand side
+        trace_end(GBEM_KERNEL_RESIDUAL, ev, s, 8.0 * ((double)np * (np + CT) / 2 + 3.0 * np * nr),
+                  2.0 * (double)np * np * nr);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ir_check(const double* R, const double* Bp, int np, int nrhs, double* norm,
                             double tol, int* flags, cudaStream_t s)
 {
-    ir_check<<<1, 256, 0, s>>>(R, Bp, np, nrhs, norm, tol, flags);
+    ir_check<<<1, 1024, 0, s>>>(R, Bp, np, nrhs, norm, tol, flags);
     count_launch();
     return cudaGetLastError();
 }
@@ -786,7 +979,7 @@ cudaError_t launch_batch_iteration(const BatchView& v, size_t vec_total, long lo
     else if (max_nc <= 8) trsv_batched<8><<<v.nb, 256, 0, s>>>(v);
     else trsv_batched<16><<<v.nb, 256, 0, s>>>(v);
     count_launch();
-    batch_add<<<g, 256, 0, s>>>(v.W, v.X, vec_total);
+    batch_add<<<g, 256, 0, s>>>(v.W, v.X, v.Xdf, vec_total);
     count_launch();
     if (max_nc <= 4) residual_batched<4><<<(unsigned)row_blocks, 256, 0, s>>>(v);
     else if (max_nc <= 8) residual_batched<8><<<(unsigned)row_blocks, 256, 0, s>>>(v);

@@ -109,7 +109,8 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
             return fail(e, "trsv");
         if ((e = launch_unpack(Wd, npi, n, nrhs, X_dev, ldx, s)) != cudaSuccess) return fail(e, "unpack");
     } else {
-        float* Wf = static_cast<float*>(W);
+        float* Wf = static_cast<float*>(W);                       // W and its work half: the first vec
+        float2* Xdf = reinterpret_cast<float2*>(base + 4 * vec);  // X as float pairs: the second vec
         const int* done = flags + 1;
         if ((e = launch_ir_begin(Bp, npi, nrhs, X, R, norm, flags, s)) != cudaSuccess) return fail(e, "ir begin");
         int host_flags[3] = {0, 0, 0};
@@ -118,8 +119,9 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
             if ((e = launch_to_f32(R, npi, nrhs, Wf, done, s)) != cudaSuccess ||
                 (e = launch_trsv_f32_guarded(m->A32, static_cast<const float*>(m->Linv), npi, m->nb, Wf, nrhs,
                                              sync, flags + 3, done, s)) != cudaSuccess ||
-                (e = launch_add_f32(Wf, npi, nrhs, X, done, s)) != cudaSuccess ||
-                (e = launch_residual(m->A64, npi, Bp, X, nrhs, R, done, s)) != cudaSuccess ||
+                (e = launch_add_f32(Wf, npi, nrhs, X, Xdf, done, s)) != cudaSuccess ||
+                (e = launch_residual_df(reinterpret_cast<const float2*>(m->A64), npi, Bp, Xdf, nrhs, R, done, s)) !=
+                    cudaSuccess ||
                 (e = launch_ir_check(R, Bp, npi, nrhs, norm, ctx->tune.ir_tol, flags, s)) != cudaSuccess)
                 return fail(e, "refinement");
             if ((e = cudaMemcpyAsync(host_flags, flags, sizeof(host_flags), cudaMemcpyDeviceToHost, s)) !=
