@@ -356,10 +356,10 @@ PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
 
 KERNEL_NAMES = {
     "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
-    "panel": "panel_step: panel products, strip update and hi/lo split (cooperative)",
-    "update": "step_fused: diagonal factor+inverse in CTA 0, tcgen05 3xTF32 trailing update in the rest",
+    "factor": "factor_step: one launch per elimination step (panel rows, strip update, next diagonal "
+              "block factor+inverse, tcgen05 3xTF32 trailing tiles)",
     "sweep": "trsv_fwd/trsv_bwd: persistent cooperative triangular sweeps",
-    "residual": "residual: FP64 R = B - A X over the lower triangle",
+    "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
 }
 FP64_PEAK_TF = 1.25   # nominal GB300 FP64 (non-tensor) rate
 

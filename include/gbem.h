@@ -236,11 +236,11 @@ gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset);
  * launch, so time the workload itself with level 1 or 0. */
 enum {
     GBEM_KERNEL_ASSEMBLE = 0,  /* one CTA per 32 x 32 tile: Galerkin entries */
-    GBEM_KERNEL_PANEL = 1,     /* FP32 factor: panel products, strip update, hi/lo split */
-    GBEM_KERNEL_UPDATE = 2,    /* FP32 factor: diagonal block + tensor-core trailing update */
-    GBEM_KERNEL_SWEEP = 3,     /* persistent forward/backward triangular sweeps */
-    GBEM_KERNEL_RESIDUAL = 4,  /* FP64 residual R = B - A X */
-    GBEM_NKERNEL = 5
+    GBEM_KERNEL_FACTOR = 1,    /* FP32 factor, one launch per elimination step: panel,
+                                  strip update, next diagonal block, tensor-core tiles */
+    GBEM_KERNEL_SWEEP = 2,     /* persistent forward/backward triangular sweeps */
+    GBEM_KERNEL_RESIDUAL = 3,  /* residual R = B - A X (FP64, or compensated FP32 in mixed mode) */
+    GBEM_NKERNEL = 4
 };
 typedef struct {
     double ms[GBEM_NKERNEL];

@@ -12,13 +12,12 @@
 //   3. syrk_update: A_ij -= L_ik L_jk^T on the lower tiles of the trailing
 //                   matrix.
 // FP32 storage (mixed mode, whose FP64 refinement restores the solution's
-// accuracy), two launches per block column k:
-//   1. panel_step:  L_ik for every block below, the update of the next one or
-//                   two block columns (the strip), and the TF32 hi/lo split
-//                   of the panel;
-//   2. step_fused:  CTA 0 factors and inverts diagonal block k+1 while the
-//                   other CTAs apply the panel to the rest of the trailing
-//                   matrix on the tensor cores (tc_syrk.cuh).
+// accuracy): one launch per block column k (factor_step), whose CTAs take,
+// in the order they start, the panel work of every row block below the
+// diagonal (products, strip update of the next one or two block columns,
+// TF32 hi/lo split), the factorisation and inverse of diagonal block k+1, and
+// the tensor-core update of the remaining trailing tiles (tc_syrk.cuh); each
+// waits on release flags for exactly the panel rows it needs.
 // A non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
 // factorisation completes without NaNs; the host reports GBEM_ERR_NOT_SPD.
 #include <algorithm>
@@ -71,6 +70,18 @@ __device__ __forceinline__ void load4(const float* p, float v[4])
 __device__ __forceinline__ void load4(const double* p, double v[4])
 {
     const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+// Global memory only, through L2: the block may have been written by another
+// CTA of the same launch.
+__device__ __forceinline__ void load4_l2(const float* p, float v[4])
+{
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void load4_l2(const double* p, double v[4])
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
 }
 __device__ __forceinline__ void store4(float* p, float a, float b, float c, float d)
@@ -142,7 +153,7 @@ __device__ __forceinline__ void potrf_work(T* __restrict__ L, int ld, int k0, T*
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         T col[4] = {T(0), T(0), T(0), T(0)};
-        if (act) load4(L + (size_t)(k0 + r0) + (size_t)(k0 + c0 + v) * ld, col);
+        if (act) load4_l2(L + (size_t)(k0 + r0) + (size_t)(k0 + c0 + v) * ld, col);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             z[u][v] = col[u];
@@ -294,7 +305,7 @@ __device__ void strip_rows(const float* __restrict__ L, int ld, int k0, const fl
         for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
             const int t = e >> 4, r = (e & 15) * 4;
             *reinterpret_cast<float4*>(&aT[t][r]) =
-                *reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld);
+                __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld));
         }
         __syncthreads();
         float acc[4][4] = {};
@@ -424,32 +435,65 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-// Panel step k of the FP32 factorisation, one CTA per row block
-// i = k + 1 + blockIdx.x below diagonal block k:
+constexpr long long kFlagSpinLimit = 1LL << 24;   // ~1 s of polling
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until every flag in f[0..n) has reached `token` (bounded);
+// the CTA then proceeds together.  False (and status = GBEM_ERR_TIMEOUT) if
+// a wait gave up or another CTA's already had.
+__device__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        for (int q = 0; q < n && ok; ++q) {
+            long long spins = 0;
+            while (ld_acquire(f + q) < token) {
+                if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
+                    atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Panel work of row block i at step k (one CTA):
 //   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
 //      so the sum over t stops at the output column);
 //   2. row blocks at or below r0 write the TF32 hi/lo split of L_ik in the
 //      tensor-core operand layout;
 //   3. A_ic -= L_ik L_ck^T for the sw strip blocks c = k+1 .. k+sw, c <= i,
 //      with L_ck (lsT, t-major) computed by the CTA that factored block k.
-// The strip targets are read at the start, so their latency overlaps the
-// panel product.
-__global__ void __launch_bounds__(256) panel_step(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv,
-                                                  int sw, int r0, unsigned char* __restrict__ hi,
-                                                  unsigned char* __restrict__ lo, const float* __restrict__ lsT)
+// The strip targets are read first, so their latency overlaps the product.
+__device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int r0,
+                          unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
+                          const float* __restrict__ lsT, int i, unsigned char* smem)
 {
-    pdl_wait();
-    pdl_trigger();
     // Blocks are stored t-major (rows padded to 68 floats) so that a
     // thread's four rows or columns at one t are one 16-byte load.
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
-    float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_ik, then L_ik
-    float(*lcT)[PT] = aT + NB;                                    // lcT[s * 64 + t][c] = L_ck[c][t]
+    float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem);   // ivT[t][c] = Linv_kk[c][t]
+    float(*aT)[PT] = ivT + NB;                                // aT[t][r] = A_ik, then L_ik
+    float(*lcT)[PT] = aT + NB;                                // lcT[s * 64 + t][c] = L_ck[c][t]
     const int tid = threadIdx.x;
     const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
-    const int k0 = k * NB;
-    const int i = k + 1 + blockIdx.x, rI = i * NB;
+    const int k0 = k * NB, rI = i * NB;
     const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
     float4 tgt[2][4];
 #pragma unroll
@@ -528,33 +572,65 @@ __global__ void __launch_bounds__(256) panel_step(float* __restrict__ L, int ld,
     }
 }
 
-constexpr size_t kPanelSmem = 4 * NB * PT * sizeof(float);
-
-// One launch of the FP32 factorisation step: CTA 0 factors the next
-// diagonal block (k0n, already brought up to date by the panel kernel) and
-// computes the ns strip rows of the next panel step, while the other CTAs
-// apply the current panel to the tensor-core region [r0, np)^2, which touches
-// neither.  The diagonal factorisation is thereby hidden behind the trailing
-// update.
-__global__ void __launch_bounds__(256) step_fused(float* __restrict__ L, int ld, int k0n, float* __restrict__ Linv,
-                                                  int* __restrict__ info, int r0, const unsigned char* __restrict__ hi,
-                                                  const unsigned char* __restrict__ lo, float* __restrict__ lsT, int ns)
+// Elimination step k of the FP32 factorisation in one launch.  Every CTA
+// draws a ticket in the order the CTAs start (an atomic counter per step), and
+// the ticket gives its role:
+//   tickets 0 .. m-1   panel work of row block k + 1 + ticket (panel_row),
+//                      then a release flag pflag[i] = k + 1;
+//   ticket  m          after the flags of row blocks k+1 .. k+1+ns: factor
+//                      and invert diagonal block k+1 and compute the ns strip
+//                      rows of step k+1 (into lsT_out);
+//   tickets > m        one 128 x 128 lower tile of [r0, np)^2 each, after the
+//                      flags of its four row blocks: 3xTF32 tensor-core update
+//                      with the split panel (tc_syrk.cuh).
+// A CTA only waits for CTAs holding smaller tickets, which have started and
+// wait for nothing later, so the launch cannot deadlock however many CTAs
+// are resident.  Waits are bounded; one that gives up sets status
+// GBEM_ERR_TIMEOUT and its CTA skips its work.
+__global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
+                                                   int* __restrict__ info, int nblk, int sw, int r0,
+                                                   unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
+                                                   const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
+                                                   int ns_next, unsigned* __restrict__ pflag,
+                                                   unsigned* __restrict__ tickets)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ int s_ticket;
     pdl_wait();
     pdl_trigger();
-    if (blockIdx.x == 0) {
-        potrf_body<float>(L, ld, k0n, Linv, info);
-        if (ns > 0) strip_rows(L, ld, k0n, Linv, lsT, ns);
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(tickets + k, 1u);
+    __syncthreads();
+    const int t = s_ticket;
+    const int m = nblk - k - 1;
+    const unsigned token = (unsigned)k + 1;
+    int* status = info + 3;
+    if (t < m) {
+        const int i = k + 1 + t;
+        panel_row(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, tc_smem);
+        __syncthreads();   // the whole row block is stored
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
+            __threadfence();
+            st_release(pflag + i, token);
+        }
         return;
     }
-    long long b = blockIdx.x - 1;
+    if (t == m) {
+        // diagonal block k+1 and the strip rows k+2 .. k+1+ns_next of column k+1
+        if (!wait_flags(pflag + k + 1, 1 + ns_next, token, status)) return;
+        potrf_body<float>(L, ld, (k + 1) * NB, Linv, info);
+        if (ns_next > 0) strip_rows(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next);
+        return;
+    }
+    const long long b = t - m - 1;
     int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
     const int J = (int)(b - (long long)I * (I + 1) / 2);
+    const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
+    if (!wait_flags(pflag + bI, 2, token, status) || !wait_flags(pflag + bJ, 2, token, status)) return;
     if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem) && threadIdx.x == 0)
-        atomicCAS(info + 3, 0, (int)GBEM_ERR_TIMEOUT);
+        atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
 }
 
 template <typename T>
@@ -568,73 +644,70 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                                   (int)sizeof(PotrfSmem<T>))) != cudaSuccess)
         return e;
     if constexpr (kTensor) {
-        if ((e = cudaFuncSetAttribute(step_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(panel_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem)) !=
+        if ((e = cudaFuncSetAttribute(factor_step, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(potrf_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
                 cudaSuccess)
             return e;
+        // work space: hi and lo panel copies, two strip-row buffers, panel
+        // flags and per-step tickets (cholesky_f32_split_bytes)
+        const size_t oper = (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
         unsigned char* hi = split;
-        unsigned char* lo = split + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
-        float* lsT = reinterpret_cast<float*>(lo + (size_t)(np / tc::TM + 1) * tc::OPER_BYTES);
+        unsigned char* lo = split + oper;
+        float* lsT = reinterpret_cast<float*>(split + 2 * oper);   // 2 x (2 x 64 x 64)
+        unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
+        unsigned* tickets = pflag + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        // strip width of panel step k: one or two column blocks, leaving an
-        // even number of blocks (whole 128-tiles) for the tensor cores
+        if ((e = cudaMemsetAsync(pflag, 0, 2 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        // strip width of step k: one or two column blocks, leaving an even
+        // number of blocks (whole 128-tiles) for the tensor cores
         auto strip_width = [nblk](int k) {
             const int m = nblk - k - 1;
             return m <= 0 ? 0 : (((m - 1) & 1) ? 2 : 1);
         };
         // block 0 is factored alone; every later diagonal block is factored
-        // inside the fused launch of the previous step
+        // inside the launch of the previous step
         potrf_first<<<1, 256, kStripSmem, s>>>(Lf, np, Linvf, info, lsT, strip_width(0));
         count_launch();
         cudaLaunchAttribute pdl[1];
         pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         pdl[0].val.programmaticStreamSerializationAllowed = 1;
         for (int k = 0; k + 1 < nblk; ++k) {
-            const int k0 = k * NB;
             const int m = nblk - k - 1;   // row blocks below the diagonal
             const int sw = strip_width(k);
-            const int r0 = k0 + NB + NB * sw;
+            const int r0 = (k + 1 + sw) * NB;
+            const long long nt = (np - r0) / tc::TM;
+            const long long tiles = nt * (nt + 1) / 2;
+            float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
+            float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(m);
+            cfg.gridDim = dim3((unsigned)(m + 1 + tiles));
             cfg.blockDim = dim3(256);
-            cfg.dynamicSmemBytes = kPanelSmem;
+            cfg.dynamicSmemBytes = tc::SMEM_BYTES;
             cfg.stream = s;
             cfg.attrs = pdl;
             cfg.numAttrs = 1;
             cudaEvent_t ev = trace_begin(s);
-            if ((e = cudaLaunchKernelEx(&cfg, panel_step, Lf, np, k, (const float*)Linvf, sw, r0, hi, lo,
-                                        (const float*)lsT)) != cudaSuccess)
+            if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
+                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets)) !=
+                cudaSuccess)
                 return e;
             count_launch();
             {
-                // per row block: A_ik read, L_ik written, its hi/lo split
-                // written (below r0), the strip blocks read and written
-                const double blk = 4.0 * NB * NB;
+                // algorithmic bytes: per row block A_ik read, L_ik and its
+                // hi/lo split written, strip blocks read and written; every
+                // lower 128-tile of [r0, np)^2 read and written once and the
+                // split panel read once; the diagonal block read, its factor
+                // and inverse written.  Useful flops: panel products, strip
+                // and tile updates, diagonal factor and inverse.
+                const double blk = 4.0 * NB * NB, tb = 4.0 * tc::TM * tc::TM;
                 const double strips = (double)m * sw - (sw - 1);
-                const double split_rows = (double)(np - r0);
-                trace_end(GBEM_KERNEL_PANEL, ev, s, 2.0 * m * blk + blk + 8.0 * split_rows * NB + 2.0 * strips * blk,
-                          (double)m * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB);
-            }
-            const long long nt = (np - r0) / tc::TM;
-            cfg.gridDim = dim3((unsigned)(1 + nt * (nt + 1) / 2));
-            cfg.dynamicSmemBytes = tc::SMEM_BYTES;
-            ev = trace_begin(s);
-            if ((e = cudaLaunchKernelEx(&cfg, step_fused, Lf, np, k0 + NB, Linvf, info, r0, (const unsigned char*)hi,
-                                        (const unsigned char*)lo, lsT, strip_width(k + 1))) != cudaSuccess)
-                return e;
-            count_launch();
-            {
-                // every lower 128-tile of [r0, np)^2 read and written once, the
-                // hi/lo panel read once; the diagonal block read, its factor
-                // and inverse written
-                const double tiles = (double)nt * (nt + 1) / 2;
-                const double tb = 4.0 * tc::TM * tc::TM;
-                trace_end(GBEM_KERNEL_UPDATE, ev, s, 2.0 * tiles * tb + 8.0 * (np - r0) * NB + 3.0 * 4.0 * NB * NB,
-                          tiles * 2.0 * tc::TM * tc::TM * tc::TK + 2.0 * NB * NB * NB / 3.0);
+                const double bytes = 2.0 * m * blk + 8.0 * (np - r0) * NB + 2.0 * strips * blk +
+                                     2.0 * tiles * tb + 8.0 * (np - r0) * NB + 3.0 * blk;
+                const double flops = (double)m * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
+                                     (double)tiles * 2.0 * tc::TM * tc::TM * tc::TK + 2.0 * NB * NB * NB / 3.0;
+                trace_end(GBEM_KERNEL_FACTOR, ev, s, bytes, flops);
             }
         }
         return cudaGetLastError();
@@ -699,7 +772,9 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 2 * NB * NB * sizeof(float);   // + strip rows
+    // hi/lo panel copies, two strip-row buffers, panel flags and step tickets
+    return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
+           2 * (size_t)(np / NB) * sizeof(unsigned);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,

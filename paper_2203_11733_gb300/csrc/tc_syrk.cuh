@@ -23,8 +23,10 @@
 //      one pair);
 //   3. after the bounded wait, one thread issues 8 K-steps x 3 tcgen05.mma
 //      (M = N = 128, K = 8) and commits them to a second mbarrier;
-//   4. every warp waits (bounded), reads 32 accumulator lanes x 64 columns
-//      with tcgen05.ld and subtracts them from C in global memory;
+//   4. every thread loads its 64 entries of C into registers before the
+//      waits, so their latency overlaps the copies and the MMAs; after the
+//      bounded wait every warp reads 32 accumulator lanes x 64 columns with
+//      tcgen05.ld and stores C minus the product;
 //   5. warp 0 frees the TMEM columns.
 #pragma once
 
@@ -169,6 +171,9 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         const uint32_t parts = (I == J) ? 2 : 4;
+        // the split may have been written by other CTAs of this launch
+        // (generic-proxy stores): order them before the async-proxy copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         mbar_expect_tx(bar_ld, parts * OPER_BYTES);
         bulk_g2s(smem_u32(a_hi), hi + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
         bulk_g2s(smem_u32(a_lo), lo + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
@@ -181,6 +186,14 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    // this thread's 64 entries of C (row q * 32 + lane, columns 64 half ..),
+    // loaded now so that their latency overlaps the operand copies and MMAs
+    const int q = warp & 3, half = warp >> 2;
+    const int row = q * 32 + (tid & 31);
+    float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
+    float cpre[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
 
     bool ok = true;
     if (tid == 0) {
@@ -207,17 +220,12 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
-        const int q = warp & 3, half = warp >> 2;
-        const int row = q * 32 + (tid & 31);
-        float* crow = L + (size_t)(rI + row);
-#pragma unroll 1
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
-            float v[16], c[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) c[i] = crow[(size_t)(rJ + c0 + i) * ld];
+        for (int cc = 0; cc < 64; cc += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64 + cc), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) crow[(size_t)(rJ + c0 + i) * ld] = c[i] - v[i];
+            for (int i = 0; i < 16; ++i) crow[(size_t)(cc + i) * ld] = cpre[cc + i] - v[i];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -123,14 +123,14 @@ class Stats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 5), ("calls", ctypes.c_longlong * 5), ("launches", ctypes.c_longlong)]
 
 
-KERNELS = ["assemble", "panel", "update", "sweep", "residual"]
+KERNELS = ["assemble", "factor", "sweep", "residual"]
 
 
 class KernelStats(ctypes.Structure):
     """gbem_kernel_stats: per traced kernel, device time, launches and the
     algorithmic bytes and flops of those launches."""
-    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_longlong * 5),
-                ("bytes", ctypes.c_double * 5), ("flops", ctypes.c_double * 5)]
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_longlong * 4),
+                ("bytes", ctypes.c_double * 4), ("flops", ctypes.c_double * 4)]
 
 
 def set_timing(ctx, level: int):
