@@ -281,6 +281,45 @@ __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T*
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+constexpr long long kFlagSpinLimit = 1LL << 24;   // ~1 s of polling
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until every flag in f[0..n) has reached `token` (bounded);
+// the CTA then proceeds together.  False (and status = GBEM_ERR_TIMEOUT) if
+// a wait gave up or another CTA's already had.
+__device__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        for (int q = 0; q < n && ok; ++q) {
+            long long spins = 0;
+            while (ld_acquire(f + q) < token) {
+                if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
+                    atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 constexpr int PT = NB + 4;   // padded row of a t-major 64 x 64 block in shared memory
 
 // L_ck = A_ck Linv_kk^T for the ns row blocks c = k+1 .. k+ns below diagonal
@@ -319,22 +358,79 @@ __device__ void strip_rows(const float* __restrict__ L, int ld, int k0, const fl
                 for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
         }
         float* dst = lsT + (size_t)sidx * NB * NB;
+        float(*lT)[PT] = aT + NB;   // the first strip row stays in shared memory
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-            *reinterpret_cast<float4*>(dst + (size_t)(tc + v) * NB + tr) =
-                make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+        for (int v = 0; v < 4; ++v) {
+            const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+            *reinterpret_cast<float4*>(dst + (size_t)(tc + v) * NB + tr) = q;
+            if (sidx == 0) *reinterpret_cast<float4*>(&lT[tc + v][tr]) = q;
+        }
     }
 }
 
-constexpr size_t kStripSmem = 2 * NB * PT * sizeof(float);
+// Lookahead: the panel work of row block c = k+1 (k0 = 64 k, the block just
+// factored) for elimination step k, done by the CTA that factored block k
+// right after strip_rows, so that the next diagonal block is ready when step
+// k's launch starts:
+//   L_ck (the first strip row, in shared memory) is written to L, and
+//   A_cc -= L_ck L_ck^T, once A_cc has every earlier panel applied (after
+//   `ready`, when given: the tile that applies the previous panel to it);
+// then pflag_c = token.
+__device__ void lookahead_row(float* __restrict__ L, int ld, int k0, const unsigned* ready, unsigned* pflag_c,
+                              unsigned token, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*lT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw) + 2 * NB;   // lT[t][r] = L_ck[r][t]
+    const int tid = threadIdx.x;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const int rc = k0 + NB;
+    __syncthreads();   // lT complete
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+        const int t = e >> 4, r = (e & 15) * 4;
+        *reinterpret_cast<float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld) =
+            *reinterpret_cast<const float4*>(&lT[t][r]);
+    }
+    if (ready && !wait_flags(ready, 1, 1u, status)) return;
+    float acc[4][4] = {};
+    for (int t = 0; t < NB; ++t) {
+        const float4 x = *reinterpret_cast<const float4*>(&lT[t][tr]);
+        const float4 y = *reinterpret_cast<const float4*>(&lT[t][tc]);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        float4* p = reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld);
+        float4 o = __ldcg(p);
+        o.x -= acc[0][v];
+        o.y -= acc[1][v];
+        o.z -= acc[2][v];
+        o.w -= acc[3][v];
+        *p = o;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        st_release(pflag_c, token);
+    }
+}
 
-// The first diagonal block of the FP32 factorisation and the strip rows of
-// panel step 0.
+constexpr size_t kStripSmem = 3 * NB * PT * sizeof(float);
+
+// The first diagonal block of the FP32 factorisation, the strip rows of step
+// 0 and the lookahead panel work of row block 1.
 __global__ void __launch_bounds__(256) potrf_first(float* __restrict__ L, int ld, float* __restrict__ Linv,
-                                                   int* __restrict__ info, float* __restrict__ lsT, int ns)
+                                                   int* __restrict__ info, float* __restrict__ lsT, int ns,
+                                                   unsigned* __restrict__ pflag)
 {
     potrf_body<float>(L, ld, 0, Linv, info);
-    if (ns > 0) strip_rows(L, ld, 0, Linv, lsT, ns);
+    if (ns > 0) {
+        strip_rows(L, ld, 0, Linv, lsT, ns);
+        lookahead_row(L, ld, 0, nullptr, pflag + 1, 1u, info + 3);
+    }
 }
 
 template <typename T>
@@ -435,45 +531,6 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-constexpr long long kFlagSpinLimit = 1LL << 24;   // ~1 s of polling
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Thread 0 waits until every flag in f[0..n) has reached `token` (bounded);
-// the CTA then proceeds together.  False (and status = GBEM_ERR_TIMEOUT) if
-// a wait gave up or another CTA's already had.
-__device__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
-{
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        for (int q = 0; q < n && ok; ++q) {
-            long long spins = 0;
-            while (ld_acquire(f + q) < token) {
-                if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
-                    atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(20);
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Panel work of row block i at step k (one CTA):
 //   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
 //      so the sum over t stops at the output column);
@@ -572,27 +629,34 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
     }
 }
 
-// Elimination step k of the FP32 factorisation in one launch.  Every CTA
-// draws a ticket in the order the CTAs start (an atomic counter per step), and
-// the ticket gives its role:
-//   tickets 0 .. m-1   panel work of row block k + 1 + ticket (panel_row),
+// Elimination step k of the FP32 factorisation in one launch.  Row block
+// k+1 was already done by the previous launch (lookahead).  Every CTA draws a
+// ticket in the order the CTAs start (an atomic counter per step), and the
+// ticket gives its role (m = row blocks below diagonal block k):
+//   tickets 0 .. m-2   panel work of row block k + 2 + ticket (panel_row),
 //                      then a release flag pflag[i] = k + 1;
-//   ticket  m          after the flags of row blocks k+1 .. k+1+ns: factor
-//                      and invert diagonal block k+1 and compute the ns strip
-//                      rows of step k+1 (into lsT_out);
-//   tickets > m        one 128 x 128 lower tile of [r0, np)^2 each, after the
+//   ticket  m-1        factor and invert diagonal block k+1; after the flags
+//                      of row blocks k+2 .. k+1+ns, the ns strip rows of
+//                      step k+1 (into lsT_out) and the lookahead panel work of
+//                      row block k+2 for step k+1 (pflag[k+2] = k + 2), after
+//                      tile (0, 0) when that tile holds block (k+2, k+2);
+//   tickets >= m       one 128 x 128 lower tile of [r0, np)^2 each, after the
 //                      flags of its four row blocks: 3xTF32 tensor-core update
-//                      with the split panel (tc_syrk.cuh).
-// A CTA only waits for CTAs holding smaller tickets, which have started and
-// wait for nothing later, so the launch cannot deadlock however many CTAs
-// are resident.  Waits are bounded; one that gives up sets status
-// GBEM_ERR_TIMEOUT and its CTA skips its work.
+//                      with the split panel (tc_syrk.cuh); tile (0, 0) then
+//                      sets tdone[k].
+// Panel CTAs wait for nothing; tiles wait for panel tickets (smaller, so
+// already started); the diagonal CTA waits for panel tickets and for tile
+// (0, 0), the very next ticket: until that CTA starts, every started CTA
+// besides the diagonal one is a panel CTA, which finishes and frees its SM.
+// So the launch cannot deadlock however many CTAs are resident.  Waits are
+// bounded; one that gives up sets status GBEM_ERR_TIMEOUT and its CTA skips
+// its work.
 __global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
                                                    int* __restrict__ info, int nblk, int sw, int r0,
                                                    unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
-                                                   unsigned* __restrict__ tickets)
+                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ tdone)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -601,11 +665,11 @@ __global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld
     if (threadIdx.x == 0) s_ticket = (int)atomicAdd(tickets + k, 1u);
     __syncthreads();
     const int t = s_ticket;
-    const int m = nblk - k - 1;
+    const int npanel = nblk - k - 2;
     const unsigned token = (unsigned)k + 1;
     int* status = info + 3;
-    if (t < m) {
-        const int i = k + 1 + t;
+    if (t < npanel) {
+        const int i = k + 2 + t;
         panel_row(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, tc_smem);
         __syncthreads();   // the whole row block is stored
         if (threadIdx.x == 0) {
@@ -615,22 +679,34 @@ __global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld
         }
         return;
     }
-    if (t == m) {
-        // diagonal block k+1 and the strip rows k+2 .. k+1+ns_next of column k+1
-        if (!wait_flags(pflag + k + 1, 1 + ns_next, token, status)) return;
+    if (t == npanel) {
+        if (!wait_flags(pflag + k + 1, 1, token, status)) return;
         potrf_body<float>(L, ld, (k + 1) * NB, Linv, info);
-        if (ns_next > 0) strip_rows(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next);
+        if (ns_next > 0) {
+            if (!wait_flags(pflag + k + 2, ns_next, token, status)) return;
+            strip_rows(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next);
+            lookahead_row(L, ld, (k + 1) * NB, sw == 1 ? tdone + k : nullptr, pflag + k + 2, token + 1, status);
+        }
         return;
     }
-    const long long b = t - m - 1;
+    const long long b = t - npanel - 1;
     int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
     const int J = (int)(b - (long long)I * (I + 1) / 2);
     const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
     if (!wait_flags(pflag + bI, 2, token, status) || !wait_flags(pflag + bJ, 2, token, status)) return;
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem) && threadIdx.x == 0)
-        atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem)) {
+        if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+        return;
+    }
+    if (b == 0) {
+        __syncthreads();   // the whole tile is stored
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(tdone + k, 1u);
+        }
+    }
 }
 
 template <typename T>
@@ -657,9 +733,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         float* lsT = reinterpret_cast<float*>(split + 2 * oper);   // 2 x (2 x 64 x 64)
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
         unsigned* tickets = pflag + nblk;
+        unsigned* tdone = tickets + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        if ((e = cudaMemsetAsync(pflag, 0, 2 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pflag, 0, 3 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
         // strip width of step k: one or two column blocks, leaving an even
         // number of blocks (whole 128-tiles) for the tensor cores
         auto strip_width = [nblk](int k) {
@@ -668,7 +745,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         };
         // block 0 is factored alone; every later diagonal block is factored
         // inside the launch of the previous step
-        potrf_first<<<1, 256, kStripSmem, s>>>(Lf, np, Linvf, info, lsT, strip_width(0));
+        potrf_first<<<1, 256, kStripSmem, s>>>(Lf, np, Linvf, info, lsT, strip_width(0), pflag);
         count_launch();
         cudaLaunchAttribute pdl[1];
         pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -682,7 +759,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
             float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)(m + 1 + tiles));
+            cfg.gridDim = dim3((unsigned)(m + tiles));   // m - 1 panel rows, the diagonal CTA, the tiles
             cfg.blockDim = dim3(256);
             cfg.dynamicSmemBytes = tc::SMEM_BYTES;
             cfg.stream = s;
@@ -690,7 +767,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cfg.numAttrs = 1;
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
-                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets)) !=
+                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets, tdone)) !=
                 cudaSuccess)
                 return e;
             count_launch();
@@ -772,9 +849,10 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    // hi/lo panel copies, two strip-row buffers, panel flags and step tickets
+    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets and
+    // first-tile flags
     return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
-           2 * (size_t)(np / NB) * sizeof(unsigned);
+           3 * (size_t)(np / NB) * sizeof(unsigned);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
