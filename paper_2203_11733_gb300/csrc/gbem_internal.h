@@ -214,6 +214,9 @@ cudaError_t launch_to_f32(const double* R, int np, int nrhs, float* W, const int
 // X += W; with Xdf, also X as float pairs for launch_residual_df.
 cudaError_t launch_add_f32(const float* W, int np, int nrhs, double* X, float2* Xdf, const int* done,
                            cudaStream_t s);
+// FP32: W (np x nrhs) is followed by 3 x np x nrhs floats of work space (the
+// forward result, then 64-bit epoch-tagged words through which the CTAs of a
+// sweep exchange solved blocks); sync is unused.  Skipped once *done is set.
 cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, int nb, float* W,
                                     int nrhs, unsigned* sync, int* status, const int* done, cudaStream_t s);
 cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,

@@ -221,6 +221,196 @@ __global__ void __launch_bounds__(256) trsv_bwd(const T* __restrict__ L, const T
     }
 }
 
+// ---- FP32 sweeps with self-validating data.  A solved block is published
+// as 64-bit words (epoch << 32 | value bits), each single-copy atomic, so a
+// consumer polls the words it needs until they carry this launch's epoch:
+// one L2 round trip instead of a flag, a fence and a second load.
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits (bounded) for the tagged word and returns its value; gives up,
+// setting status, after kPollLimit polls (each an L2 round trip, about a
+// second in all) or once another wait has given up.
+constexpr long long kPollLimit = 1LL << 21;
+__device__ __forceinline__ float poll_tagged(const unsigned long long* p, unsigned epoch, int* status)
+{
+    long long spins = 0;
+    for (;;) {
+        const unsigned long long w = ld_relaxed_u64(p);
+        if ((unsigned)(w >> 32) == epoch) return __uint_as_float((unsigned)w);
+        if (++spins > kPollLimit || *(volatile int*)status != 0) {
+            atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+            return 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long tagged(float v, unsigned epoch)
+{
+    return ((unsigned long long)epoch << 32) | __float_as_uint(v);
+}
+
+// out[t][c] = sum_k iv[k][t] w[k][c] (TRANS) or iv[t][k] w[k][c]: the
+// diagonal-block inverse is stored with zeros above its diagonal, so all 64
+// terms are summed, unrolled, in four independent chains.
+template <int R, bool TRANS>
+__device__ __forceinline__ float apply_inv(const float (*iv)[NB + 1], const float (*w)[R], int t, int c)
+{
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < NB; ++k) a[k & 3] += (TRANS ? iv[k][t] : iv[t][k]) * w[k][c];
+    return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+// Forward sweep Y = L^-1 W on columns [0, nr) (FP32).
+template <int R>
+__global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L, const float* __restrict__ Linv,
+                                                     int np, const float* __restrict__ W, float* __restrict__ Y,
+                                                     unsigned long long* __restrict__ tag, int nr, unsigned epoch,
+                                                     int* status, const int* done)
+{
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    SweepSmem<float, R>& S = *reinterpret_cast<SweepSmem<float, R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;   // row of the block, column quarter
+    const int nblk = np / NB;
+    constexpr int QW = NB / 4;
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int b0 = b * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+        float rhs[R], acc[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            rhs[c] = (q == 0 && c < nr) ? W[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
+            acc[c] = 0.f;
+        }
+        float lnext[QW];
+        if (b > 0)
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lnext[tt] = L[(size_t)(b0 + r) + (size_t)(q * QW + tt) * np];
+        for (int j = 0; j < b; ++j) {
+            float lcur[QW];
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
+            if (j + 1 < b)
+#pragma unroll
+                for (int tt = 0; tt < QW; ++tt)
+                    lnext[tt] = L[(size_t)(b0 + r) + (size_t)((j + 1) * NB + q * QW + tt) * np];
+            const int j0 = j * NB;
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) {
+                const int t = q * QW + tt;
+#pragma unroll
+                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[t][c];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        if (q == 0)
+#pragma unroll
+            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            if (c >= nr) continue;
+            const float y = apply_inv<R, false>(S.iv, S.w, t, c);
+            const size_t idx = (size_t)(b0 + t) + (size_t)c * np;
+            tag[idx] = tagged(y, epoch);
+            Y[idx] = y;
+        }
+        __syncthreads();
+    }
+}
+
+// Backward sweep X = L^-T Y, written into X; block rows in falling order.
+template <int R>
+__global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L, const float* __restrict__ Linv,
+                                                     int np, const float* __restrict__ Y, float* __restrict__ X,
+                                                     unsigned long long* __restrict__ tag, int nr, unsigned epoch,
+                                                     int* status, const int* done)
+{
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    SweepSmem<float, R>& S = *reinterpret_cast<SweepSmem<float, R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;
+    const int nblk = np / NB;
+    constexpr int QW = NB / 4;
+    for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
+        const int b0 = b * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+        float rhs[R], acc[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            rhs[c] = (q == 0 && c < nr) ? Y[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
+            acc[c] = 0.f;
+        }
+        // row r of L_jb^T is column (b0 + r) of L, rows j0 + q * 16 ..
+        const float* col = L + (size_t)(b0 + r) * np + q * QW;
+        float lnext[QW];
+        if (b < nblk - 1)
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(nblk - 1) * NB + tt];
+        for (int j = nblk - 1; j > b; --j) {
+            float lcur[QW];
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
+            if (j - 1 > b)
+#pragma unroll
+                for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(j - 1) * NB + tt];
+            const int j0 = j * NB;
+            for (int e = tid; e < NB * R; e += blockDim.x) {
+                const int t = e % NB, c = e / NB;
+                S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int tt = 0; tt < QW; ++tt) {
+#pragma unroll
+                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[q * QW + tt][c];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+        if (q == 0)
+#pragma unroll
+            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            if (c >= nr) continue;
+            const float x = apply_inv<R, true>(S.iv, S.w, t, c);
+            const size_t idx = (size_t)(b0 + t) + (size_t)c * np;
+            tag[idx] = tagged(x, epoch);
+            X[idx] = x;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename K>
 int coop_grid(K kernel, size_t smem, int nblk)
 {
@@ -271,6 +461,48 @@ cudaError_t sweep_pair(const T* L, const T* Linv, int np, T* W, T* Y, int nr, un
                         (void*)&sync, (void*)&e2, (void*)&status, (void*)&done};
         cudaEvent_t ev = trace_begin(s);
         if ((e = cudaLaunchCooperativeKernel((void*)trsv_bwd<T, R>, grid, 256, args, smem, s)) != cudaSuccess)
+            return e;
+        count_launch();
+        trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
+    }
+    return cudaSuccess;
+}
+
+template <int R>
+cudaError_t sweep_pair_f32(const float* L, const float* Linv, int np, float* W, float* Y, unsigned long long* tag,
+                           int nr, int* status, const int* done, cudaStream_t s)
+{
+    const size_t smem = sizeof(SweepSmem<float, R>);
+    const int nblk = np / NB;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(sweep_fwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(sweep_bwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    unsigned e1 = g_epoch.fetch_add(2);
+    if (e1 == 0) e1 = g_epoch.fetch_add(2);   // 0 marks a cleared word
+    unsigned e2 = e1 + 1;
+    const double sweep_bytes = 4.0 * ((double)np * (np + NB) / 2 + (double)np * NB + 3.0 * np * nr);
+    const double sweep_flops = (double)np * np * nr;
+    {
+        const float* Wc = W;
+        int grid = coop_grid(sweep_fwd_f32<R>, smem, nblk);
+        void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Wc, (void*)&Y, (void*)&tag,
+                        (void*)&nr, (void*)&e1, (void*)&status, (void*)&done};
+        cudaEvent_t ev = trace_begin(s);
+        if ((e = cudaLaunchCooperativeKernel((void*)sweep_fwd_f32<R>, grid, 256, args, smem, s)) != cudaSuccess)
+            return e;
+        count_launch();
+        trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
+    }
+    {
+        const float* Yc = Y;
+        int grid = coop_grid(sweep_bwd_f32<R>, smem, nblk);
+        void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Yc, (void*)&W, (void*)&tag,
+                        (void*)&nr, (void*)&e2, (void*)&status, (void*)&done};
+        cudaEvent_t ev = trace_begin(s);
+        if ((e = cudaLaunchCooperativeKernel((void*)sweep_bwd_f32<R>, grid, 256, args, smem, s)) != cudaSuccess)
             return e;
         count_launch();
         trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
@@ -849,7 +1081,24 @@ cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, i
                                     int nrhs, unsigned* sync, int* status, const int* done, cudaStream_t s)
 {
     if (nb != NB || nrhs <= 0) return cudaErrorInvalidValue;
-    return trsv<float>(L, Linv, np, W, W + (size_t)np * nrhs, nrhs, sync, status, done, s);
+    (void)sync;
+    float* Y = W + (size_t)np * nrhs;
+    unsigned long long* tag = reinterpret_cast<unsigned long long*>(W + 2 * (size_t)np * nrhs);
+    // no stale word may carry a live epoch (epochs are never 0)
+    cudaError_t ez = cudaMemsetAsync(tag, 0, sizeof(unsigned long long) * (size_t)np * nrhs, s);
+    if (ez != cudaSuccess) return ez;
+    for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
+        const int nr = std::min(MAXR, nrhs - c0);
+        float* Wc = W + (size_t)c0 * np;
+        float* Yc = Y + (size_t)c0 * np;
+        unsigned long long* Tc = tag + (size_t)c0 * np;
+        cudaError_t e;
+        if (nr <= 4) e = sweep_pair_f32<4>(L, Linv, np, Wc, Yc, Tc, nr, status, done, s);
+        else if (nr <= 8) e = sweep_pair_f32<8>(L, Linv, np, Wc, Yc, Tc, nr, status, done, s);
+        else e = sweep_pair_f32<16>(L, Linv, np, Wc, Yc, Tc, nr, status, done, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pack_rhs(const double* B, int ldb, int n, int np, int nrhs, double* Bp,
