@@ -340,6 +340,14 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
 }
 
 // Backward sweep X = L^-T Y, written into X; block rows in falling order.
+// Block (j, b) of L is read along its columns (coalesced) into registers one
+// step ahead and staged through shared memory as its transpose.
+template <int R>
+struct SweepBwdSmem {
+    SweepSmem<float, R> base;
+    float lt[NB][NB + 1];   // lt[r][t] = L[j0 + t][b0 + r]
+};
+
 template <int R>
 __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L, const float* __restrict__ Linv,
                                                      int np, const float* __restrict__ Y, float* __restrict__ X,
@@ -348,7 +356,8 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
 {
     if (done && *done) return;
     extern __shared__ unsigned char smem_raw[];
-    SweepSmem<float, R>& S = *reinterpret_cast<SweepSmem<float, R>*>(smem_raw);
+    SweepBwdSmem<R>& SB = *reinterpret_cast<SweepBwdSmem<R>*>(smem_raw);
+    SweepSmem<float, R>& S = SB.base;
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;
     const int nblk = np / NB;
@@ -362,19 +371,18 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
             rhs[c] = (q == 0 && c < nr) ? Y[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
             acc[c] = 0.f;
         }
-        // row r of L_jb^T is column (b0 + r) of L, rows j0 + q * 16 ..
-        const float* col = L + (size_t)(b0 + r) * np + q * QW;
+        // thread tid holds L[j0 + (tid & 63)][b0 + (tid >> 6) + 4 k], k < 16
+        const float* colb = L + (size_t)(tid & 63) + (size_t)(b0 + (tid >> 6)) * np;
         float lnext[QW];
         if (b < nblk - 1)
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(nblk - 1) * NB + tt];
+            for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(nblk - 1) * NB + (size_t)(4 * k) * np];
         for (int j = nblk - 1; j > b; --j) {
-            float lcur[QW];
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
+            for (int k = 0; k < QW; ++k) SB.lt[(tid >> 6) + 4 * k][tid & 63] = lnext[k];
             if (j - 1 > b)
 #pragma unroll
-                for (int tt = 0; tt < QW; ++tt) lnext[tt] = col[(size_t)(j - 1) * NB + tt];
+                for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(j - 1) * NB + (size_t)(4 * k) * np];
             const int j0 = j * NB;
             for (int e = tid; e < NB * R; e += blockDim.x) {
                 const int t = e % NB, c = e / NB;
@@ -383,8 +391,9 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
             __syncthreads();
 #pragma unroll
             for (int tt = 0; tt < QW; ++tt) {
+                const float l = SB.lt[r][q * QW + tt];
 #pragma unroll
-                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[q * QW + tt][c];
+                for (int c = 0; c < R; ++c) acc[c] += l * S.v[q * QW + tt][c];
             }
             __syncthreads();
         }
@@ -472,12 +481,12 @@ template <int R>
 cudaError_t sweep_pair_f32(const float* L, const float* Linv, int np, float* W, float* Y, unsigned long long* tag,
                            int nr, int* status, const int* done, cudaStream_t s)
 {
-    const size_t smem = sizeof(SweepSmem<float, R>);
+    const size_t smem = sizeof(SweepSmem<float, R>), smem_b = sizeof(SweepBwdSmem<R>);
     const int nblk = np / NB;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(sweep_fwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess ||
-        (e = cudaFuncSetAttribute(sweep_bwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        (e = cudaFuncSetAttribute(sweep_bwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b)) !=
             cudaSuccess)
         return e;
     unsigned e1 = g_epoch.fetch_add(2);
@@ -498,11 +507,11 @@ cudaError_t sweep_pair_f32(const float* L, const float* Linv, int np, float* W, 
     }
     {
         const float* Yc = Y;
-        int grid = coop_grid(sweep_bwd_f32<R>, smem, nblk);
+        int grid = coop_grid(sweep_bwd_f32<R>, smem_b, nblk);
         void* args[] = {(void*)&L, (void*)&Linv, (void*)&np, (void*)&Yc, (void*)&W, (void*)&tag,
                         (void*)&nr, (void*)&e2, (void*)&status, (void*)&done};
         cudaEvent_t ev = trace_begin(s);
-        if ((e = cudaLaunchCooperativeKernel((void*)sweep_bwd_f32<R>, grid, 256, args, smem, s)) != cudaSuccess)
+        if ((e = cudaLaunchCooperativeKernel((void*)sweep_bwd_f32<R>, grid, 256, args, smem_b, s)) != cudaSuccess)
             return e;
         count_launch();
         trace_end(GBEM_KERNEL_SWEEP, ev, s, sweep_bytes, sweep_flops);
