@@ -64,15 +64,20 @@ template <> __device__ __forceinline__ float glw<float>(int n, int i) { return c
 // Outer sum of the quadrature: plain FP64 in FP64 mode; in mixed mode a
 // compensated (Kahan) FP32 sum, which keeps FP64 instructions -- about 70x
 // dearer than FP32 ones here -- out of the far field.
+// Far-field entries: double in FP64 mode; in mixed mode an unevaluated float
+// pair (hi, lo) formed without any FP64 instruction.
+template <typename T> struct FarVal { using type = double; };
+template <> struct FarVal<float> { using type = float2; };
+
 template <typename T>
 struct OuterSum {
     double s = 0.0;
     __device__ __forceinline__ void add(T v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double scaled(double f) const { return s * f; }
 };
 template <>
 struct OuterSum<float> {
-    float s = 0.f, c = 0.f;
+    float s = 0.f, c = 0.f;   // the sum is s - c
     __device__ __forceinline__ void add(float v)
     {
         const float y = v - c;
@@ -80,7 +85,13 @@ struct OuterSum<float> {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s; }
+    // (s - c) f as hi + lo: the product's rounding error (exact by FMA) plus
+    // the compensation term
+    __device__ __forceinline__ float2 scaled(float f) const
+    {
+        const float hi = __fmul_rn(s, f);
+        return make_float2(hi, __fmaf_rn(s, f, -hi) - c * f);
+    }
 };
 
 // Tensor Gauss-Legendre sum of 1/r over N x N nodes on each panel, without
@@ -90,7 +101,7 @@ struct OuterSum<float> {
 // half extents ai, bi (panel i) and aj, bj (panel j).  The outer loop runs
 // over node pairs along p, the inner (unrolled) one over node pairs along q.
 template <typename T, int N>
-__device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
+__device__ __noinline__ OuterSum<T> far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
 {
     T Q[N * N], WQ[N * N];
 #pragma unroll
@@ -112,7 +123,7 @@ __device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
         for (int k = 0; k < N * N; ++k) si += WQ[k] * rsq(p + Q[k]);
         s.add(glw<T>(N, a) * glw<T>(N, c) * si);
     }
-    return s.value();
+    return s;
 }
 
 // Perpendicular panels: shared-axis offset ds with half extents si, sj; the
@@ -120,7 +131,7 @@ __device__ __noinline__ double far_par(T dp, T dq, T w, T ai, T bi, T aj, T bj)
 // along j's normal) and dw of panel i's plane from panel j's centre (half
 // extent tj of j along i's normal).
 template <typename T, int N>
-__device__ __noinline__ double far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj)
+__device__ __noinline__ OuterSum<T> far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj)
 {
     T VW[N * N], WVW[N * N];
 #pragma unroll
@@ -143,7 +154,7 @@ __device__ __noinline__ double far_orth(T ds, T si, T sj, T dv, T ti, T dw, T tj
         for (int k = 0; k < N * N; ++k) acc += WVW[k] * rsq(p + VW[k]);
         s.add(glw<T>(N, a) * glw<T>(N, c) * acc);
     }
-    return s.value();
+    return s;
 }
 
 // ------------------------------------------------------------------ near field
@@ -253,7 +264,7 @@ __device__ __forceinline__ double near_scale(const TileGeo& G, int s, int t)
 
 // Far entry of order N for the pair (s, t), T the arithmetic type.
 template <typename T, int N>
-__device__ double far_entry(const TileGeo& G, int s, int t)
+__device__ typename FarVal<T>::type far_entry(const TileGeo& G, int s, int t)
 {
     const int ki = G.axis[s], kj = G.axis[t];
     T d[3];
@@ -272,7 +283,7 @@ __device__ double far_entry(const TileGeo& G, int s, int t)
 #pragma unroll
         for (int e = 0; e < 3; ++e) d[e] = (G.chi[e][s] - G.chi[e][t]) + (G.clo[e][s] - G.clo[e][t]);
     }
-    double sum;
+    OuterSum<T> sum;
     if (ki == kj) {
         const int p = ax_p(ki), q = ax_q(ki);
         T ai, bi, aj, bj;
@@ -287,7 +298,7 @@ __device__ double far_entry(const TileGeo& G, int s, int t)
             aj = G.half[p][t];
             bj = G.half[q][t];
         }
-        if constexpr (N == 1) sum = 4.0 * (double)rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if constexpr (N == 1) sum.add(T(4) * rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
         else sum = far_par<T, N>(d[p], d[q], d[ki], ai, bi, aj, bj);
     } else {
         const int sh = 3 - ki - kj;
@@ -304,11 +315,11 @@ __device__ double far_entry(const TileGeo& G, int s, int t)
             hv_i = G.half[kj][s];
             hw_j = G.half[ki][t];
         }
-        if constexpr (N == 1) sum = 4.0 * (double)rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if constexpr (N == 1) sum.add(T(4) * rsq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
         else sum = far_orth<T, N>(d[sh], hs_i, hs_j, d[kj], hv_i, d[ki], hw_j);
     }
     // I = (product of half extents) * sum and |I_i||I_j| = 16 * (same product)
-    return sum * (1.0 / (64.0 * kPi));
+    return sum.scaled(T(1.0 / (64.0 * kPi)));
 }
 
 constexpr int kThreads = 256;
@@ -317,12 +328,16 @@ constexpr int kPairs = GBEM_TILE * GBEM_TILE;
 // a far pair of order n = 1..6 (o = 1 if perpendicular).
 constexpr int kClasses = 2 + 2 * GBEM_GL_MAX;
 
+__device__ __forceinline__ double near_entry(const TileGeo& G, int cls, int s, int t)
+{
+    return (cls == 0 ? near_par(G, s, t) : near_orth(G, s, t)) * near_scale(G, s, t);
+}
+
+// Far classes only (cls >= 2).
 template <typename T>
-__device__ double eval_class(const TileGeo& G, int cls, int s, int t)
+__device__ typename FarVal<T>::type eval_far(const TileGeo& G, int cls, int s, int t)
 {
     switch (cls) {
-    case 0: return near_par(G, s, t) * near_scale(G, s, t);
-    case 1: return near_orth(G, s, t) * near_scale(G, s, t);
     case 2: case 3: return far_entry<T, 1>(G, s, t);
     case 4: case 5: return far_entry<T, 2>(G, s, t);
     case 6: case 7: return far_entry<T, 3>(G, s, t);
@@ -336,7 +351,7 @@ __device__ double eval_class(const TileGeo& G, int cls, int s, int t)
 template <bool MIXED>
 __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_near, double* __restrict__ A64,
                                           float* __restrict__ A32, unsigned long long* __restrict__ counts,
-                                          long long b)
+                                          long long b, int nt_band)
 {
     using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ TileGeo G;
@@ -347,12 +362,27 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
 
     const int tid = threadIdx.x;
     if (tid == 0) {
-        // lower-triangular tile coordinates (TI >= TJ) from the linear tile index
-        int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-        while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
-        while ((long long)TI * (TI + 1) / 2 > b) --TI;
-        tile_ij[0] = TI;
-        tile_ij[1] = (int)(b - (long long)TI * (TI + 1) / 2);
+        if (nt_band > 0) {
+            // band order: the diagonal tiles first, then the first
+            // subdiagonal, ...  Tiles near the diagonal hold the near pairs
+            // (FP64 closed forms), so the costly tiles start first and the
+            // cheap far-field tiles fill the tail.  Band d starts at
+            // d nt - d (d - 1) / 2.
+            const double h = 2.0 * nt_band + 1.0;
+            int d = (int)((h - sqrt(fmax(h * h - 8.0 * (double)b, 0.0))) * 0.5);
+            auto off = [nt_band](long long dd) { return dd * nt_band - dd * (dd - 1) / 2; };
+            while (d > 0 && off(d) > b) --d;
+            while (d + 1 < nt_band && off(d + 1) <= b) ++d;
+            tile_ij[1] = (int)(b - off(d));
+            tile_ij[0] = tile_ij[1] + d;
+        } else {
+            // lower-triangular tile coordinates (TI >= TJ) from the linear tile index
+            int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+            while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
+            while ((long long)TI * (TI + 1) / 2 > b) --TI;
+            tile_ij[0] = TI;
+            tile_ij[1] = (int)(b - (long long)TI * (TI + 1) / 2);
+        }
     }
     if (tid < kClasses) cls_cnt[tid] = 0;
     __syncthreads();
@@ -468,16 +498,24 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
     for (int x = tid; x < total; x += kThreads) {
         const int e = list[x];
         const int ii = e & (GBEM_TILE - 1), jj = e >> 5;
-        const double v = eval_class<T>(G, cls_of[e], ii, GBEM_TILE + jj);
+        const int cls = cls_of[e];
         const size_t i = (size_t)TI * GBEM_TILE + ii, j = (size_t)TJ * GBEM_TILE + jj;
-        if (MIXED) {
-            // FP64 entry kept as an unevaluated float pair (hi + lo) for the
+        if constexpr (MIXED) {
+            // entries kept as unevaluated float pairs (hi + lo) for the
             // compensated FP32 residual; hi is also the factor's copy
-            const float h = __double2float_rn(v);
-            reinterpret_cast<float2*>(A64)[i + j * (size_t)np] = make_float2(h, __double2float_rn(v - (double)h));
-            A32[i + j * (size_t)np] = h;
+            float2 pr;
+            if (cls < 2) {
+                const double v = near_entry(G, cls, ii, GBEM_TILE + jj);
+                const float h = __double2float_rn(v);
+                pr = make_float2(h, __double2float_rn(v - (double)h));
+            } else {
+                pr = eval_far<T>(G, cls, ii, GBEM_TILE + jj);
+            }
+            reinterpret_cast<float2*>(A64)[i + j * (size_t)np] = pr;
+            A32[i + j * (size_t)np] = pr.x;
         } else {
-            A64[i + j * (size_t)np] = v;
+            A64[i + j * (size_t)np] = (cls < 2) ? near_entry(G, cls, ii, GBEM_TILE + jj)
+                                                : eval_far<T>(G, cls, ii, GBEM_TILE + jj);
         }
     }
     // class counts: near pairs, then far pairs by order
@@ -493,7 +531,7 @@ __global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, 
                                                            float* __restrict__ A32,
                                                            unsigned long long* __restrict__ counts)
 {
-    tile_body<MIXED>(g, np, q_near, A64, A32, counts, blockIdx.x);
+    tile_body<MIXED>(g, np, q_near, A64, A32, counts, blockIdx.x, (g.n + GBEM_TILE - 1) / GBEM_TILE);
 }
 
 // Batched assembly: CTA index -> (structure, tile) through the prefix sums of
@@ -516,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) assemble_batched(BatchView v, float 
     g.cond = v.cond + po;
     g.n = v.n[b];
     tile_body<MIXED>(g, v.np[b], q_near, v.A64 + v.moff[b], MIXED ? v.A32 + v.moff[b] : nullptr, nullptr,
-                     (long long)blockIdx.x - v.tile_prefix[b]);
+                     (long long)blockIdx.x - v.tile_prefix[b], 0);
 }
 
 // Identity padding of every structure of a batch (rows n..np-1, lower part;
