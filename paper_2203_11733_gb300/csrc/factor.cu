@@ -419,6 +419,9 @@ __device__ void lookahead_row(float* __restrict__ L, int ld, int k0, const unsig
 }
 
 constexpr size_t kStripSmem = 3 * NB * PT * sizeof(float);
+constexpr size_t kPanelRowSmem = 4 * NB * PT * sizeof(float);
+// every role of factor_step within one dynamic allocation: two CTAs per SM
+constexpr size_t kFactorSmem = kPanelRowSmem > (size_t)tc::SMEM_BYTES ? kPanelRowSmem : (size_t)tc::SMEM_BYTES;
 
 // The first diagonal block of the FP32 factorisation, the strip rows of step
 // 0 and the lookahead panel work of row block 1.
@@ -552,6 +555,7 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
     const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
     const int k0 = k * NB, rI = i * NB;
     const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
+    const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
     float4 tgt[2][4];
 #pragma unroll
     for (int sidx = 0; sidx < 2; ++sidx)
@@ -591,7 +595,7 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int rr = rI - r0 + tr + u;
-            const size_t off = (size_t)(rr / tc::TM) * tc::OPER_BYTES + tc::kmajor_offset(rr % tc::TM, tc);
+            const size_t off = tc::split_offset(rr, tc, stage_stride);
             float h[4], l[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -651,7 +655,7 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
 // So the launch cannot deadlock however many CTAs are resident.  Waits are
 // bounded; one that gives up sets status GBEM_ERR_TIMEOUT and its CTA skips
 // its work.
-__global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
+__global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
                                                    int* __restrict__ info, int nblk, int sw, int r0,
                                                    unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
@@ -696,7 +700,8 @@ __global__ void __launch_bounds__(256) factor_step(float* __restrict__ L, int ld
     const int J = (int)(b - (long long)I * (I + 1) / 2);
     const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
     if (!wait_flags(pflag + bI, 2, token, status) || !wait_flags(pflag + bJ, 2, token, status)) return;
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, I, J, tc_smem)) {
+    const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem)) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
         return;
     }
@@ -720,7 +725,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                                   (int)sizeof(PotrfSmem<T>))) != cudaSuccess)
         return e;
     if constexpr (kTensor) {
-        if ((e = cudaFuncSetAttribute(factor_step, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES)) !=
+        if ((e = cudaFuncSetAttribute(factor_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmem)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(potrf_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
                 cudaSuccess)
@@ -761,7 +766,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)(m + tiles));   // m - 1 panel rows, the diagonal CTA, the tiles
             cfg.blockDim = dim3(256);
-            cfg.dynamicSmemBytes = tc::SMEM_BYTES;
+            cfg.dynamicSmemBytes = kFactorSmem;
             cfg.stream = s;
             cfg.attrs = pdl;
             cfg.numAttrs = 1;

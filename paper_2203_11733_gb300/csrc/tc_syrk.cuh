@@ -8,25 +8,28 @@
 // the error of the update near FP32 rounding.
 //
 // The panel columns [k0, k0 + 64) are split once per elimination step (by
-// the panel kernel, as it produces them) into hi and lo copies laid out, per 128-row block, exactly as
-// the tensor core reads them from shared memory: the canonical K-major layout
-// without swizzle, 8-row x 16-byte core matrices consecutive along K (leading
-// byte offset 128 B, 16 of them for the 64 panel columns) and then along M/N
-// (stride byte offset 2048 B).  A 128-row block of one part is 32 KB of
-// contiguous bytes.
+// the panel work, as it produces them) into hi and lo copies laid out, per K
+// stage of 32 columns and 128-row block, exactly as the tensor core reads
+// them from shared memory: the canonical K-major layout without swizzle,
+// 8-row x 16-byte core matrices consecutive along K (leading byte offset
+// 128 B, 8 of them for 32 columns) and then along M/N (stride byte offset
+// 1024 B).  One stage of a 128-row block of one part is 16 KB of contiguous
+// bytes.
 //
-// One CTA (8 warps) owns one 128 x 128 tile:
+// One CTA (8 warps) owns one 128 x 128 tile, with the 64-wide panel taken in
+// two K stages of 32 so that a tile needs 64 KB of shared memory and two tile
+// CTAs share an SM:
 //   1. warp 0 allocates 128 TMEM columns (the FP32 accumulator, one lane per
-//      tile row);
-//   2. one thread bulk-copies the hi/lo blocks of rows I and J into shared
-//      memory (cp.async.bulk, completing on an mbarrier; diagonal tiles copy
-//      one pair);
-//   3. after the bounded wait, one thread issues 8 K-steps x 3 tcgen05.mma
-//      (M = N = 128, K = 8) and commits them to a second mbarrier;
-//   4. every thread loads its 64 entries of C into registers before the
-//      waits, so their latency overlaps the copies and the MMAs; after the
-//      bounded wait every warp reads 32 accumulator lanes x 64 columns with
-//      tcgen05.ld and stores C minus the product;
+//      tile row); one thread bulk-copies (cp.async.bulk, completing on an
+//      mbarrier) the stage-0 hi/lo blocks of rows I and J (diagonal tiles
+//      copy one pair);
+//   2. every thread loads its 64 entries of C into registers, so that their
+//      latency overlaps the copies and the MMAs;
+//   3. thread 0 issues the stage's 4 K-steps x 3 tcgen05.mma (M = N = 128,
+//      K = 8) and commits them to a second mbarrier; once they have read the
+//      stage, it copies stage 1 into the same buffers and issues its MMAs;
+//   4. after the bounded wait every warp reads 32 accumulator lanes x 64
+//      columns with tcgen05.ld and stores C minus the product;
 //   5. warp 0 frees the TMEM columns.
 #pragma once
 
@@ -36,8 +39,10 @@ namespace tc {
 
 constexpr int TM = 128;       // tile rows (MMA M) and columns (MMA N)
 constexpr int TK = 64;        // panel width (sum over K)
-constexpr int OPER_BYTES = TM * TK * 4;                 // one operand part (hi or lo)
-constexpr int SMEM_BYTES = 4 * OPER_BYTES + 256;        // A_hi, A_lo, B_hi, B_lo, barrier + TMEM slot
+constexpr int KH = 32;        // K per pipeline stage (two stages per panel)
+constexpr int OPER_BYTES = TM * TK * 4;                 // one operand part (hi or lo) of a 128-row block
+constexpr int HALF_BYTES = TM * KH * 4;                 // ... and of one stage
+constexpr int SMEM_BYTES = 4 * HALF_BYTES + 256;        // A_hi, A_lo, B_hi, B_lo of a stage, barriers + TMEM slot
 constexpr long long kWaitLimit = 1LL << 20;             // bounded mbarrier polling
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -45,11 +50,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row r, k) of a 128 x 64 fp32 operand in the K-major,
-// no-swizzle core-matrix layout.
+// Byte offset of element (row r, k) of a 128 x 32 fp32 stage operand in the
+// K-major, no-swizzle core-matrix layout.
 __device__ __forceinline__ uint32_t kmajor_offset(int r, int k)
 {
-    return (uint32_t)((k >> 2) * 128 + (r >> 3) * (TK / 4) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((k >> 2) * 128 + (r >> 3) * (KH / 4) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Byte offset of panel element (row rr from r0, column k < 64) in one part of
+// the split buffer: stage k / 32, then 128-row block, then the stage layout.
+__device__ __forceinline__ size_t split_offset(int rr, int k, size_t stage_stride)
+{
+    return (size_t)(k / KH) * stage_stride + (size_t)(rr / TM) * HALF_BYTES + kmajor_offset(rr % TM, k % KH);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits
@@ -60,7 +72,7 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(((TK / 4) * 128) >> 4) << 32;
+    d |= (uint64_t)(((KH / 4) * 128) >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -136,29 +148,42 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait on phase 0 of an mbarrier.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar)
+// Bounded wait on the given phase parity of an mbarrier.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity = 0)
 {
     long long spins = 0;
-    while (!mbar_try_wait(bar, 0))
+    while (!mbar_try_wait(bar, parity))
         if (++spins > kWaitLimit) return false;
     return true;
 }
 
 // C[rI + .., rJ + ..] -= A_I A_J^T for one 128 x 128 tile.  I and J index the
-// 128-row blocks of the split panel (rows rI = r0 + 128 I, rJ = r0 + 128 J).
+// 128-row blocks of the split panel (rows rI = r0 + 128 I, rJ = r0 + 128 J);
+// stage_stride is the byte distance between the two K stages of a part.
 // 256 threads.  Returns false if a bounded wait gave up.
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
-                          const unsigned char* __restrict__ lo, int I, int J, unsigned char* smem)
+                          const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
+                          unsigned char* smem)
 {
     unsigned char* a_hi = smem;
-    unsigned char* a_lo = smem + OPER_BYTES;
-    unsigned char* b_hi = (I == J) ? a_hi : smem + 2 * OPER_BYTES;
-    unsigned char* b_lo = (I == J) ? a_lo : smem + 3 * OPER_BYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * OPER_BYTES);   // [0] operands, [1] MMAs
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * OPER_BYTES + 64);
+    unsigned char* a_lo = smem + HALF_BYTES;
+    unsigned char* b_hi = (I == J) ? a_hi : smem + 2 * HALF_BYTES;
+    unsigned char* b_lo = (I == J) ? a_lo : smem + 3 * HALF_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * HALF_BYTES);   // [0] operands, [1] MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * HALF_BYTES + 64);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+    const uint32_t parts = (I == J) ? 2 : 4;
+    auto issue = [&](int h) {
+        mbar_expect_tx(bar_ld, parts * HALF_BYTES);
+        const size_t o = (size_t)h * stage_stride;
+        bulk_g2s(smem_u32(a_hi), hi + o + (size_t)I * HALF_BYTES, HALF_BYTES, bar_ld);
+        bulk_g2s(smem_u32(a_lo), lo + o + (size_t)I * HALF_BYTES, HALF_BYTES, bar_ld);
+        if (I != J) {
+            bulk_g2s(smem_u32(b_hi), hi + o + (size_t)J * HALF_BYTES, HALF_BYTES, bar_ld);
+            bulk_g2s(smem_u32(b_lo), lo + o + (size_t)J * HALF_BYTES, HALF_BYTES, bar_ld);
+        }
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -170,24 +195,17 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
         mbar_init(bar_ld, 1);
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t parts = (I == J) ? 2 : 4;
         // the split may have been written by other CTAs of this launch
         // (generic-proxy stores): order them before the async-proxy copies
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        mbar_expect_tx(bar_ld, parts * OPER_BYTES);
-        bulk_g2s(smem_u32(a_hi), hi + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
-        bulk_g2s(smem_u32(a_lo), lo + (size_t)I * OPER_BYTES, OPER_BYTES, bar_ld);
-        if (I != J) {
-            bulk_g2s(smem_u32(b_hi), hi + (size_t)J * OPER_BYTES, OPER_BYTES, bar_ld);
-            bulk_g2s(smem_u32(b_lo), lo + (size_t)J * OPER_BYTES, OPER_BYTES, bar_ld);
-        }
+        issue(0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     // this thread's 64 entries of C (row q * 32 + lane, columns 64 half ..),
-    // loaded now so that their latency overlaps the operand copies and MMAs
+    // loaded now so that their latency overlaps the copies and MMAs
     const int q = warp & 3, half = warp >> 2;
     const int row = q * 32 + (tid & 31);
     float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
@@ -195,28 +213,42 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
 #pragma unroll
     for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
 
-    bool ok = true;
+    // thread 0: stage 0 MMAs, then (once they have read shared memory) the
+    // stage-1 copies into the same buffers, then the stage-1 MMAs
+    int ok = 1, loads = 1, commits = 0;
     if (tid == 0) {
-        ok = mbar_wait_bounded(bar_ld);
-        if (ok) {
-            const uint32_t idesc = make_idesc();
-            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        const uint32_t idesc = make_idesc();
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        for (int h = 0; h < 2 && ok; ++h) {
+            if (!mbar_wait_bounded(bar_ld, h)) {
+                ok = 0;
+                break;
+            }
 #pragma unroll
-            for (int ks = 0; ks < TK / 8; ++ks) {
+            for (int ks = 0; ks < KH / 8; ++ks) {
                 const uint32_t off = ks * 256;   // 8 tf32 = two core matrices along K
-                mma_tf32(tmem, make_desc(ah + off), make_desc(bh + off), idesc, ks > 0);
+                mma_tf32(tmem, make_desc(ah + off), make_desc(bh + off), idesc, h > 0 || ks > 0);
                 mma_tf32(tmem, make_desc(ah + off), make_desc(bl + off), idesc, 1);
                 mma_tf32(tmem, make_desc(al + off), make_desc(bh + off), idesc, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              bar_mma)
                          : "memory");
+            ++commits;
+            if (h == 0) {
+                if (!mbar_wait_bounded(bar_mma, 0)) {
+                    ok = 0;
+                    break;
+                }
+                issue(1);
+                ++loads;
+            }
         }
     }
-    // every thread learns whether the operand wait succeeded
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
-    if (ok) ok = mbar_wait_bounded(bar_mma);
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    // every thread learns whether thread 0's waits succeeded
+    ok = __syncthreads_and(ok);
+    if (ok) ok = mbar_wait_bounded(bar_mma, 1);
+    ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
@@ -227,6 +259,12 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
 #pragma unroll
             for (int i = 0; i < 16; ++i) crow[(size_t)(cc + i) * ld] = cpre[cc + i] - v[i];
         }
+    }
+    // after a failed wait, give the copies and MMAs still in flight a bounded
+    // chance to finish before the shared memory and TMEM are released
+    if (!ok && tid == 0) {
+        for (int h = 0; h < loads; ++h) mbar_wait_bounded(bar_ld, h);
+        for (int h = 0; h < commits; ++h) mbar_wait_bounded(bar_mma, h);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
