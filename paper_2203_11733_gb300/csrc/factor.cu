@@ -322,34 +322,50 @@ __device__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status
 
 constexpr int PT = NB + 4;   // padded row of a t-major 64 x 64 block in shared memory
 
-// L_ck = A_ck Linv_kk^T for the ns row blocks c = k+1 .. k+ns below diagonal
-// block k (k0 = 64 k), which its CTA has just factored.  Stored t-major,
-// lsT[s * 4096 + t * 64 + r] = L_ck[r][t], for the strip update of the next
-// panel step.  All 256 threads; shared memory: two t-major blocks.
-__device__ void strip_rows(const float* __restrict__ L, int ld, int k0, const float* __restrict__ Linv,
-                           float* __restrict__ lsT, int ns)
+// The work that follows the factorisation of diagonal block k (k0 = 64 k) in
+// the same CTA, all 256 threads, arranged so that every global read is
+// issued in one phase:
+//   1. the strip rows of step k: L_ck = A_ck Linv_kk^T for the ns row blocks
+//      c = k+1 .. k+ns, stored t-major in lsT[s * 4096 + t * 64 + r] =
+//      L_ck[r][t] for the strip update of that step's panel work;
+//   2. the lookahead panel work of row block c = k+1 for step k: L_ck is
+//      written to L, and A_cc -= L_ck L_ck^T once A_cc has every earlier
+//      panel applied (after `ready`, when given: the tile that applies the
+//      previous panel to it); then pflag_c = token.  The next launch orders
+//      these writes before its reads, so the flag needs no fence.
+// Shared memory: four t-major 64 x 68 blocks.
+__device__ void diag_tail(float* __restrict__ L, int ld, int k0, const float* __restrict__ Linv,
+                          float* __restrict__ lsT, int ns, const unsigned* ready, unsigned* pflag_c, unsigned token,
+                          int* status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv_kk[c][t]
-    float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_ck[r][t]
+    float(*aT)[PT] = ivT + NB;                                    // aT[s * 64 + t][r] = A_ck[r][t]
+    float(*lT)[PT] = ivT + 3 * NB;                                // lT[t][r] = L_ck[r][t], c = k+1
     const int tid = threadIdx.x;
     const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const int rc = k0 + NB;
     const float* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
     __syncthreads();   // the factorisation is done with shared memory, its stores are issued
-    for (int e = tid; e < NB * NB / 4; e += blockDim.x)
-        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = __ldcg(reinterpret_cast<const float4*>(Lb) + e);
+    // 1. every read at once: the inverse (just written by this CTA), the
+    // strip blocks, and A_cc unless it still waits for a tile
+    float4 cc[4];
+    if (!ready)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            cc[v] = __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld));
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+        const int t = e >> 4, r = (e & 15) * 4;
+        *reinterpret_cast<float4*>(&ivT[t][r]) = __ldcg(reinterpret_cast<const float4*>(Lb) + e);
+        for (int sidx = 0; sidx < ns; ++sidx)
+            *reinterpret_cast<float4*>(&aT[sidx * NB + t][r]) = __ldcg(
+                reinterpret_cast<const float4*>(L + (size_t)(rc + sidx * NB + r) + (size_t)(k0 + t) * ld));
+    }
+    __syncthreads();
     for (int sidx = 0; sidx < ns; ++sidx) {
-        const int rc = k0 + NB * (1 + sidx);
-        if (sidx) __syncthreads();
-        for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
-            const int t = e >> 4, r = (e & 15) * 4;
-            *reinterpret_cast<float4*>(&aT[t][r]) =
-                __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld));
-        }
-        __syncthreads();
         float acc[4][4] = {};
         for (int t = 0; t < tc + 4; ++t) {   // Linv_kk is lower triangular
-            const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+            const float4 x = *reinterpret_cast<const float4*>(&aT[sidx * NB + t][tr]);
             const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
             const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
@@ -358,39 +374,27 @@ __device__ void strip_rows(const float* __restrict__ L, int ld, int k0, const fl
                 for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
         }
         float* dst = lsT + (size_t)sidx * NB * NB;
-        float(*lT)[PT] = aT + NB;   // the first strip row stays in shared memory
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
             *reinterpret_cast<float4*>(dst + (size_t)(tc + v) * NB + tr) = q;
-            if (sidx == 0) *reinterpret_cast<float4*>(&lT[tc + v][tr]) = q;
+            if (sidx == 0) {
+                *reinterpret_cast<float4*>(&lT[tc + v][tr]) = q;
+                // L_ck into L: column k0 + tc + v, rows rc + tr ..
+                *reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(k0 + tc + v) * ld) = q;
+            }
         }
     }
-}
-
-// Lookahead: the panel work of row block c = k+1 (k0 = 64 k, the block just
-// factored) for elimination step k, done by the CTA that factored block k
-// right after strip_rows, so that the next diagonal block is ready when step
-// k's launch starts:
-//   L_ck (the first strip row, in shared memory) is written to L, and
-//   A_cc -= L_ck L_ck^T, once A_cc has every earlier panel applied (after
-//   `ready`, when given: the tile that applies the previous panel to it);
-// then pflag_c = token.
-__device__ void lookahead_row(float* __restrict__ L, int ld, int k0, const unsigned* ready, unsigned* pflag_c,
-                              unsigned token, int* status)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float(*lT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw) + 2 * NB;   // lT[t][r] = L_ck[r][t]
-    const int tid = threadIdx.x;
-    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
-    const int rc = k0 + NB;
-    __syncthreads();   // lT complete
-    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
-        const int t = e >> 4, r = (e & 15) * 4;
-        *reinterpret_cast<float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld) =
-            *reinterpret_cast<const float4*>(&lT[t][r]);
+    if (ns <= 0) return;
+    // 2. the lookahead update of A_cc
+    if (ready) {
+        if (!wait_flags(ready, 1, 1u, status)) return;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            cc[v] = __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld));
+    } else {
+        __syncthreads();   // lT complete
     }
-    if (ready && !wait_flags(ready, 1, 1u, status)) return;
     float acc[4][4] = {};
     for (int t = 0; t < NB; ++t) {
         const float4 x = *reinterpret_cast<const float4*>(&lT[t][tr]);
@@ -403,37 +407,29 @@ __device__ void lookahead_row(float* __restrict__ L, int ld, int k0, const unsig
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        float4* p = reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld);
-        float4 o = __ldcg(p);
+        float4 o = cc[v];
         o.x -= acc[0][v];
         o.y -= acc[1][v];
         o.z -= acc[2][v];
         o.w -= acc[3][v];
-        *p = o;
+        *reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld) = o;
     }
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        st_release(pflag_c, token);
-    }
+    if (tid == 0) *(volatile unsigned*)pflag_c = token;
 }
 
-constexpr size_t kStripSmem = 3 * NB * PT * sizeof(float);
+constexpr size_t kStripSmem = 4 * NB * PT * sizeof(float);
 constexpr size_t kPanelRowSmem = 4 * NB * PT * sizeof(float);
 // every role of factor_step within one dynamic allocation: two CTAs per SM
 constexpr size_t kFactorSmem = kPanelRowSmem > (size_t)tc::SMEM_BYTES ? kPanelRowSmem : (size_t)tc::SMEM_BYTES;
 
 // The first diagonal block of the FP32 factorisation, the strip rows of step
-// 0 and the lookahead panel work of row block 1.
+// 0 and the lookahead panel work of row block 1 (diag_tail).
 __global__ void __launch_bounds__(256) potrf_first(float* __restrict__ L, int ld, float* __restrict__ Linv,
                                                    int* __restrict__ info, float* __restrict__ lsT, int ns,
                                                    unsigned* __restrict__ pflag)
 {
     potrf_body<float>(L, ld, 0, Linv, info);
-    if (ns > 0) {
-        strip_rows(L, ld, 0, Linv, lsT, ns);
-        lookahead_row(L, ld, 0, nullptr, pflag + 1, 1u, info + 3);
-    }
+    if (ns > 0) diag_tail(L, ld, 0, Linv, lsT, ns, nullptr, pflag + 1, 1u, info + 3);
 }
 
 template <typename T>
@@ -688,8 +684,8 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
         potrf_body<float>(L, ld, (k + 1) * NB, Linv, info);
         if (ns_next > 0) {
             if (!wait_flags(pflag + k + 2, ns_next, token, status)) return;
-            strip_rows(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next);
-            lookahead_row(L, ld, (k + 1) * NB, sw == 1 ? tdone + k : nullptr, pflag + k + 2, token + 1, status);
+            diag_tail(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next, sw == 1 ? tdone + k : nullptr, pflag + k + 2,
+                      token + 1, status);
         }
         return;
     }
