@@ -552,6 +552,8 @@ def run_serving(args):
     wait = np.array([i["start_s"] - i["submit_s"] for i in infos]) * 1e3
     span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
     ok = all(i["status"] == 0 for i in infos)
+    failed = [{"id": int(i["id"]), "status": int(i["status"]), "n_panels": int(i["n_panels"]),
+               "residual": float(i["residual"])} for i in infos if i["status"] != 0]
     ns = np.array([i["n_panels"] for i in infos])
     # one at a time on the same GPU: the first requests, FP64 then mixed
     ctx = gbem.Context(local)
@@ -582,7 +584,7 @@ def run_serving(args):
                    "hbm_budget_gb": args.serve_budget_gb, "n_max": int(ns.max()), "n_median": int(np.median(ns))},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "queue_wait_p50_ms": float(np.percentile(wait, 50)),
-        "queue_wait_p99_ms": float(np.percentile(wait, 99)), "all_ok": ok,
+        "queue_wait_p99_ms": float(np.percentile(wait, 99)), "all_ok": ok, "failed": failed,
         "peak_reserved_gb": stats["peak_reserved"] / (1 << 30),
         "one_at_a_time_fp64": {"requests": len(t64), "extractions_per_s": len(t64) / float(t64.sum()),
                                "p50_ms": float(np.percentile(t64, 50) * 1e3)},

@@ -686,8 +686,10 @@ __device__ __forceinline__ void residual_body(const double* __restrict__ A, int 
 //   a x = a.x x.x + e + (a.x x.y + a.y x.x),  e = fma(a.x, x.x, -a.x x.x) exact,
 // summed into (s, c) with s + p = s' + err exactly.  The dropped a.y x.y term
 // and the FP32 rounding of the tail sums leave a relative error of a few
-// 2^-48 per partial sum, far below the refinement tolerance.  The explicit
-// _rn intrinsics keep the compiler from contracting the exact steps.
+// 2^-48 per term; each thread folds its pair into an FP64 sum every 64 terms
+// (residual_df_body), which keeps the residual accurate to about 1e-13 at
+// any order.  The explicit _rn intrinsics keep the compiler from contracting
+// the exact steps.
 __device__ __forceinline__ void df_acc(float& s, float& c, float2 a, float2 x)
 {
     const float p = __fmul_rn(a.x, x.x);
@@ -773,8 +775,12 @@ __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, i
             cp_async_commit();
         }
         float sh[RR], sl[RR];
+        double sd[RR];   // FP64 sum of the flushed float pairs
 #pragma unroll
-        for (int c = 0; c < RR; ++c) sh[c] = sl[c] = 0.0f;
+        for (int c = 0; c < RR; ++c) {
+            sh[c] = sl[c] = 0.0f;
+            sd[c] = 0.0;
+        }
         for (int jb = 0; jb < nblk; ++jb) {
             if (jb + S - 1 < nblk) issue(jb + S - 1);
             cp_async_commit();
@@ -788,13 +794,22 @@ __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, i
 #pragma unroll
                 for (int c = 0; c < RR; ++c) df_acc(sh[c], sl[c], av, ring.xs[st][jj][c]);
             }
+            // a float pair loses about 2^-48 of the partial sum per term: fold
+            // it into FP64 every 64 terms, so the error stays near 1e-13 of
+            // the largest partial sum whatever the order
+            if ((jb & 15) == 15)
+#pragma unroll
+                for (int c = 0; c < RR; ++c) {
+                    sd[c] += (double)sh[c] + (double)sl[c];
+                    sh[c] = sl[c] = 0.0f;
+                }
             __syncthreads();          // the stage is free for the copy issued next
         }
         cp_async_wait<0>();
         double acc[RR];
 #pragma unroll
         for (int c = 0; c < RR; ++c) {
-            acc[c] = (double)sh[c] + (double)sl[c];
+            acc[c] = sd[c] + ((double)sh[c] + (double)sl[c]);
             acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
         }
         __syncthreads();

@@ -227,3 +227,21 @@ def test_kernel_trace_covers_the_mixed_path(ctx):
     assert k["factor"]["flops"] > 0 and k["residual"]["flops"] > 0
     empty = gbem.get_kernel_stats(ctx)
     assert all(d["launches"] == 0 for d in empty.values())
+
+
+@pytest.mark.slow
+def test_mixed_refinement_converges_at_large_order(ctx):
+    """The compensated FP32 residual must stay accurate enough for the FP64
+    refinement to reach its 1e-12 tolerance at large N (the three-layer bus,
+    N = 23172)."""
+    from paper_2203_11733_gb300 import gbem
+    boxes, params = W.bus_3layer_5x5x5()
+    mesh = ctx.mesh(boxes, params)
+    assert mesh.n == 23172
+    mat = gbem.gbem_assemble(mesh, 1)
+    C, res = gbem.gbem_capacitance(mesh, mat, W.EPS_R_SIO2)
+    mat.close()
+    mesh.close()
+    assert res <= 1e-12
+    assert np.all(np.diag(C) > 0) and np.all(C - np.diag(np.diag(C)) <= 0)
+    assert np.all(C.sum(axis=1) > 0)
