@@ -283,6 +283,11 @@ def run_ours(args):
     gbem.set_timing(ctx, 0)
     gbem.get_stats(ctx, reset=True)
 
+    # the final relative residual of the refinement (one extra, untimed extraction)
+    mat_r = gbem.gbem_assemble(mesh, gbem.GBEM_MIXED, stream)
+    _, ir_residual = gbem.gbem_capacitance(mesh, mat_r, eps_r, stream, want_residual=True)
+    mat_r.close()
+
     # ---- FP64 path on the same GPU
     step(gbem.GBEM_FP64)
     barrier()
@@ -335,6 +340,7 @@ def run_ours(args):
                      "cap_rel_err_vs_oracle": err_fp64},
             "mixed_over_fp64": ms64_step / ms_step,
             "cap_rel_err_vs_oracle": err_mixed,
+            "ir_residual": ir_residual,
             "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": int(stats["launches"]),

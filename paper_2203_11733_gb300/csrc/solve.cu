@@ -255,6 +255,22 @@ __device__ __forceinline__ unsigned long long tagged(float v, unsigned epoch)
     return ((unsigned long long)epoch << 32) | __float_as_uint(v);
 }
 
+// acc += aj with Kahan compensation: a thread sums one 16-term product per
+// earlier block, so the long sum over blocks carries no rounding drift into
+// the solve (the refinement's contraction, about the square of the solve's
+// error per two iterations, depends on it).
+template <int R>
+__device__ __forceinline__ void kahan_add(float (&acc)[R], float (&comp)[R], const float (&aj)[R])
+{
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        const float y = __fsub_rn(aj[c], comp[c]);
+        const float t = __fadd_rn(acc[c], y);
+        comp[c] = __fsub_rn(__fsub_rn(t, acc[c]), y);
+        acc[c] = t;
+    }
+}
+
 // out[t][c] = sum_k iv[k][t] w[k][c] (TRANS) or iv[t][k] w[k][c]: the
 // diagonal-block inverse is stored with zeros above its diagonal, so all 64
 // terms are summed, unrolled, in four independent chains.
@@ -284,11 +300,11 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
     for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int b0 = b * NB;
         for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
-        float rhs[R], acc[R];
+        float rhs[R], acc[R], comp[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) {
             rhs[c] = (q == 0 && c < nr) ? W[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
-            acc[c] = 0.f;
+            acc[c] = comp[c] = 0.f;
         }
         float lnext[QW];
         if (b > 0)
@@ -308,12 +324,16 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
                 S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
             }
             __syncthreads();
+            float aj[R];
+#pragma unroll
+            for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
             for (int tt = 0; tt < QW; ++tt) {
                 const int t = q * QW + tt;
 #pragma unroll
-                for (int c = 0; c < R; ++c) acc[c] += lcur[tt] * S.v[t][c];
+                for (int c = 0; c < R; ++c) aj[c] += lcur[tt] * S.v[t][c];
             }
+            kahan_add(acc, comp, aj);
             __syncthreads();
         }
 #pragma unroll
@@ -365,11 +385,11 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
     for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
         const int b0 = b * NB;
         for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
-        float rhs[R], acc[R];
+        float rhs[R], acc[R], comp[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) {
             rhs[c] = (q == 0 && c < nr) ? Y[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
-            acc[c] = 0.f;
+            acc[c] = comp[c] = 0.f;
         }
         // thread tid holds L[j0 + (tid & 63)][b0 + (tid >> 6) + 4 k], k < 16
         const float* colb = L + (size_t)(tid & 63) + (size_t)(b0 + (tid >> 6)) * np;
@@ -389,12 +409,16 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
                 S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
             }
             __syncthreads();
+            float aj[R];
+#pragma unroll
+            for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
             for (int tt = 0; tt < QW; ++tt) {
                 const float l = SB.lt[r][q * QW + tt];
 #pragma unroll
-                for (int c = 0; c < R; ++c) acc[c] += l * S.v[q * QW + tt][c];
+                for (int c = 0; c < R; ++c) aj[c] += l * S.v[q * QW + tt][c];
             }
+            kahan_add(acc, comp, aj);
             __syncthreads();
         }
 #pragma unroll
