@@ -428,8 +428,10 @@ def roofline(kst, steps, ms_traced_step):
 
 def run_batch(args):
     """512 independent 2-6 bar structures (N log-uniform in [200, 3000]):
-    one graph launch for the whole batch, against one-at-a-time extractions
-    (mixed and FP64) of the same structures on the same GPU."""
+    the autotuned batch (groups of structures whose graphs run concurrently,
+    fewest refinement passes that meet the tolerance) against the untuned one
+    and against one-at-a-time extractions (mixed and FP64) of the same
+    structures on the same GPU."""
     import numpy as np
     import torch
     world, rank, local = dist_env()
@@ -441,27 +443,41 @@ def run_batch(args):
     ctx = gbem.Context(local)
     meshes = [ctx.mesh(b, p) for b, p in structs]
     ns = np.array([m.n for m in meshes])
-    t0 = time.perf_counter()
-    batch = gbem.Batch(ctx, meshes)
-    t_create = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
+
+    def timed_runs(batch, k):
+        total = 0.0
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = batch.run(W.EPS_R_SIO2, stream)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / k, out
+
+    # the untuned batch (one group, three refinement passes) for comparison
+    t0 = time.perf_counter()
+    base = gbem.Batch(ctx, meshes, iters=3)
+    t_create = time.perf_counter() - t0
     for _ in range(args.warmup):
-        Cs, res = batch.run(W.EPS_R_SIO2, stream)
+        base.run(W.EPS_R_SIO2, stream)
+    ms_base, _ = timed_runs(base, args.steps)
+    base.close()
+    # the autotuned batch (groups and refinement passes), cache in a temporary file
+    cache = os.path.join(tempfile.mkdtemp(), "batch_tuning.txt")
+    t0 = time.perf_counter()
+    batch, choice = gbem.Batch.autotune(ctx, meshes, max_iters=3, cache_path=cache)
+    t_tune = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        batch.run(W.EPS_R_SIO2, stream)
     gbem.get_stats(ctx, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
-    total = 0.0
-    for _ in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        Cs, res = batch.run(W.EPS_R_SIO2, stream)
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
+    ms_batch, (Cs, res) = timed_runs(batch, args.steps)
     clk = clocks.stop()
     st = gbem.get_stats(ctx, reset=True)
-    ms_batch = total / args.steps
     # one at a time, same structures, same GPU
     def one_at_a_time(prec, idx):
         t = 0.0
@@ -494,7 +510,10 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": f"batch{n_ext}: 2-6 parallel/crossing bars, N log-uniform [200,3000]",
                    "n_structures": n_ext, "n_panels_total": int(ns.sum()), "n_min": int(ns.min()),
-                   "n_max": int(ns.max()), "refinement_passes": 3, "graph_kernels_per_launch": int(st["launches"] / args.steps)},
+                   "n_max": int(ns.max()), "refinement_passes": choice["iters"], "groups": choice["groups"],
+                   "graph_kernels_per_launch": int(st["launches"] / args.steps)},
+        "autotune": {"choice": choice, "tune_s": t_tune, "untuned_ms_per_step": ms_base,
+                     "untuned_config": {"groups": 1, "refinement_passes": 3}},
         "pairs_per_s": world * float((ns * (ns + 1) / 2).sum()) / (ms_batch * 1e-3),
         "one_at_a_time_mixed": {"extractions_per_s": n_ext / (t_mixed * 1e-3), "ms_total": t_mixed},
         "one_at_a_time_fp64": {"extractions_per_s": len(sub) / (t64 * 1e-3), "structures": len(sub)},

@@ -275,6 +275,35 @@ gbem_status gbem_batch_info(const gbem_batch_t* batch, int* count, long long* c_
                             long long* c_offset);
 void gbem_batch_destroy(gbem_batch_t* batch);
 
+/* Batches in groups.  gbem_batch_create_grouped splits the structures into
+ * `groups` parts of similar factorisation work (sum of np^3); each part has
+ * its own pooled buffers, stream and graph, and the parts' graphs run
+ * concurrently (small structures then need not wait for the elimination
+ * steps of the largest).  Results come back in the caller's order; groups 1
+ * is gbem_batch_create.  Not in the paper (a batching choice). */
+gbem_status gbem_batch_create_grouped(gbem_ctx* ctx, int count, gbem_mesh_t* const* meshes, int groups,
+                                      int iters, gbem_batch_t** out);
+/* The groups and refinement passes a batch was built with. */
+gbem_status gbem_batch_config(const gbem_batch_t* batch, int* groups, int* iters);
+/* Autotuner for the batched form.  Tries 1, 2 and 4 groups; for each, the
+ * fewest refinement passes (at most max_iters, 0 selects 3) after which
+ * every structure's relative residual meets the context's tolerance, then
+ * the time of three runs after a warm-up (CUDA events, default stream).  The
+ * fastest is returned built in *out, and appended to cache_path (may be NULL)
+ * as a line "<key> <groups> <passes> <ms>", keyed by a hash of the count,
+ * every structure's order and conductor count, and max_iters; a later call
+ * with the same key builds that configuration without timing (from_cache =
+ * 1).  The runs execute the batch, so the meshes must be valid; the panels
+ * are copied and the meshes may be destroyed afterwards. */
+typedef struct {
+    int groups;
+    int iters;
+    double ms;        /* per run when timed, or as cached */
+    int from_cache;
+} gbem_batch_tuning;
+gbem_status gbem_batch_autotune(gbem_ctx* ctx, int count, gbem_mesh_t* const* meshes, int max_iters,
+                                const char* cache_path, gbem_batch_t** out, gbem_batch_tuning* report);
+
 /* Extraction server (continuous batching).  Requests are meshed on the host
  * when submitted, so their device footprint is known; they wait in a
  * first-in first-out queue and are admitted by `slots` worker threads (each

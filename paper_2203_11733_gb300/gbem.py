@@ -105,6 +105,11 @@ _SIGS = {
     "gbem_batch_run": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "gbem_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong), _P]),
     "gbem_batch_destroy": (None, [_P]),
+    "gbem_batch_create_grouped": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(_P)]),
+    "gbem_batch_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "gbem_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_P),
+                                           _P]),
     "gbem_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(_P)]),
     "gbem_server_submit": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(_Box), ctypes.c_int,
@@ -339,22 +344,56 @@ class Matrix:
             pass
 
 
-class Batch:
-    """Batched extraction of independent structures (one CUDA graph)."""
+class BatchTuning(ctypes.Structure):
+    """gbem_batch_tuning: the configuration the autotuner chose."""
+    _fields_ = [("groups", ctypes.c_int), ("iters", ctypes.c_int), ("ms", ctypes.c_double),
+                ("from_cache", ctypes.c_int)]
 
-    def __init__(self, ctx: Context, meshes, iters: int = 0):
+
+class Batch:
+    """Batched extraction of independent structures (one CUDA graph per
+    group of structures; the groups run concurrently)."""
+
+    def __init__(self, ctx: Context, meshes, iters: int = 0, groups: int = 1, _handle=None):
         self.ctx, self.meshes = ctx, list(meshes)
-        arr = (ctypes.c_void_p * len(self.meshes))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
-                                                      for m in self.meshes])
-        h = ctypes.c_void_p()
-        ctx.check(ctx.lib.gbem_batch_create(ctx.h, len(self.meshes), ctypes.cast(arr, ctypes.c_void_p), int(iters),
-                                            ctypes.byref(h)))
+        if _handle is None:
+            arr = self._mesh_array(self.meshes)
+            h = ctypes.c_void_p()
+            ctx.check(ctx.lib.gbem_batch_create_grouped(ctx.h, len(self.meshes), ctypes.cast(arr, ctypes.c_void_p),
+                                                        int(groups), int(iters), ctypes.byref(h)))
+        else:
+            h = _handle
         self.h = h
         ctx._children.add(self)
         cnt, tot = ctypes.c_int(), ctypes.c_longlong()
         self.c_offset = np.zeros(len(self.meshes), np.int64)
         ctx.check(ctx.lib.gbem_batch_info(h, ctypes.byref(cnt), ctypes.byref(tot), _ptr(self.c_offset)))
         self.c_total = tot.value
+
+    @staticmethod
+    def _mesh_array(meshes):
+        return (ctypes.c_void_p * len(meshes))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
+                                                 for m in meshes])
+
+    @classmethod
+    def autotune(cls, ctx: Context, meshes, max_iters: int = 0, cache_path: str | None = None):
+        """The fastest of 1, 2 and 4 groups with the fewest refinement passes
+        that meet the tolerance (gbem_batch_autotune); returns (batch, choice)."""
+        meshes = list(meshes)
+        arr = cls._mesh_array(meshes)
+        h = ctypes.c_void_p()
+        rep = BatchTuning()
+        ctx.check(ctx.lib.gbem_batch_autotune(ctx.h, len(meshes), ctypes.cast(arr, ctypes.c_void_p), int(max_iters),
+                                              cache_path.encode() if cache_path else None, ctypes.byref(h),
+                                              ctypes.byref(rep)))
+        choice = {"groups": rep.groups, "iters": rep.iters, "ms": rep.ms, "from_cache": bool(rep.from_cache)}
+        return cls(ctx, meshes, _handle=h), choice
+
+    @property
+    def config(self):
+        g, i = ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.gbem_batch_config(self.h, ctypes.byref(g), ctypes.byref(i)))
+        return {"groups": g.value, "iters": i.value}
 
     def run(self, eps_r: float, stream=None):
         """List of capacitance matrices (farads) and the residual of each."""

@@ -58,3 +58,45 @@ def test_batch_mixed_sizes_and_padding(ctx):
     for (boxes, params), C in zip(structs, Cs):
         a, g, c = O.mesh_boxes(boxes, **params)
         assert _err(C, O.capacitance(a, g, c, 1.0)) <= 1e-6
+
+
+def test_grouped_batch_equals_single_group(ctx):
+    """Splitting a batch into groups (parts whose graphs run concurrently)
+    changes no result: every structure's computation is its own."""
+    from paper_2203_11733_gb300 import gbem
+    structs = W.batch_small_structures(seed=321, count=9, n_lo=150, n_hi=900)
+    meshes = [ctx.mesh(b, p) for b, p in structs]
+    one = gbem.Batch(ctx, meshes, iters=3, groups=1)
+    three = gbem.Batch(ctx, meshes, iters=3, groups=3)
+    assert three.config == {"groups": 3, "iters": 3}
+    C1, r1 = one.run(W.EPS_R_SIO2)
+    C3, r3 = three.run(W.EPS_R_SIO2)
+    for a, b in zip(C1, C3):
+        assert np.array_equal(a, b)
+    assert np.array_equal(r1, r3)
+    one.close()
+    three.close()
+
+
+def test_autotune_picks_a_converging_configuration_and_caches_it(ctx, tmp_path):
+    from paper_2203_11733_gb300 import gbem
+    structs = W.batch_small_structures(seed=555, count=12, n_lo=150, n_hi=900)
+    meshes = [ctx.mesh(b, p) for b, p in structs]
+    cache = str(tmp_path / "batch_tuning.txt")
+    batch, choice = gbem.Batch.autotune(ctx, meshes, max_iters=3, cache_path=cache)
+    assert choice["groups"] in (1, 2, 4) and 1 <= choice["iters"] <= 3 and choice["ms"] > 0
+    assert not choice["from_cache"]
+    assert batch.config == {"groups": choice["groups"], "iters": choice["iters"]}
+    Cs, res = batch.run(W.EPS_R_SIO2)
+    assert np.all(res <= 1e-12), res
+    ref = gbem.Batch(ctx, meshes, iters=3)
+    Cr, _ = ref.run(W.EPS_R_SIO2)
+    for a, b in zip(Cs, Cr):
+        assert _err(a, b) <= 1e-9
+    batch.close()
+    ref.close()
+    # the same batch again: the cached choice, without timing runs
+    batch2, choice2 = gbem.Batch.autotune(ctx, meshes, max_iters=3, cache_path=cache)
+    assert choice2["from_cache"]
+    assert (choice2["groups"], choice2["iters"]) == (choice["groups"], choice["iters"])
+    batch2.close()
