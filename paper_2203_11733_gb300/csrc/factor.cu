@@ -417,6 +417,87 @@ __device__ void diag_tail(float* __restrict__ L, int ld, int k0, const float* __
     if (tid == 0) *(volatile unsigned*)pflag_c = token;
 }
 
+// A helper CTA of step k (k0 = 64 (k+1), the diagonal block the step's
+// diagonal CTA factors): strip row s of step k+1, L_c,k+1 = A_c,k+1 Linv^T
+// with c = k+2+s, into lsT[s] (t-major); for s = 0 also the lookahead panel
+// work of row block k+2 (L_k+2,k+1 into L, A_k+2,k+2 -= L L^T, then
+// pflag_c = token + 1).  The blocks of A are read as soon as the panel rows
+// (and, when it holds A_k+2,k+2, tile (0, 0)) are done, before the inverse is
+// ready, so only the inverse's read and the products follow the diagonal
+// block.  All 256 threads; shared memory: three t-major blocks.
+__device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* __restrict__ Linv,
+                            float* __restrict__ lsT_s, int sidx, const unsigned* pflag_row, const unsigned* ready,
+                            const unsigned* dflag, unsigned token, unsigned* pflag_c, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv[c][t]
+    float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_c,k+1[r][t]
+    float(*lT)[PT] = ivT + 2 * NB;                                // lT[t][r] = L_c,k+1[r][t]
+    const int tid = threadIdx.x;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const int rc = k0 + NB * (1 + sidx);
+    const bool look = sidx == 0;
+    if (!wait_flags(pflag_row, 1, token, status)) return;
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+        const int t = e >> 4, r = (e & 15) * 4;
+        *reinterpret_cast<float4*>(&aT[t][r]) =
+            __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld));
+    }
+    float4 cc[4];
+    if (look) {
+        if (ready && !wait_flags(ready, 1, 1u, status)) return;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            cc[v] = __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld));
+    }
+    if (!wait_flags(dflag, 1, token, status)) return;
+    const float* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x)
+        *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = __ldcg(reinterpret_cast<const float4*>(Lb) + e);
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int t = 0; t < tc + 4; ++t) {   // the inverse is lower triangular
+        const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+        const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+        *reinterpret_cast<float4*>(lsT_s + (size_t)(tc + v) * NB + tr) = q;
+        if (look) {
+            *reinterpret_cast<float4*>(&lT[tc + v][tr]) = q;
+            *reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(k0 + tc + v) * ld) = q;
+        }
+    }
+    if (!look) return;
+    __syncthreads();   // lT complete
+    float acc2[4][4] = {};
+    for (int t = 0; t < NB; ++t) {
+        const float4 x = *reinterpret_cast<const float4*>(&lT[t][tr]);
+        const float4 y = *reinterpret_cast<const float4*>(&lT[t][tc]);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        float4 o = cc[v];
+        o.x -= acc2[0][v];
+        o.y -= acc2[1][v];
+        o.z -= acc2[2][v];
+        o.w -= acc2[3][v];
+        *reinterpret_cast<float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld) = o;
+    }
+    if (tid == 0) *(volatile unsigned*)pflag_c = token + 1;
+}
+
 constexpr size_t kStripSmem = 4 * NB * PT * sizeof(float);
 constexpr size_t kPanelRowSmem = 4 * NB * PT * sizeof(float);
 // every role of factor_step within one dynamic allocation: two CTAs per SM
@@ -656,7 +737,8 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
                                                    unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
-                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ tdone)
+                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ tdone,
+                                                   unsigned* __restrict__ dflag)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -682,14 +764,20 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     if (t == npanel) {
         if (!wait_flags(pflag + k + 1, 1, token, status)) return;
         potrf_body<float>(L, ld, (k + 1) * NB, Linv, info);
-        if (ns_next > 0) {
-            if (!wait_flags(pflag + k + 2, ns_next, token, status)) return;
-            diag_tail(L, ld, (k + 1) * NB, Linv, lsT_out, ns_next, sw == 1 ? tdone + k : nullptr, pflag + k + 2,
-                      token + 1, status);
+        __syncthreads();   // the inverse is stored
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(dflag + k, token);
         }
         return;
     }
-    const long long b = t - npanel - 1;
+    if (t <= npanel + ns_next) {
+        const int sidx = t - npanel - 1;
+        tail_helper(L, ld, (k + 1) * NB, Linv, lsT_out + (size_t)sidx * NB * NB, sidx, pflag + k + 2 + sidx,
+                    sw == 1 ? tdone + k : nullptr, dflag + k, token, pflag + k + 2, status);
+        return;
+    }
+    const long long b = t - npanel - 1 - ns_next;
     int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
@@ -735,9 +823,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
         unsigned* tickets = pflag + nblk;
         unsigned* tdone = tickets + nblk;
+        unsigned* dflag = tdone + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        if ((e = cudaMemsetAsync(pflag, 0, 3 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
         // strip width of step k: one or two column blocks, leaving an even
         // number of blocks (whole 128-tiles) for the tensor cores
         auto strip_width = [nblk](int k) {
@@ -760,7 +849,8 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
             float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)(m + tiles));   // m - 1 panel rows, the diagonal CTA, the tiles
+            // m - 1 panel rows, the diagonal CTA, its strip-row helpers, the tiles
+            cfg.gridDim = dim3((unsigned)(m + strip_width(k + 1) + tiles));
             cfg.blockDim = dim3(256);
             cfg.dynamicSmemBytes = kFactorSmem;
             cfg.stream = s;
@@ -768,7 +858,8 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cfg.numAttrs = 1;
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
-                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets, tdone)) !=
+                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets, tdone,
+                                        dflag)) !=
                 cudaSuccess)
                 return e;
             count_launch();
@@ -850,10 +941,10 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets and
-    // first-tile flags
+    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets,
+    // first-tile flags and diagonal-block flags
     return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
-           3 * (size_t)(np / NB) * sizeof(unsigned);
+           4 * (size_t)(np / NB) * sizeof(unsigned);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
