@@ -295,29 +295,32 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 waits until every flag in f[0..n) has reached `token` (bounded);
-// the CTA then proceeds together.  False (and status = GBEM_ERR_TIMEOUT) if
-// a wait gave up or another CTA's already had.
-__device__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
+// Waits until every flag in f0[0..n0) and f1[0..n1) has reached `token`
+// (bounded; n0 + n1 <= blockDim.x): thread q polls one flag, so the polls'
+// latencies overlap, and the CTA then proceeds together.  False (and status =
+// GBEM_ERR_TIMEOUT) if a wait gave up or another CTA's already had.
+__device__ bool wait_flags(const unsigned* f0, int n0, const unsigned* f1, int n1, unsigned token, int* status)
 {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        for (int q = 0; q < n && ok; ++q) {
-            long long spins = 0;
-            while (ld_acquire(f + q) < token) {
-                if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
-                    atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(20);
+    const int q = threadIdx.x;
+    int ok = 1;
+    if (q < n0 + n1) {
+        const unsigned* f = q < n0 ? f0 + q : f1 + (q - n0);
+        long long spins = 0;
+        while (ld_acquire(f) < token) {
+            if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
+                atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            __nanosleep(20);
         }
-        s_ok = ok;
     }
-    __syncthreads();
-    return s_ok != 0;
+    return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
+{
+    return wait_flags(f, n, nullptr, 0, token, status);
 }
 
 constexpr int PT = NB + 4;   // padded row of a t-major 64 x 64 block in shared memory
@@ -750,6 +753,11 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     const int npanel = nblk - k - 2;
     const unsigned token = (unsigned)k + 1;
     int* status = info + 3;
+    // roles without tensor-core work give up the CTA's TMEM allocation permit
+    // at once: while a CTA holds it, no second CTA of the kernel is placed on
+    // its SM
+    if (t <= npanel + ns_next && threadIdx.x < 32)
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (t < npanel) {
         const int i = k + 2 + t;
         panel_row(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, tc_smem);
@@ -783,9 +791,9 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     while ((long long)I * (I + 1) / 2 > b) --I;
     const int J = (int)(b - (long long)I * (I + 1) / 2);
     const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
-    if (!wait_flags(pflag + bI, 2, token, status) || !wait_flags(pflag + bJ, 2, token, status)) return;
     const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem)) {
+    auto ready = [&]() { return wait_flags(pflag + bI, 2, pflag + bJ, 2, token, status); };
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready)) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
         return;
     }

@@ -160,10 +160,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity 
 // C[rI + .., rJ + ..] -= A_I A_J^T for one 128 x 128 tile.  I and J index the
 // 128-row blocks of the split panel (rows rI = r0 + 128 I, rJ = r0 + 128 J);
 // stage_stride is the byte distance between the two K stages of a part.
-// 256 threads.  Returns false if a bounded wait gave up.
+// 256 threads.  `ready()` (called by every thread, returns whether the split
+// panel rows this tile reads are written) is called after the accumulator is
+// allocated, the CTA has given up its TMEM allocation permit and the tile of C
+// is loaded into registers: C is not written by this launch before the tile,
+// and a CTA that holds the permit keeps the SM from taking a second CTA of the
+// kernel.  Returns false if a wait gave up.
+template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
-                          unsigned char* smem)
+                          unsigned char* smem, Ready ready)
 {
     unsigned char* a_hi = smem;
     unsigned char* a_lo = smem + HALF_BYTES;
@@ -195,28 +201,31 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
         mbar_init(bar_ld, 1);
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // the split may have been written by other CTAs of this launch
-        // (generic-proxy stores): order them before the async-proxy copies
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        issue(0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     // this thread's 64 entries of C (row q * 32 + lane, columns 64 half ..),
-    // loaded now so that their latency overlaps the copies and MMAs
+    // loaded now so that their latency overlaps the wait, the copies and MMAs
     const int q = warp & 3, half = warp >> 2;
     const int row = q * 32 + (tid & 31);
     float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
     float cpre[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
+    int ok = ready() ? 1 : 0;
+    int loads = ok, commits = 0;
+    if (ok && tid == 32) {
+        // the split was written by other CTAs of this launch (generic-proxy
+        // stores): order them before the async-proxy copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        issue(0);
+    }
 
     // thread 0: stage 0 MMAs, then (once they have read shared memory) the
     // stage-1 copies into the same buffers, then the stage-1 MMAs
-    int ok = 1, loads = 1, commits = 0;
-    if (tid == 0) {
+    if (ok && tid == 0) {
         const uint32_t idesc = make_idesc();
         const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
         for (int h = 0; h < 2 && ok; ++h) {
