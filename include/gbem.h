@@ -117,6 +117,19 @@ gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget,
 void gbem_destroy(gbem_ctx* ctx);
 const char* gbem_last_error(const gbem_ctx* ctx);
 gbem_status gbem_set_tuning(gbem_ctx* ctx, const gbem_tuning* t);
+/* Mixed mode: overlap the assembly with the factorisation.  gbem_assemble
+ * assembles the first columns (about `first_fraction` of the lower entries,
+ * at least three 64-column blocks) on the caller's stream and the rest in
+ * `groups - 1` column groups of equal entry counts on a low-priority stream
+ * of the context; gbem_factor then runs on a high-priority stream and adds
+ * each group into the FP32 copy before the first elimination step that reads
+ * it (Sec. 3.4 entries, Cholesky blocked by 64 columns).  groups <= 1 turns
+ * the overlap off.  Calls on a stream under graph capture never overlap.
+ * Default: off (groups 1, first_fraction 0.08): on a GB300 the co-running
+ * assembly tiles slow the latency-bound elimination steps by more than the
+ * assembly time they hide.  The environment variable GBEM_OVERLAP
+ * ("groups[,first_fraction]") sets a context's initial values. */
+gbem_status gbem_set_overlap(gbem_ctx* ctx, int groups, double first_fraction);
 /* Bytes currently held by the context's handles. */
 size_t gbem_bytes_in_use(const gbem_ctx* ctx);
 

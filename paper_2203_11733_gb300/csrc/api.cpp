@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -302,6 +304,98 @@ void ctx_free(gbem_ctx* ctx, void* p, size_t bytes, cudaStream_t s)
     ctx->in_use -= std::min(ctx->in_use, bytes);
 }
 
+// ---- assembly overlapped with the factorisation (mixed mode)
+
+// Column groups [b_g, b_g+1) in elements, 64-aligned, b_0 = 0, last = np: the
+// first holds about `first` of the lower 64-blocks (at least three block
+// columns, which the first elimination step reads outside its tiles), the
+// others equal shares of the rest.  One group when the overlap is off or the
+// matrix is small.
+static std::vector<int> overlap_plan(const gbem_ctx* ctx, int np)
+{
+    const int nblk = np / 64;
+    std::vector<int> b{0};
+    if (ctx->overlap_groups <= 1 || nblk < 16) {
+        b.push_back(np);
+        return b;
+    }
+    // block column c holds nblk - c lower blocks
+    const double total = 0.5 * nblk * (nblk + 1.0);
+    auto before = [nblk](int c) { return c * (double)nblk - 0.5 * c * (c - 1.0); };
+    int c1 = 3;
+    while (c1 < nblk - 1 && before(c1) < ctx->overlap_first * total) ++c1;
+    b.push_back(c1 * 64);
+    const int rest = ctx->overlap_groups - 1;
+    const double w0 = before(c1);
+    for (int gi = 1; gi < rest; ++gi) {
+        const double want = w0 + (total - w0) * gi / rest;
+        int c = b.back() / 64 + 1;
+        while (c < nblk - 1 && before(c) < want) ++c;
+        if (c * 64 > b.back() && c < nblk) b.push_back(c * 64);
+    }
+    if (b.back() < np) b.push_back(np);
+    return b;
+}
+
+static bool overlap_streams(gbem_ctx* ctx)
+{
+    if (ctx->side && ctx->fast) return true;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        (!ctx->side && cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least) != cudaSuccess) ||
+        (!ctx->fast && cudaStreamCreateWithPriority(&ctx->fast, cudaStreamNonBlocking, greatest) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// `to` waits for the work `from` has queued so far.
+static cudaError_t stream_after(cudaStream_t to, cudaStream_t from)
+{
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev, from)) == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
+}
+
+// `s` waits for every column group still being assembled.
+static cudaError_t join_groups(gbem_matrix_t* m, cudaStream_t s)
+{
+    for (auto& gr : m->groups) {
+        cudaError_t e = cudaStreamWaitEvent(s, gr.ev, 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Before elimination step k: add in the groups whose first block column c0
+// is read finally by step c0 - 1 (its diagonal block factor and lookahead row).
+static cudaError_t add_groups_hook(void* user, int k, cudaStream_t s)
+{
+    gbem_matrix_t* m = static_cast<gbem_matrix_t*>(user);
+    for (auto& gr : m->groups) {
+        if (gr.added || gr.c0 / 64 - 1 > k) continue;
+        cudaError_t e = cudaStreamWaitEvent(s, gr.ev, 0);
+        if (e == cudaSuccess) e = launch_add_hi(m->A64, m->A32, m->np, gr.c0, gr.c1, s);
+        if (e != cudaSuccess) return e;
+        gr.added = true;
+    }
+    return cudaSuccess;
+}
+
+static bool stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return true;   // unknown: do not fork
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
 // ------------------------------------------------------------------ ABI
 
 extern "C" {
@@ -320,6 +414,15 @@ gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget, gbem_allo
     ctx->free_fn = free_fn;
     ctx->user = user;
     ctx->tune = default_tuning();
+    // GBEM_OVERLAP="groups[,first_fraction]" overrides the overlap defaults
+    if (const char* ov = std::getenv("GBEM_OVERLAP")) {
+        int gr = ctx->overlap_groups;
+        double fr = ctx->overlap_first;
+        if (std::sscanf(ov, "%d,%lf", &gr, &fr) >= 1 && gr <= 64 && fr > 0.0 && fr < 1.0) {
+            ctx->overlap_groups = gr;
+            ctx->overlap_first = fr;
+        }
+    }
     if (device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || device >= count) {
@@ -347,7 +450,20 @@ void gbem_destroy(gbem_ctx* ctx)
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
+    if (ctx->side || ctx->fast) {
+        DeviceGuard g(ctx->device);
+        if (ctx->side) cudaStreamDestroy(ctx->side);
+        if (ctx->fast) cudaStreamDestroy(ctx->fast);
+    }
     delete ctx;
+}
+
+gbem_status gbem_set_overlap(gbem_ctx* ctx, int groups, double first_fraction)
+{
+    if (!ctx || !(first_fraction > 0.0 && first_fraction < 1.0) || groups > 64) return GBEM_ERR_ARG;
+    ctx->overlap_groups = groups;
+    ctx->overlap_first = first_fraction;
+    return GBEM_OK;
 }
 
 const char* gbem_last_error(const gbem_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
@@ -555,14 +671,36 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
         return GBEM_ERR_OOM;
     }
     PhaseTimer pt(ctx, GBEM_PHASE_ASSEMBLE, s);
+    const double qn = prec == GBEM_MIXED ? ctx->tune.q_near_mixed : ctx->tune.q_near_fp64;
+    std::vector<int> plan{0, m->np};
+    if (prec == GBEM_MIXED && !stream_capturing(s)) {
+        plan = overlap_plan(ctx, m->np);
+        if (plan.size() > 2 && !overlap_streams(ctx)) plan = {0, m->np};
+    }
     bool ok = cuda_ok(ctx, cudaMemsetAsync(m->dflags, 0, 4 * sizeof(int), s), "memset") &&
               cuda_ok(ctx, cudaMemsetAsync(m->dcounts, 0, 8 * sizeof(unsigned long long), s), "memset") &&
-              cuda_ok(ctx, launch_pad(m->A64, m->A32, m->n, m->np, s), "pad") &&
-              cuda_ok(ctx,
-                      launch_assemble(mesh->dev, m->np, prec,
-                                      prec == GBEM_MIXED ? ctx->tune.q_near_mixed : ctx->tune.q_near_fp64,
-                                      m->A64, m->A32, m->dcounts, s),
-                      "assemble");
+              cuda_ok(ctx, launch_pad(m->A64, m->A32, m->n, m->np, s), "pad");
+    if (ok && plan.size() <= 2) {
+        ok = cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s), "assemble");
+    } else if (ok) {
+        // the first group on the caller's stream, the others (float pairs
+        // only) on the side stream while the factorisation runs
+        ok = cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s, 0, plan[1]),
+                     "assemble") &&
+             cuda_ok(ctx, stream_after(ctx->side, s), "fork");
+        for (size_t gi = 1; ok && gi + 1 < plan.size(); ++gi) {
+            gbem_matrix_t::Group gr{plan[gi], plan[gi + 1], nullptr, false};
+            ok = cuda_ok(ctx, cudaEventCreateWithFlags(&gr.ev, cudaEventDisableTiming), "event");
+            if (!ok) break;
+            m->groups.push_back(gr);
+            ok = cuda_ok(ctx,
+                         launch_assemble(mesh->dev, m->np, prec, qn, m->A64, nullptr, m->dcounts, ctx->side, gr.c0,
+                                         gr.c1),
+                         "assemble") &&
+                 cuda_ok(ctx, cudaEventRecord(gr.ev, ctx->side), "event");
+        }
+        if (ok) m->zero_col = plan[1];
+    }
     if (!ok) {
         gbem_matrix_destroy(m);
         return GBEM_ERR_CUDA;
@@ -600,10 +738,24 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
         if (!m->Linv) m->Linv = mat_alloc<float>(m, nblk * m->nb * m->nb, s);
         if (!m->split) m->split = mat_alloc<unsigned char>(m, cholesky_f32_split_bytes(m->np), s);
         if (!m->Linv || !m->split) return GBEM_ERR_OOM;
-        if (!cuda_ok(ctx,
-                     launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, m->split, s),
-                     "cholesky"))
-            return GBEM_ERR_CUDA;
+        if (m->groups.empty()) {
+            if (!cuda_ok(ctx,
+                         launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags,
+                                             m->split, s),
+                         "cholesky"))
+                return GBEM_ERR_CUDA;
+        } else {
+            // on the high-priority stream, so that its steps take the SMs
+            // first as the side stream's assembly tiles finish; each group
+            // is added in before the step that first reads it
+            if (!cuda_ok(ctx, stream_after(ctx->fast, s), "fork") ||
+                !cuda_ok(ctx,
+                         launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags,
+                                             m->split, ctx->fast, m->zero_col, add_groups_hook, m),
+                         "cholesky") ||
+                !cuda_ok(ctx, join_groups(m, ctx->fast), "join") || !cuda_ok(ctx, stream_after(s, ctx->fast), "join"))
+                return GBEM_ERR_CUDA;
+        }
     }
     m->factored = true;
     m->last = s;
@@ -685,7 +837,8 @@ gbem_status gbem_matrix_download(gbem_matrix_t* m, double* host)
     gbem_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
     const int n = m->n, np = m->np;
-    if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync")) return GBEM_ERR_CUDA;
+    if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync"))
+        return GBEM_ERR_CUDA;
     // column j of the lower triangle: rows j..n-1
     if (!cuda_ok(ctx,
                  cudaMemcpy2D(host, sizeof(double) * n, m->A64, sizeof(double) * np, sizeof(double) * n, n,
@@ -711,7 +864,7 @@ gbem_status gbem_matrix_status(gbem_matrix_t* m)
     gbem_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
     int flags[4] = {0, 0, 0, 0};
-    if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
+    if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
         !cuda_ok(ctx, cudaMemcpy(flags, m->dflags, sizeof(flags), cudaMemcpyDeviceToHost), "d2h"))
         return GBEM_ERR_CUDA;
     if (flags[0]) return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "Cholesky met a non-positive pivot");
@@ -727,7 +880,7 @@ gbem_status gbem_matrix_info(gbem_matrix_t* m, int* n, long long* counts)
     if (n) *n = m->n;
     if (counts) {
         unsigned long long c[8] = {};
-        if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
+        if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
             !cuda_ok(ctx, cudaMemcpy(c, m->dcounts, sizeof(c), cudaMemcpyDeviceToHost), "d2h"))
             return GBEM_ERR_CUDA;
         for (int k = 0; k < 7; ++k) counts[k] = (long long)c[k];
@@ -739,7 +892,13 @@ void gbem_matrix_destroy(gbem_matrix_t* m)
 {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
-    if (m->last) cudaStreamSynchronize(m->last);
+    if (m->last) {
+        join_groups(m, m->last);
+        cudaStreamSynchronize(m->last);
+    } else {
+        for (auto& gr : m->groups) cudaEventSynchronize(gr.ev);
+    }
+    for (auto& gr : m->groups) cudaEventDestroy(gr.ev);
     for (auto& a : m->allocs) ctx_free(m->ctx, a.first, a.second, m->last);
     delete m;
 }

@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
                                                    unsigned* __restrict__ tickets, unsigned* __restrict__ tdone,
-                                                   unsigned* __restrict__ dflag)
+                                                   unsigned* __restrict__ dflag, int zero_col)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -793,7 +793,8 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
     const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
     auto ready = [&]() { return wait_flags(pflag + bI, 2, pflag + bJ, 2, token, status); };
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready)) {
+    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready,
+                       k == 0 ? zero_col : 1 << 30)) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
         return;
     }
@@ -807,7 +808,8 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
 }
 
 template <typename T>
-cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s)
+cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s,
+                     int zero_col = 1 << 30, StepHook pre_step = nullptr, void* hook_user = nullptr)
 {
     const int nblk = np / NB;
     const size_t smem = 2 * NB * (NB + 1) * sizeof(T);
@@ -856,6 +858,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             const long long tiles = nt * (nt + 1) / 2;
             float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
             float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
+            if (pre_step && (e = pre_step(hook_user, k, s)) != cudaSuccess) return e;
             cudaLaunchConfig_t cfg = {};
             // m - 1 panel rows, the diagonal CTA, its strip-row helpers, the tiles
             cfg.gridDim = dim3((unsigned)(m + strip_width(k + 1) + tiles));
@@ -867,7 +870,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
                                         (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets, tdone,
-                                        dflag)) !=
+                                        dflag, zero_col)) !=
                 cudaSuccess)
                 return e;
             count_launch();
@@ -956,10 +959,13 @@ size_t cholesky_f32_split_bytes(int np)
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
-                                cudaStream_t s)
+                                cudaStream_t s, int zero_col, StepHook pre_step, void* hook_user)
 {
     if (nb != NB || np % tc::TM || !split) return cudaErrorInvalidValue;
-    return cholesky<float>(L, np, Linv, info, split, s);
+    // the columns the first step reads outside its tiles (the strip and the
+    // lookahead row, up to 3 blocks) must be assembled
+    if (zero_col < 3 * NB) return cudaErrorInvalidValue;
+    return cholesky<float>(L, np, Linv, info, split, s, zero_col, pre_step, hook_user);
 }
 
 cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long long* steps_dev,

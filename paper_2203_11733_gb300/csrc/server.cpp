@@ -194,6 +194,9 @@ gbem_status gbem_server_create(int device, size_t hbm_budget, int slots, gbem_pr
         gbem_ctx* ctx = nullptr;
         cudaStream_t s = nullptr;
         gbem_status st = gbem_create(&ctx, device, 0, srv_alloc, srv_free, nullptr);
+        // requests overlap one another; within a request the assembly is
+        // not overlapped with the factorisation
+        if (st == GBEM_OK) st = gbem_set_overlap(ctx, 1, 0.08);
         if (st == GBEM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = GBEM_ERR_CUDA;
         if (st != GBEM_OK) {
             if (ctx) gbem_destroy(ctx);

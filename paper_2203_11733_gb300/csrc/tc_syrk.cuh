@@ -165,11 +165,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity 
 // allocated, the CTA has given up its TMEM allocation permit and the tile of C
 // is loaded into registers: C is not written by this launch before the tile,
 // and a CTA that holds the permit keeps the SM from taking a second CTA of the
-// kernel.  Returns false if a wait gave up.
+// kernel.  Columns from zero_col on are taken as zero instead of read (C
+// not assembled yet).  Returns false if a wait gave up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
-                          unsigned char* smem, Ready ready)
+                          unsigned char* smem, Ready ready, int zero_col)
 {
     unsigned char* a_hi = smem;
     unsigned char* a_lo = smem + HALF_BYTES;
@@ -212,8 +213,13 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     const int row = q * 32 + (tid & 31);
     float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
     float cpre[64];
+    if (rJ + half * 64 < zero_col) {
 #pragma unroll
-    for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
+        for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) cpre[i] = 0.f;
+    }
     int ok = ready() ? 1 : 0;
     int loads = ok, commits = 0;
     if (ok && tid == 32) {

@@ -82,6 +82,7 @@ _SIGS = {
     "gbem_destroy": (None, [_P]),
     "gbem_last_error": (ctypes.c_char_p, [_P]),
     "gbem_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_Tuning)]),
+    "gbem_set_overlap": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "gbem_bytes_in_use": (ctypes.c_size_t, [_P]),
     "gbem_mesh": (ctypes.c_int, [_P, ctypes.POINTER(_Box), ctypes.c_int, ctypes.POINTER(_MeshParams),
                                  ctypes.POINTER(_P)]),
@@ -240,6 +241,12 @@ class Context:
     def set_tuning(self, q_near_fp64=0.0, q_near_mixed=0.0, ir_tol=0.0, ir_max_iter=0, nb=0):
         t = _Tuning(q_near_fp64, q_near_mixed, ir_tol, ir_max_iter, nb)
         self.check(self.lib.gbem_set_tuning(self.h, ctypes.byref(t)))
+
+    def set_overlap(self, groups: int = 1, first_fraction: float = 0.08):
+        """Mixed mode: assemble all but the first ~first_fraction of the entries
+        in groups - 1 column groups while the factorisation runs (groups <= 1,
+        the default: off)."""
+        self.check(self.lib.gbem_set_overlap(self.h, int(groups), float(first_fraction)))
 
     def bytes_in_use(self) -> int:
         return int(self.lib.gbem_bytes_in_use(self.h))
