@@ -425,17 +425,21 @@ __device__ void diag_tail(float* __restrict__ L, int ld, int k0, const float* __
 // with c = k+2+s, into lsT[s] (t-major); for s = 0 also the lookahead panel
 // work of row block k+2 (L_k+2,k+1 into L, A_k+2,k+2 -= L L^T, then
 // pflag_c = token + 1).  The blocks of A are read as soon as the panel rows
-// (and, when it holds A_k+2,k+2, tile (0, 0)) are done, before the inverse is
-// ready, so only the inverse's read and the products follow the diagonal
-// block.  All 256 threads; shared memory: three t-major blocks.
+// are done, before the inverse is ready, so only the inverse's read and the
+// products follow the diagonal block.  When block (k+2, k+2) lies in step k's
+// tensor-core tile (0, 0), lk points at L_k+2,k (step k's panel row k+2) and
+// the helper applies step k's update to the block too, before the inverse is
+// ready; the tile leaves that quadrant alone.  All 256 threads; shared
+// memory: four t-major blocks.
 __device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* __restrict__ Linv,
-                            float* __restrict__ lsT_s, int sidx, const unsigned* pflag_row, const unsigned* ready,
+                            float* __restrict__ lsT_s, int sidx, const unsigned* pflag_row, const float* lk,
                             const unsigned* dflag, unsigned token, unsigned* pflag_c, int* status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem_raw);   // ivT[t][c] = Linv[c][t]
     float(*aT)[PT] = ivT + NB;                                    // aT[t][r] = A_c,k+1[r][t]
     float(*lT)[PT] = ivT + 2 * NB;                                // lT[t][r] = L_c,k+1[r][t]
+    float(*lkT)[PT] = ivT + 3 * NB;                               // lkT[t][r] = L_c,k[r][t], then A_cc
     const int tid = threadIdx.x;
     const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
     const int rc = k0 + NB * (1 + sidx);
@@ -446,12 +450,42 @@ __device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* 
         *reinterpret_cast<float4*>(&aT[t][r]) =
             __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + r) + (size_t)(k0 + t) * ld));
     }
-    float4 cc[4];
     if (look) {
-        if (ready && !wait_flags(ready, 1, 1u, status)) return;
+        float4 cc[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             cc[v] = __ldcg(reinterpret_cast<const float4*>(L + (size_t)(rc + tr) + (size_t)(rc + tc + v) * ld));
+        if (lk) {
+            for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+                const int t = e >> 4, r = (e & 15) * 4;
+                *reinterpret_cast<float4*>(&lkT[t][r]) =
+                    __ldcg(reinterpret_cast<const float4*>(lk + (size_t)r + (size_t)t * ld));
+            }
+            __syncthreads();
+            // step k's update of A_cc: A_cc -= L_ck L_ck^T
+            float acc0[4][4] = {};
+#pragma unroll 4
+            for (int t = 0; t < NB; ++t) {
+                const float4 x = *reinterpret_cast<const float4*>(&lkT[t][tr]);
+                const float4 y = *reinterpret_cast<const float4*>(&lkT[t][tc]);
+                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc0[u][v] += xs[u] * ys[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                cc[v].x -= acc0[0][v];
+                cc[v].y -= acc0[1][v];
+                cc[v].z -= acc0[2][v];
+                cc[v].w -= acc0[3][v];
+            }
+            __syncthreads();   // lkT is read
+        }
+        // A_cc waits in shared memory for the lookahead update
+#pragma unroll
+        for (int v = 0; v < 4; ++v) *reinterpret_cast<float4*>(&lkT[tc + v][tr]) = cc[v];
     }
     if (!wait_flags(dflag, 1, token, status)) return;
     const float* Lb = Linv + (size_t)(k0 / NB) * NB * NB;
@@ -491,7 +525,7 @@ __device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* 
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        float4 o = cc[v];
+        float4 o = *reinterpret_cast<const float4*>(&lkT[tc + v][tr]);
         o.x -= acc2[0][v];
         o.y -= acc2[1][v];
         o.z -= acc2[2][v];
@@ -716,32 +750,29 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
 // Elimination step k of the FP32 factorisation in one launch.  Row block
 // k+1 was already done by the previous launch (lookahead).  Every CTA draws a
 // ticket in the order the CTAs start (an atomic counter per step), and the
-// ticket gives its role (m = row blocks below diagonal block k):
+// ticket gives its role (m = row blocks below diagonal block k, ns = strip
+// width of step k+1):
 //   tickets 0 .. m-2   panel work of row block k + 2 + ticket (panel_row),
 //                      then a release flag pflag[i] = k + 1;
-//   ticket  m-1        factor and invert diagonal block k+1; after the flags
-//                      of row blocks k+2 .. k+1+ns, the ns strip rows of
-//                      step k+1 (into lsT_out) and the lookahead panel work of
-//                      row block k+2 for step k+1 (pflag[k+2] = k + 2), after
-//                      tile (0, 0) when that tile holds block (k+2, k+2);
-//   tickets >= m       one 128 x 128 lower tile of [r0, np)^2 each, after the
+//   ticket  m-1        factor and invert diagonal block k+1, then dflag[k];
+//   next ns tickets    helpers (tail_helper): the strip rows of step k+1 and,
+//                      for the first, the lookahead panel work of row block
+//                      k+2 (pflag[k+2] = k + 2);
+//   the rest           one 128 x 128 lower tile of [r0, np)^2 each, after the
 //                      flags of its four row blocks: 3xTF32 tensor-core update
-//                      with the split panel (tc_syrk.cuh); tile (0, 0) then
-//                      sets tdone[k].
-// Panel CTAs wait for nothing; tiles wait for panel tickets (smaller, so
-// already started); the diagonal CTA waits for panel tickets and for tile
-// (0, 0), the very next ticket: until that CTA starts, every started CTA
-// besides the diagonal one is a panel CTA, which finishes and frees its SM.
-// So the launch cannot deadlock however many CTAs are resident.  Waits are
-// bounded; one that gives up sets status GBEM_ERR_TIMEOUT and its CTA skips
-// its work.
+//                      with the split panel (tc_syrk.cuh).
+// Every wait is on a smaller ticket, a CTA that has already started: panel
+// CTAs wait for nothing, the diagonal CTA for the previous launch, helpers
+// for their panel row and the diagonal CTA, tiles for panel rows.  So the
+// launch cannot deadlock however many CTAs are resident.  Waits are bounded;
+// one that gives up sets status GBEM_ERR_TIMEOUT and its CTA skips its work.
 __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
                                                    int* __restrict__ info, int nblk, int sw, int r0,
                                                    unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
-                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ tdone,
-                                                   unsigned* __restrict__ dflag, int zero_col)
+                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ dflag,
+                                                   int zero_col)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -781,8 +812,10 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     }
     if (t <= npanel + ns_next) {
         const int sidx = t - npanel - 1;
+        // with a strip one block wide, block (k+2, k+2) lies in tile (0, 0)
+        const float* lk = sw == 1 ? L + (size_t)((k + 2) * NB) + (size_t)(k * NB) * ld : nullptr;
         tail_helper(L, ld, (k + 1) * NB, Linv, lsT_out + (size_t)sidx * NB * NB, sidx, pflag + k + 2 + sidx,
-                    sw == 1 ? tdone + k : nullptr, dflag + k, token, pflag + k + 2, status);
+                    lk, dflag + k, token, pflag + k + 2, status);
         return;
     }
     const long long b = t - npanel - 1 - ns_next;
@@ -793,17 +826,12 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
     const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
     auto ready = [&]() { return wait_flags(pflag + bI, 2, pflag + bJ, 2, token, status); };
+    // tile (0, 0) leaves block (k+2, k+2) to the lookahead helper when the
+    // strip is one block wide
     if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready,
-                       k == 0 ? zero_col : 1 << 30)) {
+                       k == 0 ? zero_col : 1 << 30, b == 0 && sw == 1)) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
         return;
-    }
-    if (b == 0) {
-        __syncthreads();   // the whole tile is stored
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release(tdone + k, 1u);
-        }
     }
 }
 
@@ -832,11 +860,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         float* lsT = reinterpret_cast<float*>(split + 2 * oper);   // 2 x (2 x 64 x 64)
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
         unsigned* tickets = pflag + nblk;
-        unsigned* tdone = tickets + nblk;
-        unsigned* dflag = tdone + nblk;
+        unsigned* dflag = tickets + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pflag, 0, 3 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
         // strip width of step k: one or two column blocks, leaving an even
         // number of blocks (whole 128-tiles) for the tensor cores
         auto strip_width = [nblk](int k) {
@@ -869,7 +896,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cfg.numAttrs = 1;
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
-                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets, tdone,
+                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets,
                                         dflag, zero_col)) !=
                 cudaSuccess)
                 return e;
@@ -952,10 +979,10 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets,
-    // first-tile flags and diagonal-block flags
+    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets
+    // and diagonal-block flags
     return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
-           4 * (size_t)(np / NB) * sizeof(unsigned);
+           3 * (size_t)(np / NB) * sizeof(unsigned);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,

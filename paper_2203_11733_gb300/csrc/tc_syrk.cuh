@@ -166,11 +166,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity 
 // is loaded into registers: C is not written by this launch before the tile,
 // and a CTA that holds the permit keeps the SM from taking a second CTA of the
 // kernel.  Columns from zero_col on are taken as zero instead of read (C
-// not assembled yet).  Returns false if a wait gave up.
+// not assembled yet).  With skip00 the top-left 64 x 64 quadrant of the tile
+// is neither read nor written (another CTA updates it).  Returns false if a
+// wait gave up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
-                          unsigned char* smem, Ready ready, int zero_col)
+                          unsigned char* smem, Ready ready, int zero_col, bool skip00)
 {
     unsigned char* a_hi = smem;
     unsigned char* a_lo = smem + HALF_BYTES;
@@ -212,11 +214,11 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     const int q = warp & 3, half = warp >> 2;
     const int row = q * 32 + (tid & 31);
     float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
+    const bool mine = !(skip00 && q < 2 && half == 0);   // warp-uniform
     float cpre[64];
-    if (rJ + half * 64 < zero_col) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
-    } else {
+    for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
+    if (rJ + half * 64 >= zero_col) {   // not assembled yet: the loaded values are discarded
 #pragma unroll
         for (int i = 0; i < 64; ++i) cpre[i] = 0.f;
     }
@@ -265,7 +267,7 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     if (ok) ok = mbar_wait_bounded(bar_mma, 1);
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    if (ok && mine) {
         // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
 #pragma unroll
         for (int cc = 0; cc < 64; cc += 16) {
