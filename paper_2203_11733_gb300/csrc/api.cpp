@@ -178,6 +178,12 @@ gbem_status ensure_solve_buffers(gbem_matrix_t* m, int nrhs, cudaStream_t s)
     m->X = mat_alloc<double>(m, np * nrhs, s);
     m->R = mat_alloc<double>(m, np * nrhs, s);
     m->B = mat_alloc<double>(m, np * nrhs, s);
+    m->dchk = mat_alloc<unsigned long long>(m, 2 * (size_t)nrhs + 1, s);
+    if (m->dchk &&
+        cudaMemsetAsync(m->dchk, 0, (2 * (size_t)nrhs + 1) * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GBEM_ERR_CUDA;
+    }
     // W: FP64 mode, solve vectors and work (2 x np x nrhs doubles); mixed
     // mode, FP32 solve vectors and work, then X as float pairs (4 x np x nrhs
     // floats): the same bytes
@@ -238,10 +244,10 @@ gbem_status solve_padded(gbem_matrix_t* m, int nrhs, cudaStream_t s, int* iters,
             !cuda_ok(ctx, launch_trsv_f32_guarded(Lf, Li, np, m->nb, W, nrhs, m->dsync, m->dflags + 3, done, s),
                      "trsv") ||
             !cuda_ok(ctx, launch_add_f32(W, np, nrhs, m->X, Xdf, done, s), "add") ||
-            !cuda_ok(ctx, launch_residual_df(reinterpret_cast<const float2*>(m->A64), np, m->B, Xdf, nrhs, m->R, done, s),
-                     "residual") ||
-            !cuda_ok(ctx, launch_ir_check(m->R, m->B, np, nrhs, m->dnorm, ctx->tune.ir_tol, m->dflags, s),
-                     "ir check"))
+            !cuda_ok(ctx,
+                     launch_residual_df(reinterpret_cast<const float2*>(m->A64), np, m->B, Xdf, nrhs, m->R, done, s,
+                                        m->dchk, m->dnorm, ctx->tune.ir_tol, m->dflags),
+                     "residual"))
             return GBEM_ERR_CUDA;
         // read the flags back: stop once converged.  The first two
         // iterations go out together (a converged iteration leaves the next

@@ -157,6 +157,7 @@ struct gbem_matrix_s {
     unsigned* dsync = nullptr;  // one flag per 64-row block for the persistent solves
     unsigned long long* dcounts = nullptr; // pair class counts (8)
     double* dnorm = nullptr;    // IR: [0] residual, [1..] scratch
+    unsigned long long* dchk = nullptr;   // IR test folded into the residual: 2 cap_rhs + 1 words
     // solve work buffers (np x cap_rhs)
     int cap_rhs = 0;
     double* X = nullptr;
@@ -255,9 +256,12 @@ cudaError_t launch_trsv_f32_guarded(const float* L, const float* Linv, int np, i
 cudaError_t launch_residual(const double* A, int np, const double* Bp, const double* X, int nrhs,
                             double* R, const int* done, cudaStream_t s);
 // R = B - A X with A and X stored as float pairs (mixed mode's FP64 storage),
-// in compensated FP32 arithmetic.
+// in compensated FP32 arithmetic.  With chk (2 nrhs + 1 zeroed words), the
+// refinement test of launch_ir_check is folded in: norm[0] = max over columns
+// of max|R| / max|B|, flags[2] += 1, flags[1] = 1 if that is at most tol.
 cudaError_t launch_residual_df(const float2* A, int np, const double* Bp, const float2* Xdf, int nrhs,
-                               double* R, const int* done, cudaStream_t s);
+                               double* R, const int* done, cudaStream_t s, unsigned long long* chk = nullptr,
+                               double* norm = nullptr, double tol = 0.0, int* flags = nullptr);
 cudaError_t launch_ir_check(const double* R, const double* Bp, int np, int nrhs, double* norm,
                             double tol, int* flags, cudaStream_t s);
 cudaError_t launch_indicator_rhs(const int32_t* cond, int n, int np, int n_cond, double* Bp,

@@ -748,11 +748,28 @@ struct DfRes {
         sizeof(Ring) > sizeof(double) * 8 * RT * RR ? sizeof(Ring) : sizeof(double) * 8 * RT * RR;
 };
 
+// The refinement's convergence test folded into the residual: per column c
+// the largest |R| and |B| (non-negative doubles ordered as their bit
+// patterns) are combined with atomicMax into chk[2 c], chk[2 c + 1]; the last
+// CTA of the launch (counted in chk[2 nrhs_all]) forms max_c |R|/|B|, stores
+// it in norm[0], counts the iteration in flags[2], sets flags[1] if it is at
+// most tol, and clears chk for the next call.
+struct IrCheck {
+    unsigned long long* chk = nullptr;   // 2 per column, then the CTA counter
+    int col0 = 0;                         // this launch's first column
+    int ncols = 0;                        // columns of every launch of the call
+    bool finalize = false;                // the call's last launch: test and clear
+    double* norm = nullptr;
+    double tol = 0.0;
+    int* flags = nullptr;
+};
+
 template <int RR>
 __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, int np, const double* __restrict__ Bp,
                                                  const float2* __restrict__ X, int nrhs, double* __restrict__ R,
-                                                 int blk)
+                                                 int blk, const IrCheck& ck)
 {
+    __shared__ unsigned long long smax[2][RR];
     constexpr int S = DfRes<RR>::STAGES;
     __shared__ __align__(16) unsigned char smem[DfRes<RR>::BYTES];
     auto& ring = *reinterpret_cast<typename DfRes<RR>::Ring*>(smem);
@@ -764,6 +781,7 @@ __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, i
     for (int c0 = 0; c0 < nrhs; c0 += RR) {
         const int nr = min(RR, nrhs - c0);
         __syncthreads();   // the previous pass is done reading its partial sums
+        if (tid < 2 * RR) smax[tid / RR][tid % RR] = 0ull;
         for (int e = tid; e < S * CT * RR; e += blockDim.x) {   // unused columns read as zero
             const int st = e / (CT * RR), r = (e / RR) % CT, c = e % RR;
             if (c >= nr) ring.xs[st][r][c] = make_float2(0.0f, 0.0f);
@@ -846,7 +864,41 @@ __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, i
             double sum = 0.0;
             for (int g = 0; g < 8; ++g) sum += part[g][r][c];
             size_t idx = (size_t)(i0 + r) + (size_t)(c0 + c) * np;
-            R[idx] = Bp[idx] - sum;
+            const double b = Bp[idx], rv = b - sum;
+            R[idx] = rv;
+            if (ck.chk) {
+                atomicMax(&smax[0][c], (unsigned long long)__double_as_longlong(fabs(rv)));
+                atomicMax(&smax[1][c], (unsigned long long)__double_as_longlong(fabs(b)));
+            }
+        }
+        if (ck.chk) {
+            __syncthreads();
+            if (tid < 2 * nr) {
+                const int c = tid % nr, w = tid / nr;
+                atomicMax(&ck.chk[2 * (ck.col0 + c0 + c) + w], smax[w][c]);
+                __threadfence();   // performed before this CTA is counted
+            }
+        }
+    }
+    if (!ck.chk) return;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        unsigned long long* counter = ck.chk + 2 * ck.ncols;
+        if (atomicAdd(counter, 1ull) == (unsigned long long)gridDim.x - 1) {
+            __threadfence();
+            if (ck.finalize) {
+                double worst = 0.0;
+                for (int c = 0; c < ck.ncols; ++c) {
+                    const double mr = __longlong_as_double((long long)atomicExch(&ck.chk[2 * c], 0ull));
+                    const double mb = __longlong_as_double((long long)atomicExch(&ck.chk[2 * c + 1], 0ull));
+                    worst = fmax(worst, (mb > 0.0) ? mr / mb : mr);
+                }
+                ck.norm[0] = worst;
+                ck.flags[2] += 1;
+                if (worst <= ck.tol) ck.flags[1] = 1;
+            }
+            *counter = 0ull;
         }
     }
 }
@@ -854,10 +906,10 @@ __device__ __forceinline__ void residual_df_body(const float2* __restrict__ A, i
 template <int RR>
 __global__ void __launch_bounds__(256) residual_df(const float2* __restrict__ A, int np,
                                                    const double* __restrict__ Bp, const float2* __restrict__ X,
-                                                   int nrhs, double* __restrict__ R, const int* done)
+                                                   int nrhs, double* __restrict__ R, const int* done, IrCheck ck)
 {
     if (done && *done) return;
-    residual_df_body<RR>(A, np, Bp, X, nrhs, R, blockIdx.x);
+    residual_df_body<RR>(A, np, Bp, X, nrhs, R, blockIdx.x, ck);
 }
 
 template <int RR>
@@ -1074,7 +1126,7 @@ __global__ void __launch_bounds__(256) residual_batched(BatchView v)
     const int b = sb;
     const long long o = v.voff[b];
     residual_df_body<RR>(reinterpret_cast<const float2*>(v.A64) + v.moff[b], v.np[b], v.B + o, v.Xdf + o, v.nc[b],
-                         v.R + o, (int)(blockIdx.x - v.rows_prefix[b]));
+                         v.R + o, (int)(blockIdx.x - v.rows_prefix[b]), IrCheck{});
 }
 
 // Final relative residual and capacitance of each structure (one CTA each).
@@ -1214,7 +1266,8 @@ cudaError_t launch_residual(const double* A, int np, const double* Bp, const dou
 }
 
 cudaError_t launch_residual_df(const float2* A, int np, const double* Bp, const float2* Xdf, int nrhs,
-                               double* R, const int* done, cudaStream_t s)
+                               double* R, const int* done, cudaStream_t s, unsigned long long* chk, double* norm,
+                               double tol, int* flags)
 {
     if (np % CT) return cudaErrorInvalidValue;
     for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
@@ -1222,10 +1275,20 @@ cudaError_t launch_residual_df(const float2* A, int np, const double* Bp, const 
         const double* Bc = Bp + (size_t)c0 * np;
         const float2* Xc = Xdf + (size_t)c0 * np;
         double* Rc = R + (size_t)c0 * np;
+        IrCheck ck;
+        if (chk) {
+            ck.chk = chk;
+            ck.col0 = c0;
+            ck.ncols = nrhs;
+            ck.finalize = c0 + MAXR >= nrhs;
+            ck.norm = norm;
+            ck.tol = tol;
+            ck.flags = flags;
+        }
         cudaEvent_t ev = trace_begin(s);
-        if (nr <= 4) residual_df<4><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
-        else if (nr <= 8) residual_df<8><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
-        else residual_df<16><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done);
+        if (nr <= 4) residual_df<4><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done, ck);
+        else if (nr <= 8) residual_df<8><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done, ck);
+        else residual_df<16><<<np / RT, 256, 0, s>>>(A, np, Bc, Xc, nr, Rc, done, ck);
         count_launch();
         // the lower triangle of A (float pairs) once, B and X read and R
         // written; each lower entry serves two products per right-hand side
