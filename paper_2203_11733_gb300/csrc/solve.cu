@@ -271,16 +271,163 @@ __device__ __forceinline__ void kahan_add(float (&acc)[R], float (&comp)[R], con
     }
 }
 
-// out[t][c] = sum_k iv[k][t] w[k][c] (TRANS) or iv[t][k] w[k][c]: the
-// diagonal-block inverse is stored with zeros above its diagonal, so all 64
-// terms are summed, unrolled, in four independent chains.
-template <int R, bool TRANS>
-__device__ __forceinline__ float apply_inv(const float (*iv)[NB + 1], const float (*w)[R], int t, int c)
+// Shared memory of the FP32 sweeps.  Per block row b the solution is split
+// as x_b = z_b - M_b x_p, with p the neighbouring row solved just before
+// (b - 1 forward, b + 1 backward), M_b = Linv_b L_bp (forward) or
+// Linv_b^T L_pb^T (backward), and z_b the inverse applied to the right-hand
+// side minus the compensated sum over every other earlier row.  M_b and z_b
+// are ready before x_p arrives, so the critical path from one row to the
+// next is one polled block and one 64-term dot product per output.  The row
+// of M_b a thread needs is held in its registers, and the vectors are laid
+// out so that a thread reads four of them with one 16-byte shared load (all
+// lanes of a warp read the same address).
+template <int R>
+struct SweepF32Smem {
+    float v[NB][R];            // solved block of another row, v[t][c]
+    float part[4][NB][R];      // partial sums of the four column quarters
+    float wT[R][NB];           // right-hand side minus the sums, wT[c][k]
+    float vT[R][NB];           // the neighbouring row's solved block, vT[c][k]
+    float lp[NB][NB + 4];      // L_bp (forward: lp[j][k] = L_bp[j][k]; backward: lp[j][k] = L_pb[k][j])
+    float m[NB][NB + 4];       // M_b, m[t][k]
+    float iv[NB][NB + 4];      // the inverse (forward) or its transpose (backward), iv[t][k]
+};
+template <int R>
+struct SweepBwdSmem {
+    SweepF32Smem<R> base;
+    float lt[NB][NB + 1];      // lt[r][t] = L[j0 + t][b0 + r]
+};
+
+// sum_k li[k] w[k] with w in shared memory (16-byte aligned), four chains
+__device__ __forceinline__ float dot64(const float (&li)[NB], const float* __restrict__ w)
 {
     float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < NB; ++k) a[k & 3] += (TRANS ? iv[k][t] : iv[t][k]) * w[k][c];
+    for (int k = 0; k < NB; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(w + k);
+        a[0] = fmaf(li[k], x.x, a[0]);
+        a[1] = fmaf(li[k + 1], x.y, a[1]);
+        a[2] = fmaf(li[k + 2], x.z, a[2]);
+        a[3] = fmaf(li[k + 3], x.w, a[3]);
+    }
     return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+// sum_k a[k] w[k] for two 16-byte aligned rows of shared memory
+__device__ __forceinline__ float dot64s(const float* __restrict__ a, const float* __restrict__ w)
+{
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < NB; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(a + k);
+        const float4 y = *reinterpret_cast<const float4*>(w + k);
+        s4[0] = fmaf(x.x, y.x, s4[0]);
+        s4[1] = fmaf(x.y, y.y, s4[1]);
+        s4[2] = fmaf(x.z, y.z, s4[2]);
+        s4[3] = fmaf(x.w, y.w, s4[3]);
+    }
+    return (s4[0] + s4[1]) + (s4[2] + s4[3]);
+}
+
+// aj[c] += l * v[c] for c < R, v 16-byte aligned
+template <int R>
+__device__ __forceinline__ void axpy_row(float (&aj)[R], float l, const float* __restrict__ v)
+{
+#pragma unroll
+    for (int c = 0; c < R; c += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(v + c);
+        aj[c] = fmaf(l, x.x, aj[c]);
+        if (c + 1 < R) aj[c + 1] = fmaf(l, x.y, aj[c + 1]);
+        if (c + 2 < R) aj[c + 2] = fmaf(l, x.z, aj[c + 2]);
+        if (c + 3 < R) aj[c + 3] = fmaf(l, x.w, aj[c + 3]);
+    }
+}
+
+// Row r of M_b into mrow: m[r][k] = sum_j iv[r][j] lp[j][k] (the caller has
+// filled iv and lp); thread (r, q) forms the 16 columns of quarter q, then
+// every thread reads its whole row back.
+__device__ __forceinline__ void form_m(float (*m)[NB + 4], const float (*lp)[NB + 4], const float (*iv)[NB + 4],
+                                       float (&mrow)[NB])
+{
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = 0.f;
+    for (int j0 = 0; j0 < NB; j0 += 4) {
+        const float4 l4 = *reinterpret_cast<const float4*>(&iv[r][j0]);
+        const float ls[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float l = ls[u];
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+                const float4 x = *reinterpret_cast<const float4*>(&lp[j0 + u][16 * q + i]);
+                a[i] = fmaf(l, x.x, a[i]);
+                a[i + 1] = fmaf(l, x.y, a[i + 1]);
+                a[i + 2] = fmaf(l, x.z, a[i + 2]);
+                a[i + 3] = fmaf(l, x.w, a[i + 3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i += 4)
+        *reinterpret_cast<float4*>(&m[r][16 * q + i]) = make_float4(a[i], a[i + 1], a[i + 2], a[i + 3]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NB; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(&m[r][k]);
+        mrow[k] = x.x, mrow[k + 1] = x.y, mrow[k + 2] = x.z, mrow[k + 3] = x.w;
+    }
+}
+
+// z_b for thread (t = r, c = q + 4 i): acc (this thread's compensated sum
+// for row r, quarter q) and rhs (row r's right-hand side, held by quarter 0)
+// give w = rhs - sum over quarters in wT; then z = iv[r] . w.
+template <int R>
+__device__ __forceinline__ void form_z(SweepF32Smem<R>& S, const float (&acc)[R], const float (&rhs)[R],
+                                       float (&z)[(R + 3) / 4])
+{
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;
+#pragma unroll
+    for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
+    if (q == 0)
+#pragma unroll
+        for (int c = 0; c < R; ++c) S.wT[c][r] = rhs[c];
+    __syncthreads();
+    for (int c = q; c < R; c += 4)
+        S.wT[c][r] -= ((S.part[0][r][c] + S.part[1][r][c]) + S.part[2][r][c]) + S.part[3][r][c];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < (R + 3) / 4; ++i) z[i] = (q + 4 * i < R) ? dot64s(&S.iv[r][0], &S.wT[q + 4 * i][0]) : 0.f;
+}
+
+// The last step of a row: wait for the neighbouring row p's solved block
+// (skipped when there is none), x = z - M_b x_p, publish x.
+template <int R>
+__device__ __forceinline__ void finish_row(SweepF32Smem<R>& S, const float (&z)[(R + 3) / 4],
+                                           const float (&mrow)[NB], bool has_p, int p0, int b0, int np, int nr,
+                                           unsigned epoch, unsigned long long* __restrict__ tag,
+                                           float* __restrict__ out, int* status)
+{
+    const int tid = threadIdx.x;
+    const int r = tid & (NB - 1), q = tid >> 6;
+    if (has_p) {
+        for (int e = tid; e < NB * R; e += blockDim.x) {
+            const int t = e % NB, c = e / NB;
+            S.vT[c][t] = (c < nr) ? poll_tagged(tag + (size_t)(p0 + t) + (size_t)c * np, epoch, status) : 0.f;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < (R + 3) / 4; ++i) {
+        const int c = q + 4 * i;
+        if (c >= nr) break;
+        const float y = has_p ? z[i] - dot64(mrow, &S.vT[c][0]) : z[i];
+        const size_t idx = (size_t)(b0 + r) + (size_t)c * np;
+        tag[idx] = tagged(y, epoch);
+        out[idx] = y;
+    }
 }
 
 // Forward sweep Y = L^-1 W on columns [0, nr) (FP32).
@@ -291,14 +438,15 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
                                                      int* status, const int* done)
 {
     if (done && *done) return;
-    extern __shared__ unsigned char smem_raw[];
-    SweepSmem<float, R>& S = *reinterpret_cast<SweepSmem<float, R>*>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepF32Smem<R>& S = *reinterpret_cast<SweepF32Smem<R>*>(smem_raw);
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;   // row of the block, column quarter
     const int nblk = np / NB;
     constexpr int QW = NB / 4;
     for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int b0 = b * NB;
+        // the diagonal-block inverse (stored column-major, zeros above), iv[t][k]
         for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
         float rhs[R], acc[R], comp[R];
 #pragma unroll
@@ -306,15 +454,28 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
             rhs[c] = (q == 0 && c < nr) ? W[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
             acc[c] = comp[c] = 0.f;
         }
+        // M_b = Linv_b L_b,b-1, row r
+        float mrow[NB];
+        if (b > 0) {
+            for (int e = tid; e < NB * NB; e += blockDim.x) {
+                const int j = e % NB, k = e / NB;
+                S.lp[j][k] = L[(size_t)(b0 + j) + (size_t)(b0 - NB + k) * np];
+            }
+            __syncthreads();
+            form_m(S.m, S.lp, S.iv, mrow);
+        } else {
+            __syncthreads();   // iv complete
+        }
+        // the compensated sum over rows j < b - 1
         float lnext[QW];
-        if (b > 0)
+        if (b > 1)
 #pragma unroll
             for (int tt = 0; tt < QW; ++tt) lnext[tt] = L[(size_t)(b0 + r) + (size_t)(q * QW + tt) * np];
-        for (int j = 0; j < b; ++j) {
+        for (int j = 0; j + 1 < b; ++j) {
             float lcur[QW];
 #pragma unroll
             for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
-            if (j + 1 < b)
+            if (j + 2 < b)
 #pragma unroll
                 for (int tt = 0; tt < QW; ++tt)
                     lnext[tt] = L[(size_t)(b0 + r) + (size_t)((j + 1) * NB + q * QW + tt) * np];
@@ -328,33 +489,13 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
 #pragma unroll
             for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) {
-                const int t = q * QW + tt;
-#pragma unroll
-                for (int c = 0; c < R; ++c) aj[c] += lcur[tt] * S.v[t][c];
-            }
+            for (int tt = 0; tt < QW; ++tt) axpy_row<R>(aj, lcur[tt], &S.v[q * QW + tt][0]);
             kahan_add(acc, comp, aj);
             __syncthreads();
         }
-#pragma unroll
-        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
-        if (q == 0)
-#pragma unroll
-            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
-        __syncthreads();
-        for (int e = tid; e < NB * R; e += blockDim.x) {
-            const int t = e % NB, c = e / NB;
-            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * R; e += blockDim.x) {
-            const int t = e % NB, c = e / NB;
-            if (c >= nr) continue;
-            const float y = apply_inv<R, false>(S.iv, S.w, t, c);
-            const size_t idx = (size_t)(b0 + t) + (size_t)c * np;
-            tag[idx] = tagged(y, epoch);
-            Y[idx] = y;
-        }
+        float z[(R + 3) / 4];
+        form_z<R>(S, acc, rhs, z);
+        finish_row<R>(S, z, mrow, b > 0, b0 - NB, b0, np, nr, epoch, tag, Y, status);
         __syncthreads();
     }
 }
@@ -363,44 +504,52 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
 // Block (j, b) of L is read along its columns (coalesced) into registers one
 // step ahead and staged through shared memory as its transpose.
 template <int R>
-struct SweepBwdSmem {
-    SweepSmem<float, R> base;
-    float lt[NB][NB + 1];   // lt[r][t] = L[j0 + t][b0 + r]
-};
-
-template <int R>
 __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L, const float* __restrict__ Linv,
                                                      int np, const float* __restrict__ Y, float* __restrict__ X,
                                                      unsigned long long* __restrict__ tag, int nr, unsigned epoch,
                                                      int* status, const int* done)
 {
     if (done && *done) return;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepBwdSmem<R>& SB = *reinterpret_cast<SweepBwdSmem<R>*>(smem_raw);
-    SweepSmem<float, R>& S = SB.base;
+    SweepF32Smem<R>& S = SB.base;
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;
     const int nblk = np / NB;
     constexpr int QW = NB / 4;
     for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
         const int b0 = b * NB;
-        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e % NB][e / NB] = Linv[(size_t)b * NB * NB + e];
+        // the transpose of the diagonal-block inverse, iv[t][k] = Linv[k][t]
+        for (int e = tid; e < NB * NB; e += blockDim.x) S.iv[e / NB][e % NB] = Linv[(size_t)b * NB * NB + e];
         float rhs[R], acc[R], comp[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) {
             rhs[c] = (q == 0 && c < nr) ? Y[(size_t)(b0 + r) + (size_t)c * np] : 0.f;
             acc[c] = comp[c] = 0.f;
         }
+        // M_b = Linv_b^T L_b+1,b^T, row r: m[r][k] = sum_j Linv[j][r] L_b+1,b[k][j]
+        float mrow[NB];
+        if (b < nblk - 1) {
+            for (int e = tid; e < NB * NB; e += blockDim.x) {
+                const int k = e % NB, j = e / NB;
+                S.lp[j][k] = L[(size_t)(b0 + NB + k) + (size_t)(b0 + j) * np];
+            }
+            __syncthreads();
+            form_m(S.m, S.lp, S.iv, mrow);
+        } else {
+            __syncthreads();   // iv complete
+        }
+        // the compensated sum over rows j > b + 1
         // thread tid holds L[j0 + (tid & 63)][b0 + (tid >> 6) + 4 k], k < 16
         const float* colb = L + (size_t)(tid & 63) + (size_t)(b0 + (tid >> 6)) * np;
         float lnext[QW];
-        if (b < nblk - 1)
+        if (b < nblk - 2)
 #pragma unroll
             for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(nblk - 1) * NB + (size_t)(4 * k) * np];
-        for (int j = nblk - 1; j > b; --j) {
+        for (int j = nblk - 1; j > b + 1; --j) {
 #pragma unroll
             for (int k = 0; k < QW; ++k) SB.lt[(tid >> 6) + 4 * k][tid & 63] = lnext[k];
-            if (j - 1 > b)
+            if (j - 1 > b + 1)
 #pragma unroll
                 for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(j - 1) * NB + (size_t)(4 * k) * np];
             const int j0 = j * NB;
@@ -413,33 +562,13 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
 #pragma unroll
             for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) {
-                const float l = SB.lt[r][q * QW + tt];
-#pragma unroll
-                for (int c = 0; c < R; ++c) aj[c] += l * S.v[q * QW + tt][c];
-            }
+            for (int tt = 0; tt < QW; ++tt) axpy_row<R>(aj, SB.lt[r][q * QW + tt], &S.v[q * QW + tt][0]);
             kahan_add(acc, comp, aj);
             __syncthreads();
         }
-#pragma unroll
-        for (int c = 0; c < R; ++c) S.part[q][r][c] = acc[c];
-        if (q == 0)
-#pragma unroll
-            for (int c = 0; c < R; ++c) S.w[r][c] = rhs[c];
-        __syncthreads();
-        for (int e = tid; e < NB * R; e += blockDim.x) {
-            const int t = e % NB, c = e / NB;
-            S.w[t][c] -= ((S.part[0][t][c] + S.part[1][t][c]) + S.part[2][t][c]) + S.part[3][t][c];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * R; e += blockDim.x) {
-            const int t = e % NB, c = e / NB;
-            if (c >= nr) continue;
-            const float x = apply_inv<R, true>(S.iv, S.w, t, c);
-            const size_t idx = (size_t)(b0 + t) + (size_t)c * np;
-            tag[idx] = tagged(x, epoch);
-            X[idx] = x;
-        }
+        float z[(R + 3) / 4];
+        form_z<R>(S, acc, rhs, z);
+        finish_row<R>(S, z, mrow, b < nblk - 1, b0 + NB, b0, np, nr, epoch, tag, X, status);
         __syncthreads();
     }
 }
@@ -505,7 +634,7 @@ template <int R>
 cudaError_t sweep_pair_f32(const float* L, const float* Linv, int np, float* W, float* Y, unsigned long long* tag,
                            int nr, int* status, const int* done, cudaStream_t s)
 {
-    const size_t smem = sizeof(SweepSmem<float, R>), smem_b = sizeof(SweepBwdSmem<R>);
+    const size_t smem = sizeof(SweepF32Smem<R>), smem_b = sizeof(SweepBwdSmem<R>);
     const int nblk = np / NB;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(sweep_fwd_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
