@@ -364,7 +364,7 @@ KERNEL_NAMES = {
     "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
     "factor": "factor_step: one launch per elimination step (panel rows, strip update, next diagonal "
               "block factor+inverse, tcgen05 3xTF32 trailing tiles)",
-    "sweep": "trsv_fwd/trsv_bwd: persistent cooperative triangular sweeps",
+    "sweep": "sweep_fwd_f32/sweep_bwd_f32: persistent cooperative triangular sweeps (x_b = z_b - M_b x_p)",
     "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
 }
 FP64_PEAK_TF = 1.25   # nominal GB300 FP64 (non-tensor) rate
