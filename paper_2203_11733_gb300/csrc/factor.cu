@@ -648,76 +648,81 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-// Panel work of row block i at step k (one CTA):
-//   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
-//      so the sum over t stops at the output column);
-//   2. row blocks at or below r0 write the TF32 hi/lo split of L_ik in the
-//      tensor-core operand layout;
-//   3. A_ic -= L_ik L_ck^T for the sw strip blocks c = k+1 .. k+sw, c <= i,
-//      with L_ck (lsT, t-major) computed by the CTA that factored block k.
-// The strip targets are read first, so their latency overlaps the product.
-__device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int r0,
-                          unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
-                          const float* __restrict__ lsT, int i, unsigned char* smem)
+// Panel work of half h (rows 32 h .. 32 h + 31) of row block i at step k
+// (one CTA; the two halves of a row block run in two CTAs):
+//   1. L_ik = A_ik Linv_kk^T for those rows, written in place (Linv_kk is
+//      lower triangular, so the sum over t stops at the output column);
+//   2. row blocks at or below r0 write the TF32 hi/lo split of those rows in
+//      the tensor-core operand layout;
+//   3. A_ic -= L_ik L_ck^T on those rows for the sw strip blocks
+//      c = k+1 .. k+sw, c <= i, with L_ck (lsT, t-major) computed by the
+//      helpers of the previous step.
+// A thread owns 2 rows x 4 columns.  The strip targets are read first, so
+// their latency overlaps the product.
+__device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int r0,
+                           unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
+                           const float* __restrict__ lsT, int i, int h, unsigned char* smem)
 {
+    constexpr int HR = NB / 2;   // rows of a half
     // Blocks are stored t-major (rows padded to 68 floats) so that a
-    // thread's four rows or columns at one t are one 16-byte load.
+    // thread's rows or columns at one t are one 8- or 16-byte load.
     float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem);   // ivT[t][c] = Linv_kk[c][t]
-    float(*aT)[PT] = ivT + NB;                                // aT[t][r] = A_ik, then L_ik
+    float(*aT)[PT] = ivT + NB;                                // aT[t][r] = A_ik, then L_ik (r < 32)
     float(*lcT)[PT] = aT + NB;                                // lcT[s * 64 + t][c] = L_ck[c][t]
     const int tid = threadIdx.x;
-    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
-    const int k0 = k * NB, rI = i * NB;
+    const int tr = (tid & 15) * 2, tc = (tid >> 4) * 4;
+    const int k0 = k * NB, rI = i * NB, rh = rI + HR * h;
     const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
     const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
-    float4 tgt[2][4];
+    float2 tgt[2][4];
 #pragma unroll
     for (int sidx = 0; sidx < 2; ++sidx)
         if (sidx < nstrip)
 #pragma unroll
             for (int v = 0; v < 4; ++v)
-                tgt[sidx][v] = *reinterpret_cast<const float4*>(L + (size_t)(rI + tr) +
+                tgt[sidx][v] = *reinterpret_cast<const float2*>(L + (size_t)(rh + tr) +
                                                                 (size_t)((k + 1 + sidx) * NB + tc + v) * ld);
     const float* Lb = Linv + (size_t)k * NB * NB;
-    for (int e = tid; e < NB * NB / 4; e += blockDim.x) {   // Linv_kk column-major: 4e = c + 64 t
+    for (int e = tid; e < NB * NB / 4; e += blockDim.x)   // Linv_kk column-major: 4e = c + 64 t
         *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(Lb)[e];
-        const int t = e >> 4, r = (e & 15) * 4;
+    for (int e = tid; e < NB * HR / 4; e += blockDim.x) {
+        const int t = e >> 3, r = (e & 7) * 4;
         *reinterpret_cast<float4*>(&aT[t][r]) =
-            *reinterpret_cast<const float4*>(L + (size_t)(rI + r) + (size_t)(k0 + t) * ld);
+            *reinterpret_cast<const float4*>(L + (size_t)(rh + r) + (size_t)(k0 + t) * ld);
     }
     for (int e = tid; e < nstrip * NB * NB / 4; e += blockDim.x)
         *reinterpret_cast<float4*>(&lcT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(lsT)[e];
     __syncthreads();
-    float acc[4][4] = {};
+    float acc[2][4] = {};
     for (int t = 0; t < tc + 4; ++t) {
-        const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+        const float2 x = *reinterpret_cast<const float2*>(&aT[t][tr]);
         const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
-        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+        const float xs[2] = {x.x, x.y}, ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
     }
     __syncthreads();   // every thread is done reading A_ik
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
-        *reinterpret_cast<float4*>(&aT[tc + v][tr]) = q;
-        *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(k0 + tc + v) * ld) = q;
+        const float2 q = make_float2(acc[0][v], acc[1][v]);
+        *reinterpret_cast<float2*>(&aT[tc + v][tr]) = q;
+        *reinterpret_cast<float2*>(L + (size_t)(rh + tr) + (size_t)(k0 + tc + v) * ld) = q;
     }
     if (rI >= r0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int rr = rI - r0 + tr + u;
+        for (int u = 0; u < 2; ++u) {
+            const int rr = rh - r0 + tr + u;
             const size_t off = tc::split_offset(rr, tc, stage_stride);
-            float h[4], l[4];
+            float hv[4], lv[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                h[v] = tc::to_tf32(acc[u][v]);
-                l[v] = acc[u][v] - h[v];
+                hv[v] = tc::to_tf32(acc[u][v]);
+                lv[v] = acc[u][v] - hv[v];
             }
-            *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<float4*>(hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            *reinterpret_cast<float4*>(lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
     }
     __syncthreads();   // aT holds L_ik
@@ -725,24 +730,22 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
     for (int sidx = 0; sidx < 2; ++sidx) {
         if (sidx >= nstrip) break;
         const float(*bT)[PT] = lcT + sidx * NB;
-        float acc2[4][4] = {};
+        float acc2[2][4] = {};
         for (int t = 0; t < NB; ++t) {
-            const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+            const float2 x = *reinterpret_cast<const float2*>(&aT[t][tr]);
             const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
-            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+            const float xs[2] = {x.x, x.y}, ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 2; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            float4 o = tgt[sidx][v];
+            float2 o = tgt[sidx][v];
             o.x -= acc2[0][v];
             o.y -= acc2[1][v];
-            o.z -= acc2[2][v];
-            o.w -= acc2[3][v];
-            *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld) = o;
+            *reinterpret_cast<float2*>(L + (size_t)(rh + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld) = o;
         }
     }
 }
@@ -752,9 +755,10 @@ __device__ void panel_row(float* __restrict__ L, int ld, int k, const float* __r
 // ticket in the order the CTAs start (an atomic counter per step), and the
 // ticket gives its role (m = row blocks below diagonal block k, ns = strip
 // width of step k+1):
-//   tickets 0 .. m-2   panel work of row block k + 2 + ticket (panel_row),
-//                      then a release flag pflag[i] = k + 1;
-//   ticket  m-1        factor and invert diagonal block k+1, then dflag[k];
+//   tickets 0 .. 2m-3  panel work of half ticket % 2 of row block
+//                      i = k + 2 + ticket / 2 (panel_half); the second half
+//                      to finish sets the release flag pflag[i] = k + 1;
+//   ticket  2m-2       factor and invert diagonal block k+1, then dflag[k];
 //   next ns tickets    helpers (tail_helper): the strip rows of step k+1 and,
 //                      for the first, the lookahead panel work of row block
 //                      k+2 (pflag[k+2] = k + 2);
@@ -772,7 +776,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
                                                    unsigned* __restrict__ tickets, unsigned* __restrict__ dflag,
-                                                   int zero_col)
+                                                   unsigned* __restrict__ halves, int zero_col)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -780,8 +784,11 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     pdl_trigger();
     if (threadIdx.x == 0) s_ticket = (int)atomicAdd(tickets + k, 1u);
     __syncthreads();
-    const int t = s_ticket;
-    const int npanel = nblk - k - 2;
+    const int t_raw = s_ticket;
+    const int npanel = nblk - k - 2;   // panel row blocks, two CTAs each
+    // after the 2 npanel half-panel tickets, the roles count as if one CTA
+    // per row block: t = npanel is the diagonal CTA, and so on
+    const int t = t_raw < 2 * npanel ? t_raw / 2 : t_raw - npanel;
     const unsigned token = (unsigned)k + 1;
     int* status = info + 3;
     // roles without tensor-core work give up the CTA's TMEM allocation permit
@@ -791,12 +798,17 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (t < npanel) {
         const int i = k + 2 + t;
-        panel_row(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, tc_smem);
-        __syncthreads();   // the whole row block is stored
+        panel_half(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, t_raw & 1, tc_smem);
+        __syncthreads();   // the half is stored
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
             __threadfence();
-            st_release(pflag + i, token);
+            // halves[i] only grows (two per step): the second half to finish
+            // sees an odd count and releases the row block
+            if (atomicAdd(halves + i, 1u) & 1u) {
+                __threadfence();
+                st_release(pflag + i, token);
+            }
         }
         return;
     }
@@ -861,9 +873,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
         unsigned* tickets = pflag + nblk;
         unsigned* dflag = tickets + nblk;
+        unsigned* halves = dflag + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        if ((e = cudaMemsetAsync(pflag, 0, 3 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
         // strip width of step k: one or two column blocks, leaving an even
         // number of blocks (whole 128-tiles) for the tensor cores
         auto strip_width = [nblk](int k) {
@@ -887,8 +900,8 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
             if (pre_step && (e = pre_step(hook_user, k, s)) != cudaSuccess) return e;
             cudaLaunchConfig_t cfg = {};
-            // m - 1 panel rows, the diagonal CTA, its strip-row helpers, the tiles
-            cfg.gridDim = dim3((unsigned)(m + strip_width(k + 1) + tiles));
+            // 2 (m - 1) half panel rows, the diagonal CTA, its strip-row helpers, the tiles
+            cfg.gridDim = dim3((unsigned)(2 * (m - 1) + 1 + strip_width(k + 1) + tiles));
             cfg.blockDim = dim3(256);
             cfg.dynamicSmemBytes = kFactorSmem;
             cfg.stream = s;
@@ -897,7 +910,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
                                         (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets,
-                                        dflag, zero_col)) !=
+                                        dflag, halves, zero_col)) !=
                 cudaSuccess)
                 return e;
             count_launch();
@@ -979,10 +992,10 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets
-    // and diagonal-block flags
+    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets,
+    // diagonal-block flags and half-panel counters
     return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
-           3 * (size_t)(np / NB) * sizeof(unsigned);
+           4 * (size_t)(np / NB) * sizeof(unsigned);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
