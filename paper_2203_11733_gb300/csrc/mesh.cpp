@@ -113,6 +113,9 @@ gbem_status mesh_build_boxes(const gbem_box* boxes, int nbox, const gbem_mesh_pa
     axis.clear();
     geo.clear();
     cond_raw.clear();
+    axis.reserve((size_t)est);
+    geo.reserve(5 * (size_t)est);
+    cond_raw.reserve((size_t)est);
     for (int b = 0; b < nbox; ++b) {
         const gbem_box& B = boxes[b];
         for (int k = 0; k < 3; ++k) {
@@ -177,19 +180,28 @@ void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector
         }
         code[i] = m;
     }
-    std::vector<size_t> idx(n);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
-        if (cond[a] != cond[b]) return cond[a] < cond[b];
-        return code[a] < code[b];
+    // sort flat records (conductor, code, original index): the index breaks
+    // ties, so the order is that of a stable sort on (conductor, code)
+    struct Key {
+        int32_t cond;
+        uint32_t idx;
+        uint64_t code;
+    };
+    std::vector<Key> keys(n);
+    for (size_t i = 0; i < n; ++i) keys[i] = Key{cond[i], (uint32_t)i, code[i]};
+    std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+        if (a.cond != b.cond) return a.cond < b.cond;
+        if (a.code != b.code) return a.code < b.code;
+        return a.idx < b.idx;
     });
     std::vector<int8_t> ax2(n);
     std::vector<double> g2(5 * n);
     std::vector<int32_t> c2(n);
     for (size_t t = 0; t < n; ++t) {
-        ax2[t] = axis[idx[t]];
-        c2[t] = cond[idx[t]];
-        for (int e = 0; e < 5; ++e) g2[5 * t + e] = geo[5 * idx[t] + e];
+        const size_t j = keys[t].idx;
+        ax2[t] = axis[j];
+        c2[t] = cond[j];
+        for (int e = 0; e < 5; ++e) g2[5 * t + e] = geo[5 * j + e];
     }
     axis.swap(ax2);
     geo.swap(g2);
