@@ -541,8 +541,11 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
     }
 }
 
+// Register caps of 80 (mixed: three CTAs an SM) and 128 (FP64: two): the
+// kernel is latency-bound (FP64 closed forms, MUFU, barrier waits), so the
+// extra warps pay for the few spilled registers.
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads) assemble_tiles(DevPanels g, int np, float q_near,
+__global__ void __launch_bounds__(kThreads, MIXED ? 3 : 2) assemble_tiles(DevPanels g, int np, float q_near,
                                                            double* __restrict__ A64,
                                                            float* __restrict__ A32,
                                                            unsigned long long* __restrict__ counts, int tj0)
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(256) add_hi(const double* __restrict__ A64, fl
 // Batched assembly: CTA index -> (structure, tile) through the prefix sums of
 // the structures' tile counts.
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads) assemble_batched(BatchView v, float q_near)
+__global__ void __launch_bounds__(kThreads, MIXED ? 3 : 2) assemble_batched(BatchView v, float q_near)
 {
     __shared__ int sb;
     if (threadIdx.x == 0) sb = batch_find(v.tile_prefix, v.nb, (long long)blockIdx.x);
