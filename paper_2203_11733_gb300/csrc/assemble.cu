@@ -541,11 +541,11 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
     }
 }
 
-// Register caps of 80 (mixed: three CTAs an SM) and 128 (FP64: two): the
+// Register caps of 64 (mixed: four CTAs an SM) and 128 (FP64: two): the
 // kernel is latency-bound (FP64 closed forms, MUFU, barrier waits), so the
 // extra warps pay for the few spilled registers.
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, MIXED ? 3 : 2) assemble_tiles(DevPanels g, int np, float q_near,
+__global__ void __launch_bounds__(kThreads, MIXED ? 4 : 2) assemble_tiles(DevPanels g, int np, float q_near,
                                                            double* __restrict__ A64,
                                                            float* __restrict__ A32,
                                                            unsigned long long* __restrict__ counts, int tj0)
