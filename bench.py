@@ -39,7 +39,8 @@ UNIT = "pairs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 30; 10 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -57,7 +58,10 @@ def parse():
     ap.add_argument("--profile-workload", default="crossing_bus_2x2",
                     choices=["crossing_bus_2x2", "two_bars", "bus_3layer_5x5x5"],
                     help="structure of the --profile run (two_bars: a small case for pass counts)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else 30
+    return args
 
 
 def dist_env():
@@ -70,25 +74,52 @@ def dist_env():
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of SM clock and throttle reasons every 50 ms, each
+    row time-stamped, so that the rows taken inside the timed region
+    (begin() .. end()) are the ones reported.  The GPU is addressed by its PCI
+    bus id (nvidia-smi's index order need not match CUDA's), else by index."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+
+    def _target(self):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.index)
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+            r = subprocess.run(["nvidia-smi", f"--id={bus}", "--query-gpu=index", "--format=csv,noheader"],
+                               capture_output=True, timeout=20)
+            if r.returncode == 0 and r.stdout.strip():
+                return bus
+        except Exception:
+            pass
+        return str(self.index)
 
     def start(self):
+        """Start sampling; give nvidia-smi time to take its first sample."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--id={self._target()}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -98,13 +129,31 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, parts[1:]))
         os.unlink(self.path)
-        if not rows:
+        inside = [r for ts, r in rows if ts is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 <= ts <= self.t1]
+        # a region shorter than the interval may hold no sample: then the
+        # samples of the 0.5 s around it (the warm-up runs just before)
+        window = "timed region"
+        if not inside:
+            inside = [r for ts, r in rows if ts is not None and self.t0 is not None and self.t1 is not None
+                      and self.t0 - 0.5 <= ts <= self.t1 + 0.5]
+            window = "timed region +- 0.5 s"
+        if not inside:
+            inside = [r for _, r in rows]
+            window = "whole sampler run"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
         def num(x):
@@ -112,12 +161,11 @@ class ClockSampler:
                 return float(x)
             except ValueError:
                 return None
-        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
-        mx = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        sm = sorted(v for v in (num(r[1]) for r in inside) if v is not None)
+        mx = max((v for v in (num(r[2]) for r in inside) if v is not None), default=None)
+        reasons = sorted({self.NAMES[k] for r in inside for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(inside), "window": window}
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
@@ -260,14 +308,16 @@ def run_ours(args):
         return float(t.item()), out
 
     # ---- mixed precision (the headline path)
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step(gbem.GBEM_MIXED)
     barrier()
     gbem.set_timing(ctx, 1)
     stats = gbem.get_stats(ctx, reset=True)
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.begin()
     ms_total, C_mixed = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
+    clocks.end()
     clk = clocks.stop()
     barrier()
     stats = gbem.get_stats(ctx, reset=True)
@@ -470,12 +520,14 @@ def run_batch(args):
     t0 = time.perf_counter()
     batch, choice = gbem.Batch.autotune(ctx, meshes, max_iters=3, cache_path=cache)
     t_tune = time.perf_counter() - t0
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         batch.run(W.EPS_R_SIO2, stream)
     gbem.get_stats(ctx, reset=True)
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.begin()
     ms_batch, (Cs, res) = timed_runs(batch, args.steps)
+    clocks.end()
     clk = clocks.stop()
     st = gbem.get_stats(ctx, reset=True)
     # one at a time, same structures, same GPU
@@ -570,7 +622,9 @@ def run_serving(args):
     # the generator's arrival times are for rate 1/s: scale them to `rate`
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.begin()
     got, stats = run_stream(reqs, rate_scale=1.0 / rate)
+    clocks.end()
     clk = clocks.stop()
     infos = [got[k][0] for k in range(len(reqs))]
     lat = np.array([i["done_s"] - i["submit_s"] for i in infos]) * 1e3
