@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(256) add_hi(const double* __restrict__ A64, fl
 // Batched assembly: CTA index -> (structure, tile) through the prefix sums of
 // the structures' tile counts.
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, MIXED ? 4 : 2) assemble_batched(BatchView v, float q_near)
+__global__ void __launch_bounds__(kThreads) assemble_batched(BatchView v, float q_near)
 {
     __shared__ int sb;
     if (threadIdx.x == 0) sb = batch_find(v.tile_prefix, v.nb, (long long)blockIdx.x);
