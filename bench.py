@@ -71,6 +71,40 @@ def dist_env():
     return world, rank, local
 
 
+def dist_start(world: int, backend: str = "nccl"):
+    """One process per GPU under torchrun: join the process group (the ranks
+    exchange only timings, never data of the extraction)."""
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def dist_stop(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (a time): the whole job ends with its
+    slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed (each rank the same number) per second of
+    the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -244,9 +278,7 @@ def run_ours(args):
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist_start(world)
     from paper_2203_11733_gb300 import build as B
     from paper_2203_11733_gb300 import gbem, workloads as W
     if rank == 0 or world == 1:
@@ -302,10 +334,7 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item()), out
+        return max_over_ranks(total, world), out
 
     # ---- mixed precision (the headline path)
     clocks = ClockSampler(local)
@@ -322,7 +351,7 @@ def run_ours(args):
     barrier()
     stats = gbem.get_stats(ctx, reset=True)
     ms_step = ms_total / args.steps
-    value = world * pairs * args.steps / (ms_total * 1e-3)
+    value = whole_job_rate(pairs * args.steps, world, ms_total * 1e-3)
 
     # ---- the same steps again with an event pair around every launch of the
     # traced kernels (kept out of the headline timing: the events cost time)
@@ -354,7 +383,7 @@ def run_ours(args):
     step_e2e()
     barrier()
     ms_e2e, _ = timed(step_e2e, args.steps)
-    value_e2e = world * pairs * args.steps / (ms_e2e * 1e-3)
+    value_e2e = whole_job_rate(pairs * args.steps, world, ms_e2e * 1e-3)
     h2d = n * (5 * 8 + 1 + 4)
     d2h = nc * nc * 8
 
@@ -403,8 +432,7 @@ def run_ours(args):
         print(json.dumps(line))
     mesh.close()
     ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    dist_stop(world)
 
 
 PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
@@ -486,9 +514,11 @@ def run_batch(args):
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
+    dist_start(world)
     from paper_2203_11733_gb300 import build as B
     from paper_2203_11733_gb300 import gbem, workloads as W
     B.build()
+    # each rank its own structures: independent problems, no data exchanged
     structs = W.batch_small_structures(seed=4242 + rank, count=args.batch_count)
     ctx = gbem.Context(local)
     meshes = [ctx.mesh(b, p) for b, p in structs]
@@ -525,10 +555,14 @@ def run_batch(args):
     for _ in range(args.warmup):
         batch.run(W.EPS_R_SIO2, stream)
     gbem.get_stats(ctx, reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clocks.begin()
     ms_batch, (Cs, res) = timed_runs(batch, args.steps)
     clocks.end()
     clk = clocks.stop()
+    ms_batch = max_over_ranks(ms_batch, world)
     st = gbem.get_stats(ctx, reset=True)
     # one at a time, same structures, same GPU
     def one_at_a_time(prec, idx):
@@ -556,7 +590,7 @@ def run_batch(args):
     err_vs_single = max(float(np.max(np.abs(Cs[i] - C)) / np.max(np.abs(C))) for i, C in zip(idx, C_mixed))
     n_ext = len(meshes)
     line = {
-        "metric": "extractions/s", "value": world * n_ext / (ms_batch * 1e-3), "unit": "extractions/s",
+        "metric": "extractions/s", "value": whole_job_rate(n_ext, world, ms_batch * 1e-3), "unit": "extractions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
         "data": "synthetic",
@@ -566,7 +600,7 @@ def run_batch(args):
                    "graph_kernels_per_launch": int(st["launches"] / args.steps)},
         "autotune": {"choice": choice, "tune_s": t_tune, "untuned_ms_per_step": ms_base,
                      "untuned_config": {"groups": 1, "refinement_passes": 3}},
-        "pairs_per_s": world * float((ns * (ns + 1) / 2).sum()) / (ms_batch * 1e-3),
+        "pairs_per_s": whole_job_rate(float((ns * (ns + 1) / 2).sum()), world, ms_batch * 1e-3),
         "one_at_a_time_mixed": {"extractions_per_s": n_ext / (t_mixed * 1e-3), "ms_total": t_mixed},
         "one_at_a_time_fp64": {"extractions_per_s": len(sub) / (t64 * 1e-3), "structures": len(sub)},
         "batch_over_single_mixed": t_mixed / ms_batch,
@@ -578,6 +612,7 @@ def run_batch(args):
         print(json.dumps(line))
     batch.close()
     ctx.close()
+    dist_stop(world)
 
 
 def run_serving(args):
@@ -589,6 +624,7 @@ def run_serving(args):
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
+    dist_start(world)
     from paper_2203_11733_gb300 import build as B
     from paper_2203_11733_gb300 import gbem, workloads as W
     B.build()
@@ -622,6 +658,8 @@ def run_serving(args):
     # the generator's arrival times are for rate 1/s: scale them to `rate`
     clocks = ClockSampler(local)
     clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
     clocks.begin()
     got, stats = run_stream(reqs, rate_scale=1.0 / rate)
     clocks.end()
@@ -629,7 +667,7 @@ def run_serving(args):
     infos = [got[k][0] for k in range(len(reqs))]
     lat = np.array([i["done_s"] - i["submit_s"] for i in infos]) * 1e3
     wait = np.array([i["start_s"] - i["submit_s"] for i in infos]) * 1e3
-    span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
+    span = max_over_ranks(max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos), world)
     ok = all(i["status"] == 0 for i in infos)
     failed = [{"id": int(i["id"]), "status": int(i["status"]), "n_panels": int(i["n_panels"]),
                "residual": float(i["residual"])} for i in infos if i["status"] != 0]
@@ -655,7 +693,8 @@ def run_serving(args):
     err = max(float(np.max(np.abs(got[k][1] - C64[k])) / np.max(np.abs(C64[k]))) for k in range(len(C64)))
     ctx.close()
     line = {
-        "metric": "extractions/s", "value": world * len(reqs) / span, "unit": "extractions/s", "n_gpus": world,
+        "metric": "extractions/s", "value": whole_job_rate(len(reqs), world, span), "unit": "extractions/s",
+        "n_gpus": world,
         "steps": len(reqs), "warmup": len(cal), "ms_per_step": 1e3 * span / len(reqs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": {"workload": f"serving: Poisson stream of {len(reqs)} 2-15 conductor buses, N log-uniform [500,30000]",
@@ -672,6 +711,7 @@ def run_serving(args):
     }
     if rank == 0:
         print(json.dumps(line))
+    dist_stop(world)
 
 
 def main():
