@@ -130,7 +130,11 @@ gbem_status gbem_set_tuning(gbem_ctx* ctx, const gbem_tuning* t);
  * assembly time they hide.  The environment variable GBEM_OVERLAP
  * ("groups[,first_fraction]") sets a context's initial values. */
 gbem_status gbem_set_overlap(gbem_ctx* ctx, int groups, double first_fraction);
-/* Bytes currently held by the context's handles. */
+/* Bytes currently held by the context: its handles' buffers, and the
+ * buffers of the last destroyed matrix, which the context keeps (idle) for
+ * the next matrix's allocations of the same size and releases at the next
+ * matrix destroy, when an allocation would exceed the budget or is refused,
+ * and in gbem_destroy. */
 size_t gbem_bytes_in_use(const gbem_ctx* ctx);
 
 /* Mesh the surfaces of `nbox` disjoint cuboids (Sec. 3.1, Sec. 3.3).
@@ -359,6 +363,9 @@ void gbem_server_destroy(gbem_server_t* srv);
  * closed form, and by Gauss-Legendre order 1..6 (counts[0] closed form,
  * counts[n] order n; array of 7).  Waits for the assembly stream. */
 gbem_status gbem_matrix_info(gbem_matrix_t* mat, int* n, long long* counts);
+/* Waits for the matrix's last stream, then hands its device buffers to the
+ * context, which offers them to the next matrix of the same size (see
+ * gbem_bytes_in_use); a context made by the server frees them at once. */
 void gbem_matrix_destroy(gbem_matrix_t* mat);
 
 #ifdef __cplusplus

@@ -112,12 +112,26 @@ struct DeviceGuard {
 
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
-// Allocate from the context and remember it in the matrix for release.
+// A spare buffer of exactly `bytes` (idle), or null.
+void* take_spare(gbem_ctx* ctx, size_t bytes)
+{
+    for (size_t i = ctx->spare.size(); i-- > 0;) {
+        if (ctx->spare[i].bytes != bytes) continue;
+        void* p = ctx->spare[i].p;
+        ctx->spare.erase(ctx->spare.begin() + (long)i);
+        return p;
+    }
+    return nullptr;
+}
+
+// Allocate from the context (a spare buffer of the same size first) and
+// remember it in the matrix for release.
 template <typename T>
 T* mat_alloc(gbem_matrix_t* m, size_t count, cudaStream_t s)
 {
     size_t bytes = round_up(std::max<size_t>(count * sizeof(T), 256), 256);
-    void* p = ctx_alloc(m->ctx, bytes, s);
+    void* p = take_spare(m->ctx, bytes);
+    if (!p) p = ctx_alloc(m->ctx, bytes, s);
     if (p) m->allocs.emplace_back(p, bytes);
     return static_cast<T*>(p);
 }
@@ -282,13 +296,8 @@ gbem_status ctx_fail(gbem_ctx* ctx, gbem_status st, const std::string& msg)
     return st;
 }
 
-void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s)
+static void* raw_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s)
 {
-    if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
-        ctx->err = "HBM budget exceeded: " + std::to_string(ctx->in_use + bytes) + " > " +
-                   std::to_string(ctx->budget) + " bytes";
-        return nullptr;
-    }
     void* p = nullptr;
     if (ctx->alloc) {
         p = ctx->alloc(bytes, (gbem_stream)s, ctx->user);
@@ -297,6 +306,22 @@ void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s)
         cudaGetLastError();
         p = nullptr;
         ctx->err = "cudaMalloc failed for " + std::to_string(bytes) + " bytes";
+    }
+    return p;
+}
+
+void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s)
+{
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) ctx_drop_spare(ctx);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
+        ctx->err = "HBM budget exceeded: " + std::to_string(ctx->in_use + bytes) + " > " +
+                   std::to_string(ctx->budget) + " bytes";
+        return nullptr;
+    }
+    void* p = raw_alloc(ctx, bytes, s);
+    if (!p && !ctx->spare.empty()) {   // the spare buffers may be what is missing
+        ctx_drop_spare(ctx);
+        p = raw_alloc(ctx, bytes, s);
     }
     if (p) ctx->in_use += bytes;
     return p;
@@ -308,6 +333,13 @@ void ctx_free(gbem_ctx* ctx, void* p, size_t bytes, cudaStream_t s)
     if (ctx->free_fn) ctx->free_fn(p, bytes, (gbem_stream)s, ctx->user);
     else cudaFree(p);
     ctx->in_use -= std::min(ctx->in_use, bytes);
+}
+
+void ctx_drop_spare(gbem_ctx* ctx)
+{
+    std::vector<gbem_ctx::Spare> sp;
+    sp.swap(ctx->spare);
+    for (auto& a : sp) ctx_free(ctx, a.p, a.bytes, a.stream);
 }
 
 // ---- assembly overlapped with the factorisation (mixed mode)
@@ -452,6 +484,10 @@ gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget, gbem_allo
 void gbem_destroy(gbem_ctx* ctx)
 {
     if (!ctx) return;
+    if (!ctx->spare.empty()) {
+        DeviceGuard g(ctx->device);
+        ctx_drop_spare(ctx);
+    }
     for (auto& p : ctx->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -712,6 +748,7 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
         return GBEM_ERR_CUDA;
     }
     m->last = s;
+    m->used = true;
     *out = m;
     return GBEM_OK;
 }
@@ -765,6 +802,7 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
     }
     m->factored = true;
     m->last = s;
+    m->used = true;
     return GBEM_OK;
 }
 
@@ -790,6 +828,7 @@ gbem_status gbem_solve(gbem_matrix_t* m, const double* B_dev, int nrhs, int ldb,
         *ir_iters = it;
     }
     m->last = s;
+    m->used = true;
     return st;
 }
 
@@ -832,6 +871,7 @@ gbem_status gbem_capacitance(gbem_mesh_t* mesh, gbem_matrix_t* m, double eps_r, 
         return GBEM_ERR_CUDA;
     if (resid_out) *resid_out = resid;
     m->last = s;
+    m->used = true;
     if (flags[0]) return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "Cholesky met a non-positive pivot");
     if (flags[3]) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
     return solve_st;
@@ -898,14 +938,23 @@ void gbem_matrix_destroy(gbem_matrix_t* m)
 {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
-    if (m->last) {
+    if (m->used) {
         join_groups(m, m->last);
         cudaStreamSynchronize(m->last);
     } else {
         for (auto& gr : m->groups) cudaEventSynchronize(gr.ev);
     }
     for (auto& gr : m->groups) cudaEventDestroy(gr.ev);
-    for (auto& a : m->allocs) ctx_free(m->ctx, a.first, a.second, m->last);
+    gbem_ctx* ctx = m->ctx;
+    // the previous matrix's buffers that this one did not take go now; this
+    // one's wait for the next matrix if they are known to be idle (a matrix
+    // that never finished its assembly call has no synchronised stream)
+    ctx_drop_spare(ctx);
+    const bool keep = ctx->keep_spare && m->used;
+    for (auto& a : m->allocs) {
+        if (keep) ctx->spare.push_back({a.first, a.second, m->last});
+        else ctx_free(ctx, a.first, a.second, m->last);
+    }
     delete m;
 }
 

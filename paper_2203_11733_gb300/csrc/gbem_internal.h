@@ -69,6 +69,18 @@ struct gbem_ctx_s {
     double overlap_first = 0.08;
     cudaStream_t side = nullptr;
     cudaStream_t fast = nullptr;
+    // buffers of the last destroyed matrix (idle: its stream was synchronised
+    // before they came here), offered to the next matrix's allocations of the
+    // same size so that repeated extractions of one size make no allocator
+    // calls; still counted in in_use.  Dropped at the next matrix destroy,
+    // under budget pressure, when the allocator refuses, and with the context.
+    struct Spare {
+        void* p;
+        size_t bytes;
+        cudaStream_t stream;   // where the buffer was last used
+    };
+    std::vector<Spare> spare;
+    bool keep_spare = true;
 };
 
 // Kernels launched by the library in this process.
@@ -165,7 +177,8 @@ struct gbem_matrix_s {
     double* B = nullptr;
     void* W = nullptr;          // T: triangular-solve work
     bool factored = false;
-    cudaStream_t last = nullptr;
+    cudaStream_t last = nullptr;   // the stream of the last call (null: the default stream)
+    bool used = false;             // `last` holds a stream that work was enqueued on
     std::vector<std::pair<void*, size_t>> allocs;
     // Mixed mode with the assembly overlapped with the factorisation: the
     // column groups after the first, assembled on the context's side stream
@@ -189,6 +202,7 @@ struct TraceScope {
 gbem_status ctx_fail(gbem_ctx* ctx, gbem_status st, const std::string& msg);
 void* ctx_alloc(gbem_ctx* ctx, size_t bytes, cudaStream_t s);
 void ctx_free(gbem_ctx* ctx, void* p, size_t bytes, cudaStream_t s);
+void ctx_drop_spare(gbem_ctx* ctx);
 
 // ---- mesher (mesh.cpp)
 gbem_status mesh_build_boxes(const gbem_box* boxes, int nbox, const gbem_mesh_params* p,

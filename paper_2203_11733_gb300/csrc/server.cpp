@@ -197,6 +197,9 @@ gbem_status gbem_server_create(int device, size_t hbm_budget, int slots, gbem_pr
         // requests overlap one another; within a request the assembly is
         // not overlapped with the factorisation
         if (st == GBEM_OK) st = gbem_set_overlap(ctx, 1, 0.08);
+        // a worker's next request has its own size and its memory is
+        // reserved at admission: keep no buffers between requests
+        if (st == GBEM_OK) ctx->keep_spare = false;
         if (st == GBEM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = GBEM_ERR_CUDA;
         if (st != GBEM_OK) {
             if (ctx) gbem_destroy(ctx);
