@@ -397,6 +397,9 @@ def run_ours(args):
         err_fp64 = float(np.max(np.abs(C_fp64 - C_ref)) / scale)
 
     roof, kern = roofline(kst, args.steps, ms_traced / args.steps)
+    # the same pairs over the assembly phase alone (its CUDA-event time)
+    asm_ms = stats["ms"][PHASES.index("assemble")] / args.steps
+    asm_rate = world * pairs / (asm_ms * 1e-3) if asm_ms > 0 else None
     line = None
     if rank == 0:
         cpu = None
@@ -412,6 +415,7 @@ def run_ours(args):
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "extractions_per_s": world * 1e3 / ms_step,
+            "assembly_pairs_per_s": asm_rate,
             "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, stats["ms"])},
             "fp64": {"value": world * pairs / (ms64_step * 1e-3), "ms_per_step": ms64_step,
                      "extractions_per_s": world * 1e3 / ms64_step,
