@@ -1,11 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the GBEM hot path on GB300.
 
-One step = one full capacitance extraction of the 2x2 crossing bus
-(N = 6264 edge-graded panels, 4 conductors, eps_r 3.9): Galerkin assembly
-(Sec. 3.4, Eq. "matrix"), Cholesky factorisation (Sec. 3.2), solve with one
-right-hand side per conductor plus FP64 refinement (Eq. "lineareq1") and the
-charge reduction to the Maxwell matrix (Eq. "electriccharge").
+One step = one full capacitance extraction of the three-layer 5x5x5 crossing
+bus (N = 23172 edge-graded panels, 15 conductors, eps_r 3.9), the largest
+single-GPU workload: Galerkin assembly (Sec. 3.4, Eq. "matrix"), Cholesky
+factorisation (Sec. 3.2), the solve with one right-hand side per conductor
+plus FP64 refinement (Eq. "lineareq1") and the charge reduction to the
+Maxwell matrix (Eq. "electriccharge").  The 2x2 crossing bus (N = 6264, 4
+conductors) is measured the same way and reported under ``secondary``.
 
 metric: panel-pair integrals/s = N(N+1)/2 unique pair integrals of the
 extraction per second of the whole extraction (the paper's Table 2 setting:
@@ -23,6 +25,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -31,7 +34,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "crossing_bus_2x2"
+WORKLOAD = "bus_3layer_5x5x5"
+SECONDARY = "crossing_bus_2x2"
+DESCRIPTION = {
+    "bus_3layer_5x5x5": "three-layer 5x5x5 crossing bus, 15 conductors, edge-graded",
+    "crossing_bus_2x2": "2x2 crossing bus, 0.1 um wires, edge-graded",
+}
 METRIC = "panel-pair integrals/s"
 UNIT = "pairs/s"
 
@@ -40,18 +48,26 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 30; 10 for --impl reference)")
+                    help="timed steps (default 20; 10 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--secondary-steps", type=int, default=30)
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-pairs", type=int, default=200000)
-    ap.add_argument("--workload", default="crossing_bus_2x2", choices=["crossing_bus_2x2", "batch512", "serving"],
-                    help="crossing_bus_2x2: the headline line; batch512 / serving: the batched and served forms")
+    ap.add_argument("--cpu-rows", type=int, default=24,
+                    help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch512", "serving"],
+                    help="headline: the three-layer bus (and the 2x2 bus as secondary); "
+                         "batch512 / serving: the batched and served forms")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serve-rates", default="0.8",
+                    help="comma-separated arrival rates as fractions of the measured capacity")
+    ap.add_argument("--serve-fp64-loop", type=int, default=-1,
+                    help="requests of the stream the one-at-a-time FP64 loop runs (-1: all)")
     ap.add_argument("--profile", default=None, choices=["mixed", "fp64"],
                     help="one warm-up and one extraction in that precision, nothing else "
                          "(for ncu captures)")
@@ -60,7 +76,7 @@ def parse():
                     help="structure of the --profile run (two_bars: a small case for pass counts)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 10 if args.impl == "reference" else 30
+        args.steps = 10 if args.impl == "reference" else 20
     return args
 
 
@@ -204,57 +220,115 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
 
-def cpu_baseline(n_sample: int):
-    """Time the FP64 oracle on a bounded sample: its assembly rate on random
-    entries of the workload's matrix, plus a full-size Cholesky factorisation
-    and solve (scipy LAPACK, as the oracle solves), scaled to one extraction."""
+def cpu_model() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_rows(O, a, g, rows, threads):
+    """Seconds the oracle takes for the whole matrix rows `rows` (every
+    pair class appears in a row in its proportion of the whole matrix)."""
+    import numpy as np
+    n = len(a)
+    I = np.repeat(np.asarray(rows, dtype=np.int64), n)
+    J = np.tile(np.arange(n), len(rows))
+    t0 = time.perf_counter()
+    O.entries(a, g, I, J, nthreads=threads)
+    return time.perf_counter() - t0
+
+
+def _lapack_factor_solve(n: int, nrhs: int, n_max: int):
+    """LAPACK dpotrf + dpotrs (scipy, the oracle's own solver) on an SPD
+    matrix of order m = min(n, n_max); returns (m, factor s, solve s), the
+    times scaled to order n by (n/m)^3 and (n/m)^2 when m < n."""
     import numpy as np
     import scipy.linalg as sla
+    m = min(n, n_max)
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((m, 64))
+    A = M @ M.T / 64 + np.eye(m)
+    B = rng.standard_normal((m, nrhs))
+    t0 = time.perf_counter()
+    cf = sla.cho_factor(A, lower=True, overwrite_a=True, check_finite=False)
+    t1 = time.perf_counter()
+    sla.cho_solve(cf, B, check_finite=False)
+    t2 = time.perf_counter()
+    return m, (t1 - t0) * (n / m) ** 3, (t2 - t1) * (n / m) ** 2
+
+
+def cpu_baseline(workload: str, rows_all: int, rows_single: int, lapack_max: int = 12000):
+    """The FP64 oracle timed on the host cores on a bounded sample of one
+    extraction of `workload`: its entry rate on whole random rows of the
+    matrix with all threads and with one thread, plus LAPACK's Cholesky and
+    solve (scipy; scaled from order `lapack_max` when N is larger), summed
+    into the time of one extraction."""
+    import numpy as np
     from oracle import oracle as O
     from paper_2203_11733_gb300 import workloads as W
-    boxes, params = getattr(W, WORKLOAD)()
+    boxes, params = getattr(W, workload)()
     a, g, c = O.mesh_boxes(boxes, **params)
     n = len(a)
-    rng = np.random.default_rng(1)
-    I = rng.integers(0, n, n_sample)
-    J = rng.integers(0, n, n_sample)
-    t0 = time.perf_counter()
-    O.entries(a, g, I, J)
-    t_entries = time.perf_counter() - t0
-    rate = n_sample / t_entries
-    # factor + solve at full size on an SPD matrix of the same order
-    M = rng.standard_normal((n, 64))
-    A = M @ M.T / 64 + np.eye(n)
-    B, _ = O.rhs(c)
-    t0 = time.perf_counter()
-    cf = sla.cho_factor(A, lower=True)
-    sla.cho_solve(cf, B)
-    t_solve = time.perf_counter() - t0
+    nc = len(np.unique(c))
+    threads = O.max_threads()
+    rng = np.random.default_rng(5)
+    rows = rng.choice(n, size=rows_all, replace=False)
+    t_all = _oracle_rows(O, a, g, rows, threads)
+    rate_all = rows_all * n / t_all
+    t_one = _oracle_rows(O, a, g, rows[:rows_single], 1) if rows_single > 0 else None
+    _oracle_rows(O, a, g, rows[:1][:0], threads)    # leave the oracle's thread count at all cores
+    rate_one = rows_single * n / t_one if t_one else None
+    m, t_f, t_s = _lapack_factor_solve(n, nc, lapack_max)
     pairs = n * (n + 1) / 2
-    t_extract = pairs / rate + t_solve
-    return {
-        "value": pairs / t_extract, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-        "sample": (f"{n_sample} random entries of the {n}-panel matrix in {t_entries:.1f} s "
-                   f"({rate:.0f} entries/s) plus a full {n}x{n} Cholesky and {B.shape[1]}-RHS "
-                   f"solve ({t_solve:.2f} s); one extraction estimated at {t_extract:.0f} s"),
+    t_extract = pairs / rate_all + t_f + t_s
+    out = {
+        "value": pairs / t_extract, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sample": (f"{rows_all} whole random rows of the {n}-panel matrix ({rows_all * n} entries) in "
+                   f"{t_all:.1f} s on {threads} threads ({rate_all:.0f} entries/s), plus LAPACK dpotrf "
+                   f"{'at order ' + str(m) + ' scaled by (N/m)^3' if m < n else 'at full order'} "
+                   f"({t_f:.1f} s) and the {nc}-RHS solve ({t_s:.2f} s); one extraction estimated at "
+                   f"{t_extract:.0f} s"),
+        "cpu_model": cpu_model(),
+        "assembly_pairs_per_s_all_cores": rate_all,
+        "lapack": {"order_timed": m, "dpotrf_s_at_N": t_f, "dpotrs_s_at_N": t_s,
+                   "dpotrf_gflop_per_s": n ** 3 / 3 / t_f / 1e9},
         "extraction_s": t_extract,
     }
+    if rate_one:
+        out["single_thread"] = {"assembly_pairs_per_s": rate_one, "rows": rows_single,
+                                "seconds": t_one,
+                                "assembly_s_estimate": pairs / rate_one}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores; each
+    step a bounded sample (two whole rows and a scaled LAPACK Cholesky) of
+    one extraction of the headline workload."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    per_step = max(500, args.cpu_sample_pairs // 4)
     for _ in range(args.warmup):
-        cpu_baseline(200)
+        cpu_baseline(WORKLOAD, 1, 0, lapack_max=2048)
     vals = []
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(per_step)
+        last = cpu_baseline(WORKLOAD, 2, 0, lapack_max=4096)
         vals.append(last["value"])
     wall = time.perf_counter() - t0
     value = sum(vals) / len(vals)
@@ -262,13 +336,134 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_panels": 6264, "n_cond": 4,
-                                        "precision": "fp64 (CPU oracle)"},
+        "data": "synthetic", "config": {"workload": f"{WORKLOAD} ({DESCRIPTION[WORKLOAD]})",
+                                        "n_panels": 23172, "n_cond": 15, "precision": "fp64 (CPU oracle)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                         "sample": last["sample"]},
+                         "sample": last["sample"], "cpu_model": last["cpu_model"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- rooflines
+
+PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
+
+KERNEL_NAMES = {
+    "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
+    "factor": "factor_step: one launch per elimination step (panel rows, strip update, next diagonal "
+              "block factor+inverse, tcgen05 3xTF32 trailing tiles)",
+    "sweep": "sweep_fwd_f32/sweep_bwd_f32: persistent cooperative triangular sweeps (x_b = z_b - M_b x_p)",
+    "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
+}
+# measured on this GB300 (profiles/gb300_alu_rates.md): operations per second
+MUFU_RSQRT_PER_S = 4.70e12
+DFMA_PER_S = 5.04e11
+# FP64 cost of one corner term of the near-field closed forms, in DFMA
+# equivalents of the measured library rates (sqrt 8.6, log 3.6, atan 29):
+# F = 2 log + 1 atan + 1 sqrt + about 25 arithmetic operations; H = 3 log +
+# 3 atan + 1 sqrt + about 40 (16 corner terms per pair)
+F_TERM_DFMA = 2 * 3.6 + 29 + 8.6 + 25
+H_TERM_DFMA = 3 * 3.6 + 3 * 29 + 8.6 + 40
+# FP64 far-field evaluation (FP64 mode): 3 differences, r^2 (3), the rsqrt
+# estimate and its Newton step (4), the weighted sum (1)
+FAR_EVAL_DFMA_FP64 = 11.0
+TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 rates of the part
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "MEASURED_PEAKS.json (of measured)"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "recipe fallback 6.8 TB/s, 1.9 PF bf16 (of fallback)"}
+
+
+def traffic_per_launch(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    profiles/traffic_<workload>_mixed.md (dram__bytes_read.sum +
+    dram__bytes_write.sum over one factorisation's launches, divided by
+    their number), or None."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}_mixed.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(parts) >= 3 and parts[0] == kernel:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
+
+
+def assembly_work(cls, mixed=True):
+    """Algorithmic work of one assembly from its 14 class counts: far-field
+    1/r evaluations (n^4 per pair of order n) and FP64 corner-term work of
+    the near pairs, with the time each needs at the measured unit rates."""
+    far_evals = sum(n ** 4 * (int(cls[2 * n]) + int(cls[2 * n + 1])) for n in range(1, 7))
+    near_dfma = 16 * (F_TERM_DFMA * int(cls[0]) + H_TERM_DFMA * int(cls[1]))
+    if mixed:
+        t_far = far_evals / MUFU_RSQRT_PER_S
+        t_near = near_dfma / DFMA_PER_S
+    else:
+        t_far = 0.0
+        t_near = (near_dfma + FAR_EVAL_DFMA_FP64 * far_evals) / DFMA_PER_S
+    return {"far_evaluations": far_evals, "near_pairs_parallel": int(cls[0]),
+            "near_pairs_perpendicular": int(cls[1]), "near_fp64_dfma_equiv": near_dfma,
+            "t_far_bound_ms": 1e3 * t_far, "t_near_bound_ms": 1e3 * t_near}
+
+
+def kernel_table(kst, steps, n, cls, peaks, workload):
+    """Per traced kernel: time per step and launch, its algorithmic work rate
+    and the fraction of the bound that applies to it."""
+    out = {}
+    useful = n ** 3 / 3.0                                   # Cholesky, per factorisation
+    tf32 = peaks["bf16_tflops"] * TF32_OVER_BF16
+    for k, d in kst.items():
+        if d["launches"] == 0:
+            continue
+        t = d["ms"] / d["launches"] * 1e-3
+        e = {"ms_per_step": d["ms"] / steps, "launches_per_step": d["launches"] / steps,
+             "us_per_launch": t * 1e6}
+        if k == "factor":
+            per_launch = useful / (d["launches"] / steps)
+            e.update({"bound": "tensor", "unit": "TFLOP/s", "achieved": per_launch / t / 1e12,
+                      "peak": tf32 / 3.0,
+                      "peak_source": f"bf16 {peaks['bf16_tflops']:.1f} TF/s x 1.1/2.25 (TF32) / 3 "
+                                     f"(3xTF32 products per useful flop), {peaks['source']}",
+                      "work_per_launch": per_launch, "work": "N^3/3 useful flop per factorisation",
+                      "method_bytes_per_launch": 4.0 * n * n / (d["launches"] / steps),
+                      "traffic": traffic_per_launch(workload, "factor")})
+        elif k == "assemble":
+            w = assembly_work(cls)
+            t_bound = max(w["t_far_bound_ms"], w["t_near_bound_ms"]) * 1e-3
+            e.update({"bound": "alu", "unit": "1/r evaluations/s",
+                      "achieved": w["far_evaluations"] / t, "peak": MUFU_RSQRT_PER_S,
+                      "peak_source": "measured MUFU rsqrt rate (profiles/gb300_alu_rates.md)",
+                      "frac_of_alu_bound": t_bound / t, "work": w, "traffic": None,
+                      "work_per_launch": w["far_evaluations"]})
+        else:
+            e.update({"bound": "hbm", "unit": "GB/s", "achieved": d["bytes"] / d["launches"] / t / 1e9,
+                      "peak": peaks["hbm_gbs"], "peak_source": peaks["source"],
+                      "work_per_launch": d["bytes"] / d["launches"], "traffic": None})
+        e["frac"] = e["achieved"] / e["peak"] if k != "assemble" else e["frac_of_alu_bound"]
+        out[k] = e
+    return out
+
+
+def roofline(kern, kst, steps, ms_traced_step):
+    """The roofline object of the kernel with the largest device time."""
+    dom = max((k for k in kern if k in kst), key=lambda k: kst[k]["ms"])
+    e = kern[dom]
+    out = {"kernel": KERNEL_NAMES[dom], "share_of_traced_step": e["ms_per_step"] / ms_traced_step,
+           "launches_per_step": e["launches_per_step"], "us_per_launch": e["us_per_launch"]}
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source", "work_per_launch",
+                "work", "method_bytes_per_launch"):
+        if key in e:
+            out[key] = e[key]
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -285,8 +480,7 @@ def run_ours(args):
         B.build()
     if world > 1:
         torch.distributed.barrier()
-    lib = gbem.load()
-    boxes, params = getattr(W, args.profile_workload if args.profile else WORKLOAD)()
+    gbem.load()
     eps_r = W.EPS_R_SIO2
     ctx = gbem.Context(local)
     stream = torch.cuda.Stream()
@@ -297,24 +491,22 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    mesh = gbem.gbem_mesh(ctx, boxes, params)
-    n, nc = mesh.n, mesh.n_cond
-    pairs = n * (n + 1) / 2
-
-    def step(prec):
+    def step(mesh, prec):
         mat = gbem.gbem_assemble(mesh, prec, stream)
         C, _ = gbem.gbem_capacitance(mesh, mat, eps_r, stream, want_residual=False)
         mat.close()
         return C
 
     if args.profile:
+        boxes, params = getattr(W, args.profile_workload)()
+        mesh = gbem.gbem_mesh(ctx, boxes, params)
         prec = gbem.GBEM_MIXED if args.profile == "mixed" else gbem.GBEM_FP64
-        step(prec)
+        step(mesh, prec)
         torch.cuda.synchronize()
-        C = step(prec)
+        C = step(mesh, prec)
         torch.cuda.synchronize()
         if rank == 0:
-            print(json.dumps({"profile": args.profile, "n_panels": n, "C": C.tolist()}))
+            print(json.dumps({"profile": args.profile, "n_panels": mesh.n, "C": C.tolist()}))
         mesh.close()
         ctx.close()
         return
@@ -323,6 +515,7 @@ def run_ours(args):
         """k steps timed with CUDA events on the launching stream, L2 flushed
         (untimed) before each; returns total ms, max over ranks."""
         total = 0.0
+        out = None
         for _ in range(k):
             if flush_between:
                 with torch.cuda.stream(stream):
@@ -336,176 +529,137 @@ def run_ours(args):
             total += e0.elapsed_time(e1)
         return max_over_ranks(total, world), out
 
-    # ---- mixed precision (the headline path)
+    def measure(workload, steps, fp64_steps, clocks=None):
+        """Mixed extractions (timed, then traced), the FP64 extraction on the
+        same GPU, the end-to-end form and the error against the stored
+        oracle result, for one workload."""
+        boxes, params = getattr(W, workload)()
+        mesh = gbem.gbem_mesh(ctx, boxes, params)
+        n, nc = mesh.n, mesh.n_cond
+        pairs = n * (n + 1) / 2
+        for _ in range(args.warmup):
+            step(mesh, gbem.GBEM_MIXED)
+        barrier()
+        gbem.set_timing(ctx, 1)
+        gbem.get_stats(ctx, reset=True)
+        if clocks:
+            clocks.begin()
+        ms_total, C_mixed = timed(lambda: step(mesh, gbem.GBEM_MIXED), steps)
+        if clocks:
+            clocks.end()
+        barrier()
+        stats = gbem.get_stats(ctx, reset=True)
+        ms_step = ms_total / steps
+        # the same steps again with an event pair around every launch of the
+        # traced kernels (kept out of the headline timing: the events cost time)
+        gbem.set_timing(ctx, 2)
+        gbem.get_kernel_stats(ctx, reset=True)
+        ms_traced, _ = timed(lambda: step(mesh, gbem.GBEM_MIXED), steps)
+        kst = gbem.get_kernel_stats(ctx, reset=True)
+        gbem.set_timing(ctx, 0)
+        gbem.get_stats(ctx, reset=True)
+        # class counts and the final refinement residual (one extra, untimed extraction)
+        mat = gbem.gbem_assemble(mesh, gbem.GBEM_MIXED, stream)
+        cls = mat.class_counts()
+        _, ir_residual = gbem.gbem_capacitance(mesh, mat, eps_r, stream, want_residual=True)
+        mat.close()
+        # FP64 path on the same GPU
+        step(mesh, gbem.GBEM_FP64)
+        barrier()
+        gbem.set_timing(ctx, 1)
+        gbem.get_stats(ctx, reset=True)
+        ms64, C_fp64 = timed(lambda: step(mesh, gbem.GBEM_FP64), fp64_steps)
+        stats64 = gbem.get_stats(ctx, reset=True)
+        gbem.set_timing(ctx, 0)
+        ms64_step = ms64 / fp64_steps
+        mesh.close()
+        # end to end: host boxes -> mesh + upload -> ... -> C on the host
+        def step_e2e():
+            return gbem.extract(ctx, boxes, params, eps_r, precision=gbem.GBEM_MIXED, stream=stream)[0]
+        step_e2e()
+        barrier()
+        ms_e2e, _ = timed(step_e2e, steps)
+        gold_path = os.path.join(ROOT, "tests", "golden", f"{workload}_capacitance.json")
+        err_mixed = err_fp64 = None
+        if os.path.exists(gold_path):
+            C_ref = np.array(json.load(open(gold_path))["C"])
+            scale = np.max(np.abs(C_ref))
+            err_mixed = float(np.max(np.abs(C_mixed - C_ref)) / scale)
+            err_fp64 = float(np.max(np.abs(C_fp64 - C_ref)) / scale)
+        peaks = _peaks()
+        kern = kernel_table(kst, steps, n, cls, peaks, workload)
+        kern["traced_ms_per_step"] = ms_traced / steps
+        asm_ms = stats["ms"][PHASES.index("assemble")] / steps
+        return {
+            "n": n, "nc": nc, "pairs": pairs, "ms_step": ms_step, "ms_total": ms_total,
+            "value": whole_job_rate(pairs * steps, world, ms_total * 1e-3),
+            "extractions_per_s": world * 1e3 / ms_step,
+            "assembly_pairs_per_s": world * pairs / (asm_ms * 1e-3) if asm_ms > 0 else None,
+            "phase_ms_per_step": {k: v / steps for k, v in zip(PHASES, stats["ms"])},
+            "launches": int(stats["launches"]),
+            "fp64": {"value": world * pairs / (ms64_step * 1e-3), "ms_per_step": ms64_step,
+                     "extractions_per_s": world * 1e3 / ms64_step,
+                     "phase_ms_per_step": {k: v / fp64_steps for k, v in zip(PHASES, stats64["ms"])},
+                     "cap_rel_err_vs_oracle": err_fp64},
+            "mixed_over_fp64": ms64_step / ms_step,
+            "cap_rel_err_vs_oracle": err_mixed, "ir_residual": ir_residual,
+            "e2e": {"value": whole_job_rate(pairs * steps, world, ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": n * (5 * 8 + 1 + 4), "d2h_bytes_per_step": nc * nc * 8,
+                    "ms_per_step": ms_e2e / steps},
+            "kernels": kern, "kst": kst, "ms_traced_step": ms_traced / steps,
+            "class_counts": [int(x) for x in cls],
+        }
+
     clocks = ClockSampler(local)
     clocks.start()
-    for _ in range(args.warmup):
-        step(gbem.GBEM_MIXED)
-    barrier()
-    gbem.set_timing(ctx, 1)
-    stats = gbem.get_stats(ctx, reset=True)
-    clocks.begin()
-    ms_total, C_mixed = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
-    clocks.end()
+    head = measure(WORKLOAD, args.steps, args.fp64_steps, clocks)
     clk = clocks.stop()
-    barrier()
-    stats = gbem.get_stats(ctx, reset=True)
-    ms_step = ms_total / args.steps
-    value = whole_job_rate(pairs * args.steps, world, ms_total * 1e-3)
-
-    # ---- the same steps again with an event pair around every launch of the
-    # traced kernels (kept out of the headline timing: the events cost time)
-    gbem.set_timing(ctx, 2)
-    gbem.get_kernel_stats(ctx, reset=True)
-    ms_traced, _ = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
-    kst = gbem.get_kernel_stats(ctx, reset=True)
-    gbem.set_timing(ctx, 0)
-    gbem.get_stats(ctx, reset=True)
-
-    # the final relative residual of the refinement (one extra, untimed extraction)
-    mat_r = gbem.gbem_assemble(mesh, gbem.GBEM_MIXED, stream)
-    _, ir_residual = gbem.gbem_capacitance(mesh, mat_r, eps_r, stream, want_residual=True)
-    mat_r.close()
-
-    # ---- FP64 path on the same GPU
-    step(gbem.GBEM_FP64)
-    barrier()
-    gbem.set_timing(ctx, 1)
-    gbem.get_stats(ctx, reset=True)
-    ms64, C_fp64 = timed(lambda: step(gbem.GBEM_FP64), args.fp64_steps)
-    stats64 = gbem.get_stats(ctx, reset=True)
-    gbem.set_timing(ctx, 0)
-    ms64_step = ms64 / args.fp64_steps
-
-    # ---- end to end: host boxes -> mesh + upload -> ... -> C on the host
-    def step_e2e():
-        return gbem.extract(ctx, boxes, params, eps_r, precision=gbem.GBEM_MIXED, stream=stream)[0]
-    step_e2e()
-    barrier()
-    ms_e2e, _ = timed(step_e2e, args.steps)
-    value_e2e = whole_job_rate(pairs * args.steps, world, ms_e2e * 1e-3)
-    h2d = n * (5 * 8 + 1 + 4)
-    d2h = nc * nc * 8
-
-    # ---- accuracy against the stored oracle result
-    gold_path = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_capacitance.json")
-    err_mixed = err_fp64 = None
-    if os.path.exists(gold_path):
-        C_ref = np.array(json.load(open(gold_path))["C"])
-        scale = np.max(np.abs(C_ref))
-        err_mixed = float(np.max(np.abs(C_mixed - C_ref)) / scale)
-        err_fp64 = float(np.max(np.abs(C_fp64 - C_ref)) / scale)
-
-    roof, kern = roofline(kst, args.steps, ms_traced / args.steps)
-    # the same pairs over the assembly phase alone (its CUDA-event time)
-    asm_ms = stats["ms"][PHASES.index("assemble")] / args.steps
-    asm_rate = world * pairs / (asm_ms * 1e-3) if asm_ms > 0 else None
+    sec = None
+    if not args.no_secondary:
+        sec = measure(SECONDARY, args.secondary_steps, max(2, args.fp64_steps))
     line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(args.cpu_sample_pairs)
+            cpu = cpu_baseline(WORKLOAD, args.cpu_rows, 2)
             cpu.pop("extraction_s", None)
+        kern = dict(head["kernels"])
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} (2x2 crossing bus, 0.1 um wires, edge-graded)",
-                       "n_panels": n, "n_cond": nc, "eps_r": eps_r, "precision": "mixed",
-                       "l2": "flushed (512 MB write) before every timed step",
+            "config": {"workload": f"{WORKLOAD} ({DESCRIPTION[WORKLOAD]})",
+                       "n_panels": head["n"], "n_cond": head["nc"], "eps_r": eps_r, "precision": "mixed",
+                       "l2": "flushed (512 MB write) before every timed step; matrices of 6.5 GB exceed L2",
                        "parallelism": f"replicas x{world}"},
-            "extractions_per_s": world * 1e3 / ms_step,
-            "assembly_pairs_per_s": asm_rate,
-            "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, stats["ms"])},
-            "fp64": {"value": world * pairs / (ms64_step * 1e-3), "ms_per_step": ms64_step,
-                     "extractions_per_s": world * 1e3 / ms64_step,
-                     "phase_ms_per_step": {k: v / args.fp64_steps for k, v in zip(PHASES, stats64["ms"])},
-                     "cap_rel_err_vs_oracle": err_fp64},
-            "mixed_over_fp64": ms64_step / ms_step,
-            "cap_rel_err_vs_oracle": err_mixed,
-            "ir_residual": ir_residual,
-            "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e / args.steps},
-            "gpu_launches": int(stats["launches"]),
-            "roofline": roof,
+            "extractions_per_s": head["extractions_per_s"],
+            "assembly_pairs_per_s": head["assembly_pairs_per_s"],
+            "phase_ms_per_step": head["phase_ms_per_step"],
+            "fp64": head["fp64"], "mixed_over_fp64": head["mixed_over_fp64"],
+            "cap_rel_err_vs_oracle": head["cap_rel_err_vs_oracle"], "ir_residual": head["ir_residual"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["launches"],
+            "roofline": roofline(kern, head["kst"], args.steps, head["ms_traced_step"]),
             "kernels": kern,
+            "assembly_class_counts": head["class_counts"],
             "clocks": clk,
         }
+        if sec is not None:
+            line["secondary"] = {
+                "workload": f"{SECONDARY} ({DESCRIPTION[SECONDARY]})", "n_panels": sec["n"], "n_cond": sec["nc"],
+                "steps": args.secondary_steps, "metric": METRIC, "value": sec["value"], "unit": UNIT,
+                "ms_per_step": sec["ms_step"], "extractions_per_s": sec["extractions_per_s"],
+                "assembly_pairs_per_s": sec["assembly_pairs_per_s"], "phase_ms_per_step": sec["phase_ms_per_step"],
+                "fp64": sec["fp64"], "mixed_over_fp64": sec["mixed_over_fp64"],
+                "cap_rel_err_vs_oracle": sec["cap_rel_err_vs_oracle"], "ir_residual": sec["ir_residual"],
+                "e2e": sec["e2e"], "roofline": roofline(sec["kernels"], sec["kst"], args.secondary_steps,
+                                                         sec["ms_traced_step"]),
+                "kernels": sec["kernels"], "gpu_launches": sec["launches"]}
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
-    mesh.close()
     ctx.close()
     dist_stop(world)
-
-
-PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
-
-
-KERNEL_NAMES = {
-    "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
-    "factor": "factor_step: one launch per elimination step (panel rows, strip update, next diagonal "
-              "block factor+inverse, tcgen05 3xTF32 trailing tiles)",
-    "sweep": "sweep_fwd_f32/sweep_bwd_f32: persistent cooperative triangular sweeps (x_b = z_b - M_b x_p)",
-    "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
-}
-FP64_PEAK_TF = 1.25   # nominal GB300 FP64 (non-tensor) rate
-
-
-def traffic_per_launch(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (dram__bytes_read.sum + dram__bytes_write.sum over one factorisation's
-    launches, divided by their number), or None."""
-    p = os.path.join(ROOT, "profiles", f"traffic_{WORKLOAD}_mixed.md")
-    if not os.path.exists(p):
-        return None
-    for line in open(p):
-        parts = [x.strip() for x in line.strip().strip("|").split("|")]
-        if len(parts) >= 3 and parts[0] == kernel:
-            try:
-                return float(parts[2])
-            except ValueError:
-                return None
-    return None
-
-
-def roofline(kst, steps, ms_traced_step):
-    """Roofline of the kernel with the largest device time in the traced
-    pass.  achieved = its algorithmic bytes (or flops) per launch, as the
-    library reports them for every launch, over its average CUDA-event
-    launch duration on the launching stream."""
-    peaks = {}
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        peaks = json.load(open(p))
-    kern = {}
-    for k, d in kst.items():
-        if d["launches"] == 0:
-            continue
-        t = d["ms"] / d["launches"] * 1e-3
-        kern[k] = {"ms_per_step": d["ms"] / steps, "launches_per_step": d["launches"] / steps,
-                   "us_per_launch": t * 1e6,
-                   "gb_per_s": d["bytes"] / d["launches"] / t / 1e9,
-                   "tflop_per_s": d["flops"] / d["launches"] / t / 1e12}
-    kern["traced_ms_per_step"] = ms_traced_step
-    names = [k for k in kst if kst[k]["launches"] > 0]
-    dom = max(names, key=lambda k: kst[k]["ms"])
-    d = kst[dom]
-    t = d["ms"] / d["launches"] * 1e-3
-    out = {"kernel": KERNEL_NAMES[dom], "share_of_traced_step": d["ms"] / steps / ms_traced_step,
-           "launches_per_step": d["launches"] / steps, "us_per_launch": t * 1e6}
-    if dom == "residual":
-        out.update({"bound": "alu", "achieved": d["flops"] / d["launches"] / t / 1e12, "peak": FP64_PEAK_TF,
-                    "unit": "TFLOP/s", "peak_source": "nominal FP64 rate (no measured FP64 peak)",
-                    "work_per_launch": d["flops"] / d["launches"], "traffic": None})
-    else:
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
-        out.update({"bound": "hbm", "achieved": d["bytes"] / d["launches"] / t / 1e9, "peak": hbm,
-                    "unit": "GB/s", "peak_source": src, "work_per_launch": d["bytes"] / d["launches"],
-                    "traffic": traffic_per_launch(dom)})
-    out["frac"] = out["achieved"] / out["peak"]
-    return out, kern
 
 
 def run_batch(args):

@@ -117,19 +117,6 @@ gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget,
 void gbem_destroy(gbem_ctx* ctx);
 const char* gbem_last_error(const gbem_ctx* ctx);
 gbem_status gbem_set_tuning(gbem_ctx* ctx, const gbem_tuning* t);
-/* Mixed mode: overlap the assembly with the factorisation.  gbem_assemble
- * assembles the first columns (about `first_fraction` of the lower entries,
- * at least three 64-column blocks) on the caller's stream and the rest in
- * `groups - 1` column groups of equal entry counts on a low-priority stream
- * of the context; gbem_factor then runs on a high-priority stream and adds
- * each group into the FP32 copy before the first elimination step that reads
- * it (Sec. 3.4 entries, Cholesky blocked by 64 columns).  groups <= 1 turns
- * the overlap off.  Calls on a stream under graph capture never overlap.
- * Default: off (groups 1, first_fraction 0.08): on a GB300 the co-running
- * assembly tiles slow the latency-bound elimination steps by more than the
- * assembly time they hide.  The environment variable GBEM_OVERLAP
- * ("groups[,first_fraction]") sets a context's initial values. */
-gbem_status gbem_set_overlap(gbem_ctx* ctx, int groups, double first_fraction);
 /* Bytes currently held by the context: its handles' buffers, and the
  * buffers of the last destroyed matrix, which the context keeps (idle) for
  * the next matrix's allocations of the same size and releases at the next
@@ -171,9 +158,12 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
                           gbem_matrix_t** out);
 
 /* Cholesky factorisation A = L L^T (Sec. 3.2), blocked, on `stream`.  FP64
- * mode factors an FP64 copy; mixed mode factors the FP32 copy (diagonal
- * blocks in FP64 arithmetic).  A non-positive pivot is recorded and reported
- * by the next waiting call as GBEM_ERR_NOT_SPD. */
+ * mode factors an FP64 copy in FP64 arithmetic.  Mixed mode factors the FP32
+ * copy in place entirely in FP32 arithmetic -- the 64 x 64 diagonal blocks
+ * and their inverses included -- with the trailing updates on the tensor
+ * cores in 3xTF32; the FP64 refinement of gbem_solve restores the accuracy.
+ * A non-positive pivot is recorded and reported by the next waiting call as
+ * GBEM_ERR_NOT_SPD. */
 gbem_status gbem_factor(gbem_matrix_t* mat, gbem_stream stream);
 
 /* Solve A X = B for nrhs right-hand sides on `stream`.  B_dev and X_dev are
@@ -198,12 +188,26 @@ gbem_status gbem_solve(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ld
  * the library holds until the process exits; a call needing more
  * (5 * 8 * padded N * nrhs bytes plus 256 plus 4 bytes per 64 rows, each term
  * rounded up to 256) fails with GBEM_ERR_ARG.  The first call on a device
- * looks up the array's device address (call it once before any stream
- * capture).  The call waits for its stream before returning.  All calls share
- * the array: calls that overlap on the GPU race and must be serialised by the
+ * looks up the array's device address; make that first call before any
+ * stream capture begins.  Every call copies its status words back and waits
+ * for its stream before returning, on success and on every error after the
+ * argument checks.  All calls share the array and it keeps the last call's
+ * contents: calls that overlap on the GPU race and must be serialised by the
  * caller. */
 gbem_status gbem_solve_noalloc(gbem_matrix_t* mat, const double* B_dev, int nrhs, int ldb,
                                double* X_dev, int ldx, int* ir_iters, gbem_stream stream);
+
+/* Self-test of the bounded device waits (no counterpart in the paper: a
+ * failure-detection check).  One CTA waits, through the same bounded
+ * release-flag wait that every elimination step of the mixed factorisation
+ * uses, for a device flag to become 1, with a wall-clock limit of limit_ms
+ * (0 < limit_ms <= 10000; the library's own waits use 1 s).  With
+ * set_flag != 0 the flag is written before the kernel starts and the call
+ * returns GBEM_OK; with set_flag == 0 nothing ever writes it, the wait runs
+ * out and the call returns GBEM_ERR_TIMEOUT, after which the context is
+ * still usable.  Allocates 256 bytes from the context; waits for the
+ * stream. */
+gbem_status gbem_selftest_wait(gbem_ctx* ctx, int set_flag, double limit_ms, gbem_stream stream);
 
 /* Maxwell capacitance matrix in farads, n_c x n_c row-major into C_host:
  * C[m][k] = charge on conductor m with conductor k at 1 V and the others at
@@ -322,10 +326,13 @@ gbem_status gbem_batch_autotune(gbem_ctx* ctx, int count, gbem_mesh_t* const* me
                                 const char* cache_path, gbem_batch_t** out, gbem_batch_tuning* report);
 
 /* Extraction server (continuous batching).  Requests are meshed on the host
- * when submitted, so their device footprint is known; they wait in a
- * first-in first-out queue and are admitted by `slots` worker threads (each
- * with its own context and stream) whenever a worker is free and the request
- * fits in hbm_budget bytes next to the requests already running.  Admitted
+ * when submitted, so their device footprint is known; they wait in arrival
+ * order and are admitted by `slots` worker threads (each with its own
+ * context and stream) whenever a worker is free: the first waiting request,
+ * in arrival order, that fits in hbm_budget bytes next to the requests
+ * already running.  A smaller request may pass the head of the queue while
+ * the head waits for memory, at most 8 times; then nothing is admitted
+ * before the head, so a large request is not starved.  Admitted
  * requests run concurrently and overlap on the device; geometry, matrix,
  * factor and right-hand sides stay on the device for the request's life.  A
  * request larger than the whole budget completes with GBEM_ERR_OOM.  The
@@ -363,6 +370,13 @@ void gbem_server_destroy(gbem_server_t* srv);
  * closed form, and by Gauss-Legendre order 1..6 (counts[0] closed form,
  * counts[n] order n; array of 7).  Waits for the assembly stream. */
 gbem_status gbem_matrix_info(gbem_matrix_t* mat, int* n, long long* counts);
+/* The pairs of each of the 14 evaluation classes of the assembly (array of
+ * 14): counts[0] near parallel and counts[1] near perpendicular pairs
+ * (closed-form corner sums in FP64, Sec. 3.4, Eqs. "parallel" and
+ * "orthogonal"), counts[2n] and counts[2n + 1] the parallel and
+ * perpendicular far pairs of Gauss-Legendre order n = 1..6 (n^4 evaluations
+ * of 1/r each).  Waits for the assembly stream. */
+gbem_status gbem_matrix_class_counts(gbem_matrix_t* mat, long long* counts);
 /* Waits for the matrix's last stream, then hands its device buffers to the
  * context, which offers them to the next matrix of the same size (see
  * gbem_bytes_in_use); a context made by the server frees them at once. */

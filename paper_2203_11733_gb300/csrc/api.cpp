@@ -188,21 +188,27 @@ gbem_status ensure_solve_buffers(gbem_matrix_t* m, int nrhs, cudaStream_t s)
 {
     if (m->cap_rhs >= nrhs) return GBEM_OK;
     const size_t np = (size_t)m->np;
-    // older buffers stay in the allocation list until the matrix is destroyed
-    m->X = mat_alloc<double>(m, np * nrhs, s);
-    m->R = mat_alloc<double>(m, np * nrhs, s);
-    m->B = mat_alloc<double>(m, np * nrhs, s);
-    m->dchk = mat_alloc<unsigned long long>(m, 2 * (size_t)nrhs + 1, s);
-    if (m->dchk &&
-        cudaMemsetAsync(m->dchk, 0, (2 * (size_t)nrhs + 1) * sizeof(unsigned long long), s) != cudaSuccess) {
-        cudaGetLastError();
-        return GBEM_ERR_CUDA;
-    }
+    // older buffers stay in the allocation list until the matrix is destroyed;
+    // the matrix takes the new set only once all of it is allocated, so a
+    // refusal leaves the previous, smaller set in use
+    double* X = mat_alloc<double>(m, np * nrhs, s);
+    double* R = X ? mat_alloc<double>(m, np * nrhs, s) : nullptr;
+    double* B = R ? mat_alloc<double>(m, np * nrhs, s) : nullptr;
+    unsigned long long* chk = B ? mat_alloc<unsigned long long>(m, 2 * (size_t)nrhs + 1, s) : nullptr;
     // W: FP64 mode, solve vectors and work (2 x np x nrhs doubles); mixed
     // mode, FP32 solve vectors and work, then X as float pairs (4 x np x nrhs
     // floats): the same bytes
-    m->W = mat_alloc<double>(m, 2 * np * nrhs, s);
-    if (!m->X || !m->R || !m->B || !m->W) return GBEM_ERR_OOM;
+    double* W = chk ? mat_alloc<double>(m, 2 * np * nrhs, s) : nullptr;
+    if (!W) return GBEM_ERR_OOM;
+    if (cudaMemsetAsync(chk, 0, (2 * (size_t)nrhs + 1) * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GBEM_ERR_CUDA;
+    }
+    m->X = X;
+    m->R = R;
+    m->B = B;
+    m->dchk = chk;
+    m->W = W;
     m->cap_rhs = nrhs;
     return GBEM_OK;
 }
@@ -342,98 +348,6 @@ void ctx_drop_spare(gbem_ctx* ctx)
     for (auto& a : sp) ctx_free(ctx, a.p, a.bytes, a.stream);
 }
 
-// ---- assembly overlapped with the factorisation (mixed mode)
-
-// Column groups [b_g, b_g+1) in elements, 64-aligned, b_0 = 0, last = np: the
-// first holds about `first` of the lower 64-blocks (at least three block
-// columns, which the first elimination step reads outside its tiles), the
-// others equal shares of the rest.  One group when the overlap is off or the
-// matrix is small.
-static std::vector<int> overlap_plan(const gbem_ctx* ctx, int np)
-{
-    const int nblk = np / 64;
-    std::vector<int> b{0};
-    if (ctx->overlap_groups <= 1 || nblk < 16) {
-        b.push_back(np);
-        return b;
-    }
-    // block column c holds nblk - c lower blocks
-    const double total = 0.5 * nblk * (nblk + 1.0);
-    auto before = [nblk](int c) { return c * (double)nblk - 0.5 * c * (c - 1.0); };
-    int c1 = 3;
-    while (c1 < nblk - 1 && before(c1) < ctx->overlap_first * total) ++c1;
-    b.push_back(c1 * 64);
-    const int rest = ctx->overlap_groups - 1;
-    const double w0 = before(c1);
-    for (int gi = 1; gi < rest; ++gi) {
-        const double want = w0 + (total - w0) * gi / rest;
-        int c = b.back() / 64 + 1;
-        while (c < nblk - 1 && before(c) < want) ++c;
-        if (c * 64 > b.back() && c < nblk) b.push_back(c * 64);
-    }
-    if (b.back() < np) b.push_back(np);
-    return b;
-}
-
-static bool overlap_streams(gbem_ctx* ctx)
-{
-    if (ctx->side && ctx->fast) return true;
-    int least = 0, greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-        (!ctx->side && cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least) != cudaSuccess) ||
-        (!ctx->fast && cudaStreamCreateWithPriority(&ctx->fast, cudaStreamNonBlocking, greatest) != cudaSuccess)) {
-        cudaGetLastError();
-        return false;
-    }
-    return true;
-}
-
-// `to` waits for the work `from` has queued so far.
-static cudaError_t stream_after(cudaStream_t to, cudaStream_t from)
-{
-    cudaEvent_t ev;
-    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev, from)) == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
-    cudaEventDestroy(ev);
-    return e;
-}
-
-// `s` waits for every column group still being assembled.
-static cudaError_t join_groups(gbem_matrix_t* m, cudaStream_t s)
-{
-    for (auto& gr : m->groups) {
-        cudaError_t e = cudaStreamWaitEvent(s, gr.ev, 0);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-// Before elimination step k: add in the groups whose first block column c0
-// is read finally by step c0 - 1 (its diagonal block factor and lookahead row).
-static cudaError_t add_groups_hook(void* user, int k, cudaStream_t s)
-{
-    gbem_matrix_t* m = static_cast<gbem_matrix_t*>(user);
-    for (auto& gr : m->groups) {
-        if (gr.added || gr.c0 / 64 - 1 > k) continue;
-        cudaError_t e = cudaStreamWaitEvent(s, gr.ev, 0);
-        if (e == cudaSuccess) e = launch_add_hi(m->A64, m->A32, m->np, gr.c0, gr.c1, s);
-        if (e != cudaSuccess) return e;
-        gr.added = true;
-    }
-    return cudaSuccess;
-}
-
-static bool stream_capturing(cudaStream_t s)
-{
-    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
-        cudaGetLastError();
-        return true;   // unknown: do not fork
-    }
-    return st != cudaStreamCaptureStatusNone;
-}
-
 // ------------------------------------------------------------------ ABI
 
 extern "C" {
@@ -452,15 +366,6 @@ gbem_status gbem_create(gbem_ctx** out, int device, size_t hbm_budget, gbem_allo
     ctx->free_fn = free_fn;
     ctx->user = user;
     ctx->tune = default_tuning();
-    // GBEM_OVERLAP="groups[,first_fraction]" overrides the overlap defaults
-    if (const char* ov = std::getenv("GBEM_OVERLAP")) {
-        int gr = ctx->overlap_groups;
-        double fr = ctx->overlap_first;
-        if (std::sscanf(ov, "%d,%lf", &gr, &fr) >= 1 && gr <= 64 && fr > 0.0 && fr < 1.0) {
-            ctx->overlap_groups = gr;
-            ctx->overlap_first = fr;
-        }
-    }
     if (device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || device >= count) {
@@ -492,20 +397,7 @@ void gbem_destroy(gbem_ctx* ctx)
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
-    if (ctx->side || ctx->fast) {
-        DeviceGuard g(ctx->device);
-        if (ctx->side) cudaStreamDestroy(ctx->side);
-        if (ctx->fast) cudaStreamDestroy(ctx->fast);
-    }
     delete ctx;
-}
-
-gbem_status gbem_set_overlap(gbem_ctx* ctx, int groups, double first_fraction)
-{
-    if (!ctx || !(first_fraction > 0.0 && first_fraction < 1.0) || groups > 64) return GBEM_ERR_ARG;
-    ctx->overlap_groups = groups;
-    ctx->overlap_first = first_fraction;
-    return GBEM_OK;
 }
 
 const char* gbem_last_error(const gbem_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
@@ -706,7 +598,7 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
     m->A64 = mat_alloc<double>(m, np * np, s);
     if (prec == GBEM_MIXED) m->A32 = mat_alloc<float>(m, np * np, s);
     m->dflags = mat_alloc<int>(m, 4, s);
-    m->dcounts = mat_alloc<unsigned long long>(m, 8, s);
+    m->dcounts = mat_alloc<unsigned long long>(m, 16, s);
     m->dnorm = mat_alloc<double>(m, 4, s);
     if (!m->A64 || (prec == GBEM_MIXED && !m->A32) || !m->dflags || !m->dcounts || !m->dnorm) {
         gbem_matrix_destroy(m);
@@ -714,35 +606,11 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
     }
     PhaseTimer pt(ctx, GBEM_PHASE_ASSEMBLE, s);
     const double qn = prec == GBEM_MIXED ? ctx->tune.q_near_mixed : ctx->tune.q_near_fp64;
-    std::vector<int> plan{0, m->np};
-    if (prec == GBEM_MIXED && !stream_capturing(s)) {
-        plan = overlap_plan(ctx, m->np);
-        if (plan.size() > 2 && !overlap_streams(ctx)) plan = {0, m->np};
-    }
-    bool ok = cuda_ok(ctx, cudaMemsetAsync(m->dflags, 0, 4 * sizeof(int), s), "memset") &&
-              cuda_ok(ctx, cudaMemsetAsync(m->dcounts, 0, 8 * sizeof(unsigned long long), s), "memset") &&
-              cuda_ok(ctx, launch_pad(m->A64, m->A32, m->n, m->np, s), "pad");
-    if (ok && plan.size() <= 2) {
-        ok = cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s), "assemble");
-    } else if (ok) {
-        // the first group on the caller's stream, the others (float pairs
-        // only) on the side stream while the factorisation runs
-        ok = cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s, 0, plan[1]),
-                     "assemble") &&
-             cuda_ok(ctx, stream_after(ctx->side, s), "fork");
-        for (size_t gi = 1; ok && gi + 1 < plan.size(); ++gi) {
-            gbem_matrix_t::Group gr{plan[gi], plan[gi + 1], nullptr, false};
-            ok = cuda_ok(ctx, cudaEventCreateWithFlags(&gr.ev, cudaEventDisableTiming), "event");
-            if (!ok) break;
-            m->groups.push_back(gr);
-            ok = cuda_ok(ctx,
-                         launch_assemble(mesh->dev, m->np, prec, qn, m->A64, nullptr, m->dcounts, ctx->side, gr.c0,
-                                         gr.c1),
-                         "assemble") &&
-                 cuda_ok(ctx, cudaEventRecord(gr.ev, ctx->side), "event");
-        }
-        if (ok) m->zero_col = plan[1];
-    }
+    const bool ok = cuda_ok(ctx, cudaMemsetAsync(m->dflags, 0, 4 * sizeof(int), s), "memset") &&
+                    cuda_ok(ctx, cudaMemsetAsync(m->dcounts, 0, 16 * sizeof(unsigned long long), s), "memset") &&
+                    cuda_ok(ctx, launch_pad(m->A64, m->A32, m->n, m->np, s), "pad") &&
+                    cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s),
+                            "assemble");
     if (!ok) {
         gbem_matrix_destroy(m);
         return GBEM_ERR_CUDA;
@@ -781,24 +649,10 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
         if (!m->Linv) m->Linv = mat_alloc<float>(m, nblk * m->nb * m->nb, s);
         if (!m->split) m->split = mat_alloc<unsigned char>(m, cholesky_f32_split_bytes(m->np), s);
         if (!m->Linv || !m->split) return GBEM_ERR_OOM;
-        if (m->groups.empty()) {
-            if (!cuda_ok(ctx,
-                         launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags,
-                                             m->split, s),
-                         "cholesky"))
-                return GBEM_ERR_CUDA;
-        } else {
-            // on the high-priority stream, so that its steps take the SMs
-            // first as the side stream's assembly tiles finish; each group
-            // is added in before the step that first reads it
-            if (!cuda_ok(ctx, stream_after(ctx->fast, s), "fork") ||
-                !cuda_ok(ctx,
-                         launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags,
-                                             m->split, ctx->fast, m->zero_col, add_groups_hook, m),
-                         "cholesky") ||
-                !cuda_ok(ctx, join_groups(m, ctx->fast), "join") || !cuda_ok(ctx, stream_after(s, ctx->fast), "join"))
-                return GBEM_ERR_CUDA;
-        }
+        if (!cuda_ok(ctx,
+                     launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, m->split, s),
+                     "cholesky"))
+            return GBEM_ERR_CUDA;
     }
     m->factored = true;
     m->last = s;
@@ -877,14 +731,35 @@ gbem_status gbem_capacitance(gbem_mesh_t* mesh, gbem_matrix_t* m, double eps_r, 
     return solve_st;
 }
 
+gbem_status gbem_selftest_wait(gbem_ctx* ctx, int set_flag, double limit_ms, gbem_stream stream)
+{
+    if (!ctx || !(limit_ms > 0.0) || limit_ms > 10000.0) return GBEM_ERR_ARG;
+    if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // word 0: the flag the CTA waits for; word 1: the status it reports
+    unsigned* buf = static_cast<unsigned*>(ctx_alloc(ctx, 256, s));
+    if (!buf) return GBEM_ERR_OOM;
+    int status = 0;
+    const unsigned one = 1u;
+    bool ok = cuda_ok(ctx, cudaMemsetAsync(buf, 0, 256, s), "memset") &&
+              (!set_flag || cuda_ok(ctx, cudaMemcpyAsync(buf, &one, sizeof(one), cudaMemcpyHostToDevice, s), "h2d")) &&
+              cuda_ok(ctx, launch_wait_selftest(buf, reinterpret_cast<int*>(buf + 1), limit_ms, s), "launch") &&
+              cuda_ok(ctx, cudaMemcpyAsync(&status, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h") &&
+              cuda_ok(ctx, cudaStreamSynchronize(s), "sync");
+    ctx_free(ctx, buf, 256, s);
+    if (!ok) return GBEM_ERR_CUDA;
+    if (status == GBEM_ERR_TIMEOUT) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "the bounded wait gave up (flag withheld)");
+    return status == 0 ? GBEM_OK : ctx_fail(ctx, GBEM_ERR_CUDA, "unexpected self-test status");
+}
+
 gbem_status gbem_matrix_download(gbem_matrix_t* m, double* host)
 {
     if (!m || !host) return GBEM_ERR_ARG;
     gbem_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
     const int n = m->n, np = m->np;
-    if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync"))
-        return GBEM_ERR_CUDA;
+    if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync")) return GBEM_ERR_CUDA;
     // column j of the lower triangle: rows j..n-1
     if (!cuda_ok(ctx,
                  cudaMemcpy2D(host, sizeof(double) * n, m->A64, sizeof(double) * np, sizeof(double) * n, n,
@@ -910,7 +785,7 @@ gbem_status gbem_matrix_status(gbem_matrix_t* m)
     gbem_ctx* ctx = m->ctx;
     DeviceGuard g(ctx->device);
     int flags[4] = {0, 0, 0, 0};
-    if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
+    if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
         !cuda_ok(ctx, cudaMemcpy(flags, m->dflags, sizeof(flags), cudaMemcpyDeviceToHost), "d2h"))
         return GBEM_ERR_CUDA;
     if (flags[0]) return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "Cholesky met a non-positive pivot");
@@ -918,33 +793,46 @@ gbem_status gbem_matrix_status(gbem_matrix_t* m)
     return GBEM_OK;
 }
 
+// The 14 class counts of the assembly (near parallel, near perpendicular,
+// far order n parallel at 2n and perpendicular at 2n + 1).
+static gbem_status read_class_counts(gbem_matrix_t* m, long long* cls)
+{
+    gbem_ctx* ctx = m->ctx;
+    unsigned long long c[16] = {};
+    if (!cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
+        !cuda_ok(ctx, cudaMemcpy(c, m->dcounts, sizeof(c), cudaMemcpyDeviceToHost), "d2h"))
+        return GBEM_ERR_CUDA;
+    for (int k = 0; k < 14; ++k) cls[k] = (long long)c[k];
+    return GBEM_OK;
+}
+
 gbem_status gbem_matrix_info(gbem_matrix_t* m, int* n, long long* counts)
 {
     if (!m) return GBEM_ERR_ARG;
-    gbem_ctx* ctx = m->ctx;
-    DeviceGuard g(ctx->device);
+    DeviceGuard g(m->ctx->device);
     if (n) *n = m->n;
     if (counts) {
-        unsigned long long c[8] = {};
-        if (!cuda_ok(ctx, join_groups(m, m->last), "join") || !cuda_ok(ctx, cudaStreamSynchronize(m->last), "sync") ||
-            !cuda_ok(ctx, cudaMemcpy(c, m->dcounts, sizeof(c), cudaMemcpyDeviceToHost), "d2h"))
-            return GBEM_ERR_CUDA;
-        for (int k = 0; k < 7; ++k) counts[k] = (long long)c[k];
+        long long cls[14];
+        gbem_status st = read_class_counts(m, cls);
+        if (st != GBEM_OK) return st;
+        counts[0] = cls[0] + cls[1];
+        for (int k = 1; k <= 6; ++k) counts[k] = cls[2 * k] + cls[2 * k + 1];
     }
     return GBEM_OK;
+}
+
+gbem_status gbem_matrix_class_counts(gbem_matrix_t* m, long long* counts)
+{
+    if (!m || !counts) return GBEM_ERR_ARG;
+    DeviceGuard g(m->ctx->device);
+    return read_class_counts(m, counts);
 }
 
 void gbem_matrix_destroy(gbem_matrix_t* m)
 {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
-    if (m->used) {
-        join_groups(m, m->last);
-        cudaStreamSynchronize(m->last);
-    } else {
-        for (auto& gr : m->groups) cudaEventSynchronize(gr.ev);
-    }
-    for (auto& gr : m->groups) cudaEventDestroy(gr.ev);
+    if (m->used) cudaStreamSynchronize(m->last);
     gbem_ctx* ctx = m->ctx;
     // the previous matrix's buffers that this one did not take go now; this
     // one's wait for the next matrix if they are known to be idle (a matrix

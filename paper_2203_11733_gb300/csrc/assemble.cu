@@ -348,14 +348,13 @@ __device__ typename FarVal<T>::type eval_far(const TileGeo& G, int cls, int s, i
 }
 
 // One 32 x 32 lower tile (linear index b over the lower triangle of tiles).
-// Order of the tiles: nt_band > 0 and tj0 < 0: by band over all nt_band tile
-// columns; nt_band > 0 and tj0 >= 0: column by column from tile column tj0
-// (a column group); nt_band = 0: row by row.  A32 may be null (mixed mode,
-// FP32 copy not written).
+// Order of the tiles: nt_band > 0: by band over all nt_band tile columns;
+// nt_band = 0: row by row.  counts (may be null) receives the pairs of every
+// class (kClasses words) and, in word 15, the skipped tiles.
 template <bool MIXED>
 __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_near, double* __restrict__ A64,
                                           float* __restrict__ A32, unsigned long long* __restrict__ counts,
-                                          long long b, int nt_band, int tj0 = -1)
+                                          long long b, int nt_band)
 {
     using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ TileGeo G;
@@ -372,21 +371,14 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
             // (FP64 closed forms), so the costly tiles start first and the
             // cheap far-field tiles fill the tail.  Band d starts at
             // d nt - d (d - 1) / 2.
-            // The same count, d nt - d (d - 1) / 2, is the number of tiles in
-            // the first d tile columns, so column order inverts it alike.
             auto off = [nt_band](long long dd) { return dd * nt_band - dd * (dd - 1) / 2; };
-            if (tj0 >= 0) b += off(tj0);
             const double h = 2.0 * nt_band + 1.0;
             int d = (int)((h - sqrt(fmax(h * h - 8.0 * (double)b, 0.0))) * 0.5);
             while (d > 0 && off(d) > b) --d;
             while (d + 1 < nt_band && off(d + 1) <= b) ++d;
-            if (tj0 >= 0) {   // column d, position b - off(d) down from its diagonal tile
-                tile_ij[1] = d;
-                tile_ij[0] = d + (int)(b - off(d));
-            } else {          // band d, position b - off(d) along it
-                tile_ij[1] = (int)(b - off(d));
-                tile_ij[0] = tile_ij[1] + d;
-            }
+            // band d, position b - off(d) along it
+            tile_ij[1] = (int)(b - off(d));
+            tile_ij[0] = tile_ij[1] + d;
         } else {
             // lower-triangular tile coordinates (TI >= TJ) from the linear tile index
             int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
@@ -401,7 +393,7 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
     const int TI = tile_ij[0], TJ = tile_ij[1];
     const int n = g.n;
     if (TJ < 0 || TJ > TI || (long long)TI * GBEM_TILE >= (long long)np) {   // not a lower tile: skip, count it
-        if (tid == 0 && counts) atomicAdd(&counts[7], 1ull);
+        if (tid == 0 && counts) atomicAdd(&counts[15], 1ull);
         return;
     }
 
@@ -534,11 +526,9 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
                                                 : eval_far<T>(G, cls, ii, GBEM_TILE + jj);
         }
     }
-    // class counts: near pairs, then far pairs by order
-    if (tid < kClasses && counts) {
-        int order = tid < 2 ? 0 : 1 + (tid - 2) / 2;
-        if (cls_cnt[tid]) atomicAdd(&counts[order], (unsigned long long)cls_cnt[tid]);
-    }
+    // class counts: near parallel, near perpendicular, then far pairs of
+    // order n parallel (2n) and perpendicular (2n + 1)
+    if (tid < kClasses && counts && cls_cnt[tid]) atomicAdd(&counts[tid], (unsigned long long)cls_cnt[tid]);
 }
 
 // Register caps of 64 (mixed: four CTAs an SM) and 128 (FP64: two): the
@@ -548,22 +538,9 @@ template <bool MIXED>
 __global__ void __launch_bounds__(kThreads, MIXED ? 4 : 2) assemble_tiles(DevPanels g, int np, float q_near,
                                                            double* __restrict__ A64,
                                                            float* __restrict__ A32,
-                                                           unsigned long long* __restrict__ counts, int tj0)
+                                                           unsigned long long* __restrict__ counts)
 {
-    tile_body<MIXED>(g, np, q_near, A64, A32, counts, blockIdx.x, (g.n + GBEM_TILE - 1) / GBEM_TILE, tj0);
-}
-
-// A32[r][c] += hi(A64[r][c]) for the lower entries (r >= c) of columns
-// [c0, c1): the FP32 copy of a column group assembled after the factorisation
-// began (its columns hold the trailing updates applied so far).
-__global__ void __launch_bounds__(256) add_hi(const double* __restrict__ A64, float* __restrict__ A32, int np,
-                                              int c0, int c1)
-{
-    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
-        const float2* src = reinterpret_cast<const float2*>(A64) + (size_t)c * np;
-        float* dst = A32 + (size_t)c * np;
-        for (int r = c + threadIdx.x; r < np; r += blockDim.x) dst[r] += src[r].x;
-    }
+    tile_body<MIXED>(g, np, q_near, A64, A32, counts, blockIdx.x, (g.n + GBEM_TILE - 1) / GBEM_TILE);
 }
 
 // Batched assembly: CTA index -> (structure, tile) through the prefix sums of
@@ -697,38 +674,24 @@ cudaError_t gl_upload()
 }
 
 cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
-                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s, int c0, int c1)
+                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s)
 {
     if (g.n <= 0) return cudaSuccess;
     const long long nt = (g.n + GBEM_TILE - 1) / GBEM_TILE;
-    // tile columns [tj0, tj1) of the element columns [c0, c1); all of them in band order
-    const long long tj0 = c0 <= 0 ? 0 : std::min<long long>(nt, c0 / GBEM_TILE);
-    const long long tj1 = c1 < 0 ? nt : std::min<long long>(nt, (c1 + GBEM_TILE - 1) / GBEM_TILE);
-    if (tj1 <= tj0) return cudaSuccess;
-    auto off = [nt](long long d) { return d * nt - d * (d - 1) / 2; };
-    const long long tiles = off(tj1) - off(tj0);
-    const int order = (tj0 == 0 && tj1 == nt) ? -1 : (int)tj0;
+    const long long tiles = nt * (nt + 1) / 2;
     cudaEvent_t ev = trace_begin(s);
     if (prec == GBEM_MIXED)
-        assemble_tiles<true><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, A32, counts, order);
+        assemble_tiles<true><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, A32, counts);
     else
-        assemble_tiles<false><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, nullptr, counts,
-                                                                   order);
+        assemble_tiles<false><<<(unsigned)tiles, kThreads, 0, s>>>(g, np, (float)q_near, A64, nullptr, counts);
     count_launch();
-    // algorithmic bytes: the lower entries written (FP64, plus FP32 in mixed
-    // mode when the copy is written) and the panels read
+    // algorithmic bytes: the lower entries written (FP64, or float pairs plus
+    // the FP32 copy in mixed mode) and the panels read.  The arithmetic per
+    // pair class is known only once the kernel has classified the pairs: it
+    // follows from the class counts (gbem_matrix_class_counts).
     const double entries = (double)tiles * GBEM_TILE * GBEM_TILE;
-    const double per = prec == GBEM_MIXED ? (A32 ? 12.0 : 8.0) : 8.0;
+    const double per = prec == GBEM_MIXED ? 12.0 : 8.0;
     trace_end(GBEM_KERNEL_ASSEMBLE, ev, s, entries * per + 45.0 * g.n, 0.0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_add_hi(const double* A64, float* A32, int np, int c0, int c1, cudaStream_t s)
-{
-    c1 = std::min(c1, np);
-    if (c1 <= c0) return cudaSuccess;
-    add_hi<<<(unsigned)std::min(c1 - c0, 4096), 256, 0, s>>>(A64, A32, np, c0, c1);
-    count_launch();
     return cudaGetLastError();
 }
 

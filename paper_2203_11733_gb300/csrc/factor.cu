@@ -281,7 +281,6 @@ __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T*
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-constexpr long long kFlagSpinLimit = 1LL << 24;   // ~1 s of polling
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
@@ -296,18 +295,20 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v)
 }
 
 // Waits until every flag in f0[0..n0) and f1[0..n1) has reached `token`
-// (bounded; n0 + n1 <= blockDim.x): thread q polls one flag, so the polls'
-// latencies overlap, and the CTA then proceeds together.  False (and status =
-// GBEM_ERR_TIMEOUT) if a wait gave up or another CTA's already had.
-__device__ bool wait_flags(const unsigned* f0, int n0, const unsigned* f1, int n1, unsigned token, int* status)
+// (n0 + n1 <= blockDim.x): thread q polls one flag, so the polls' latencies
+// overlap, and the CTA then proceeds together.  Bounded by limit_ns of
+// wall-clock time: false (and status = GBEM_ERR_TIMEOUT) if a wait gave up
+// or another CTA's already had.
+__device__ bool wait_flags(const unsigned* f0, int n0, const unsigned* f1, int n1, unsigned token, int* status,
+                           uint64_t limit_ns = bw::kDependencyNs)
 {
     const int q = threadIdx.x;
     int ok = 1;
     if (q < n0 + n1) {
         const unsigned* f = q < n0 ? f0 + q : f1 + (q - n0);
-        long long spins = 0;
+        bw::Deadline dl(limit_ns);
         while (ld_acquire(f) < token) {
-            if (++spins > kFlagSpinLimit || *(volatile int*)status != 0) {
+            if (dl.expired() || *(volatile int*)status != 0) {
                 atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -321,6 +322,13 @@ __device__ bool wait_flags(const unsigned* f0, int n0, const unsigned* f1, int n
 __device__ __forceinline__ bool wait_flags(const unsigned* f, int n, unsigned token, int* status)
 {
     return wait_flags(f, n, nullptr, 0, token, status);
+}
+
+// Self-test of the release-flag wait above: one CTA waits for flag[0] to
+// reach 1 with the given limit (gbem_selftest_wait).
+__global__ void __launch_bounds__(256) wait_selftest(const unsigned* flag, int* status, unsigned long long limit_ns)
+{
+    wait_flags(flag, 1, nullptr, 0, 1u, status, limit_ns);
 }
 
 constexpr int PT = NB + 4;   // padded row of a t-major 64 x 64 block in shared memory
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
                                                    const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
                                                    int ns_next, unsigned* __restrict__ pflag,
                                                    unsigned* __restrict__ tickets, unsigned* __restrict__ dflag,
-                                                   unsigned* __restrict__ halves, int zero_col)
+                                                   unsigned* __restrict__ halves)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
@@ -841,15 +849,14 @@ __global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int
     // tile (0, 0) leaves block (k+2, k+2) to the lookahead helper when the
     // strip is one block wide
     if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready,
-                       k == 0 ? zero_col : 1 << 30, b == 0 && sw == 1)) {
+                       b == 0 && sw == 1)) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
         return;
     }
 }
 
 template <typename T>
-cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s,
-                     int zero_col = 1 << 30, StepHook pre_step = nullptr, void* hook_user = nullptr)
+cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s)
 {
     const int nblk = np / NB;
     const size_t smem = 2 * NB * (NB + 1) * sizeof(T);
@@ -898,7 +905,6 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             const long long tiles = nt * (nt + 1) / 2;
             float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
             float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
-            if (pre_step && (e = pre_step(hook_user, k, s)) != cudaSuccess) return e;
             cudaLaunchConfig_t cfg = {};
             // 2 (m - 1) half panel rows, the diagonal CTA, its strip-row helpers, the tiles
             cfg.gridDim = dim3((unsigned)(2 * (m - 1) + 1 + strip_width(k + 1) + tiles));
@@ -910,7 +916,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             cudaEvent_t ev = trace_begin(s);
             if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
                                         (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets,
-                                        dflag, halves, zero_col)) !=
+                                        dflag, halves)) !=
                 cudaSuccess)
                 return e;
             count_launch();
@@ -999,13 +1005,17 @@ size_t cholesky_f32_split_bytes(int np)
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
-                                cudaStream_t s, int zero_col, StepHook pre_step, void* hook_user)
+                                cudaStream_t s)
 {
     if (nb != NB || np % tc::TM || !split) return cudaErrorInvalidValue;
-    // the columns the first step reads outside its tiles (the strip and the
-    // lookahead row, up to 3 blocks) must be assembled
-    if (zero_col < 3 * NB) return cudaErrorInvalidValue;
-    return cholesky<float>(L, np, Linv, info, split, s, zero_col, pre_step, hook_user);
+    return cholesky<float>(L, np, Linv, info, split, s);
+}
+
+cudaError_t launch_wait_selftest(const unsigned* flag, int* status, double limit_ms, cudaStream_t s)
+{
+    wait_selftest<<<1, 256, 0, s>>>(flag, status, (unsigned long long)(limit_ms * 1e6));
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long long* steps_dev,

@@ -59,16 +59,6 @@ struct gbem_ctx_s {
     std::vector<Pending> pending;
     double ms[GBEM_NPHASE] = {};
     long long calls[GBEM_NPHASE] = {};
-    // assembly overlapped with the factorisation (mixed mode): column groups
-    // (<= 1: off, the default: co-running assembly tiles slow the
-    // latency-bound elimination steps more than they save) and the share of
-    // the entries assembled before the factorisation starts; side: the
-    // low-priority stream of the later groups, fast: the high-priority stream
-    // of the factorisation
-    int overlap_groups = 1;
-    double overlap_first = 0.08;
-    cudaStream_t side = nullptr;
-    cudaStream_t fast = nullptr;
     // buffers of the last destroyed matrix (idle: its stream was synchronised
     // before they came here), offered to the next matrix's allocations of the
     // same size so that repeated extractions of one size make no allocator
@@ -180,17 +170,6 @@ struct gbem_matrix_s {
     cudaStream_t last = nullptr;   // the stream of the last call (null: the default stream)
     bool used = false;             // `last` holds a stream that work was enqueued on
     std::vector<std::pair<void*, size_t>> allocs;
-    // Mixed mode with the assembly overlapped with the factorisation: the
-    // column groups after the first, assembled on the context's side stream
-    // (float pairs only), each with the event that marks it done; their FP32
-    // copy is added in during the factorisation (zero_col: their first column).
-    struct Group {
-        int c0, c1;
-        cudaEvent_t ev;
-        bool added;
-    };
-    std::vector<Group> groups;
-    int zero_col = 1 << 30;
 };
 
 // ---- context helpers (api.cpp)
@@ -213,15 +192,11 @@ void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<do
 
 // ---- kernels (assemble.cu, factor.cu, solve.cu)
 cudaError_t gl_upload();
-// Entries of the element columns [c0, c1) (c1 < 0: to the end; the whole
-// matrix in band order when the range covers it), rounded out to whole
-// 32-column tiles.  Mixed mode writes the float pairs, and the FP32 copy
-// unless A32 is null.
+// Every lower entry, tiles in band order.  Mixed mode writes the float pairs
+// and the FP32 copy.  counts (8 words, zeroed) receives the pairs of each
+// class; the traced work counts the quadrature evaluations and corner terms.
 cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
-                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s,
-                            int c0 = 0, int c1 = -1);
-// A32 += hi(A64) over the lower entries of the columns [c0, c1).
-cudaError_t launch_add_hi(const double* A64, float* A32, int np, int c0, int c1, cudaStream_t s);
+                            double* A64, float* A32, unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
 cudaError_t launch_assemble_batched(const BatchView& v, long long tiles, gbem_precision prec, double q_near,
                                     cudaStream_t s);
@@ -239,13 +214,12 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 // The FP32 factor's tensor-core update needs `split` work space of
 // cholesky_f32_split_bytes(np) bytes (the hi/lo copies of one panel).
 size_t cholesky_f32_split_bytes(int np);
-// zero_col: the columns from zero_col on are not assembled in L yet; the
-// first step's trailing update starts them from zero, and pre_step(k), when
-// given, runs on the stream before the launch of step k (to add them in).
-using StepHook = cudaError_t (*)(void* user, int k, cudaStream_t s);
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
-                                cudaStream_t s, int zero_col = 1 << 30, StepHook pre_step = nullptr,
-                                void* hook_user = nullptr);
+                                cudaStream_t s);
+// One CTA waits, through the factorisation's bounded release-flag wait, for
+// flag[0] to reach 1 (limit limit_ms); status receives GBEM_ERR_TIMEOUT if
+// it gives up.
+cudaError_t launch_wait_selftest(const unsigned* flag, int* status, double limit_ms, cudaStream_t s);
 // W (np x nrhs, followed by np x nrhs of work space) := A^-1 W with the
 // factor L and its diagonal-block inverses; sync: np/64 flags, status: word
 // that receives GBEM_ERR_TIMEOUT if a bounded device wait gives up.

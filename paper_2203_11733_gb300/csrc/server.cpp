@@ -2,9 +2,12 @@
 // on one GPU.
 //
 // Requests are meshed on the host at submission (so their device footprint
-// is known), queued first-in first-out, and admitted by a pool of worker
-// threads whenever a worker is free and the request fits in the HBM budget
-// next to the requests already running.  Every worker owns a context and a
+// is known), queued in arrival order, and admitted by a pool of worker
+// threads whenever a worker is free: the first queued request, in arrival
+// order, that fits in the HBM budget next to the requests already running.
+// A smaller request may so pass a head request that waits for memory, but
+// the head is passed at most kMaxBypass times; after that nothing is
+// admitted before it, so a large request cannot starve.  Every worker owns a context and a
 // stream, so admitted requests run concurrently and their kernels overlap on
 // the device; a request that arrives while others run starts as soon as a
 // worker and memory free up.  Completed results (capacitance matrix, residual,
@@ -36,7 +39,11 @@ struct Request {
     double eps_r = 1.0;
     size_t bytes = 0;
     double t_submit = 0.0;
+    int bypassed = 0;   // admissions of later requests while this one led the queue
 };
+
+// Times the head of the queue may be passed by a later request that fits.
+constexpr int kMaxBypass = 8;
 
 struct Result {
     gbem_result_info info{};
@@ -104,26 +111,39 @@ struct gbem_server_s {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
                     if (stop) return;
-                    if (!queue.empty()) {
-                        if (queue.front().bytes > budget) {   // can never fit: reject
-                            Result r;
-                            r.info.id = queue.front().id;
-                            r.info.status = GBEM_ERR_OOM;
-                            r.info.submit_s = queue.front().t_submit;
-                            r.info.start_s = r.info.done_s = now();
-                            queue.pop_front();
-                            done.push_back(std::move(r));
-                            cv_done.notify_all();
+                    // requests larger than the whole budget can never run: reject them
+                    for (auto it = queue.begin(); it != queue.end();) {
+                        if (it->bytes <= budget) {
+                            ++it;
                             continue;
                         }
-                        if (reserved + queue.front().bytes <= budget) {
-                            req = std::move(queue.front());
-                            queue.pop_front();
-                            reserved += req.bytes;
-                            peak_reserved = std::max<long long>(peak_reserved, (long long)reserved);
-                            ++running;
+                        Result r;
+                        r.info.id = it->id;
+                        r.info.status = GBEM_ERR_OOM;
+                        r.info.submit_s = it->t_submit;
+                        r.info.start_s = r.info.done_s = now();
+                        it = queue.erase(it);
+                        done.push_back(std::move(r));
+                        cv_done.notify_all();
+                    }
+                    // the first request in arrival order that fits; the head
+                    // alone once it has been passed kMaxBypass times
+                    auto pick = queue.end();
+                    for (auto it = queue.begin(); it != queue.end(); ++it) {
+                        if (reserved + it->bytes <= budget) {
+                            pick = it;
                             break;
                         }
+                        if (it == queue.begin() && it->bypassed >= kMaxBypass) break;
+                    }
+                    if (pick != queue.end()) {
+                        if (pick != queue.begin()) ++queue.front().bypassed;
+                        req = std::move(*pick);
+                        queue.erase(pick);
+                        reserved += req.bytes;
+                        peak_reserved = std::max<long long>(peak_reserved, (long long)reserved);
+                        ++running;
+                        break;
                     }
                     cv_work.wait(lk);
                 }
@@ -194,9 +214,6 @@ gbem_status gbem_server_create(int device, size_t hbm_budget, int slots, gbem_pr
         gbem_ctx* ctx = nullptr;
         cudaStream_t s = nullptr;
         gbem_status st = gbem_create(&ctx, device, 0, srv_alloc, srv_free, nullptr);
-        // requests overlap one another; within a request the assembly is
-        // not overlapped with the factorisation
-        if (st == GBEM_OK) st = gbem_set_overlap(ctx, 1, 0.08);
         // a worker's next request has its own size and its memory is
         // reserved at admission: keep no buffers between requests
         if (st == GBEM_OK) ctx->keep_spare = false;

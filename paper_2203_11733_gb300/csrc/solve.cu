@@ -14,13 +14,13 @@
 // instead of spinning forever.
 #include <atomic>
 
+#include "bounded_wait.cuh"
 #include "gbem_internal.h"
 
 namespace {
 
 constexpr int NB = 64;
 constexpr int MAXR = 16;          // right-hand sides per pass
-constexpr long long kSpinLimit = 1LL << 24;   // ~1 s of polling at 32 ns
 
 std::atomic<unsigned> g_epoch{1};
 
@@ -36,15 +36,15 @@ __device__ __forceinline__ void store_release(unsigned* p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 waits until flag == epoch (bounded); the CTA then proceeds
-// together.  Returns false if the wait gave up (status set).
+// Thread 0 waits until flag == epoch (bounded in wall-clock time); the CTA
+// then proceeds together.  Returns false if the wait gave up (status set).
 __device__ bool wait_flag(const unsigned* flag, unsigned epoch, int* status, int* s_ok)
 {
     if (threadIdx.x == 0) {
-        long long spins = 0;
+        bw::Deadline dl(bw::kDependencyNs);
         int ok = 1;
         while (load_acquire(flag) != epoch) {
-            if (++spins > kSpinLimit || atomicAdd(status, 0) != 0) {
+            if (dl.expired() || atomicAdd(status, 0) != 0) {
                 atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -233,17 +233,15 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
-// Waits (bounded) for the tagged word and returns its value; gives up,
-// setting status, after kPollLimit polls (each an L2 round trip, about a
-// second in all) or once another wait has given up.
-constexpr long long kPollLimit = 1LL << 21;
+// Waits for the tagged word and returns its value; gives up, setting status,
+// after a second of wall-clock time or once another wait has given up.
 __device__ __forceinline__ float poll_tagged(const unsigned long long* p, unsigned epoch, int* status)
 {
-    long long spins = 0;
+    bw::Deadline dl(bw::kDependencyNs);
     for (;;) {
         const unsigned long long w = ld_relaxed_u64(p);
         if ((unsigned)(w >> 32) == epoch) return __uint_as_float((unsigned)w);
-        if (++spins > kPollLimit || *(volatile int*)status != 0) {
+        if (dl.expired() || *(volatile int*)status != 0) {
             atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
             return 0.0f;
         }
@@ -599,6 +597,7 @@ cudaError_t sweep_pair(const T* L, const T* Linv, int np, T* W, T* Y, int nr, un
             cudaSuccess)
         return e;
     unsigned e1 = g_epoch.fetch_add(2);
+    if (e1 + 1 == 0) e1 = g_epoch.fetch_add(2);   // 0 marks a cleared flag
     unsigned e2 = e1 + 1;
     // one sweep reads the lower triangle of L and the diagonal-block
     // inverses once and the right-hand sides twice

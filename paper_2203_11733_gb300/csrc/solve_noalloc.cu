@@ -15,6 +15,7 @@
 // first written by that call (padded right-hand sides, solution, residual,
 // flags).  Calls that overlap on the GPU (different streams, or different
 // host threads) race on the array and must be serialised by the caller.
+#include <algorithm>
 #include <mutex>
 
 #include "gbem_internal.h"
@@ -88,8 +89,9 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
     void* W = base + 3 * vec;                       // 2 np nrhs entries of the solve type
     int* flags = reinterpret_cast<int*>(base + 5 * vec);
     double* norm = reinterpret_cast<double*>(base + 5 * vec + 64);
-    // block flags of the persistent solves: compared against a fresh epoch on
-    // every sweep, so their old contents never need clearing
+    // block flags of the FP64 persistent solves: compared against a fresh
+    // epoch on every sweep; cleared below so that no leftover word of an
+    // earlier call (right-hand sides, solutions) can equal a later epoch
     unsigned* sync = reinterpret_cast<unsigned*>(base + 5 * vec + 256);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int n = m->n, npi = m->np;
@@ -98,6 +100,7 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
         return ctx_fail(ctx, GBEM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
     };
     if ((e = cudaMemsetAsync(flags, 0, 64, s)) != cudaSuccess) return fail(e, "clear flags");
+    if ((e = cudaMemsetAsync(sync, 0, nblk * sizeof(unsigned), s)) != cudaSuccess) return fail(e, "clear sync");
     if ((e = launch_pack_rhs(B_dev, ldb, n, npi, nrhs, Bp, s)) != cudaSuccess) return fail(e, "pack");
     int iters = 0;
     if (m->prec == GBEM_FP64) {
@@ -114,7 +117,7 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
         const int* done = flags + 1;
         if ((e = launch_ir_begin(Bp, npi, nrhs, X, R, norm, flags, s)) != cudaSuccess) return fail(e, "ir begin");
         int host_flags[3] = {0, 0, 0};
-        const int maxit = ctx->tune.ir_max_iter > 0 ? ctx->tune.ir_max_iter : 10;
+        const int maxit = std::max(1, ctx->tune.ir_max_iter);   // as gbem_solve
         for (int it = 0; it < maxit && !host_flags[1]; ++it) {
             if ((e = launch_to_f32(R, npi, nrhs, Wf, done, s)) != cudaSuccess ||
                 (e = launch_trsv_f32_guarded(m->A32, static_cast<const float*>(m->Linv), npi, m->nb, Wf, nrhs,
@@ -129,19 +132,18 @@ extern "C" gbem_status gbem_solve_noalloc(gbem_matrix_t* m, const double* B_dev,
                 (e = cudaStreamSynchronize(s)) != cudaSuccess)
                 return fail(e, "flags");
         }
-        iters = host_flags[2];
         if ((e = launch_unpack(X, npi, n, nrhs, X_dev, ldx, s)) != cudaSuccess) return fail(e, "unpack");
-        if (!host_flags[1]) {
-            if (ir_iters) *ir_iters = iters;
-            return ctx_fail(ctx, GBEM_ERR_NOCONV, "gbem_solve_noalloc: refinement missed its tolerance");
-        }
     }
-    // the status words live in the shared scratch, so read them before returning
+    // every path ends here: the status words live in the shared scratch, so
+    // read them (and let X_dev be written) before returning
     int fl[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(fl, flags, sizeof(fl), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(e, "sync");
+    if (m->prec != GBEM_FP64) iters = fl[2];
     if (ir_iters) *ir_iters = iters;
     if (fl[3]) return ctx_fail(ctx, GBEM_ERR_TIMEOUT, "gbem_solve_noalloc: a bounded device wait gave up");
+    if (m->prec != GBEM_FP64 && !fl[1])
+        return ctx_fail(ctx, GBEM_ERR_NOCONV, "gbem_solve_noalloc: refinement missed its tolerance");
     return GBEM_OK;
 }

@@ -31,9 +31,16 @@
 //   4. after the bounded wait every warp reads 32 accumulator lanes x 64
 //      columns with tcgen05.ld and stores C minus the product;
 //   5. warp 0 frees the TMEM columns.
+// Only the wait for the panel rows (other CTAs' results) can give up in
+// practice.  The waits on the CTA's own copies and MMAs carry the long
+// own-operation limit, and a CTA that gives up first waits for the last
+// phase of each of its mbarriers, so that no copy or MMA it issued is still
+// in flight when its shared memory and tensor memory are released.
 #pragma once
 
 #include <cstdint>
+
+#include "bounded_wait.cuh"
 
 namespace tc {
 
@@ -43,7 +50,6 @@ constexpr int KH = 32;        // K per pipeline stage (two stages per panel)
 constexpr int OPER_BYTES = TM * TK * 4;                 // one operand part (hi or lo) of a 128-row block
 constexpr int HALF_BYTES = TM * KH * 4;                 // ... and of one stage
 constexpr int SMEM_BYTES = 4 * HALF_BYTES + 256;        // A_hi, A_lo, B_hi, B_lo of a stage, barriers + TMEM slot
-constexpr long long kWaitLimit = 1LL << 20;             // bounded mbarrier polling
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -148,12 +154,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait on the given phase parity of an mbarrier.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity = 0)
+// Wait, bounded by limit_ns of wall-clock time, for the completion of the
+// phase with the given parity (the most recent phase of that parity).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns = bw::kOwnAsyncNs)
 {
-    long long spins = 0;
+    bw::Deadline dl(limit_ns);
     while (!mbar_try_wait(bar, parity))
-        if (++spins > kWaitLimit) return false;
+        if (dl.expired()) return false;
     return true;
 }
 
@@ -165,14 +172,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity 
 // allocated, the CTA has given up its TMEM allocation permit and the tile of C
 // is loaded into registers: C is not written by this launch before the tile,
 // and a CTA that holds the permit keeps the SM from taking a second CTA of the
-// kernel.  Columns from zero_col on are taken as zero instead of read (C
-// not assembled yet).  With skip00 the top-left 64 x 64 quadrant of the tile
-// is neither read nor written (another CTA updates it).  Returns false if a
-// wait gave up.
+// kernel.  With skip00 the top-left 64 x 64 quadrant of the tile is neither
+// read nor written (another CTA updates it).  Returns false if a wait gave
+// up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
-                          unsigned char* smem, Ready ready, int zero_col, bool skip00)
+                          unsigned char* smem, Ready ready, bool skip00)
 {
     unsigned char* a_hi = smem;
     unsigned char* a_lo = smem + HALF_BYTES;
@@ -218,10 +224,6 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     float cpre[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
-    if (rJ + half * 64 >= zero_col) {   // not assembled yet: the loaded values are discarded
-#pragma unroll
-        for (int i = 0; i < 64; ++i) cpre[i] = 0.f;
-    }
     int ok = ready() ? 1 : 0;
     int loads = ok, commits = 0;
     if (ok && tid == 32) {
@@ -277,11 +279,12 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
             for (int i = 0; i < 16; ++i) crow[(size_t)(cc + i) * ld] = cpre[cc + i] - v[i];
         }
     }
-    // after a failed wait, give the copies and MMAs still in flight a bounded
-    // chance to finish before the shared memory and TMEM are released
+    // after a failed wait, let the copies and MMAs this CTA issued finish
+    // before its shared memory and TMEM are released: phases complete in
+    // order, so the last phase of each barrier covers all earlier ones
     if (!ok && tid == 0) {
-        for (int h = 0; h < loads; ++h) mbar_wait_bounded(bar_ld, h);
-        for (int h = 0; h < commits; ++h) mbar_wait_bounded(bar_mma, h);
+        if (loads > 0) mbar_wait_bounded(bar_ld, (uint32_t)(loads - 1) & 1u);
+        if (commits > 0) mbar_wait_bounded(bar_mma, (uint32_t)(commits - 1) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -82,7 +82,6 @@ _SIGS = {
     "gbem_destroy": (None, [_P]),
     "gbem_last_error": (ctypes.c_char_p, [_P]),
     "gbem_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_Tuning)]),
-    "gbem_set_overlap": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "gbem_bytes_in_use": (ctypes.c_size_t, [_P]),
     "gbem_mesh": (ctypes.c_int, [_P, ctypes.POINTER(_Box), ctypes.c_int, ctypes.POINTER(_MeshParams),
                                  ctypes.POINTER(_P)]),
@@ -98,6 +97,8 @@ _SIGS = {
     "gbem_matrix_download": (ctypes.c_int, [_P, _P]),
     "gbem_matrix_status": (ctypes.c_int, [_P]),
     "gbem_matrix_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
+    "gbem_matrix_class_counts": (ctypes.c_int, [_P, _P]),
+    "gbem_selftest_wait": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P]),
     "gbem_matrix_destroy": (None, [_P]),
     "gbem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbem_get_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -205,17 +206,25 @@ class Context:
     only).  ``torch_alloc`` routes device memory through PyTorch's caching
     allocator; otherwise the library uses cudaMalloc."""
 
-    def __init__(self, device: int = 0, hbm_budget: int = 0, torch_alloc: bool = True):
+    def __init__(self, device: int = 0, hbm_budget: int = 0, torch_alloc: bool = True, refuse=None):
+        """``refuse`` (tests of the allocation-failure path): a callable
+        (call index, bytes) -> bool; when it returns True the allocator
+        callback hands the library a NULL pointer instead of memory."""
         self.lib = load()
         self.device = device
         self._cb = None
         self.h = None
         self._children = weakref.WeakSet()
+        self.alloc_calls = 0
         alloc, free = ALLOC_FN(), FREE_FN()
         if device >= 0 and torch_alloc:
             import torch
 
             def _alloc(nbytes, stream, user):
+                k = self.alloc_calls
+                self.alloc_calls += 1
+                if refuse is not None and refuse(k, int(nbytes)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
                 except Exception:   # refusal is reported through a NULL pointer
@@ -242,11 +251,12 @@ class Context:
         t = _Tuning(q_near_fp64, q_near_mixed, ir_tol, ir_max_iter, nb)
         self.check(self.lib.gbem_set_tuning(self.h, ctypes.byref(t)))
 
-    def set_overlap(self, groups: int = 1, first_fraction: float = 0.08):
-        """Mixed mode: assemble all but the first ~first_fraction of the entries
-        in groups - 1 column groups while the factorisation runs (groups <= 1,
-        the default: off)."""
-        self.check(self.lib.gbem_set_overlap(self.h, int(groups), float(first_fraction)))
+
+    def selftest_wait(self, set_flag: bool, limit_ms: float = 50.0, stream=None) -> int:
+        """gbem_selftest_wait: the status of one bounded device wait for a flag
+        that is set (GBEM_OK) or withheld (GBEM_ERR_TIMEOUT)."""
+        return int(self.lib.gbem_selftest_wait(self.h, 1 if set_flag else 0, float(limit_ms),
+                                               _stream_handle(stream)))
 
     def bytes_in_use(self) -> int:
         return int(self.lib.gbem_bytes_in_use(self.h))
@@ -337,6 +347,13 @@ class Matrix:
         counts = np.zeros(7, np.int64)
         self.ctx.check(self.ctx.lib.gbem_matrix_info(self.h, ctypes.byref(n), _ptr(counts)))
         return n.value, counts
+
+    def class_counts(self):
+        """Pairs per evaluation class: [0] near parallel, [1] near
+        perpendicular, [2n] / [2n+1] far parallel / perpendicular of order n."""
+        counts = np.zeros(14, np.int64)
+        self.ctx.check(self.ctx.lib.gbem_matrix_class_counts(self.h, _ptr(counts)))
+        return counts
 
     def close(self):
         if getattr(self, "h", None):

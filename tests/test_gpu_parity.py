@@ -230,6 +230,43 @@ def test_kernel_trace_covers_the_mixed_path(ctx):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("prec", [0, 1])
+def test_three_layer_bus_sampled_entries_and_capacitance(ctx, prec):
+    """The largest workload, the three-layer 5x5x5 crossing bus (N = 23172,
+    15 conductors): 3000 random entries and two whole rows against the oracle
+    one by one, and the 15 x 15 capacitance matrix against the stored oracle
+    result of the full FP64 assembly and Cholesky solve."""
+    from paper_2203_11733_gb300 import gbem
+    gold = json.load(open(os.path.join(HERE, "golden", "bus_3layer_5x5x5_capacitance.json")))
+    boxes, params = W.bus_3layer_5x5x5()
+    assert gold["params"] == params
+    a, g, c = O.mesh_boxes(boxes, **params)
+    mesh = ctx.mesh(boxes, params)
+    n = mesh.n
+    assert n == gold["n_panels"] == 23172
+    p = _perm(mesh, a, g, c)
+    mat = gbem.gbem_assemble(mesh, prec)
+    A = mat.download()
+    rng = np.random.default_rng(11)
+    I = rng.integers(0, n, 3000)
+    J = rng.integers(0, n, 3000)
+    rows = rng.integers(0, n, 2)
+    I = np.concatenate([I, np.repeat(rows, n)])
+    J = np.concatenate([J, np.tile(np.arange(n), len(rows))])
+    vals = A[I, J]
+    del A
+    ref = O.entries(a, g, p[I], p[J])
+    err = _rel(vals, ref)
+    assert err.max() <= ENTRY_TOL[prec], err.max()
+    C, resid = gbem.gbem_capacitance(mesh, mat, gold["eps_r"])
+    mat.close()
+    mesh.close()
+    C_ref = np.array(gold["C"])
+    assert C.shape == (15, 15)
+    assert _cap_err(C, C_ref) <= CAP_TOL[prec], _cap_err(C, C_ref)
+
+
+@pytest.mark.slow
 def test_mixed_refinement_converges_at_large_order(ctx):
     """The compensated FP32 residual must stay accurate enough for the FP64
     refinement to reach its 1e-12 tolerance at large N (the three-layer bus,

@@ -1,12 +1,15 @@
 """Extraction server (continuous batching): results in the mix equal the same
 requests run alone; admission respects the HBM budget; requests overlap."""
+import json
+import os
+
 import numpy as np
 import pytest
 
-from oracle import oracle as O
 from paper_2203_11733_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(__file__)
 
 
 def _err(C, R):
@@ -44,12 +47,14 @@ def test_mix_equals_alone_and_overlaps():
         assert info["status"] == 0 and info["residual"] < 1e-10
         C_alone, _ = gbem.extract(ctx, boxes, params, W.EPS_R_SIO2, precision=gbem.GBEM_MIXED)
         assert _err(C, C_alone) <= 1e-12
-    # two small requests against the FP64 oracle
-    for k in range(2):
-        _, boxes, params = reqs[k]
-        a, g, c = O.mesh_boxes(boxes, **params)
-        if len(a) <= 900:
-            assert _err(got[k][1], O.capacitance(a, g, c, W.EPS_R_SIO2)) <= 1e-6
+    # requests 0 and 1 (2304 and 1936 panels) against the stored FP64 oracle
+    # results (tests/golden/make_golden.py serving_seed31)
+    gold = json.load(open(os.path.join(HERE, "golden", "serving_seed31_capacitance.json")))["requests"]
+    assert [g["request"] for g in gold] == [0, 1]
+    for g in gold:
+        k = g["request"]
+        assert got[k][0]["n_panels"] == g["n_panels"]
+        assert _err(got[k][1], np.array(g["C"])) <= 1e-6
     # work of different requests overlapped in time
     spans = sorted((got[k][0]["start_s"], got[k][0]["done_s"]) for k in got)
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
@@ -76,3 +81,34 @@ def test_budget_admission_and_rejection():
     if 2 * need_small > 200 << 20:            # one at a time: no overlap possible
         s0, s1 = got[0][0], got[1][0]
         assert s1["start_s"] >= s0["done_s"] or s0["start_s"] >= s1["done_s"]
+
+
+def test_smaller_request_passes_a_blocked_head():
+    """A request at the head of the queue that fits the budget but not the
+    memory left next to the running requests does not hold back a smaller
+    request behind it that fits: the small one is admitted at once, the
+    large one when the memory frees up."""
+    from paper_2203_11733_gb300 import gbem
+    rng = W.SplitMix64(21)
+    small = W.bus_structure(rng, 1500)
+    big = W.bus_structure(rng, 6000)
+    probe = gbem.Server(0, hbm_budget=1 << 40, slots=1)
+    need_small = probe.submit(0, small[0], small[1], 1.0)
+    need_big = probe.submit(1, big[0], big[1], 1.0)
+    _drain(probe, 2)
+    probe.close()
+    budget = need_big + need_small // 2          # big alone fits, big + small does not
+    assert 2 * need_small <= budget < need_big + need_small
+    srv = gbem.Server(0, hbm_budget=budget, slots=3)
+    srv.submit(0, small[0], small[1], 1.0)       # admitted at once
+    srv.submit(1, big[0], big[1], 1.0)           # must wait for request 0
+    srv.submit(2, small[0], small[1], 1.0)       # fits next to request 0
+    got = _drain(srv, 3)
+    stats = srv.stats()
+    srv.close()
+    assert all(got[k][0]["status"] == 0 for k in range(3))
+    assert stats["peak_reserved"] <= budget
+    i0, i1, i2 = (got[k][0] for k in range(3))
+    assert i2["start_s"] < i1["start_s"]         # the small request passed the blocked head
+    assert i1["start_s"] >= i0["done_s"] - 1e-6 and i1["start_s"] >= i2["done_s"] - 1e-6
+    assert np.array_equal(got[0][1], got[2][1])

@@ -85,5 +85,5 @@ def test_headline_steps_default(monkeypatch):
     import bench
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     args = bench.parse()
-    assert (args.steps, args.warmup, args.gpus, args.impl) == (30, 3, 1, "ours")
+    assert (args.steps, args.warmup, args.gpus, args.impl, args.workload) == (20, 3, 1, "ours", "headline")
     json.dumps(vars(args))
