@@ -544,18 +544,26 @@ __device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* 
 }
 
 constexpr size_t kStripSmem = 4 * NB * PT * sizeof(float);
+// Panels of kPanel 64-column blocks; the split of a panel holds
+// kPanelStages K stages of 16 columns.
+constexpr int kPanel = 4;
+constexpr int kPanelStages = kPanel * tc::CHUNK_STAGES;
+// Bytes between two K stages of one part of a panel split: one stage of every
+// 128-row block of the matrix, and one more.
+inline size_t split_stage_stride(int np) { return (size_t)(np / tc::TM + 1) * tc::STAGE_BYTES; }
 constexpr size_t kPanelRowSmem = 4 * NB * PT * sizeof(float);
 // every role of factor_step within one dynamic allocation: two CTAs per SM
 constexpr size_t kFactorSmem = kPanelRowSmem > (size_t)tc::SMEM_BYTES ? kPanelRowSmem : (size_t)tc::SMEM_BYTES;
 
-// The first diagonal block of the FP32 factorisation, the strip rows of step
-// 0 and the lookahead panel work of row block 1 (diag_tail).
-__global__ void __launch_bounds__(256) potrf_first(float* __restrict__ L, int ld, float* __restrict__ Linv,
+// The first diagonal block b0 of a panel (every earlier update of it done by
+// the launches before), the strip rows of step b0 and the lookahead panel
+// work of row block b0 + 1 (diag_tail).
+__global__ void __launch_bounds__(256) panel_start(float* __restrict__ L, int ld, int b0, float* __restrict__ Linv,
                                                    int* __restrict__ info, float* __restrict__ lsT, int ns,
                                                    unsigned* __restrict__ pflag)
 {
-    potrf_body<float>(L, ld, 0, Linv, info);
-    if (ns > 0) diag_tail(L, ld, 0, Linv, lsT, ns, nullptr, pflag + 1, 1u, info + 3);
+    potrf_body<float>(L, ld, b0 * NB, Linv, info);
+    if (ns > 0) diag_tail(L, ld, b0 * NB, Linv, lsT, ns, nullptr, pflag + b0 + 1, (unsigned)b0 + 1, info + 3);
 }
 
 template <typename T>
@@ -660,16 +668,18 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
 // (one CTA; the two halves of a row block run in two CTAs):
 //   1. L_ik = A_ik Linv_kk^T for those rows, written in place (Linv_kk is
 //      lower triangular, so the sum over t stops at the output column);
-//   2. row blocks at or below r0 write the TF32 hi/lo split of those rows in
-//      the tensor-core operand layout;
+//   2. row blocks at or below srow0 write the TF32 hi/lo split of those rows
+//      in the tensor-core operand layout, as the 4 stages st_base .. of the
+//      panel's split;
 //   3. A_ic -= L_ik L_ck^T on those rows for the sw strip blocks
 //      c = k+1 .. k+sw, c <= i, with L_ck (lsT, t-major) computed by the
 //      helpers of the previous step.
 // A thread owns 2 rows x 4 columns.  The strip targets are read first, so
 // their latency overlaps the product.
-__device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int r0,
-                           unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
-                           const float* __restrict__ lsT, int i, int h, unsigned char* smem)
+__device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int srow0,
+                           int st_base, size_t stage_stride, unsigned char* __restrict__ hi,
+                           unsigned char* __restrict__ lo, const float* __restrict__ lsT, int i, int h,
+                           unsigned char* smem)
 {
     constexpr int HR = NB / 2;   // rows of a half
     // Blocks are stored t-major (rows padded to 68 floats) so that a
@@ -681,7 +691,6 @@ __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __
     const int tr = (tid & 15) * 2, tc = (tid >> 4) * 4;
     const int k0 = k * NB, rI = i * NB, rh = rI + HR * h;
     const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
-    const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
     float2 tgt[2][4];
 #pragma unroll
     for (int sidx = 0; sidx < 2; ++sidx)
@@ -718,11 +727,11 @@ __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __
         *reinterpret_cast<float2*>(&aT[tc + v][tr]) = q;
         *reinterpret_cast<float2*>(L + (size_t)(rh + tr) + (size_t)(k0 + tc + v) * ld) = q;
     }
-    if (rI >= r0) {
+    if (rI >= srow0) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int rr = rh - r0 + tr + u;
-            const size_t off = tc::split_offset(rr, tc, stage_stride);
+            const int rr = rh - srow0 + tr + u;
+            const size_t off = tc::split_offset(rr, tc, stage_stride) + (size_t)st_base * stage_stride;
             float hv[4], lv[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -758,101 +767,221 @@ __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __
     }
 }
 
+// Arguments of one elimination step of the FP32 factorisation (factor_step).
+// The factorisation runs by panels of up to four 64-column blocks
+// [b0, e): the elimination steps k = b0 .. e-1 of a panel update only the
+// panel's own columns (strip updates, the lookahead, and at its first step
+// one column of 128-tiles), and write the TF32 split of every panel row as
+// the panel's 16 K stages.  The update of the rest of the trailing matrix by
+// the whole panel (K = 256) is done by tensor-core tiles: the next panel's
+// columns ("front" tiles, in the panel's last step, after the flags of their
+// rows) and everything beyond ("rest" tiles, spread over the next panel's
+// steps but its last, which need no flags: the panel's split is complete
+// before they start, and they touch no column the next panel's steps read or
+// write).  The split is double-buffered by panel parity.
+struct StepArgs {
+    float* L;
+    int ld, k, nblk;
+    float* Linv;
+    int* info;
+    int sw;        // strip width of step k: 0, 1 or 2 blocks, within the panel
+    int p0;        // first panel row block (k+2; k+1 when row block k+1 had no lookahead)
+    int has_diag;  // factor diagonal block k+1 (in the panel) in this launch
+    int ns_next;   // strip-row helpers for step k+1 (the first also does the lookahead)
+    // the panel's split: rows from srow0, this step's chunk at stage st_base
+    unsigned char* hi;
+    unsigned char* lo;
+    int srow0, st_base;
+    size_t stage_stride;
+    int r0, icols;                // inner tiles: rows [r0, np), icols 128-columns from r0
+    int f0, fcols;                // front tiles: rows [f0, np), fcols 128-columns from f0 (16 stages)
+    int next_start;               // start the next panel (its first block f0 / 64) after front tile (0, 0)
+    int ns_start;                 // strip rows of the next panel's first step
+    const unsigned char* hi_p;    // rest tiles: the previous panel's split (rows from srow0_p),
+    const unsigned char* lo_p;    // the lower 128-tiles [rb0, rb1) of [c0r, np)^2
+    int srow0_p, c0r;
+    long long rb0, rb1;
+    const float* lsT_in;
+    float* lsT_out;
+    unsigned* pflag;
+    unsigned* tickets;
+    unsigned* dflag;
+    unsigned* halves;
+};
+
+// Tile (I, J), I >= J, of a column band of `cols` 128-columns over nrow
+// 128-rows: index t over J = 0 .. cols-1, I = J .. nrow-1.  False if t is
+// past the band.
+__device__ __forceinline__ bool band_tile(long long t, int nrow, int cols, int& I, int& J)
+{
+    for (int j = 0; j < cols; ++j) {
+        const long long nj = nrow - j;
+        if (t < nj) {
+            I = j + (int)t;
+            J = j;
+            return true;
+        }
+        t -= nj;
+    }
+    return false;
+}
+
+__host__ __device__ __forceinline__ long long band_tiles(int nrow, int cols)
+{
+    long long n = 0;
+    for (int j = 0; j < cols; ++j) n += nrow - j;
+    return n;
+}
+
 // Elimination step k of the FP32 factorisation in one launch.  Row block
-// k+1 was already done by the previous launch (lookahead).  Every CTA draws a
-// ticket in the order the CTAs start (an atomic counter per step), and the
-// ticket gives its role (m = row blocks below diagonal block k, ns = strip
-// width of step k+1):
-//   tickets 0 .. 2m-3  panel work of half ticket % 2 of row block
-//                      i = k + 2 + ticket / 2 (panel_half); the second half
-//                      to finish sets the release flag pflag[i] = k + 1;
-//   ticket  2m-2       factor and invert diagonal block k+1, then dflag[k];
-//   next ns tickets    helpers (tail_helper): the strip rows of step k+1 and,
-//                      for the first, the lookahead panel work of row block
-//                      k+2 (pflag[k+2] = k + 2);
-//   the rest           one 128 x 128 lower tile of [r0, np)^2 each, after the
-//                      flags of its four row blocks: 3xTF32 tensor-core update
-//                      with the split panel (tc_syrk.cuh).
+// k+1 was already done by the previous launch (lookahead) when p0 = k+2.
+// Every CTA draws a ticket in the order the CTAs start (an atomic counter
+// per step), and the ticket gives its role:
+//   2 (nblk - p0)   panel work of half ticket % 2 of row block
+//                   i = p0 + ticket / 2 (panel_half); the second half to
+//                   finish sets the release flag pflag[i] = k + 1;
+//   has_diag        factor and invert diagonal block k+1, then dflag[k];
+//   ns_next         helpers (tail_helper): the strip rows of step k+1 and,
+//                   for the first, the lookahead panel work of row block
+//                   k+2 (pflag[k+2] = k + 2);
+//   inner tiles     the panel's 128-tiles right of the strip, after the
+//                   flags of their four row blocks (this step's chunk);
+//   front tiles     the next panel's columns with the whole panel (K = 256),
+//                   after the flags of their row blocks; with next_start,
+//                   right after front tile (0, 0) (which holds the next
+//                   panel's first diagonal block, its strip and lookahead
+//                   blocks) comes the next panel's start: it waits for that
+//                   tile (dflag[k], unused by a step without a diagonal
+//                   block), factors block f0 / 64 and does the strip rows and
+//                   lookahead of the next step (panel_start's work);
+//   rest tiles      the previous panel's update of the matrix beyond this
+//                   panel (K = 256), no waits.
 // Every wait is on a smaller ticket, a CTA that has already started: panel
 // CTAs wait for nothing, the diagonal CTA for the previous launch, helpers
-// for their panel row and the diagonal CTA, tiles for panel rows.  So the
-// launch cannot deadlock however many CTAs are resident.  Waits are bounded;
-// one that gives up sets status GBEM_ERR_TIMEOUT and its CTA skips its work.
-__global__ void __launch_bounds__(256, 2) factor_step(float* __restrict__ L, int ld, int k, float* __restrict__ Linv,
-                                                   int* __restrict__ info, int nblk, int sw, int r0,
-                                                   unsigned char* __restrict__ hi, unsigned char* __restrict__ lo,
-                                                   const float* __restrict__ lsT_in, float* __restrict__ lsT_out,
-                                                   int ns_next, unsigned* __restrict__ pflag,
-                                                   unsigned* __restrict__ tickets, unsigned* __restrict__ dflag,
-                                                   unsigned* __restrict__ halves)
+// for their panel row and the diagonal CTA, tiles for panel rows, the next
+// panel's start for front tile (0, 0).  So the launch cannot deadlock however
+// many CTAs are resident.  Waits are bounded; one that gives up sets status
+// GBEM_ERR_TIMEOUT and its CTA skips its work.
+__global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
     pdl_wait();
     pdl_trigger();
-    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(tickets + k, 1u);
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(a.tickets + a.k, 1u);
     __syncthreads();
     const int t_raw = s_ticket;
-    const int npanel = nblk - k - 2;   // panel row blocks, two CTAs each
-    // after the 2 npanel half-panel tickets, the roles count as if one CTA
-    // per row block: t = npanel is the diagonal CTA, and so on
-    const int t = t_raw < 2 * npanel ? t_raw / 2 : t_raw - npanel;
+    const int k = a.k, ld = a.ld;
+    float* __restrict__ L = a.L;
+    const int npanel = a.nblk - a.p0;   // panel row blocks, two CTAs each
     const unsigned token = (unsigned)k + 1;
-    int* status = info + 3;
+    int* status = a.info + 3;
+    long long t = (long long)t_raw - 2 * npanel;   // index among the other roles
     // roles without tensor-core work give up the CTA's TMEM allocation permit
     // at once: while a CTA holds it, no second CTA of the kernel is placed on
     // its SM
-    if (t <= npanel + ns_next && threadIdx.x < 32)
+    const int nin = (a.ld - a.r0) / tc::TM;
+    const long long n_inner = band_tiles(nin, a.icols);
+    const long long t_start = a.has_diag + a.ns_next + n_inner + 1;   // the next panel's start, when present
+    if ((t < a.has_diag + a.ns_next || (a.next_start && t == t_start)) && threadIdx.x < 32)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    if (t < npanel) {
-        const int i = k + 2 + t;
-        panel_half(L, ld, k, Linv, sw, r0, hi, lo, lsT_in, i, t_raw & 1, tc_smem);
+    if (t < 0) {
+        const int i = a.p0 + t_raw / 2;
+        panel_half(L, ld, k, a.Linv, a.sw, a.srow0, a.st_base, a.stage_stride, a.hi, a.lo, a.lsT_in, i, t_raw & 1,
+                   tc_smem);
         __syncthreads();   // the half is stored
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
             __threadfence();
             // halves[i] only grows (two per step): the second half to finish
             // sees an odd count and releases the row block
-            if (atomicAdd(halves + i, 1u) & 1u) {
+            if (atomicAdd(a.halves + i, 1u) & 1u) {
                 __threadfence();
-                st_release(pflag + i, token);
+                st_release(a.pflag + i, token);
             }
         }
         return;
     }
-    if (t == npanel) {
-        if (!wait_flags(pflag + k + 1, 1, token, status)) return;
-        potrf_body<float>(L, ld, (k + 1) * NB, Linv, info);
-        __syncthreads();   // the inverse is stored
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release(dflag + k, token);
+    if (a.has_diag) {
+        if (t == 0) {
+            if (!wait_flags(a.pflag + k + 1, 1, token, status)) return;
+            potrf_body<float>(L, ld, (k + 1) * NB, a.Linv, a.info);
+            __syncthreads();   // the inverse is stored
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release(a.dflag + k, token);
+            }
+            return;
         }
+        --t;
+    }
+    // with a strip one block wide and a lookahead helper, block (k+2, k+2)
+    // lies in inner tile (0, 0) and the helper applies this step's update to it
+    const bool la = a.sw == 1 && a.ns_next >= 1;
+    if (t < a.ns_next) {
+        const int sidx = (int)t;
+        const float* lk = la ? L + (size_t)((k + 2) * NB) + (size_t)(k * NB) * ld : nullptr;
+        tail_helper(L, ld, (k + 1) * NB, a.Linv, a.lsT_out + (size_t)sidx * NB * NB, sidx, a.pflag + k + 2 + sidx,
+                    lk, a.dflag + k, token, a.pflag + k + 2, status);
         return;
     }
-    if (t <= npanel + ns_next) {
-        const int sidx = t - npanel - 1;
-        // with a strip one block wide, block (k+2, k+2) lies in tile (0, 0)
-        const float* lk = sw == 1 ? L + (size_t)((k + 2) * NB) + (size_t)(k * NB) * ld : nullptr;
-        tail_helper(L, ld, (k + 1) * NB, Linv, lsT_out + (size_t)sidx * NB * NB, sidx, pflag + k + 2 + sidx,
-                    lk, dflag + k, token, pflag + k + 2, status);
-        return;
+    t -= a.ns_next;
+    const int np = ld;
+    int I, J;
+    bool ok;
+    if (t < n_inner) {
+        band_tile(t, nin, a.icols, I, J);
+        const int rI = a.r0 + tc::TM * I, rJ = a.r0 + tc::TM * J;
+        const int bI = rI / NB, bJ = rJ / NB;
+        const int off = (a.r0 - a.srow0) / tc::TM;
+        auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
+        ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, a.st_base,
+                           tc::CHUNK_STAGES, tc_smem, ready, la && I == 0 && J == 0);
+    } else {
+        t -= n_inner;
+        const int nf = a.fcols > 0 ? (np - a.f0) / tc::TM : 0;
+        const long long n_front = band_tiles(nf, a.fcols);
+        if (a.next_start && t == 1) {
+            // the next panel's start, once front tile (0, 0) is stored
+            if (!wait_flags(a.dflag + k, 1, token, status)) return;
+            const int b0n = a.f0 / NB;
+            potrf_body<float>(L, ld, a.f0, a.Linv, a.info);
+            if (a.ns_start > 0)
+                diag_tail(L, ld, a.f0, a.Linv, a.lsT_out, a.ns_start, nullptr, a.pflag + b0n + 1, (unsigned)b0n + 1,
+                          status);
+            return;
+        }
+        if (a.next_start && t > 1) --t;
+        if (t < n_front) {
+            band_tile(t, nf, a.fcols, I, J);
+            const int rI = a.f0 + tc::TM * I, rJ = a.f0 + tc::TM * J;
+            const int bI = rI / NB, bJ = rJ / NB;
+            const int off = (a.f0 - a.srow0) / tc::TM;
+            auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
+            ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, 0, 4 * tc::CHUNK_STAGES,
+                               tc_smem, ready, false);
+            if (ok && t == 0 && a.next_start) {
+                // front tile (0, 0) is stored: release the next panel's start
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release(a.dflag + k, token);
+                }
+            }
+        } else {
+            t -= n_front;
+            const long long b = a.rb0 + t;   // lower-triangle tile index of [c0r, np)^2
+            I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+            while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
+            while ((long long)I * (I + 1) / 2 > b) --I;
+            J = (int)(b - (long long)I * (I + 1) / 2);
+            const int off = (a.c0r - a.srow0_p) / tc::TM;
+            auto ready = []() { return true; };
+            ok = tc::syrk_tile(L, ld, a.c0r + tc::TM * I, a.c0r + tc::TM * J, a.hi_p, a.lo_p, a.stage_stride,
+                               off + I, off + J, 0, 4 * tc::CHUNK_STAGES, tc_smem, ready, false);
+        }
     }
-    const long long b = t - npanel - 1 - ns_next;
-    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
-    while ((long long)I * (I + 1) / 2 > b) --I;
-    const int J = (int)(b - (long long)I * (I + 1) / 2);
-    const int bI = (r0 + tc::TM * I) / NB, bJ = (r0 + tc::TM * J) / NB;
-    const size_t stage_stride = (size_t)(ld / tc::TM + 1) * tc::HALF_BYTES;
-    auto ready = [&]() { return wait_flags(pflag + bI, 2, pflag + bJ, 2, token, status); };
-    // tile (0, 0) leaves block (k+2, k+2) to the lookahead helper when the
-    // strip is one block wide
-    if (!tc::syrk_tile(L, ld, r0 + tc::TM * I, r0 + tc::TM * J, hi, lo, stage_stride, I, J, tc_smem, ready,
-                       b == 0 && sw == 1)) {
-        if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
-        return;
-    }
+    if (!ok && threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
 }
 
 template <typename T>
@@ -868,73 +997,129 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
     if constexpr (kTensor) {
         if ((e = cudaFuncSetAttribute(factor_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmem)) !=
                 cudaSuccess ||
-            (e = cudaFuncSetAttribute(potrf_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
+            (e = cudaFuncSetAttribute(panel_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
                 cudaSuccess)
             return e;
-        // work space: hi and lo panel copies, two strip-row buffers, panel
-        // flags and per-step tickets (cholesky_f32_split_bytes)
-        const size_t oper = (size_t)(np / tc::TM + 1) * tc::OPER_BYTES;
-        unsigned char* hi = split;
-        unsigned char* lo = split + oper;
-        float* lsT = reinterpret_cast<float*>(split + 2 * oper);   // 2 x (2 x 64 x 64)
-        unsigned* pflag = reinterpret_cast<unsigned*>(split + 2 * oper + 4 * NB * NB * sizeof(float));
+        // work space (cholesky_f32_split_bytes): the hi and lo split of two
+        // panels (by parity), two strip-row buffers, then per 64-row block
+        // the panel flag, the step's ticket, the diagonal-block flag and the
+        // count of finished panel halves
+        const size_t stage_stride = split_stage_stride(np);
+        const size_t part = (size_t)kPanelStages * stage_stride;
+        float* lsT = reinterpret_cast<float*>(split + 4 * part);   // 2 x (2 x 64 x 64)
+        unsigned* pflag = reinterpret_cast<unsigned*>(split + 4 * part + 4 * NB * NB * sizeof(float));
         unsigned* tickets = pflag + nblk;
         unsigned* dflag = tickets + nblk;
         unsigned* halves = dflag + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
         if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
-        // strip width of step k: one or two column blocks, leaving an even
-        // number of blocks (whole 128-tiles) for the tensor cores
-        auto strip_width = [nblk](int k) {
-            const int m = nblk - k - 1;
-            return m <= 0 ? 0 : (((m - 1) & 1) ? 2 : 1);
-        };
-        // block 0 is factored alone; every later diagonal block is factored
-        // inside the launch of the previous step
-        potrf_first<<<1, 256, kStripSmem, s>>>(Lf, np, Linvf, info, lsT, strip_width(0), pflag);
-        count_launch();
+        // strip width of a step with m blocks of its panel right of the
+        // diagonal: one or two column blocks, leaving an even number (whole
+        // 128-tiles) to the tensor cores
+        auto strip_width = [](int m) { return m <= 0 ? 0 : (((m - 1) & 1) ? 2 : 1); };
         cudaLaunchAttribute pdl[1];
         pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         pdl[0].val.programmaticStreamSerializationAllowed = 1;
-        for (int k = 0; k + 1 < nblk; ++k) {
-            const int m = nblk - k - 1;   // row blocks below the diagonal
-            const int sw = strip_width(k);
-            const int r0 = (k + 1 + sw) * NB;
-            const long long nt = (np - r0) / tc::TM;
-            const long long tiles = nt * (nt + 1) / 2;
-            float* ls_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
-            float* ls_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
-            cudaLaunchConfig_t cfg = {};
-            // 2 (m - 1) half panel rows, the diagonal CTA, its strip-row helpers, the tiles
-            cfg.gridDim = dim3((unsigned)(2 * (m - 1) + 1 + strip_width(k + 1) + tiles));
-            cfg.blockDim = dim3(256);
-            cfg.dynamicSmemBytes = kFactorSmem;
-            cfg.stream = s;
-            cfg.attrs = pdl;
-            cfg.numAttrs = 1;
-            cudaEvent_t ev = trace_begin(s);
-            if ((e = cudaLaunchKernelEx(&cfg, factor_step, Lf, np, k, Linvf, info, nblk, sw, r0, hi, lo,
-                                        (const float*)ls_in, ls_out, strip_width(k + 1), pflag, tickets,
-                                        dflag, halves)) !=
-                cudaSuccess)
-                return e;
-            count_launch();
-            {
-                // algorithmic bytes: per row block A_ik read, L_ik and its
-                // hi/lo split written, strip blocks read and written; every
-                // lower 128-tile of [r0, np)^2 read and written once and the
-                // split panel read once; the diagonal block read, its factor
-                // and inverse written.  Useful flops: panel products, strip
-                // and tile updates, diagonal factor and inverse.
-                const double blk = 4.0 * NB * NB, tb = 4.0 * tc::TM * tc::TM;
-                const double strips = (double)m * sw - (sw - 1);
-                const double bytes = 2.0 * m * blk + 8.0 * (np - r0) * NB + 2.0 * strips * blk +
-                                     2.0 * tiles * tb + 8.0 * (np - r0) * NB + 3.0 * blk;
-                const double flops = (double)m * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
-                                     (double)tiles * 2.0 * tc::TM * tc::TM * tc::TK + 2.0 * NB * NB * NB / 3.0;
-                trace_end(GBEM_KERNEL_FACTOR, ev, s, bytes, flops);
+        const double blk = 4.0 * NB * NB, tb = 4.0 * tc::TM * tc::TM;
+        int prev_srow0 = 0;
+        for (int q = 0, b0 = 0; b0 < nblk; ++q, b0 += kPanel) {
+            const int e0 = std::min(b0 + kPanel, nblk);   // the panel is [b0, e0)
+            unsigned char* hi = split + (size_t)(q & 1) * 2 * part;
+            unsigned char* lo = hi + part;
+            const unsigned char* hi_p = split + (size_t)((q + 1) & 1) * 2 * part;
+            const unsigned char* lo_p = hi_p + part;
+            const int srow0 = (b0 + 1 + strip_width(e0 - b0 - 1)) * NB;   // the panel's first tile row
+            // the first diagonal block, the strip rows and lookahead of step
+            // b0: a launch of its own for the first panel, the previous
+            // panel's last step for the others
+            if (q == 0) {
+                cudaEvent_t ev = trace_begin(s);
+                panel_start<<<1, 256, kStripSmem, s>>>(Lf, np, b0, Linvf, info, lsT + (size_t)(b0 & 1) * 2 * NB * NB,
+                                                       strip_width(e0 - b0 - 1), pflag);
+                count_launch();
+                trace_end(GBEM_KERNEL_FACTOR, ev, s, 4.0 * blk, 2.0 * NB * NB * NB / 3.0);
             }
+            // the previous panel's update of [e0, np)^2, over this panel's
+            // steps but the last
+            const int c0r = e0 * NB;
+            const long long ntr = (np - c0r) / tc::TM;
+            const long long rest = q > 0 ? ntr * (ntr + 1) / 2 : 0;
+            const int rest_steps = e0 - b0 - 1;
+            for (int k = b0; k < e0; ++k) {
+                StepArgs a{};
+                a.L = Lf;
+                a.ld = np;
+                a.k = k;
+                a.nblk = nblk;
+                a.Linv = Linvf;
+                a.info = info;
+                a.sw = strip_width(e0 - k - 1);
+                a.p0 = a.sw >= 1 ? k + 2 : k + 1;
+                a.has_diag = k + 1 < e0;
+                a.ns_next = a.has_diag ? strip_width(e0 - k - 2) : 0;
+                a.hi = hi;
+                a.lo = lo;
+                a.srow0 = srow0;
+                a.st_base = (k - b0) * tc::CHUNK_STAGES;
+                a.stage_stride = stage_stride;
+                a.r0 = (k + 1 + a.sw) * NB;
+                a.icols = (e0 * NB - a.r0) / tc::TM;
+                a.f0 = e0 * NB;
+                a.fcols = (k == e0 - 1 && e0 < nblk) ? (std::min(e0 + kPanel, nblk) - e0) * NB / tc::TM : 0;
+                a.next_start = a.fcols > 0;
+                a.ns_start = a.next_start ? strip_width(std::min(e0 + kPanel, nblk) - e0 - 1) : 0;
+                a.hi_p = hi_p;
+                a.lo_p = lo_p;
+                a.srow0_p = prev_srow0;
+                a.c0r = c0r;
+                const int j = k - b0;
+                a.rb0 = (rest > 0 && j < rest_steps) ? rest * j / rest_steps : 0;
+                a.rb1 = (rest > 0 && j < rest_steps) ? rest * (j + 1) / rest_steps : 0;
+                a.lsT_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
+                a.lsT_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
+                a.pflag = pflag;
+                a.tickets = tickets;
+                a.dflag = dflag;
+                a.halves = halves;
+                // a lookahead helper that applies this step's update to block
+                // (k+2, k+2) needs the inner tile (0, 0) that leaves it alone
+                if (a.sw == 1 && a.ns_next >= 1 && a.icols < 1) return cudaErrorInvalidValue;
+                const long long npan = nblk - a.p0;
+                const long long n_in = band_tiles((np - a.r0) / tc::TM, a.icols);
+                const long long n_fr = a.fcols > 0 ? band_tiles((np - a.f0) / tc::TM, a.fcols) : 0;
+                const long long n_rest = a.rb1 - a.rb0;
+                const long long grid = 2 * npan + a.has_diag + a.ns_next + n_in + n_fr + a.next_start + n_rest;
+                if (grid == 0) continue;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)grid);
+                cfg.blockDim = dim3(256);
+                cfg.dynamicSmemBytes = kFactorSmem;
+                cfg.stream = s;
+                cfg.attrs = pdl;
+                cfg.numAttrs = 1;
+                cudaEvent_t ev = trace_begin(s);
+                if ((e = cudaLaunchKernelEx(&cfg, factor_step, a)) != cudaSuccess) return e;
+                count_launch();
+                {
+                    // algorithmic bytes: per panel row block A_ik read, L_ik
+                    // and its hi/lo split written, strip blocks read and
+                    // written; every tile read and written once and its split
+                    // rows read once; the diagonal block read, its factor and
+                    // inverse written.  Useful flops: panel products, strip
+                    // and tile updates (2mnk), diagonal factor and inverse.
+                    const double strips = (double)npan * a.sw;
+                    const double kt = (double)(n_fr + n_rest) * 4 * tc::TK + (double)n_in * tc::TK;
+                    const int diags = a.has_diag + a.next_start;
+                    const double bytes = 2.0 * npan * blk + 8.0 * npan * NB * NB + 2.0 * strips * blk +
+                                         2.0 * (n_in + n_fr + n_rest) * tb + 2.0 * 8.0 * tc::TM * kt +
+                                         3.0 * diags * blk;
+                    const double flops = (double)npan * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
+                                         2.0 * tc::TM * tc::TM * kt + diags * 2.0 * NB * NB * NB / 3.0;
+                    trace_end(GBEM_KERNEL_FACTOR, ev, s, bytes, flops);
+                }
+            }
+            prev_srow0 = srow0;
         }
         return cudaGetLastError();
     }
@@ -998,9 +1183,9 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 
 size_t cholesky_f32_split_bytes(int np)
 {
-    // hi/lo panel copies, two strip-row buffers, panel flags, step tickets,
-    // diagonal-block flags and half-panel counters
-    return 2 * (size_t)(np / tc::TM + 1) * tc::OPER_BYTES + 4 * NB * NB * sizeof(float) +
+    // hi/lo split of two panels, two strip-row buffers, panel flags, step
+    // tickets, diagonal-block flags and half-panel counters
+    return 4 * (size_t)kPanelStages * split_stage_stride(np) + 4 * NB * NB * sizeof(float) +
            4 * (size_t)(np / NB) * sizeof(unsigned);
 }
 

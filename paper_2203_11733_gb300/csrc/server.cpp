@@ -57,7 +57,7 @@ size_t request_bytes(int n, int nc, gbem_precision prec)
     size_t b = 8 * np * np;                                   // A64
     b += (prec == GBEM_MIXED ? 4 : 8) * np * np;              // A32 or the FP64 factor
     b += 8 * np * 64;                                         // diagonal-block inverses
-    b += 2 * (np / 128 + 1) * 32768;                          // split panel (mixed)
+    if (prec == GBEM_MIXED) b += cholesky_f32_split_bytes((int)np);   // split panels, flags
     b += np * (size_t)std::max(nc, 1) * 40;                   // solve vectors
     b += 45 * (size_t)n + (1u << 20);                         // panels, flags, slack
     return b;

@@ -1,35 +1,38 @@
-// Tensor-core (tcgen05, kind::tf32) trailing update of the blocked Cholesky:
+// Tensor-core (tcgen05, kind::tf32) trailing updates of the blocked Cholesky:
 //
-//     C[I, J] -= A_I A_J^T        (A_I, A_J: 128 x 64 row blocks of the panel)
+//     C[I, J] -= A_I A_J^T        (A_I, A_J: 128-row blocks of split panel columns)
 //
 // in 3xTF32 arithmetic: every fp32 operand is split as a = a_hi + a_lo with
 // a_hi = tf32(a) (round to nearest) and a_lo = a - a_hi, and the product is
 // accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi, which keeps
 // the error of the update near FP32 rounding.
 //
-// The panel columns [k0, k0 + 64) are split once per elimination step (by
-// the panel work, as it produces them) into hi and lo copies laid out, per K
-// stage of 32 columns and 128-row block, exactly as the tensor core reads
-// them from shared memory: the canonical K-major layout without swizzle,
-// 8-row x 16-byte core matrices consecutive along K (leading byte offset
-// 128 B, 8 of them for 32 columns) and then along M/N (stride byte offset
-// 1024 B).  One stage of a 128-row block of one part is 16 KB of contiguous
-// bytes.
+// Panel columns are split, by the panel work as it produces them, into hi and
+// lo copies laid out per K stage of 16 columns and 128-row block exactly as
+// the tensor core reads them from shared memory: the canonical K-major layout
+// without swizzle, 8-row x 16-byte core matrices consecutive along K (leading
+// byte offset 128 B, 4 of them for 16 columns) and then along M/N (stride
+// byte offset 512 B).  One stage of a 128-row block of one part is 8 KB of
+// contiguous bytes; a 64-column chunk of the panel is 4 stages.
 //
-// One CTA (8 warps) owns one 128 x 128 tile, with the 64-wide panel taken in
-// two K stages of 32 so that a tile needs 64 KB of shared memory and two tile
-// CTAs share an SM:
-//   1. warp 0 allocates 128 TMEM columns (the FP32 accumulator, one lane per
-//      tile row); one thread bulk-copies (cp.async.bulk, completing on an
-//      mbarrier) the stage-0 hi/lo blocks of rows I and J (diagonal tiles
-//      copy one pair);
+// One CTA (8 warps) owns one 128 x 128 tile and takes the K stages through a
+// ring of NBUF = 3 shared-memory buffers (96 KB, so two tile CTAs share an
+// SM):
+//   1. warp 0 allocates 256 TMEM columns: two FP32 accumulators (one lane per
+//      tile row) that take the 64-column chunks of the panel in turn;
 //   2. every thread loads its 64 entries of C into registers, so that their
 //      latency overlaps the copies and the MMAs;
-//   3. thread 0 issues the stage's 4 K-steps x 3 tcgen05.mma (M = N = 128,
-//      K = 8) and commits them to a second mbarrier; once they have read the
-//      stage, it copies stage 1 into the same buffers and issues its MMAs;
-//   4. after the bounded wait every warp reads 32 accumulator lanes x 64
-//      columns with tcgen05.ld and stores C minus the product;
+//   3. thread 0 bulk-copies (cp.async.bulk, completing on the buffer's
+//      "full" mbarrier) the first three stages, then for every stage waits
+//      for its copy, issues 2 K-steps x 3 tcgen05.mma (M = N = 128, K = 8)
+//      and commits them to the buffer's "empty" mbarrier, and refills the
+//      buffer of the previous stage once its MMAs have read it; after a
+//      chunk's last stage it commits to the accumulator's mbarrier;
+//   4. while thread 0 issues chunk c + 1, every warp waits for chunk c's
+//      accumulator, reads its 32 lanes x 64 columns with tcgen05.ld and
+//      subtracts them from its registers of C, so C is rounded to FP32 after
+//      every 64 columns of K as in a step-by-step update; after the last
+//      chunk the registers are stored;
 //   5. warp 0 frees the TMEM columns.
 // Only the wait for the panel rows (other CTAs' results) can give up in
 // practice.  The waits on the CTA's own copies and MMAs carry the long
@@ -45,29 +48,33 @@
 namespace tc {
 
 constexpr int TM = 128;       // tile rows (MMA M) and columns (MMA N)
-constexpr int TK = 64;        // panel width (sum over K)
-constexpr int KH = 32;        // K per pipeline stage (two stages per panel)
-constexpr int OPER_BYTES = TM * TK * 4;                 // one operand part (hi or lo) of a 128-row block
-constexpr int HALF_BYTES = TM * KH * 4;                 // ... and of one stage
-constexpr int SMEM_BYTES = 4 * HALF_BYTES + 256;        // A_hi, A_lo, B_hi, B_lo of a stage, barriers + TMEM slot
+constexpr int TK = 64;        // width of one panel chunk (an elimination step's columns)
+constexpr int KH = 16;        // K per pipeline stage
+constexpr int CHUNK_STAGES = TK / KH;                   // stages per 64-column chunk
+constexpr int NBUF = 3;                                 // stages in flight
+constexpr int STAGE_BYTES = TM * KH * 4;                // one operand part of a 128-row block, one stage
+constexpr int BUF_BYTES = 4 * STAGE_BYTES;              // A_hi, A_lo, B_hi, B_lo of a stage
+constexpr int SMEM_BYTES = NBUF * BUF_BYTES + 256;      // the ring, barriers and the TMEM slot
+constexpr int TMEM_COLS = 2 * TM;                       // two accumulators (two tile CTAs fill an SM's 512)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row r, k) of a 128 x 32 fp32 stage operand in the
+// Byte offset of element (row r, k) of a 128 x 16 fp32 stage operand in the
 // K-major, no-swizzle core-matrix layout.
 __device__ __forceinline__ uint32_t kmajor_offset(int r, int k)
 {
     return (uint32_t)((k >> 2) * 128 + (r >> 3) * (KH / 4) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
-// Byte offset of panel element (row rr from r0, column k < 64) in one part of
-// the split buffer: stage k / 32, then 128-row block, then the stage layout.
+// Byte offset of panel element (row rr from the split's first row, column k
+// of a chunk) in one part of the split buffer: stage k / 16, then 128-row
+// block, then the stage layout.
 __device__ __forceinline__ size_t split_offset(int rr, int k, size_t stage_stride)
 {
-    return (size_t)(k / KH) * stage_stride + (size_t)(rr / TM) * HALF_BYTES + kmajor_offset(rr % TM, k % KH);
+    return (size_t)(k / KH) * stage_stride + (size_t)(rr / TM) * STAGE_BYTES + kmajor_offset(rr % TM, k % KH);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits
@@ -164,51 +171,59 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return true;
 }
 
-// C[rI + .., rJ + ..] -= A_I A_J^T for one 128 x 128 tile.  I and J index the
-// 128-row blocks of the split panel (rows rI = r0 + 128 I, rJ = r0 + 128 J);
-// stage_stride is the byte distance between the two K stages of a part.
-// 256 threads.  `ready()` (called by every thread, returns whether the split
-// panel rows this tile reads are written) is called after the accumulator is
-// allocated, the CTA has given up its TMEM allocation permit and the tile of C
-// is loaded into registers: C is not written by this launch before the tile,
-// and a CTA that holds the permit keeps the SM from taking a second CTA of the
-// kernel.  With skip00 the top-left 64 x 64 quadrant of the tile is neither
-// read nor written (another CTA updates it).  Returns false if a wait gave
-// up.
+// C[rI + .., rJ + ..] -= A_I A_J^T for one 128 x 128 tile, over the split
+// stages st0 .. st0 + nst - 1.  ia and ja index the 128-row blocks of the
+// split holding rows rI and rJ; stage_stride is the byte distance between two
+// stages of a part.  256 threads.  `ready()` (called by every thread, returns
+// whether the split rows this tile reads are written) is called after the
+// accumulator is allocated, the CTA has given up its TMEM allocation permit
+// and the tile of C is loaded into registers: C is not written by this
+// launch before the tile, and a CTA that holds the permit keeps the SM from
+// taking a second CTA of the kernel.  With skip00 the top-left 64 x 64
+// quadrant of the tile is neither read nor written (another CTA updates it).
+// Returns false if a wait gave up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
-                          const unsigned char* __restrict__ lo, size_t stage_stride, int I, int J,
-                          unsigned char* smem, Ready ready, bool skip00)
+                          const unsigned char* __restrict__ lo, size_t stage_stride, int ia, int ja, int st0,
+                          int nst, unsigned char* smem, Ready ready, bool skip00)
 {
-    unsigned char* a_hi = smem;
-    unsigned char* a_lo = smem + HALF_BYTES;
-    unsigned char* b_hi = (I == J) ? a_hi : smem + 2 * HALF_BYTES;
-    unsigned char* b_lo = (I == J) ? a_lo : smem + 3 * HALF_BYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * HALF_BYTES);   // [0] operands, [1] MMAs
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4 * HALF_BYTES + 64);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
-    const uint32_t parts = (I == J) ? 2 : 4;
-    auto issue = [&](int h) {
-        mbar_expect_tx(bar_ld, parts * HALF_BYTES);
-        const size_t o = (size_t)h * stage_stride;
-        bulk_g2s(smem_u32(a_hi), hi + o + (size_t)I * HALF_BYTES, HALF_BYTES, bar_ld);
-        bulk_g2s(smem_u32(a_lo), lo + o + (size_t)I * HALF_BYTES, HALF_BYTES, bar_ld);
-        if (I != J) {
-            bulk_g2s(smem_u32(b_hi), hi + o + (size_t)J * HALF_BYTES, HALF_BYTES, bar_ld);
-            bulk_g2s(smem_u32(b_lo), lo + o + (size_t)J * HALF_BYTES, HALF_BYTES, bar_ld);
+    const bool diag = ia == ja;
+    // barriers: [b] full, [NBUF + b] empty, [2 NBUF + a] accumulator a done
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NBUF * BUF_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + NBUF * BUF_BYTES + 64);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(smem + NBUF * BUF_BYTES + 68);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = (nst + CHUNK_STAGES - 1) / CHUNK_STAGES;   // 64-column chunks
+    auto full = [&](int b) { return smem_u32(&bars[b]); };
+    auto empty = [&](int b) { return smem_u32(&bars[NBUF + b]); };
+    auto accf = [&](int a) { return smem_u32(&bars[2 * NBUF + a]); };
+    auto part = [&](int b, int p) { return smem_u32(smem + (size_t)b * BUF_BYTES + (size_t)p * STAGE_BYTES); };
+    // copy stage s (of this tile's range) into buffer b
+    auto issue = [&](int s, int b) {
+        mbar_expect_tx(full(b), (diag ? 2u : 4u) * STAGE_BYTES);
+        const size_t o = (size_t)(st0 + s) * stage_stride;
+        bulk_g2s(part(b, 0), hi + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b));
+        bulk_g2s(part(b, 1), lo + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b));
+        if (!diag) {
+            bulk_g2s(part(b, 2), hi + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b));
+            bulk_g2s(part(b, 3), lo + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b));
         }
     };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TM)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        mbar_init(bar_ld, 1);
-        mbar_init(bar_mma, 1);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(full(b), 1);
+            mbar_init(empty(b), 1);
+        }
+        mbar_init(accf(0), 1);
+        mbar_init(accf(1), 1);
+        *s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -218,79 +233,133 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     // this thread's 64 entries of C (row q * 32 + lane, columns 64 half ..),
     // loaded now so that their latency overlaps the wait, the copies and MMAs
     const int q = warp & 3, half = warp >> 2;
-    const int row = q * 32 + (tid & 31);
+    const int row = q * 32 + lane;
     float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
     const bool mine = !(skip00 && q < 2 && half == 0);   // warp-uniform
     float cpre[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
     int ok = ready() ? 1 : 0;
-    int loads = ok, commits = 0;
-    if (ok && tid == 32) {
-        // the split was written by other CTAs of this launch (generic-proxy
-        // stores): order them before the async-proxy copies
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        issue(0);
-    }
-
-    // thread 0: stage 0 MMAs, then (once they have read shared memory) the
-    // stage-1 copies into the same buffers, then the stage-1 MMAs
-    if (ok && tid == 0) {
-        const uint32_t idesc = make_idesc();
-        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-        for (int h = 0; h < 2 && ok; ++h) {
-            if (!mbar_wait_bounded(bar_ld, h)) {
-                ok = 0;
-                break;
-            }
+    // thread 0's pipeline state.  loads[b] / commits[b] / acommits[a]: phases
+    // started on the full / empty / accumulator barriers (for the drain after
+    // a failed wait)
+    int loads[NBUF], commits[NBUF], acommits[2] = {0, 0};
+    for (int b = 0; b < NBUF; ++b) loads[b] = commits[b] = 0;
+    int s_next = 0;
+    const uint32_t idesc = make_idesc();
+    // thread 0: the MMAs of chunk c into accumulator c % 2 (its stages in the
+    // ring, refilling as they are read), then a commit to that accumulator
+    auto run_chunk = [&](int c) -> bool {
+        const int s_end = min(nst, (c + 1) * CHUNK_STAGES);
+        const uint32_t acc = tmem + (uint32_t)((c & 1) * TM);
+        for (; s_next < s_end; ++s_next) {
+            const int s = s_next, b = s % NBUF;
+            if (!mbar_wait_bounded(full(b), (uint32_t)(s / NBUF) & 1u)) return false;
+            const uint32_t ah = part(b, 0), al = part(b, 1);
+            const uint32_t bh = diag ? ah : part(b, 2), bl = diag ? al : part(b, 3);
+            const bool first = s == c * CHUNK_STAGES;
 #pragma unroll
             for (int ks = 0; ks < KH / 8; ++ks) {
                 const uint32_t off = ks * 256;   // 8 tf32 = two core matrices along K
-                mma_tf32(tmem, make_desc(ah + off), make_desc(bh + off), idesc, h > 0 || ks > 0);
-                mma_tf32(tmem, make_desc(ah + off), make_desc(bl + off), idesc, 1);
-                mma_tf32(tmem, make_desc(al + off), make_desc(bh + off), idesc, 1);
+                mma_tf32(acc, make_desc(ah + off), make_desc(bh + off), idesc, !first || ks > 0);
+                mma_tf32(acc, make_desc(ah + off), make_desc(bl + off), idesc, 1);
+                mma_tf32(acc, make_desc(al + off), make_desc(bh + off), idesc, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             bar_mma)
+                             empty(b))
                          : "memory");
-            ++commits;
-            if (h == 0) {
-                if (!mbar_wait_bounded(bar_mma, 0)) {
-                    ok = 0;
-                    break;
-                }
-                issue(1);
-                ++loads;
+            ++commits[b];
+            // refill the previous stage's buffer once its MMAs have read it
+            // (this stage's MMAs keep the tensor pipe busy meanwhile)
+            const int sp = s - 1;
+            if (sp >= 0 && sp + NBUF < nst) {
+                const int bp = sp % NBUF;
+                if (!mbar_wait_bounded(empty(bp), (uint32_t)(sp / NBUF) & 1u)) return false;
+                issue(sp + NBUF, bp);
+                ++loads[bp];
             }
         }
-    }
-    // every thread learns whether thread 0's waits succeeded
-    ok = __syncthreads_and(ok);
-    if (ok) ok = mbar_wait_bounded(bar_mma, 1);
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && mine) {
-        // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
-#pragma unroll
-        for (int cc = 0; cc < 64; cc += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64 + cc), v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) crow[(size_t)(cc + i) * ld] = cpre[cc + i] - v[i];
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         accf(c & 1))
+                     : "memory");
+        ++acommits[c & 1];
+        return true;
+    };
+    if (ok && tid == 0) {
+        // the split was written by other CTAs of this launch (generic-proxy
+        // stores): order them before the async-proxy copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const int pre = nst < NBUF ? nst : NBUF;
+        for (int s = 0; s < pre; ++s) {
+            issue(s, s);
+            ++loads[s];
         }
+        if (!run_chunk(0)) {
+            ok = 0;
+            *s_fail = 1;
+        }
+    }
+    // every thread learns whether thread 0 issued chunk 0 (ok is uniform from
+    // here on: the loop's barriers are reached by all threads or by none)
+    ok = __syncthreads_and(ok);
+    for (int c = 0; c < nch && ok; ++c) {
+        if (tid == 0 && c + 1 < nch && !run_chunk(c + 1)) {
+            ok = 0;
+            *s_fail = 1;
+        }
+        __syncwarp();
+        // lane 0 of each warp waits for chunk c's accumulator (giving up at
+        // once if thread 0 has failed), the warp follows its verdict
+        int got = 1;
+        if (lane == 0) {
+            bw::Deadline dl(bw::kOwnAsyncNs);
+            while (!mbar_try_wait(accf(c & 1), (uint32_t)(c >> 1) & 1u)) {
+                if (*s_fail || dl.expired()) {
+                    got = 0;
+                    break;
+                }
+            }
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (got && mine) {
+            // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((c & 1) * TM + half * 64);
+#pragma unroll
+            for (int cc = 0; cc < 64; cc += 16) {
+                float v[16];
+                tmem_ld16(base + (uint32_t)cc, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cpre[cc + i] -= v[i];
+            }
+        }
+        if (!got) ok = 0;
+        // every warp has read accumulator c % 2 before chunk c + 2 reuses it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ok = __syncthreads_and(ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    ok = __syncthreads_and(ok);
+    if (ok && mine) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) crow[(size_t)i * ld] = cpre[i];
     }
     // after a failed wait, let the copies and MMAs this CTA issued finish
     // before its shared memory and TMEM are released: phases complete in
     // order, so the last phase of each barrier covers all earlier ones
     if (!ok && tid == 0) {
-        if (loads > 0) mbar_wait_bounded(bar_ld, (uint32_t)(loads - 1) & 1u);
-        if (commits > 0) mbar_wait_bounded(bar_mma, (uint32_t)(commits - 1) & 1u);
+        for (int b = 0; b < NBUF; ++b) {
+            if (loads[b] > 0) mbar_wait_bounded(full(b), (uint32_t)(loads[b] - 1) & 1u);
+            if (commits[b] > 0) mbar_wait_bounded(empty(b), (uint32_t)(commits[b] - 1) & 1u);
+        }
+        for (int a = 0; a < 2; ++a)
+            if (acommits[a] > 0) mbar_wait_bounded(accf(a), (uint32_t)(acommits[a] - 1) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
     return ok;
 }
