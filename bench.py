@@ -72,8 +72,10 @@ def parse():
                     help="one warm-up and one extraction in that precision, nothing else "
                          "(for ncu captures)")
     ap.add_argument("--profile-workload", default="crossing_bus_2x2",
-                    choices=["crossing_bus_2x2", "two_bars", "bus_3layer_5x5x5"],
-                    help="structure of the --profile run (two_bars: a small case for pass counts)")
+                    choices=["crossing_bus_2x2", "two_bars", "bus_3layer_5x5x5", "bus_3layer_mid"],
+                    help="structure of the --profile run (two_bars: a small case for pass counts; "
+                         "bus_3layer_mid: the three-layer bus at h 70 nm, N = 10938, matrices of 1.5 GB, "
+                         "for full-section ncu captures)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 10 if args.impl == "reference" else 20
@@ -498,7 +500,10 @@ def run_ours(args):
         return C
 
     if args.profile:
-        boxes, params = getattr(W, args.profile_workload)()
+        if args.profile_workload == "bus_3layer_mid":
+            boxes, params = W.bus_3layer_5x5x5(h=0.07, h_min=0.014)
+        else:
+            boxes, params = getattr(W, args.profile_workload)()
         mesh = gbem.gbem_mesh(ctx, boxes, params)
         prec = gbem.GBEM_MIXED if args.profile == "mixed" else gbem.GBEM_FP64
         step(mesh, prec)

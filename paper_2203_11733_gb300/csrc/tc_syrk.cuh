@@ -148,11 +148,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+// L2 policy for the split operands: kept (evict last), since every tile of
+// their row and column reads them again, while the tiles of C stream through
+// L2 once (loaded and stored with the evict-first streaming hints)
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
         : "memory");
 }
 
@@ -199,14 +210,15 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     auto accf = [&](int a) { return smem_u32(&bars[2 * NBUF + a]); };
     auto part = [&](int b, int p) { return smem_u32(smem + (size_t)b * BUF_BYTES + (size_t)p * STAGE_BYTES); };
     // copy stage s (of this tile's range) into buffer b
+    const uint64_t pol = policy_evict_last();
     auto issue = [&](int s, int b) {
         mbar_expect_tx(full(b), (diag ? 2u : 4u) * STAGE_BYTES);
         const size_t o = (size_t)(st0 + s) * stage_stride;
-        bulk_g2s(part(b, 0), hi + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b));
-        bulk_g2s(part(b, 1), lo + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b));
+        bulk_g2s(part(b, 0), hi + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+        bulk_g2s(part(b, 1), lo + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b), pol);
         if (!diag) {
-            bulk_g2s(part(b, 2), hi + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b));
-            bulk_g2s(part(b, 3), lo + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b));
+            bulk_g2s(part(b, 2), hi + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+            bulk_g2s(part(b, 3), lo + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
         }
     };
 
@@ -238,7 +250,7 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     const bool mine = !(skip00 && q < 2 && half == 0);   // warp-uniform
     float cpre[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) cpre[i] = crow[(size_t)i * ld];
+    for (int i = 0; i < 64; ++i) cpre[i] = __ldcs(crow + (size_t)i * ld);
     int ok = ready() ? 1 : 0;
     // thread 0's pipeline state.  loads[b] / commits[b] / acommits[a]: phases
     // started on the full / empty / accumulator barriers (for the drain after
@@ -342,7 +354,7 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     ok = __syncthreads_and(ok);
     if (ok && mine) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) crow[(size_t)i * ld] = cpre[i];
+        for (int i = 0; i < 64; ++i) __stcs(crow + (size_t)i * ld, cpre[i]);
     }
     // after a failed wait, let the copies and MMAs this CTA issued finish
     // before its shared memory and TMEM are released: phases complete in
