@@ -20,6 +20,8 @@
 // waits on release flags for exactly the panel rows it needs.
 // A non-positive pivot sets info[0] = 1 and is replaced by 1 so that the
 // factorisation completes without NaNs; the host reports GBEM_ERR_NOT_SPD.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "gbem_internal.h"
@@ -545,7 +547,7 @@ __device__ void tail_helper(float* __restrict__ L, int ld, int k0, const float* 
 
 constexpr size_t kStripSmem = 4 * NB * PT * sizeof(float);
 // Panels of kPanel 64-column blocks; the split of a panel holds
-// kPanelStages K stages of 16 columns.
+// kPanelStages K stages of 32 columns.
 constexpr int kPanel = 4;
 constexpr int kPanelStages = kPanel * tc::CHUNK_STAGES;
 // Bytes between two K stages of one part of a panel split: one stage of every
@@ -554,6 +556,33 @@ inline size_t split_stage_stride(int np) { return (size_t)(np / tc::TM + 1) * tc
 constexpr size_t kPanelRowSmem = 4 * NB * PT * sizeof(float);
 // every role of factor_step within one dynamic allocation: two CTAs per SM
 constexpr size_t kFactorSmem = kPanelRowSmem > (size_t)tc::SMEM_BYTES ? kPanelRowSmem : (size_t)tc::SMEM_BYTES;
+
+// The split scale of the FP16 tensor-core operands: s = 2^(15 - e) with
+// 2^e > the largest sqrt(A_rr) over the diagonal (one CTA), so that every
+// entry of the factor, |L_rt| <= sqrt(A_rr), has |s L_rt| < 2^15 (FP16's
+// largest finite value is 65504).  scale[0] = s, scale[1] = 1 / s^2.
+__global__ void __launch_bounds__(1024) split_scale(const float* __restrict__ L, int ld, float* __restrict__ scale)
+{
+    __shared__ float wmax[32];
+    float m = 0.0f;
+    for (int r = threadIdx.x; r < ld; r += blockDim.x) m = fmaxf(m, L[(size_t)r * ld + r]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            int e = 0;
+            frexpf(sqrtf(fmaxf(m, 1e-30f)), &e);   // sqrt(max) < 2^e
+            e = max(-100, min(100, e));
+            scale[0] = ldexpf(1.0f, 15 - e);
+            scale[1] = ldexpf(1.0f, 2 * (e - 15));
+        }
+    }
+}
 
 // The first diagonal block b0 of a panel (every earlier update of it done by
 // the launches before), the strip rows of step b0 and the lookahead panel
@@ -668,9 +697,9 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
 // (one CTA; the two halves of a row block run in two CTAs):
 //   1. L_ik = A_ik Linv_kk^T for those rows, written in place (Linv_kk is
 //      lower triangular, so the sum over t stops at the output column);
-//   2. row blocks at or below srow0 write the TF32 hi/lo split of those rows
-//      in the tensor-core operand layout, as the 4 stages st_base .. of the
-//      panel's split;
+//   2. row blocks at or below srow0 write the FP16 hi/lo split of those rows,
+//      scaled by split_scale, in the tensor-core operand layout, as the 2
+//      stages st_base .. of the panel's split;
 //   3. A_ic -= L_ik L_ck^T on those rows for the sw strip blocks
 //      c = k+1 .. k+sw, c <= i, with L_ck (lsT, t-major) computed by the
 //      helpers of the previous step.
@@ -679,7 +708,7 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
 __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int srow0,
                            int st_base, size_t stage_stride, unsigned char* __restrict__ hi,
                            unsigned char* __restrict__ lo, const float* __restrict__ lsT, int i, int h,
-                           unsigned char* smem)
+                           unsigned char* smem, float split_scale)
 {
     constexpr int HR = NB / 2;   // rows of a half
     // Blocks are stored t-major (rows padded to 68 floats) so that a
@@ -732,14 +761,19 @@ __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __
         for (int u = 0; u < 2; ++u) {
             const int rr = rh - srow0 + tr + u;
             const size_t off = tc::split_offset(rr, tc, stage_stride) + (size_t)st_base * stage_stride;
-            float hv[4], lv[4];
+            __half hv[4], lv[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                hv[v] = tc::to_tf32(acc[u][v]);
-                lv[v] = acc[u][v] - hv[v];
+                const float x = acc[u][v] * split_scale;   // exact: a power of two
+                hv[v] = __float2half_rn(x);
+                lv[v] = __float2half_rn(x - __half2float(hv[v]));
             }
-            *reinterpret_cast<float4*>(hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-            *reinterpret_cast<float4*>(lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            *reinterpret_cast<uint2*>(hi + off) = make_uint2(
+                (uint32_t)__half_as_ushort(hv[0]) | ((uint32_t)__half_as_ushort(hv[1]) << 16),
+                (uint32_t)__half_as_ushort(hv[2]) | ((uint32_t)__half_as_ushort(hv[3]) << 16));
+            *reinterpret_cast<uint2*>(lo + off) = make_uint2(
+                (uint32_t)__half_as_ushort(lv[0]) | ((uint32_t)__half_as_ushort(lv[1]) << 16),
+                (uint32_t)__half_as_ushort(lv[2]) | ((uint32_t)__half_as_ushort(lv[3]) << 16));
         }
     }
     __syncthreads();   // aT holds L_ik
@@ -807,6 +841,7 @@ struct StepArgs {
     unsigned* tickets;
     unsigned* dflag;
     unsigned* halves;
+    const float* scale;   // [0] the split scale s, [1] 1 / s^2 (split_scale)
 };
 
 // Tile (I, J), I >= J, of a column band of `cols` 128-columns over nrow
@@ -876,6 +911,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     const int npanel = a.nblk - a.p0;   // panel row blocks, two CTAs each
     const unsigned token = (unsigned)k + 1;
     int* status = a.info + 3;
+    const float sc = a.scale[0], unsc = a.scale[1];
     long long t = (long long)t_raw - 2 * npanel;   // index among the other roles
     // roles without tensor-core work give up the CTA's TMEM allocation permit
     // at once: while a CTA holds it, no second CTA of the kernel is placed on
@@ -888,7 +924,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     if (t < 0) {
         const int i = a.p0 + t_raw / 2;
         panel_half(L, ld, k, a.Linv, a.sw, a.srow0, a.st_base, a.stage_stride, a.hi, a.lo, a.lsT_in, i, t_raw & 1,
-                   tc_smem);
+                   tc_smem, sc);
         __syncthreads();   // the half is stored
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
@@ -936,7 +972,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
         const int off = (a.r0 - a.srow0) / tc::TM;
         auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
         ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, a.st_base,
-                           tc::CHUNK_STAGES, tc_smem, ready, la && I == 0 && J == 0);
+                           tc::CHUNK_STAGES, tc_smem, ready, la && I == 0 && J == 0, unsc);
     } else {
         t -= n_inner;
         const int nf = a.fcols > 0 ? (np - a.f0) / tc::TM : 0;
@@ -959,7 +995,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
             const int off = (a.f0 - a.srow0) / tc::TM;
             auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
             ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, 0, 4 * tc::CHUNK_STAGES,
-                               tc_smem, ready, false);
+                               tc_smem, ready, false, unsc);
             if (ok && t == 0 && a.next_start) {
                 // front tile (0, 0) is stored: release the next panel's start
                 __syncthreads();
@@ -978,7 +1014,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
             const int off = (a.c0r - a.srow0_p) / tc::TM;
             auto ready = []() { return true; };
             ok = tc::syrk_tile(L, ld, a.c0r + tc::TM * I, a.c0r + tc::TM * J, a.hi_p, a.lo_p, a.stage_stride,
-                               off + I, off + J, 0, 4 * tc::CHUNK_STAGES, tc_smem, ready, false);
+                               off + I, off + J, 0, 4 * tc::CHUNK_STAGES, tc_smem, ready, false, unsc);
         }
     }
     if (!ok && threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
@@ -1008,12 +1044,15 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
         const size_t part = (size_t)kPanelStages * stage_stride;
         float* lsT = reinterpret_cast<float*>(split + 4 * part);   // 2 x (2 x 64 x 64)
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 4 * part + 4 * NB * NB * sizeof(float));
+        float* scale = reinterpret_cast<float*>(pflag + 4 * (size_t)nblk);   // 2 floats
         unsigned* tickets = pflag + nblk;
         unsigned* dflag = tickets + nblk;
         unsigned* halves = dflag + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
         if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        split_scale<<<1, 1024, 0, s>>>(reinterpret_cast<const float*>(L), np, scale);
+        count_launch();
         // strip width of a step with m blocks of its panel right of the
         // diagonal: one or two column blocks, leaving an even number (whole
         // 128-tiles) to the tensor cores
@@ -1082,6 +1121,7 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                 a.tickets = tickets;
                 a.dflag = dflag;
                 a.halves = halves;
+                a.scale = scale;
                 // a lookahead helper that applies this step's update to block
                 // (k+2, k+2) needs the inner tile (0, 0) that leaves it alone
                 if (a.sw == 1 && a.ns_next >= 1 && a.icols < 1) return cudaErrorInvalidValue;
@@ -1109,10 +1149,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                     // inverse written.  Useful flops: panel products, strip
                     // and tile updates (2mnk), diagonal factor and inverse.
                     const double strips = (double)npan * a.sw;
-                    const double kt = (double)(n_fr + n_rest) * 4 * tc::TK + (double)n_in * tc::TK;
+                    const double kt = (double)(n_fr + n_rest) * 4 * tc::TK + (double)n_in * tc::TK;   // K summed over tiles
                     const int diags = a.has_diag + a.next_start;
                     const double bytes = 2.0 * npan * blk + 8.0 * npan * NB * NB + 2.0 * strips * blk +
-                                         2.0 * (n_in + n_fr + n_rest) * tb + 2.0 * 8.0 * tc::TM * kt +
+                                         2.0 * (n_in + n_fr + n_rest) * tb + 2.0 * 4.0 * tc::TM * kt +
                                          3.0 * diags * blk;
                     const double flops = (double)npan * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
                                          2.0 * tc::TM * tc::TM * kt + diags * 2.0 * NB * NB * NB / 3.0;
@@ -1186,7 +1226,7 @@ size_t cholesky_f32_split_bytes(int np)
     // hi/lo split of two panels, two strip-row buffers, panel flags, step
     // tickets, diagonal-block flags and half-panel counters
     return 4 * (size_t)kPanelStages * split_stage_stride(np) + 4 * NB * NB * sizeof(float) +
-           4 * (size_t)(np / NB) * sizeof(unsigned);
+           4 * (size_t)(np / NB) * sizeof(unsigned) + 2 * sizeof(float);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,

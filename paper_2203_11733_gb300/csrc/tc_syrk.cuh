@@ -1,19 +1,26 @@
-// Tensor-core (tcgen05, kind::tf32) trailing updates of the blocked Cholesky:
+// Tensor-core (tcgen05, kind::f16) trailing updates of the blocked Cholesky:
 //
 //     C[I, J] -= A_I A_J^T        (A_I, A_J: 128-row blocks of split panel columns)
 //
-// in 3xTF32 arithmetic: every fp32 operand is split as a = a_hi + a_lo with
-// a_hi = tf32(a) (round to nearest) and a_lo = a - a_hi, and the product is
-// accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi, which keeps
-// the error of the update near FP32 rounding.
+// in 3xFP16 arithmetic: every fp32 operand, scaled by a power of two s, is
+// split as s a = a_hi + a_lo with a_hi = fp16(s a) (round to nearest) and
+// a_lo = fp16(s a - a_hi), and the product is accumulated in FP32 in tensor
+// memory as hi*hi + hi*lo + lo*hi, then multiplied by 1/s^2 (exact).  FP16
+// carries the 11-bit significand of TF32 at twice its tensor rate and half its
+// bytes; the scale puts every entry of the factor in FP16's normal range: a
+// row of L has |L_rt| <= sqrt(A_rr), so s = 2^(15 - e) with 2^e >= the largest
+// sqrt(A_rr) keeps |s L| < 2^15, and only entries below 2^-29 of that bound
+// reach the subnormals (an absolute error near 2^-40 of it).  The update's
+// error stays near FP32 rounding, as with 3xTF32.
 //
 // Panel columns are split, by the panel work as it produces them, into hi and
-// lo copies laid out per K stage of 16 columns and 128-row block exactly as
+// lo copies laid out per K stage of 32 columns and 128-row block exactly as
 // the tensor core reads them from shared memory: the canonical K-major layout
-// without swizzle, 8-row x 16-byte core matrices consecutive along K (leading
-// byte offset 128 B, 4 of them for 16 columns) and then along M/N (stride
-// byte offset 512 B).  One stage of a 128-row block of one part is 8 KB of
-// contiguous bytes; a 64-column chunk of the panel is 4 stages.
+// without swizzle, 8-row x 16-byte core matrices (8 fp16 along K)
+// consecutive along K (leading byte offset 128 B, 4 of them for 32 columns)
+// and then along M/N (stride byte offset 512 B).  One stage of a 128-row block
+// of one part is 8 KB of contiguous bytes; a 64-column chunk of the panel is
+// 2 stages.
 //
 // One CTA (8 warps) owns one 128 x 128 tile and takes the K stages through a
 // ring of NBUF = 3 shared-memory buffers (96 KB, so two tile CTAs share an
@@ -24,7 +31,7 @@
 //      latency overlaps the copies and the MMAs;
 //   3. thread 0 bulk-copies (cp.async.bulk, completing on the buffer's
 //      "full" mbarrier) the first three stages, then for every stage waits
-//      for its copy, issues 2 K-steps x 3 tcgen05.mma (M = N = 128, K = 8)
+//      for its copy, issues 2 K-steps x 3 tcgen05.mma (M = N = 128, K = 16)
 //      and commits them to the buffer's "empty" mbarrier, and refills the
 //      buffer of the previous stage once its MMAs have read it; after a
 //      chunk's last stage it commits to the accumulator's mbarrier;
@@ -49,10 +56,10 @@ namespace tc {
 
 constexpr int TM = 128;       // tile rows (MMA M) and columns (MMA N)
 constexpr int TK = 64;        // width of one panel chunk (an elimination step's columns)
-constexpr int KH = 16;        // K per pipeline stage
+constexpr int KH = 32;        // K per pipeline stage (fp16 elements)
 constexpr int CHUNK_STAGES = TK / KH;                   // stages per 64-column chunk
 constexpr int NBUF = 3;                                 // stages in flight
-constexpr int STAGE_BYTES = TM * KH * 4;                // one operand part of a 128-row block, one stage
+constexpr int STAGE_BYTES = TM * KH * 2;                // one operand part of a 128-row block, one stage
 constexpr int BUF_BYTES = 4 * STAGE_BYTES;              // A_hi, A_lo, B_hi, B_lo of a stage
 constexpr int SMEM_BYTES = NBUF * BUF_BYTES + 256;      // the ring, barriers and the TMEM slot
 constexpr int TMEM_COLS = 2 * TM;                       // two accumulators (two tile CTAs fill an SM's 512)
@@ -62,15 +69,15 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row r, k) of a 128 x 16 fp32 stage operand in the
+// Byte offset of element (row r, k) of a 128 x 32 fp16 stage operand in the
 // K-major, no-swizzle core-matrix layout.
 __device__ __forceinline__ uint32_t kmajor_offset(int r, int k)
 {
-    return (uint32_t)((k >> 2) * 128 + (r >> 3) * (KH / 4) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((k >> 3) * 128 + (r >> 3) * (KH / 8) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
 // Byte offset of panel element (row rr from the split's first row, column k
-// of a chunk) in one part of the split buffer: stage k / 16, then 128-row
+// of a chunk) in one part of the split buffer: stage k / 32, then 128-row
 // block, then the stage layout.
 __device__ __forceinline__ size_t split_offset(int rr, int k, size_t stage_stride)
 {
@@ -85,32 +92,25 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(((KH / 4) * 128) >> 4) << 32;
+    d |= (uint64_t)(((KH / 8) * 128) >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D fp32 (bits 4-5 = 1), A and B tf32
-// (bits 7-9 = 2, bits 10-12 = 2), both K-major, N >> 3 in bits 17-22,
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B fp16
+// (bits 7-9 = 0, bits 10-12 = 0), both K-major, N >> 3 in bits 17-22,
 // M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t make_idesc()
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ __forceinline__ float to_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum)
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
@@ -192,11 +192,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // launch before the tile, and a CTA that holds the permit keeps the SM from
 // taking a second CTA of the kernel.  With skip00 the top-left 64 x 64
 // quadrant of the tile is neither read nor written (another CTA updates it).
-// Returns false if a wait gave up.
+// The accumulated products are multiplied by unscale = 1 / s^2.  Returns
+// false if a wait gave up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int ia, int ja, int st0,
-                          int nst, unsigned char* smem, Ready ready, bool skip00)
+                          int nst, unsigned char* smem, Ready ready, bool skip00, float unscale)
 {
     const bool diag = ia == ja;
     // barriers: [b] full, [NBUF + b] empty, [2 NBUF + a] accumulator a done
@@ -271,11 +272,11 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
             const uint32_t bh = diag ? ah : part(b, 2), bl = diag ? al : part(b, 3);
             const bool first = s == c * CHUNK_STAGES;
 #pragma unroll
-            for (int ks = 0; ks < KH / 8; ++ks) {
-                const uint32_t off = ks * 256;   // 8 tf32 = two core matrices along K
-                mma_tf32(acc, make_desc(ah + off), make_desc(bh + off), idesc, !first || ks > 0);
-                mma_tf32(acc, make_desc(ah + off), make_desc(bl + off), idesc, 1);
-                mma_tf32(acc, make_desc(al + off), make_desc(bh + off), idesc, 1);
+            for (int ks = 0; ks < KH / 16; ++ks) {
+                const uint32_t off = ks * 256;   // 16 fp16 = two core matrices along K
+                mma_f16(acc, make_desc(ah + off), make_desc(bh + off), idesc, !first || ks > 0);
+                mma_f16(acc, make_desc(ah + off), make_desc(bl + off), idesc, 1);
+                mma_f16(acc, make_desc(al + off), make_desc(bh + off), idesc, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              empty(b))
@@ -342,7 +343,7 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
                 float v[16];
                 tmem_ld16(base + (uint32_t)cc, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) cpre[cc + i] -= v[i];
+                for (int i = 0; i < 16; ++i) cpre[cc + i] = fmaf(-unscale, v[i], cpre[cc + i]);
             }
         }
         if (!got) ok = 0;
