@@ -132,6 +132,36 @@ size_t gbem_bytes_in_use(const gbem_ctx* ctx);
 gbem_status gbem_mesh(gbem_ctx* ctx, const gbem_box* boxes, int nbox,
                       const gbem_mesh_params* params, gbem_mesh_t** out);
 
+/* The paper's distance-graded partition for one main net (Sec. 3.3): every
+ * face is split by bisection of its longer edge until each panel I_j
+ * satisfies |I_j| <= p4 if its distance d to the main net is below p5 and
+ * |I_j| <= p4 * p3 * (d / p5)^3 otherwise (Sec. 3.3, from the far-field
+ * bound |dq/dtau| <= C / |x - x0|^3 of Eq. "electric_derivative"), with
+ * p4 = p1 for faces that look toward the main net and p4 = p1 * p2 for faces
+ * that look away from it.  A face looks toward the main net when some of the
+ * main net lies on the outward side of its plane; the main net's own faces
+ * and the inner faces of the enclosure always do.  d is the distance from
+ * the panel to the nearest box of the main net.  Areas in um^2, lengths in
+ * um.  h_max (0 = none) also caps every panel edge.  With has_enclosure the
+ * inner faces of the grounded box [encl_lo, encl_hi] (Sec. 3.1: the
+ * boundary of the domain, at potential 0) are meshed as conductor
+ * encl_conductor; every box must lie strictly inside it.  The mesh is meant
+ * for the column of the capacitance matrix that belongs to the main net. */
+typedef struct {
+    int32_t main_conductor;
+    double p1;
+    double p2;
+    double p3;
+    double p5;
+    double h_max;
+    int has_enclosure;
+    double encl_lo[3];
+    double encl_hi[3];
+    int32_t encl_conductor;
+} gbem_partition_params;
+gbem_status gbem_mesh_graded(gbem_ctx* ctx, const gbem_box* boxes, int nbox,
+                             const gbem_partition_params* params, gbem_mesh_t** out);
+
 /* Build a mesh from an explicit panel list, kept in the given order.
  * axis[i] in {0,1,2} is the panel's normal axis; geo[5*i..5*i+4] =
  * {c, lo0, hi0, lo1, hi1}: the plane coordinate and the extents along the two

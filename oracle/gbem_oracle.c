@@ -23,6 +23,8 @@
  *     touches I_j uses tanh-sinh (double exponential) quadrature with levels
  *     refined until two levels agree, every other piece uses adaptive tensor
  *     Gauss-Legendre (orders 8 and 16 compared, 2x2 subdivision otherwise),
+ *   - the outer quadrature runs over the panel with the smaller diagonal
+ *     (the integral is symmetric in the two panels),
  *   - pairs whose gap is at least the larger panel diagonal use a direct 4-D
  *     tensor Gauss-Legendre rule (orders 8 and 10 compared beyond three
  *     diagonals, 12 and 16 below), which avoids the cancellation of the
@@ -402,6 +404,13 @@ static double orc_pair(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
         double i16 = orc_pair_gl4(Pi, Pj, 16);
         if (fabs(i16 - i12) <= 5e-14 * fabs(i16)) return i16;
     }
+    /* The double integral is symmetric in the two panels (Eq. "matrix"; A is
+     * symmetric, Sec. 3.2), so the outer quadrature may run over either.  It
+     * runs over the one with the smaller diagonal: the exact potential of a
+     * panel that is small against its distance cancels between its corners
+     * (about eps (R/h)^2), while a large panel's potential at the points of a
+     * small one does not, and a small outer domain needs few points. */
+    if (orc_diag(Pj) < orc_diag(Pi)) return orc_pair_split(Pj, Pi, nfail);
     return orc_pair_split(Pi, Pj, nfail);
 }
 

@@ -157,6 +157,80 @@ def mesh_boxes(boxes, h: float, ratio: float = 1.0, h_min: float = 0.0):
             np.asarray(cond, dtype=np.int32))
 
 
+def mesh_graded(boxes, main, p1, p2, p3, p5, h_max=0.0, enclosure=None):
+    """The paper's distance-graded partition for the main net `main`
+    (Sec. 3.3).  A panel I on a face may stay when
+        |I| <= p4                  for d < p5,
+        |I| <= p4 p3 (d / p5)^3    for d >= p5,
+    d the distance from I to the main net's nearest box; p4 = p1 on faces
+    that look toward the main net (some of it lies beyond the face's plane on
+    the outward side; the main net's own faces and an enclosure's inner
+    faces always do), p4 = p1 p2 on faces that look away.  Larger panels are
+    halved across their longer edge (the first in-plane axis on a tie), and
+    so on.  h_max > 0 also bounds both edges.  `enclosure` = (lo, hi, cond):
+    the inner faces of a grounded box, meshed as conductor cond.  Returns
+    (axis, geo, cond) as mesh_boxes does, faces in box order, each face's
+    panels in depth-first order, first halves first."""
+    mains = [(lo, hi) for lo, hi, c in boxes if c == main]
+    if not mains:
+        raise ValueError("no box of the main net")
+    mlo = [min(b[0][d] for b in mains) for d in range(3)]
+    mhi = [max(b[1][d] for b in mains) for d in range(3)]
+
+    def dist(k, c, a0, b0, a1, b1):
+        p, q = [x for x in range(3) if x != k]
+        lo = [0.0] * 3
+        hi = [0.0] * 3
+        lo[k] = hi[k] = c
+        lo[p], hi[p], lo[q], hi[q] = a0, b0, a1, b1
+        best = math.inf
+        for blo, bhi in mains:
+            s = 0.0
+            for d in range(3):
+                g = max(0.0, max(blo[d] - hi[d], lo[d] - bhi[d]))
+                s += g * g
+            best = min(best, math.sqrt(s))
+        return best
+
+    faces = []
+    for lo, hi, c in boxes:
+        for k in range(3):
+            p, q = [x for x in range(3) if x != k]
+            for side, plane in ((0, lo[k]), (1, hi[k])):
+                toward = c == main or (mhi[k] > plane if side == 1 else mlo[k] < plane)
+                faces.append((k, plane, lo[p], hi[p], lo[q], hi[q], c, toward))
+    if enclosure is not None:
+        elo, ehi, ec = enclosure
+        for k in range(3):
+            p, q = [x for x in range(3) if x != k]
+            for plane in (elo[k], ehi[k]):
+                faces.append((k, plane, elo[p], ehi[p], elo[q], ehi[q], ec, True))
+    axis, geo, cond = [], [], []
+
+    def refine(k, plane, a0, b0, a1, b1, c, p4):
+        d = dist(k, plane, a0, b0, a1, b1)
+        limit = p4 if d < p5 else p4 * p3 * ((d / p5) * (d / p5) * (d / p5))
+        e0, e1 = b0 - a0, b1 - a1
+        if not (e0 * e1 > limit or (h_max > 0.0 and max(e0, e1) > h_max)):
+            axis.append(k)
+            geo.append((plane, a0, b0, a1, b1))
+            cond.append(c)
+            return
+        if e0 >= e1:
+            m = 0.5 * (a0 + b0)
+            refine(k, plane, a0, m, a1, b1, c, p4)
+            refine(k, plane, m, b0, a1, b1, c, p4)
+        else:
+            m = 0.5 * (a1 + b1)
+            refine(k, plane, a0, b0, a1, m, c, p4)
+            refine(k, plane, a0, b0, m, b1, c, p4)
+
+    for k, plane, a0, b0, a1, b1, c, toward in faces:
+        refine(k, plane, a0, b0, a1, b1, c, p1 if toward else p1 * p2)
+    return (np.asarray(axis, dtype=np.int32), np.asarray(geo, dtype=np.float64).reshape(-1, 5),
+            np.asarray(cond, dtype=np.int32))
+
+
 def areas(geo: np.ndarray) -> np.ndarray:
     return (geo[:, 2] - geo[:, 1]) * (geo[:, 4] - geo[:, 3])
 

@@ -514,6 +514,31 @@ gbem_status gbem_mesh(gbem_ctx* ctx, const gbem_box* boxes, int nbox, const gbem
     return GBEM_OK;
 }
 
+gbem_status gbem_mesh_graded(gbem_ctx* ctx, const gbem_box* boxes, int nbox, const gbem_partition_params* params,
+                             gbem_mesh_t** out)
+{
+    if (!ctx || !out) return GBEM_ERR_ARG;
+    *out = nullptr;
+    gbem_mesh_t* m = new (std::nothrow) gbem_mesh_t();
+    if (!m) return GBEM_ERR_OOM;
+    m->ctx = ctx;
+    std::vector<int32_t> raw;
+    gbem_status st = mesh_build_graded(boxes, nbox, params, m->axis, m->geo, raw, ctx->err);
+    if (st != GBEM_OK) {
+        delete m;
+        return st;
+    }
+    compact_conductors(m, raw);
+    mesh_order(m->axis, m->geo, m->cond);
+    m->n = (int)m->axis.size();
+    if ((st = upload_mesh(ctx, m)) != GBEM_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GBEM_OK;
+}
+
 gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis, const double* geo,
                                   const int32_t* cond, gbem_mesh_t** out)
 {

@@ -187,6 +187,9 @@ void ctx_drop_spare(gbem_ctx* ctx);
 gbem_status mesh_build_boxes(const gbem_box* boxes, int nbox, const gbem_mesh_params* p,
                              std::vector<int8_t>& axis, std::vector<double>& geo,
                              std::vector<int32_t>& cond_raw, std::string& err);
+gbem_status mesh_build_graded(const gbem_box* boxes, int nbox, const gbem_partition_params* p,
+                              std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond_raw,
+                              std::string& err);
 void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond);
 void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<double>& nodes);
 

@@ -207,3 +207,167 @@ void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector
     geo.swap(g2);
     cond.swap(c2);
 }
+
+// ---- distance-graded partition (Sec. 3.3)
+//
+// Every face is split by bisection of its longer edge until each panel I_j
+// satisfies the paper's bound for its distance d to the main net:
+//     |I_j| <= p4                      if d < p5,
+//     |I_j| <= p4 * p3 * (d / p5)^3    otherwise,
+// with p4 = p1 for a face that looks toward the main net (the main net lies
+// on the outward side of its plane; the main net's own faces and the inner
+// faces of a grounded enclosure always do) and p4 = p1 * p2 for a face that
+// looks away from it (shielded).  d is the distance between the panel and
+// the nearest box of the main net; an optional h_max caps the panel edges.
+
+namespace {
+
+struct GFace {
+    int k;         // normal axis
+    double plane;  // plane coordinate
+    double l0, h0, l1, h1;
+    int32_t cond;
+    bool toward;   // looks toward the main net
+};
+
+double rect_box_distance(int k, double c, double l0, double h0, double l1, double h1, const gbem_box& B)
+{
+    const int pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+    double lo[3], hi[3];
+    lo[k] = hi[k] = c;
+    lo[pa] = l0;
+    hi[pa] = h0;
+    lo[qa] = l1;
+    hi[qa] = h1;
+    double d2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double g = std::max(0.0, std::max(B.lo[d] - hi[d], lo[d] - B.hi[d]));
+        d2 += g * g;
+    }
+    return std::sqrt(d2);
+}
+
+}  // namespace
+
+gbem_status mesh_build_graded(const gbem_box* boxes, int nbox, const gbem_partition_params* p,
+                              std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond_raw,
+                              std::string& err)
+{
+    if (nbox <= 0 || !boxes || !p) {
+        err = "gbem_mesh_graded: no boxes";
+        return GBEM_ERR_ARG;
+    }
+    if (!(p->p1 > 0.0) || !(p->p2 >= 1.0) || !(p->p3 > 0.0) || !(p->p5 > 0.0) || !(p->h_max >= 0.0) ||
+        !std::isfinite(p->p1) || !std::isfinite(p->p2) || !std::isfinite(p->p3) || !std::isfinite(p->p5)) {
+        err = "gbem_mesh_graded: need p1 > 0, p2 >= 1, p3 > 0, p5 > 0, h_max >= 0";
+        return GBEM_ERR_ARG;
+    }
+    // the same box checks as the uniform mesher (empty, overlapping, touching)
+    {
+        gbem_mesh_params probe{1e300, 1.0, 0.0};
+        std::vector<int8_t> a;
+        std::vector<double> g;
+        std::vector<int32_t> c;
+        gbem_status st = mesh_build_boxes(boxes, nbox, &probe, a, g, c, err);
+        if (st != GBEM_OK) return st;
+    }
+    std::vector<int> mains;
+    double mlo[3] = {1e300, 1e300, 1e300}, mhi[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < nbox; ++b)
+        if (boxes[b].conductor == p->main_conductor) {
+            mains.push_back(b);
+            for (int d = 0; d < 3; ++d) {
+                mlo[d] = std::min(mlo[d], boxes[b].lo[d]);
+                mhi[d] = std::max(mhi[d], boxes[b].hi[d]);
+            }
+        }
+    if (mains.empty()) {
+        err = "gbem_mesh_graded: no box of the main conductor";
+        return GBEM_ERR_ARG;
+    }
+    std::vector<GFace> faces;
+    for (int b = 0; b < nbox; ++b) {
+        const gbem_box& B = boxes[b];
+        const bool is_main = B.conductor == p->main_conductor;
+        for (int k = 0; k < 3; ++k) {
+            const int pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+            for (int side = 0; side < 2; ++side) {
+                const double c = side ? B.hi[k] : B.lo[k];
+                // outward normal +e_k (side 1) or -e_k (side 0)
+                const bool toward = is_main || (side ? mhi[k] > c : mlo[k] < c);
+                faces.push_back(GFace{k, c, B.lo[pa], B.hi[pa], B.lo[qa], B.hi[qa], B.conductor, toward});
+            }
+        }
+    }
+    if (p->has_enclosure) {
+        const double* lo = p->encl_lo;
+        const double* hi = p->encl_hi;
+        for (int d = 0; d < 3; ++d)
+            if (!(hi[d] > lo[d])) {
+                err = "gbem_mesh_graded: empty enclosure";
+                return GBEM_ERR_MESH;
+            }
+        for (int b = 0; b < nbox; ++b)
+            for (int d = 0; d < 3; ++d)
+                if (!(boxes[b].lo[d] > lo[d] && boxes[b].hi[d] < hi[d])) {
+                    err = "gbem_mesh_graded: box " + std::to_string(b) + " is not strictly inside the enclosure";
+                    return GBEM_ERR_MESH;
+                }
+        for (int k = 0; k < 3; ++k) {
+            const int pa = (k == 0) ? 1 : 0, qa = (k == 2) ? 1 : 2;
+            for (int side = 0; side < 2; ++side)
+                faces.push_back(GFace{k, side ? hi[k] : lo[k], lo[pa], hi[pa], lo[qa], hi[qa], p->encl_conductor, true});
+        }
+    }
+    axis.clear();
+    geo.clear();
+    cond_raw.clear();
+    struct Piece {
+        double l0, h0, l1, h1;
+    };
+    std::vector<Piece> stack;
+    for (const GFace& F : faces) {
+        const double p4 = F.toward ? p->p1 : p->p1 * p->p2;
+        stack.clear();
+        stack.push_back(Piece{F.l0, F.h0, F.l1, F.h1});
+        while (!stack.empty()) {
+            const Piece r = stack.back();
+            stack.pop_back();
+            double d = 1e300;
+            for (int b : mains) d = std::min(d, rect_box_distance(F.k, F.plane, r.l0, r.h0, r.l1, r.h1, boxes[b]));
+            double limit = p4;
+            if (d >= p->p5) {
+                const double t = d / p->p5;
+                limit = p4 * p->p3 * (t * t * t);
+            }
+            const double e0 = r.h0 - r.l0, e1 = r.h1 - r.l1;
+            const bool too_big = e0 * e1 > limit || (p->h_max > 0.0 && std::max(e0, e1) > p->h_max);
+            if (!too_big) {
+                axis.push_back((int8_t)F.k);
+                geo.push_back(F.plane);
+                geo.push_back(r.l0);
+                geo.push_back(r.h0);
+                geo.push_back(r.l1);
+                geo.push_back(r.h1);
+                cond_raw.push_back(F.cond);
+                if (axis.size() > 2000000) {
+                    err = "gbem_mesh_graded: more than 2e6 panels requested";
+                    return GBEM_ERR_ARG;
+                }
+                continue;
+            }
+            // bisect the longer edge (the first on a tie); the second half is
+            // pushed first so that the first half is refined first
+            if (e0 >= e1) {
+                const double m = 0.5 * (r.l0 + r.h0);
+                stack.push_back(Piece{m, r.h0, r.l1, r.h1});
+                stack.push_back(Piece{r.l0, m, r.l1, r.h1});
+            } else {
+                const double m = 0.5 * (r.l1 + r.h1);
+                stack.push_back(Piece{r.l0, r.h0, m, r.h1});
+                stack.push_back(Piece{r.l0, r.h0, r.l1, m});
+            }
+        }
+    }
+    return GBEM_OK;
+}

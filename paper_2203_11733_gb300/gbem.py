@@ -52,6 +52,13 @@ class _Tuning(ctypes.Structure):
                 ("ir_tol", ctypes.c_double), ("ir_max_iter", ctypes.c_int), ("nb", ctypes.c_int)]
 
 
+class _PartitionParams(ctypes.Structure):
+    _fields_ = [("main_conductor", ctypes.c_int32), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
+                ("p3", ctypes.c_double), ("p5", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("has_enclosure", ctypes.c_int), ("encl_lo", ctypes.c_double * 3),
+                ("encl_hi", ctypes.c_double * 3), ("encl_conductor", ctypes.c_int32)]
+
+
 class ResultInfo(ctypes.Structure):
     _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("n_panels", ctypes.c_int),
                 ("n_cond", ctypes.c_int), ("residual", ctypes.c_double), ("submit_s", ctypes.c_double),
@@ -85,6 +92,8 @@ _SIGS = {
     "gbem_bytes_in_use": (ctypes.c_size_t, [_P]),
     "gbem_mesh": (ctypes.c_int, [_P, ctypes.POINTER(_Box), ctypes.c_int, ctypes.POINTER(_MeshParams),
                                  ctypes.POINTER(_P)]),
+    "gbem_mesh_graded": (ctypes.c_int, [_P, ctypes.POINTER(_Box), ctypes.c_int, ctypes.POINTER(_PartitionParams),
+                                        ctypes.POINTER(_P)]),
     "gbem_mesh_from_panels": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(_P)]),
     "gbem_mesh_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gbem_mesh_panels": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -523,6 +532,25 @@ def gbem_mesh(ctx: Context, boxes, params) -> Mesh:
     p = _MeshParams(float(params["h"]), float(params.get("ratio", 1.0)), float(params.get("h_min", 0.0)))
     h = ctypes.c_void_p()
     ctx.check(ctx.lib.gbem_mesh(ctx.h, arr, len(boxes), ctypes.byref(p), ctypes.byref(h)))
+    return Mesh(ctx, h)
+
+
+def gbem_mesh_graded(ctx: Context, boxes, main: int, p1: float, p2: float, p3: float, p5: float,
+                     h_max: float = 0.0, enclosure=None) -> Mesh:
+    """gbem_mesh_graded: the paper's distance-graded partition for main net
+    `main`; enclosure = (lo, hi, conductor id) of a grounded box, or None."""
+    arr = _boxes(boxes)
+    p = _PartitionParams()
+    p.main_conductor = int(main)
+    p.p1, p.p2, p.p3, p.p5, p.h_max = float(p1), float(p2), float(p3), float(p5), float(h_max)
+    if enclosure is not None:
+        lo, hi, c = enclosure
+        p.has_enclosure = 1
+        p.encl_lo[:] = [float(v) for v in lo]
+        p.encl_hi[:] = [float(v) for v in hi]
+        p.encl_conductor = int(c)
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.gbem_mesh_graded(ctx.h, arr, len(boxes), ctypes.byref(p), ctypes.byref(h)))
     return Mesh(ctx, h)
 
 
