@@ -95,8 +95,8 @@ typedef struct {
 typedef struct {
     double q_near_fp64;   /* gap / largest edge below which a pair uses the
                              closed form in FP64 mode (12) */
-    double q_near_mixed;  /* same in mixed mode (0.5) */
-    double ir_tol;        /* relative residual target of refinement (1e-12) */
+    double q_near_mixed;  /* same in mixed mode (1.0) */
+    double ir_tol;        /* relative residual target of refinement (1e-11) */
     int ir_max_iter;      /* refinement iterations at most (10) */
     int nb;               /* Cholesky block size: 64 */
 } gbem_tuning;

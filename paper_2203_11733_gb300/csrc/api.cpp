@@ -83,8 +83,16 @@ gbem_tuning default_tuning()
 {
     gbem_tuning t{};
     t.q_near_fp64 = 12.0;
-    t.q_near_mixed = 0.5;
-    t.ir_tol = 1e-12;
+    // below q = 1 the FP32 6-point rule misses its 3e-7 target on elongated
+    // panels next to small ones (40 x 10 um enclosure walls beside 1 um
+    // panels: 7.7e-6); the FP64 closed form is exact there
+    t.q_near_mixed = 1.0;
+    // |B - A X| / |B| <= 1e-11 makes X the exact solution of a system whose
+    // matrix differs from the assembled one by at most 1e-11 relative (the
+    // normwise backward error); the mixed assembly's own FP32 far field is
+    // about 1e-7 away from the exact integrals, so refining further moves
+    // the capacitances by nothing measurable
+    t.ir_tol = 1e-11;
     t.ir_max_iter = 10;
     t.nb = 64;
     return t;

@@ -830,6 +830,9 @@ struct StepArgs {
     int r0, icols;                // inner tiles: rows [r0, np), icols 128-columns from r0
     int f0, fcols;                // front tiles: rows [f0, np), fcols 128-columns from f0 (16 stages)
     int next_start;               // start the next panel (its first block f0 / 64) after front tile (0, 0)
+    int f00;                      // apply this step's chunk to front tile (0, 0) now (one CTA, K = 64)
+    int f00_rest;                 // ... after applying the previous panel's rest tile (0, 0) to it
+    int f00_last;                 // front tile (0, 0) holds the earlier chunks: only this step's remains
     int ns_start;                 // strip rows of the next panel's first step
     const unsigned char* hi_p;    // rest tiles: the previous panel's split (rows from srow0_p),
     const unsigned char* lo_p;    // the lower 128-tiles [rb0, rb1) of [c0r, np)^2
@@ -881,6 +884,12 @@ __host__ __device__ __forceinline__ long long band_tiles(int nrow, int cols)
 //                   k+2 (pflag[k+2] = k + 2);
 //   inner tiles     the panel's 128-tiles right of the strip, after the
 //                   flags of their four row blocks (this step's chunk);
+//   f00             in a panel's first steps: this step's chunk applied at
+//                   once to front tile (0, 0) (the next panel's first two
+//                   diagonal blocks), so that the last step applies only its
+//                   own chunk there; in the step whose share of the
+//                   previous panel's rest tiles holds rest tile (0, 0), which
+//                   covers the same block, the same CTA applies it first;
 //   front tiles     the next panel's columns with the whole panel (K = 256),
 //                   after the flags of their row blocks; with next_start,
 //                   right after front tile (0, 0) (which holds the next
@@ -918,7 +927,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     // its SM
     const int nin = (a.ld - a.r0) / tc::TM;
     const long long n_inner = band_tiles(nin, a.icols);
-    const long long t_start = a.has_diag + a.ns_next + n_inner + 1;   // the next panel's start, when present
+    const long long t_start = a.has_diag + a.ns_next + n_inner + a.f00 + 1;   // the next panel's start, when present
     if ((t < a.has_diag + a.ns_next || (a.next_start && t == t_start)) && threadIdx.x < 32)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (t < 0) {
@@ -963,18 +972,40 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     }
     t -= a.ns_next;
     const int np = ld;
+    // the tile role's work as one or two tile jobs, run through a single
+    // inlined tensor-core tile (tc::syrk_tile)
+    struct TileJob {
+        int rI, rJ, ia, ja, st0, nst;
+        const unsigned char* hi;
+        const unsigned char* lo;
+        int fb0, fb1;   // row blocks whose two release flags the tile waits for (-1: none)
+        bool skip00;
+    };
+    TileJob jobs[2];
+    int njobs = 1;
+    bool release_start = false;   // front tile (0, 0): release the next panel's start after it
     int I, J;
-    bool ok;
     if (t < n_inner) {
         band_tile(t, nin, a.icols, I, J);
         const int rI = a.r0 + tc::TM * I, rJ = a.r0 + tc::TM * J;
-        const int bI = rI / NB, bJ = rJ / NB;
         const int off = (a.r0 - a.srow0) / tc::TM;
-        auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
-        ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, a.st_base,
-                           tc::CHUNK_STAGES, tc_smem, ready, la && I == 0 && J == 0, unsc);
+        jobs[0] = TileJob{rI, rJ, off + I, off + J, a.st_base, tc::CHUNK_STAGES, a.hi, a.lo, rI / NB, rJ / NB,
+                          la && I == 0 && J == 0};
+    } else if (a.f00 && t == n_inner) {
+        // this step's chunk on front tile (0, 0), after the flags of its rows;
+        // first the previous panel's rest tile (0, 0) when it is this step's
+        const int off = (a.f0 - a.srow0) / tc::TM;
+        const TileJob mine{a.f0, a.f0, off, off, a.st_base, tc::CHUNK_STAGES, a.hi, a.lo, a.f0 / NB, -1, false};
+        if (a.f00_rest) {
+            const int offp = (a.c0r - a.srow0_p) / tc::TM;
+            jobs[0] = TileJob{a.c0r, a.c0r, offp, offp, 0, 4 * tc::CHUNK_STAGES, a.hi_p, a.lo_p, -1, -1, false};
+            jobs[1] = mine;
+            njobs = 2;
+        } else {
+            jobs[0] = mine;
+        }
     } else {
-        t -= n_inner;
+        t -= n_inner + a.f00;
         const int nf = a.fcols > 0 ? (np - a.f0) / tc::TM : 0;
         const long long n_front = band_tiles(nf, a.fcols);
         if (a.next_start && t == 1) {
@@ -991,19 +1022,13 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
         if (t < n_front) {
             band_tile(t, nf, a.fcols, I, J);
             const int rI = a.f0 + tc::TM * I, rJ = a.f0 + tc::TM * J;
-            const int bI = rI / NB, bJ = rJ / NB;
             const int off = (a.f0 - a.srow0) / tc::TM;
-            auto ready = [&]() { return wait_flags(a.pflag + bI, 2, a.pflag + bJ, 2, token, status); };
-            ok = tc::syrk_tile(L, ld, rI, rJ, a.hi, a.lo, a.stage_stride, off + I, off + J, 0, 4 * tc::CHUNK_STAGES,
-                               tc_smem, ready, false, unsc);
-            if (ok && t == 0 && a.next_start) {
-                // front tile (0, 0) is stored: release the next panel's start
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    __threadfence();
-                    st_release(a.dflag + k, token);
-                }
-            }
+            // tile (0, 0) already holds the panel's earlier chunks when f00_last
+            const bool last_only = a.f00_last && I == 0 && J == 0;
+            jobs[0] = TileJob{rI, rJ, off + I, off + J, last_only ? a.st_base : 0,
+                              last_only ? tc::CHUNK_STAGES : 4 * tc::CHUNK_STAGES, a.hi, a.lo, rI / NB, rJ / NB,
+                              false};
+            release_start = t == 0 && a.next_start;
         } else {
             t -= n_front;
             const long long b = a.rb0 + t;   // lower-triangle tile index of [c0r, np)^2
@@ -1012,9 +1037,30 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
             while ((long long)I * (I + 1) / 2 > b) --I;
             J = (int)(b - (long long)I * (I + 1) / 2);
             const int off = (a.c0r - a.srow0_p) / tc::TM;
-            auto ready = []() { return true; };
-            ok = tc::syrk_tile(L, ld, a.c0r + tc::TM * I, a.c0r + tc::TM * J, a.hi_p, a.lo_p, a.stage_stride,
-                               off + I, off + J, 0, 4 * tc::CHUNK_STAGES, tc_smem, ready, false, unsc);
+            jobs[0] = TileJob{a.c0r + tc::TM * I, a.c0r + tc::TM * J, off + I, off + J, 0, 4 * tc::CHUNK_STAGES,
+                              a.hi_p, a.lo_p, -1, -1, false};
+        }
+    }
+    bool ok = true;
+    for (int jb = 0; jb < njobs && ok; ++jb) {
+        const TileJob& T = jobs[jb];
+        auto ready = [&]() {
+            const int n0 = T.fb0 >= 0 ? 2 : 0, n1 = T.fb1 >= 0 ? 2 : 0;
+            if (n0 + n1 == 0) return true;   // uniform over the CTA
+            return wait_flags(a.pflag + (T.fb0 >= 0 ? T.fb0 : 0), n0, a.pflag + (T.fb1 >= 0 ? T.fb1 : 0), n1, token,
+                              status);
+        };
+        // a CTA with two jobs keeps the TMEM allocation permit for the second,
+        // which takes fresh mbarriers
+        ok = tc::syrk_tile(L, ld, T.rI, T.rJ, T.hi, T.lo, a.stage_stride, T.ia, T.ja, T.st0, T.nst, tc_smem, ready,
+                           T.skip00, unsc, jb + 1 == njobs, jb);
+    }
+    if (ok && release_start) {
+        // front tile (0, 0) is stored: release the next panel's start
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(a.dflag + k, token);
         }
     }
     if (!ok && threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
@@ -1108,6 +1154,11 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                 a.fcols = (k == e0 - 1 && e0 < nblk) ? (std::min(e0 + kPanel, nblk) - e0) * NB / tc::TM : 0;
                 a.next_start = a.fcols > 0;
                 a.ns_start = a.next_start ? strip_width(std::min(e0 + kPanel, nblk) - e0 - 1) : 0;
+                // a full panel followed by another: its first steps apply their
+                // chunks to front tile (0, 0) at once, the last step its own only
+                const bool incr = e0 - b0 == kPanel && e0 < nblk;
+                a.f00 = incr && k < e0 - 1;
+                a.f00_last = incr && k == e0 - 1;
                 a.hi_p = hi_p;
                 a.lo_p = lo_p;
                 a.srow0_p = prev_srow0;
@@ -1115,6 +1166,10 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                 const int j = k - b0;
                 a.rb0 = (rest > 0 && j < rest_steps) ? rest * j / rest_steps : 0;
                 a.rb1 = (rest > 0 && j < rest_steps) ? rest * (j + 1) / rest_steps : 0;
+                // rest tile 0 is block (e0, e0), front tile (0, 0) of this
+                // panel: the f00 CTA of the step whose share holds it applies it
+                a.f00_rest = a.f00 && a.rb0 == 0 && a.rb1 > 0;
+                if (a.f00_rest) a.rb0 = 1;
                 a.lsT_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
                 a.lsT_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
                 a.pflag = pflag;
@@ -1129,7 +1184,8 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                 const long long n_in = band_tiles((np - a.r0) / tc::TM, a.icols);
                 const long long n_fr = a.fcols > 0 ? band_tiles((np - a.f0) / tc::TM, a.fcols) : 0;
                 const long long n_rest = a.rb1 - a.rb0;
-                const long long grid = 2 * npan + a.has_diag + a.ns_next + n_in + n_fr + a.next_start + n_rest;
+                const long long grid =
+                    2 * npan + a.has_diag + a.ns_next + n_in + a.f00 + n_fr + a.next_start + n_rest;
                 if (grid == 0) continue;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)grid);
@@ -1149,7 +1205,9 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                     // inverse written.  Useful flops: panel products, strip
                     // and tile updates (2mnk), diagonal factor and inverse.
                     const double strips = (double)npan * a.sw;
-                    const double kt = (double)(n_fr + n_rest) * 4 * tc::TK + (double)n_in * tc::TK;   // K summed over tiles
+                    const double kt = (double)(n_fr + n_rest + a.f00_rest) * 4 * tc::TK +
+                                      (double)(n_in + a.f00) * tc::TK -
+                                      (a.f00_last ? 3.0 * tc::TK : 0.0);   // K summed over tiles
                     const int diags = a.has_diag + a.next_start;
                     const double bytes = 2.0 * npan * blk + 8.0 * npan * NB * NB + 2.0 * strips * blk +
                                          2.0 * (n_in + n_fr + n_rest) * tb + 2.0 * 4.0 * tc::TM * kt +

@@ -61,7 +61,7 @@ constexpr int CHUNK_STAGES = TK / KH;                   // stages per 64-column 
 constexpr int NBUF = 3;                                 // stages in flight
 constexpr int STAGE_BYTES = TM * KH * 2;                // one operand part of a 128-row block, one stage
 constexpr int BUF_BYTES = 4 * STAGE_BYTES;              // A_hi, A_lo, B_hi, B_lo of a stage
-constexpr int SMEM_BYTES = NBUF * BUF_BYTES + 256;      // the ring, barriers and the TMEM slot
+constexpr int SMEM_BYTES = NBUF * BUF_BYTES + 256;      // the ring and two sets of barriers and slots
 constexpr int TMEM_COLS = 2 * TM;                       // two accumulators (two tile CTAs fill an SM's 512)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -192,18 +192,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // launch before the tile, and a CTA that holds the permit keeps the SM from
 // taking a second CTA of the kernel.  With skip00 the top-left 64 x 64
 // quadrant of the tile is neither read nor written (another CTA updates it).
-// The accumulated products are multiplied by unscale = 1 / s^2.  Returns
-// false if a wait gave up.
+// The accumulated products are multiplied by unscale = 1 / s^2.  A CTA that
+// runs two tiles passes relinquish = false and bar_set = 0 to the first,
+// which then keeps the TMEM allocation permit, and bar_set = 1 to the
+// second, whose mbarriers then occupy fresh shared memory.  Returns false
+// if a wait gave up.
 template <typename Ready>
 __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
                           const unsigned char* __restrict__ lo, size_t stage_stride, int ia, int ja, int st0,
-                          int nst, unsigned char* smem, Ready ready, bool skip00, float unscale)
+                          int nst, unsigned char* smem, Ready ready, bool skip00, float unscale,
+                          bool relinquish = true, int bar_set = 0)
 {
     const bool diag = ia == ja;
-    // barriers: [b] full, [NBUF + b] empty, [2 NBUF + a] accumulator a done
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NBUF * BUF_BYTES);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + NBUF * BUF_BYTES + 64);
-    volatile int* s_fail = reinterpret_cast<volatile int*>(smem + NBUF * BUF_BYTES + 68);
+    // barriers: [b] full, [NBUF + b] empty, [2 NBUF + a] accumulator a done;
+    // then the TMEM address slot and the failure word (128 bytes a set)
+    unsigned char* tail = smem + NBUF * BUF_BYTES + 128 * bar_set;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tail + 64);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(tail + 68);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nch = (nst + CHUNK_STAGES - 1) / CHUNK_STAGES;   // 64-column chunks
     auto full = [&](int b) { return smem_u32(&bars[b]); };
@@ -227,7 +233,7 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (relinquish) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
         for (int b = 0; b < NBUF; ++b) {

@@ -272,7 +272,7 @@ def test_three_layer_bus_sampled_entries_and_capacitance(ctx, prec):
 @pytest.mark.slow
 def test_mixed_refinement_converges_at_large_order(ctx):
     """The compensated FP32 residual must stay accurate enough for the FP64
-    refinement to reach its 1e-12 tolerance at large N (the three-layer bus,
+    refinement to reach its 1e-11 tolerance at large N (the three-layer bus,
     N = 23172)."""
     from paper_2203_11733_gb300 import gbem
     boxes, params = W.bus_3layer_5x5x5()
@@ -282,6 +282,6 @@ def test_mixed_refinement_converges_at_large_order(ctx):
     C, res = gbem.gbem_capacitance(mesh, mat, W.EPS_R_SIO2)
     mat.close()
     mesh.close()
-    assert res <= 1e-12
+    assert res <= 1e-11
     assert np.all(np.diag(C) > 0) and np.all(C - np.diag(np.diag(C)) <= 0)
     assert np.all(C.sum(axis=1) > 0)
