@@ -354,8 +354,10 @@ PHASES = ["mesh_upload", "assemble", "factor", "solve", "reduce"]
 
 KERNEL_NAMES = {
     "assemble": "assemble_tiles<mixed>: Galerkin entries, one CTA per 32x32 lower tile",
-    "factor": "factor_step: one launch per elimination step (panel rows, strip update, next diagonal "
-              "block factor+inverse, tcgen05 3xFP16 trailing tiles, K = 256 per panel of four steps)",
+    "factor": "the FP32 factorisation, one span: factor_step (one launch per elimination step: panel "
+              "rows, strip update, next diagonal block factor+inverse, tcgen05 3xFP16 tiles of the panel's "
+              "columns) beside rest_update (second stream: warp-specialised tcgen05 3xFP16 tiles of the "
+              "trailing matrix beyond the panel, K = 256 per panel of four steps)",
     "sweep": "sweep_fwd_f32/sweep_bwd_f32: persistent cooperative triangular sweeps (x_b = z_b - M_b x_p)",
     "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
 }

@@ -287,8 +287,10 @@ gbem_status gbem_get_stats(gbem_ctx* ctx, gbem_stats* out, int reset);
  * launch, so time the workload itself with level 1 or 0. */
 enum {
     GBEM_KERNEL_ASSEMBLE = 0,  /* one CTA per 32 x 32 tile: Galerkin entries */
-    GBEM_KERNEL_FACTOR = 1,    /* FP32 factor, one launch per elimination step: panel,
-                                  strip update, next diagonal block, tensor-core tiles */
+    GBEM_KERNEL_FACTOR = 1,    /* FP32 factor, timed as one span per factorisation: its
+                                  launches per elimination step (panel, strip update,
+                                  next diagonal block, tensor-core tiles) overlap the
+                                  rest updates on a second stream */
     GBEM_KERNEL_SWEEP = 2,     /* persistent forward/backward triangular sweeps */
     GBEM_KERNEL_RESIDUAL = 3,  /* residual R = B - A X (FP64, or compensated FP32 in mixed mode) */
     GBEM_NKERNEL = 4

@@ -405,6 +405,14 @@ void gbem_destroy(gbem_ctx* ctx)
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
+    if (!ctx->side_pool.empty()) {
+        DeviceGuard g(ctx->device);
+        for (auto& sd : ctx->side_pool) {
+            cudaEventDestroy(sd.ready);
+            cudaEventDestroy(sd.done);
+            cudaStreamDestroy(sd.stream);
+        }
+    }
     delete ctx;
 }
 
@@ -682,10 +690,37 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
         if (!m->Linv) m->Linv = mat_alloc<float>(m, nblk * m->nb * m->nb, s);
         if (!m->split) m->split = mat_alloc<unsigned char>(m, cholesky_f32_split_bytes(m->np), s);
         if (!m->Linv || !m->split) return GBEM_ERR_OOM;
+        if (!m->side.stream && !ctx->side_pool.empty()) {
+            m->side = ctx->side_pool.back();
+            ctx->side_pool.pop_back();
+        }
+        if (!m->side.stream) {
+            // the stream of the rest updates, at the lowest priority (the
+            // factorisation's own launches take the highest); without it they
+            // run on the caller's stream
+            int least = 0, greatest = 0;
+            SideStream sd;
+            if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&sd.stream, cudaStreamNonBlocking, least) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sd.ready, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sd.done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                if (sd.done) cudaEventDestroy(sd.done);
+                if (sd.ready) cudaEventDestroy(sd.ready);
+                if (sd.stream) cudaStreamDestroy(sd.stream);
+                sd = SideStream{};
+            }
+            m->side = sd;
+        }
         if (!cuda_ok(ctx,
-                     launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, m->split, s),
-                     "cholesky"))
+                     launch_cholesky_f32(m->A32, m->np, m->nb, static_cast<float*>(m->Linv), m->dflags, m->split, s,
+                                         &m->side),
+                     "cholesky")) {
+            // a launch failed after the rest updates were forked: let them
+            // finish before the caller may free what they use
+            if (m->side.stream) cudaStreamSynchronize(m->side.stream);
             return GBEM_ERR_CUDA;
+        }
     }
     m->factored = true;
     m->last = s;
@@ -867,6 +902,10 @@ void gbem_matrix_destroy(gbem_matrix_t* m)
     DeviceGuard g(m->ctx->device);
     if (m->used) cudaStreamSynchronize(m->last);
     gbem_ctx* ctx = m->ctx;
+    if (m->side.stream) {
+        cudaStreamSynchronize(m->side.stream);
+        ctx->side_pool.push_back(m->side);   // idle: kept for the next matrix
+    }
     // the previous matrix's buffers that this one did not take go now; this
     // one's wait for the next matrix if they are known to be idle (a matrix
     // that never finished its assembly call has no synchronised stream)

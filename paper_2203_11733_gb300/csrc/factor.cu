@@ -693,110 +693,121 @@ __global__ void __launch_bounds__(256) syrk_update(T* __restrict__ L, int ld, in
     syrk_body<T>(L, ld, k0, blockIdx.x);
 }
 
-// Panel work of half h (rows 32 h .. 32 h + 31) of row block i at step k
-// (one CTA; the two halves of a row block run in two CTAs):
-//   1. L_ik = A_ik Linv_kk^T for those rows, written in place (Linv_kk is
-//      lower triangular, so the sum over t stops at the output column);
-//   2. row blocks at or below srow0 write the FP16 hi/lo split of those rows,
+// Panel work of the row blocks i = i0, i0 + di, ... < iend at step k (one
+// CTA; Linv_kk and the strip blocks L_ck are loaded once for all of them):
+//   1. L_ik = A_ik Linv_kk^T, written in place (Linv_kk is lower triangular,
+//      so the sum over t stops at the output column);
+//   2. row blocks at or below srow0 write the FP16 hi/lo split of the block,
 //      scaled by split_scale, in the tensor-core operand layout, as the 2
 //      stages st_base .. of the panel's split;
-//   3. A_ic -= L_ik L_ck^T on those rows for the sw strip blocks
-//      c = k+1 .. k+sw, c <= i, with L_ck (lsT, t-major) computed by the
-//      helpers of the previous step.
-// A thread owns 2 rows x 4 columns.  The strip targets are read first, so
-// their latency overlaps the product.
-__device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int srow0,
+//   3. A_ic -= L_ik L_ck^T for the sw strip blocks c = k+1 .. k+sw, c <= i,
+//      with L_ck (lsT, t-major) computed by the helpers of the previous step;
+//   4. the block's panel flag is released (token), so that the diagonal
+//      block, the helpers and the tiles of its rows can go on.
+// A thread owns 4 rows x 4 columns of a block.  The strip targets of a block
+// are read before its product, so their latency overlaps it.
+__device__ void panel_rows(float* __restrict__ L, int ld, int k, const float* __restrict__ Linv, int sw, int srow0,
                            int st_base, size_t stage_stride, unsigned char* __restrict__ hi,
-                           unsigned char* __restrict__ lo, const float* __restrict__ lsT, int i, int h,
-                           unsigned char* smem, float split_scale)
+                           unsigned char* __restrict__ lo, const float* __restrict__ lsT, int i0, int di, int iend,
+                           unsigned char* smem, float split_scale, unsigned* pflag, unsigned token)
 {
-    constexpr int HR = NB / 2;   // rows of a half
     // Blocks are stored t-major (rows padded to 68 floats) so that a
-    // thread's rows or columns at one t are one 8- or 16-byte load.
+    // thread's rows or columns at one t are one 16-byte load.
     float(*ivT)[PT] = reinterpret_cast<float(*)[PT]>(smem);   // ivT[t][c] = Linv_kk[c][t]
-    float(*aT)[PT] = ivT + NB;                                // aT[t][r] = A_ik, then L_ik (r < 32)
+    float(*aT)[PT] = ivT + NB;                                // aT[t][r] = A_ik, then L_ik
     float(*lcT)[PT] = aT + NB;                                // lcT[s * 64 + t][c] = L_ck[c][t]
     const int tid = threadIdx.x;
-    const int tr = (tid & 15) * 2, tc = (tid >> 4) * 4;
-    const int k0 = k * NB, rI = i * NB, rh = rI + HR * h;
-    const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
-    float2 tgt[2][4];
-#pragma unroll
-    for (int sidx = 0; sidx < 2; ++sidx)
-        if (sidx < nstrip)
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-                tgt[sidx][v] = *reinterpret_cast<const float2*>(L + (size_t)(rh + tr) +
-                                                                (size_t)((k + 1 + sidx) * NB + tc + v) * ld);
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+    const int k0 = k * NB;
     const float* Lb = Linv + (size_t)k * NB * NB;
     for (int e = tid; e < NB * NB / 4; e += blockDim.x)   // Linv_kk column-major: 4e = c + 64 t
         *reinterpret_cast<float4*>(&ivT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(Lb)[e];
-    for (int e = tid; e < NB * HR / 4; e += blockDim.x) {
-        const int t = e >> 3, r = (e & 7) * 4;
-        *reinterpret_cast<float4*>(&aT[t][r]) =
-            *reinterpret_cast<const float4*>(L + (size_t)(rh + r) + (size_t)(k0 + t) * ld);
-    }
-    for (int e = tid; e < nstrip * NB * NB / 4; e += blockDim.x)
+    for (int e = tid; e < sw * NB * NB / 4; e += blockDim.x)
         *reinterpret_cast<float4*>(&lcT[e >> 4][(e & 15) * 4]) = reinterpret_cast<const float4*>(lsT)[e];
-    __syncthreads();
-    float acc[2][4] = {};
-    for (int t = 0; t < tc + 4; ++t) {
-        const float2 x = *reinterpret_cast<const float2*>(&aT[t][tr]);
-        const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
-        const float xs[2] = {x.x, x.y}, ys[4] = {y.x, y.y, y.z, y.w};
+    for (int i = i0; i < iend; i += di) {
+        const int rI = i * NB;
+        const int nstrip = min(sw, i - k);   // strip blocks c = k+1 .. with c <= i
+        float4 tgt[2][4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int sidx = 0; sidx < 2; ++sidx)
+            if (sidx < nstrip)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
-    }
-    __syncthreads();   // every thread is done reading A_ik
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const float2 q = make_float2(acc[0][v], acc[1][v]);
-        *reinterpret_cast<float2*>(&aT[tc + v][tr]) = q;
-        *reinterpret_cast<float2*>(L + (size_t)(rh + tr) + (size_t)(k0 + tc + v) * ld) = q;
-    }
-    if (rI >= srow0) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int rr = rh - srow0 + tr + u;
-            const size_t off = tc::split_offset(rr, tc, stage_stride) + (size_t)st_base * stage_stride;
-            __half hv[4], lv[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float x = acc[u][v] * split_scale;   // exact: a power of two
-                hv[v] = __float2half_rn(x);
-                lv[v] = __float2half_rn(x - __half2float(hv[v]));
-            }
-            *reinterpret_cast<uint2*>(hi + off) = make_uint2(
-                (uint32_t)__half_as_ushort(hv[0]) | ((uint32_t)__half_as_ushort(hv[1]) << 16),
-                (uint32_t)__half_as_ushort(hv[2]) | ((uint32_t)__half_as_ushort(hv[3]) << 16));
-            *reinterpret_cast<uint2*>(lo + off) = make_uint2(
-                (uint32_t)__half_as_ushort(lv[0]) | ((uint32_t)__half_as_ushort(lv[1]) << 16),
-                (uint32_t)__half_as_ushort(lv[2]) | ((uint32_t)__half_as_ushort(lv[3]) << 16));
+                for (int v = 0; v < 4; ++v)
+                    tgt[sidx][v] =
+                        *reinterpret_cast<const float4*>(L + (size_t)(rI + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld);
+        for (int e = tid; e < NB * NB / 4; e += blockDim.x) {
+            const int t = e >> 4, r = (e & 15) * 4;
+            *reinterpret_cast<float4*>(&aT[t][r]) =
+                *reinterpret_cast<const float4*>(L + (size_t)(rI + r) + (size_t)(k0 + t) * ld);
         }
-    }
-    __syncthreads();   // aT holds L_ik
+        __syncthreads();   // Linv, the strip blocks and A_ik are in shared memory
+        float acc[4][4] = {};
+        for (int t = 0; t < tc + 4; ++t) {
+            const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+            const float4 y = *reinterpret_cast<const float4*>(&ivT[t][tc]);
+            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-    for (int sidx = 0; sidx < 2; ++sidx) {
-        if (sidx >= nstrip) break;
-        const float(*bT)[PT] = lcT + sidx * NB;
-        float acc2[2][4] = {};
-        for (int t = 0; t < NB; ++t) {
-            const float2 x = *reinterpret_cast<const float2*>(&aT[t][tr]);
-            const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
-            const float xs[2] = {x.x, x.y}, ys[4] = {y.x, y.y, y.z, y.w};
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
+                for (int v = 0; v < 4; ++v) acc[u][v] += xs[u] * ys[v];
         }
+        __syncthreads();   // every thread is done reading A_ik
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            float2 o = tgt[sidx][v];
-            o.x -= acc2[0][v];
-            o.y -= acc2[1][v];
-            *reinterpret_cast<float2*>(L + (size_t)(rh + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld) = o;
+            const float4 q = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+            *reinterpret_cast<float4*>(&aT[tc + v][tr]) = q;
+            *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)(k0 + tc + v) * ld) = q;
+        }
+        if (rI >= srow0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int rr = rI - srow0 + tr + u;
+                const size_t off = tc::split_offset(rr, tc, stage_stride) + (size_t)st_base * stage_stride;
+                __half hv[4], lv[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float x = acc[u][v] * split_scale;   // exact: a power of two
+                    hv[v] = __float2half_rn(x);
+                    lv[v] = __float2half_rn(x - __half2float(hv[v]));
+                }
+                *reinterpret_cast<uint2*>(hi + off) = make_uint2(
+                    (uint32_t)__half_as_ushort(hv[0]) | ((uint32_t)__half_as_ushort(hv[1]) << 16),
+                    (uint32_t)__half_as_ushort(hv[2]) | ((uint32_t)__half_as_ushort(hv[3]) << 16));
+                *reinterpret_cast<uint2*>(lo + off) = make_uint2(
+                    (uint32_t)__half_as_ushort(lv[0]) | ((uint32_t)__half_as_ushort(lv[1]) << 16),
+                    (uint32_t)__half_as_ushort(lv[2]) | ((uint32_t)__half_as_ushort(lv[3]) << 16));
+            }
+        }
+        __syncthreads();   // aT holds L_ik
+#pragma unroll
+        for (int sidx = 0; sidx < 2; ++sidx) {
+            if (sidx >= nstrip) break;
+            const float(*bT)[PT] = lcT + sidx * NB;
+            float acc2[4][4] = {};
+            for (int t = 0; t < NB; ++t) {
+                const float4 x = *reinterpret_cast<const float4*>(&aT[t][tr]);
+                const float4 y = *reinterpret_cast<const float4*>(&bT[t][tc]);
+                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc2[u][v] += xs[u] * ys[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float4 o = tgt[sidx][v];
+                o.x -= acc2[0][v];
+                o.y -= acc2[1][v];
+                o.z -= acc2[2][v];
+                o.w -= acc2[3][v];
+                *reinterpret_cast<float4*>(L + (size_t)(rI + tr) + (size_t)((k + 1 + sidx) * NB + tc + v) * ld) = o;
+            }
+        }
+        __syncthreads();   // the block is stored; aT is free for the next one
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
+            __threadfence();
+            st_release(pflag + i, token);
         }
     }
 }
@@ -804,18 +815,20 @@ __device__ void panel_half(float* __restrict__ L, int ld, int k, const float* __
 // Arguments of one elimination step of the FP32 factorisation (factor_step).
 // The factorisation runs by panels of up to four 64-column blocks
 // [b0, e): the elimination steps k = b0 .. e-1 of a panel update only the
-// panel's own columns (strip updates, the lookahead, and at its first step
-// one column of 128-tiles), and write the TF32 split of every panel row as
-// the panel's 16 K stages.  The update of the rest of the trailing matrix by
-// the whole panel (K = 256) is done by tensor-core tiles: the next panel's
-// columns ("front" tiles, in the panel's last step, after the flags of their
-// rows) and everything beyond ("rest" tiles, spread over the next panel's
-// steps but its last, which need no flags: the panel's split is complete
-// before they start, and they touch no column the next panel's steps read or
-// write).  The split is double-buffered by panel parity.
+// panel's own columns (strip updates, the lookahead, and inner 128-tiles),
+// and write the FP16 hi/lo split of every panel row as the panel's 8 K
+// stages.  The update of the rest of the trailing matrix by the whole panel
+// (K = 256) is done by tensor-core tiles: the next panel's columns ("front"
+// tiles, in the panel's last step, after the flags of their rows) and
+// everything beyond ("rest" tiles: one rest_update launch on a second
+// stream, which runs beside the next panel's steps but its last; it needs
+// no flags, since the panel's split is complete before it starts, and it
+// touches no column the next panel's steps read or write).  The split is
+// double-buffered by panel parity.
 struct StepArgs {
     float* L;
     int ld, k, nblk;
+    int pctas;                    // panel CTAs: the row blocks p0 + j, p0 + j + pctas, ... for CTA j
     float* Linv;
     int* info;
     int sw;        // strip width of step k: 0, 1 or 2 blocks, within the panel
@@ -834,16 +847,14 @@ struct StepArgs {
     int f00_rest;                 // ... after applying the previous panel's rest tile (0, 0) to it
     int f00_last;                 // front tile (0, 0) holds the earlier chunks: only this step's remains
     int ns_start;                 // strip rows of the next panel's first step
-    const unsigned char* hi_p;    // rest tiles: the previous panel's split (rows from srow0_p),
-    const unsigned char* lo_p;    // the lower 128-tiles [rb0, rb1) of [c0r, np)^2
+    const unsigned char* hi_p;    // f00_rest: the previous panel's split (rows from srow0_p)
+    const unsigned char* lo_p;    // and the block (c0r, c0r) it updates
     int srow0_p, c0r;
-    long long rb0, rb1;
     const float* lsT_in;
     float* lsT_out;
     unsigned* pflag;
     unsigned* tickets;
     unsigned* dflag;
-    unsigned* halves;
     const float* scale;   // [0] the split scale s, [1] 1 / s^2 (split_scale)
 };
 
@@ -875,13 +886,18 @@ __host__ __device__ __forceinline__ long long band_tiles(int nrow, int cols)
 // k+1 was already done by the previous launch (lookahead) when p0 = k+2.
 // Every CTA draws a ticket in the order the CTAs start (an atomic counter
 // per step), and the ticket gives its role:
-//   2 (nblk - p0)   panel work of half ticket % 2 of row block
-//                   i = p0 + ticket / 2 (panel_half); the second half to
-//                   finish sets the release flag pflag[i] = k + 1;
+//   pctas           panel work (panel_rows) of the row blocks
+//                   i = p0 + ticket, p0 + ticket + pctas, ... (at most one
+//                   CTA per SM: the panel is one wave and the tiles take the
+//                   other slots); each block, once done, sets its release
+//                   flag pflag[i] = k + 1;
 //   has_diag        factor and invert diagonal block k+1, then dflag[k];
 //   ns_next         helpers (tail_helper): the strip rows of step k+1 and,
 //                   for the first, the lookahead panel work of row block
 //                   k+2 (pflag[k+2] = k + 2);
+//   rest tiles      the previous panel's update of the matrix beyond this
+//                   panel (K = 256), no waits: they fill the SMs while the
+//                   panel rows are computed;
 //   inner tiles     the panel's 128-tiles right of the strip, after the
 //                   flags of their four row blocks (this step's chunk);
 //   f00             in a panel's first steps: this step's chunk applied at
@@ -897,9 +913,7 @@ __host__ __device__ __forceinline__ long long band_tiles(int nrow, int cols)
 //                   blocks) comes the next panel's start: it waits for that
 //                   tile (dflag[k], unused by a step without a diagonal
 //                   block), factors block f0 / 64 and does the strip rows and
-//                   lookahead of the next step (panel_start's work);
-//   rest tiles      the previous panel's update of the matrix beyond this
-//                   panel (K = 256), no waits.
+//                   lookahead of the next step (panel_start's work).
 // Every wait is on a smaller ticket, a CTA that has already started: panel
 // CTAs wait for nothing, the diagonal CTA for the previous launch, helpers
 // for their panel row and the diagonal CTA, tiles for panel rows, the next
@@ -917,11 +931,10 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     const int t_raw = s_ticket;
     const int k = a.k, ld = a.ld;
     float* __restrict__ L = a.L;
-    const int npanel = a.nblk - a.p0;   // panel row blocks, two CTAs each
     const unsigned token = (unsigned)k + 1;
     int* status = a.info + 3;
     const float sc = a.scale[0], unsc = a.scale[1];
-    long long t = (long long)t_raw - 2 * npanel;   // index among the other roles
+    long long t = (long long)t_raw - a.pctas;   // index among the other roles
     // roles without tensor-core work give up the CTA's TMEM allocation permit
     // at once: while a CTA holds it, no second CTA of the kernel is placed on
     // its SM
@@ -931,20 +944,9 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     if ((t < a.has_diag + a.ns_next || (a.next_start && t == t_start)) && threadIdx.x < 32)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (t < 0) {
-        const int i = a.p0 + t_raw / 2;
-        panel_half(L, ld, k, a.Linv, a.sw, a.srow0, a.st_base, a.stage_stride, a.hi, a.lo, a.lsT_in, i, t_raw & 1,
-                   tc_smem, sc);
-        __syncthreads();   // the half is stored
-        if (threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.global;" ::: "memory");   // the split is read by bulk copies
-            __threadfence();
-            // halves[i] only grows (two per step): the second half to finish
-            // sees an odd count and releases the row block
-            if (atomicAdd(a.halves + i, 1u) & 1u) {
-                __threadfence();
-                st_release(a.pflag + i, token);
-            }
-        }
+        // panel row blocks p0 + t_raw, p0 + t_raw + pctas, ...
+        panel_rows(L, ld, k, a.Linv, a.sw, a.srow0, a.st_base, a.stage_stride, a.hi, a.lo, a.lsT_in, a.p0 + t_raw,
+                   a.pctas, a.nblk, tc_smem, sc, a.pflag, token);
         return;
     }
     if (a.has_diag) {
@@ -1030,15 +1032,7 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
                               false};
             release_start = t == 0 && a.next_start;
         } else {
-            t -= n_front;
-            const long long b = a.rb0 + t;   // lower-triangle tile index of [c0r, np)^2
-            I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-            while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
-            while ((long long)I * (I + 1) / 2 > b) --I;
-            J = (int)(b - (long long)I * (I + 1) / 2);
-            const int off = (a.c0r - a.srow0_p) / tc::TM;
-            jobs[0] = TileJob{a.c0r + tc::TM * I, a.c0r + tc::TM * J, off + I, off + J, 0, 4 * tc::CHUNK_STAGES,
-                              a.hi_p, a.lo_p, -1, -1, false};
+            njobs = 0;   // beyond the step's roles (not launched)
         }
     }
     bool ok = true;
@@ -1066,8 +1060,40 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
     if (!ok && threadIdx.x == 0) atomicCAS(status, 0, (int)GBEM_ERR_TIMEOUT);
 }
 
+// The previous panel's update of the matrix beyond the current panel (the
+// "rest" tiles): the lower 128-tiles tb0, tb0 + 1, ... of [c0r, np)^2 in
+// lower-triangle order, one warp-specialised CTA each, with the previous
+// panel's split (rows from srow0).  Launched on a second stream beside the
+// panel's steps: it waits for nothing.
+struct RestArgs {
+    float* L;
+    int ld;
+    const unsigned char* hi;
+    const unsigned char* lo;
+    size_t stage_stride;
+    int c0r, srow0;
+    long long tb0;
+    const float* scale;
+    int* status;
+};
+
+__global__ void __launch_bounds__(tc::WS_THREADS, 2) rest_update(const RestArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char ws_smem[];
+    const long long b = a.tb0 + blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
+    while ((long long)I * (I + 1) / 2 > b) --I;
+    const int J = (int)(b - (long long)I * (I + 1) / 2);
+    const int off = (a.c0r - a.srow0) / tc::TM;
+    const bool ok = tc::syrk_tile_ws(a.L, a.ld, a.c0r + tc::TM * I, a.c0r + tc::TM * J, a.hi, a.lo, a.stage_stride,
+                                     off + I, off + J, 0, 4 * tc::CHUNK_STAGES, ws_smem, a.scale[1]);
+    if (!ok && threadIdx.x == 0) atomicCAS(a.status, 0, (int)GBEM_ERR_TIMEOUT);
+}
+
 template <typename T>
-cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s)
+cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cudaStream_t s,
+                     const SideStream* side = nullptr)
 {
     const int nblk = np / NB;
     const size_t smem = 2 * NB * (NB + 1) * sizeof(T);
@@ -1084,28 +1110,48 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             return e;
         // work space (cholesky_f32_split_bytes): the hi and lo split of two
         // panels (by parity), two strip-row buffers, then per 64-row block
-        // the panel flag, the step's ticket, the diagonal-block flag and the
-        // count of finished panel halves
+        // the panel flag, the step's ticket and the diagonal-block flag
         const size_t stage_stride = split_stage_stride(np);
         const size_t part = (size_t)kPanelStages * stage_stride;
         float* lsT = reinterpret_cast<float*>(split + 4 * part);   // 2 x (2 x 64 x 64)
         unsigned* pflag = reinterpret_cast<unsigned*>(split + 4 * part + 4 * NB * NB * sizeof(float));
-        float* scale = reinterpret_cast<float*>(pflag + 4 * (size_t)nblk);   // 2 floats
+        float* scale = reinterpret_cast<float*>(pflag + 3 * (size_t)nblk);   // 2 floats
         unsigned* tickets = pflag + nblk;
         unsigned* dflag = tickets + nblk;
-        unsigned* halves = dflag + nblk;
         float* Lf = reinterpret_cast<float*>(L);
         float* Linvf = reinterpret_cast<float*>(Linv);
-        if ((e = cudaMemsetAsync(pflag, 0, 4 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pflag, 0, 3 * (size_t)nblk * sizeof(unsigned), s)) != cudaSuccess) return e;
+        // panel CTAs of a step: one per SM at most (each takes a share of the
+        // row blocks), so that the panel work is one wave beside the tiles
+        int dev = 0, nsm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
         split_scale<<<1, 1024, 0, s>>>(reinterpret_cast<const float*>(L), np, scale);
         count_launch();
         // strip width of a step with m blocks of its panel right of the
         // diagonal: one or two column blocks, leaving an even number (whole
         // 128-tiles) to the tensor cores
         auto strip_width = [](int m) { return m <= 0 ? 0 : (((m - 1) & 1) ? 2 : 1); };
-        cudaLaunchAttribute pdl[1];
-        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        pdl[0].val.programmaticStreamSerializationAllowed = 1;
+        // the per-step launches on the main stream at the highest priority,
+        // so that the block scheduler gives their CTAs the SM slots that the
+        // concurrent rest updates (second stream, lowest priority) free up
+        int prio_least = 0, prio_greatest = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest)) != cudaSuccess) return e;
+        cudaLaunchAttribute attrs[2];
+        attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attrs[0].val.programmaticStreamSerializationAllowed = 1;
+        attrs[1].id = cudaLaunchAttributePriority;
+        attrs[1].val.priority = prio_greatest;
+        if ((e = cudaFuncSetAttribute(rest_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc::WS_SMEM_BYTES)) != cudaSuccess)
+            return e;
+        cudaStream_t rs = side && side->stream ? side->stream : s;   // where the rest updates run
+        bool joined = true;                                          // no rest update pending on rs
+        // the whole factorisation is one traced span (its launches overlap);
+        // algorithmic bytes and useful flops are summed over the launches
+        double tr_bytes = 0.0, tr_flops = 0.0;
+        cudaEvent_t ev_all = trace_begin(s);
         const double blk = 4.0 * NB * NB, tb = 4.0 * tc::TM * tc::TM;
         int prev_srow0 = 0;
         for (int q = 0, b0 = 0; b0 < nblk; ++q, b0 += kPanel) {
@@ -1119,19 +1165,50 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
             // b0: a launch of its own for the first panel, the previous
             // panel's last step for the others
             if (q == 0) {
-                cudaEvent_t ev = trace_begin(s);
                 panel_start<<<1, 256, kStripSmem, s>>>(Lf, np, b0, Linvf, info, lsT + (size_t)(b0 & 1) * 2 * NB * NB,
                                                        strip_width(e0 - b0 - 1), pflag);
                 count_launch();
-                trace_end(GBEM_KERNEL_FACTOR, ev, s, 4.0 * blk, 2.0 * NB * NB * NB / 3.0);
+                tr_bytes += 4.0 * blk;
+                tr_flops += 2.0 * NB * NB * NB / 3.0;
             }
-            // the previous panel's update of [e0, np)^2, over this panel's
-            // steps but the last
+            // a full panel followed by another: its first steps apply their
+            // chunks to front tile (0, 0) at once, the last step its own only
+            const bool incr = e0 - b0 == kPanel && e0 < nblk;
+            // the previous panel's update of [e0, np)^2 (one rest_update
+            // launch, beside this panel's steps but the last).  Its tile 0 is
+            // block (e0, e0), front tile (0, 0) of this panel: with incr the
+            // f00 CTA of the first step applies it, before that step's chunk.
             const int c0r = e0 * NB;
             const long long ntr = (np - c0r) / tc::TM;
             const long long rest = q > 0 ? ntr * (ntr + 1) / 2 : 0;
-            const int rest_steps = e0 - b0 - 1;
+            const bool f00_rest = incr && rest > 0;
+            const long long tb0 = f00_rest ? 1 : 0;
+            if (rest - tb0 > 0) {
+                if (rs != s) {
+                    // the previous panel's split is complete once the launches
+                    // issued so far on the main stream are
+                    if ((e = cudaEventRecord(side->ready, s)) != cudaSuccess ||
+                        (e = cudaStreamWaitEvent(rs, side->ready, 0)) != cudaSuccess)
+                        return e;
+                }
+                RestArgs ra{Lf, np, hi_p, lo_p, stage_stride, c0r, prev_srow0, tb0, scale, info + 3};
+                rest_update<<<(unsigned)(rest - tb0), tc::WS_THREADS, tc::WS_SMEM_BYTES, rs>>>(ra);
+                count_launch();
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                if (rs != s) {
+                    if ((e = cudaEventRecord(side->done, rs)) != cudaSuccess) return e;
+                    joined = false;
+                }
+                const double kt = (double)(rest - tb0) * 4 * tc::TK;   // K summed over tiles
+                tr_bytes += 2.0 * (rest - tb0) * tb + 2.0 * 4.0 * tc::TM * kt;
+                tr_flops += 2.0 * tc::TM * tc::TM * kt;
+            }
             for (int k = b0; k < e0; ++k) {
+                // the last step's front tiles overlap the rest region
+                if (k == e0 - 1 && !joined) {
+                    if ((e = cudaStreamWaitEvent(s, side->done, 0)) != cudaSuccess) return e;
+                    joined = true;
+                }
                 StepArgs a{};
                 a.L = Lf;
                 a.ld = np;
@@ -1154,71 +1231,56 @@ cudaError_t cholesky(T* L, int np, T* Linv, int* info, unsigned char* split, cud
                 a.fcols = (k == e0 - 1 && e0 < nblk) ? (std::min(e0 + kPanel, nblk) - e0) * NB / tc::TM : 0;
                 a.next_start = a.fcols > 0;
                 a.ns_start = a.next_start ? strip_width(std::min(e0 + kPanel, nblk) - e0 - 1) : 0;
-                // a full panel followed by another: its first steps apply their
-                // chunks to front tile (0, 0) at once, the last step its own only
-                const bool incr = e0 - b0 == kPanel && e0 < nblk;
                 a.f00 = incr && k < e0 - 1;
                 a.f00_last = incr && k == e0 - 1;
+                a.f00_rest = f00_rest && k == b0;
                 a.hi_p = hi_p;
                 a.lo_p = lo_p;
                 a.srow0_p = prev_srow0;
                 a.c0r = c0r;
-                const int j = k - b0;
-                a.rb0 = (rest > 0 && j < rest_steps) ? rest * j / rest_steps : 0;
-                a.rb1 = (rest > 0 && j < rest_steps) ? rest * (j + 1) / rest_steps : 0;
-                // rest tile 0 is block (e0, e0), front tile (0, 0) of this
-                // panel: the f00 CTA of the step whose share holds it applies it
-                a.f00_rest = a.f00 && a.rb0 == 0 && a.rb1 > 0;
-                if (a.f00_rest) a.rb0 = 1;
                 a.lsT_in = lsT + (size_t)(k & 1) * 2 * NB * NB;
                 a.lsT_out = lsT + (size_t)((k + 1) & 1) * 2 * NB * NB;
                 a.pflag = pflag;
                 a.tickets = tickets;
                 a.dflag = dflag;
-                a.halves = halves;
                 a.scale = scale;
                 // a lookahead helper that applies this step's update to block
                 // (k+2, k+2) needs the inner tile (0, 0) that leaves it alone
                 if (a.sw == 1 && a.ns_next >= 1 && a.icols < 1) return cudaErrorInvalidValue;
                 const long long npan = nblk - a.p0;
+                a.pctas = (int)std::min<long long>(npan, nsm);
                 const long long n_in = band_tiles((np - a.r0) / tc::TM, a.icols);
                 const long long n_fr = a.fcols > 0 ? band_tiles((np - a.f0) / tc::TM, a.fcols) : 0;
-                const long long n_rest = a.rb1 - a.rb0;
-                const long long grid =
-                    2 * npan + a.has_diag + a.ns_next + n_in + a.f00 + n_fr + a.next_start + n_rest;
+                const long long grid = a.pctas + a.has_diag + a.ns_next + n_in + a.f00 + n_fr + a.next_start;
                 if (grid == 0) continue;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)grid);
                 cfg.blockDim = dim3(256);
                 cfg.dynamicSmemBytes = kFactorSmem;
                 cfg.stream = s;
-                cfg.attrs = pdl;
-                cfg.numAttrs = 1;
-                cudaEvent_t ev = trace_begin(s);
+                cfg.attrs = attrs;
+                cfg.numAttrs = 2;
                 if ((e = cudaLaunchKernelEx(&cfg, factor_step, a)) != cudaSuccess) return e;
                 count_launch();
-                {
-                    // algorithmic bytes: per panel row block A_ik read, L_ik
-                    // and its hi/lo split written, strip blocks read and
-                    // written; every tile read and written once and its split
-                    // rows read once; the diagonal block read, its factor and
-                    // inverse written.  Useful flops: panel products, strip
-                    // and tile updates (2mnk), diagonal factor and inverse.
-                    const double strips = (double)npan * a.sw;
-                    const double kt = (double)(n_fr + n_rest + a.f00_rest) * 4 * tc::TK +
-                                      (double)(n_in + a.f00) * tc::TK -
-                                      (a.f00_last ? 3.0 * tc::TK : 0.0);   // K summed over tiles
-                    const int diags = a.has_diag + a.next_start;
-                    const double bytes = 2.0 * npan * blk + 8.0 * npan * NB * NB + 2.0 * strips * blk +
-                                         2.0 * (n_in + n_fr + n_rest) * tb + 2.0 * 4.0 * tc::TM * kt +
-                                         3.0 * diags * blk;
-                    const double flops = (double)npan * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
-                                         2.0 * tc::TM * tc::TM * kt + diags * 2.0 * NB * NB * NB / 3.0;
-                    trace_end(GBEM_KERNEL_FACTOR, ev, s, bytes, flops);
-                }
+                // algorithmic bytes: per panel row block A_ik read, L_ik and
+                // its hi/lo split written, strip blocks read and written;
+                // every tile read and written once and its split rows read
+                // once; the diagonal block read, its factor and inverse
+                // written.  Useful flops: panel products, strip and tile
+                // updates (2mnk), diagonal factor and inverse.
+                const double strips = (double)npan * a.sw;
+                const double kt = (double)(n_fr + a.f00_rest) * 4 * tc::TK + (double)(n_in + a.f00) * tc::TK -
+                                  (a.f00_last ? 3.0 * tc::TK : 0.0);   // K summed over tiles
+                const int diags = a.has_diag + a.next_start;
+                tr_bytes += 2.0 * npan * blk + 8.0 * npan * NB * NB + 2.0 * strips * blk +
+                            2.0 * (n_in + n_fr + a.f00_rest) * tb + 2.0 * 4.0 * tc::TM * kt + 3.0 * diags * blk;
+                tr_flops += (double)npan * NB * NB * (NB + 1) + 2.0 * strips * NB * NB * NB +
+                            2.0 * tc::TM * tc::TM * kt + diags * 2.0 * NB * NB * NB / 3.0;
             }
             prev_srow0 = srow0;
         }
+        if (!joined && (e = cudaStreamWaitEvent(s, side->done, 0)) != cudaSuccess) return e;
+        trace_end(GBEM_KERNEL_FACTOR, ev_all, s, tr_bytes, tr_flops);
         return cudaGetLastError();
     }
     if ((e = cudaFuncSetAttribute(trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -1282,16 +1344,16 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 size_t cholesky_f32_split_bytes(int np)
 {
     // hi/lo split of two panels, two strip-row buffers, panel flags, step
-    // tickets, diagonal-block flags and half-panel counters
+    // tickets and diagonal-block flags
     return 4 * (size_t)kPanelStages * split_stage_stride(np) + 4 * NB * NB * sizeof(float) +
-           4 * (size_t)(np / NB) * sizeof(unsigned) + 2 * sizeof(float);
+           3 * (size_t)(np / NB) * sizeof(unsigned) + 2 * sizeof(float);
 }
 
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
-                                cudaStream_t s)
+                                cudaStream_t s, const SideStream* side)
 {
     if (nb != NB || np % tc::TM || !split) return cudaErrorInvalidValue;
-    return cholesky<float>(L, np, Linv, info, split, s);
+    return cholesky<float>(L, np, Linv, info, split, s, side);
 }
 
 cudaError_t launch_wait_selftest(const unsigned* flag, int* status, double limit_ms, cudaStream_t s)

@@ -37,6 +37,14 @@ extern thread_local KernelTrace* g_trace;
 cudaEvent_t trace_begin(cudaStream_t s);
 void trace_end(int kind, cudaEvent_t a, cudaStream_t s, double bytes, double flops);
 
+// A second stream of the FP32 factorisation, owned by the matrix: the
+// trailing updates beyond each panel run on it beside the panel's steps,
+// ordered by the two events.  With no stream they run on the main stream.
+struct SideStream {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+};
+
 struct gbem_ctx_s {
     int device = -1;
     int num_sms = 0;
@@ -71,6 +79,8 @@ struct gbem_ctx_s {
     };
     std::vector<Spare> spare;
     bool keep_spare = true;
+    // side streams of destroyed matrices (idle), for the next matrices' factors
+    std::vector<SideStream> side_pool;
 };
 
 // Kernels launched by the library in this process.
@@ -142,6 +152,7 @@ struct gbem_mesh_s {
     DevPanels dev;
 };
 
+
 struct gbem_matrix_s {
     gbem_ctx* ctx = nullptr;
     gbem_mesh_t* mesh = nullptr;
@@ -167,6 +178,7 @@ struct gbem_matrix_s {
     double* B = nullptr;
     void* W = nullptr;          // T: triangular-solve work
     bool factored = false;
+    SideStream side;               // mixed factor: the stream of its rest updates (created at first use)
     cudaStream_t last = nullptr;   // the stream of the last call (null: the default stream)
     bool used = false;             // `last` holds a stream that work was enqueued on
     std::vector<std::pair<void*, size_t>> allocs;
@@ -218,7 +230,7 @@ cudaError_t launch_cholesky_f64(double* L, int np, int nb, double* Linv, int* in
 // cholesky_f32_split_bytes(np) bytes (the hi/lo copies of one panel).
 size_t cholesky_f32_split_bytes(int np);
 cudaError_t launch_cholesky_f32(float* L, int np, int nb, float* Linv, int* info, unsigned char* split,
-                                cudaStream_t s);
+                                cudaStream_t s, const SideStream* side);
 // One CTA waits, through the factorisation's bounded release-flag wait, for
 // flag[0] to reach 1 (limit limit_ms); status receives GBEM_ERR_TIMEOUT if
 // it gives up.

@@ -383,4 +383,200 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
     return ok;
 }
 
+// The same update of one 128 x 128 tile by a warp-specialised CTA of
+// WS_THREADS = 288 threads (syrk_tile_ws), for tiles that wait for nothing:
+// warp 8 allocates the TMEM and its lane 0 is the producer, which streams the
+// stages through the ring and issues the MMAs without ever waiting for the
+// epilogue, except before an accumulator is reused; warps 0-7 load C, drain
+// each chunk's accumulator into it (as in syrk_tile) and report every drain
+// on the accumulator's "drained" mbarrier (one arrival per warp).  The copy
+// stream is then never held up by the C loads, the drains or their barriers,
+// which with one thread doing both roles cost a K = 256 tile about 40 % of
+// its time.
+constexpr int WS_THREADS = 288;
+constexpr int WS_SMEM_BYTES = NBUF * BUF_BYTES + 256;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ bool syrk_tile_ws(float* __restrict__ L, int ld, int rI, int rJ, const unsigned char* __restrict__ hi,
+                             const unsigned char* __restrict__ lo, size_t stage_stride, int ia, int ja, int st0,
+                             int nst, unsigned char* smem, float unscale)
+{
+    const bool diag = ia == ja;
+    // barriers: [b] full, [NBUF + b] empty, [2 NBUF + a] accumulator a done,
+    // [2 NBUF + 2 + a] accumulator a drained; then the TMEM address slot and
+    // the failure word
+    unsigned char* tail = smem + NBUF * BUF_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tail + 8 * (2 * NBUF + 4));
+    volatile int* s_fail = reinterpret_cast<volatile int*>(tail + 8 * (2 * NBUF + 4) + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = (nst + CHUNK_STAGES - 1) / CHUNK_STAGES;
+    auto full = [&](int b) { return smem_u32(&bars[b]); };
+    auto empty = [&](int b) { return smem_u32(&bars[NBUF + b]); };
+    auto accf = [&](int a) { return smem_u32(&bars[2 * NBUF + a]); };
+    auto accd = [&](int a) { return smem_u32(&bars[2 * NBUF + 2 + a]); };
+    auto part = [&](int b, int p) { return smem_u32(smem + (size_t)b * BUF_BYTES + (size_t)p * STAGE_BYTES); };
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (lane == 0) {
+            for (int b = 0; b < NBUF; ++b) {
+                mbar_init(full(b), 1);
+                mbar_init(empty(b), 1);
+            }
+            for (int a = 0; a < 2; ++a) {
+                mbar_init(accf(a), 1);
+                mbar_init(accd(a), 8);
+            }
+            *s_fail = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    int ok = 1;
+    if (warp == 8) {
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_last();
+            auto issue = [&](int s, int b) {
+                mbar_expect_tx(full(b), (diag ? 2u : 4u) * STAGE_BYTES);
+                const size_t o = (size_t)(st0 + s) * stage_stride;
+                bulk_g2s(part(b, 0), hi + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+                bulk_g2s(part(b, 1), lo + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+                if (!diag) {
+                    bulk_g2s(part(b, 2), hi + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+                    bulk_g2s(part(b, 3), lo + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
+                }
+            };
+            // phases started on each barrier, for the drain after a failed wait
+            int loads[NBUF], commits[NBUF], acommits[2] = {0, 0};
+            for (int b = 0; b < NBUF; ++b) loads[b] = commits[b] = 0;
+            const uint32_t idesc = make_idesc();
+            const int pre = nst < NBUF ? nst : NBUF;
+            for (int s = 0; s < pre; ++s) {
+                issue(s, s);
+                ++loads[s];
+            }
+            int s = 0;
+            for (int c = 0; c < nch && ok; ++c) {
+                // accumulator c % 2 is free once every warp has drained chunk c - 2
+                if (c >= 2 && !mbar_wait_bounded(accd(c & 1), (uint32_t)((c - 2) >> 1) & 1u)) {
+                    ok = 0;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)((c & 1) * TM);
+                const int s_end = min(nst, (c + 1) * CHUNK_STAGES);
+                for (; s < s_end; ++s) {
+                    const int b = s % NBUF;
+                    if (!mbar_wait_bounded(full(b), (uint32_t)(s / NBUF) & 1u)) {
+                        ok = 0;
+                        break;
+                    }
+                    const uint32_t ah = part(b, 0), al = part(b, 1);
+                    const uint32_t bh = diag ? ah : part(b, 2), bl = diag ? al : part(b, 3);
+                    const bool first = s == c * CHUNK_STAGES;
+#pragma unroll
+                    for (int ks = 0; ks < KH / 16; ++ks) {
+                        const uint32_t off = ks * 256;
+                        mma_f16(acc, make_desc(ah + off), make_desc(bh + off), idesc, !first || ks > 0);
+                        mma_f16(acc, make_desc(ah + off), make_desc(bl + off), idesc, 1);
+                        mma_f16(acc, make_desc(al + off), make_desc(bh + off), idesc, 1);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     empty(b))
+                                 : "memory");
+                    ++commits[b];
+                    // refill the previous stage's buffer once its MMAs have read it
+                    const int sp = s - 1;
+                    if (sp >= 0 && sp + NBUF < nst) {
+                        const int bp = sp % NBUF;
+                        if (!mbar_wait_bounded(empty(bp), (uint32_t)(sp / NBUF) & 1u)) {
+                            ok = 0;
+                            break;
+                        }
+                        issue(sp + NBUF, bp);
+                        ++loads[bp];
+                    }
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 accf(c & 1))
+                             : "memory");
+                ++acommits[c & 1];
+            }
+            if (!ok) {
+                // let the copies and MMAs issued so far finish before the
+                // shared memory and TMEM are released
+                *s_fail = 1;
+                for (int b = 0; b < NBUF; ++b) {
+                    if (loads[b] > 0) mbar_wait_bounded(full(b), (uint32_t)(loads[b] - 1) & 1u);
+                    if (commits[b] > 0) mbar_wait_bounded(empty(b), (uint32_t)(commits[b] - 1) & 1u);
+                }
+                for (int a = 0; a < 2; ++a)
+                    if (acommits[a] > 0) mbar_wait_bounded(accf(a), (uint32_t)(acommits[a] - 1) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // warp w: accumulator lanes 32 (w % 4).., columns 64 (w / 4)..
+        const int q = warp & 3, half = warp >> 2;
+        const int row = q * 32 + lane;
+        float* crow = L + (size_t)(rI + row) + (size_t)(rJ + half * 64) * ld;
+        float cpre[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) cpre[i] = __ldcs(crow + (size_t)i * ld);
+        for (int c = 0; c < nch; ++c) {
+            // lane 0 waits for chunk c (giving up at once if the producer
+            // has failed), the warp follows its verdict
+            int got = 1;
+            if (lane == 0) {
+                bw::Deadline dl(bw::kOwnAsyncNs);
+                while (!mbar_try_wait(accf(c & 1), (uint32_t)(c >> 1) & 1u)) {
+                    if (*s_fail || dl.expired()) {
+                        got = 0;
+                        break;
+                    }
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                ok = 0;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((c & 1) * TM + half * 64);
+#pragma unroll
+            for (int cc = 0; cc < 64; cc += 16) {
+                float v[16];
+                tmem_ld16(base + (uint32_t)cc, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cpre[cc + i] = fmaf(-unscale, v[i], cpre[cc + i]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(accd(c & 1));
+        }
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) __stcs(crow + (size_t)i * ld, cpre[i]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok && !*s_fail);
+    if (warp == 8) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+    return ok;
+}
+
 }  // namespace tc
