@@ -281,7 +281,6 @@ __device__ __forceinline__ void potrf_body(T* __restrict__ L, int ld, int k0, T*
 // (a no-op when launched without the attribute), and let the next one be
 // scheduled early; it waits in turn before touching memory.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
@@ -924,8 +923,10 @@ __global__ void __launch_bounds__(256, 2) factor_step(const StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int s_ticket;
+    // the next step's launch begins as this one's CTAs exit (no early
+    // trigger): CTAs of the next step waiting here would hold SM slots, at
+    // the highest priority, that the concurrent rest update needs
     pdl_wait();
-    pdl_trigger();
     if (threadIdx.x == 0) s_ticket = (int)atomicAdd(a.tickets + a.k, 1u);
     __syncthreads();
     const int t_raw = s_ticket;
