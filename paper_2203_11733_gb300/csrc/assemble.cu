@@ -52,7 +52,16 @@ __device__ __forceinline__ double rsq(double x)
     double e = fma(-x * y, y, 1.0);
     return fma(0.5 * y, e, y);
 }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// 1/sqrt(x) in FP32: the hardware approximation (PTX rsqrt.approx, relative
+// error below 2^-22), flush-to-zero form, one instruction.  The arguments are
+// squared distances between quadrature nodes of separated panels, always
+// normal numbers, so no subnormal handling is needed.
+__device__ __forceinline__ float rsq(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 template <typename T> __device__ __forceinline__ T glx(int n, int i);
 template <typename T> __device__ __forceinline__ T glw(int n, int i);
@@ -113,7 +122,10 @@ __device__ __noinline__ OuterSum<T> far_par(T dp, T dq, T w, T ai, T bi, T aj, T
             WQ[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
     OuterSum<T> s;
-#pragma unroll 1
+    // low orders (the bulk of the pairs) unrolled whole: nodes and weights
+    // become immediate operands
+    constexpr int kUnroll = N <= 3 ? N * N : 1;
+#pragma unroll kUnroll
     for (int ac = 0; ac < N * N; ++ac) {
         const int a = ac / N, c = ac % N;
         T t = dp + glx<T>(N, a) * ai - glx<T>(N, c) * aj;
@@ -144,7 +156,8 @@ __device__ __noinline__ OuterSum<T> far_orth(T ds, T si, T sj, T dv, T ti, T dw,
             WVW[b * N + d] = glw<T>(N, b) * glw<T>(N, d);
         }
     OuterSum<T> s;
-#pragma unroll 1
+    constexpr int kUnroll = N <= 3 ? N * N : 1;
+#pragma unroll kUnroll
     for (int ac = 0; ac < N * N; ++ac) {
         const int a = ac / N, c = ac % N;
         T t = ds + glx<T>(N, a) * si - glx<T>(N, c) * sj;
