@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=24,
                     help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch512", "serving"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch512", "serving", "partition"],
                     help="headline: the three-layer bus (and the 2x2 bus as secondary); "
                          "batch512 / serving: the batched and served forms")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -913,6 +913,88 @@ def run_serving(args):
     dist_stop(world)
 
 
+def run_partition(args):
+    """Panels for accuracy (Sec. 3.3): the column of the Maxwell matrix that
+    belongs to net 0, in FP64, from uniform meshes, edge-graded meshes and the
+    paper's distance-graded partition for main net 0, each against the same
+    column from a fine mesh of the same structure.  One JSON line per
+    structure; the paper's Table 2 geometry (two crossing bars in a grounded
+    40 x 40 x 10 um box, eps_r = 1) adds its printed converged values."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem, workloads as W
+    B.build()
+    ctx = gbem.Context(0)
+
+    def column(mesh, eps_r):
+        mat = gbem.gbem_assemble(mesh, gbem.GBEM_FP64)
+        try:
+            C, _ = gbem.gbem_capacitance(mesh, mat, eps_r)
+        finally:
+            mat.close()
+        return np.asarray(C)[:, 0]
+
+    def graded(boxes, p1, p5, encl, h_max=0.0):
+        return gbem.gbem_mesh_graded(ctx, boxes, 0, p1, 4.0, 1.0, p5, h_max=h_max, enclosure=encl)
+
+    bars, box = W.paper_two_bars()
+    studies = [
+        # name, boxes, enclosure, eps_r, reference mesh maker, uniform meshes, edge-graded meshes,
+        # the paper's p1 values (p2 = 4, p3 = 1), p5
+        ("two_bars", W.two_bars()[0], None, W.EPS_R_SIO2,
+         ("edge_graded", dict(h=0.01, ratio=1.3, h_min=0.002)),
+         [0.2, 0.1, 0.05, 0.03], [0.2, 0.15, 0.1, 0.06], [0.02, 0.01, 0.005, 0.0025, 0.00125], 0.1),
+        ("crossing_bus_2x2", W.crossing_bus_2x2()[0], None, W.EPS_R_SIO2,
+         ("edge_graded", dict(h=0.015, ratio=1.3, h_min=0.002)),
+         [0.1, 0.05, 0.03, 0.02], [0.15, 0.1, 0.06, 0.04], [0.004, 0.002, 0.001, 0.0005, 0.00025], 0.1),
+        ("paper_table2", bars, box, 1.0, ("paper_graded", dict(p1=0.02, p5=1.0)),
+         [4.0, 2.0, 1.0], [], [3.0, 1.5, 0.75, 0.375, 0.1875], 1.0),
+    ]
+    for name, boxes, encl, eps_r, (ref_kind, ref_p), hs_u, hs_g, p1s, p5 in studies:
+        if ref_kind == "edge_graded":
+            mesh = gbem.gbem_mesh(ctx, boxes, ref_p)
+        else:
+            mesh = graded(boxes, ref_p["p1"], ref_p["p5"], encl)
+        n_ref = mesh.n
+        ref = column(mesh, eps_r)
+        mesh.close()
+        rows = []
+
+        def add(kind, param, mesh):
+            col = column(mesh, eps_r)
+            rows.append({"mesh": kind, "param": param, "panels": mesh.n,
+                         "c00_aF": float(col[0] * 1e18), "c10_aF": float(col[1] * 1e18),
+                         "err_c00": float(abs(col[0] - ref[0]) / abs(ref[0])),
+                         "err_column": float(np.max(np.abs(col - ref)) / abs(ref[0]))})
+            mesh.close()
+        for h in hs_u:
+            if encl is None:
+                add("uniform", {"h": h}, gbem.gbem_mesh(ctx, boxes, dict(h=h, ratio=1.0, h_min=0.0)))
+            else:   # no area bound, edges capped at h: a uniform grid of nets and walls
+                add("uniform", {"h": h}, graded(boxes, 1e9, p5, encl, h_max=h))
+        for h in hs_g:
+            add("edge_graded", {"h": h, "ratio": 1.5, "h_min": h / 6},
+                gbem.gbem_mesh(ctx, boxes, dict(h=h, ratio=1.5, h_min=h / 6)))
+        for p1 in p1s:
+            add("paper_graded", {"p1": p1, "p2": 4.0, "p3": 1.0, "p5": p5, "main": 0}, graded(boxes, p1, p5, encl))
+        # fewest panels within 5 % and 1 % on the column, per kind
+        best = {}
+        for tol in (0.05, 0.01):
+            for kind in ("uniform", "edge_graded", "paper_graded"):
+                ok = [r["panels"] for r in rows if r["mesh"] == kind and r["err_column"] <= tol]
+                best[f"{kind}_within_{int(tol * 100)}pct"] = min(ok) if ok else None
+        out = {"study": "panels_for_accuracy", "structure": name, "net": 0, "precision": "fp64", "eps_r": eps_r,
+               "reference": {"mesh": ref_kind, **ref_p, "panels": n_ref,
+                             "c00_aF": float(ref[0] * 1e18), "c10_aF": float(ref[1] * 1e18)},
+               "fewest_panels": best, "rows": rows}
+        if name == "paper_table2":
+            out["paper_converged_aF"] = {"C11": 226.0, "C21": -58.7, "panels": 594}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -921,6 +1003,8 @@ def main():
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "partition":
+        run_partition(args)
     else:
         run_ours(args)
 
