@@ -253,6 +253,34 @@ __device__ __forceinline__ unsigned long long tagged(float v, unsigned epoch)
     return ((unsigned long long)epoch << 32) | __float_as_uint(v);
 }
 
+// The 64 x R tagged block of rows j0 .. j0 + 63 (columns c < nr; zero for
+// c >= nr) into shared memory at dst(t, c), 256 threads.  Every thread issues
+// its R / 4 loads at once and polls again only the words not yet tagged with
+// this epoch, so a block that is ready costs one L2 round trip, not R / 4.
+template <int R, typename Dst>
+__device__ __forceinline__ void load_tagged_block(const unsigned long long* __restrict__ tag, int j0, int np, int nr,
+                                                  unsigned epoch, int* status, Dst dst)
+{
+    constexpr int K = NB * R / 256;
+    static_assert(K * 256 == NB * R, "R a multiple of 4");
+    const int tid = threadIdx.x;
+    unsigned long long w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = tid + 256 * k, t = e % NB, c = e / NB;
+        w[k] = c < nr ? ld_relaxed_u64(tag + (size_t)(j0 + t) + (size_t)c * np) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = tid + 256 * k, t = e % NB, c = e / NB;
+        float v = 0.f;
+        if (c < nr)
+            v = ((unsigned)(w[k] >> 32) == epoch) ? __uint_as_float((unsigned)w[k])
+                                                   : poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status);
+        dst(t, c) = v;
+    }
+}
+
 // acc += aj with Kahan compensation: a thread sums one 16-term product per
 // earlier block, so the long sum over blocks carries no rounding drift into
 // the solve (the refinement's contraction, about the square of the solve's
@@ -411,10 +439,7 @@ __device__ __forceinline__ void finish_row(SweepF32Smem<R>& S, const float (&z)[
     const int tid = threadIdx.x;
     const int r = tid & (NB - 1), q = tid >> 6;
     if (has_p) {
-        for (int e = tid; e < NB * R; e += blockDim.x) {
-            const int t = e % NB, c = e / NB;
-            S.vT[c][t] = (c < nr) ? poll_tagged(tag + (size_t)(p0 + t) + (size_t)c * np, epoch, status) : 0.f;
-        }
+        load_tagged_block<R>(tag, p0, np, nr, epoch, status, [&](int t, int c) -> float& { return S.vT[c][t]; });
         __syncthreads();
     }
 #pragma unroll
@@ -477,11 +502,7 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
 #pragma unroll
                 for (int tt = 0; tt < QW; ++tt)
                     lnext[tt] = L[(size_t)(b0 + r) + (size_t)((j + 1) * NB + q * QW + tt) * np];
-            const int j0 = j * NB;
-            for (int e = tid; e < NB * R; e += blockDim.x) {
-                const int t = e % NB, c = e / NB;
-                S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
-            }
+            load_tagged_block<R>(tag, j * NB, np, nr, epoch, status, [&](int t, int c) -> float& { return S.v[t][c]; });
             __syncthreads();
             float aj[R];
 #pragma unroll
@@ -550,11 +571,7 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
             if (j - 1 > b + 1)
 #pragma unroll
                 for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(j - 1) * NB + (size_t)(4 * k) * np];
-            const int j0 = j * NB;
-            for (int e = tid; e < NB * R; e += blockDim.x) {
-                const int t = e % NB, c = e / NB;
-                S.v[t][c] = (c < nr) ? poll_tagged(tag + (size_t)(j0 + t) + (size_t)c * np, epoch, status) : 0.f;
-            }
+            load_tagged_block<R>(tag, j * NB, np, nr, epoch, status, [&](int t, int c) -> float& { return S.v[t][c]; });
             __syncthreads();
             float aj[R];
 #pragma unroll
