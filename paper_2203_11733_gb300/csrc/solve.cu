@@ -307,9 +307,10 @@ __device__ __forceinline__ void kahan_add(float (&acc)[R], float (&comp)[R], con
 // of M_b a thread needs is held in its registers, and the vectors are laid
 // out so that a thread reads four of them with one 16-byte shared load (all
 // lanes of a warp read the same address).
+constexpr int SG = 2;          // earlier blocks taken per step of a sweep's sum
 template <int R>
 struct SweepF32Smem {
-    float v[NB][R];            // solved block of another row, v[t][c]
+    float v[SG][NB][R];        // solved blocks of other rows, v[g][t][c]
     float part[4][NB][R];      // partial sums of the four column quarters
     float wT[R][NB];           // right-hand side minus the sums, wT[c][k]
     float vT[R][NB];           // the neighbouring row's solved block, vT[c][k]
@@ -320,7 +321,7 @@ struct SweepF32Smem {
 template <int R>
 struct SweepBwdSmem {
     SweepF32Smem<R> base;
-    float lt[NB][NB + 1];      // lt[r][t] = L[j0 + t][b0 + r]
+    float lt[SG][NB][NB + 1];  // lt[g][r][t] = L[j0 + t][b0 + r] of block g
 };
 
 // sum_k li[k] w[k] with w in shared memory (16-byte aligned), four chains
@@ -489,26 +490,31 @@ __global__ void __launch_bounds__(256) sweep_fwd_f32(const float* __restrict__ L
         } else {
             __syncthreads();   // iv complete
         }
-        // the compensated sum over rows j < b - 1
-        float lnext[QW];
-        if (b > 1)
+        // the compensated sum over rows j < b - 1, SG blocks a step: this
+        // thread's L_bj entries and the solved blocks are loaded together
+        for (int j = 0; j + 1 < b; j += SG) {
+            const int gn = min(SG, b - 1 - j);
+            float lc[SG][QW];
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) lnext[tt] = L[(size_t)(b0 + r) + (size_t)(q * QW + tt) * np];
-        for (int j = 0; j + 1 < b; ++j) {
-            float lcur[QW];
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) lcur[tt] = lnext[tt];
-            if (j + 2 < b)
+                    for (int tt = 0; tt < QW; ++tt)
+                        lc[g][tt] = L[(size_t)(b0 + r) + (size_t)((j + g) * NB + q * QW + tt) * np];
 #pragma unroll
-                for (int tt = 0; tt < QW; ++tt)
-                    lnext[tt] = L[(size_t)(b0 + r) + (size_t)((j + 1) * NB + q * QW + tt) * np];
-            load_tagged_block<R>(tag, j * NB, np, nr, epoch, status, [&](int t, int c) -> float& { return S.v[t][c]; });
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
+                    load_tagged_block<R>(tag, (j + g) * NB, np, nr, epoch, status,
+                                         [&](int t, int c) -> float& { return S.v[g][t][c]; });
             __syncthreads();
             float aj[R];
 #pragma unroll
             for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) axpy_row<R>(aj, lcur[tt], &S.v[q * QW + tt][0]);
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
+#pragma unroll
+                    for (int tt = 0; tt < QW; ++tt) axpy_row<R>(aj, lc[g][tt], &S.v[g][q * QW + tt][0]);
             kahan_add(acc, comp, aj);
             __syncthreads();
         }
@@ -558,26 +564,38 @@ __global__ void __launch_bounds__(256) sweep_bwd_f32(const float* __restrict__ L
         } else {
             __syncthreads();   // iv complete
         }
-        // the compensated sum over rows j > b + 1
-        // thread tid holds L[j0 + (tid & 63)][b0 + (tid >> 6) + 4 k], k < 16
+        // the compensated sum over rows j > b + 1, SG blocks a step (falling
+        // j): thread tid reads L[j0 + (tid & 63)][b0 + (tid >> 6) + 4 k],
+        // k < 16, of each block (coalesced along the columns) into lt
         const float* colb = L + (size_t)(tid & 63) + (size_t)(b0 + (tid >> 6)) * np;
-        float lnext[QW];
-        if (b < nblk - 2)
+        for (int j = nblk - 1; j > b + 1; j -= SG) {
+            const int gn = min(SG, j - b - 1);
+            float lc[SG][QW];
 #pragma unroll
-            for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(nblk - 1) * NB + (size_t)(4 * k) * np];
-        for (int j = nblk - 1; j > b + 1; --j) {
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
 #pragma unroll
-            for (int k = 0; k < QW; ++k) SB.lt[(tid >> 6) + 4 * k][tid & 63] = lnext[k];
-            if (j - 1 > b + 1)
+                    for (int k = 0; k < QW; ++k) lc[g][k] = colb[(size_t)(j - g) * NB + (size_t)(4 * k) * np];
 #pragma unroll
-                for (int k = 0; k < QW; ++k) lnext[k] = colb[(size_t)(j - 1) * NB + (size_t)(4 * k) * np];
-            load_tagged_block<R>(tag, j * NB, np, nr, epoch, status, [&](int t, int c) -> float& { return S.v[t][c]; });
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
+                    load_tagged_block<R>(tag, (j - g) * NB, np, nr, epoch, status,
+                                         [&](int t, int c) -> float& { return S.v[g][t][c]; });
+#pragma unroll
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
+#pragma unroll
+                    for (int k = 0; k < QW; ++k) SB.lt[g][(tid >> 6) + 4 * k][tid & 63] = lc[g][k];
             __syncthreads();
             float aj[R];
 #pragma unroll
             for (int c = 0; c < R; ++c) aj[c] = 0.f;
 #pragma unroll
-            for (int tt = 0; tt < QW; ++tt) axpy_row<R>(aj, SB.lt[r][q * QW + tt], &S.v[q * QW + tt][0]);
+            for (int g = 0; g < SG; ++g)
+                if (g < gn)
+#pragma unroll
+                    for (int tt = 0; tt < QW; ++tt)
+                        axpy_row<R>(aj, SB.lt[g][r][q * QW + tt], &S.v[g][q * QW + tt][0]);
             kahan_add(acc, comp, aj);
             __syncthreads();
         }
