@@ -385,8 +385,11 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
             // cheap far-field tiles fill the tail.  Band d starts at
             // d nt - d (d - 1) / 2.
             auto off = [nt_band](long long dd) { return dd * nt_band - dd * (dd - 1) / 2; };
-            const double h = 2.0 * nt_band + 1.0;
-            int d = (int)((h - sqrt(fmax(h * h - 8.0 * (double)b, 0.0))) * 0.5);
+            // a float estimate (an FP64 square root costs microseconds of
+            // latency here), corrected by the two loops below
+            const float h = 2.0f * nt_band + 1.0f;
+            int d = (int)((h - sqrtf(fmaxf(h * h - 8.0f * (float)b, 0.0f))) * 0.5f);
+            d = max(0, min(d, nt_band - 1));
             while (d > 0 && off(d) > b) --d;
             while (d + 1 < nt_band && off(d + 1) <= b) ++d;
             // band d, position b - off(d) along it
@@ -394,7 +397,7 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
             tile_ij[0] = tile_ij[1] + d;
         } else {
             // lower-triangular tile coordinates (TI >= TJ) from the linear tile index
-            int TI = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+            int TI = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
             while ((long long)(TI + 1) * (TI + 2) / 2 <= b) ++TI;
             while ((long long)TI * (TI + 1) / 2 > b) --TI;
             tile_ij[0] = TI;

@@ -651,7 +651,7 @@ __device__ __forceinline__ void syrk_body(T* __restrict__ L, int ld, int k0, lon
     extern __shared__ unsigned char smem_raw[];
     T* sa = reinterpret_cast<T*>(smem_raw);   // [NB][NB+1]  rows of block I
     T* sb = sa + NB * (NB + 1);               // [NB][NB+1]  rows of block J
-    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
     int J = (int)(b - (long long)I * (I + 1) / 2);
@@ -1082,7 +1082,7 @@ __global__ void __launch_bounds__(tc::WS_THREADS, 2) rest_update(const RestArgs 
 {
     extern __shared__ __align__(1024) unsigned char ws_smem[];
     const long long b = a.tb0 + blockIdx.x;
-    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    int I = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
     while ((long long)(I + 1) * (I + 2) / 2 <= b) ++I;
     while ((long long)I * (I + 1) / 2 > b) --I;
     const int J = (int)(b - (long long)I * (I + 1) / 2);
