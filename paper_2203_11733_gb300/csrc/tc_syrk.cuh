@@ -384,16 +384,17 @@ __device__ bool syrk_tile(float* __restrict__ L, int ld, int rI, int rJ, const u
 }
 
 // The same update of one 128 x 128 tile by a warp-specialised CTA of
-// WS_THREADS = 288 threads (syrk_tile_ws), for tiles that wait for nothing:
-// warp 8 allocates the TMEM and its lane 0 is the producer, which streams the
-// stages through the ring and issues the MMAs without ever waiting for the
-// epilogue, except before an accumulator is reused; warps 0-7 load C, drain
-// each chunk's accumulator into it (as in syrk_tile) and report every drain
-// on the accumulator's "drained" mbarrier (one arrival per warp).  The copy
-// stream is then never held up by the C loads, the drains or their barriers,
-// which with one thread doing both roles cost a K = 256 tile about 40 % of
-// its time.
-constexpr int WS_THREADS = 288;
+// WS_THREADS = 320 threads (syrk_tile_ws), for tiles that wait for nothing:
+// warp 9's lane 0 is the loader, which streams the stages through the ring,
+// refilling each buffer as soon as the MMAs that read it are done; warp 8
+// allocates the TMEM and its lane 0 issues the MMAs, waiting only for data
+// and, before an accumulator is reused, for its drain; warps 0-7 load C,
+// drain each chunk's accumulator into it (as in syrk_tile) and report every
+// drain on the accumulator's "drained" mbarrier (one arrival per warp).  The
+// copy stream is then held up neither by the C loads, the drains and their
+// barriers (with one thread in every role they cost a K = 256 tile about
+// 40 % of its time) nor by the MMA issuer's waits (another 5 %).
+constexpr int WS_THREADS = 320;
 constexpr int WS_SMEM_BYTES = NBUF * BUF_BYTES + 256;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
@@ -443,10 +444,21 @@ __device__ bool syrk_tile_ws(float* __restrict__ L, int ld, int rI, int rJ, cons
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     int ok = 1;
-    if (warp == 8) {
+    if (warp == 9) {
+        // the loader: every stage into its buffer as soon as the MMAs that
+        // read the buffer's previous stage are done
         if (lane == 0) {
             const uint64_t pol = policy_evict_last();
-            auto issue = [&](int s, int b) {
+            int issued[NBUF];   // phases started on each full barrier, for the drain after a failure
+            for (int b = 0; b < NBUF; ++b) issued[b] = 0;
+            for (int s = 0; s < nst; ++s) {
+                const int b = s % NBUF;
+                if (s >= NBUF && !mbar_wait_bounded(empty(b), (uint32_t)((s / NBUF) - 1) & 1u)) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (*s_fail) break;
+                ++issued[b];
                 mbar_expect_tx(full(b), (diag ? 2u : 4u) * STAGE_BYTES);
                 const size_t o = (size_t)(st0 + s) * stage_stride;
                 bulk_g2s(part(b, 0), hi + o + (size_t)ia * STAGE_BYTES, STAGE_BYTES, full(b), pol);
@@ -455,16 +467,21 @@ __device__ bool syrk_tile_ws(float* __restrict__ L, int ld, int rI, int rJ, cons
                     bulk_g2s(part(b, 2), hi + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
                     bulk_g2s(part(b, 3), lo + o + (size_t)ja * STAGE_BYTES, STAGE_BYTES, full(b), pol);
                 }
-            };
-            // phases started on each barrier, for the drain after a failed wait
-            int loads[NBUF], commits[NBUF], acommits[2] = {0, 0};
-            for (int b = 0; b < NBUF; ++b) loads[b] = commits[b] = 0;
-            const uint32_t idesc = make_idesc();
-            const int pre = nst < NBUF ? nst : NBUF;
-            for (int s = 0; s < pre; ++s) {
-                issue(s, s);
-                ++loads[s];
             }
+            // after a failure the copies issued so far land before the
+            // shared memory is released
+            if (*s_fail)
+                for (int b = 0; b < NBUF; ++b)
+                    if (issued[b] > 0) mbar_wait_bounded(full(b), (uint32_t)(issued[b] - 1) & 1u);
+        }
+        __syncwarp();
+    } else if (warp == 8) {
+        // the MMA issuer: waits only for data and for drained accumulators
+        if (lane == 0) {
+            // phases started on each barrier, for the drain after a failed wait
+            int commits[NBUF], acommits[2] = {0, 0};
+            for (int b = 0; b < NBUF; ++b) commits[b] = 0;
+            const uint32_t idesc = make_idesc();
             int s = 0;
             for (int c = 0; c < nch && ok; ++c) {
                 // accumulator c % 2 is free once every warp has drained chunk c - 2
@@ -495,17 +512,6 @@ __device__ bool syrk_tile_ws(float* __restrict__ L, int ld, int rI, int rJ, cons
                                      empty(b))
                                  : "memory");
                     ++commits[b];
-                    // refill the previous stage's buffer once its MMAs have read it
-                    const int sp = s - 1;
-                    if (sp >= 0 && sp + NBUF < nst) {
-                        const int bp = sp % NBUF;
-                        if (!mbar_wait_bounded(empty(bp), (uint32_t)(sp / NBUF) & 1u)) {
-                            ok = 0;
-                            break;
-                        }
-                        issue(sp + NBUF, bp);
-                        ++loads[bp];
-                    }
                 }
                 if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -514,13 +520,11 @@ __device__ bool syrk_tile_ws(float* __restrict__ L, int ld, int rI, int rJ, cons
                 ++acommits[c & 1];
             }
             if (!ok) {
-                // let the copies and MMAs issued so far finish before the
-                // shared memory and TMEM are released
+                // let the MMAs issued so far finish before the shared memory
+                // and TMEM are released (the loader drains its copies)
                 *s_fail = 1;
-                for (int b = 0; b < NBUF; ++b) {
-                    if (loads[b] > 0) mbar_wait_bounded(full(b), (uint32_t)(loads[b] - 1) & 1u);
+                for (int b = 0; b < NBUF; ++b)
                     if (commits[b] > 0) mbar_wait_bounded(empty(b), (uint32_t)(commits[b] - 1) & 1u);
-                }
                 for (int a = 0; a < 2; ++a)
                     if (acommits[a] > 0) mbar_wait_bounded(accf(a), (uint32_t)(acommits[a] - 1) & 1u);
             }
