@@ -95,7 +95,9 @@ typedef struct {
 typedef struct {
     double q_near_fp64;   /* gap / largest edge below which a pair uses the
                              closed form in FP64 mode (12) */
-    double q_near_mixed;  /* same in mixed mode (1.0) */
+    double q_near_mixed;  /* mixed mode: below 0.5 every pair takes the closed
+                             form, below q_near_mixed (1.0) the pairs whose
+                             largest edges differ by more than 1.5x */
     double ir_tol;        /* relative residual target of refinement (1e-11) */
     int ir_max_iter;      /* refinement iterations at most (10) */
     int nb;               /* Cholesky block size: 64 */

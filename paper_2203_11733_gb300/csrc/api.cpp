@@ -83,9 +83,10 @@ gbem_tuning default_tuning()
 {
     gbem_tuning t{};
     t.q_near_fp64 = 12.0;
-    // below q = 1 the FP32 6-point rule misses its 3e-7 target on elongated
+    // below q = 1 the FP32 6-point rule misses its 3e-7 target on large
     // panels next to small ones (40 x 10 um enclosure walls beside 1 um
-    // panels: 7.7e-6); the FP64 closed form is exact there
+    // panels: 7.7e-6); the FP64 closed form is exact there.  Pairs of similar
+    // sizes keep the 6-point rule down to q = 0.5 (the assembly's switch)
     t.q_near_mixed = 1.0;
     // |B - A X| / |B| <= 1e-11 makes X the exact solution of a system whose
     // matrix differs from the assembled one by at most 1e-11 relative (the

@@ -336,6 +336,8 @@ __device__ typename FarVal<T>::type far_entry(const TileGeo& G, int s, int t)
 }
 
 constexpr int kThreads = 256;
+// mixed mode: gap ratio below which every pair uses the closed form
+constexpr float kMixedCfAll = 0.5f;
 constexpr int kPairs = GBEM_TILE * GBEM_TILE;
 // Pair classes: 0 near parallel, 1 near perpendicular, 2 + 2 (n - 1) + o for
 // a far pair of order n = 1..6 (o = 1 if perpendicular).
@@ -479,8 +481,16 @@ __device__ __forceinline__ void tile_body(const DevPanels& g, int np, float q_ne
             // below 2e-12 relative, else use quadrature when an order fits.
             const float R = gap + G.lmax[s] + G.lmax[t];
             const bool cf_ok = (q < q_near) && (R * R * R * R <= 1.8e4f * G.area[s] * G.area[t]);
+            // mixed mode: the FP64 closed form below q = 0.5 for every pair,
+            // and below q_near only for pairs whose largest edges differ by
+            // more than 1.5x (there the FP32 6-point rule can miss its target:
+            // 3.1e-6 on the paper's Table 2 partition with a 6x limit; for
+            // the others it meets it at a fraction of the closed form's cost,
+            // about 5000 FP64 operations a pair on this part)
+            const bool mixed_cf =
+                q < kMixedCfAll || (q < q_near && fmaxf(G.lmax[s], G.lmax[t]) > 1.5f * fminf(G.lmax[s], G.lmax[t]));
             int order = 0;
-            if (MIXED ? (q >= q_near) : !cf_ok) {
+            if (MIXED ? !mixed_cf : !cf_ok) {
 #pragma unroll
                 for (int m = GBEM_GL_MAX; m >= 1; --m)
                     if (q >= c_qmin[mode][m]) order = m;
