@@ -691,11 +691,11 @@ gbem_status gbem_factor(gbem_matrix_t* m, gbem_stream stream)
         if (!m->Linv) m->Linv = mat_alloc<float>(m, nblk * m->nb * m->nb, s);
         if (!m->split) m->split = mat_alloc<unsigned char>(m, cholesky_f32_split_bytes(m->np), s);
         if (!m->Linv || !m->split) return GBEM_ERR_OOM;
-        if (!m->side.stream && !ctx->side_pool.empty()) {
+        if (ctx->side_stream && !m->side.stream && !ctx->side_pool.empty()) {
             m->side = ctx->side_pool.back();
             ctx->side_pool.pop_back();
         }
-        if (!m->side.stream) {
+        if (ctx->side_stream && !m->side.stream) {
             // the stream of the rest updates, at the lowest priority (the
             // factorisation's own launches take the highest); without it they
             // run on the caller's stream

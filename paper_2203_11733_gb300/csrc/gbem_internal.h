@@ -81,6 +81,9 @@ struct gbem_ctx_s {
     bool keep_spare = true;
     // side streams of destroyed matrices (idle), for the next matrices' factors
     std::vector<SideStream> side_pool;
+    // mixed factors run their rest updates on a second stream; off, they run
+    // on the caller's stream (the server's workers, already concurrent)
+    bool side_stream = true;
 };
 
 // Kernels launched by the library in this process.

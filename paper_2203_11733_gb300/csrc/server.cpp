@@ -217,6 +217,9 @@ gbem_status gbem_server_create(int device, size_t hbm_budget, int slots, gbem_pr
         // a worker's next request has its own size and its memory is
         // reserved at admission: keep no buffers between requests
         if (st == GBEM_OK) ctx->keep_spare = false;
+        // the workers already run factorisations side by side: each keeps
+        // its rest updates on its own stream instead of forking a second one
+        if (st == GBEM_OK) ctx->side_stream = false;
         if (st == GBEM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = GBEM_ERR_CUDA;
         if (st != GBEM_OK) {
             if (ctx) gbem_destroy(ctx);
