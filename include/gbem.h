@@ -164,6 +164,27 @@ typedef struct {
 gbem_status gbem_mesh_graded(gbem_ctx* ctx, const gbem_box* boxes, int nbox,
                              const gbem_partition_params* params, gbem_mesh_t** out);
 
+/* Error-driven refinement of a mesh (Sec. 3.2, Proposition "error": the
+ * charge error on a net is bounded by C sup_j |I_j| sup_{x in I_j} |dq/dtau|).
+ * density[i] is the charge density of panel i of `mesh` (in the order of
+ * gbem_mesh_panels) from a solve for the net of interest, e.g. X_i / |I_i|
+ * for its column of X; only differences and ratios of it matter.  The
+ * tangential derivative on panel j is estimated from the panels of the same
+ * conductor that share a segment of its boundary (across face edges too; a
+ * common corner alone does not count) as the largest
+ * |density_k - density_j| / |c_k - c_j| (c: panel centres), and the
+ * indicator is eta_j = |I_j| times that.  Every panel with
+ * eta_j >= theta * max_k eta_k (0 <= theta <= 1; nothing when that maximum
+ * is 0) is bisected across its longer edge (the first in-plane axis on a
+ * tie); the others are kept.  *out receives a new mesh of the same context,
+ * conductor ids kept, in the library's panel order; eta (optional, mesh->n
+ * entries) the indicators; n_marked (optional) the number of bisected
+ * panels.  The input mesh is not changed.  Errors: GBEM_ERR_ARG for a NULL
+ * argument, theta outside [0, 1], a non-finite density or more than 2e6
+ * panels; GBEM_ERR_OOM. */
+gbem_status gbem_mesh_refine(const gbem_mesh_t* mesh, const double* density, double theta, double* eta,
+                             gbem_mesh_t** out, int* n_marked);
+
 /* Build a mesh from an explicit panel list, kept in the given order.
  * axis[i] in {0,1,2} is the panel's normal axis; geo[5*i..5*i+4] =
  * {c, lo0, hi0, lo1, hi1}: the plane coordinate and the extents along the two

@@ -12,6 +12,11 @@ It implements, plainly and slowly, every step of the extraction:
 * ``entries`` / ``assemble`` -- the Galerkin matrix of Eq. "matrix",
                          a_ij = (1/(4 pi |I_i||I_j|)) int int 1/|x-y|, computed
                          in ``gbem_oracle.c`` (see its header for the method).
+* ``refine``          -- the error-driven refinement behind Sec. 3.2's
+                         Proposition "error" (charge error bounded by
+                         C sup_j |I_j| sup |dq/dtau| on I_j): indicators from
+                         the densities of touching panels, bisection of the
+                         panels with the largest ones.
 * ``capacitance``     -- the right-hand sides b of Eq. "lineareq1" (f0 = 1 on
                          the main net, 0 elsewhere, Sec. 3.1), the solve A X = b
                          by Cholesky (Sec. 3.2: A is symmetric positive
@@ -229,6 +234,71 @@ def mesh_graded(boxes, main, p1, p2, p3, p5, h_max=0.0, enclosure=None):
         refine(k, plane, a0, b0, a1, b1, c, p1 if toward else p1 * p2)
     return (np.asarray(axis, dtype=np.int32), np.asarray(geo, dtype=np.float64).reshape(-1, 5),
             np.asarray(cond, dtype=np.int32))
+
+
+def refine(axis, geo, cond, density, theta: float):
+    """Error-driven refinement (Sec. 3.2, Proposition "error": the charge
+    error on a net is at most C sup_j |I_j| sup_{x in I_j} |dq/dtau|).
+
+    The density is constant on each panel, so its tangential derivative on
+    panel j is estimated with difference quotients to the panels that share a
+    piece of its boundary: the same conductor and closed rectangles that meet
+    in a segment of positive length (also across the edge between two faces;
+    a common corner alone does not count), quotient
+    |density_k - density_j| / |centre_k - centre_j|, the largest one kept.
+    eta_j = |I_j| times it.  Panels with eta_j >= theta * max(eta) (none when
+    max(eta) is 0) are halved across their longer edge (the first in-plane
+    axis on a tie).  Plain O(N^2) neighbour search.
+
+    Returns (axis, geo, cond) of the refined panels (input order, each
+    bisected panel replaced by its lower half then its upper half), eta and
+    the number of bisected panels."""
+    axis = np.asarray(axis, dtype=np.int64)
+    geo = np.asarray(geo, dtype=np.float64).reshape(-1, 5)
+    cond = np.asarray(cond)
+    d = np.asarray(density, dtype=np.float64)
+    n = len(axis)
+    lo = np.zeros((n, 3))
+    hi = np.zeros((n, 3))
+    for i in range(n):
+        k = int(axis[i])
+        p = 1 if k == 0 else 0
+        q = 1 if k == 2 else 2
+        lo[i, k] = hi[i, k] = geo[i, 0]
+        lo[i, p], hi[i, p] = geo[i, 1], geo[i, 2]
+        lo[i, q], hi[i, q] = geo[i, 3], geo[i, 4]
+    ctr = 0.5 * (lo + hi)
+    area = (geo[:, 2] - geo[:, 1]) * (geo[:, 4] - geo[:, 3])
+    tol = 1e-9 * (1.0 + np.max(np.abs(geo)))
+    grad = np.zeros(n)
+    for j in range(n):
+        ov = np.minimum(hi[j], hi) - np.maximum(lo[j], lo)   # overlap per axis
+        touch = np.all(ov >= -tol, axis=1) & (np.max(ov, axis=1) > tol)
+        touch &= cond == cond[j]
+        touch[j] = False
+        k = np.nonzero(touch)[0]
+        if len(k):
+            dist = np.sqrt(np.sum((ctr[k] - ctr[j]) ** 2, axis=1))
+            grad[j] = np.max(np.abs(d[k] - d[j]) / dist)
+    eta = area * grad
+    emax = eta.max() if n else 0.0
+    a2, g2, c2 = [], [], []
+    marked = 0
+    for i in range(n):
+        c0, l0, h0, l1, h1 = geo[i]
+        if not (emax > 0.0 and eta[i] >= theta * emax):
+            a2.append(axis[i]); g2.append((c0, l0, h0, l1, h1)); c2.append(cond[i])
+            continue
+        marked += 1
+        if h0 - l0 >= h1 - l1:
+            m = 0.5 * (l0 + h0)
+            halves = [(c0, l0, m, l1, h1), (c0, m, h0, l1, h1)]
+        else:
+            m = 0.5 * (l1 + h1)
+            halves = [(c0, l0, h0, l1, m), (c0, l0, h0, m, h1)]
+        for h_ in halves:
+            a2.append(axis[i]); g2.append(h_); c2.append(cond[i])
+    return (np.array(a2, np.int32), np.array(g2, np.float64).reshape(-1, 5), np.array(c2, np.int32), eta, marked)
 
 
 def areas(geo: np.ndarray) -> np.ndarray:

@@ -556,6 +556,42 @@ gbem_status gbem_mesh_graded(gbem_ctx* ctx, const gbem_box* boxes, int nbox, con
     return GBEM_OK;
 }
 
+gbem_status gbem_mesh_refine(const gbem_mesh_t* mesh, const double* density, double theta, double* eta,
+                             gbem_mesh_t** out, int* n_marked)
+{
+    if (!mesh || !density || !out) return GBEM_ERR_ARG;
+    *out = nullptr;
+    gbem_ctx* ctx = mesh->ctx;
+    if (!(theta >= 0.0 && theta <= 1.0)) return ctx_fail(ctx, GBEM_ERR_ARG, "theta outside [0, 1]");
+    for (int i = 0; i < mesh->n; ++i)
+        if (!std::isfinite(density[i])) return ctx_fail(ctx, GBEM_ERR_ARG, "density not finite");
+    std::vector<int8_t> a;
+    std::vector<double> g, e;
+    std::vector<int32_t> c;
+    int nm = 0;
+    gbem_status st = mesh_refine(mesh->axis, mesh->geo, mesh->cond, density, theta, a, g, c, e, nm);
+    if (st != GBEM_OK) return st;
+    if (a.size() > 2000000) return ctx_fail(ctx, GBEM_ERR_ARG, "gbem_mesh_refine: more than 2e6 panels");
+    gbem_mesh_t* m = new (std::nothrow) gbem_mesh_t();
+    if (!m) return GBEM_ERR_OOM;
+    m->ctx = ctx;
+    m->axis = std::move(a);
+    m->geo = std::move(g);
+    std::vector<int32_t> raw(c.size());
+    for (size_t i = 0; i < c.size(); ++i) raw[i] = mesh->cond_ids[c[i]];   // the caller's conductor ids
+    compact_conductors(m, raw);
+    mesh_order(m->axis, m->geo, m->cond);
+    m->n = (int)m->axis.size();
+    if ((st = upload_mesh(ctx, m)) != GBEM_OK) {
+        delete m;
+        return st;
+    }
+    if (eta) std::memcpy(eta, e.data(), sizeof(double) * (size_t)mesh->n);
+    if (n_marked) *n_marked = nm;
+    *out = m;
+    return GBEM_OK;
+}
+
 gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis, const double* geo,
                                   const int32_t* cond, gbem_mesh_t** out)
 {

@@ -206,6 +206,12 @@ gbem_status mesh_build_graded(const gbem_box* boxes, int nbox, const gbem_partit
                               std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond_raw,
                               std::string& err);
 void mesh_order(std::vector<int8_t>& axis, std::vector<double>& geo, std::vector<int32_t>& cond);
+// Error-driven refinement of a panel list (gbem_mesh_refine): eta receives
+// the indicator per input panel, n_marked the number of bisected panels.
+gbem_status mesh_refine(const std::vector<int8_t>& axis, const std::vector<double>& geo,
+                        const std::vector<int32_t>& cond, const double* density, double theta,
+                        std::vector<int8_t>& axis_out, std::vector<double>& geo_out,
+                        std::vector<int32_t>& cond_out, std::vector<double>& eta, int& n_marked);
 void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<double>& nodes);
 
 // ---- kernels (assemble.cu, factor.cu, solve.cu)

@@ -371,3 +371,126 @@ gbem_status mesh_build_graded(const gbem_box* boxes, int nbox, const gbem_partit
     }
     return GBEM_OK;
 }
+
+// Error-driven refinement (Sec. 3.2, Proposition "error": a net's charge
+// error is bounded by C sup_j |I_j| sup_{x in I_j} |dq/dtau|).  With the
+// piecewise-constant density of a solve, the tangential derivative on panel j
+// is estimated from the panels that share a piece of its boundary (same
+// conductor, closed rectangles meeting in a segment of positive length,
+// across face edges too) as the largest |q_k - q_j| / |c_k - c_j| (c: panel
+// centres); eta_j = |I_j| times that.
+// Panels with eta_j >= theta max_k eta_k (when that maximum is positive) are
+// bisected across their longer edge (the first in-plane axis on a tie).
+// Neighbours are found by a sweep over the panels' boxes sorted along the
+// axis of the largest spread.
+gbem_status mesh_refine(const std::vector<int8_t>& axis, const std::vector<double>& geo,
+                        const std::vector<int32_t>& cond, const double* density, double theta,
+                        std::vector<int8_t>& axis_out, std::vector<double>& geo_out,
+                        std::vector<int32_t>& cond_out, std::vector<double>& eta, int& n_marked)
+{
+    const int n = (int)axis.size();
+    auto inplane = [](int k, int& p, int& q) {
+        p = k == 0 ? 1 : 0;
+        q = k == 2 ? 1 : 2;
+    };
+    // closed boxes and centres
+    std::vector<double> lo(3 * (size_t)n), hi(3 * (size_t)n), ctr(3 * (size_t)n), area(n);
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double* g = &geo[5 * (size_t)i];
+        int p, q;
+        inplane(axis[i], p, q);
+        const int k = axis[i];
+        lo[3 * i + k] = hi[3 * i + k] = ctr[3 * i + k] = g[0];
+        lo[3 * i + p] = g[1];
+        hi[3 * i + p] = g[2];
+        ctr[3 * i + p] = 0.5 * (g[1] + g[2]);
+        lo[3 * i + q] = g[3];
+        hi[3 * i + q] = g[4];
+        ctr[3 * i + q] = 0.5 * (g[3] + g[4]);
+        area[i] = (g[2] - g[1]) * (g[4] - g[3]);
+        for (int e = 0; e < 5; ++e) scale = std::max(scale, std::fabs(g[e]));
+    }
+    const double tol = 1e-9 * (1.0 + scale);
+    // sweep axis: the one with the largest spread of box starts
+    int ax = 0;
+    double best = -1.0;
+    for (int a = 0; a < 3; ++a) {
+        double mn = 1e300, mx = -1e300;
+        for (int i = 0; i < n; ++i) {
+            mn = std::min(mn, lo[3 * i + a]);
+            mx = std::max(mx, lo[3 * i + a]);
+        }
+        if (mx - mn > best) {
+            best = mx - mn;
+            ax = a;
+        }
+    }
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return lo[3 * a + ax] < lo[3 * b + ax]; });
+    std::vector<double> grad(n, 0.0);
+    for (int u = 0; u < n; ++u) {
+        const int j = order[u];
+        for (int w = u + 1; w < n; ++w) {
+            const int k = order[w];
+            if (lo[3 * k + ax] > hi[3 * j + ax] + tol) break;
+            if (cond[k] != cond[j]) continue;
+            // closed rectangles meeting in a segment of positive length
+            bool touch = true;
+            double longest = 0.0;
+            for (int a = 0; a < 3 && touch; ++a) {
+                const double ov = std::min(hi[3 * j + a], hi[3 * k + a]) - std::max(lo[3 * j + a], lo[3 * k + a]);
+                touch = ov >= -tol;
+                longest = std::max(longest, ov);
+            }
+            if (!touch || !(longest > tol)) continue;
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = ctr[3 * j + a] - ctr[3 * k + a];
+                d2 += d * d;
+            }
+            const double g = std::fabs(density[k] - density[j]) / std::sqrt(d2);
+            grad[j] = std::max(grad[j], g);
+            grad[k] = std::max(grad[k], g);
+        }
+    }
+    eta.assign(n, 0.0);
+    double eta_max = 0.0;
+    for (int i = 0; i < n; ++i) {
+        eta[i] = area[i] * grad[i];
+        eta_max = std::max(eta_max, eta[i]);
+    }
+    axis_out.clear();
+    geo_out.clear();
+    cond_out.clear();
+    n_marked = 0;
+    for (int i = 0; i < n; ++i) {
+        const double* g = &geo[5 * (size_t)i];
+        const bool mark = eta_max > 0.0 && eta[i] >= theta * eta_max;
+        auto push = [&](double l0, double h0, double l1, double h1) {
+            axis_out.push_back(axis[i]);
+            geo_out.push_back(g[0]);
+            geo_out.push_back(l0);
+            geo_out.push_back(h0);
+            geo_out.push_back(l1);
+            geo_out.push_back(h1);
+            cond_out.push_back(cond[i]);
+        };
+        if (!mark) {
+            push(g[1], g[2], g[3], g[4]);
+            continue;
+        }
+        ++n_marked;
+        if (g[2] - g[1] >= g[4] - g[3]) {
+            const double m = 0.5 * (g[1] + g[2]);
+            push(g[1], m, g[3], g[4]);
+            push(m, g[2], g[3], g[4]);
+        } else {
+            const double m = 0.5 * (g[3] + g[4]);
+            push(g[1], g[2], g[3], m);
+            push(g[1], g[2], m, g[4]);
+        }
+    }
+    return GBEM_OK;
+}

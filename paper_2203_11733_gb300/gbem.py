@@ -97,6 +97,7 @@ _SIGS = {
     "gbem_mesh_from_panels": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(_P)]),
     "gbem_mesh_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gbem_mesh_panels": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gbem_mesh_refine": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     "gbem_mesh_destroy": (None, [_P]),
     "gbem_assemble": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "gbem_factor": (ctypes.c_int, [_P, _P]),
@@ -552,6 +553,21 @@ def gbem_mesh_graded(ctx: Context, boxes, main: int, p1: float, p2: float, p3: f
     h = ctypes.c_void_p()
     ctx.check(ctx.lib.gbem_mesh_graded(ctx.h, arr, len(boxes), ctypes.byref(p), ctypes.byref(h)))
     return Mesh(ctx, h)
+
+
+def gbem_mesh_refine(mesh: Mesh, density, theta: float):
+    """gbem_mesh_refine: bisect the panels whose indicator |I_j| |dq/dtau|_j
+    is at least theta times the largest; density per panel of `mesh` (its
+    panel order).  Returns (new Mesh, indicators float64[n], panels bisected)."""
+    density = np.ascontiguousarray(density, dtype=np.float64)
+    if density.shape != (mesh.n,):
+        raise ValueError("density needs one value per panel")
+    eta = np.empty(mesh.n, np.float64)
+    h = ctypes.c_void_p()
+    nm = ctypes.c_int(0)
+    mesh.ctx.check(mesh.ctx.lib.gbem_mesh_refine(mesh.h, _ptr(density), float(theta), _ptr(eta), ctypes.byref(h),
+                                                 ctypes.byref(nm)))
+    return Mesh(mesh.ctx, h), eta, nm.value
 
 
 def gbem_mesh_from_panels(ctx: Context, axis, geo, cond) -> Mesh:
