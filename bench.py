@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=24,
                     help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch512", "serving", "partition"],
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "batch512", "serving", "partition", "unit_rates"],
                     help="headline: the three-layer bus (and the 2x2 bus as secondary); "
-                         "batch512 / serving: the batched and served forms")
+                         "batch512 / serving: the batched and served forms; unit_rates: the "
+                         "arithmetic-unit rates that bound the assembly, nothing else")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=1000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -361,15 +363,17 @@ KERNEL_NAMES = {
     "sweep": "sweep_fwd_f32/sweep_bwd_f32: persistent cooperative triangular sweeps (x_b = z_b - M_b x_p)",
     "residual": "residual_df: R = B - A X, compensated FP32 over float-pair storage",
 }
-# measured on this GB300 (profiles/gb300_alu_rates.md): operations per second
-MUFU_RSQRT_PER_S = 4.70e12
-DFMA_PER_S = 5.04e11
 # FP64 cost of one corner term of the near-field closed forms, in DFMA
-# equivalents of the measured library rates (sqrt 8.6, log 3.6, atan 29):
-# F = 2 log + 1 atan + 1 sqrt + about 25 arithmetic operations; H = 3 log +
-# 3 atan + 1 sqrt + about 40 (16 corner terms per pair)
-F_TERM_DFMA = 2 * 3.6 + 29 + 8.6 + 25
-H_TERM_DFMA = 3 * 3.6 + 3 * 29 + 8.6 + 40
+# equivalents of the library calls' rates measured on the GPU at hand
+# (gbem_unit_rates): F = 2 log + 1 atan + 1 sqrt + about 25 arithmetic
+# operations; H = 3 log + 3 atan + 1 sqrt + about 40 (16 corner terms per pair)
+def term_dfma(rates):
+    eq = {k: rates["dfma"] / rates[k] for k in ("dsqrt", "dlog", "datan")}
+    f = 2 * eq["dlog"] + eq["datan"] + eq["dsqrt"] + 25
+    h = 3 * eq["dlog"] + 3 * eq["datan"] + eq["dsqrt"] + 40
+    return f, h, eq
+
+
 # FP64 far-field evaluation (FP64 mode): 3 differences, r^2 (3), the rsqrt
 # estimate and its Newton step (4), the weighted sum (1)
 FAR_EVAL_DFMA_FP64 = 11.0
@@ -404,24 +408,26 @@ def traffic_per_launch(workload, kernel):
     return None
 
 
-def assembly_work(cls, mixed=True):
+def assembly_work(cls, rates, mixed=True):
     """Algorithmic work of one assembly from its 14 class counts: far-field
     1/r evaluations (n^4 per pair of order n) and FP64 corner-term work of
-    the near pairs, with the time each needs at the measured unit rates."""
+    the near pairs, with the time each needs at the unit rates `rates`
+    (gbem_unit_rates, operations per second)."""
+    f_term, h_term, _ = term_dfma(rates)
     far_evals = sum(n ** 4 * (int(cls[2 * n]) + int(cls[2 * n + 1])) for n in range(1, 7))
-    near_dfma = 16 * (F_TERM_DFMA * int(cls[0]) + H_TERM_DFMA * int(cls[1]))
+    near_dfma = 16 * (f_term * int(cls[0]) + h_term * int(cls[1]))
     if mixed:
-        t_far = far_evals / MUFU_RSQRT_PER_S
-        t_near = near_dfma / DFMA_PER_S
+        t_far = far_evals / rates["mufu_rsqrt"]
+        t_near = near_dfma / rates["dfma"]
     else:
         t_far = 0.0
-        t_near = (near_dfma + FAR_EVAL_DFMA_FP64 * far_evals) / DFMA_PER_S
+        t_near = (near_dfma + FAR_EVAL_DFMA_FP64 * far_evals) / rates["dfma"]
     return {"far_evaluations": far_evals, "near_pairs_parallel": int(cls[0]),
             "near_pairs_perpendicular": int(cls[1]), "near_fp64_dfma_equiv": near_dfma,
             "t_far_bound_ms": 1e3 * t_far, "t_near_bound_ms": 1e3 * t_near}
 
 
-def kernel_table(kst, steps, n, cls, peaks, workload):
+def kernel_table(kst, steps, n, cls, peaks, workload, rates):
     """Per traced kernel: time per step and launch, its algorithmic work rate
     and the fraction of the bound that applies to it."""
     out = {}
@@ -443,11 +449,12 @@ def kernel_table(kst, steps, n, cls, peaks, workload):
                       "method_bytes_per_launch": 4.0 * n * n / (d["launches"] / steps),
                       "traffic": traffic_per_launch(workload, "factor")})
         elif k == "assemble":
-            w = assembly_work(cls)
+            w = assembly_work(cls, rates)
             t_bound = max(w["t_far_bound_ms"], w["t_near_bound_ms"]) * 1e-3
             e.update({"bound": "alu", "unit": "1/r evaluations/s",
-                      "achieved": w["far_evaluations"] / t, "peak": MUFU_RSQRT_PER_S,
-                      "peak_source": "measured MUFU rsqrt rate (profiles/gb300_alu_rates.md)",
+                      "achieved": w["far_evaluations"] / t, "peak": rates["mufu_rsqrt"],
+                      "peak_source": "MUFU rsqrt rate measured on this GPU before the timed region "
+                                     "(gbem_unit_rates)",
                       "frac_of_alu_bound": t_bound / t, "work": w, "traffic": None,
                       "work_per_launch": w["far_evaluations"]})
         else:
@@ -490,6 +497,8 @@ def run_ours(args):
     eps_r = W.EPS_R_SIO2
     ctx = gbem.Context(local)
     stream = torch.cuda.Stream()
+    # unit rates of this GPU, the assembly's roofline (measured outside the timed region)
+    rates = ctx.unit_rates(stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
 
     def barrier():
@@ -596,7 +605,7 @@ def run_ours(args):
             err_mixed = float(np.max(np.abs(C_mixed - C_ref)) / scale)
             err_fp64 = float(np.max(np.abs(C_fp64 - C_ref)) / scale)
         peaks = _peaks()
-        kern = kernel_table(kst, steps, n, cls, peaks, workload)
+        kern = kernel_table(kst, steps, n, cls, peaks, workload, rates)
         kern["traced_ms_per_step"] = ms_traced / steps
         asm_ms = stats["ms"][PHASES.index("assemble")] / steps
         return {
@@ -651,6 +660,7 @@ def run_ours(args):
             "roofline": roofline(kern, head["kst"], args.steps, head["ms_traced_step"]),
             "kernels": kern,
             "assembly_class_counts": head["class_counts"],
+            "unit_rates_per_s": rates,
             "clocks": clk,
         }
         if sec is not None:
@@ -1032,6 +1042,31 @@ def run_partition(args):
     ctx.close()
 
 
+def run_unit_rates():
+    """One JSON line: the rates gbem_unit_rates measures on cuda:0, the SM
+    clock around the call, and each FP64 library call in DFMA equivalents."""
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem
+    B.build()
+    gbem.load()
+    torch.cuda.set_device(0)
+    ctx = gbem.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.unit_rates(stream)                     # warm the clocks
+    clocks = ClockSampler(0)
+    clocks.start()
+    clocks.begin()
+    rates = ctx.unit_rates(stream)
+    clocks.end()
+    clk = clocks.stop()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+    per_sm_clk = {k: v / (sms * mhz * 1e6) for k, v in rates.items()} if mhz else None
+    print(json.dumps({"unit_rates_per_s": rates, "per_sm_per_clock": per_sm_clk, "sms": sms,
+                      "dfma_equivalents": term_dfma(rates)[2], "clocks": clk}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1042,6 +1077,8 @@ def main():
         run_serving(args)
     elif args.workload == "partition":
         run_partition(args)
+    elif args.workload == "unit_rates":
+        run_unit_rates()
     else:
         run_ours(args)
 

@@ -262,6 +262,31 @@ gbem_status gbem_solve_noalloc(gbem_matrix_t* mat, const double* B_dev, int nrhs
  * stream. */
 gbem_status gbem_selftest_wait(gbem_ctx* ctx, int set_flag, double limit_ms, gbem_stream stream);
 
+/* Arithmetic units whose throughput bounds the assembly: the far field's 1/r
+ * evaluations go through the MUFU reciprocal square root, the near field's
+ * closed forms (Eqs. "F" and "H", Appendix) through FP64 arithmetic and the
+ * FP64 log, atan and sqrt. */
+typedef enum {
+    GBEM_RATE_DFMA = 0,        /* FP64 fused multiply-add */
+    GBEM_RATE_FFMA = 1,        /* FP32 fused multiply-add */
+    GBEM_RATE_MUFU_RSQRT = 2,  /* FP32 approximate reciprocal square root */
+    GBEM_RATE_DSQRT = 3,       /* FP64 sqrt (with one FP64 add) */
+    GBEM_RATE_DLOG = 4,        /* FP64 log (with one FP64 add) */
+    GBEM_RATE_DATAN = 5,       /* FP64 atan (with one FP64 add) */
+    GBEM_RATE_DRSQRT = 6,      /* FP64 rsqrt (with one FP64 add) */
+    GBEM_RATE_COUNT = 7
+} gbem_unit_rate;
+
+/* Measurement helper with no counterpart in the paper: the roofline of the
+ * assembly needs the rates of the units above on the GPU at hand.  Writes
+ * rates[k] = operations per second over the whole device (an FMA counts as
+ * one operation) for k = 0 .. n_rates-1 (1 <= n_rates <= GBEM_RATE_COUNT),
+ * each the best of three timed launches of independent dependency chains
+ * after one warm-up, 8 CTAs of 256 threads per SM.  Takes about 0.3 s;
+ * allocates 2.5 MB (152 SMs) from the context for the duration of the call;
+ * waits for the stream.  Rates reflect the clocks at the time of the call. */
+gbem_status gbem_unit_rates(gbem_ctx* ctx, double* rates, int n_rates, gbem_stream stream);
+
 /* Maxwell capacitance matrix in farads, n_c x n_c row-major into C_host:
  * C[m][k] = charge on conductor m with conductor k at 1 V and the others at
  * 0 V (Eqs. "lineareq1", "electriccharge"), rows and columns in ascending

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgbem.so")
 
-SOURCES = ["api.cpp", "mesh.cpp", "batch.cpp", "server.cpp", "assemble.cu", "factor.cu", "solve.cu", "solve_noalloc.cu"]
+SOURCES = ["api.cpp", "mesh.cpp", "batch.cpp", "server.cpp", "assemble.cu", "factor.cu", "solve.cu", "solve_noalloc.cu",
+           "unit_rates.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", INCLUDE, "-I", CSRC]

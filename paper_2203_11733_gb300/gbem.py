@@ -30,6 +30,8 @@ STATUS = {
 }
 GBEM_FP64 = 0
 GBEM_MIXED = 1
+# gbem_unit_rate, in enum order
+UNIT_RATE_NAMES = ("dfma", "ffma", "mufu_rsqrt", "dsqrt", "dlog", "datan", "drsqrt")
 EPS0 = 8.8541878128e-12
 
 
@@ -109,6 +111,7 @@ _SIGS = {
     "gbem_matrix_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "gbem_matrix_class_counts": (ctypes.c_int, [_P, _P]),
     "gbem_selftest_wait": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P]),
+    "gbem_unit_rates": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "gbem_matrix_destroy": (None, [_P]),
     "gbem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbem_get_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -267,6 +270,13 @@ class Context:
         that is set (GBEM_OK) or withheld (GBEM_ERR_TIMEOUT)."""
         return int(self.lib.gbem_selftest_wait(self.h, 1 if set_flag else 0, float(limit_ms),
                                                _stream_handle(stream)))
+
+    def unit_rates(self, stream=None) -> dict:
+        """gbem_unit_rates: operations per second of the units that bound the
+        assembly, measured on this context's GPU."""
+        out = (ctypes.c_double * len(UNIT_RATE_NAMES))()
+        self.check(self.lib.gbem_unit_rates(self.h, out, len(UNIT_RATE_NAMES), _stream_handle(stream)))
+        return {k: float(out[i]) for i, k in enumerate(UNIT_RATE_NAMES)}
 
     def bytes_in_use(self) -> int:
         return int(self.lib.gbem_bytes_in_use(self.h))

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI: the library loads and exports every entry
 point declared in include/gbem.h, and the host mesher (Sec. 3.1/3.3) builds
 the same panels as the oracle's mesher.  No GPU is touched."""
+import ctypes
 import os
 import re
 
@@ -109,6 +110,13 @@ def test_host_context_refuses_compute(lib):
     with pytest.raises(gbem.GbemError) as e:
         m.assemble(gbem.GBEM_FP64, stream=0)
     assert e.value.status == -9
+    with pytest.raises(gbem.GbemError) as e:
+        ctx.unit_rates(stream=0)
+    assert e.value.status == -9
+    out = (ctypes.c_double * 8)()
+    assert lib.gbem_unit_rates(ctx.h, out, 0, None) == -1           # no rate asked for
+    assert lib.gbem_unit_rates(ctx.h, out, 8, None) == -1           # more than GBEM_RATE_COUNT
+    assert lib.gbem_unit_rates(None, out, 1, None) == -1
 
 
 def test_graded_division_matches_definition(lib):
