@@ -32,6 +32,15 @@
  * Gauss-Legendre nodes are computed here by Newton's method on the Legendre
  * recurrence.
  *
+ * Double layer (Sec. 4, the integrals Q_ij of the multi-dielectric system):
+ *     d_ij = 1 / (4 pi) * int_{I_i} int_{I_j} (x_k - y_k) / |x - y|^3 dy dx,
+ * k the normal axis of I_j, i.e. Q_ij for the normal +e_k of I_j.  Same
+ * method: the inner integral is the exact solid-angle function of the
+ * rectangle I_j seen from x (corner sum of atan(s t / (w rho))), the outer
+ * one the same split tanh-sinh / adaptive Gauss-Legendre quadrature over
+ * I_i (never swapped: the kernel is not symmetric), and separated pairs a
+ * direct 4-D Gauss-Legendre rule.  Coplanar pairs give 0.
+ *
  * Coordinates: a panel has a normal axis k in {0,1,2}, a plane coordinate c,
  * and extents [lo0,hi0] x [lo1,hi1] along the two remaining axes taken in
  * increasing axis order.  geo[5*i .. 5*i+4] = {c, lo0, hi0, lo1, hi1}.
@@ -127,6 +136,27 @@ static double orc_point_potential(const orc_panel* P, const double x[3])
     return orc_K(s1, t1, w) - orc_K(s0, t1, w) - orc_K(s1, t0, w) + orc_K(s0, t0, w);
 }
 
+/* atan(s t / (w rho)): d^2 / ds dt = w / rho^3 (w != 0). */
+static double orc_L(double s, double t, double w)
+{
+    if (s == 0.0 || t == 0.0) return 0.0;
+    double rho = sqrt(s * s + t * t + w * w);
+    return atan(s * t / (w * rho));
+}
+
+/* int_P (x_k - y_k) / |x - y|^3 dy, k the normal axis of P: the solid angle
+ * that P subtends at x, signed by the side of P's plane x lies on; 0 in the
+ * plane. */
+static double orc_point_dlayer(const orc_panel* P, const double x[3])
+{
+    int p = P->a[0], q = P->a[1];
+    double w = x[P->k] - P->c;
+    if (w == 0.0) return 0.0;
+    double s0 = P->lo[p] - x[p], s1 = P->hi[p] - x[p];
+    double t0 = P->lo[q] - x[q], t1 = P->hi[q] - x[q];
+    return orc_L(s1, t1, w) - orc_L(s0, t1, w) - orc_L(s1, t0, w) + orc_L(s0, t0, w);
+}
+
 /* ------------------------------------------------------------------ */
 /* Gauss-Legendre nodes on [-1,1] by Newton iteration on P_n.          */
 /* ------------------------------------------------------------------ */
@@ -199,6 +229,8 @@ int orc_gl_nodes(int n, double* x, double* w)
 typedef struct {
     const orc_panel* Pi;   /* outer panel (gives the plane) */
     const orc_panel* Pj;   /* inner panel */
+    int kind;              /* 0: single layer 1/r, 1: double layer */
+    double floor;          /* absolute size below which differences count as converged */
 } orc_outer;
 
 static double orc_outer_f(const orc_outer* O, double u0, double u1)
@@ -207,7 +239,7 @@ static double orc_outer_f(const orc_outer* O, double u0, double u1)
     x[O->Pi->k] = O->Pi->c;
     x[O->Pi->a[0]] = u0;
     x[O->Pi->a[1]] = u1;
-    return orc_point_potential(O->Pj, x);
+    return O->kind ? orc_point_dlayer(O->Pj, x) : orc_point_potential(O->Pj, x);
 }
 
 static double orc_outer_gl(const orc_outer* O, const double lo[2], const double hi[2], int n)
@@ -231,10 +263,11 @@ static double orc_outer_adaptive(const orc_outer* O, const double lo[2], const d
     double i8 = orc_outer_gl(O, lo, hi, 8);
     double i16 = orc_outer_gl(O, lo, hi, 16);
     double diff = fabs(i16 - i8);
-    if (diff <= 1e-14 * fabs(i16)) return i16;
+    double mag = fmax(fabs(i16), O->floor);
+    if (diff <= 1e-14 * mag) return i16;
     /* below 1e-12 the two orders differ by the rounding of the corner sums,
      * not by truncation; subdividing further cannot improve on that */
-    if (depth >= 4 && diff <= 1e-12 * fabs(i16)) return i16;
+    if (depth >= 4 && diff <= 1e-12 * mag) return i16;
     if (depth >= 7) {
         ++*nfail;
         return i16;
@@ -293,7 +326,7 @@ static double orc_outer_ts(const orc_outer* O, const double lo[2], const double 
         /* the tanh-sinh weights do not depend on h, so the running sum over
          * every point of this level's grid times h^2 is this level's estimate */
         est = total * h * h;
-        if (L > 2 && fabs(est - prev) <= 1e-14 * fabs(est)) return est;
+        if (L > 2 && fabs(est - prev) <= 1e-14 * fmax(fabs(est), O->floor)) return est;
         prev = est;
     }
     ++*nfail;
@@ -331,10 +364,10 @@ static int orc_breaks(const orc_panel* Pj, int d, double lo, double hi, double* 
     return n;
 }
 
-/* Split-outer method: int_{Pi} [int_{Pj} 1/|x-y| dy] dx */
-static double orc_pair_split(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
+/* Split-outer method: int_{Pi} [int_{Pj} kernel dy] dx */
+static double orc_pair_split_k(const orc_panel* Pi, const orc_panel* Pj, int kind, double floor, int* nfail)
 {
-    orc_outer O = {Pi, Pj};
+    orc_outer O = {Pi, Pj, kind, floor};
     double b0[4], b1[4];
     int p = Pi->a[0], q = Pi->a[1];
     int n0 = orc_breaks(Pj, p, Pi->lo[p], Pi->hi[p], b0);
@@ -356,8 +389,14 @@ static double orc_pair_split(const orc_panel* Pi, const orc_panel* Pj, int* nfai
     return s;
 }
 
-/* Direct 4-D tensor GL of 1/|x-y| on two well-separated panels. */
-static double orc_pair_gl4(const orc_panel* Pi, const orc_panel* Pj, int n)
+static double orc_pair_split(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
+{
+    return orc_pair_split_k(Pi, Pj, 0, 0.0, nfail);
+}
+
+/* Direct 4-D tensor GL of 1/|x-y| (kind 0) or (x_k - y_k)/|x-y|^3, k the
+ * normal axis of Pj (kind 1), on two well-separated panels. */
+static double orc_pair_gl4_k(const orc_panel* Pi, const orc_panel* Pj, int n, int kind)
 {
     int pi0 = Pi->a[0], pi1 = Pi->a[1], pj0 = Pj->a[0], pj1 = Pj->a[1];
     double mi0 = 0.5 * (Pi->lo[pi0] + Pi->hi[pi0]), hi0 = 0.5 * (Pi->hi[pi0] - Pi->lo[pi0]);
@@ -380,11 +419,41 @@ static double orc_pair_gl4(const orc_panel* Pi, const orc_panel* Pj, int n)
                     y[pj0] = mj0 + hj0 * orc_glx[n][c];
                     y[pj1] = mj1 + hj1 * orc_glx[n][d];
                     double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
-                    sy += orc_glw[n][c] * orc_glw[n][d] / sqrt(dx * dx + dy * dy + dz * dz);
+                    double r = sqrt(dx * dx + dy * dy + dz * dz);
+                    double f = kind ? (x[Pj->k] - y[Pj->k]) / (r * r * r) : 1.0 / r;
+                    sy += orc_glw[n][c] * orc_glw[n][d] * f;
                 }
             s += wx * sy;
         }
     return s * hi0 * hi1 * hj0 * hj1;
+}
+
+static double orc_pair_gl4(const orc_panel* Pi, const orc_panel* Pj, int n)
+{
+    return orc_pair_gl4_k(Pi, Pj, n, 0);
+}
+
+/* int_{Pi} int_{Pj} (x_k - y_k)/|x-y|^3 dy dx, k = Pj->k (no 1/(4 pi)).
+ * Convergence tests are relative to the larger of the value and
+ * |Pi||Pj| / (gap + dmax)^2, the size of the integral of 1/|x-y|^2: a pair
+ * whose contributions cancel (perpendicular panels placed symmetrically)
+ * converges in absolute terms. */
+static double orc_pair_dl(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
+{
+    if (Pi->k == Pj->k && Pi->c == Pj->c) return 0.0;
+    double g = orc_gap(Pi, Pj);
+    double dmax = fmax(orc_diag(Pi), orc_diag(Pj));
+    double floor = orc_area(Pi) * orc_area(Pj) / ((g + dmax) * (g + dmax));
+    if (g >= 3.0 * dmax) {
+        double i8 = orc_pair_gl4_k(Pi, Pj, 8, 1);
+        double i10 = orc_pair_gl4_k(Pi, Pj, 10, 1);
+        if (fabs(i10 - i8) <= 5e-14 * fmax(fabs(i10), floor)) return i10;
+    } else if (g >= dmax) {
+        double i12 = orc_pair_gl4_k(Pi, Pj, 12, 1);
+        double i16 = orc_pair_gl4_k(Pi, Pj, 16, 1);
+        if (fabs(i16 - i12) <= 5e-14 * fmax(fabs(i16), floor)) return i16;
+    }
+    return orc_pair_split_k(Pi, Pj, 1, floor, nfail);
 }
 
 /* int_{Pi} int_{Pj} 1/|x-y| dy dx  (no 1/(4 pi), no area normalisation).
@@ -439,6 +508,43 @@ double orc_pair_integral(int axis_i, const double* geo_i, int axis_j, const doub
     double r = (method == 1) ? orc_pair_split(&Pi, &Pj, &nf) : orc_pair(&Pi, &Pj, &nf);
     if (nfail) *nfail = nf;
     return r;
+}
+
+double orc_rect_dlayer(int axis, const double* geo, const double* x)
+{
+    orc_panel P;
+    orc_make_panel(axis, geo, &P);
+    return orc_point_dlayer(&P, x);
+}
+
+/* Double-layer entries d_ij = (1/(4 pi)) int int (x_k - y_k)/r^3, k the normal
+ * axis of panel j, for m sampled pairs (Sec. 4, Q_ij for the normal +e_k). */
+int orc_dl_entries(int n, const int32_t* axis, const double* geo, int64_t m, const int32_t* I,
+                   const int32_t* J, double* out, int nthreads)
+{
+    orc_gl_init();
+    int nf_total = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : nf_total)
+    for (int64_t t = 0; t < m; ++t) {
+        int i = I[t], j = J[t];
+        if (i < 0 || j < 0 || i >= n || j >= n) {
+            out[t] = NAN;
+            continue;
+        }
+        orc_panel Pi, Pj;
+        orc_make_panel(axis[i], geo + 5 * (size_t)i, &Pi);
+        orc_make_panel(axis[j], geo + 5 * (size_t)j, &Pj);
+        int nf = 0;
+        double v = orc_pair_dl(&Pi, &Pj, &nf);
+        nf_total += nf;
+        out[t] = v / (4.0 * ORC_PI);
+    }
+    return nf_total;
 }
 
 /* Matrix entries a_ij = int int 1/r / (4 pi |I_i| |I_j|) for m sampled pairs. */
