@@ -58,10 +58,11 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=24,
                     help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch512", "serving", "partition", "unit_rates"],
+                    choices=["headline", "batch512", "serving", "partition", "unit_rates", "stack"],
                     help="headline: the three-layer bus (and the 2x2 bus as secondary); "
                          "batch512 / serving: the batched and served forms; unit_rates: the "
-                         "arithmetic-unit rates that bound the assembly, nothing else")
+                         "arithmetic-unit rates that bound the assembly, nothing else; stack: the "
+                         "multi-dielectric system of a layered stack")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=1000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -681,6 +682,198 @@ def run_ours(args):
     dist_stop(world)
 
 
+def stack_cpu_baseline(spec, rows_all: int = 16, rows_single: int = 2):
+    """The multi-dielectric oracle timed on the host cores on a bounded sample
+    of one extraction: its rate of single- and double-layer entries on whole
+    random rows of the system (all threads, and one thread), plus LAPACK's LU
+    and solve (scipy) at the full order, summed into one extraction."""
+    import numpy as np
+    import scipy.linalg as sla
+    from oracle import dielectric as D
+    from oracle import oracle as O
+    st = D.Stack(spec["lo"], spec["hi"], spec["z"], spec["eps_r"], spec["face_bc"])
+    m = D.mesh_stack(st, spec["boxes"], spec["h"], spec["h_outer"])
+    rows, _, _, ids = D.layout(m)
+    ra, rb = m["region_a"], m["region_b"]
+    regions = [np.nonzero((ra == a) | (rb == a))[0] for a in range(len(spec["eps_r"]))]
+    pairs = sum(len(P) ** 2 for P in regions)
+    rng = np.random.default_rng(11)
+    threads = O.max_threads()
+
+    def rate(nrows, nthreads):
+        I, K = [], []
+        for r in rng.integers(0, len(rows), nrows):
+            a, i = rows[r]
+            I.append(np.full(len(regions[a]), i))
+            K.append(regions[a])
+        I, K = np.concatenate(I), np.concatenate(K)
+        t0 = time.perf_counter()
+        D.slayer_entries(m["axis"], m["geo"], I, K, nthreads)
+        D.dlayer_entries(m["axis"], m["geo"], I, K, nthreads)
+        return len(I) / (time.perf_counter() - t0), len(I), time.perf_counter() - t0
+
+    r_all, e_all, s_all = rate(rows_all, threads)
+    r_one, e_one, s_one = rate(rows_single, 1)
+    n = len(rows)
+    A = np.random.default_rng(3).standard_normal((n, n)) + n * np.eye(n)
+    t0 = time.perf_counter()
+    f = sla.lu_factor(A, check_finite=False)
+    t_lu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sla.lu_solve(f, np.ones((n, len(ids))), check_finite=False)
+    t_solve = time.perf_counter() - t0
+    t_ext = pairs / r_all + t_lu + t_solve
+    return {"value": 1.0 / t_ext, "unit": "extractions/s", "cores": threads, "kind": "oracle",
+            "sample": f"{rows_all} whole random rows of the {n}-equation system ({e_all} pairs, single and "
+                      f"double layer) in {s_all:.1f} s on {threads} threads, plus LAPACK getrf/getrs at order {n} "
+                      f"({t_lu:.2f} + {t_solve:.2f} s); one extraction estimated at {t_ext:.0f} s",
+            "cpu_model": platform.processor() or platform.machine(),
+            "pairs_per_s_all_cores": r_all, "lapack_getrf_s": t_lu,
+            "single_thread": {"pairs_per_s": r_one, "rows": rows_single, "seconds": s_one}}
+
+
+def run_stack(args):
+    """The multi-dielectric path (Sec. 4) on a layered stack: per step the
+    assembly of the per-layer system, its LU factorisation with partial
+    pivoting, the solve for every conductor and the charges, timed with CUDA
+    events on the stream (the 2 x 244 MB of matrices exceed L2, and L2 is
+    flushed before each step as well); end to end adds the mesh from the host
+    boxes, its upload and the copy of C back."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_start(world)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem, workloads as W
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    gbem.load()
+    ctx = gbem.Context(local)
+    stream = torch.cuda.Stream()
+    rates = ctx.unit_rates(stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    spec = W.stack_3layer_5wires()
+
+    def make():
+        return gbem.Stack(ctx, spec["lo"], spec["hi"], spec["z"], spec["eps_r"], spec["face_bc"], spec["boxes"],
+                          spec["h"], spec["h_outer"])
+
+    S = make()
+
+    def step():
+        S.assemble(stream)
+        return S.capacitance(stream)
+
+    def timed(fn, k):
+        total = 0.0
+        out = None
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return max_over_ranks(total, world), out
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = gbem.get_stats(ctx)["launches"]
+    clocks.begin()
+    ms_total, (C, resid) = timed(step, args.steps)
+    clocks.end()
+    clk = clocks.stop()
+    launches = (gbem.get_stats(ctx)["launches"] - launches0) // args.steps
+    ms_step = ms_total / args.steps
+    # per-span device times (assembly, LU, sweeps, residual)
+    gbem.set_timing(ctx, 2)
+    gbem.get_kernel_stats(ctx, reset=True)
+    ms_traced, _ = timed(step, args.steps)
+    kst = gbem.get_kernel_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 0)
+
+    def step_e2e():
+        T = make()
+        try:
+            return T.capacitance(stream)
+        finally:
+            T.close()
+
+    step_e2e()
+    ms_e2e, _ = timed(step_e2e, args.steps)
+    np_ = (S.n_eq + 63) // 64 * 64
+    names = {"assemble": "stack_assemble: single- and double-layer entries of every layer's rows, FP64",
+             "factor": "the LU factorisation, one span: lu_panel (one CTA, partial pivoting), lu_swap, lu_trsm "
+                       "and lu_gemm (FP64 64 x 64 tiles) per block of 64 columns",
+             "sweep": "the two triangular sweeps (tri_block / tri_update per block)",
+             "residual": "stack_residual: B - M X in FP64"}
+    kern = {}
+    for k, d in kst.items():
+        if d["launches"] == 0:
+            continue
+        t = d["ms"] / d["launches"] * 1e-3
+        e = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps}
+        if k == "factor":
+            e.update({"bound": "alu", "unit": "TFLOP/s", "achieved": 2.0 * np_ ** 3 / 3.0 / t / 1e12,
+                      "peak": 2.0 * rates["dfma"] / 1e12,
+                      "peak_source": "2 x the DFMA rate measured on this GPU (gbem_unit_rates)",
+                      "work_per_launch": 2.0 * np_ ** 3 / 3.0, "work": "2 np^3 / 3 flop per factorisation"})
+        else:
+            e.update({"bound": "hbm", "unit": "GB/s", "achieved": d["bytes"] / d["launches"] / t / 1e9,
+                      "peak": _peaks()["hbm_gbs"], "peak_source": _peaks()["source"],
+                      "work_per_launch": d["bytes"] / d["launches"]})
+        e["frac"] = e["achieved"] / e["peak"]
+        kern[k] = e
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = {"kernel": names[dom], "share_of_traced_step": kern[dom]["ms_per_step"] / (ms_traced / args.steps)}
+    for key in ("bound", "achieved", "peak", "unit", "frac", "peak_source", "work_per_launch", "work"):
+        if key in kern[dom]:
+            roof[key] = kern[dom][key]
+    roof["traffic"] = None
+    if rank == 0:
+        p = S.panels()
+        line = {
+            "metric": "extractions/s", "value": whole_job_rate(args.steps, world, ms_total * 1e-3),
+            "unit": "extractions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "stack_3layer_5wires (12 x 12 x 4 um, eps_r 3.9 / 2.5 / 7.0, five wires, "
+                                   "grounded top and bottom, insulating sides)",
+                       "n_panels": S.n, "n_eq": S.n_eq, "n_cond": S.n_cond,
+                       "panels_by_kind": {k: int(np.sum(p["kind"] == v)) for k, v in
+                                          (("conductor", 0), ("face", 1), ("interface", 2))},
+                       "l2": "flushed (512 MB write) before every timed step; the two matrices (2 x 244 MB) "
+                             "exceed L2", "parallelism": f"replicas x{world}"},
+            "residual": resid, "capacitance_aF": (C * 1e18).round(4).tolist(),
+            "e2e": {"value": whole_job_rate(args.steps, world, ms_e2e * 1e-3), "unit": "extractions/s",
+                    "ms_per_step": ms_e2e / args.steps,
+                    # the stack's geometry and layout (62 B per panel, 4 per row,
+                    # the layer tables) and the quadrature nodes; C, the
+                    # residual norms and the status back
+                    "h2d_bytes_per_step": 62 * S.n + 4 * S.n_eq + 20 * (len(spec["eps_r"]) + 1) + 672,
+                    "d2h_bytes_per_step": 8 * S.n_cond * S.n_cond + 16 * S.n_cond + 4},
+            "gpu_launches": int(launches), "roofline": roof, "kernels": kern,
+            "unit_rates_per_s": rates, "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = stack_cpu_baseline(spec)
+        print(json.dumps(line))
+    S.close()
+    ctx.close()
+    dist_stop(world)
+
+
 def run_batch(args):
     """512 independent 2-6 bar structures (N log-uniform in [200, 3000]):
     the autotuned batch (groups of structures whose graphs run concurrently,
@@ -1079,6 +1272,8 @@ def main():
         run_partition(args)
     elif args.workload == "unit_rates":
         run_unit_rates()
+    elif args.workload == "stack":
+        run_stack(args)
     else:
         run_ours(args)
 

@@ -18,6 +18,9 @@
  *   charge                Q_n = eps * sum_{I_j on net n} X_j
  *                         (Eq. "electriccharge")                  -> gbem_capacitance
  *
+ * and its multi-dielectric case, Sec. 4, for layered stacks (per-layer
+ * equations with single- and double-layer integrals, LU)    -> gbem_stack_*
+ *
  * Units: lengths in micrometres; A in 1/um; X in um; capacitances in farads,
  * C = eps0 * eps_r * 1e-6 * X (eps0 = 8.8541878128e-12 F/m).  The kernel
  * 1/(4 pi |x-y|) is the paper's u* (Sec. 2.1, Eq. "representation"); the
@@ -57,7 +60,8 @@ typedef enum {
     GBEM_ERR_ARG = -1,      /* invalid argument (null pointer, size, id) */
     GBEM_ERR_OOM = -2,      /* allocator refused, or HBM budget exceeded */
     GBEM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
-    GBEM_ERR_NOT_SPD = -4,  /* Cholesky met a non-positive pivot */
+    GBEM_ERR_NOT_SPD = -4,  /* Cholesky met a non-positive pivot, or LU a
+                               zero one (singular stack system) */
     GBEM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
     GBEM_ERR_NOCONV = -6,   /* iterative refinement missed its tolerance */
     GBEM_ERR_MESH = -7,     /* malformed geometry: empty, degenerate or
@@ -461,6 +465,87 @@ gbem_status gbem_matrix_class_counts(gbem_matrix_t* mat, long long* counts);
  * context, which offers them to the next matrix of the same size (see
  * gbem_bytes_in_use); a context made by the server frees them at once. */
 void gbem_matrix_destroy(gbem_matrix_t* mat);
+
+/* ---------------------------------------------------------------------------
+ * Several dielectrics (Sec. 4).  A layered stack: the box enclosure
+ * [lo, hi] (um) cut by the planes z = z[1] < ... < z[n_layers-1] into
+ * n_layers horizontal layers (z[0] = lo[2], z[n_layers] = hi[2]) of relative
+ * permittivity eps_r[a], with disjoint cuboid conductors, each strictly
+ * inside one layer and the enclosure (no box touches another, a layer plane
+ * or the enclosure).  face_bc[2k + s] sets the enclosure face normal to axis
+ * k at lo[k] (s = 0) or hi[k] (s = 1): GBEM_FACE_GROUND (u = 0),
+ * GBEM_FACE_NEUMANN (insulating, du/dn = 0) or a conductor id >= 0 (the
+ * face is an electrode held at that conductor's potential).
+ *
+ * Panels: the conductors' faces cut as gbem_mesh cuts them with cells of at
+ * most h; the enclosure faces (side faces cut at every layer plane) and the
+ * interfaces z = z[a] with cells of at most h_outer (0: h).
+ *
+ * The system (Sec. 4, "Linear Equation"): for every layer a and every panel
+ * I_i of its boundary one row
+ *     (1/2) |I_i| u_i + sum_k Q^a_ik u_k - sum_j U_ij q^a_j = 0,
+ * U_ij = int int 1/(4 pi |x-y|), Q^a_ik = int int <x-y, n_a(y)>/(4 pi |x-y|^3)
+ * over I_i x I_k, n_a the outward normal of the layer, u and q = du/dn_a
+ * constant on every panel.  Across an interface u is continuous and
+ * eps_a q^a = -eps_b q^b.  Rows: for a = 0, 1, ... the panels of layer a's
+ * boundary in panel order.  Columns: for each panel in order its unknown u
+ * (insulating faces and interfaces) and then its unknown q (all panels but
+ * insulating faces; on an interface the flux of the layer below).
+ * Right-hand side m: conductor cond_ids[m] at 1 V, every other conductor and
+ * the grounded faces at 0 V.  The charge of conductor n is
+ * eps0 sum over its panels of eps_a q^a_j |I_j| (farads with lengths in um
+ * scaled by 1e-6).  Entries in FP64 (closed-form corner sums for near pairs,
+ * Gauss-Legendre for far ones); the matrix is not symmetric and is factored
+ * by LU with partial pivoting in FP64.
+ * ------------------------------------------------------------------------- */
+#define GBEM_MAX_LAYERS 16
+#define GBEM_FACE_GROUND (-1)
+#define GBEM_FACE_NEUMANN (-2)
+#define GBEM_PANEL_INTERFACE (-3)  /* the cond value of interface panels */
+
+typedef struct {
+    double lo[3];
+    double hi[3];
+    int32_t n_layers;
+    double z[GBEM_MAX_LAYERS + 1];
+    double eps_r[GBEM_MAX_LAYERS];
+    int32_t face_bc[6];
+    double h;        /* largest cell edge on conductors */
+    double h_outer;  /* largest cell edge on faces and interfaces (0: h) */
+} gbem_stack;
+
+typedef struct gbem_stack_s gbem_stack_t;
+
+/* Mesh a stack and lay out its system (host); on a device context also
+ * upload the geometry.  GBEM_ERR_MESH for boxes outside a layer or the
+ * enclosure, touching boxes, or no conductor; GBEM_ERR_ARG for malformed
+ * parameters or more than 32768 equations. */
+gbem_status gbem_stack_mesh(gbem_ctx* ctx, const gbem_stack* stack, const gbem_box* boxes, int nbox,
+                            gbem_stack_t** out);
+gbem_status gbem_stack_info(const gbem_stack_t* s, int* n_panels, int* n_eq, int* n_cond);
+/* The panels (each pointer may be NULL): axis, geo (5 per panel: plane,
+ * lo0, hi0, lo1, hi1 as gbem_mesh_panels), kind (0 conductor face,
+ * 1 enclosure face, 2 interface), cond (conductor id, GBEM_FACE_GROUND,
+ * GBEM_FACE_NEUMANN or GBEM_PANEL_INTERFACE), region_a (the layer whose
+ * boundary it is; the layer below for an interface), region_b (the layer
+ * above an interface, else -1), sign (the outward normal of region_a is
+ * sign * e_axis), cond_ids (n_cond, ascending: the right-hand sides). */
+gbem_status gbem_stack_panels(const gbem_stack_t* s, int8_t* axis, double* geo, int32_t* kind, int32_t* cond,
+                              int32_t* region_a, int32_t* region_b, int8_t* sign, int32_t* cond_ids);
+/* Assemble the system and its right-hand sides on the device (allocates
+ * 2 np^2 doubles, np = n_eq rounded up to 64, plus the solve's buffers). */
+gbem_status gbem_stack_assemble(gbem_stack_t* s, gbem_stream stream);
+/* The assembled matrix (n_eq x n_eq, row-major) and right-hand sides
+ * (n_eq x n_cond, row-major) on the host; either may be NULL.  Waits. */
+gbem_status gbem_stack_system(gbem_stack_t* s, double* M_host, double* B_host);
+/* Capacitance matrix in farads, n_cond x n_cond row-major into C_host
+ * (C[n][m] = charge on conductor cond_ids[n] for right-hand side m).
+ * Assembles first if needed, factors once (LU, partial pivoting), solves;
+ * resid (may be NULL) receives max over right-hand sides of
+ * max |B - M X| / max |B|.  GBEM_ERR_NOT_SPD if a pivot is exactly zero
+ * (singular system).  Waits for the stream. */
+gbem_status gbem_stack_capacitance(gbem_stack_t* s, gbem_stream stream, double* C_host, double* resid);
+void gbem_stack_destroy(gbem_stack_t* s);
 
 #ifdef __cplusplus
 }

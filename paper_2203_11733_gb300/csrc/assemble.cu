@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "gbem_internal.h"
+#include "near_field.cuh"
 
 namespace {
 
@@ -44,14 +45,8 @@ constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ far field
 
-// 1/sqrt(x) in FP64: single-precision estimate refined by one Newton step
-// y <- y + y (1 - x y^2) / 2 (relative error about 1.5 e0^2 < 1e-13).
-__device__ __forceinline__ double rsq(double x)
-{
-    double y = (double)rsqrtf((float)x);
-    double e = fma(-x * y, y, 1.0);
-    return fma(0.5 * y, e, y);
-}
+// 1/sqrt(x) in FP64 (near_field.cuh).
+__device__ __forceinline__ double rsq(double x) { return rsq64(x); }
 // 1/sqrt(x) in FP32: the hardware approximation (PTX rsqrt.approx, relative
 // error below 2^-22), flush-to-zero form, one instruction.  The arguments are
 // squared distances between quadrature nodes of separated panels, always
@@ -171,43 +166,6 @@ __device__ __noinline__ OuterSum<T> far_orth(T ds, T si, T sj, T dv, T ti, T dw,
 }
 
 // ------------------------------------------------------------------ near field
-
-// coef * ln(t + rho) with rho = sqrt(t^2 + r2); 0 * ln 0 -> 0; the t < 0 branch
-// uses ln(t + rho) = ln(r2 / (rho - t)) to avoid cancellation.
-__device__ __forceinline__ double xlog(double coef, double t, double r2, double rho)
-{
-    if (coef == 0.0) return 0.0;
-    return (t >= 0.0) ? coef * log(t + rho) : coef * log(r2 / (rho - t));
-}
-
-// F(u,v,w) = v/2 (u^2-w^2) ln(v+rho) + u/2 (v^2-w^2) ln(u+rho)
-//            - (u^2+v^2-2w^2) rho/6 - u v w atan(u v/(w rho))
-__device__ __noinline__ double F_par(double u, double v, double w)
-{
-    double u2 = u * u, v2 = v * v, w2 = w * w;
-    double rho = sqrt(u2 + v2 + w2);
-    double r = xlog(0.5 * v * (u2 - w2), v, u2 + w2, rho) + xlog(0.5 * u * (v2 - w2), u, v2 + w2, rho) -
-               (u2 + v2 - 2.0 * w2) * rho * (1.0 / 6.0);
-    double uvw = u * v * w;
-    if (uvw != 0.0) r -= uvw * atan(u * v / (w * rho));
-    return r;
-}
-
-// H(u,v,w) = u v w ln(u+rho) + w(3u^2-w^2)/6 ln(v+rho) + v(3u^2-v^2)/6 ln(w+rho)
-//            - v w rho/3 - u w^2/2 atan(uv/(w rho)) - u v^2/2 atan(uw/(v rho))
-//            - u^3/6 atan(vw/(u rho))
-__device__ __noinline__ double H_orth(double u, double v, double w)
-{
-    double u2 = u * u, v2 = v * v, w2 = w * w;
-    double rho = sqrt(u2 + v2 + w2);
-    double r = xlog(u * v * w, u, v2 + w2, rho) +
-               xlog(w * (3.0 * u2 - w2) * (1.0 / 6.0), v, u2 + w2, rho) +
-               xlog(v * (3.0 * u2 - v2) * (1.0 / 6.0), w, u2 + v2, rho) - v * w * rho * (1.0 / 3.0);
-    if (u * w != 0.0 && v != 0.0) r -= 0.5 * u * w2 * atan(u * v / (w * rho));
-    if (u * v != 0.0 && w != 0.0) r -= 0.5 * u * v2 * atan(u * w / (v * rho));
-    if (u != 0.0 && v * w != 0.0) r -= (u * u2 * (1.0 / 6.0)) * atan(v * w / (u * rho));
-    return r;
-}
 
 // ------------------------------------------------------------------ tile kernel
 
@@ -642,6 +600,8 @@ __global__ void copy_lower(const double* __restrict__ A, double* __restrict__ L,
     }
 }
 
+}  // namespace
+
 // Gauss-Legendre nodes on [-1,1] from Newton's method on the three-term
 // Legendre recurrence (host side, computed once per process).
 void gl_nodes(int n, double* x, double* w)
@@ -677,8 +637,6 @@ void gl_nodes(int n, double* x, double* w)
         w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
-
-}  // namespace
 
 cudaError_t gl_upload()
 {

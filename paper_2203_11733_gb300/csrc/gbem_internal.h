@@ -216,6 +216,8 @@ void mesh_divide(double lo, double hi, const gbem_mesh_params* p, std::vector<do
 
 // ---- kernels (assemble.cu, factor.cu, solve.cu)
 cudaError_t gl_upload();
+// Gauss-Legendre nodes and weights of order n on [-1, 1] (host).
+void gl_nodes(int n, double* x, double* w);
 // Every lower entry, tiles in band order.  Mixed mode writes the float pairs
 // and the FP32 copy.  counts (8 words, zeroed) receives the pairs of each
 // class; the traced work counts the quadrature evaluations and corner terms.
@@ -280,3 +282,34 @@ cudaError_t launch_indicator_rhs(const int32_t* cond, int n, int np, int n_cond,
                                  cudaStream_t s);
 cudaError_t launch_capacitance(const int32_t* cond, int n, int np, int n_cond, const double* X,
                                double scale, double* C, cudaStream_t s);
+
+// ---- multi-dielectric system (stack.cpp, dielectric.cu)
+// Device view of a layered stack's system.  Panels as DevPanels; rows of
+// region a are reg_off[a] .. reg_off[a+1]-1, row r belongs to panel
+// row_panel[r]; ucol / qcol: the column of the panel's unknown u / q (-1:
+// known); bcol: the right-hand side of a panel held at a conductor's
+// potential (-1: none); cidx: the conductor index of a conductor or
+// electrode panel (-1: none).  M: np x np column-major (the factor after
+// launch_stack_lu), M0: its copy before factoring, B: np x nc.
+struct StackView {
+    int n = 0, n_eq = 0, np = 0, nc = 0, R = 0;
+    const double *c = nullptr, *lo0 = nullptr, *hi0 = nullptr, *lo1 = nullptr, *hi1 = nullptr;
+    const int8_t *axis = nullptr, *sign = nullptr;
+    const int32_t *ra = nullptr, *ucol = nullptr, *qcol = nullptr, *bcol = nullptr, *cidx = nullptr;
+    const int32_t *row_panel = nullptr, *reg_off = nullptr;
+    const long long* tile_off = nullptr;
+    const double* eps = nullptr;
+    double *M = nullptr, *M0 = nullptr, *B = nullptr, *C = nullptr;
+    int *ipiv = nullptr, *status = nullptr;
+};
+cudaError_t stack_gl_upload(cudaStream_t s);
+cudaError_t launch_stack_assemble(const StackView& v, long long tiles, cudaStream_t s);
+cudaError_t launch_stack_lu(const StackView& v, cudaStream_t s);
+// X (np x nc) := M^-1 B with the LU factor and its interchanges; perm: np
+// ints of work space; then C (nc x nc) from X.  norms: 2 nc words, zeroed.
+cudaError_t launch_stack_solve(const StackView& v, double* X, int* perm, unsigned long long* norms,
+                               double eps0, cudaStream_t s);
+// norms[m] = max_r |B - M0 X|[r, m] and norms[nc + m] = max_r |B[r, m]| (as
+// the bit patterns of non-negative doubles).
+cudaError_t launch_stack_residual(const StackView& v, const double* M0, const double* X,
+                                  unsigned long long* norms, cudaStream_t s);

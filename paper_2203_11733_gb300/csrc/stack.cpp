@@ -1,0 +1,477 @@
+// Layered dielectric stacks (Wu & Li, Sec. 4): the host mesher, the layout of
+// the per-region system and the gbem_stack_* entry points.  The kernels are
+// in dielectric.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "gbem_internal.h"
+
+struct gbem_stack_s {
+    gbem_ctx* ctx = nullptr;
+    int n = 0, n_eq = 0, np = 0, nc = 0, R = 0;
+    // panels, in mesher order
+    std::vector<int8_t> axis, sign;
+    std::vector<double> geo;        // 5 per panel
+    std::vector<int32_t> kind, cond, ra, rb;
+    std::vector<double> eps;
+    // layout
+    std::vector<int32_t> ucol, qcol, bcol, cidx, row_panel, reg_off, cond_ids;
+    std::vector<long long> tile_off;
+    // device
+    void* meta = nullptr;
+    size_t meta_bytes = 0;
+    double* M = nullptr;
+    double* M0 = nullptr;
+    size_t mat_bytes = 0;
+    void* work = nullptr;           // B, X, C, ipiv, perm, status, norms
+    size_t work_bytes = 0;
+    StackView v;
+    double* X = nullptr;
+    int* perm = nullptr;
+    unsigned long long* norms = nullptr;
+    bool assembled = false, factored = false;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+struct Dev {
+    int prev = -1;
+    explicit Dev(int d)
+    {
+        if (d >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
+        else prev = -1;
+    }
+    ~Dev()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void cells(double lo, double hi, double h, std::vector<double>& out)
+{
+    gbem_mesh_params p{h, 1.0, 0.0};
+    mesh_divide(lo, hi, &p, out);
+}
+
+struct Mesher {
+    gbem_stack_s* S;
+    void add(int k, double c, double a0, double b0, double a1, double b1, int kind, int cond, int ra, int rb,
+             int sign)
+    {
+        S->axis.push_back((int8_t)k);
+        const double g[5] = {c, a0, b0, a1, b1};
+        S->geo.insert(S->geo.end(), g, g + 5);
+        S->kind.push_back(kind);
+        S->cond.push_back(cond);
+        S->ra.push_back(ra);
+        S->rb.push_back(rb);
+        S->sign.push_back((int8_t)sign);
+    }
+    // every cell of the tensor grid of [a0,b0] x [a1,b1]
+    void grid(int k, double c, double a0, double b0, double a1, double b1, double h, int kind, int cond, int ra,
+              int rb, int sign)
+    {
+        std::vector<double> n0, n1;
+        cells(a0, b0, h, n0);
+        cells(a1, b1, h, n1);
+        for (size_t i = 0; i + 1 < n0.size(); ++i)
+            for (size_t j = 0; j + 1 < n1.size(); ++j) add(k, c, n0[i], n0[i + 1], n1[j], n1[j + 1], kind, cond, ra, rb, sign);
+    }
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, gbem_stack_s* S, std::string& err)
+{
+    const int R = st->n_layers;
+    if (R < 1 || R > GBEM_MAX_LAYERS) return err = "n_layers must be 1 .. GBEM_MAX_LAYERS", GBEM_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(st->lo[d] < st->hi[d]) || !std::isfinite(st->lo[d]) || !std::isfinite(st->hi[d]))
+            return err = "empty enclosure", GBEM_ERR_MESH;
+    if (st->z[0] != st->lo[2] || st->z[R] != st->hi[2]) return err = "layer planes must span lo[2] .. hi[2]", GBEM_ERR_ARG;
+    for (int a = 0; a < R; ++a) {
+        if (!(st->z[a] < st->z[a + 1])) return err = "layer planes must increase", GBEM_ERR_ARG;
+        if (!finite_pos(st->eps_r[a])) return err = "eps_r must be positive", GBEM_ERR_ARG;
+    }
+    for (int f = 0; f < 6; ++f)
+        if (st->face_bc[f] < GBEM_FACE_NEUMANN) return err = "bad face condition", GBEM_ERR_ARG;
+    if (!finite_pos(st->h) || !(st->h_outer >= 0.0) || !std::isfinite(st->h_outer))
+        return err = "cell sizes must be positive", GBEM_ERR_ARG;
+    if (nbox < 0 || (nbox > 0 && !boxes)) return err = "boxes", GBEM_ERR_ARG;
+    const double h_out = st->h_outer > 0.0 ? st->h_outer : st->h;
+    Mesher m{S};
+    for (int b = 0; b < nbox; ++b) {
+        const gbem_box& B = boxes[b];
+        if (B.conductor < 0) return err = "conductor ids must be >= 0", GBEM_ERR_ARG;
+        int layer = -1, count = 0;
+        for (int a = 0; a < R; ++a)
+            if (st->z[a] < B.lo[2] && B.hi[2] < st->z[a + 1]) {
+                layer = a;
+                ++count;
+            }
+        bool inside = true;
+        for (int d = 0; d < 3; ++d) inside = inside && st->lo[d] < B.lo[d] && B.hi[d] < st->hi[d] && B.lo[d] < B.hi[d];
+        if (count != 1 || !inside)
+            return err = "every box must lie strictly inside one layer and the enclosure", GBEM_ERR_MESH;
+        for (int c = 0; c < b; ++c) {
+            bool apart = false;
+            for (int d = 0; d < 3; ++d) apart = apart || boxes[c].hi[d] < B.lo[d] || B.hi[d] < boxes[c].lo[d];
+            if (!apart) return err = "boxes must not touch or overlap", GBEM_ERR_MESH;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const int p = k == 0 ? 1 : 0, q = k == 2 ? 1 : 2;
+            // the region lies outside the box: its outward normal points into it
+            m.grid(k, B.lo[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 0, B.conductor, layer, -1, 1);
+            m.grid(k, B.hi[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 0, B.conductor, layer, -1, -1);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int p = k == 0 ? 1 : 0, q = k == 2 ? 1 : 2;
+        for (int s = 0; s < 2; ++s) {
+            const double plane = s ? st->hi[k] : st->lo[k];
+            const int bc = st->face_bc[2 * k + s], sign = s ? 1 : -1;
+            if (k == 2) {
+                m.grid(k, plane, st->lo[p], st->hi[p], st->lo[q], st->hi[q], h_out, 1, bc, s ? R - 1 : 0, -1, sign);
+            } else {
+                // q == 2: the face is cut at every layer plane
+                for (int a = 0; a < R; ++a)
+                    m.grid(k, plane, st->lo[p], st->hi[p], st->z[a], st->z[a + 1], h_out, 1, bc, a, -1, sign);
+            }
+        }
+    }
+    for (int a = 1; a < R; ++a)
+        m.grid(2, st->z[a], st->lo[0], st->hi[0], st->lo[1], st->hi[1], h_out, 2, GBEM_PANEL_INTERFACE, a - 1, a, 1);
+    S->eps.assign(st->eps_r, st->eps_r + R);
+    S->R = R;
+    S->n = (int)S->axis.size();
+    return GBEM_OK;
+}
+
+// Rows: per region, its boundary panels in panel order.  Columns: per panel,
+// u (insulating faces, interfaces) then q (all but insulating faces).
+gbem_status stack_layout(gbem_stack_s* S, std::string& err)
+{
+    const int n = S->n, R = S->R;
+    S->reg_off.assign(R + 1, 0);
+    S->row_panel.clear();
+    for (int a = 0; a < R; ++a) {
+        S->reg_off[a] = (int32_t)S->row_panel.size();
+        for (int i = 0; i < n; ++i)
+            if (S->ra[i] == a || S->rb[i] == a) S->row_panel.push_back(i);
+    }
+    S->reg_off[R] = (int32_t)S->row_panel.size();
+    S->ucol.assign(n, -1);
+    S->qcol.assign(n, -1);
+    int col = 0;
+    for (int i = 0; i < n; ++i) {
+        if (S->cond[i] == GBEM_FACE_NEUMANN || S->cond[i] == GBEM_PANEL_INTERFACE) S->ucol[i] = col++;
+        if (S->cond[i] != GBEM_FACE_NEUMANN) S->qcol[i] = col++;
+    }
+    S->n_eq = (int)S->row_panel.size();
+    if (col != S->n_eq) return err = "the stack's system is not square", GBEM_ERR_MESH;
+    std::vector<int32_t> ids;
+    for (int i = 0; i < n; ++i)
+        if (S->cond[i] >= 0) ids.push_back(S->cond[i]);
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    if (ids.empty()) return err = "no conductor", GBEM_ERR_MESH;
+    S->cond_ids = ids;
+    S->nc = (int)ids.size();
+    S->bcol.assign(n, -1);
+    S->cidx.assign(n, -1);
+    for (int i = 0; i < n; ++i)
+        if (S->cond[i] >= 0) {
+            const int m = (int)(std::lower_bound(ids.begin(), ids.end(), S->cond[i]) - ids.begin());
+            S->cidx[i] = m;
+            if (S->ucol[i] < 0) S->bcol[i] = m;
+        }
+    S->tile_off.assign(R + 1, 0);
+    for (int a = 0; a < R; ++a) {
+        const long long nt = (S->reg_off[a + 1] - S->reg_off[a] + 31) / 32;
+        S->tile_off[a + 1] = S->tile_off[a] + nt * nt;
+    }
+    S->np = (S->n_eq + 63) / 64 * 64;
+    return GBEM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// One device allocation for the geometry and layout; views into it.
+gbem_status stack_upload(gbem_stack_s* S)
+{
+    gbem_ctx* ctx = S->ctx;
+    const size_t n = S->n, R = S->R;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_geo = take(sizeof(double) * 5 * n), o_axis = take(n), o_sign = take(n);
+    const size_t o_ra = take(4 * n), o_u = take(4 * n), o_q = take(4 * n), o_b = take(4 * n), o_ci = take(4 * n);
+    const size_t o_rows = take(4 * (size_t)S->n_eq), o_reg = take(4 * (R + 1)), o_tile = take(8 * (R + 1));
+    const size_t o_eps = take(8 * R);
+    std::vector<unsigned char> host(off, 0);
+    double* geo = reinterpret_cast<double*>(host.data() + o_geo);
+    for (size_t i = 0; i < n; ++i)
+        for (int e = 0; e < 5; ++e) geo[e * n + i] = S->geo[5 * i + e];
+    std::memcpy(host.data() + o_axis, S->axis.data(), n);
+    std::memcpy(host.data() + o_sign, S->sign.data(), n);
+    std::memcpy(host.data() + o_ra, S->ra.data(), 4 * n);
+    std::memcpy(host.data() + o_u, S->ucol.data(), 4 * n);
+    std::memcpy(host.data() + o_q, S->qcol.data(), 4 * n);
+    std::memcpy(host.data() + o_b, S->bcol.data(), 4 * n);
+    std::memcpy(host.data() + o_ci, S->cidx.data(), 4 * n);
+    std::memcpy(host.data() + o_rows, S->row_panel.data(), 4 * (size_t)S->n_eq);
+    std::memcpy(host.data() + o_reg, S->reg_off.data(), 4 * (R + 1));
+    std::memcpy(host.data() + o_tile, S->tile_off.data(), 8 * (R + 1));
+    std::memcpy(host.data() + o_eps, S->eps.data(), 8 * R);
+    void* d = ctx_alloc(ctx, off, nullptr);
+    if (!d) return ctx_fail(ctx, GBEM_ERR_OOM, "stack geometry");
+    S->meta = d;
+    S->meta_bytes = off;
+    if (cudaMemcpy(d, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess)
+        return ctx_fail(ctx, GBEM_ERR_CUDA, "stack upload");
+    unsigned char* b = static_cast<unsigned char*>(d);
+    StackView& v = S->v;
+    v.n = S->n;
+    v.n_eq = S->n_eq;
+    v.np = S->np;
+    v.nc = S->nc;
+    v.R = S->R;
+    const double* g = reinterpret_cast<const double*>(b + o_geo);
+    v.c = g;
+    v.lo0 = g + n;
+    v.hi0 = g + 2 * n;
+    v.lo1 = g + 3 * n;
+    v.hi1 = g + 4 * n;
+    v.axis = reinterpret_cast<const int8_t*>(b + o_axis);
+    v.sign = reinterpret_cast<const int8_t*>(b + o_sign);
+    v.ra = reinterpret_cast<const int32_t*>(b + o_ra);
+    v.ucol = reinterpret_cast<const int32_t*>(b + o_u);
+    v.qcol = reinterpret_cast<const int32_t*>(b + o_q);
+    v.bcol = reinterpret_cast<const int32_t*>(b + o_b);
+    v.cidx = reinterpret_cast<const int32_t*>(b + o_ci);
+    v.row_panel = reinterpret_cast<const int32_t*>(b + o_rows);
+    v.reg_off = reinterpret_cast<const int32_t*>(b + o_reg);
+    v.tile_off = reinterpret_cast<const long long*>(b + o_tile);
+    v.eps = reinterpret_cast<const double*>(b + o_eps);
+    return GBEM_OK;
+}
+
+// The matrices and the solve's buffers, at first use.
+gbem_status stack_alloc(gbem_stack_s* S, cudaStream_t s)
+{
+    if (S->M) return GBEM_OK;
+    gbem_ctx* ctx = S->ctx;
+    const size_t np = S->np, nc = S->nc;
+    S->mat_bytes = sizeof(double) * np * np;
+    S->M = static_cast<double*>(ctx_alloc(ctx, S->mat_bytes, s));
+    if (!S->M) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix");
+    S->M0 = static_cast<double*>(ctx_alloc(ctx, S->mat_bytes, s));
+    if (!S->M0) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix copy");
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_B = take(8 * np * nc), o_X = take(8 * np * nc), o_C = take(8 * nc * nc);
+    const size_t o_piv = take(4 * np), o_perm = take(4 * np), o_st = take(4), o_nrm = take(16 * nc);
+    S->work = ctx_alloc(ctx, off, s);
+    if (!S->work) return ctx_fail(ctx, GBEM_ERR_OOM, "stack work space");
+    S->work_bytes = off;
+    unsigned char* b = static_cast<unsigned char*>(S->work);
+    S->v.M = S->M;
+    S->v.M0 = S->M0;
+    S->v.B = reinterpret_cast<double*>(b + o_B);
+    S->X = reinterpret_cast<double*>(b + o_X);
+    S->v.C = reinterpret_cast<double*>(b + o_C);
+    S->v.ipiv = reinterpret_cast<int*>(b + o_piv);
+    S->perm = reinterpret_cast<int*>(b + o_perm);
+    S->v.status = reinterpret_cast<int*>(b + o_st);
+    S->norms = reinterpret_cast<unsigned long long*>(b + o_nrm);
+    return GBEM_OK;
+}
+
+bool ok(gbem_ctx* ctx, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return true;
+    ctx_fail(ctx, GBEM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return false;
+}
+
+}  // namespace
+
+gbem_status gbem_stack_mesh(gbem_ctx* ctx, const gbem_stack* stack, const gbem_box* boxes, int nbox,
+                            gbem_stack_t** out)
+{
+    if (!ctx || !stack || !out) return GBEM_ERR_ARG;
+    *out = nullptr;
+    gbem_stack_s* S = new (std::nothrow) gbem_stack_s();
+    if (!S) return GBEM_ERR_OOM;
+    S->ctx = ctx;
+    std::string err;
+    gbem_status st = stack_build(stack, boxes, nbox, S, err);
+    if (st == GBEM_OK) st = stack_layout(S, err);
+    if (st == GBEM_OK && S->n_eq > 32768) {
+        err = "more than 32768 equations";
+        st = GBEM_ERR_ARG;
+    }
+    if (st != GBEM_OK) {
+        delete S;
+        return ctx_fail(ctx, st, err);
+    }
+    if (ctx->device >= 0) {
+        Dev g(ctx->device);
+        st = stack_upload(S);
+        if (st != GBEM_OK) {
+            gbem_stack_destroy(S);
+            return st;
+        }
+    }
+    *out = S;
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_info(const gbem_stack_t* S, int* n_panels, int* n_eq, int* n_cond)
+{
+    if (!S) return GBEM_ERR_ARG;
+    if (n_panels) *n_panels = S->n;
+    if (n_eq) *n_eq = S->n_eq;
+    if (n_cond) *n_cond = S->nc;
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_panels(const gbem_stack_t* S, int8_t* axis, double* geo, int32_t* kind, int32_t* cond,
+                              int32_t* region_a, int32_t* region_b, int8_t* sign, int32_t* cond_ids)
+{
+    if (!S) return GBEM_ERR_ARG;
+    const size_t n = S->n;
+    if (axis) std::memcpy(axis, S->axis.data(), n);
+    if (geo) std::memcpy(geo, S->geo.data(), sizeof(double) * 5 * n);
+    if (kind) std::memcpy(kind, S->kind.data(), 4 * n);
+    if (cond) std::memcpy(cond, S->cond.data(), 4 * n);
+    if (region_a) std::memcpy(region_a, S->ra.data(), 4 * n);
+    if (region_b) std::memcpy(region_b, S->rb.data(), 4 * n);
+    if (sign) std::memcpy(sign, S->sign.data(), n);
+    if (cond_ids) std::memcpy(cond_ids, S->cond_ids.data(), 4 * (size_t)S->nc);
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_assemble(gbem_stack_t* S, gbem_stream stream)
+{
+    if (!S) return GBEM_ERR_ARG;
+    gbem_ctx* ctx = S->ctx;
+    if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
+    Dev g(ctx->device);
+    TraceScope ts(ctx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gbem_status st = stack_alloc(S, s);
+    if (st != GBEM_OK) return st;
+    S->last = s;
+    S->assembled = S->factored = false;
+    if (!ok(ctx, stack_gl_upload(s), "quadrature nodes") ||
+        !ok(ctx, launch_stack_assemble(S->v, S->tile_off[S->R], s), "stack assembly") ||
+        !ok(ctx, cudaMemcpyAsync(S->M0, S->M, S->mat_bytes, cudaMemcpyDeviceToDevice, s), "matrix copy"))
+        return GBEM_ERR_CUDA;
+    S->assembled = true;
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_system(gbem_stack_t* S, double* M_host, double* B_host)
+{
+    if (!S) return GBEM_ERR_ARG;
+    gbem_ctx* ctx = S->ctx;
+    if (!S->assembled) return ctx_fail(ctx, GBEM_ERR_STATE, "system not assembled");
+    Dev g(ctx->device);
+    if (!ok(ctx, cudaStreamSynchronize(S->last), "sync")) return GBEM_ERR_CUDA;
+    const size_t n = S->n_eq, np = S->np;
+    if (M_host) {
+        std::vector<double> col(np * n);
+        if (!ok(ctx, cudaMemcpy(col.data(), S->M0, sizeof(double) * np * n, cudaMemcpyDeviceToHost), "download"))
+            return GBEM_ERR_CUDA;
+        for (size_t c = 0; c < n; ++c)
+            for (size_t r = 0; r < n; ++r) M_host[r * n + c] = col[c * np + r];
+    }
+    if (B_host) {
+        std::vector<double> col(np * S->nc);
+        if (!ok(ctx, cudaMemcpy(col.data(), S->v.B, sizeof(double) * np * S->nc, cudaMemcpyDeviceToHost), "download"))
+            return GBEM_ERR_CUDA;
+        for (size_t m = 0; m < (size_t)S->nc; ++m)
+            for (size_t r = 0; r < n; ++r) B_host[r * S->nc + m] = col[m * np + r];
+    }
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_capacitance(gbem_stack_t* S, gbem_stream stream, double* C_host, double* resid)
+{
+    if (!S || !C_host) return GBEM_ERR_ARG;
+    gbem_ctx* ctx = S->ctx;
+    if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
+    if (!S->assembled) {
+        gbem_status st = gbem_stack_assemble(S, stream);
+        if (st != GBEM_OK) return st;
+    }
+    Dev g(ctx->device);
+    TraceScope ts(ctx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (s != S->last) {
+        // order this stream after the last one's work on the stack
+        cudaEvent_t ev;
+        if (!ok(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event")) return GBEM_ERR_CUDA;
+        cudaEventRecord(ev, S->last);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        S->last = s;
+    }
+    if (!S->factored) {
+        if (!ok(ctx, cudaMemsetAsync(S->v.status, 0, sizeof(int), s), "memset") ||
+            !ok(ctx, launch_stack_lu(S->v, s), "LU"))
+            return GBEM_ERR_CUDA;
+        S->factored = true;
+    }
+    const double eps0 = 8.8541878128e-12;
+    if (!ok(ctx, launch_stack_solve(S->v, S->X, S->perm, S->norms, eps0, s), "solve") ||
+        !ok(ctx, launch_stack_residual(S->v, S->M0, S->X, S->norms, s), "residual"))
+        return GBEM_ERR_CUDA;
+    const size_t nc = S->nc;
+    std::vector<unsigned long long> nrm(2 * nc);
+    int status = 0;
+    if (!ok(ctx, cudaMemcpyAsync(C_host, S->v.C, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
+        !ok(ctx, cudaMemcpyAsync(nrm.data(), S->norms, 16 * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
+        !ok(ctx, cudaMemcpyAsync(&status, S->v.status, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h") ||
+        !ok(ctx, cudaStreamSynchronize(s), "sync"))
+        return GBEM_ERR_CUDA;
+    if (status != 0) {
+        S->factored = false;
+        return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "LU met a zero pivot: the stack's system is singular");
+    }
+    double worst = 0.0;
+    for (size_t m = 0; m < nc; ++m) {
+        double r, b;
+        std::memcpy(&r, &nrm[m], 8);
+        std::memcpy(&b, &nrm[nc + m], 8);
+        worst = std::max(worst, b > 0.0 ? r / b : r);
+    }
+    if (resid) *resid = worst;
+    return GBEM_OK;
+}
+
+void gbem_stack_destroy(gbem_stack_t* S)
+{
+    if (!S) return;
+    gbem_ctx* ctx = S->ctx;
+    if (ctx->device >= 0 && (S->meta || S->M || S->work)) {
+        Dev g(ctx->device);
+        cudaStreamSynchronize(S->last);
+        if (S->work) ctx_free(ctx, S->work, S->work_bytes, S->last);
+        if (S->M0) ctx_free(ctx, S->M0, S->mat_bytes, S->last);
+        if (S->M) ctx_free(ctx, S->M, S->mat_bytes, S->last);
+        if (S->meta) ctx_free(ctx, S->meta, S->meta_bytes, nullptr);
+    }
+    delete S;
+}

@@ -100,6 +100,13 @@ _SIGS = {
     "gbem_mesh_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gbem_mesh_panels": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gbem_mesh_refine": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    "gbem_stack_mesh": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "gbem_stack_info": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gbem_stack_panels": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gbem_stack_assemble": (ctypes.c_int, [_P, _P]),
+    "gbem_stack_system": (ctypes.c_int, [_P, _P, _P]),
+    "gbem_stack_capacitance": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gbem_stack_destroy": (None, [_P]),
     "gbem_mesh_destroy": (None, [_P]),
     "gbem_assemble": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "gbem_factor": (ctypes.c_int, [_P, _P]),
@@ -470,6 +477,86 @@ def _boxes(boxes):
         arr[i].hi[:] = [float(v) for v in hi]
         arr[i].conductor = int(c)
     return arr
+
+
+MAX_LAYERS = 16
+FACE_GROUND, FACE_NEUMANN, PANEL_INTERFACE = -1, -2, -3
+
+
+class _Stack(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("n_layers", ctypes.c_int32),
+                ("z", ctypes.c_double * (MAX_LAYERS + 1)), ("eps_r", ctypes.c_double * MAX_LAYERS),
+                ("face_bc", ctypes.c_int32 * 6), ("h", ctypes.c_double), ("h_outer", ctypes.c_double)]
+
+
+class Stack:
+    """A layered dielectric stack and its system (gbem_stack_*, Sec. 4)."""
+
+    def __init__(self, ctx: Context, lo, hi, z, eps_r, face_bc, boxes, h: float, h_outer: float = 0.0):
+        p = _Stack()
+        p.lo[:] = [float(v) for v in lo]
+        p.hi[:] = [float(v) for v in hi]
+        p.n_layers = len(eps_r)
+        if len(z) != len(eps_r) + 1 or len(eps_r) > MAX_LAYERS:
+            raise ValueError("z needs one more entry than eps_r, at most MAX_LAYERS layers")
+        for a, v in enumerate(z):
+            p.z[a] = float(v)
+        for a, v in enumerate(eps_r):
+            p.eps_r[a] = float(v)
+        p.face_bc[:] = [int(v) for v in face_bc]
+        p.h, p.h_outer = float(h), float(h_outer)
+        self.ctx, self.h = ctx, None
+        self.eps_r = [float(v) for v in eps_r]
+        arr = _boxes(boxes) if boxes else None
+        out = _P()
+        ctx.check(ctx.lib.gbem_stack_mesh(ctx.h, ctypes.byref(p), arr, len(boxes), ctypes.byref(out)))
+        self.h = out
+        ctx._children.add(self)
+        n, neq, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ctx.check(ctx.lib.gbem_stack_info(out, ctypes.byref(n), ctypes.byref(neq), ctypes.byref(nc)))
+        self.n, self.n_eq, self.n_cond = n.value, neq.value, nc.value
+
+    def panels(self) -> dict:
+        """The panels as arrays (the same keys as the oracle's stack mesh)."""
+        n = self.n
+        d = {"axis": np.empty(n, np.int8), "geo": np.empty((n, 5), np.float64), "kind": np.empty(n, np.int32),
+             "cond": np.empty(n, np.int32), "region_a": np.empty(n, np.int32), "region_b": np.empty(n, np.int32),
+             "sign": np.empty(n, np.int8)}
+        ids = np.empty(self.n_cond, np.int32)
+        self.ctx.check(self.ctx.lib.gbem_stack_panels(
+            self.h, _ptr(d["axis"]), _ptr(d["geo"]), _ptr(d["kind"]), _ptr(d["cond"]), _ptr(d["region_a"]),
+            _ptr(d["region_b"]), _ptr(d["sign"]), _ptr(ids)))
+        d["cond_ids"] = ids
+        return d
+
+    def assemble(self, stream=None):
+        self.ctx.check(self.ctx.lib.gbem_stack_assemble(self.h, _stream_handle(stream)))
+
+    def system(self):
+        """(M float64[n_eq, n_eq], B float64[n_eq, n_cond]) as assembled."""
+        M = np.empty((self.n_eq, self.n_eq), np.float64)
+        B = np.empty((self.n_eq, self.n_cond), np.float64)
+        self.ctx.check(self.ctx.lib.gbem_stack_system(self.h, _ptr(M), _ptr(B)))
+        return M, B
+
+    def capacitance(self, stream=None):
+        """(C float64[n_cond, n_cond] in farads, relative residual)."""
+        C = np.empty((self.n_cond, self.n_cond), np.float64)
+        r = ctypes.c_double()
+        self.ctx.check(self.ctx.lib.gbem_stack_capacitance(self.h, _stream_handle(stream), _ptr(C), ctypes.byref(r)))
+        return C, r.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            if self.ctx.h is not None:
+                self.ctx.lib.gbem_stack_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -271,3 +271,21 @@ def serving_requests(seed: int = 777, count: int = 1000, rate_per_s: float = 50.
         boxes, params = bus_structure(rng, n_target)
         out.append((t, boxes, params))
     return out
+
+
+def stack_3layer_5wires(h: float = 0.25, h_outer: float = 0.6):
+    """A layered dielectric stack (Sec. 4; the paper's own six-conductor case
+    is not public, so this one is synthetic): a 12 x 12 x 4 um enclosure with
+    grounded bottom and top and insulating sides (the boundary conditions of
+    the paper's multi-dielectric experiment, Sec. 5), three layers of
+    eps_r 3.9 / 2.5 / 7.0 (oxide, low-k, nitride) split at z = 1 and 2.5, and
+    five parallel 1 x 10 x 0.5 um wires at 2 um pitch inside the middle one.
+    Returns a dict of the gbem_stack fields and the boxes; with the default
+    cells the system has 5520 equations."""
+    face_ground, face_neumann = -1, -2
+    return {
+        "lo": [-6.0, -6.0, 0.0], "hi": [6.0, 6.0, 4.0], "z": [0.0, 1.0, 2.5, 4.0], "eps_r": [3.9, 2.5, 7.0],
+        "face_bc": [face_neumann] * 4 + [face_ground, face_ground],
+        "boxes": [([-4.0 + 2 * i, -5.0, 1.5], [-3.0 + 2 * i, 5.0, 2.0], i) for i in range(5)],
+        "h": h, "h_outer": h_outer,
+    }

@@ -1,0 +1,76 @@
+"""Host side of the multi-dielectric path (Sec. 4): the library's stack mesher
+builds the same panels, regions and normals as the oracle's, in the same
+order, and lays out a square system of the same size; malformed stacks are
+refused.  No GPU is touched."""
+import numpy as np
+import pytest
+
+from oracle import dielectric as D
+from paper_2203_11733_gb300 import build as B
+from paper_2203_11733_gb300 import gbem
+
+CASES = [
+    # (lo, hi, z, eps, face_bc, boxes, h, h_outer)
+    ([0, 0, 0], [4, 4, 3], [0, 1.5, 3], [1.0, 3.0], [D.GROUND] * 6,
+     [([1, 1, 0.5], [2, 3, 1], 0), ([2.5, 1, 1.8], [3, 3, 2.5], 1)], 0.5, 1.0),
+    ([0, 0, 0], [2, 2, 2], [0, 1, 2], [1.0, 4.0], [D.NEUMANN] * 4 + [D.GROUND, 0], [], 0.25, 0.0),
+    ([-3, -2, 0], [3, 2, 2.5], [0, 0.7, 1.6, 2.5], [3.9, 2.2, 7.0], [D.NEUMANN] * 4 + [D.GROUND, D.GROUND],
+     [([-2, -1, 0.2], [-0.5, 1, 0.5], 4), ([0.5, -1.5, 0.9], [2.5, -1.0, 1.3], 2), ([0.5, 1.0, 0.9], [2.5, 1.5, 1.3], 7)],
+     0.3, 0.8),
+]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return gbem.load()
+
+
+def _ctx():
+    return gbem.Context(device=-1, torch_alloc=False)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_stack_mesh_matches_oracle(lib, case):
+    lo, hi, z, eps, bc, boxes, h, ho = CASES[case]
+    ctx = _ctx()
+    S = gbem.Stack(ctx, lo, hi, z, eps, bc, boxes, h, ho)
+    got = S.panels()
+    ref = D.mesh_stack(D.Stack(lo, hi, z, eps, bc), boxes, h, ho)
+    for k in ("axis", "kind", "cond", "region_a", "region_b", "sign"):
+        assert np.array_equal(got[k].astype(np.int64), ref[k].astype(np.int64)), k
+    assert np.array_equal(got["geo"], ref["geo"])
+    rows, ucol, qcol, ids = D.layout(ref)
+    assert S.n_eq == len(rows)
+    assert np.array_equal(got["cond_ids"], ids)
+    S.close()
+    ctx.close()
+
+
+def test_stack_guards(lib):
+    ctx = _ctx()
+    lo, hi, z, eps, bc = [0, 0, 0], [4, 4, 3], [0, 1.5, 3], [1.0, 3.0], [D.GROUND] * 6
+    bad_boxes = [
+        [([1, 1, 1.0], [2, 2, 2.0], 0)],                              # crosses a layer plane
+        [([0, 1, 0.5], [2, 2, 1.0], 0)],                              # touches the enclosure
+        [([1, 1, 0.5], [2, 2, 1.0], 0), ([2, 1, 0.5], [3, 2, 1.0], 1)],  # boxes touch
+    ]
+    for boxes in bad_boxes:
+        with pytest.raises(gbem.GbemError) as e:
+            gbem.Stack(ctx, lo, hi, z, eps, bc, boxes, 0.5)
+        assert e.value.status == -7
+    with pytest.raises(gbem.GbemError) as e:   # no conductor at all
+        gbem.Stack(ctx, lo, hi, z, eps, bc, [], 0.5)
+    assert e.value.status == -7
+    with pytest.raises(gbem.GbemError) as e:   # planes do not span the enclosure
+        gbem.Stack(ctx, lo, hi, [0, 1.5, 2.9], eps, bc, [([1, 1, 0.5], [2, 3, 1], 0)], 0.5)
+    assert e.value.status == -1
+    with pytest.raises(gbem.GbemError) as e:   # non-positive permittivity
+        gbem.Stack(ctx, lo, hi, z, [1.0, 0.0], bc, [([1, 1, 0.5], [2, 3, 1], 0)], 0.5)
+    assert e.value.status == -1
+    S = gbem.Stack(ctx, lo, hi, z, eps, bc, [([1, 1, 0.5], [2, 3, 1], 0)], 0.5)
+    with pytest.raises(gbem.GbemError) as e:   # a host context cannot assemble
+        S.assemble(stream=0)
+    assert e.value.status == -9
+    S.close()
+    ctx.close()
