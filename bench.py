@@ -764,7 +764,7 @@ def run_stack(args):
     S = make()
 
     def step():
-        S.assemble(stream)
+        S.assemble(gbem.GBEM_MIXED, stream)
         return S.capacitance(stream)
 
     def timed(fn, k):
@@ -803,9 +803,21 @@ def run_stack(args):
     kst = gbem.get_kernel_stats(ctx, reset=True)
     gbem.set_timing(ctx, 0)
 
+    iters_mixed = S.iterations()
+
+    # the same extraction in FP64 (entries and LU), on the same GPU
+    def step64():
+        S.assemble(gbem.GBEM_FP64, stream)
+        return S.capacitance(stream)
+
+    step64()
+    ms64, (C64, resid64) = timed(step64, max(1, min(args.steps, 3)))
+    ms64_step = ms64 / max(1, min(args.steps, 3))
+
     def step_e2e():
         T = make()
         try:
+            T.assemble(gbem.GBEM_MIXED, stream)
             return T.capacitance(stream)
         finally:
             T.close()
@@ -813,11 +825,12 @@ def run_stack(args):
     step_e2e()
     ms_e2e, _ = timed(step_e2e, args.steps)
     np_ = (S.n_eq + 63) // 64 * 64
-    names = {"assemble": "stack_assemble: single- and double-layer entries of every layer's rows, FP64",
-             "factor": "the LU factorisation, one span: lu_panel (one CTA, partial pivoting), lu_swap, lu_trsm "
-                       "and lu_gemm (FP64 64 x 64 tiles) per block of 64 columns",
-             "sweep": "the two triangular sweeps (tri_block / tri_update per block)",
-             "residual": "stack_residual: B - M X in FP64"}
+    names = {"assemble": "stack_assemble<mixed>: single- and double-layer entries of every layer's rows (FP64 "
+                         "closed forms near, FP32 Gauss-Legendre far)",
+             "factor": "the FP32 LU factorisation, one span: lu_panel (one CTA, partial pivoting), lu_swap, "
+                       "lu_trsm and lu_gemm_f32 (128 x 128 tiles) per block of 64 columns",
+             "sweep": "the refinement corrections: FP32 triangular sweeps (tri_block / tri_update per block)",
+             "residual": "residual_partial / residual_finish: B - M0 X in FP64"}
     kern = {}
     for k, d in kst.items():
         if d["launches"] == 0:
@@ -826,8 +839,8 @@ def run_stack(args):
         e = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps}
         if k == "factor":
             e.update({"bound": "alu", "unit": "TFLOP/s", "achieved": 2.0 * np_ ** 3 / 3.0 / t / 1e12,
-                      "peak": 2.0 * rates["dfma"] / 1e12,
-                      "peak_source": "2 x the DFMA rate measured on this GPU (gbem_unit_rates)",
+                      "peak": 2.0 * rates["ffma"] / 1e12,
+                      "peak_source": "2 x the FFMA rate measured on this GPU (gbem_unit_rates): the FP32 LU",
                       "work_per_launch": 2.0 * np_ ** 3 / 3.0, "work": "2 np^3 / 3 flop per factorisation"})
         else:
             e.update({"bound": "hbm", "unit": "GB/s", "achieved": d["bytes"] / d["launches"] / t / 1e9,
@@ -847,7 +860,7 @@ def run_stack(args):
             "metric": "extractions/s", "value": whole_job_rate(args.steps, world, ms_total * 1e-3),
             "unit": "extractions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": "stack_3layer_5wires (12 x 12 x 4 um, eps_r 3.9 / 2.5 / 7.0, five wires, "
                                    "grounded top and bottom, insulating sides)",
                        "n_panels": S.n, "n_eq": S.n_eq, "n_cond": S.n_cond,
@@ -855,7 +868,10 @@ def run_stack(args):
                                           (("conductor", 0), ("face", 1), ("interface", 2))},
                        "l2": "flushed (512 MB write) before every timed step; the two matrices (2 x 244 MB) "
                              "exceed L2", "parallelism": f"replicas x{world}"},
-            "residual": resid, "capacitance_aF": (C * 1e18).round(4).tolist(),
+            "residual": resid, "refinement_iterations": iters_mixed,
+            "capacitance_aF": (C * 1e18).round(4).tolist(),
+            "fp64": {"ms_per_step": ms64_step, "value": world * 1e3 / ms64_step, "residual": resid64,
+                     "mixed_vs_fp64_rel": float(np.abs(C - C64).max() / np.abs(C64).max())},
             "e2e": {"value": whole_job_rate(args.steps, world, ms_e2e * 1e-3), "unit": "extractions/s",
                     "ms_per_step": ms_e2e / args.steps,
                     # the stack's geometry and layout (62 B per panel, 4 per row,
@@ -1238,6 +1254,7 @@ def run_partition(args):
 def run_unit_rates():
     """One JSON line: the rates gbem_unit_rates measures on cuda:0, the SM
     clock around the call, and each FP64 library call in DFMA equivalents."""
+    import torch
     from paper_2203_11733_gb300 import build as B
     from paper_2203_11733_gb300 import gbem
     B.build()

@@ -494,9 +494,9 @@ void gbem_matrix_destroy(gbem_matrix_t* mat);
  * Right-hand side m: conductor cond_ids[m] at 1 V, every other conductor and
  * the grounded faces at 0 V.  The charge of conductor n is
  * eps0 sum over its panels of eps_a q^a_j |I_j| (farads with lengths in um
- * scaled by 1e-6).  Entries in FP64 (closed-form corner sums for near pairs,
- * Gauss-Legendre for far ones); the matrix is not symmetric and is factored
- * by LU with partial pivoting in FP64.
+ * scaled by 1e-6).  Entries by closed-form corner sums for near pairs and
+ * Gauss-Legendre for far ones; the matrix is not symmetric and is factored
+ * by LU with partial pivoting (see gbem_stack_assemble for the precisions).
  * ------------------------------------------------------------------------- */
 #define GBEM_MAX_LAYERS 16
 #define GBEM_FACE_GROUND (-1)
@@ -532,19 +532,30 @@ gbem_status gbem_stack_info(const gbem_stack_t* s, int* n_panels, int* n_eq, int
  * sign * e_axis), cond_ids (n_cond, ascending: the right-hand sides). */
 gbem_status gbem_stack_panels(const gbem_stack_t* s, int8_t* axis, double* geo, int32_t* kind, int32_t* cond,
                               int32_t* region_a, int32_t* region_b, int8_t* sign, int32_t* cond_ids);
-/* Assemble the system and its right-hand sides on the device (allocates
- * 2 np^2 doubles, np = n_eq rounded up to 64, plus the solve's buffers). */
-gbem_status gbem_stack_assemble(gbem_stack_t* s, gbem_stream stream);
+/* Assemble the system and its right-hand sides on the device.  GBEM_FP64:
+ * every entry in FP64 (closed forms or Gauss-Legendre, about 1e-11
+ * relative), factored by LU in FP64.  GBEM_MIXED: near pairs (gap below 1.5
+ * largest edges) in FP64 closed form, far pairs by FP32 Gauss-Legendre
+ * (about 1e-7 relative), the system kept in FP64 and factored in FP32, the
+ * solve refined against the FP64 system.  Allocates np^2 doubles plus np^2
+ * doubles (FP64) or floats (mixed), np = n_eq rounded up to 64, and the
+ * solve's buffers; enqueues only. */
+gbem_status gbem_stack_assemble(gbem_stack_t* s, gbem_precision prec, gbem_stream stream);
 /* The assembled matrix (n_eq x n_eq, row-major) and right-hand sides
  * (n_eq x n_cond, row-major) on the host; either may be NULL.  Waits. */
 gbem_status gbem_stack_system(gbem_stack_t* s, double* M_host, double* B_host);
 /* Capacitance matrix in farads, n_cond x n_cond row-major into C_host
  * (C[n][m] = charge on conductor cond_ids[n] for right-hand side m).
- * Assembles first if needed, factors once (LU, partial pivoting), solves;
- * resid (may be NULL) receives max over right-hand sides of
- * max |B - M X| / max |B|.  GBEM_ERR_NOT_SPD if a pivot is exactly zero
- * (singular system).  Waits for the stream. */
+ * Assembles first (FP64) if needed, factors once (LU, partial pivoting),
+ * then corrects X += (LU)^-1 P (B - M X), the residual in FP64 against the
+ * assembled system, until max |B - M X| / max |B| over the right-hand sides
+ * is at most the context's ir_tol (1e-11), at most ir_max_iter (10) times;
+ * resid (may be NULL) receives that ratio.  GBEM_ERR_NOT_SPD if a pivot is
+ * exactly zero (singular system), GBEM_ERR_NOCONV if the tolerance is
+ * missed (C_host is still written).  Waits for the stream. */
 gbem_status gbem_stack_capacitance(gbem_stack_t* s, gbem_stream stream, double* C_host, double* resid);
+/* Corrections the last gbem_stack_capacitance made. */
+gbem_status gbem_stack_iterations(const gbem_stack_t* s, int* iters);
 void gbem_stack_destroy(gbem_stack_t* s);
 
 #ifdef __cplusplus

@@ -20,6 +20,7 @@
 // them), the row interchanges are applied to the other columns, a triangular
 // solve forms the panel's block row of U, and a tiled FP64 update applies
 // the panel to the trailing matrix.  No kernel here waits on another CTA.
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "gbem_internal.h"
@@ -31,6 +32,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kGl = 6;   // largest Gauss-Legendre order
 __constant__ double c_sx[kGl + 1][kGl];
 __constant__ double c_sw[kGl + 1][kGl];
+__constant__ float c_sxf[kGl + 1][kGl];
+__constant__ float c_swf[kGl + 1][kGl];
 
 __device__ __forceinline__ int axp(int k) { return k == 0 ? 1 : 0; }
 __device__ __forceinline__ int axq(int k) { return k == 2 ? 1 : 2; }
@@ -40,7 +43,19 @@ struct PanelGeo {
     int axis;
 };
 
+__device__ __forceinline__ float mufu_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // U and D (D: the double layer for the normal +e_k of panel k) of one pair.
+// FP64 mode: closed forms while their cancellation allows (below), FP64
+// Gauss-Legendre for the rest, about 1e-11 relative.  Mixed mode: closed
+// forms below q = 1.5, FP32 Gauss-Legendre (FP64 node offsets, FP32 inner
+// sums, FP64 outer sums) for the rest, about 1e-7 relative.
+template <bool MIXED>
 __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double& D)
 {
     const int ki = I.axis, kk = K.axis;
@@ -69,7 +84,7 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
     // closed forms while their corner sums lose at most about 2e-12
     // (eps R^4 / (|I_i| |I_k|), R the pair's bounding diagonal), and always
     // below q = 3, where the quadrature would need more than 6 points
-    const bool closed = q < 3.0 || (q < 12.0 && R2 * R2 <= 9000.0 * ai * ak);
+    const bool closed = MIXED ? q < 1.5 : (q < 3.0 || (q < 12.0 && R2 * R2 <= 9000.0 * ai * ak));
     if (closed) {
         double su = 0.0, sd = 0.0;
         if (ki == kk) {
@@ -112,8 +127,8 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
         return;
     }
     // tensor Gauss-Legendre of 1/r and (x_k - y_k)/r^3 at shared nodes; the
-    // order for the double layer's relative error below about 1e-11
-    const int n = q >= 320.0 ? 2 : q >= 40.0 ? 3 : q >= 10.0 ? 4 : q >= 5.0 ? 5 : 6;
+    // order for the double layer's relative error below about 1e-11 (FP64)
+    // or 1e-7 (mixed)
     double d0[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) d0[d] = 0.5 * (lo_i[d] + hi_i[d]) - 0.5 * (lo_k[d] + hi_k[d]);
@@ -121,6 +136,39 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
     const double hk_p = 0.5 * (K.hi0 - K.lo0), hk_q = 0.5 * (K.hi1 - K.lo1);
     const int ip = axp(ki), iq = axq(ki), kp = axp(kk), kq = axq(kk);
     double su = 0.0, sd = 0.0;
+    if (MIXED) {
+        const int n = q >= 40.0 ? 2 : q >= 6.0 ? 3 : q >= 3.0 ? 4 : q >= 2.0 ? 5 : 6;
+        const float fp = (float)hi_p, fq = (float)hi_q, gp = (float)hk_p, gq = (float)hk_q;
+#pragma unroll 1
+        for (int a = 0; a < n; ++a)
+#pragma unroll 1
+            for (int b = 0; b < n; ++b) {
+                float x[3] = {(float)d0[0], (float)d0[1], (float)d0[2]};
+                x[ip] += fp * c_sxf[n][a];
+                x[iq] += fq * c_sxf[n][b];
+                float tu = 0.0f, td = 0.0f;
+#pragma unroll 1
+                for (int c = 0; c < n; ++c)
+#pragma unroll 1
+                    for (int d = 0; d < n; ++d) {
+                        float y[3] = {x[0], x[1], x[2]};
+                        y[kp] -= gp * c_sxf[n][c];
+                        y[kq] -= gq * c_sxf[n][d];
+                        const float ri = mufu_rsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+                        const float wcd = c_swf[n][c] * c_swf[n][d];
+                        tu = fmaf(wcd, ri, tu);
+                        td = fmaf(wcd * y[kk], ri * ri * ri, td);
+                    }
+                const double wab = c_sw[n][a] * c_sw[n][b];
+                su = fma(wab, (double)tu, su);
+                sd = fma(wab, (double)td, sd);
+            }
+        const double f = hi_p * hi_q * hk_p * hk_q * (1.0 / (4.0 * kPi));
+        U = su * f;
+        D = sd * f;
+        return;
+    }
+    const int n = q >= 320.0 ? 2 : q >= 40.0 ? 3 : q >= 10.0 ? 4 : q >= 5.0 ? 5 : 6;
 #pragma unroll 1
     for (int a = 0; a < n; ++a)
 #pragma unroll 1
@@ -152,12 +200,13 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
 }
 
 // One 32 x 32 tile of one region's pairs (rows: the region's panels I_i,
-// columns: its panels I_k).  Tiles of region a are tile_off[a] .. .
+// columns: its panels I_k) into M0.  Tiles of region a are tile_off[a] .. .
+template <bool MIXED>
 __global__ void __launch_bounds__(256) stack_assemble(StackView v)
 {
     const long long b = blockIdx.x;
     int a = 0;
-    while (a + 1 < v.R && v.tile_off[a + 1] <= b) ++a;
+    while (a + 1 < v.R_layers && v.tile_off[a + 1] <= b) ++a;
     const int r0 = v.reg_off[a], na = v.reg_off[a + 1] - r0;
     const int nt = (na + 31) / 32;
     const long long t = b - v.tile_off[a];
@@ -182,16 +231,16 @@ __global__ void __launch_bounds__(256) stack_assemble(StackView v)
         if (i < 0 || k < 0) continue;
         const long long row = r0 + ti * 32 + li;
         double U, D;
-        pair_UD(sg[li], sg[32 + lk], U, D);
+        pair_UD<MIXED>(sg[li], sg[32 + lk], U, D);
         const bool own = v.ra[k] == a;
         const double s = own ? (double)v.sign[k] : -(double)v.sign[k];
         double cu = s * D;
         if (i == k) cu += 0.5 * (sg[li].hi0 - sg[li].lo0) * (sg[li].hi1 - sg[li].lo1);
         const double g = own ? 1.0 : -v.eps[v.ra[k]] / ea;
         const size_t ld = (size_t)v.np;
-        if (v.ucol[k] >= 0) v.M[row + (size_t)v.ucol[k] * ld] = cu;
+        if (v.ucol[k] >= 0) v.M0[row + (size_t)v.ucol[k] * ld] = cu;
         else if (v.bcol[k] >= 0) atomicAdd(&v.B[row + (size_t)v.bcol[k] * ld], -cu);
-        if (v.qcol[k] >= 0) v.M[row + (size_t)v.qcol[k] * ld] = -U * g;
+        if (v.qcol[k] >= 0) v.M0[row + (size_t)v.qcol[k] * ld] = -U * g;
     }
 }
 
@@ -202,19 +251,29 @@ __global__ void stack_pad(double* M, int n_eq, int np)
         M[(size_t)r + (size_t)r * np] = 1.0;
 }
 
+// The FP32 copy that the mixed mode factors.
+__global__ void to_f32(const double* __restrict__ A, float* __restrict__ B, size_t count)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        B[e] = (float)A[e];
+}
+
+
 // ------------------------------------------------------------------ LU
 
 constexpr int NB = 64;     // block columns
 constexpr int SUB = 8;     // sub-panel columns
 constexpr int PT = 512;    // panel threads
 
-// argmax of |M[r, c]| over r in [c, np): the first row of the largest value.
-__device__ int block_argmax(const double* __restrict__ col, int c, int np, double* sv, int* si)
+// argmax of |M[r, c]| over r in [c, np): the first row of the largest value
+// (np if no value compares, i.e. NaN entries).
+template <typename T>
+__device__ int block_argmax(const T* __restrict__ col, int c, int np, double* sv, int* si)
 {
     double best = -1.0;
     int bi = np;
     for (int r = c + threadIdx.x; r < np; r += blockDim.x) {
-        const double x = fabs(col[r]);
+        const double x = fabs((double)col[r]);
         if (x > best) {
             best = x;
             bi = r;
@@ -253,18 +312,19 @@ __device__ int block_argmax(const double* __restrict__ col, int c, int np, doubl
 // panel; ipiv[c] = the row swapped with row c at column c.  A zero pivot
 // (or a column without a comparable value) sets *status = GBEM_ERR_NOT_SPD
 // and leaves its column unscaled.
-__global__ void __launch_bounds__(PT) lu_panel(double* __restrict__ M, int np, int j0, int* __restrict__ ipiv,
+template <typename T>
+__global__ void __launch_bounds__(PT) lu_panel(T* __restrict__ M, int np, int j0, int* __restrict__ ipiv,
                                                int* status)
 {
     __shared__ double sv[PT / 32];
     __shared__ int si[PT / 32];
-    __shared__ double urow[NB];
-    __shared__ double ublk[SUB][NB];
+    __shared__ T urow[NB];
+    __shared__ T ublk[SUB][NB];
     const size_t ld = (size_t)np;
     const int tid = threadIdx.x;
     for (int s0 = j0; s0 < j0 + NB; s0 += SUB) {
         for (int c = s0; c < s0 + SUB; ++c) {
-            double* col = M + (size_t)c * ld;
+            T* col = M + (size_t)c * ld;
             int p = block_argmax(col, c, np, sv, si);
             if (p >= np) {   // no comparable value (NaN entries): keep the row, flag the system
                 p = c;
@@ -273,27 +333,27 @@ __global__ void __launch_bounds__(PT) lu_panel(double* __restrict__ M, int np, i
             if (tid == 0) ipiv[c] = p;
             // swap rows c and p across the panel's columns
             if (p != c && tid < NB) {
-                double* e = M + (size_t)(j0 + tid) * ld;
-                const double t = e[c];
+                T* e = M + (size_t)(j0 + tid) * ld;
+                const T t = e[c];
                 e[c] = e[p];
                 e[p] = t;
             }
             __syncthreads();
-            const double piv = col[c];
-            if (piv == 0.0) {
+            const T piv = col[c];
+            if (piv == T(0)) {
                 if (tid == 0) atomicExch(status, (int)GBEM_ERR_NOT_SPD);
                 __syncthreads();
                 continue;
             }
             if (tid < s0 + SUB - c - 1) urow[tid] = M[(size_t)c + (size_t)(c + 1 + tid) * ld];
             __syncthreads();
-            const double inv = 1.0 / piv;
+            const T inv = T(1) / piv;
             const int ncol = s0 + SUB - c - 1;
             for (int r = c + 1 + tid; r < np; r += PT) {
-                const double l = col[r] * inv;
+                const T l = col[r] * inv;
                 col[r] = l;
                 for (int k = 0; k < ncol; ++k) {
-                    double* e = M + (size_t)(c + 1 + k) * ld + r;
+                    T* e = M + (size_t)(c + 1 + k) * ld + r;
                     *e = fma(-l, urow[k], *e);
                 }
             }
@@ -305,10 +365,10 @@ __global__ void __launch_bounds__(PT) lu_panel(double* __restrict__ M, int np, i
         // panel columns, L_ss^-1 times them (unit lower 8 x 8)
         if (tid < rest) {
             const int cc = s0 + SUB + tid;
-            double x[SUB];
+            T x[SUB];
 #pragma unroll
             for (int r = 0; r < SUB; ++r) {
-                double t = M[(size_t)(s0 + r) + (size_t)cc * ld];
+                T t = M[(size_t)(s0 + r) + (size_t)cc * ld];
 #pragma unroll
                 for (int k = 0; k < r; ++k) t = fma(-M[(size_t)(s0 + r) + (size_t)(s0 + k) * ld], x[k], t);
                 x[r] = t;
@@ -322,12 +382,12 @@ __global__ void __launch_bounds__(PT) lu_panel(double* __restrict__ M, int np, i
         __syncthreads();
         // rank-8 update of the rows below
         for (int r = s0 + SUB + tid; r < np; r += PT) {
-            double l[SUB];
+            T l[SUB];
 #pragma unroll
             for (int k = 0; k < SUB; ++k) l[k] = M[(size_t)r + (size_t)(s0 + k) * ld];
             for (int j = 0; j < rest; ++j) {
-                double* e = M + (size_t)(s0 + SUB + j) * ld + r;
-                double t = *e;
+                T* e = M + (size_t)(s0 + SUB + j) * ld + r;
+                T t = *e;
 #pragma unroll
                 for (int k = 0; k < SUB; ++k) t = fma(-l[k], ublk[k][j], t);
                 *e = t;
@@ -337,8 +397,155 @@ __global__ void __launch_bounds__(PT) lu_panel(double* __restrict__ M, int np, i
     }
 }
 
+// The FP32 panel factorisation across a thread-block cluster: CTA r of the
+// cluster holds rows j0 + r*rows .. of the panel's 64 columns in shared
+// memory (row-major, rows padded to 65 floats).  Per column every CTA publishes its
+// candidate pivot (|value|, row, the row's 64 values) and, if it owns the
+// diagonal row, that row, in a slot of its own shared memory; after one
+// cluster barrier every CTA reads the slots of all CTAs (distributed shared
+// memory), takes the largest candidate (the first row on a tie), swaps rows
+// locally and applies the rank-1 update to its rows.  The slots alternate
+// between two buffers, so the next column's barrier also orders this
+// column's reads before their reuse.  Same results as lu_panel's partial
+// pivoting; a zero or incomparable pivot sets *status.
+struct PivotSlot {
+    float val;
+    int row;
+    float vals[NB];
+};
+constexpr int LDA = NB + 1;   // shared row stride: a column's rows fall in distinct banks
+constexpr size_t kPanelSmemMax = 220 * 1024;
+constexpr size_t panel_cluster_smem(int rows) { return sizeof(float) * (size_t)rows * LDA + 4 * sizeof(PivotSlot); }
+
+__global__ void __launch_bounds__(256) lu_panel_cluster(float* __restrict__ M, int np, int j0, int rows,
+                                                       int* __restrict__ ipiv, int* status)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), csize = (int)cluster.num_blocks();
+    extern __shared__ float psm[];
+    float* A = psm;                                                   // rows x LDA
+    PivotSlot* cand = reinterpret_cast<PivotSlot*>(psm + (size_t)rows * LDA);  // [2]
+    PivotSlot* diag = cand + 2;                                       // [2]: the diagonal row
+    __shared__ float pivrow[NB], oldrow[NB];
+    __shared__ float wv[8];
+    __shared__ int wi[8];
+    __shared__ int win_rank, win_row, diag_rank;
+    const size_t ld = (size_t)np;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int base = j0 + rank * rows;                                // first global row held here
+    const int mine = max(0, min(rows, np - base));                    // rows held
+    for (int e = tid; e < mine * NB; e += nt) {
+        const int i = e % mine, j = e / mine;
+        A[(size_t)i * LDA + j] = M[(size_t)(base + i) + (size_t)(j0 + j) * ld];
+    }
+    __syncthreads();
+    for (int c = 0; c < NB; ++c) {
+        const int g = j0 + c, buf = c & 1;
+        // local candidate among the held rows >= g
+        float best = -1.0f;
+        int bi = np;
+        for (int i = tid; i < mine; i += nt) {
+            const int r = base + i;
+            if (r < g) continue;
+            const float x = fabsf(A[(size_t)i * LDA + c]);
+            if (x > best) {
+                best = x;
+                bi = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if ((tid & 31) == 0) {
+            wv[tid >> 5] = best;
+            wi[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < nt / 32; ++k)
+                if (wv[k] > wv[0] || (wv[k] == wv[0] && wi[k] < wi[0])) {
+                    wv[0] = wv[k];
+                    wi[0] = wi[k];
+                }
+            cand[buf].val = wv[0];
+            cand[buf].row = wi[0];
+        }
+        __syncthreads();
+        const int lrow = wi[0];
+        if (tid < NB) {
+            cand[buf].vals[tid] = lrow < np ? A[(size_t)(lrow - base) * LDA + tid] : 0.0f;
+            if (g >= base && g < base + mine) diag[buf].vals[tid] = A[(size_t)(g - base) * LDA + tid];
+        }
+        cluster.sync();
+        // the winner over the cluster, and the two rows it exchanges
+        if (tid == 0) {
+            float bv = -1.0f;
+            int br = np, bk = 0;
+            for (int k = 0; k < csize; ++k) {
+                const PivotSlot* o = cluster.map_shared_rank(cand + buf, k);
+                if (o->val > bv || (o->val == bv && o->row < br)) {
+                    bv = o->val;
+                    br = o->row;
+                    bk = k;
+                }
+            }
+            if (br >= np) {   // no comparable value: keep the diagonal row
+                br = g;
+                bk = (g - j0) / rows;
+                if (rank == 0) atomicExch(status, (int)GBEM_ERR_NOT_SPD);
+            }
+            win_rank = bk;
+            win_row = br;
+            diag_rank = (g - j0) / rows;
+            if (rank == 0) ipiv[g] = br;
+        }
+        __syncthreads();
+        const int w = win_row;
+        if (tid < NB) {
+            const PivotSlot* ws = cluster.map_shared_rank(cand + buf, win_rank);
+            const PivotSlot* ds = cluster.map_shared_rank(diag + buf, diag_rank);
+            pivrow[tid] = w == g ? ds->vals[tid] : ws->vals[tid];
+            oldrow[tid] = ds->vals[tid];
+        }
+        __syncthreads();
+        if (tid < NB) {
+            if (g >= base && g < base + mine) A[(size_t)(g - base) * LDA + tid] = pivrow[tid];
+            if (w != g && w >= base && w < base + mine) A[(size_t)(w - base) * LDA + tid] = oldrow[tid];
+        }
+        __syncthreads();
+        const float piv = pivrow[c];
+        if (piv == 0.0f) {
+            if (rank == 0 && tid == 0) atomicExch(status, (int)GBEM_ERR_NOT_SPD);
+        } else {
+            const float inv = 1.0f / piv;
+            for (int i = tid; i < mine; i += nt) {
+                if (base + i <= g) continue;
+                float* a = A + (size_t)i * LDA;
+                const float l = a[c] * inv;
+                a[c] = l;
+                for (int j = c + 1; j < NB; ++j) a[j] = fmaf(-l, pivrow[j], a[j]);
+            }
+        }
+        __syncthreads();
+    }
+    // the next kernel reads the other CTAs' rows only through global memory
+    cluster.sync();
+    for (int e = tid; e < mine * NB; e += nt) {
+        const int i = e % mine, j = e / mine;
+        M[(size_t)(base + i) + (size_t)(j0 + j) * ld] = A[(size_t)i * LDA + j];
+    }
+}
+
 // The panel's interchanges applied, in order, to every column outside it.
-__global__ void lu_swap(double* __restrict__ M, int np, int j0, const int* __restrict__ ipiv)
+template <typename T>
+__global__ void lu_swap(T* __restrict__ M, int np, int j0, const int* __restrict__ ipiv)
 {
     __shared__ int piv[NB];
     if (threadIdx.x < NB) piv[threadIdx.x] = ipiv[j0 + threadIdx.x];
@@ -346,11 +553,11 @@ __global__ void lu_swap(double* __restrict__ M, int np, int j0, const int* __res
     const int ncols = np - NB;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncols; t += gridDim.x * blockDim.x) {
         const int c = t < j0 ? t : t + NB;
-        double* e = M + (size_t)c * np;
+        T* e = M + (size_t)c * np;
         for (int k = 0; k < NB; ++k) {
             const int p = piv[k], r = j0 + k;
             if (p != r) {
-                const double x = e[r];
+                const T x = e[r];
                 e[r] = e[p];
                 e[p] = x;
             }
@@ -359,9 +566,10 @@ __global__ void lu_swap(double* __restrict__ M, int np, int j0, const int* __res
 }
 
 // U12 = L11^-1 A12 for 64 columns per CTA (L11 the panel's unit lower block).
-__global__ void __launch_bounds__(NB) lu_trsm(double* __restrict__ M, int np, int j0)
+template <typename T>
+__global__ void __launch_bounds__(NB) lu_trsm(T* __restrict__ M, int np, int j0)
 {
-    __shared__ double L[NB][NB + 1];
+    __shared__ T L[NB][NB + 1];
     const size_t ld = (size_t)np;
     const int tid = threadIdx.x;
     for (int e = tid; e < NB * NB; e += NB) {
@@ -370,13 +578,13 @@ __global__ void __launch_bounds__(NB) lu_trsm(double* __restrict__ M, int np, in
     }
     __syncthreads();
     const int cc = j0 + NB + blockIdx.x * NB + tid;
-    double* col = M + (size_t)cc * ld + j0;
-    double x[NB];
+    T* col = M + (size_t)cc * ld + j0;
+    T x[NB];
 #pragma unroll
     for (int r = 0; r < NB; ++r) x[r] = col[r];
 #pragma unroll
     for (int r = 1; r < NB; ++r) {
-        double t = x[r];
+        T t = x[r];
 #pragma unroll
         for (int k = 0; k < r; ++k) t = fma(-L[r][k], x[k], t);
         x[r] = t;
@@ -385,12 +593,12 @@ __global__ void __launch_bounds__(NB) lu_trsm(double* __restrict__ M, int np, in
     for (int r = 0; r < NB; ++r) col[r] = x[r];
 }
 
-// A22 -= L21 U12, one 64 x 64 tile per CTA, 4 x 4 outputs per thread.
-constexpr size_t kGemmSmem = 2 * sizeof(double) * NB * (NB + 1);
-__global__ void __launch_bounds__(256) lu_gemm(double* __restrict__ M, int np, int j0)
+// A22 -= L21 U12 in FP64: one 64 x 64 tile per CTA, 4 x 4 outputs per thread.
+constexpr size_t kGemmSmem64 = 2 * sizeof(double) * NB * (NB + 1);
+__global__ void __launch_bounds__(256) lu_gemm_f64(double* __restrict__ M, int np, int j0)
 {
     extern __shared__ double gsm[];
-    double(*Ls)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(gsm);            // Ls[k][r] = L21[r][k]
+    double(*Ls)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(gsm);                  // Ls[k][r] = L21[r][k]
     double(*Us)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(gsm + NB * (NB + 1));  // Us[k][c] = U12[k][c]
     const size_t ld = (size_t)np;
     const int i0 = j0 + NB + blockIdx.x * NB, c0 = j0 + NB + blockIdx.y * NB;
@@ -425,6 +633,57 @@ __global__ void __launch_bounds__(256) lu_gemm(double* __restrict__ M, int np, i
         }
 }
 
+// A22 -= L21 U12 in FP32: one 128 x 128 tile per CTA, 8 x 8 outputs per
+// thread (rows tx + 16 i, columns ty + 16 j), K = 64; the trailing order is a
+// multiple of 64, so edge tiles skip their missing half.
+constexpr int GT = 128;
+constexpr size_t kGemmSmem32 = 2 * sizeof(float) * NB * (GT + 4);
+__global__ void __launch_bounds__(256) lu_gemm_f32(float* __restrict__ M, int np, int j0)
+{
+    extern __shared__ float fsm[];
+    float(*Ls)[GT + 4] = reinterpret_cast<float(*)[GT + 4]>(fsm);                   // Ls[k][r]
+    float(*Us)[GT + 4] = reinterpret_cast<float(*)[GT + 4]>(fsm + NB * (GT + 4));  // Us[k][c]
+    const size_t ld = (size_t)np;
+    const int base = j0 + NB;
+    const int i0 = base + blockIdx.x * GT, c0 = base + blockIdx.y * GT;
+    const int rows = min(GT, np - i0), cols = min(GT, np - c0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * GT; e += 256) {
+        const int r = e % GT, k = e / GT;
+        Ls[k][r] = r < rows ? M[(size_t)(i0 + r) + (size_t)(j0 + k) * ld] : 0.0f;
+    }
+    for (int e = tid; e < NB * GT; e += 256) {
+        const int k = e % NB, c = e / NB;
+        Us[k][c] = c < cols ? M[(size_t)(j0 + k) + (size_t)(c0 + c) * ld] : 0.0f;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[8][8] = {};
+#pragma unroll 2
+    for (int k = 0; k < NB; ++k) {
+        float a[8], b[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            a[x] = Ls[k][tx + 16 * x];
+            b[x] = Us[k][ty + 16 * x];
+        }
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+        const int c = ty + 16 * y;
+        if (c >= cols) continue;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int r = tx + 16 * x;
+            if (r < rows) M[(size_t)(i0 + r) + (size_t)(c0 + c) * ld] -= acc[x][y];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ solve
 
 // perm[r] = the original row that ends at row r after ipiv[0..np-1].
@@ -444,32 +703,32 @@ __global__ void __launch_bounds__(256) lu_perm(const int* __restrict__ ipiv, int
     for (int r = threadIdx.x; r < np; r += blockDim.x) perm[r] = sperm[r];
 }
 
-// X[r, m] = B[perm[r], m]
-__global__ void permute_rhs(const double* __restrict__ B, const int* __restrict__ perm, int np, int nc,
-                            double* __restrict__ X)
+// W[r, m] = R[perm[r], m] in the factor's type.
+template <typename T>
+__global__ void permute_rhs(const double* __restrict__ R, const int* __restrict__ perm, int np, int nc,
+                            T* __restrict__ W)
 {
     const long long total = (long long)np * nc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e % np), m = (int)(e / np);
-        X[e] = B[(size_t)perm[r] + (size_t)m * np];
+        W[e] = (T)R[(size_t)perm[r] + (size_t)m * np];
     }
 }
 
 // Diagonal block b of the forward (unit lower) or backward (upper) sweep:
 // X_b := T_bb^-1 X_b; thread r owns row r of the block, 16 right-hand sides
 // at a time, one barrier per eliminated row.
-template <bool LOWER>
-__global__ void __launch_bounds__(NB) tri_block(const double* __restrict__ M, int np, int b, int nc,
-                                                double* __restrict__ X)
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(NB) tri_block(const T* __restrict__ M, int np, int b, int nc, T* __restrict__ X)
 {
-    __shared__ double T[NB][NB + 1];
-    __shared__ double xs[NB][17];
+    __shared__ T Tb[NB][NB + 1];
+    __shared__ T xs[NB][17];
     const size_t ld = (size_t)np;
     const int j0 = b * NB, r = threadIdx.x;
     for (int e = threadIdx.x; e < NB * NB; e += NB) {
         const int i = e % NB, c = e / NB;
-        T[i][c] = M[(size_t)(j0 + i) + (size_t)(j0 + c) * ld];
+        Tb[i][c] = M[(size_t)(j0 + i) + (size_t)(j0 + c) * ld];
     }
     for (int m0 = 0; m0 < nc; m0 += 16) {
         const int mn = min(16, nc - m0);
@@ -479,16 +738,16 @@ __global__ void __launch_bounds__(NB) tri_block(const double* __restrict__ M, in
         if (LOWER) {
             for (int k = 0; k < NB - 1; ++k) {
                 if (r > k)
-                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-T[r][k], xs[k][m], xs[r][m]);
+                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-Tb[r][k], xs[k][m], xs[r][m]);
                 __syncthreads();
             }
         } else {
             for (int k = NB - 1; k >= 0; --k) {
                 if (r == k)
-                    for (int m = 0; m < mn; ++m) xs[k][m] = xs[k][m] / T[k][k];
+                    for (int m = 0; m < mn; ++m) xs[k][m] = xs[k][m] / Tb[k][k];
                 __syncthreads();
                 if (r < k)
-                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-T[r][k], xs[k][m], xs[r][m]);
+                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-Tb[r][k], xs[k][m], xs[r][m]);
                 __syncthreads();
             }
         }
@@ -496,49 +755,112 @@ __global__ void __launch_bounds__(NB) tri_block(const double* __restrict__ M, in
     }
 }
 
-// X[r] -= M[r, block b] X_b for the rows below block b (LOWER) or above it.
-template <bool LOWER>
-__global__ void __launch_bounds__(256) tri_update(const double* __restrict__ M, int np, int b, int nc,
-                                                  double* __restrict__ X)
+// X[r] -= M[r, block b] X_b for the rows below block b (LOWER) or above it;
+// NR right-hand sides per pass, the block row's 64 entries loaded 16 at a time.
+template <typename T, bool LOWER, int NR>
+__global__ void __launch_bounds__(256) tri_update(const T* __restrict__ M, int np, int b, int nc, T* __restrict__ X)
 {
-    __shared__ double xb[16][NB];
+    __shared__ T xb[NR][NB];
     const size_t ld = (size_t)np;
     const int j0 = b * NB;
     const int rlo = LOWER ? j0 + NB : 0, rhi = LOWER ? np : j0;
-    for (int m0 = 0; m0 < nc; m0 += 16) {
-        const int mn = min(16, nc - m0);
+    for (int m0 = 0; m0 < nc; m0 += NR) {
+        const int mn = min(NR, nc - m0);
         __syncthreads();
-        for (int e = threadIdx.x; e < mn * NB; e += blockDim.x)
-            xb[e / NB][e % NB] = X[(size_t)(m0 + e / NB) * np + j0 + e % NB];
+        for (int e = threadIdx.x; e < NR * NB; e += blockDim.x)
+            xb[e / NB][e % NB] = e / NB < mn ? X[(size_t)(m0 + e / NB) * np + j0 + e % NB] : T(0);
         __syncthreads();
         for (int r = rlo + blockIdx.x * blockDim.x + threadIdx.x; r < rhi; r += gridDim.x * blockDim.x) {
-            double acc[16] = {};
-            for (int k = 0; k < NB; ++k) {
-                const double l = M[(size_t)r + (size_t)(j0 + k) * ld];
+            T acc[NR] = {};
+            const T* row = M + (size_t)r + (size_t)j0 * ld;
+#pragma unroll 1
+            for (int k0 = 0; k0 < NB; k0 += 16) {
+                T l[16];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) acc[m] = fma(l, xb[m][k], acc[m]);
+                for (int k = 0; k < 16; ++k) l[k] = row[(size_t)(k0 + k) * ld];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+#pragma unroll
+                    for (int m = 0; m < NR; ++m) acc[m] = fma(l[k], xb[m][k0 + k], acc[m]);
             }
             for (int m = 0; m < mn; ++m) X[(size_t)(m0 + m) * np + r] -= acc[m];
         }
     }
 }
 
-// R = B - M X over the first n_eq rows; rnorm[m] = max |R[., m]| / max |B[., m]|
-// accumulated by atomicMax on the bit patterns of non-negative doubles.
-__global__ void __launch_bounds__(256) stack_residual(const double* __restrict__ M, int n_eq, int np, int nc,
-                                                      const double* __restrict__ B, const double* __restrict__ X,
-                                                      unsigned long long* rmax, unsigned long long* bmax)
+template <typename T, bool LOWER>
+void launch_tri_update(const T* M, int np, int b, int nc, T* X, cudaStream_t s)
+{
+    const int j0 = b * NB;
+    const int rows = LOWER ? np - j0 - NB : j0;
+    const int grid = max(1, min(2 * 152, (rows + 255) / 256));
+    if (nc <= 4) tri_update<T, LOWER, 4><<<grid, 256, 0, s>>>(M, np, b, nc, X);
+    else if (nc <= 8) tri_update<T, LOWER, 8><<<grid, 256, 0, s>>>(M, np, b, nc, X);
+    else tri_update<T, LOWER, 16><<<grid, 256, 0, s>>>(M, np, b, nc, X);
+    count_launch();
+}
+
+// X += W
+template <typename T>
+__global__ void add_correction(double* __restrict__ X, const T* __restrict__ W, size_t count)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        X[e] += (double)W[e];
+}
+
+// Partial products of M0 X in FP64: chunk blockIdx.y of the columns, rows
+// blockIdx.x * 128 + threadIdx.x, up to 16 right-hand sides per pass;
+// P[(chunk * nc + m) * np + r].
+constexpr int kResChunks = 8;
+__global__ void __launch_bounds__(128) residual_partial(const double* __restrict__ M0, int n_eq, int np, int nc,
+                                                        const double* __restrict__ X, double* __restrict__ P)
 {
     const size_t ld = (size_t)np;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_eq; r += gridDim.x * blockDim.x)
-        for (int m = 0; m < nc; ++m) {
-            double t = B[(size_t)r + (size_t)m * ld];
-            const double b = fabs(t);
-            const double* x = X + (size_t)m * ld;
-            for (int c = 0; c < n_eq; ++c) t = fma(-M[(size_t)r + (size_t)c * ld], x[c], t);
-            atomicMax(rmax + m, (unsigned long long)__double_as_longlong(fabs(t)));
-            atomicMax(bmax + m, (unsigned long long)__double_as_longlong(b));
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = (n_eq + kResChunks - 1) / kResChunks;
+    const int c_lo = blockIdx.y * per, c_hi = min(n_eq, c_lo + per);
+    __shared__ double xs[16][128];
+    for (int m0 = 0; m0 < nc; m0 += 16) {
+        const int mn = min(16, nc - m0);
+        double acc[16] = {};
+        for (int cb = c_lo; cb < c_hi; cb += 128) {
+            const int cn = min(128, c_hi - cb);
+            __syncthreads();
+            for (int e = threadIdx.x; e < 16 * 128; e += blockDim.x) {
+                const int m = e / 128, c = e % 128;
+                xs[m][c] = (m < mn && c < cn) ? X[(size_t)(cb + c) + (size_t)(m0 + m) * ld] : 0.0;
+            }
+            __syncthreads();
+            if (r < n_eq)
+                for (int c = 0; c < cn; ++c) {
+                    const double a = M0[(size_t)r + (size_t)(cb + c) * ld];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) acc[m] = fma(a, xs[m][c], acc[m]);
+                }
         }
+        if (r < n_eq)
+            for (int m = 0; m < mn; ++m) P[((size_t)blockIdx.y * nc + m0 + m) * ld + r] = acc[m];
+    }
+}
+
+// R = B - sum of the partials (rows < n_eq; 0 below); rnorm[m] = max |R[., m]|,
+// bnorm[m] = max |B[., m]| as the bit patterns of non-negative doubles.
+__global__ void residual_finish(const double* __restrict__ B, const double* __restrict__ P, int n_eq, int np, int nc,
+                                double* __restrict__ R, unsigned long long* rmax, unsigned long long* bmax)
+{
+    const long long total = (long long)np * nc;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % np), m = (int)(e / np);
+        double t = 0.0;
+        if (r < n_eq) {
+            t = B[e];
+            for (int k = 0; k < kResChunks; ++k) t -= P[((size_t)k * nc + m) * np + r];
+            atomicMax(rmax + m, (unsigned long long)__double_as_longlong(fabs(t)));
+            atomicMax(bmax + m, (unsigned long long)__double_as_longlong(fabs(B[e])));
+        }
+        R[e] = t;
+    }
 }
 
 // C[n][m] = eps0 1e-6 sum over conductor n's panels of eps_a |I_j| q_j (X's
@@ -561,108 +883,236 @@ __global__ void __launch_bounds__(256) stack_charges(StackView v, const double* 
     if (threadIdx.x == 0) v.C[(size_t)nidx * v.nc + m] = eps0 * 1e-6 * red[0];
 }
 
+// Cluster size for the FP32 panel (16 where the device schedules such
+// clusters with the largest shared memory, else 8), 0 if neither.
+int panel_cluster_size()
+{
+    static int dev_sizes[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (known[dev]) return dev_sizes[dev];
+    int best = 0;
+    const size_t smem = kPanelSmemMax;
+    if (cudaFuncSetAttribute(lu_panel_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+        cudaFuncSetAttribute(lu_panel_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        for (int cs : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cs;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cs);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = smem;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, lu_panel_cluster, &cfg) == cudaSuccess && n > 0) {
+                best = cs;
+                break;
+            }
+        }
+    }
+    cudaGetLastError();
+    dev_sizes[dev] = best;
+    known[dev] = true;
+    return best;
+}
+
+// One panel in FP32 through a cluster when its rows fit the cluster's shared
+// memory; false if not (the caller uses lu_panel).
+bool panel_f32_cluster(float* M, int np, int j0, const StackView& v, int csize, cudaStream_t s, cudaError_t& err)
+{
+    if (csize <= 0) return false;
+    const int m = np - j0;
+    const int rows = (m + csize - 1) / csize;
+    const size_t smem = panel_cluster_smem(rows);
+    if (smem > kPanelSmemMax) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, lu_panel_cluster, M, np, j0, rows, v.ipiv, v.status);
+    count_launch();
+    return true;
+}
+
+template <typename T>
+cudaError_t lu_run(T* M, const StackView& v, cudaStream_t s)
+{
+    const int np = v.np;
+    const int csize = sizeof(T) == 4 ? panel_cluster_size() : 0;
+    for (int j0 = 0; j0 < np; j0 += NB) {
+        cudaError_t e = cudaSuccess;
+        bool done = false;
+        if constexpr (sizeof(T) == 4) done = panel_f32_cluster(M, np, j0, v, csize, s, e);
+        if (e != cudaSuccess) return e;
+        if (!done) {
+            lu_panel<T><<<1, PT, 0, s>>>(M, np, j0, v.ipiv, v.status);
+            count_launch();
+        }
+        lu_swap<T><<<(np + 255) / 256, 256, 0, s>>>(M, np, j0, v.ipiv);
+        count_launch();
+        const int nrest = (np - j0 - NB) / NB;
+        if (nrest > 0) {
+            lu_trsm<T><<<nrest, NB, 0, s>>>(M, np, j0);
+            if constexpr (sizeof(T) == 8) {
+                lu_gemm_f64<<<dim3(nrest, nrest), 256, kGemmSmem64, s>>>(M, np, j0);
+            } else {
+                const int nt = (nrest * NB + GT - 1) / GT;
+                lu_gemm_f32<<<dim3(nt, nt), 256, kGemmSmem32, s>>>(M, np, j0);
+            }
+            count_launch(2);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sweeps(const T* M, const StackView& v, T* W, cudaStream_t s)
+{
+    const int np = v.np, nb = np / NB;
+    for (int b = 0; b < nb; ++b) {
+        tri_block<T, true><<<1, NB, 0, s>>>(M, np, b, v.nc, W);
+        count_launch();
+        if (b + 1 < nb) launch_tri_update<T, true>(M, np, b, v.nc, W, s);
+    }
+    for (int b = nb - 1; b >= 0; --b) {
+        tri_block<T, false><<<1, NB, 0, s>>>(M, np, b, v.nc, W);
+        count_launch();
+        if (b > 0) launch_tri_update<T, false>(M, np, b, v.nc, W, s);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t stack_gl_upload(cudaStream_t s)
 {
     static double hx[kGl + 1][kGl], hw[kGl + 1][kGl];
+    static float fx[kGl + 1][kGl], fw[kGl + 1][kGl];
     static bool ready = false;
     if (!ready) {
         hx[1][0] = 0.0;
         hw[1][0] = 2.0;
         for (int n = 2; n <= kGl; ++n) gl_nodes(n, hx[n], hw[n]);
+        for (int n = 1; n <= kGl; ++n)
+            for (int i = 0; i < n; ++i) {
+                fx[n][i] = (float)hx[n][i];
+                fw[n][i] = (float)hw[n][i];
+            }
         ready = true;
     }
     cudaError_t e = cudaMemcpyToSymbolAsync(c_sx, hx, sizeof(hx), 0, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_sw, hw, sizeof(hw), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_sxf, fx, sizeof(fx), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_swf, fw, sizeof(fw), 0, cudaMemcpyHostToDevice, s);
     return e;
 }
 
-cudaError_t launch_stack_assemble(const StackView& v, long long tiles, cudaStream_t s)
+cudaError_t launch_stack_assemble(const StackView& v, long long tiles, bool mixed, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(v.M, 0, sizeof(double) * (size_t)v.np * v.np, s);
+    const size_t entries = (size_t)v.np * v.np;
+    cudaError_t e = cudaMemsetAsync(v.M0, 0, sizeof(double) * entries, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.B, 0, sizeof(double) * (size_t)v.np * v.nc, s);
     if (e != cudaSuccess) return e;
     cudaEvent_t ev = trace_begin(s);
-    stack_assemble<<<(unsigned)tiles, 256, 0, s>>>(v);
+    if (mixed) stack_assemble<true><<<(unsigned)tiles, 256, 0, s>>>(v);
+    else stack_assemble<false><<<(unsigned)tiles, 256, 0, s>>>(v);
     count_launch();
     trace_end(GBEM_KERNEL_ASSEMBLE, ev, s, 8.0 * (double)v.n_eq * v.n_eq, 0.0);
     if (v.np > v.n_eq) {
-        stack_pad<<<(v.np - v.n_eq + 255) / 256, 256, 0, s>>>(v.M, v.n_eq, v.np);
+        stack_pad<<<(v.np - v.n_eq + 255) / 256, 256, 0, s>>>(v.M0, v.n_eq, v.np);
         count_launch();
+    }
+    // the copy the factorisation overwrites
+    if (mixed) {
+        to_f32<<<1024, 256, 0, s>>>(v.M0, v.M32, entries);
+        count_launch();
+    } else {
+        e = cudaMemcpyAsync(v.M, v.M0, sizeof(double) * entries, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_stack_lu(const StackView& v, cudaStream_t s)
+cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s)
 {
-    const int np = v.np;
-    cudaError_t e = cudaFuncSetAttribute(lu_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    cudaError_t e = mixed ? cudaFuncSetAttribute(lu_gemm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kGemmSmem32)
+                          : cudaFuncSetAttribute(lu_gemm_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kGemmSmem64);
     if (e != cudaSuccess) return e;
+    const size_t perm_smem = sizeof(int) * (size_t)v.np;
+    if (perm_smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(lu_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)perm_smem);
+        if (e != cudaSuccess) return e;
+    }
     // traced as one span per factorisation: 2 np^3 / 3 flop, the matrix read
     // and written once
     cudaEvent_t ev = trace_begin(s);
-    for (int j0 = 0; j0 < np; j0 += NB) {
-        lu_panel<<<1, PT, 0, s>>>(v.M, np, j0, v.ipiv, v.status);
-        lu_swap<<<(np + 255) / 256, 256, 0, s>>>(v.M, np, j0, v.ipiv);
-        count_launch(2);
-        const int nrest = (np - j0 - NB) / NB;
-        if (nrest > 0) {
-            lu_trsm<<<nrest, NB, 0, s>>>(v.M, np, j0);
-            lu_gemm<<<dim3(nrest, nrest), 256, kGemmSmem, s>>>(v.M, np, j0);
-            count_launch(2);
-        }
-    }
-    const double n = (double)np;
-    trace_end(GBEM_KERNEL_FACTOR, ev, s, 16.0 * n * n, 2.0 * n * n * n / 3.0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stack_solve(const StackView& v, double* X, int* perm, unsigned long long* norms,
-                               double eps0, cudaStream_t s)
-{
-    const int np = v.np, nb = np / NB;
-    const size_t perm_smem = sizeof(int) * (size_t)np;
-    if (perm_smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(lu_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)perm_smem);
-        if (e != cudaSuccess) return e;
-    }
-    lu_perm<<<1, 256, perm_smem, s>>>(v.ipiv, np, perm);
-    permute_rhs<<<256, 256, 0, s>>>(v.B, perm, np, v.nc, X);
-    count_launch(2);
-    const int ug = 2 * 152;
-    // the two sweeps as one traced span: the factor read once, 2 np^2 nc flop
-    cudaEvent_t ev = trace_begin(s);
-    for (int b = 0; b < nb; ++b) {
-        tri_block<true><<<1, NB, 0, s>>>(v.M, np, b, v.nc, X);
-        count_launch();
-        if (b + 1 < nb) {
-            tri_update<true><<<ug, 256, 0, s>>>(v.M, np, b, v.nc, X);
-            count_launch();
-        }
-    }
-    for (int b = nb - 1; b >= 0; --b) {
-        tri_block<false><<<1, NB, 0, s>>>(v.M, np, b, v.nc, X);
-        count_launch();
-        if (b > 0) {
-            tri_update<false><<<ug, 256, 0, s>>>(v.M, np, b, v.nc, X);
-            count_launch();
-        }
-    }
-    trace_end(GBEM_KERNEL_SWEEP, ev, s, 8.0 * (double)np * np, 2.0 * (double)np * np * v.nc);
-    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(unsigned long long) * 2 * (size_t)v.nc, s);
+    e = mixed ? lu_run<float>(v.M32, v, s) : lu_run<double>(v.M, v, s);
+    const double n = (double)v.np;
+    trace_end(GBEM_KERNEL_FACTOR, ev, s, (mixed ? 8.0 : 16.0) * n * n, 2.0 * n * n * n / 3.0);
     if (e != cudaSuccess) return e;
-    stack_charges<<<dim3(v.nc, v.nc), 256, 0, s>>>(v, X, eps0);
+    lu_perm<<<1, 256, perm_smem, s>>>(v.ipiv, v.np, v.perm);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_stack_residual(const StackView& v, const double* M0, const double* X,
-                                  unsigned long long* norms, cudaStream_t s)
+cudaError_t launch_stack_correct(const StackView& v, bool mixed, cudaStream_t s)
 {
+    const size_t count = (size_t)v.np * v.nc;
     cudaEvent_t ev = trace_begin(s);
-    stack_residual<<<(v.n_eq + 255) / 256, 256, 0, s>>>(M0, v.n_eq, v.np, v.nc, v.B, X, norms, norms + v.nc);
+    cudaError_t e;
+    if (mixed) {
+        float* W = reinterpret_cast<float*>(v.W);
+        permute_rhs<float><<<256, 256, 0, s>>>(v.R, v.perm, v.np, v.nc, W);
+        count_launch();
+        e = sweeps<float>(v.M32, v, W, s);
+        add_correction<float><<<256, 256, 0, s>>>(v.X, W, count);
+    } else {
+        double* W = reinterpret_cast<double*>(v.W);
+        permute_rhs<double><<<256, 256, 0, s>>>(v.R, v.perm, v.np, v.nc, W);
+        count_launch();
+        e = sweeps<double>(v.M, v, W, s);
+        add_correction<double><<<256, 256, 0, s>>>(v.X, W, count);
+    }
     count_launch();
+    // the two sweeps as one traced span: the factor read once, 2 np^2 nc flop
+    const double n = (double)v.np;
+    trace_end(GBEM_KERNEL_SWEEP, ev, s, (mixed ? 4.0 : 8.0) * n * n, 2.0 * n * n * v.nc);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stack_residual(const StackView& v, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(v.norms, 0, sizeof(unsigned long long) * 2 * (size_t)v.nc, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev = trace_begin(s);
+    residual_partial<<<dim3((v.n_eq + 127) / 128, kResChunks), 128, 0, s>>>(v.M0, v.n_eq, v.np, v.nc, v.X, v.P);
+    residual_finish<<<256, 256, 0, s>>>(v.B, v.P, v.n_eq, v.np, v.nc, v.R, v.norms, v.norms + v.nc);
+    count_launch(2);
     trace_end(GBEM_KERNEL_RESIDUAL, ev, s, 8.0 * (double)v.n_eq * v.n_eq, 2.0 * (double)v.n_eq * v.n_eq * v.nc);
+    return cudaGetLastError();
+}
+
+size_t stack_partial_bytes(int np, int nc) { return sizeof(double) * (size_t)kResChunks * np * nc; }
+
+cudaError_t launch_stack_charges(const StackView& v, double eps0, cudaStream_t s)
+{
+    stack_charges<<<dim3(v.nc, v.nc), 256, 0, s>>>(v, v.X, eps0);
+    count_launch();
     return cudaGetLastError();
 }

@@ -289,27 +289,35 @@ cudaError_t launch_capacitance(const int32_t* cond, int n, int np, int n_cond, c
 // row_panel[r]; ucol / qcol: the column of the panel's unknown u / q (-1:
 // known); bcol: the right-hand side of a panel held at a conductor's
 // potential (-1: none); cidx: the conductor index of a conductor or
-// electrode panel (-1: none).  M: np x np column-major (the factor after
-// launch_stack_lu), M0: its copy before factoring, B: np x nc.
+// electrode panel (-1: none).  Matrices np x np column-major: M0 the
+// assembled system (FP64), factored in place as M (FP64 mode) or M32 (mixed
+// mode); B, X, R: np x nc FP64; W: np x nc in the factor's type.
 struct StackView {
-    int n = 0, n_eq = 0, np = 0, nc = 0, R = 0;
+    int n = 0, n_eq = 0, np = 0, nc = 0, R_layers = 0;
     const double *c = nullptr, *lo0 = nullptr, *hi0 = nullptr, *lo1 = nullptr, *hi1 = nullptr;
     const int8_t *axis = nullptr, *sign = nullptr;
     const int32_t *ra = nullptr, *ucol = nullptr, *qcol = nullptr, *bcol = nullptr, *cidx = nullptr;
     const int32_t *row_panel = nullptr, *reg_off = nullptr;
     const long long* tile_off = nullptr;
     const double* eps = nullptr;
-    double *M = nullptr, *M0 = nullptr, *B = nullptr, *C = nullptr;
-    int *ipiv = nullptr, *status = nullptr;
+    double *M0 = nullptr, *M = nullptr;
+    float* M32 = nullptr;
+    double *B = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *C = nullptr;
+    void* W = nullptr;
+    int *ipiv = nullptr, *perm = nullptr, *status = nullptr;
+    unsigned long long* norms = nullptr;
 };
 cudaError_t stack_gl_upload(cudaStream_t s);
-cudaError_t launch_stack_assemble(const StackView& v, long long tiles, cudaStream_t s);
-cudaError_t launch_stack_lu(const StackView& v, cudaStream_t s);
-// X (np x nc) := M^-1 B with the LU factor and its interchanges; perm: np
-// ints of work space; then C (nc x nc) from X.  norms: 2 nc words, zeroed.
-cudaError_t launch_stack_solve(const StackView& v, double* X, int* perm, unsigned long long* norms,
-                               double eps0, cudaStream_t s);
-// norms[m] = max_r |B - M0 X|[r, m] and norms[nc + m] = max_r |B[r, m]| (as
-// the bit patterns of non-negative doubles).
-cudaError_t launch_stack_residual(const StackView& v, const double* M0, const double* X,
-                                  unsigned long long* norms, cudaStream_t s);
+// M0 and B from the geometry (entries FP64, or FP32 far field in mixed
+// mode), then the copy to factor (M, or M32 in mixed mode).
+cudaError_t launch_stack_assemble(const StackView& v, long long tiles, bool mixed, cudaStream_t s);
+// LU with partial pivoting of M (M32), ipiv, and perm from ipiv.
+cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s);
+// One correction: W = (LU)^-1 P R in the factor's type, X += W.
+cudaError_t launch_stack_correct(const StackView& v, bool mixed, cudaStream_t s);
+// R = B - M0 X in FP64; norms[m] = max_r |R[r, m]|, norms[nc + m] = max_r
+// |B[r, m]| (bit patterns of non-negative doubles).
+cudaError_t launch_stack_residual(const StackView& v, cudaStream_t s);
+size_t stack_partial_bytes(int np, int nc);
+// C (nc x nc) from X.
+cudaError_t launch_stack_charges(const StackView& v, double eps0, cudaStream_t s);

@@ -22,16 +22,15 @@ struct gbem_stack_s {
     // device
     void* meta = nullptr;
     size_t meta_bytes = 0;
-    double* M = nullptr;
-    double* M0 = nullptr;
-    size_t mat_bytes = 0;
-    void* work = nullptr;           // B, X, C, ipiv, perm, status, norms
+    gbem_precision prec = GBEM_FP64;
+    void* M0 = nullptr;             // the assembled system (FP64)
+    void* Mf = nullptr;             // the copy factored in place (FP64, or FP32 in mixed mode)
+    size_t m0_bytes = 0, mf_bytes = 0;
+    void* work = nullptr;           // B, X, R, W, P, C, ipiv, perm, status, norms
     size_t work_bytes = 0;
     StackView v;
-    double* X = nullptr;
-    int* perm = nullptr;
-    unsigned long long* norms = nullptr;
     bool assembled = false, factored = false;
+    int iters = 0;                  // corrections of the last solve
     cudaStream_t last = nullptr;
 };
 
@@ -241,7 +240,7 @@ gbem_status stack_upload(gbem_stack_s* S)
     v.n_eq = S->n_eq;
     v.np = S->np;
     v.nc = S->nc;
-    v.R = S->R;
+    v.R_layers = S->R;
     const double* g = reinterpret_cast<const double*>(b + o_geo);
     v.c = g;
     v.lo0 = g + n;
@@ -262,38 +261,62 @@ gbem_status stack_upload(gbem_stack_s* S)
     return GBEM_OK;
 }
 
-// The matrices and the solve's buffers, at first use.
-gbem_status stack_alloc(gbem_stack_s* S, cudaStream_t s)
+void stack_free(gbem_stack_s* S, cudaStream_t s)
 {
-    if (S->M) return GBEM_OK;
+    gbem_ctx* ctx = S->ctx;
+    if (S->work) ctx_free(ctx, S->work, S->work_bytes, s);
+    if (S->Mf) ctx_free(ctx, S->Mf, S->mf_bytes, s);
+    if (S->M0) ctx_free(ctx, S->M0, S->m0_bytes, s);
+    S->work = S->Mf = S->M0 = nullptr;
+}
+
+// The matrices and the solve's buffers for precision `prec` (kept while the
+// precision stays the same).
+gbem_status stack_alloc(gbem_stack_s* S, gbem_precision prec, cudaStream_t s)
+{
+    if (S->M0 && S->prec == prec) return GBEM_OK;
+    if (S->M0) {
+        if (cudaStreamSynchronize(S->last) != cudaSuccess) return ctx_fail(S->ctx, GBEM_ERR_CUDA, "sync");
+        stack_free(S, S->last);
+    }
     gbem_ctx* ctx = S->ctx;
     const size_t np = S->np, nc = S->nc;
-    S->mat_bytes = sizeof(double) * np * np;
-    S->M = static_cast<double*>(ctx_alloc(ctx, S->mat_bytes, s));
-    if (!S->M) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix");
-    S->M0 = static_cast<double*>(ctx_alloc(ctx, S->mat_bytes, s));
-    if (!S->M0) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix copy");
+    const bool mixed = prec == GBEM_MIXED;
+    S->prec = prec;
+    S->m0_bytes = sizeof(double) * np * np;
+    S->mf_bytes = (mixed ? sizeof(float) : sizeof(double)) * np * np;
+    S->M0 = ctx_alloc(ctx, S->m0_bytes, s);
+    if (!S->M0) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix");
+    S->Mf = ctx_alloc(ctx, S->mf_bytes, s);
+    if (!S->Mf) return ctx_fail(ctx, GBEM_ERR_OOM, "stack matrix copy");
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off = align256(off + bytes);
         return o;
     };
-    const size_t o_B = take(8 * np * nc), o_X = take(8 * np * nc), o_C = take(8 * nc * nc);
+    const size_t vec = 8 * np * nc;
+    const size_t o_B = take(vec), o_X = take(vec), o_R = take(vec), o_W = take(vec);
+    const size_t o_P = take(stack_partial_bytes((int)np, (int)nc)), o_C = take(8 * nc * nc);
     const size_t o_piv = take(4 * np), o_perm = take(4 * np), o_st = take(4), o_nrm = take(16 * nc);
     S->work = ctx_alloc(ctx, off, s);
     if (!S->work) return ctx_fail(ctx, GBEM_ERR_OOM, "stack work space");
     S->work_bytes = off;
     unsigned char* b = static_cast<unsigned char*>(S->work);
-    S->v.M = S->M;
-    S->v.M0 = S->M0;
-    S->v.B = reinterpret_cast<double*>(b + o_B);
-    S->X = reinterpret_cast<double*>(b + o_X);
-    S->v.C = reinterpret_cast<double*>(b + o_C);
-    S->v.ipiv = reinterpret_cast<int*>(b + o_piv);
-    S->perm = reinterpret_cast<int*>(b + o_perm);
-    S->v.status = reinterpret_cast<int*>(b + o_st);
-    S->norms = reinterpret_cast<unsigned long long*>(b + o_nrm);
+    StackView& v = S->v;
+    v.M0 = static_cast<double*>(S->M0);
+    v.M = mixed ? nullptr : static_cast<double*>(S->Mf);
+    v.M32 = mixed ? static_cast<float*>(S->Mf) : nullptr;
+    v.B = reinterpret_cast<double*>(b + o_B);
+    v.X = reinterpret_cast<double*>(b + o_X);
+    v.R = reinterpret_cast<double*>(b + o_R);
+    v.W = b + o_W;
+    v.P = reinterpret_cast<double*>(b + o_P);
+    v.C = reinterpret_cast<double*>(b + o_C);
+    v.ipiv = reinterpret_cast<int*>(b + o_piv);
+    v.perm = reinterpret_cast<int*>(b + o_perm);
+    v.status = reinterpret_cast<int*>(b + o_st);
+    v.norms = reinterpret_cast<unsigned long long*>(b + o_nrm);
     return GBEM_OK;
 }
 
@@ -362,21 +385,21 @@ gbem_status gbem_stack_panels(const gbem_stack_t* S, int8_t* axis, double* geo, 
     return GBEM_OK;
 }
 
-gbem_status gbem_stack_assemble(gbem_stack_t* S, gbem_stream stream)
+gbem_status gbem_stack_assemble(gbem_stack_t* S, gbem_precision prec, gbem_stream stream)
 {
     if (!S) return GBEM_ERR_ARG;
     gbem_ctx* ctx = S->ctx;
     if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
+    if (prec != GBEM_FP64 && prec != GBEM_MIXED) return ctx_fail(ctx, GBEM_ERR_ARG, "bad precision");
     Dev g(ctx->device);
     TraceScope ts(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    gbem_status st = stack_alloc(S, s);
+    gbem_status st = stack_alloc(S, prec, s);
     if (st != GBEM_OK) return st;
     S->last = s;
     S->assembled = S->factored = false;
     if (!ok(ctx, stack_gl_upload(s), "quadrature nodes") ||
-        !ok(ctx, launch_stack_assemble(S->v, S->tile_off[S->R], s), "stack assembly") ||
-        !ok(ctx, cudaMemcpyAsync(S->M0, S->M, S->mat_bytes, cudaMemcpyDeviceToDevice, s), "matrix copy"))
+        !ok(ctx, launch_stack_assemble(S->v, S->tile_off[S->R], prec == GBEM_MIXED, s), "stack assembly"))
         return GBEM_ERR_CUDA;
     S->assembled = true;
     return GBEM_OK;
@@ -392,7 +415,7 @@ gbem_status gbem_stack_system(gbem_stack_t* S, double* M_host, double* B_host)
     const size_t n = S->n_eq, np = S->np;
     if (M_host) {
         std::vector<double> col(np * n);
-        if (!ok(ctx, cudaMemcpy(col.data(), S->M0, sizeof(double) * np * n, cudaMemcpyDeviceToHost), "download"))
+        if (!ok(ctx, cudaMemcpy(col.data(), S->v.M0, sizeof(double) * np * n, cudaMemcpyDeviceToHost), "download"))
             return GBEM_ERR_CUDA;
         for (size_t c = 0; c < n; ++c)
             for (size_t r = 0; r < n; ++r) M_host[r * n + c] = col[c * np + r];
@@ -413,7 +436,7 @@ gbem_status gbem_stack_capacitance(gbem_stack_t* S, gbem_stream stream, double* 
     gbem_ctx* ctx = S->ctx;
     if (ctx->device < 0) return ctx_fail(ctx, GBEM_ERR_NODEV, "context has no device");
     if (!S->assembled) {
-        gbem_status st = gbem_stack_assemble(S, stream);
+        gbem_status st = gbem_stack_assemble(S, GBEM_FP64, stream);
         if (st != GBEM_OK) return st;
     }
     Dev g(ctx->device);
@@ -428,36 +451,60 @@ gbem_status gbem_stack_capacitance(gbem_stack_t* S, gbem_stream stream, double* 
         cudaEventDestroy(ev);
         S->last = s;
     }
+    const bool mixed = S->prec == GBEM_MIXED;
+    StackView& v = S->v;
+    const size_t np = S->np, nc = S->nc;
     if (!S->factored) {
-        if (!ok(ctx, cudaMemsetAsync(S->v.status, 0, sizeof(int), s), "memset") ||
-            !ok(ctx, launch_stack_lu(S->v, s), "LU"))
+        if (!ok(ctx, cudaMemsetAsync(v.status, 0, sizeof(int), s), "memset") ||
+            !ok(ctx, launch_stack_lu(v, mixed, s), "LU"))
             return GBEM_ERR_CUDA;
         S->factored = true;
     }
-    const double eps0 = 8.8541878128e-12;
-    if (!ok(ctx, launch_stack_solve(S->v, S->X, S->perm, S->norms, eps0, s), "solve") ||
-        !ok(ctx, launch_stack_residual(S->v, S->M0, S->X, S->norms, s), "residual"))
+    // X = 0, R = B; corrections X += (LU)^-1 P R, R = B - M0 X until the
+    // residual meets the tolerance (one correction in FP64 mode, normally)
+    const double tol = ctx->tune.ir_tol > 0.0 ? ctx->tune.ir_tol : 1e-11;
+    const int max_iter = ctx->tune.ir_max_iter > 0 ? ctx->tune.ir_max_iter : 10;
+    if (!ok(ctx, cudaMemsetAsync(v.X, 0, sizeof(double) * np * nc, s), "memset") ||
+        !ok(ctx, cudaMemcpyAsync(v.R, v.B, sizeof(double) * np * nc, cudaMemcpyDeviceToDevice, s), "copy"))
         return GBEM_ERR_CUDA;
-    const size_t nc = S->nc;
     std::vector<unsigned long long> nrm(2 * nc);
+    double worst = 0.0;
     int status = 0;
-    if (!ok(ctx, cudaMemcpyAsync(C_host, S->v.C, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
-        !ok(ctx, cudaMemcpyAsync(nrm.data(), S->norms, 16 * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
-        !ok(ctx, cudaMemcpyAsync(&status, S->v.status, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h") ||
+    S->iters = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        if (!ok(ctx, launch_stack_correct(v, mixed, s), "solve") || !ok(ctx, launch_stack_residual(v, s), "residual") ||
+            !ok(ctx, cudaMemcpyAsync(nrm.data(), v.norms, 16 * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
+            !ok(ctx, cudaMemcpyAsync(&status, v.status, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h") ||
+            !ok(ctx, cudaStreamSynchronize(s), "sync"))
+            return GBEM_ERR_CUDA;
+        S->iters = it + 1;
+        if (status != 0) {
+            S->factored = false;
+            return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "LU met a zero pivot: the stack's system is singular");
+        }
+        worst = 0.0;
+        for (size_t m = 0; m < nc; ++m) {
+            double r, b;
+            std::memcpy(&r, &nrm[m], 8);
+            std::memcpy(&b, &nrm[nc + m], 8);
+            worst = std::max(worst, b > 0.0 ? r / b : r);
+        }
+        if (!(worst > tol)) break;
+    }
+    const double eps0 = 8.8541878128e-12;
+    if (!ok(ctx, launch_stack_charges(v, eps0, s), "charges") ||
+        !ok(ctx, cudaMemcpyAsync(C_host, v.C, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, s), "d2h") ||
         !ok(ctx, cudaStreamSynchronize(s), "sync"))
         return GBEM_ERR_CUDA;
-    if (status != 0) {
-        S->factored = false;
-        return ctx_fail(ctx, GBEM_ERR_NOT_SPD, "LU met a zero pivot: the stack's system is singular");
-    }
-    double worst = 0.0;
-    for (size_t m = 0; m < nc; ++m) {
-        double r, b;
-        std::memcpy(&r, &nrm[m], 8);
-        std::memcpy(&b, &nrm[nc + m], 8);
-        worst = std::max(worst, b > 0.0 ? r / b : r);
-    }
     if (resid) *resid = worst;
+    if (!(worst <= tol)) return ctx_fail(ctx, GBEM_ERR_NOCONV, "refinement missed its tolerance");
+    return GBEM_OK;
+}
+
+gbem_status gbem_stack_iterations(const gbem_stack_t* S, int* iters)
+{
+    if (!S || !iters) return GBEM_ERR_ARG;
+    *iters = S->iters;
     return GBEM_OK;
 }
 
@@ -465,12 +512,10 @@ void gbem_stack_destroy(gbem_stack_t* S)
 {
     if (!S) return;
     gbem_ctx* ctx = S->ctx;
-    if (ctx->device >= 0 && (S->meta || S->M || S->work)) {
+    if (ctx->device >= 0 && (S->meta || S->M0 || S->work)) {
         Dev g(ctx->device);
         cudaStreamSynchronize(S->last);
-        if (S->work) ctx_free(ctx, S->work, S->work_bytes, S->last);
-        if (S->M0) ctx_free(ctx, S->M0, S->mat_bytes, S->last);
-        if (S->M) ctx_free(ctx, S->M, S->mat_bytes, S->last);
+        stack_free(S, S->last);
         if (S->meta) ctx_free(ctx, S->meta, S->meta_bytes, nullptr);
     }
     delete S;

@@ -103,7 +103,8 @@ _SIGS = {
     "gbem_stack_mesh": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "gbem_stack_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "gbem_stack_panels": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gbem_stack_assemble": (ctypes.c_int, [_P, _P]),
+    "gbem_stack_assemble": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "gbem_stack_iterations": (ctypes.c_int, [_P, _P]),
     "gbem_stack_system": (ctypes.c_int, [_P, _P, _P]),
     "gbem_stack_capacitance": (ctypes.c_int, [_P, _P, _P, _P]),
     "gbem_stack_destroy": (None, [_P]),
@@ -529,8 +530,13 @@ class Stack:
         d["cond_ids"] = ids
         return d
 
-    def assemble(self, stream=None):
-        self.ctx.check(self.ctx.lib.gbem_stack_assemble(self.h, _stream_handle(stream)))
+    def assemble(self, precision=GBEM_FP64, stream=None):
+        self.ctx.check(self.ctx.lib.gbem_stack_assemble(self.h, int(precision), _stream_handle(stream)))
+
+    def iterations(self) -> int:
+        it = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.gbem_stack_iterations(self.h, ctypes.byref(it)))
+        return it.value
 
     def system(self):
         """(M float64[n_eq, n_eq], B float64[n_eq, n_cond]) as assembled."""

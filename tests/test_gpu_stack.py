@@ -1,4 +1,5 @@
-"""Parity of the multi-dielectric path (Sec. 4) on the GPU with the oracle:
+"""Parity of the multi-dielectric path (Sec. 4) on the GPU with the oracle, in
+FP64 and in mixed mode:
 the assembled system entry by entry and the capacitance matrix after the LU
 solve, on stacks of 184, 512 and 592 equations (ragged and whole 64-blocks);
 at 5520 equations, sampled entries against the oracle's integrals and the
@@ -38,7 +39,7 @@ def test_system_and_capacitance_match_oracle(ctx, case):
     S, ref = _stack(ctx, CASES[case])
     eps = CASES[case][3]
     stream = torch.cuda.Stream()
-    S.assemble(stream)
+    S.assemble(gbem.GBEM_FP64, stream)
     M, Bg = S.system()
     M_ref, B_ref, ids = D.system(ref, eps)
     # every entry within 1e-10 of its row's largest entry
@@ -67,7 +68,7 @@ def test_full_size_sampled_entries(ctx):
     entries of every kind against the oracle's integrals."""
     S, ref = _stack(ctx, BENCH_STACK)
     assert S.n_eq == 5520
-    S.assemble(torch.cuda.Stream())
+    S.assemble(gbem.GBEM_FP64, torch.cuda.Stream())
     M, Bg = S.system()
     rows, ucol, qcol, ids = D.layout(ref)
     eps = BENCH_STACK[3]
@@ -128,4 +129,39 @@ def test_single_dielectric_equals_single_layer_path(ctx):
     assert np.abs(C - C1[:3, :3]).max() <= 1e-9 * np.abs(C1).max()
     mat.close()
     mesh.close()
+    S.close()
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mixed_matches_oracle(ctx, case):
+    """Mixed mode: FP32 far field and FP32 LU, refined against the FP64-stored
+    system: entries within 2e-6 of their row's scale, C within 1e-6."""
+    S, ref = _stack(ctx, CASES[case])
+    eps = CASES[case][3]
+    stream = torch.cuda.Stream()
+    S.assemble(gbem.GBEM_MIXED, stream)
+    M, Bg = S.system()
+    M_ref, B_ref, ids = D.system(ref, eps)
+    scale = np.abs(M_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(M - M_ref) <= 2e-6 * scale)
+    assert np.abs(Bg - B_ref).max() <= 2e-6 * np.abs(B_ref).max()
+    C, resid = S.capacitance(stream)
+    import scipy.linalg as sla
+    C_ref = D.charges(ref, eps, sla.lu_solve(sla.lu_factor(M_ref), B_ref), ids)
+    assert resid <= 1e-11 and S.iterations() <= 6
+    assert np.abs(C - C_ref).max() <= 1e-6 * np.abs(C_ref).max()
+    S.close()
+
+
+def test_mixed_full_size_against_fp64(ctx):
+    """5520 equations: the mixed extraction against the FP64 one."""
+    S, _ = _stack(ctx, BENCH_STACK)
+    stream = torch.cuda.Stream()
+    S.assemble(gbem.GBEM_FP64, stream)
+    C64, r64 = S.capacitance(stream)
+    assert S.iterations() == 1 and r64 <= 1e-12
+    S.assemble(gbem.GBEM_MIXED, stream)
+    C32, r32 = S.capacitance(stream)
+    assert r32 <= 1e-11 and S.iterations() <= 6
+    assert np.abs(C32 - C64).max() <= 1e-6 * np.abs(C64).max()
     S.close()

@@ -70,7 +70,7 @@ def test_stack_guards(lib):
     assert e.value.status == -1
     S = gbem.Stack(ctx, lo, hi, z, eps, bc, [([1, 1, 0.5], [2, 3, 1], 0)], 0.5)
     with pytest.raises(gbem.GbemError) as e:   # a host context cannot assemble
-        S.assemble(stream=0)
+        S.assemble(gbem.GBEM_FP64, stream=0)
     assert e.value.status == -9
     S.close()
     ctx.close()
