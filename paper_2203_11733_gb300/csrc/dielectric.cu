@@ -50,16 +50,12 @@ __device__ __forceinline__ float mufu_rsqrt(float x)
     return y;
 }
 
-// U and D (D: the double layer for the normal +e_k of panel k) of one pair.
-// FP64 mode: closed forms while their cancellation allows (below), FP64
-// Gauss-Legendre for the rest, about 1e-11 relative.  Mixed mode: closed
-// forms below q = 1.5, FP32 Gauss-Legendre (FP64 node offsets, FP32 inner
-// sums, FP64 outer sums) for the rest, about 1e-7 relative.
-template <bool MIXED>
-__device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double& D)
+// Box extents per global axis of a panel, its gap ratio q = gap / largest
+// edge of the pair, and the squared bounding diagonal of the pair.
+__device__ __forceinline__ void pair_geometry(const PanelGeo& I, const PanelGeo& K, double* lo_i, double* hi_i,
+                                              double* lo_k, double* hi_k, double& q, double& R2)
 {
     const int ki = I.axis, kk = K.axis;
-    double lo_i[3], hi_i[3], lo_k[3], hi_k[3];
     lo_i[ki] = hi_i[ki] = I.c;
     lo_i[axp(ki)] = I.lo0;
     hi_i[axp(ki)] = I.hi0;
@@ -70,7 +66,8 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
     hi_k[axp(kk)] = K.hi0;
     lo_k[axq(kk)] = K.lo1;
     hi_k[axq(kk)] = K.hi1;
-    double g2 = 0.0, R2 = 0.0;
+    double g2 = 0.0;
+    R2 = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double g = fmax(0.0, fmax(lo_k[d] - hi_i[d], lo_i[d] - hi_k[d]));
@@ -78,14 +75,41 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
         const double e = fmax(hi_i[d], hi_k[d]) - fmin(lo_i[d], lo_k[d]);
         R2 += e * e;
     }
-    const double ai = (I.hi0 - I.lo0) * (I.hi1 - I.lo1), ak = (K.hi0 - K.lo0) * (K.hi1 - K.lo1);
     const double lmax = fmax(fmax(I.hi0 - I.lo0, I.hi1 - I.lo1), fmax(K.hi0 - K.lo0, K.hi1 - K.lo1));
-    const double q = sqrt(g2) / lmax;
-    // closed forms while their corner sums lose at most about 2e-12
-    // (eps R^4 / (|I_i| |I_k|), R the pair's bounding diagonal), and always
-    // below q = 3, where the quadrature would need more than 6 points
-    const bool closed = MIXED ? q < 1.5 : (q < 3.0 || (q < 12.0 && R2 * R2 <= 9000.0 * ai * ak));
-    if (closed) {
+    q = sqrt(g2) / lmax;
+}
+
+// How a pair is evaluated: 0 closed forms, else the Gauss-Legendre order.
+// FP64 mode: closed forms while their corner sums lose at most about 2e-12
+// (eps R^4 / (|I_i| |I_k|), R the pair's bounding diagonal), always below
+// q = 3; FP64 Gauss-Legendre for the rest, about 1e-11 relative.  Mixed
+// mode: closed forms below q = 1.5, FP32 Gauss-Legendre for the rest, about
+// 1e-7 relative.
+template <bool MIXED>
+__device__ int pair_class(const PanelGeo& I, const PanelGeo& K)
+{
+    double lo_i[3], hi_i[3], lo_k[3], hi_k[3], q, R2;
+    pair_geometry(I, K, lo_i, hi_i, lo_k, hi_k, q, R2);
+    if (MIXED) {
+        if (q < 1.5) return 0;
+        return q >= 40.0 ? 2 : q >= 6.0 ? 3 : q >= 3.0 ? 4 : q >= 2.0 ? 5 : 6;
+    }
+    const double ai = (I.hi0 - I.lo0) * (I.hi1 - I.lo1), ak = (K.hi0 - K.lo0) * (K.hi1 - K.lo1);
+    if (q < 3.0 || (q < 12.0 && R2 * R2 <= 9000.0 * ai * ak)) return 0;
+    return q >= 320.0 ? 2 : q >= 40.0 ? 3 : q >= 10.0 ? 4 : q >= 5.0 ? 5 : 6;
+}
+
+// U and D (D: the double layer for the normal +e_k of panel k) of one pair
+// of class cls (pair_class): FP64 closed forms, FP64 Gauss-Legendre, or in
+// mixed mode FP32 Gauss-Legendre (FP64 node offsets, FP32 inner sums, FP64
+// outer sums).
+template <bool MIXED>
+__device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, int cls, double& U, double& D)
+{
+    const int ki = I.axis, kk = K.axis;
+    double lo_i[3], hi_i[3], lo_k[3], hi_k[3], q, R2;
+    pair_geometry(I, K, lo_i, hi_i, lo_k, hi_k, q, R2);
+    if (cls == 0) {
         double su = 0.0, sd = 0.0;
         if (ki == kk) {
             const double w = I.c - K.c;
@@ -94,8 +118,9 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
                 const int al = c & 1, be = (c >> 1) & 1, ga = (c >> 2) & 1, de = (c >> 3) & 1;
                 const double u = (al ? I.hi0 : I.lo0) - (be ? K.hi0 : K.lo0);
                 const double v = (ga ? I.hi1 : I.lo1) - (de ? K.hi1 : K.lo1);
-                const double f = F_par(u, v, w);
-                const double p = w != 0.0 ? Phi_par(u, v, w) : 0.0;
+                double f, p = 0.0;
+                if (w != 0.0) FPhi_par(u, v, w, f, p);
+                else f = F_par(u, v, w);
                 const bool neg = (al + be + ga + de) & 1;
                 su += neg ? -f : f;
                 sd += neg ? -p : p;
@@ -115,8 +140,8 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
                 const double u = (al ? p1 : p0) - (be ? r1 : r0);
                 const double v = (ga ? q1 : q0) - K.c;
                 const double w = I.c - (de ? t1 : t0);
-                const double h = H_orth(u, v, w);
-                const double t = Theta_orth(u, v, w);
+                double h, t;
+                HTheta_orth(u, v, w, h, t);
                 const bool neg = (al + be + ga + de) & 1;
                 su += neg ? -h : h;
                 sd += neg ? -t : t;
@@ -136,8 +161,8 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
     const double hk_p = 0.5 * (K.hi0 - K.lo0), hk_q = 0.5 * (K.hi1 - K.lo1);
     const int ip = axp(ki), iq = axq(ki), kp = axp(kk), kq = axq(kk);
     double su = 0.0, sd = 0.0;
+    const int n = cls;
     if (MIXED) {
-        const int n = q >= 40.0 ? 2 : q >= 6.0 ? 3 : q >= 3.0 ? 4 : q >= 2.0 ? 5 : 6;
         const float fp = (float)hi_p, fq = (float)hi_q, gp = (float)hk_p, gq = (float)hk_q;
 #pragma unroll 1
         for (int a = 0; a < n; ++a)
@@ -168,7 +193,6 @@ __device__ void pair_UD(const PanelGeo& I, const PanelGeo& K, double& U, double&
         D = sd * f;
         return;
     }
-    const int n = q >= 320.0 ? 2 : q >= 40.0 ? 3 : q >= 10.0 ? 4 : q >= 5.0 ? 5 : 6;
 #pragma unroll 1
     for (int a = 0; a < n; ++a)
 #pragma unroll 1
@@ -224,14 +248,40 @@ __global__ void __launch_bounds__(256) stack_assemble(StackView v)
         sp[tid] = p;
     }
     __syncthreads();
-    const double ea = v.eps[a];
+    // classify the tile's pairs, then evaluate them class by class (closed
+    // forms first), so that warps run one kind of evaluation: an FP64 closed
+    // form with most lanes of a warp idle would stall the scarce FP64 pipe
+    __shared__ unsigned char cls_s[1024];
+    __shared__ unsigned short order[1024];
+    __shared__ int cnt[8], pos[8];
+    if (tid < 8) cnt[tid] = 0;
+    __syncthreads();
     for (int e = tid; e < 1024; e += blockDim.x) {
         const int li = e & 31, lk = e >> 5;
+        const int c = (sp[li] < 0 || sp[32 + lk] < 0) ? 7 : pair_class<MIXED>(sg[li], sg[32 + lk]);
+        cls_s[e] = (unsigned char)c;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < 8; ++c) {
+            pos[c] = acc;
+            acc += cnt[c];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 1024; e += blockDim.x) order[atomicAdd(&pos[cls_s[e]], 1)] = (unsigned short)e;
+    __syncthreads();
+    const int total = 1024 - cnt[7];
+    const double ea = v.eps[a];
+    for (int t = tid; t < total; t += blockDim.x) {
+        const int e = order[t];
+        const int li = e & 31, lk = e >> 5;
         const int i = sp[li], k = sp[32 + lk];
-        if (i < 0 || k < 0) continue;
         const long long row = r0 + ti * 32 + li;
         double U, D;
-        pair_UD<MIXED>(sg[li], sg[32 + lk], U, D);
+        pair_UD<MIXED>(sg[li], sg[32 + lk], cls_s[e], U, D);
         const bool own = v.ra[k] == a;
         const double s = own ? (double)v.sign[k] : -(double)v.sign[k];
         double cu = s * D;
@@ -484,27 +534,38 @@ __global__ void __launch_bounds__(256) lu_panel_cluster(float* __restrict__ M, i
             if (g >= base && g < base + mine) diag[buf].vals[tid] = A[(size_t)(g - base) * LDA + tid];
         }
         cluster.sync();
-        // the winner over the cluster, and the two rows it exchanges
-        if (tid == 0) {
+        // the winner over the cluster (warp 0, one slot a lane), and the two
+        // rows it exchanges
+        if (tid < 32) {
             float bv = -1.0f;
-            int br = np, bk = 0;
-            for (int k = 0; k < csize; ++k) {
-                const PivotSlot* o = cluster.map_shared_rank(cand + buf, k);
-                if (o->val > bv || (o->val == bv && o->row < br)) {
-                    bv = o->val;
-                    br = o->row;
-                    bk = k;
+            int br = np, bk = tid;
+            if (tid < csize) {
+                const PivotSlot* o = cluster.map_shared_rank(cand + buf, tid);
+                bv = o->val;
+                br = o->row;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int orow = __shfl_down_sync(0xffffffffu, br, o);
+                const int ok = __shfl_down_sync(0xffffffffu, bk, o);
+                if (ov > bv || (ov == bv && orow < br)) {
+                    bv = ov;
+                    br = orow;
+                    bk = ok;
                 }
             }
-            if (br >= np) {   // no comparable value: keep the diagonal row
-                br = g;
-                bk = (g - j0) / rows;
-                if (rank == 0) atomicExch(status, (int)GBEM_ERR_NOT_SPD);
+            if (tid == 0) {
+                if (br >= np) {   // no comparable value: keep the diagonal row
+                    br = g;
+                    bk = (g - j0) / rows;
+                    if (rank == 0) atomicExch(status, (int)GBEM_ERR_NOT_SPD);
+                }
+                win_rank = bk;
+                win_row = br;
+                diag_rank = (g - j0) / rows;
+                if (rank == 0) ipiv[g] = br;
             }
-            win_rank = bk;
-            win_row = br;
-            diag_rank = (g - j0) / rows;
-            if (rank == 0) ipiv[g] = br;
         }
         __syncthreads();
         const int w = win_row;
@@ -543,25 +604,89 @@ __global__ void __launch_bounds__(256) lu_panel_cluster(float* __restrict__ M, i
     }
 }
 
-// The panel's interchanges applied, in order, to every column outside it.
-template <typename T>
-__global__ void lu_swap(T* __restrict__ M, int np, int j0, const int* __restrict__ ipiv)
+// The panel's 64 interchanges composed into one permutation of the rows they
+// touch (at most 128): plan[0] = count, then (destination, source) pairs with
+// destination != source.  One warp: rows j0..j0+63 take slots 0..63, every
+// other row the slot 64 + (its rank among the other rows by first
+// appearance); lane 0 then replays the 64 exchanges on the slots.
+__global__ void __launch_bounds__(32) lu_swap_plan(const int* __restrict__ ipiv, int j0, int* __restrict__ plan)
 {
-    __shared__ int piv[NB];
-    if (threadIdx.x < NB) piv[threadIdx.x] = ipiv[j0 + threadIdx.x];
+    __shared__ int piv[NB], slot[NB], first[NB];
+    __shared__ int row[2 * NB], content[2 * NB];
+    const int lane = threadIdx.x;
+    for (int k = lane; k < NB; k += 32) piv[k] = ipiv[j0 + k];
+    __syncwarp();
+    // first appearance of each outside row
+    for (int k = lane; k < NB; k += 32) {
+        int f = k;
+        if (piv[k] >= j0 + NB)
+            for (int t = 0; t < k; ++t)
+                if (piv[t] == piv[k]) {
+                    f = t;
+                    break;
+                }
+        first[k] = f;
+    }
+    __syncwarp();
+    for (int k = lane; k < NB; k += 32) {
+        const int p = piv[k];
+        if (p < j0 + NB) {
+            slot[k] = p - j0;
+        } else {
+            int rnk = 0;   // outside rows first seen before first[k]
+            for (int t = 0; t < first[k]; ++t) rnk += (piv[t] >= j0 + NB && first[t] == t) ? 1 : 0;
+            slot[k] = NB + rnk;
+            if (first[k] == k) {
+                row[NB + rnk] = p;
+                content[NB + rnk] = p;
+            }
+        }
+    }
+    for (int k = lane; k < NB; k += 32) {
+        row[k] = j0 + k;
+        content[k] = j0 + k;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int n = NB;
+        for (int k = 0; k < NB; ++k) {
+            const int sp = slot[k];
+            n = max(n, sp + 1);
+            const int t = content[k];
+            content[k] = content[sp];
+            content[sp] = t;
+        }
+        int m = 0;
+        for (int t = 0; t < n; ++t)
+            if (content[t] != row[t]) {
+                plan[1 + 2 * m] = row[t];
+                plan[2 + 2 * m] = content[t];
+                ++m;
+            }
+        plan[0] = m;
+    }
+}
+
+// The panel's interchanges applied to every column outside it: each thread
+// gathers the moved rows of its column at once, then writes them.
+template <typename T>
+__global__ void __launch_bounds__(128) lu_swap(T* __restrict__ M, int np, int j0, const int* __restrict__ plan)
+{
+    __shared__ int pl[1 + 4 * NB];
+    for (int e = threadIdx.x; e < 1 + 4 * NB; e += blockDim.x) pl[e] = plan[e];
     __syncthreads();
+    const int m = pl[0];
     const int ncols = np - NB;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncols; t += gridDim.x * blockDim.x) {
         const int c = t < j0 ? t : t + NB;
         T* e = M + (size_t)c * np;
-        for (int k = 0; k < NB; ++k) {
-            const int p = piv[k], r = j0 + k;
-            if (p != r) {
-                const T x = e[r];
-                e[r] = e[p];
-                e[p] = x;
-            }
-        }
+        T v[2 * NB];
+#pragma unroll 16
+        for (int i = 0; i < 2 * NB; ++i)
+            if (i < m) v[i] = e[pl[2 + 2 * i]];
+#pragma unroll 16
+        for (int i = 0; i < 2 * NB; ++i)
+            if (i < m) e[pl[1 + 2 * i]] = v[i];
     }
 }
 
@@ -633,20 +758,21 @@ __global__ void __launch_bounds__(256) lu_gemm_f64(double* __restrict__ M, int n
         }
 }
 
-// A22 -= L21 U12 in FP32: one 128 x 128 tile per CTA, 8 x 8 outputs per
-// thread (rows tx + 16 i, columns ty + 16 j), K = 64; the trailing order is a
-// multiple of 64, so edge tiles skip their missing half.
+// A22 -= L21 U12 in FP32 for the columns c_lo .. c_hi-1: one 128 x 128 tile
+// per CTA, 8 x 8 outputs per thread (rows tx + 16 i, columns ty + 16 j),
+// K = 64; the orders are multiples of 64, so edge tiles skip their missing
+// half.
 constexpr int GT = 128;
 constexpr size_t kGemmSmem32 = 2 * sizeof(float) * NB * (GT + 4);
-__global__ void __launch_bounds__(256) lu_gemm_f32(float* __restrict__ M, int np, int j0)
+__global__ void __launch_bounds__(256) lu_gemm_f32(float* __restrict__ M, int np, int j0, int c_lo, int c_hi)
 {
     extern __shared__ float fsm[];
     float(*Ls)[GT + 4] = reinterpret_cast<float(*)[GT + 4]>(fsm);                   // Ls[k][r]
     float(*Us)[GT + 4] = reinterpret_cast<float(*)[GT + 4]>(fsm + NB * (GT + 4));  // Us[k][c]
     const size_t ld = (size_t)np;
     const int base = j0 + NB;
-    const int i0 = base + blockIdx.x * GT, c0 = base + blockIdx.y * GT;
-    const int rows = min(GT, np - i0), cols = min(GT, np - c0);
+    const int i0 = base + blockIdx.x * GT, c0 = c_lo + blockIdx.y * GT;
+    const int rows = min(GT, np - i0), cols = min(GT, c_hi - c0);
     const int tid = threadIdx.x;
     for (int e = tid; e < NB * GT; e += 256) {
         const int r = e % GT, k = e / GT;
@@ -716,60 +842,77 @@ __global__ void permute_rhs(const double* __restrict__ R, const int* __restrict_
     }
 }
 
-// Diagonal block b of the forward (unit lower) or backward (upper) sweep:
-// X_b := T_bb^-1 X_b; thread r owns row r of the block, 16 right-hand sides
-// at a time, one barrier per eliminated row.
-template <typename T, bool LOWER>
-__global__ void __launch_bounds__(NB) tri_block(const T* __restrict__ M, int np, int b, int nc, T* __restrict__ X)
+// Inverses of the diagonal blocks of the factor, for the sweeps: Inv[2 b]
+// = L_bb^-1 (unit lower), Inv[2 b + 1] = U_bb^-1, each 64 x 64 column-major.
+// Thread c forms column c of both by substitution.
+template <typename T>
+__global__ void __launch_bounds__(NB) tri_inverse(const T* __restrict__ M, int np, T* __restrict__ Inv)
 {
     __shared__ T Tb[NB][NB + 1];
-    __shared__ T xs[NB][17];
     const size_t ld = (size_t)np;
-    const int j0 = b * NB, r = threadIdx.x;
+    const int j0 = blockIdx.x * NB, c = threadIdx.x;
     for (int e = threadIdx.x; e < NB * NB; e += NB) {
-        const int i = e % NB, c = e / NB;
-        Tb[i][c] = M[(size_t)(j0 + i) + (size_t)(j0 + c) * ld];
+        const int i = e % NB, k = e / NB;
+        Tb[i][k] = M[(size_t)(j0 + i) + (size_t)(j0 + k) * ld];
     }
-    for (int m0 = 0; m0 < nc; m0 += 16) {
-        const int mn = min(16, nc - m0);
-        __syncthreads();
-        for (int m = 0; m < mn; ++m) xs[r][m] = X[(size_t)(m0 + m) * np + j0 + r];
-        __syncthreads();
-        if (LOWER) {
-            for (int k = 0; k < NB - 1; ++k) {
-                if (r > k)
-                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-Tb[r][k], xs[k][m], xs[r][m]);
-                __syncthreads();
-            }
-        } else {
-            for (int k = NB - 1; k >= 0; --k) {
-                if (r == k)
-                    for (int m = 0; m < mn; ++m) xs[k][m] = xs[k][m] / Tb[k][k];
-                __syncthreads();
-                if (r < k)
-                    for (int m = 0; m < mn; ++m) xs[r][m] = fma(-Tb[r][k], xs[k][m], xs[r][m]);
-                __syncthreads();
-            }
-        }
-        for (int m = 0; m < mn; ++m) X[(size_t)(m0 + m) * np + j0 + r] = xs[r][m];
+    __syncthreads();
+    T* Li = Inv + (size_t)(2 * blockIdx.x) * NB * NB;
+    T* Ui = Li + NB * NB;
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        T t = r == c ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k < r; ++k) t = fma(-Tb[r][k], x[k], t);
+        x[r] = t;
     }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) Li[(size_t)c * NB + r] = x[r];
+#pragma unroll
+    for (int r = NB - 1; r >= 0; --r) {
+        T t = r == c ? T(1) : T(0);
+#pragma unroll
+        for (int k = r + 1; k < NB; ++k) t = fma(-Tb[r][k], x[k], t);
+        x[r] = t / Tb[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) Ui[(size_t)c * NB + r] = x[r];
 }
 
-// X[r] -= M[r, block b] X_b for the rows below block b (LOWER) or above it;
-// NR right-hand sides per pass, the block row's 64 entries loaded 16 at a time.
+// One step of the forward (LOWER: In = W, Out = Y) or backward sweep (In = Y,
+// Out = W) for block b: every CTA forms x_b = T_bb^-1 In_b from the stored
+// inverse; CTA 0 writes it to Out_b; every CTA subtracts M[r, block b] x_b
+// from the rows of In below (LOWER) or above block b.  In_b is not written
+// in this launch, so the CTAs agree on x_b.
 template <typename T, bool LOWER, int NR>
-__global__ void __launch_bounds__(256) tri_update(const T* __restrict__ M, int np, int b, int nc, T* __restrict__ X)
+__global__ void __launch_bounds__(256) sweep_step(const T* __restrict__ M, const T* __restrict__ Inv, int np, int b,
+                                                  int nc, T* __restrict__ In, T* __restrict__ Out)
 {
+    __shared__ T inv[NB][NB + 1];
+    __shared__ T xin[NR][NB];
     __shared__ T xb[NR][NB];
     const size_t ld = (size_t)np;
     const int j0 = b * NB;
+    const T* src = Inv + (size_t)(2 * b + (LOWER ? 0 : 1)) * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) inv[e % NB][e / NB] = src[e];
     const int rlo = LOWER ? j0 + NB : 0, rhi = LOWER ? np : j0;
     for (int m0 = 0; m0 < nc; m0 += NR) {
         const int mn = min(NR, nc - m0);
         __syncthreads();
         for (int e = threadIdx.x; e < NR * NB; e += blockDim.x)
-            xb[e / NB][e % NB] = e / NB < mn ? X[(size_t)(m0 + e / NB) * np + j0 + e % NB] : T(0);
+            xin[e / NB][e % NB] = e / NB < mn ? In[(size_t)(m0 + e / NB) * np + j0 + e % NB] : T(0);
         __syncthreads();
+        for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+            const int m = e / NB, r = e % NB;
+            T t = T(0);
+#pragma unroll 16
+            for (int k = 0; k < NB; ++k) t = fma(inv[r][k], xin[m][k], t);
+            xb[m][r] = t;
+        }
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (int e = threadIdx.x; e < mn * NB; e += blockDim.x)
+                Out[(size_t)(m0 + e / NB) * np + j0 + e % NB] = xb[e / NB][e % NB];
         for (int r = rlo + blockIdx.x * blockDim.x + threadIdx.x; r < rhi; r += gridDim.x * blockDim.x) {
             T acc[NR] = {};
             const T* row = M + (size_t)r + (size_t)j0 * ld;
@@ -783,20 +926,27 @@ __global__ void __launch_bounds__(256) tri_update(const T* __restrict__ M, int n
 #pragma unroll
                     for (int m = 0; m < NR; ++m) acc[m] = fma(l[k], xb[m][k0 + k], acc[m]);
             }
-            for (int m = 0; m < mn; ++m) X[(size_t)(m0 + m) * np + r] -= acc[m];
+            for (int m = 0; m < mn; ++m) In[(size_t)(m0 + m) * np + r] -= acc[m];
         }
     }
 }
 
 template <typename T, bool LOWER>
-void launch_tri_update(const T* M, int np, int b, int nc, T* X, cudaStream_t s)
+void launch_sweep_step(const T* M, const T* Inv, int np, int b, int nc, T* In, T* Out, cudaStream_t s)
 {
     const int j0 = b * NB;
     const int rows = LOWER ? np - j0 - NB : j0;
     const int grid = max(1, min(2 * 152, (rows + 255) / 256));
-    if (nc <= 4) tri_update<T, LOWER, 4><<<grid, 256, 0, s>>>(M, np, b, nc, X);
-    else if (nc <= 8) tri_update<T, LOWER, 8><<<grid, 256, 0, s>>>(M, np, b, nc, X);
-    else tri_update<T, LOWER, 16><<<grid, 256, 0, s>>>(M, np, b, nc, X);
+    // at most 16 right-hand sides per pass in FP32, 8 in FP64 (48 KB of
+    // static shared memory)
+    if (nc <= 4) {
+        sweep_step<T, LOWER, 4><<<grid, 256, 0, s>>>(M, Inv, np, b, nc, In, Out);
+    } else if constexpr (sizeof(T) == 8) {
+        sweep_step<T, LOWER, 8><<<grid, 256, 0, s>>>(M, Inv, np, b, nc, In, Out);
+    } else {
+        if (nc <= 8) sweep_step<T, LOWER, 8><<<grid, 256, 0, s>>>(M, Inv, np, b, nc, In, Out);
+        else sweep_step<T, LOWER, 16><<<grid, 256, 0, s>>>(M, Inv, np, b, nc, In, Out);
+    }
     count_launch();
 }
 
@@ -951,18 +1101,11 @@ template <typename T>
 cudaError_t lu_run(T* M, const StackView& v, cudaStream_t s)
 {
     const int np = v.np;
-    const int csize = sizeof(T) == 4 ? panel_cluster_size() : 0;
     for (int j0 = 0; j0 < np; j0 += NB) {
-        cudaError_t e = cudaSuccess;
-        bool done = false;
-        if constexpr (sizeof(T) == 4) done = panel_f32_cluster(M, np, j0, v, csize, s, e);
-        if (e != cudaSuccess) return e;
-        if (!done) {
-            lu_panel<T><<<1, PT, 0, s>>>(M, np, j0, v.ipiv, v.status);
-            count_launch();
-        }
-        lu_swap<T><<<(np + 255) / 256, 256, 0, s>>>(M, np, j0, v.ipiv);
-        count_launch();
+        lu_panel<T><<<1, PT, 0, s>>>(M, np, j0, v.ipiv, v.status);
+        lu_swap_plan<<<1, 32, 0, s>>>(v.ipiv, j0, v.plan);
+        lu_swap<T><<<(np + 127) / 128, 128, 0, s>>>(M, np, j0, v.plan);
+        count_launch(3);
         const int nrest = (np - j0 - NB) / NB;
         if (nrest > 0) {
             lu_trsm<T><<<nrest, NB, 0, s>>>(M, np, j0);
@@ -970,7 +1113,7 @@ cudaError_t lu_run(T* M, const StackView& v, cudaStream_t s)
                 lu_gemm_f64<<<dim3(nrest, nrest), 256, kGemmSmem64, s>>>(M, np, j0);
             } else {
                 const int nt = (nrest * NB + GT - 1) / GT;
-                lu_gemm_f32<<<dim3(nt, nt), 256, kGemmSmem32, s>>>(M, np, j0);
+                lu_gemm_f32<<<dim3(nt, nt), 256, kGemmSmem32, s>>>(M, np, j0, j0 + NB, np);
             }
             count_launch(2);
         }
@@ -978,20 +1121,61 @@ cudaError_t lu_run(T* M, const StackView& v, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The FP32 factorisation with one panel of lookahead: after panel k's row
+// moves and block row of U, its update of block column k+1 runs first, then
+// panel k+1 (cluster kernel, on the side stream) runs beside panel k's
+// update of the columns beyond k+1 (main stream); the two touch disjoint
+// columns.  Events join the streams before panel k+1's row moves.
+cudaError_t lu_run_lookahead(float* M, const StackView& v, int csize, cudaStream_t s, cudaStream_t side,
+                             cudaEvent_t ready, cudaEvent_t done)
+{
+    const int np = v.np;
+    cudaError_t e = cudaSuccess;
+    if (!panel_f32_cluster(M, np, 0, v, csize, s, e)) {
+        lu_panel<float><<<1, PT, 0, s>>>(M, np, 0, v.ipiv, v.status);
+        count_launch();
+    }
+    if (e != cudaSuccess) return e;
+    lu_swap_plan<<<1, 32, 0, s>>>(v.ipiv, 0, v.plan);
+    count_launch();
+    for (int j0 = 0; j0 < np; j0 += NB) {
+        lu_swap<float><<<(np + 127) / 128, 128, 0, s>>>(M, np, j0, v.plan);
+        count_launch();
+        const int nrest = (np - j0 - NB) / NB;
+        if (nrest == 0) break;
+        lu_trsm<float><<<nrest, NB, 0, s>>>(M, np, j0);
+        const int nt = (nrest * NB + GT - 1) / GT;
+        lu_gemm_f32<<<dim3(nt, 1), 256, kGemmSmem32, s>>>(M, np, j0, j0 + NB, j0 + 2 * NB);
+        count_launch(2);
+        if ((e = cudaEventRecord(ready, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ready, 0)) != cudaSuccess) return e;
+        const int j1 = j0 + NB;
+        if (!panel_f32_cluster(M, np, j1, v, csize, side, e)) {
+            lu_panel<float><<<1, PT, 0, side>>>(M, np, j1, v.ipiv, v.status);
+            count_launch();
+        }
+        if (e != cudaSuccess) return e;
+        lu_swap_plan<<<1, 32, 0, side>>>(v.ipiv, j1, v.plan);
+        count_launch();
+        if (nrest > 1) {
+            lu_gemm_f32<<<dim3(nt, (nrest - 1 + 1) / 2), 256, kGemmSmem32, s>>>(M, np, j0, j0 + 2 * NB, np);
+            count_launch();
+        }
+        if ((e = cudaEventRecord(done, side)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, done, 0)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t sweeps(const T* M, const StackView& v, T* W, cudaStream_t s)
 {
+    // forward W -> Y, backward Y -> W
     const int np = v.np, nb = np / NB;
-    for (int b = 0; b < nb; ++b) {
-        tri_block<T, true><<<1, NB, 0, s>>>(M, np, b, v.nc, W);
-        count_launch();
-        if (b + 1 < nb) launch_tri_update<T, true>(M, np, b, v.nc, W, s);
-    }
-    for (int b = nb - 1; b >= 0; --b) {
-        tri_block<T, false><<<1, NB, 0, s>>>(M, np, b, v.nc, W);
-        count_launch();
-        if (b > 0) launch_tri_update<T, false>(M, np, b, v.nc, W, s);
-    }
+    const T* Inv = static_cast<const T*>(v.Inv);
+    T* Y = static_cast<T*>(v.Y);
+    for (int b = 0; b < nb; ++b) launch_sweep_step<T, true>(M, Inv, np, b, v.nc, W, Y, s);
+    for (int b = nb - 1; b >= 0; --b) launch_sweep_step<T, false>(M, Inv, np, b, v.nc, Y, W, s);
     return cudaGetLastError();
 }
 
@@ -1046,7 +1230,8 @@ cudaError_t launch_stack_assemble(const StackView& v, long long tiles, bool mixe
     return cudaGetLastError();
 }
 
-cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s)
+cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s, cudaStream_t side, cudaEvent_t ready,
+                            cudaEvent_t done)
 {
     cudaError_t e = mixed ? cudaFuncSetAttribute(lu_gemm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kGemmSmem32)
@@ -1061,7 +1246,18 @@ cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s)
     // traced as one span per factorisation: 2 np^3 / 3 flop, the matrix read
     // and written once
     cudaEvent_t ev = trace_begin(s);
-    e = mixed ? lu_run<float>(v.M32, v, s) : lu_run<double>(v.M, v, s);
+    if (mixed) {
+        const int csize = panel_cluster_size();
+        e = side ? lu_run_lookahead(v.M32, v, csize, s, side, ready, done) : lu_run<float>(v.M32, v, s);
+    } else {
+        e = lu_run<double>(v.M, v, s);
+    }
+    if (e == cudaSuccess) {
+        if (mixed) tri_inverse<float><<<v.np / NB, NB, 0, s>>>(v.M32, v.np, static_cast<float*>(v.Inv));
+        else tri_inverse<double><<<v.np / NB, NB, 0, s>>>(v.M, v.np, static_cast<double*>(v.Inv));
+        count_launch();
+        e = cudaGetLastError();
+    }
     const double n = (double)v.np;
     trace_end(GBEM_KERNEL_FACTOR, ev, s, (mixed ? 8.0 : 16.0) * n * n, 2.0 * n * n * n / 3.0);
     if (e != cudaSuccess) return e;

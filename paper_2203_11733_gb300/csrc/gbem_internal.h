@@ -291,7 +291,7 @@ cudaError_t launch_capacitance(const int32_t* cond, int n, int np, int n_cond, c
 // potential (-1: none); cidx: the conductor index of a conductor or
 // electrode panel (-1: none).  Matrices np x np column-major: M0 the
 // assembled system (FP64), factored in place as M (FP64 mode) or M32 (mixed
-// mode); B, X, R: np x nc FP64; W: np x nc in the factor's type.
+// mode); B, X, R: np x nc FP64; W, Y: np x nc in the factor's type.
 struct StackView {
     int n = 0, n_eq = 0, np = 0, nc = 0, R_layers = 0;
     const double *c = nullptr, *lo0 = nullptr, *hi0 = nullptr, *lo1 = nullptr, *hi1 = nullptr;
@@ -304,15 +304,21 @@ struct StackView {
     float* M32 = nullptr;
     double *B = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *C = nullptr;
     void* W = nullptr;
+    void* Y = nullptr;      // np x nc, the forward sweep's result (factor's type)
+    void* Inv = nullptr;    // np/64 x 2 inverses of the factor's 64 x 64 diagonal blocks
     int *ipiv = nullptr, *perm = nullptr, *status = nullptr;
+    int* plan = nullptr;    // 1 + 4 * 64 ints: one panel's row moves
     unsigned long long* norms = nullptr;
 };
 cudaError_t stack_gl_upload(cudaStream_t s);
 // M0 and B from the geometry (entries FP64, or FP32 far field in mixed
 // mode), then the copy to factor (M, or M32 in mixed mode).
 cudaError_t launch_stack_assemble(const StackView& v, long long tiles, bool mixed, cudaStream_t s);
-// LU with partial pivoting of M (M32), ipiv, and perm from ipiv.
-cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s);
+// LU with partial pivoting of M (M32), ipiv, and perm from ipiv.  In mixed
+// mode with a side stream (and two events) each panel after the first runs
+// there beside the previous panel's trailing update.
+cudaError_t launch_stack_lu(const StackView& v, bool mixed, cudaStream_t s, cudaStream_t side, cudaEvent_t ready,
+                            cudaEvent_t done);
 // One correction: W = (LU)^-1 P R in the factor's type, X += W.
 cudaError_t launch_stack_correct(const StackView& v, bool mixed, cudaStream_t s);
 // R = B - M0 X in FP64; norms[m] = max_r |R[r, m]|, norms[nc + m] = max_r

@@ -70,25 +70,36 @@ __device__ __noinline__ double H_orth(double u, double v, double w)
     return r;
 }
 
-// Phi(u,v,w) above; w != 0 (coplanar panels have no double-layer entry).
-__device__ __noinline__ double Phi_par(double u, double v, double w)
+// F and Phi at one corner together (parallel panels, w != 0): they share
+// rho, ln(u + rho), ln(v + rho) and atan(u v / (w rho)).
+__device__ __noinline__ void FPhi_par(double u, double v, double w, double& f, double& phi)
 {
     double u2 = u * u, v2 = v * v, w2 = w * w;
     double rho = sqrt(u2 + v2 + w2);
-    double r = xlog(u * w, u, v2 + w2, rho) + xlog(v * w, v, u2 + w2, rho) - 0.5 * u * w * log(v2 + w2) -
-               0.5 * v * w * log(u2 + w2) - w * rho;
-    if (u * v != 0.0) r += u * v * atan(u * v / (w * rho));
-    return r;
+    const double lu = (u != 0.0) ? xlog(1.0, u, v2 + w2, rho) : 0.0;   // ln(u + rho)
+    const double lv = (v != 0.0) ? xlog(1.0, v, u2 + w2, rho) : 0.0;   // ln(v + rho)
+    const double at = (u * v != 0.0) ? atan(u * v / (w * rho)) : 0.0;
+    f = 0.5 * v * (u2 - w2) * lv + 0.5 * u * (v2 - w2) * lu - (u2 + v2 - 2.0 * w2) * rho * (1.0 / 6.0) -
+        u * v * w * at;
+    phi = u * w * lu + v * w * lv - 0.5 * u * w * log(v2 + w2) - 0.5 * v * w * log(u2 + w2) - w * rho + u * v * at;
 }
 
-// Theta(u,v,w) above.
-__device__ __noinline__ double Theta_orth(double u, double v, double w)
+// H and Theta at one corner together (perpendicular panels): they share rho,
+// ln(u + rho), ln(w + rho) and atan(u w / (v rho)).
+__device__ __noinline__ void HTheta_orth(double u, double v, double w, double& h, double& theta)
 {
     double u2 = u * u, v2 = v * v, w2 = w * w;
     double rho = sqrt(u2 + v2 + w2);
-    double r = xlog(-u * w, u, v2 + w2, rho) + xlog(-0.5 * (u2 - v2), w, u2 + v2, rho) + 0.5 * w * rho;
-    if (u * v != 0.0 && w != 0.0) r += u * v * atan(u * w / (v * rho));
-    return r;
+    // ln(u + rho) and ln(w + rho), 0 where the argument vanishes (their
+    // coefficients vanish there too: the 0 ln 0 limits)
+    const double lu = (v2 + w2 != 0.0 || u > 0.0) ? xlog(1.0, u, v2 + w2, rho) : 0.0;
+    const double lw = (u2 + v2 != 0.0 || w > 0.0) ? xlog(1.0, w, u2 + v2, rho) : 0.0;
+    const double a_uw = (u * v != 0.0 && w != 0.0) ? atan(u * w / (v * rho)) : 0.0;
+    h = u * v * w * lu + xlog(w * (3.0 * u2 - w2) * (1.0 / 6.0), v, u2 + w2, rho) +
+        v * (3.0 * u2 - v2) * (1.0 / 6.0) * lw - v * w * rho * (1.0 / 3.0) - 0.5 * u * v2 * a_uw;
+    if (u * w != 0.0 && v != 0.0) h -= 0.5 * u * w2 * atan(u * v / (w * rho));
+    if (u != 0.0 && v * w != 0.0) h -= (u * u2 * (1.0 / 6.0)) * atan(v * w / (u * rho));
+    theta = -u * w * lu - 0.5 * (u2 - v2) * lw + 0.5 * w * rho + u * v * a_uw;
 }
 
 }  // namespace

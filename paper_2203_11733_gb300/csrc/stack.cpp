@@ -26,12 +26,16 @@ struct gbem_stack_s {
     void* M0 = nullptr;             // the assembled system (FP64)
     void* Mf = nullptr;             // the copy factored in place (FP64, or FP32 in mixed mode)
     size_t m0_bytes = 0, mf_bytes = 0;
-    void* work = nullptr;           // B, X, R, W, P, C, ipiv, perm, status, norms
+    void* work = nullptr;           // B, X, R, W, Y, Inv, P, C, ipiv, perm, status, norms
     size_t work_bytes = 0;
     StackView v;
     bool assembled = false, factored = false;
     int iters = 0;                  // corrections of the last solve
     cudaStream_t last = nullptr;
+    // the mixed factor's lookahead: panels on a second stream (highest
+    // priority), joined by two events; created at first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
 };
 
 namespace {
@@ -296,9 +300,11 @@ gbem_status stack_alloc(gbem_stack_s* S, gbem_precision prec, cudaStream_t s)
         return o;
     };
     const size_t vec = 8 * np * nc;
-    const size_t o_B = take(vec), o_X = take(vec), o_R = take(vec), o_W = take(vec);
+    const size_t o_B = take(vec), o_X = take(vec), o_R = take(vec), o_W = take(vec), o_Y = take(vec);
+    const size_t o_inv = take((mixed ? 4 : 8) * np * 2 * 64);
     const size_t o_P = take(stack_partial_bytes((int)np, (int)nc)), o_C = take(8 * nc * nc);
     const size_t o_piv = take(4 * np), o_perm = take(4 * np), o_st = take(4), o_nrm = take(16 * nc);
+    const size_t o_plan = take(4 * (1 + 4 * 64));
     S->work = ctx_alloc(ctx, off, s);
     if (!S->work) return ctx_fail(ctx, GBEM_ERR_OOM, "stack work space");
     S->work_bytes = off;
@@ -311,12 +317,15 @@ gbem_status stack_alloc(gbem_stack_s* S, gbem_precision prec, cudaStream_t s)
     v.X = reinterpret_cast<double*>(b + o_X);
     v.R = reinterpret_cast<double*>(b + o_R);
     v.W = b + o_W;
+    v.Y = b + o_Y;
+    v.Inv = b + o_inv;
     v.P = reinterpret_cast<double*>(b + o_P);
     v.C = reinterpret_cast<double*>(b + o_C);
     v.ipiv = reinterpret_cast<int*>(b + o_piv);
     v.perm = reinterpret_cast<int*>(b + o_perm);
     v.status = reinterpret_cast<int*>(b + o_st);
     v.norms = reinterpret_cast<unsigned long long*>(b + o_nrm);
+    v.plan = reinterpret_cast<int*>(b + o_plan);
     return GBEM_OK;
 }
 
@@ -454,9 +463,17 @@ gbem_status gbem_stack_capacitance(gbem_stack_t* S, gbem_stream stream, double* 
     const bool mixed = S->prec == GBEM_MIXED;
     StackView& v = S->v;
     const size_t np = S->np, nc = S->nc;
+    if (mixed && !S->side) {
+        int least = 0, greatest = 0;
+        if (!ok(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priorities") ||
+            !ok(ctx, cudaStreamCreateWithPriority(&S->side, cudaStreamNonBlocking, greatest), "stream") ||
+            !ok(ctx, cudaEventCreateWithFlags(&S->ev_ready, cudaEventDisableTiming), "event") ||
+            !ok(ctx, cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming), "event"))
+            return GBEM_ERR_CUDA;
+    }
     if (!S->factored) {
         if (!ok(ctx, cudaMemsetAsync(v.status, 0, sizeof(int), s), "memset") ||
-            !ok(ctx, launch_stack_lu(v, mixed, s), "LU"))
+            !ok(ctx, launch_stack_lu(v, mixed, s, mixed ? S->side : nullptr, S->ev_ready, S->ev_done), "LU"))
             return GBEM_ERR_CUDA;
         S->factored = true;
     }
@@ -515,8 +532,12 @@ void gbem_stack_destroy(gbem_stack_t* S)
     if (ctx->device >= 0 && (S->meta || S->M0 || S->work)) {
         Dev g(ctx->device);
         cudaStreamSynchronize(S->last);
+        if (S->side) cudaStreamSynchronize(S->side);
         stack_free(S, S->last);
         if (S->meta) ctx_free(ctx, S->meta, S->meta_bytes, nullptr);
+        if (S->ev_ready) cudaEventDestroy(S->ev_ready);
+        if (S->ev_done) cudaEventDestroy(S->ev_done);
+        if (S->side) cudaStreamDestroy(S->side);
     }
     delete S;
 }
