@@ -753,8 +753,6 @@ def run_stack(args):
     gbem.load()
     ctx = gbem.Context(local)
     stream = torch.cuda.Stream()
-    rates = ctx.unit_rates(stream)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     spec = W.stack_3layer_5wires()
 
     def make():
@@ -762,6 +760,19 @@ def run_stack(args):
                           spec["h"], spec["h_outer"])
 
     S = make()
+    if args.profile:
+        # one warm-up and one extraction in that precision, nothing else
+        prec = gbem.GBEM_MIXED if args.profile == "mixed" else gbem.GBEM_FP64
+        for _ in range(2):
+            S.assemble(prec, stream)
+            C, resid = S.capacitance(stream)
+        if rank == 0:
+            print(json.dumps({"profile": args.profile, "n_eq": S.n_eq, "residual": resid, "C": C.tolist()}))
+        S.close()
+        ctx.close()
+        return
+    rates = ctx.unit_rates(stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
         S.assemble(gbem.GBEM_MIXED, stream)

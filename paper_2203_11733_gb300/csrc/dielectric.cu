@@ -667,18 +667,21 @@ __global__ void __launch_bounds__(32) lu_swap_plan(const int* __restrict__ ipiv,
     }
 }
 
-// The panel's interchanges applied to every column outside it: each thread
-// gathers the moved rows of its column at once, then writes them.
+// The panel's interchanges applied to the columns c_lo .. c_hi-1 outside
+// skip_lo .. skip_hi-1: each thread gathers the moved rows of its column at
+// once, then writes them.
 template <typename T>
-__global__ void __launch_bounds__(128) lu_swap(T* __restrict__ M, int np, int j0, const int* __restrict__ plan)
+__global__ void __launch_bounds__(128) lu_swap(T* __restrict__ M, int np, int c_lo, int c_hi, int skip_lo,
+                                               int skip_hi, const int* __restrict__ plan)
 {
     __shared__ int pl[1 + 4 * NB];
     for (int e = threadIdx.x; e < 1 + 4 * NB; e += blockDim.x) pl[e] = plan[e];
     __syncthreads();
     const int m = pl[0];
-    const int ncols = np - NB;
+    // columns c_lo .. c_hi-1 except skip_lo .. skip_hi-1 (inside the range)
+    const int ncols = (c_hi - c_lo) - (skip_hi - skip_lo);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncols; t += gridDim.x * blockDim.x) {
-        const int c = t < j0 ? t : t + NB;
+        const int c = c_lo + t < skip_lo ? c_lo + t : c_lo + t + (skip_hi - skip_lo);
         T* e = M + (size_t)c * np;
         T v[2 * NB];
 #pragma unroll 16
@@ -690,9 +693,10 @@ __global__ void __launch_bounds__(128) lu_swap(T* __restrict__ M, int np, int j0
     }
 }
 
-// U12 = L11^-1 A12 for 64 columns per CTA (L11 the panel's unit lower block).
+// U12 = L11^-1 A12 for 64 columns per CTA from column c_lo on (L11 the
+// panel's unit lower block).
 template <typename T>
-__global__ void __launch_bounds__(NB) lu_trsm(T* __restrict__ M, int np, int j0)
+__global__ void __launch_bounds__(NB) lu_trsm(T* __restrict__ M, int np, int j0, int c_lo)
 {
     __shared__ T L[NB][NB + 1];
     const size_t ld = (size_t)np;
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(NB) lu_trsm(T* __restrict__ M, int np, int j0)
         L[r][c] = M[(size_t)(j0 + r) + (size_t)(j0 + c) * ld];
     }
     __syncthreads();
-    const int cc = j0 + NB + blockIdx.x * NB + tid;
+    const int cc = c_lo + blockIdx.x * NB + tid;
     T* col = M + (size_t)cc * ld + j0;
     T x[NB];
 #pragma unroll
@@ -1104,11 +1108,11 @@ cudaError_t lu_run(T* M, const StackView& v, cudaStream_t s)
     for (int j0 = 0; j0 < np; j0 += NB) {
         lu_panel<T><<<1, PT, 0, s>>>(M, np, j0, v.ipiv, v.status);
         lu_swap_plan<<<1, 32, 0, s>>>(v.ipiv, j0, v.plan);
-        lu_swap<T><<<(np + 127) / 128, 128, 0, s>>>(M, np, j0, v.plan);
+        lu_swap<T><<<(np + 127) / 128, 128, 0, s>>>(M, np, 0, np, j0, j0 + NB, v.plan);
         count_launch(3);
         const int nrest = (np - j0 - NB) / NB;
         if (nrest > 0) {
-            lu_trsm<T><<<nrest, NB, 0, s>>>(M, np, j0);
+            lu_trsm<T><<<nrest, NB, 0, s>>>(M, np, j0, j0 + NB);
             if constexpr (sizeof(T) == 8) {
                 lu_gemm_f64<<<dim3(nrest, nrest), 256, kGemmSmem64, s>>>(M, np, j0);
             } else {
@@ -1139,28 +1143,41 @@ cudaError_t lu_run_lookahead(float* M, const StackView& v, int csize, cudaStream
     lu_swap_plan<<<1, 32, 0, s>>>(v.ipiv, 0, v.plan);
     count_launch();
     for (int j0 = 0; j0 < np; j0 += NB) {
-        lu_swap<float><<<(np + 127) / 128, 128, 0, s>>>(M, np, j0, v.plan);
-        count_launch();
         const int nrest = (np - j0 - NB) / NB;
-        if (nrest == 0) break;
-        lu_trsm<float><<<nrest, NB, 0, s>>>(M, np, j0);
+        if (nrest == 0) {
+            lu_swap<float><<<(np + 127) / 128, 128, 0, s>>>(M, np, 0, np, j0, j0 + NB, v.plan);
+            count_launch();
+            break;
+        }
+        // what the next panel needs first: its block column swapped, its
+        // block row of U, and this panel's update of it
+        const int j1 = j0 + NB, j2 = j0 + 2 * NB;
+        lu_swap<float><<<1, 128, 0, s>>>(M, np, j1, j2, j1, j1, v.plan);
+        lu_trsm<float><<<1, NB, 0, s>>>(M, np, j0, j1);
         const int nt = (nrest * NB + GT - 1) / GT;
-        lu_gemm_f32<<<dim3(nt, 1), 256, kGemmSmem32, s>>>(M, np, j0, j0 + NB, j0 + 2 * NB);
-        count_launch(2);
+        lu_gemm_f32<<<dim3(nt, 1), 256, kGemmSmem32, s>>>(M, np, j0, j1, j2);
+        count_launch(3);
         if ((e = cudaEventRecord(ready, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ready, 0)) != cudaSuccess) return e;
-        const int j1 = j0 + NB;
         if (!panel_f32_cluster(M, np, j1, v, csize, side, e)) {
             lu_panel<float><<<1, PT, 0, side>>>(M, np, j1, v.ipiv, v.status);
             count_launch();
         }
         if (e != cudaSuccess) return e;
-        lu_swap_plan<<<1, 32, 0, side>>>(v.ipiv, j1, v.plan);
+        // the rest beside the next panel: the other columns' row moves (the
+        // plan is rewritten only after this, on the side stream), their
+        // block row of U and the trailing update
+        lu_swap<float><<<(np + 127) / 128, 128, 0, s>>>(M, np, 0, np, j0, j2, v.plan);
         count_launch();
         if (nrest > 1) {
-            lu_gemm_f32<<<dim3(nt, (nrest - 1 + 1) / 2), 256, kGemmSmem32, s>>>(M, np, j0, j0 + 2 * NB, np);
-            count_launch();
+            lu_trsm<float><<<nrest - 1, NB, 0, s>>>(M, np, j0, j2);
+            lu_gemm_f32<<<dim3(nt, nrest / 2), 256, kGemmSmem32, s>>>(M, np, j0, j2, np);
+            count_launch(2);
         }
+        if ((e = cudaEventRecord(ready, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ready, 0)) != cudaSuccess) return e;
+        lu_swap_plan<<<1, 32, 0, side>>>(v.ipiv, j1, v.plan);
+        count_launch();
         if ((e = cudaEventRecord(done, side)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(s, done, 0)) != cudaSuccess) return e;
     }
