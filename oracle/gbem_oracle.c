@@ -41,6 +41,11 @@
  * I_i (never swapped: the kernel is not symmetric), and separated pairs a
  * direct 4-D Gauss-Legendre rule.  Coplanar pairs give 0.
  *
+ * Flat triangles (general conductors): the same a_ij over triangles T_i, T_j,
+ * with the exact potential of a uniformly charged triangle inside and an
+ * adaptive collapsed Gauss-Legendre rule (midpoint subdivision) outside;
+ * separated pairs by the collapsed rule on both triangles.
+ *
  * Coordinates: a panel has a normal axis k in {0,1,2}, a plane coordinate c,
  * and extents [lo0,hi0] x [lo1,hi1] along the two remaining axes taken in
  * increasing axis order.  geo[5*i .. 5*i+4] = {c, lo0, hi0, lo1, hi1}.
@@ -484,6 +489,203 @@ static double orc_pair(const orc_panel* Pi, const orc_panel* Pj, int* nfail)
 }
 
 /* ------------------------------------------------------------------ */
+/* Flat triangles (general conductors).                                */
+/* ------------------------------------------------------------------ */
+
+/* Vertices a, b, c; unit normal along (b - a) x (c - a); area. */
+typedef struct {
+    double v[3][3];
+    double n[3];
+    double area;
+    double diam;
+} orc_tri;
+
+static void orc_cross(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double orc_dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void orc_make_tri(const double* p, orc_tri* T)
+{
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) T->v[k][d] = p[3 * k + d];
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; ++d) {
+        e1[d] = T->v[1][d] - T->v[0][d];
+        e2[d] = T->v[2][d] - T->v[0][d];
+    }
+    orc_cross(e1, e2, T->n);
+    double len = sqrt(orc_dot(T->n, T->n));
+    T->area = 0.5 * len;
+    for (int d = 0; d < 3; ++d) T->n[d] /= len;
+    T->diam = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) {
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) s += (T->v[i][d] - T->v[j][d]) * (T->v[i][d] - T->v[j][d]);
+            T->diam = fmax(T->diam, sqrt(s));
+        }
+}
+
+/* ln(R + l) with R = sqrt(l^2 + r0sq), without cancellation for l < 0. */
+static double orc_lnp(double l, double r0sq, double R)
+{
+    if (l >= 0.0) return log(R + l);
+    return log(r0sq / (R - l));
+}
+
+/* int_T 1/|x - y| dy: the potential of a uniformly charged flat triangle
+ * (the edge-by-edge closed form: for each edge, with x projected to rho in
+ * the plane at signed height h, the edge's direction l, its outward in-plane
+ * normal u, P0 = (edge start - rho).u, and l+- the edge ends' coordinates
+ * along l,  P0 ln((R+ + l+)/(R- + l-)) - |h| [atan(P0 l+/(R0^2 + |h| R+)) -
+ * atan(P0 l-/(R0^2 + |h| R-))]). */
+static double orc_tri_potential(const orc_tri* T, const double x[3])
+{
+    double h = 0.0, rho[3];
+    for (int d = 0; d < 3; ++d) h += (x[d] - T->v[0][d]) * T->n[d];
+    for (int d = 0; d < 3; ++d) rho[d] = x[d] - h * T->n[d];
+    const double ah = fabs(h);
+    double s = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        const double* p = T->v[e];
+        const double* q = T->v[(e + 1) % 3];
+        double l[3], u[3], L = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            l[d] = q[d] - p[d];
+            L += l[d] * l[d];
+        }
+        L = sqrt(L);
+        for (int d = 0; d < 3; ++d) l[d] /= L;
+        orc_cross(l, T->n, u);
+        double qp[3], pp[3];
+        for (int d = 0; d < 3; ++d) {
+            qp[d] = q[d] - rho[d];
+            pp[d] = p[d] - rho[d];
+        }
+        const double lp = orc_dot(qp, l), lm = orc_dot(pp, l), P0 = orc_dot(pp, u);
+        const double r0sq = P0 * P0 + h * h;
+        const double Rp = sqrt(lp * lp + r0sq), Rm = sqrt(lm * lm + r0sq);
+        if (P0 != 0.0) {
+            s += P0 * (orc_lnp(lp, r0sq, Rp) - orc_lnp(lm, r0sq, Rm));
+            if (ah != 0.0) s -= ah * (atan(P0 * lp / (r0sq + ah * Rp)) - atan(P0 * lm / (r0sq + ah * Rm)));
+        }
+    }
+    return s;
+}
+
+/* Collapsed Gauss-Legendre rule of order n on triangle (a, b, c) applied to
+ * the potential of Tj: y = a + xi ((b - a) + eta (c - b)), dy = 2 |T| xi dxi deta. */
+static double orc_tri_outer_gl(const double a[3], const double b[3], const double c[3], const orc_tri* Tj, int n)
+{
+    double ab[3], bc[3], cr[3];
+    for (int d = 0; d < 3; ++d) {
+        ab[d] = b[d] - a[d];
+        bc[d] = c[d] - b[d];
+    }
+    orc_cross(ab, bc, cr);
+    const double j2 = sqrt(orc_dot(cr, cr));   /* 2 |T| */
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double xi = 0.5 * (orc_glx[n][i] + 1.0);
+        double row = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double eta = 0.5 * (orc_glx[n][k] + 1.0);
+            double y[3];
+            for (int d = 0; d < 3; ++d) y[d] = a[d] + xi * (ab[d] + eta * bc[d]);
+            row += orc_glw[n][k] * orc_tri_potential(Tj, y);
+        }
+        s += orc_glw[n][i] * xi * row;
+    }
+    return 0.25 * j2 * s;
+}
+
+/* Adaptive outer quadrature: orders 12 and 16 compared on the triangle,
+ * else its four midpoint children. */
+static double orc_tri_outer(const double a[3], const double b[3], const double c[3], const orc_tri* Tj,
+                            double floor, int depth, int* nfail)
+{
+    const double i12 = orc_tri_outer_gl(a, b, c, Tj, 12);
+    const double i16 = orc_tri_outer_gl(a, b, c, Tj, 16);
+    const double diff = fabs(i16 - i12), mag = fmax(fabs(i16), floor);
+    if (diff <= 1e-14 * mag || (depth >= 5 && diff <= 1e-12 * mag)) return i16;
+    if (depth >= 9) {
+        ++*nfail;
+        return i16;
+    }
+    double ab[3], bc[3], ca[3];
+    for (int d = 0; d < 3; ++d) {
+        ab[d] = 0.5 * (a[d] + b[d]);
+        bc[d] = 0.5 * (b[d] + c[d]);
+        ca[d] = 0.5 * (c[d] + a[d]);
+    }
+    return orc_tri_outer(a, ab, ca, Tj, floor, depth + 1, nfail) + orc_tri_outer(ab, b, bc, Tj, floor, depth + 1, nfail) +
+           orc_tri_outer(ca, bc, c, Tj, floor, depth + 1, nfail) + orc_tri_outer(ab, bc, ca, Tj, floor, depth + 1, nfail);
+}
+
+/* int_Ti int_Tj 1/|x - y| (no 1/(4 pi)).  Separated pairs (centroid distance
+ * at least three diameters) use the collapsed rule on both triangles, orders
+ * 8 and 10 compared; otherwise the adaptive outer quadrature of Tj's exact
+ * potential over the smaller triangle (the integral is symmetric). */
+static double orc_tri_pair(const orc_tri* Ti, const orc_tri* Tj, int* nfail)
+{
+    double ci[3], cj[3], dist = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        ci[d] = (Ti->v[0][d] + Ti->v[1][d] + Ti->v[2][d]) / 3.0;
+        cj[d] = (Tj->v[0][d] + Tj->v[1][d] + Tj->v[2][d]) / 3.0;
+        dist += (ci[d] - cj[d]) * (ci[d] - cj[d]);
+    }
+    dist = sqrt(dist);
+    const double dmax = fmax(Ti->diam, Tj->diam);
+    const orc_tri* O = Ti->area <= Tj->area ? Ti : Tj;
+    const orc_tri* I = O == Ti ? Tj : Ti;
+    if (dist >= 3.0 * dmax) {
+        double r[2];
+        for (int t = 0; t < 2; ++t) {
+            const int n = t ? 10 : 8;
+            double abi[3], bci[3], abj[3], bcj[3], cr[3];
+            for (int d = 0; d < 3; ++d) {
+                abi[d] = O->v[1][d] - O->v[0][d];
+                bci[d] = O->v[2][d] - O->v[1][d];
+                abj[d] = I->v[1][d] - I->v[0][d];
+                bcj[d] = I->v[2][d] - I->v[1][d];
+            }
+            orc_cross(abi, bci, cr);
+            const double ji = sqrt(orc_dot(cr, cr));
+            orc_cross(abj, bcj, cr);
+            const double jj = sqrt(orc_dot(cr, cr));
+            double s = 0.0;
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    const double xa = 0.5 * (orc_glx[n][a] + 1.0), eb = 0.5 * (orc_glx[n][b] + 1.0);
+                    double x[3];
+                    for (int d = 0; d < 3; ++d) x[d] = O->v[0][d] + xa * (abi[d] + eb * bci[d]);
+                    double sy = 0.0;
+                    for (int c = 0; c < n; ++c)
+                        for (int e = 0; e < n; ++e) {
+                            const double xc = 0.5 * (orc_glx[n][c] + 1.0), ee = 0.5 * (orc_glx[n][e] + 1.0);
+                            double y[3], q = 0.0;
+                            for (int d = 0; d < 3; ++d) {
+                                y[d] = I->v[0][d] + xc * (abj[d] + ee * bcj[d]) - x[d];
+                                q += y[d] * y[d];
+                            }
+                            sy += orc_glw[n][c] * orc_glw[n][e] * xc / sqrt(q);
+                        }
+                    s += orc_glw[n][a] * orc_glw[n][b] * xa * sy;
+                }
+            r[t] = s * ji * jj / 16.0;
+        }
+        if (fabs(r[1] - r[0]) <= 5e-14 * fabs(r[1])) return r[1];
+    }
+    const double floor = O->area * I->area / (dist + dmax);
+    return orc_tri_outer(O->v[0], O->v[1], O->v[2], I, floor, 0, nfail);
+}
+
+/* ------------------------------------------------------------------ */
 /* Exported entry points (ctypes).                                     */
 /* ------------------------------------------------------------------ */
 
@@ -612,4 +814,41 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+double orc_tri_potential_at(const double* tri, const double* x)
+{
+    orc_tri T;
+    orc_make_tri(tri, &T);
+    return orc_tri_potential(&T, x);
+}
+
+/* Galerkin entries of flat triangles, a_ij = int int 1/r / (4 pi |T_i| |T_j|),
+ * for m sampled pairs (tri: 9 doubles per triangle, its three vertices). */
+int orc_tri_entries(int n, const double* tri, int64_t m, const int32_t* I, const int32_t* J, double* out,
+                    int nthreads)
+{
+    orc_gl_init();
+    int nf_total = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : nf_total)
+    for (int64_t t = 0; t < m; ++t) {
+        int i = I[t], j = J[t];
+        if (i < 0 || j < 0 || i >= n || j >= n) {
+            out[t] = NAN;
+            continue;
+        }
+        orc_tri Ti, Tj;
+        orc_make_tri(tri + 9 * (size_t)i, &Ti);
+        orc_make_tri(tri + 9 * (size_t)j, &Tj);
+        int nf = 0;
+        double v = orc_tri_pair(&Ti, &Tj, &nf);
+        nf_total += nf;
+        out[t] = v / (4.0 * ORC_PI * Ti.area * Tj.area);
+    }
+    return nf_total;
 }

@@ -289,3 +289,28 @@ def stack_3layer_5wires(h: float = 0.25, h_outer: float = 0.6):
         "boxes": [([-4.0 + 2 * i, -5.0, 1.5], [-3.0 + 2 * i, 5.0, 2.0], i) for i in range(5)],
         "h": h, "h_outer": h_outer,
     }
+
+
+def icosphere(R: float = 1.0, level: int = 2, centre=(0.0, 0.0, 0.0)):
+    """Flat triangles inscribed in a sphere of radius R: the icosahedron,
+    each face split into four by its edge midpoints `level` times, the new
+    vertices pushed out to the sphere.  Returns float64[20 * 4**level, 9]
+    (each row the three vertices, counter-clockwise seen from outside)."""
+    import numpy as np
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    tris = np.array([[v[a], v[b], v[c]] for a, b, c in f])
+    for _ in range(level):
+        a, b, c = tris[:, 0], tris[:, 1], tris[:, 2]
+        ab, bc, ca = a + b, b + c, c + a
+        ab /= np.linalg.norm(ab, axis=1, keepdims=True)
+        bc /= np.linalg.norm(bc, axis=1, keepdims=True)
+        ca /= np.linalg.norm(ca, axis=1, keepdims=True)
+        tris = np.concatenate([np.stack([a, ab, ca], 1), np.stack([ab, b, bc], 1), np.stack([ca, bc, c], 1),
+                               np.stack([ab, bc, ca], 1)])
+    return (R * tris + np.asarray(centre, dtype=np.float64)).reshape(-1, 9)
