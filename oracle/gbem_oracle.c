@@ -42,8 +42,10 @@
  * direct 4-D Gauss-Legendre rule.  Coplanar pairs give 0.
  *
  * Flat triangles (general conductors): the same a_ij over triangles T_i, T_j,
- * with the exact potential of a uniformly charged triangle inside and an
- * adaptive collapsed Gauss-Legendre rule (midpoint subdivision) outside;
+ * with the exact potential of a uniformly charged triangle inside; outside,
+ * for triangles that share a vertex (or are the same), a tanh-sinh rule in
+ * both coordinates of the collapsed map, refined until two levels agree,
+ * else an adaptive collapsed Gauss-Legendre rule (midpoint subdivision);
  * separated pairs by the collapsed rule on both triangles.
  *
  * Coordinates: a panel has a normal axis k in {0,1,2}, a plane coordinate c,
@@ -627,6 +629,58 @@ static double orc_tri_outer(const double a[3], const double b[3], const double c
            orc_tri_outer(ca, bc, c, Tj, floor, depth + 1, nfail) + orc_tri_outer(ab, bc, ca, Tj, floor, depth + 1, nfail);
 }
 
+/* Tanh-sinh rule in both coordinates of the collapsed map of triangle
+ * (a, b, c), for an outer integrand whose derivatives are singular on the
+ * triangle's sides and corners (the potential of a triangle that shares a
+ * vertex, a side or the whole triangle): every side lies on the boundary of
+ * the unit square, where the double-exponential rule converges fast.  Level
+ * L uses the step 2^-L; levels are refined until two agree. */
+static double orc_tri_outer_ts(const double a[3], const double b[3], const double c[3], const orc_tri* Tj,
+                               double floor, int* nfail)
+{
+    double ab[3], bc[3], cr[3];
+    for (int d = 0; d < 3; ++d) {
+        ab[d] = b[d] - a[d];
+        bc[d] = c[d] - b[d];
+    }
+    orc_cross(ab, bc, cr);
+    const double j2 = sqrt(orc_dot(cr, cr));
+    double total = 0.0, prev = 0.0, est = 0.0;
+    for (int L = 2; L <= ORC_TS_LMAX; ++L) {
+        const double h = 1.0 / (double)(1 << L);
+        const int kmax = (int)(ORC_TS_TMAX / h);
+        for (int ia = -kmax; ia <= kmax; ++ia) {
+            double xi, wx;
+            orc_ts_node(0.0, 1.0, ia * h, &xi, &wx);
+            if (wx == 0.0) continue;
+            double row = 0.0;
+            for (int ib = -kmax; ib <= kmax; ++ib) {
+                if (L > 2 && ((ia & 1) == 0) && ((ib & 1) == 0)) continue;
+                double eta, we;
+                orc_ts_node(0.0, 1.0, ib * h, &eta, &we);
+                if (we == 0.0) continue;
+                double y[3];
+                for (int d = 0; d < 3; ++d) y[d] = a[d] + xi * (ab[d] + eta * bc[d]);
+                row += we * orc_tri_potential(Tj, y);
+            }
+            total += wx * xi * row;
+        }
+        est = total * h * h * j2;
+        if (L > 2 && fabs(est - prev) <= 1e-14 * fmax(fabs(est), floor)) return est;
+        prev = est;
+    }
+    ++*nfail;
+    return est;
+}
+
+static int orc_tri_touch(const orc_tri* A, const orc_tri* B)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (A->v[i][0] == B->v[j][0] && A->v[i][1] == B->v[j][1] && A->v[i][2] == B->v[j][2]) return 1;
+    return 0;
+}
+
 /* int_Ti int_Tj 1/|x - y| (no 1/(4 pi)).  Separated pairs (centroid distance
  * at least three diameters) use the collapsed rule on both triangles, orders
  * 8 and 10 compared; otherwise the adaptive outer quadrature of Tj's exact
@@ -682,6 +736,7 @@ static double orc_tri_pair(const orc_tri* Ti, const orc_tri* Tj, int* nfail)
         if (fabs(r[1] - r[0]) <= 5e-14 * fabs(r[1])) return r[1];
     }
     const double floor = O->area * I->area / (dist + dmax);
+    if (orc_tri_touch(O, I)) return orc_tri_outer_ts(O->v[0], O->v[1], O->v[2], I, floor, nfail);
     return orc_tri_outer(O->v[0], O->v[1], O->v[2], I, floor, 0, nfail);
 }
 
