@@ -58,11 +58,11 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=24,
                     help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch512", "serving", "partition", "unit_rates", "stack"],
+                    choices=["headline", "batch512", "serving", "partition", "unit_rates", "stack", "sphere"],
                     help="headline: the three-layer bus (and the 2x2 bus as secondary); "
                          "batch512 / serving: the batched and served forms; unit_rates: the "
                          "arithmetic-unit rates that bound the assembly, nothing else; stack: the "
-                         "multi-dielectric system of a layered stack")
+                         "multi-dielectric system of a layered stack; sphere: flat triangles")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=1000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -901,6 +901,176 @@ def run_stack(args):
     dist_stop(world)
 
 
+# FP64 cost of the triangle entries in DFMA equivalents at the measured
+# library rates: a potential evaluation is three edges of 2 logs, 2 atans,
+# 2 square roots and about 40 arithmetic operations; a far-rule evaluation
+# about 14 operations with its reciprocal square root
+def tri_work(counts, rates):
+    eq = term_dfma(rates)[2]
+    pot = 3 * (2 * eq["dlog"] + 2 * eq["datan"] + 2 * eq["dsqrt"] + 40)
+    work = counts[1] * 39 * 39 * pot + counts[2] * 256 * pot + sum(counts[k] * k ** 4 * 14 for k in range(3, 7))
+    return work
+
+
+def run_sphere(args):
+    """Flat triangles (general conductors): the capacitance of a sphere of
+    radius 1 um from a level-4 icosphere (5120 triangles), per step the
+    assembly (FP64 entries, stored for the mixed factor), the FP32 factor with
+    refinement and the charge; against 4 pi eps0 R and the FP64 run."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_start(world)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem, workloads as W
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    gbem.load()
+    ctx = gbem.Context(local)
+    stream = torch.cuda.Stream()
+    rates = ctx.unit_rates(stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tris = W.icosphere(1.0, 4)
+    cond = np.zeros(len(tris), np.int32)
+    n = len(tris)
+    pairs = n * (n + 1) / 2
+    c_exact = 4 * math.pi * 8.8541878128e-12 * 1e-6
+    mesh = ctx.mesh_from_triangles(tris, cond)
+
+    def step(prec):
+        mat = mesh.assemble(prec, stream)
+        try:
+            return gbem.gbem_capacitance(mesh, mat, 1.0, stream)
+        finally:
+            mat.close()
+
+    def timed(fn, k):
+        total = 0.0
+        out = None
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return max_over_ranks(total, world), out
+
+    for _ in range(args.warmup):
+        step(gbem.GBEM_MIXED)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = gbem.get_stats(ctx)["launches"]
+    clocks.begin()
+    ms, (C, resid) = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
+    clocks.end()
+    clk = clocks.stop()
+    launches = (gbem.get_stats(ctx)["launches"] - l0) // args.steps
+    gbem.set_timing(ctx, 2)
+    gbem.get_kernel_stats(ctx, reset=True)
+    ms_traced, _ = timed(lambda: step(gbem.GBEM_MIXED), args.steps)
+    kst = gbem.get_kernel_stats(ctx, reset=True)
+    gbem.set_timing(ctx, 0)
+    mat = mesh.assemble(gbem.GBEM_MIXED, stream)
+    counts = mat.class_counts()
+    mat.close()
+    k64 = max(1, min(args.steps, 2))
+    ms64, (C64, _) = timed(lambda: step(gbem.GBEM_FP64), k64)
+
+    def e2e():
+        m = ctx.mesh_from_triangles(tris, cond)
+        try:
+            mat = m.assemble(gbem.GBEM_MIXED, stream)
+            try:
+                return gbem.gbem_capacitance(m, mat, 1.0, stream)
+            finally:
+                mat.close()
+        finally:
+            m.close()
+
+    e2e()
+    ms_e2e, _ = timed(e2e, args.steps)
+    ms_step = ms / args.steps
+    work = tri_work([int(x) for x in counts[:7]], rates)
+    kern = {}
+    for k, d in kst.items():
+        if d["launches"] == 0:
+            continue
+        t = d["ms"] / d["launches"] * 1e-3
+        e = {"ms_per_step": d["ms"] / args.steps, "launches_per_step": d["launches"] / args.steps}
+        if k == "assemble":
+            e.update({"bound": "alu", "unit": "DFMA-eq/s", "achieved": work / t, "peak": rates["dfma"],
+                      "peak_source": "DFMA rate measured on this GPU (gbem_unit_rates)", "work_per_launch": work,
+                      "work": "FP64 closed-form and quadrature work of the pair classes, in DFMA equivalents"})
+        elif k == "factor":
+            np_ = (n + 127) // 128 * 128
+            e.update({"bound": "tensor", "unit": "TFLOP/s", "achieved": np_ ** 3 / 3.0 / t / 1e12,
+                      "peak": _peaks()["bf16_tflops"] / 3.0,
+                      "peak_source": "dense bf16/fp16 / 3 (3xFP16 products per useful flop), " + _peaks()["source"],
+                      "work_per_launch": np_ ** 3 / 3.0, "work": "N^3/3 useful flop per factorisation"})
+        else:
+            e.update({"bound": "hbm", "unit": "GB/s", "achieved": d["bytes"] / d["launches"] / t / 1e9,
+                      "peak": _peaks()["hbm_gbs"], "peak_source": _peaks()["source"],
+                      "work_per_launch": d["bytes"] / d["launches"]})
+        e["frac"] = e["achieved"] / e["peak"]
+        kern[k] = e
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = {"kernel": dom, "share_of_traced_step": kern[dom]["ms_per_step"] / (ms_traced / args.steps),
+            "traffic": None}
+    for key in ("bound", "achieved", "peak", "unit", "frac", "peak_source", "work_per_launch", "work"):
+        if key in kern[dom]:
+            roof[key] = kern[dom][key]
+    if rank == 0:
+        line = {
+            "metric": "extractions/s", "value": whole_job_rate(args.steps, world, ms * 1e-3),
+            "unit": "extractions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 entries, f32+f64 (mixed) solve", "data": "synthetic",
+            "config": {"workload": "sphere of radius 1 um, level-4 icosphere", "n_panels": n,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+            "pairs_per_s": whole_job_rate(pairs * args.steps, world, ms * 1e-3),
+            "c_over_4pi_eps_r": float(C[0, 0] / c_exact), "residual": resid,
+            "fp64": {"ms_per_step": ms64 / k64, "mixed_vs_fp64_rel": float(abs(C[0, 0] / C64[0, 0] - 1.0))},
+            "class_counts": [int(x) for x in counts[:7]],
+            "e2e": {"value": whole_job_rate(args.steps, world, ms_e2e * 1e-3), "unit": "extractions/s",
+                    "ms_per_step": ms_e2e / args.steps, "h2d_bytes_per_step": n * (72 + 4),
+                    "d2h_bytes_per_step": 8 + 8},
+            "gpu_launches": int(launches), "roofline": roof, "kernels": kern, "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            from oracle import oracle as O
+            from oracle import triangles as T
+            rng = np.random.default_rng(9)
+            rows = rng.integers(0, n, 8)
+            I, J = np.repeat(rows, n), np.tile(np.arange(n), len(rows))
+            t0 = time.perf_counter()
+            T.tri_entries(tris, I, J)
+            r_all = len(I) / (time.perf_counter() - t0)
+            import scipy.linalg as sla
+            A = np.eye(n) * n + np.random.default_rng(1).standard_normal((n, n)) * 0.01
+            A = 0.5 * (A + A.T)
+            t0 = time.perf_counter()
+            sla.cho_factor(A)
+            t_chol = time.perf_counter() - t0
+            t_ext = pairs / r_all + t_chol
+            line["cpu_baseline"] = {"value": 1.0 / t_ext, "unit": "extractions/s", "cores": O.max_threads(),
+                                    "kind": "oracle",
+                                    "sample": f"8 whole random rows ({len(I)} triangle pairs) on {O.max_threads()} "
+                                              f"threads, plus LAPACK dpotrf at order {n} ({t_chol:.2f} s); one "
+                                              f"extraction estimated at {t_ext:.0f} s"}
+        print(json.dumps(line))
+    mesh.close()
+    ctx.close()
+    dist_stop(world)
+
+
 def run_batch(args):
     """512 independent 2-6 bar structures (N log-uniform in [200, 3000]):
     the autotuned batch (groups of structures whose graphs run concurrently,
@@ -1302,6 +1472,8 @@ def main():
         run_unit_rates()
     elif args.workload == "stack":
         run_stack(args)
+    elif args.workload == "sphere":
+        run_sphere(args)
     else:
         run_ours(args)
 

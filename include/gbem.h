@@ -197,6 +197,25 @@ gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis,
                                   const double* geo, const int32_t* cond,
                                   gbem_mesh_t** out);
 
+/* A mesh of n flat triangles (general, non-Manhattan conductors; the paper's
+ * Galerkin formulation, Sec. 3.1 and Eq. "matrix", with triangles for
+ * panels): tri holds 9 doubles per triangle, its three vertices (um);
+ * cond[i] the conductor id.  Triangles of one conductor that touch must
+ * share whole edges or vertices with identical coordinates.  Entries are
+ * evaluated in FP64 in both precisions: the self-integral in closed form,
+ * touching pairs by the exact potential of one triangle under a tanh-sinh
+ * rule over the other, the rest by Gauss-Legendre rules (about 1e-10
+ * relative); GBEM_MIXED stores them as for rectangles and factors in FP32
+ * with refinement.  Such a mesh works with gbem_assemble, gbem_factor,
+ * gbem_solve and gbem_capacitance; refinement, batches and
+ * gbem_mesh_panels' rectangle arrays return GBEM_ERR_STATE.  GBEM_ERR_MESH
+ * for non-finite coordinates or zero area. */
+gbem_status gbem_mesh_from_triangles(gbem_ctx* ctx, int n, const double* tri, const int32_t* cond,
+                                     gbem_mesh_t** out);
+/* The triangles of a triangle mesh (9 doubles each) and their conductor ids;
+ * GBEM_ERR_STATE for a rectangle mesh. */
+gbem_status gbem_mesh_triangles(const gbem_mesh_t* mesh, double* tri, int32_t* cond);
+
 /* Panel count and conductor count of a mesh. */
 gbem_status gbem_mesh_info(const gbem_mesh_t* mesh, int* n_panels, int* n_cond);
 
@@ -459,7 +478,9 @@ gbem_status gbem_matrix_info(gbem_matrix_t* mat, int* n, long long* counts);
  * (closed-form corner sums in FP64, Sec. 3.4, Eqs. "parallel" and
  * "orthogonal"), counts[2n] and counts[2n + 1] the parallel and
  * perpendicular far pairs of Gauss-Legendre order n = 1..6 (n^4 evaluations
- * of 1/r each).  Waits for the assembly stream. */
+ * of 1/r each).  For a triangle mesh: counts[0] self pairs, [1] pairs
+ * sharing a vertex, [2] near pairs, [3..6] far pairs of product-rule order
+ * 3..6, the rest 0.  Waits for the assembly stream. */
 gbem_status gbem_matrix_class_counts(gbem_matrix_t* mat, long long* counts);
 /* Waits for the matrix's last stream, then hands its device buffers to the
  * context, which offers them to the next matrix of the same size (see

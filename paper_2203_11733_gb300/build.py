@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgbem.so")
 
 SOURCES = ["api.cpp", "mesh.cpp", "batch.cpp", "server.cpp", "assemble.cu", "factor.cu", "solve.cu", "solve_noalloc.cu",
-           "unit_rates.cu", "stack.cpp", "dielectric.cu"]
+           "unit_rates.cu", "stack.cpp", "dielectric.cu", "triangles.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", INCLUDE, "-I", CSRC]

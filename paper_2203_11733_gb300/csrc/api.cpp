@@ -563,6 +563,7 @@ gbem_status gbem_mesh_refine(const gbem_mesh_t* mesh, const double* density, dou
     *out = nullptr;
     gbem_ctx* ctx = mesh->ctx;
     if (!(theta >= 0.0 && theta <= 1.0)) return ctx_fail(ctx, GBEM_ERR_ARG, "theta outside [0, 1]");
+    if (!mesh->tri.empty()) return ctx_fail(ctx, GBEM_ERR_STATE, "refinement takes rectangle meshes");
     for (int i = 0; i < mesh->n; ++i)
         if (!std::isfinite(density[i])) return ctx_fail(ctx, GBEM_ERR_ARG, "density not finite");
     std::vector<int8_t> a;
@@ -623,6 +624,75 @@ gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis, cons
     return GBEM_OK;
 }
 
+// Device copy of a triangle mesh: the vertices (9 doubles a panel) and the
+// conductor indices.
+static gbem_status upload_triangles(gbem_ctx* ctx, gbem_mesh_t* m)
+{
+    if (ctx->device < 0) return GBEM_OK;
+    DeviceGuard g(ctx->device);
+    const size_t n = (size_t)m->n;
+    const size_t off_cond = round_up(9 * n * sizeof(double), 256);
+    const size_t bytes = off_cond + round_up(n * sizeof(int32_t), 256);
+    void* buf = ctx_alloc(ctx, bytes, nullptr);
+    if (!buf) return GBEM_ERR_OOM;
+    m->dbuf = buf;
+    m->dbytes = bytes;
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data(), m->tri.data(), 9 * n * sizeof(double));
+    std::memcpy(host.data() + off_cond, m->cond.data(), n * sizeof(int32_t));
+    if (!cuda_ok(ctx, cudaMemcpy(buf, host.data(), bytes, cudaMemcpyHostToDevice), "mesh upload"))
+        return GBEM_ERR_CUDA;
+    m->dev = DevPanels{};
+    m->dev.tri = static_cast<const double*>(buf);
+    m->dev.cond = reinterpret_cast<const int32_t*>(static_cast<unsigned char*>(buf) + off_cond);
+    m->dev.n = m->n;
+    return GBEM_OK;
+}
+
+gbem_status gbem_mesh_from_triangles(gbem_ctx* ctx, int n, const double* tri, const int32_t* cond, gbem_mesh_t** out)
+{
+    if (!ctx || !out) return GBEM_ERR_ARG;
+    *out = nullptr;
+    if (n <= 0 || !tri || !cond) return ctx_fail(ctx, GBEM_ERR_ARG, "empty triangle list");
+    if (n > 2000000) return ctx_fail(ctx, GBEM_ERR_ARG, "more than 2e6 triangles");
+    for (int i = 0; i < n; ++i) {
+        const double* t = tri + 9 * (size_t)i;
+        for (int e = 0; e < 9; ++e)
+            if (!std::isfinite(t[e])) return ctx_fail(ctx, GBEM_ERR_MESH, "triangle coordinate not finite");
+        const double e1[3] = {t[3] - t[0], t[4] - t[1], t[5] - t[2]}, e2[3] = {t[6] - t[0], t[7] - t[1], t[8] - t[2]};
+        const double c0 = e1[1] * e2[2] - e1[2] * e2[1], c1 = e1[2] * e2[0] - e1[0] * e2[2],
+                     c2 = e1[0] * e2[1] - e1[1] * e2[0];
+        const double l2 = std::max({e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]});
+        if (!(c0 * c0 + c1 * c1 + c2 * c2 > 1e-24 * l2 * l2))
+            return ctx_fail(ctx, GBEM_ERR_MESH, "triangle " + std::to_string(i) + " has zero area");
+    }
+    gbem_mesh_t* m = new (std::nothrow) gbem_mesh_t();
+    if (!m) return GBEM_ERR_OOM;
+    m->ctx = ctx;
+    m->n = n;
+    m->tri.assign(tri, tri + 9 * (size_t)n);
+    std::vector<int32_t> raw(cond, cond + n);
+    compact_conductors(m, raw);
+    gbem_status st = upload_triangles(ctx, m);
+    if (st != GBEM_OK) {
+        if (m->dbuf) ctx_free(ctx, m->dbuf, m->dbytes, nullptr);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GBEM_OK;
+}
+
+gbem_status gbem_mesh_triangles(const gbem_mesh_t* mesh, double* tri, int32_t* cond)
+{
+    if (!mesh) return GBEM_ERR_ARG;
+    if (mesh->tri.empty()) return GBEM_ERR_STATE;
+    if (tri) std::memcpy(tri, mesh->tri.data(), sizeof(double) * 9 * mesh->n);
+    if (cond)
+        for (int i = 0; i < mesh->n; ++i) cond[i] = mesh->cond_ids[mesh->cond[i]];
+    return GBEM_OK;
+}
+
 gbem_status gbem_mesh_info(const gbem_mesh_t* mesh, int* n_panels, int* n_cond)
 {
     if (!mesh) return GBEM_ERR_ARG;
@@ -635,6 +705,7 @@ gbem_status gbem_mesh_panels(const gbem_mesh_t* mesh, int8_t* axis, double* geo,
                              int32_t* cond_ids)
 {
     if (!mesh) return GBEM_ERR_ARG;
+    if (!mesh->tri.empty() && (axis || geo)) return GBEM_ERR_STATE;   // a triangle mesh has no rectangles
     if (axis) std::memcpy(axis, mesh->axis.data(), mesh->n);
     if (geo) std::memcpy(geo, mesh->geo.data(), sizeof(double) * 5 * mesh->n);
     if (cond)
@@ -687,7 +758,10 @@ gbem_status gbem_assemble(gbem_mesh_t* mesh, gbem_precision prec, gbem_stream st
     const bool ok = cuda_ok(ctx, cudaMemsetAsync(m->dflags, 0, 4 * sizeof(int), s), "memset") &&
                     cuda_ok(ctx, cudaMemsetAsync(m->dcounts, 0, 16 * sizeof(unsigned long long), s), "memset") &&
                     cuda_ok(ctx, launch_pad(m->A64, m->A32, m->n, m->np, s), "pad") &&
-                    cuda_ok(ctx, launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s),
+                    cuda_ok(ctx,
+                            mesh->tri.empty()
+                                ? launch_assemble(mesh->dev, m->np, prec, qn, m->A64, m->A32, m->dcounts, s)
+                                : launch_assemble_tri(mesh->dev.tri, m->n, m->np, prec, m->A64, m->A32, m->dcounts, s),
                             "assemble");
     if (!ok) {
         gbem_matrix_destroy(m);

@@ -53,6 +53,7 @@ static gbem_status part_create(gbem_ctx* ctx, int count, gbem_mesh_t* const* mes
     for (int b = 0; b < count; ++b) {
         if (!meshes[b] || meshes[b]->ctx != ctx) return ctx_fail(ctx, GBEM_ERR_ARG, "mesh from another context");
         if (meshes[b]->n_cond > 16) return ctx_fail(ctx, GBEM_ERR_ARG, "batched structures have at most 16 conductors");
+        if (!meshes[b]->tri.empty()) return ctx_fail(ctx, GBEM_ERR_STATE, "batches take rectangle meshes");
     }
     int prev = -1;
     cudaGetDevice(&prev);

@@ -98,6 +98,7 @@ struct DevPanels {
     const double* lo1 = nullptr;  // extents on the second in-plane axis
     const double* hi1 = nullptr;
     const int8_t* axis = nullptr; // normal axis
+    const double* tri = nullptr;  // triangle meshes: 9 per panel (vertices), else null
     const int32_t* cond = nullptr;// conductor index 0..n_c-1
     int n = 0;
 };
@@ -150,6 +151,7 @@ struct gbem_mesh_s {
     std::vector<double> geo;        // 5 per panel
     std::vector<int32_t> cond;      // conductor index (0..n_c-1)
     std::vector<int32_t> cond_ids;  // conductor index -> caller's id
+    std::vector<double> tri;        // flat triangles: 9 per panel (empty for rectangles)
     void* dbuf = nullptr;
     size_t dbytes = 0;
     DevPanels dev;
@@ -224,6 +226,12 @@ void gl_nodes(int n, double* x, double* w);
 cudaError_t launch_assemble(const DevPanels& g, int np, gbem_precision prec, double q_near,
                             double* A64, float* A32, unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_pad(double* A64, float* A32, int n, int np, cudaStream_t s);
+// Every lower entry of a mesh of flat triangles (tri: 9 per panel), FP64,
+// stored as for rectangles (float pairs and the FP32 copy in mixed mode);
+// counts (zeroed) receives the pairs of each class: self, touching, near,
+// far of order 3..6.
+cudaError_t launch_assemble_tri(const double* tri, int n, int np, gbem_precision prec, double* A64, float* A32,
+                                unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_assemble_batched(const BatchView& v, long long tiles, gbem_precision prec, double q_near,
                                     cudaStream_t s);
 cudaError_t launch_cholesky_batched(const BatchView& v, int nsteps, const long long* steps_dev,

@@ -100,6 +100,8 @@ _SIGS = {
     "gbem_mesh_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "gbem_mesh_panels": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gbem_mesh_refine": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    "gbem_mesh_from_triangles": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "gbem_mesh_triangles": (ctypes.c_int, [_P, _P, _P]),
     "gbem_stack_mesh": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "gbem_stack_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "gbem_stack_panels": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -295,6 +297,16 @@ class Context:
     def mesh_from_panels(self, axis, geo, cond) -> "Mesh":
         return gbem_mesh_from_panels(self, axis, geo, cond)
 
+    def mesh_from_triangles(self, tri, cond) -> "Mesh":
+        """gbem_mesh_from_triangles: tri float64[n, 9] (vertices), cond int32[n]."""
+        t = np.ascontiguousarray(tri, dtype=np.float64).reshape(-1, 9)
+        c = np.ascontiguousarray(cond, dtype=np.int32)
+        if len(c) != len(t):
+            raise ValueError("one conductor id per triangle")
+        out = _P()
+        self.check(self.lib.gbem_mesh_from_triangles(self.h, len(t), _ptr(t), _ptr(c), ctypes.byref(out)))
+        return Mesh(self, out)
+
     def close(self):
         """Destroy the context; matrices and meshes made from it go first."""
         if getattr(self, "h", None):
@@ -333,6 +345,13 @@ class Mesh:
 
     def assemble(self, precision=GBEM_FP64, stream=None) -> "Matrix":
         return gbem_assemble(self, precision, stream)
+
+    def triangles(self):
+        """(tri float64[n, 9], conductor ids int32[n]) of a triangle mesh."""
+        t = np.empty((self.n, 9), np.float64)
+        c = np.empty(self.n, np.int32)
+        self.ctx.check(self.ctx.lib.gbem_mesh_triangles(self.h, _ptr(t), _ptr(c)))
+        return t, c
 
     def close(self):
         if getattr(self, "h", None):
