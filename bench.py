@@ -903,13 +903,16 @@ def run_stack(args):
 
 # FP64 cost of the triangle entries in DFMA equivalents at the measured
 # library rates: a potential evaluation is three edges of 2 logs, 2 atans,
-# 2 square roots and about 40 arithmetic operations; a far-rule evaluation
-# about 14 operations with its reciprocal square root
-def tri_work(counts, rates):
+# 2 square roots and about 40 arithmetic operations.  Mixed mode: 25 x 25
+# tanh-sinh nodes per touching pair, 36 per near pair, the far rules in FP32
+# (not counted); FP64: 39 x 39, 256, and about 14 operations per far-rule
+# evaluation.
+def tri_work(counts, rates, mixed=True):
     eq = term_dfma(rates)[2]
     pot = 3 * (2 * eq["dlog"] + 2 * eq["datan"] + 2 * eq["dsqrt"] + 40)
-    work = counts[1] * 39 * 39 * pot + counts[2] * 256 * pot + sum(counts[k] * k ** 4 * 14 for k in range(3, 7))
-    return work
+    if mixed:
+        return counts[1] * 25 * 25 * pot + counts[2] * 36 * pot
+    return counts[1] * 39 * 39 * pot + counts[2] * 256 * pot + sum(counts[k] * k ** 4 * 14 for k in range(3, 7))
 
 
 def run_sphere(args):
@@ -1008,7 +1011,8 @@ def run_sphere(args):
         if k == "assemble":
             e.update({"bound": "alu", "unit": "DFMA-eq/s", "achieved": work / t, "peak": rates["dfma"],
                       "peak_source": "DFMA rate measured on this GPU (gbem_unit_rates)", "work_per_launch": work,
-                      "work": "FP64 closed-form and quadrature work of the pair classes, in DFMA equivalents"})
+                      "work": "FP64 work of the touching and near pairs (exact potentials under tanh-sinh and "
+                              "Gauss-Legendre rules) in DFMA equivalents; the FP32 far rules are not counted"})
         elif k == "factor":
             np_ = (n + 127) // 128 * 128
             e.update({"bound": "tensor", "unit": "TFLOP/s", "achieved": np_ ** 3 / 3.0 / t / 1e12,
@@ -1032,7 +1036,8 @@ def run_sphere(args):
             "metric": "extractions/s", "value": whole_job_rate(args.steps, world, ms * 1e-3),
             "unit": "extractions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 entries, f32+f64 (mixed) solve", "data": "synthetic",
+            "dtype": "f32+f64 (mixed): FP32 far rules, FP64 near entries, FP32 factor refined in FP64",
+            "data": "synthetic",
             "config": {"workload": "sphere of radius 1 um, level-4 icosphere", "n_panels": n,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
             "pairs_per_s": whole_job_rate(pairs * args.steps, world, ms * 1e-3),

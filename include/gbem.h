@@ -201,12 +201,13 @@ gbem_status gbem_mesh_from_panels(gbem_ctx* ctx, int n, const int8_t* axis,
  * Galerkin formulation, Sec. 3.1 and Eq. "matrix", with triangles for
  * panels): tri holds 9 doubles per triangle, its three vertices (um);
  * cond[i] the conductor id.  Triangles of one conductor that touch must
- * share whole edges or vertices with identical coordinates.  Entries are
- * evaluated in FP64 in both precisions: the self-integral in closed form,
- * touching pairs by the exact potential of one triangle under a tanh-sinh
- * rule over the other, the rest by Gauss-Legendre rules (about 1e-10
- * relative); GBEM_MIXED stores them as for rectangles and factors in FP32
- * with refinement.  Such a mesh works with gbem_assemble, gbem_factor,
+ * share whole edges or vertices with identical coordinates.  Entries: the
+ * self-integral in closed form, touching pairs by the exact potential of one
+ * triangle under a tanh-sinh rule over the other, near pairs by the exact
+ * potential under Gauss-Legendre, far pairs by Gauss-Legendre product rules
+ * (FP64, about 1e-10 relative; in GBEM_MIXED the far rules run in FP32,
+ * about 1e-7, stored as for rectangles and factored in FP32 with
+ * refinement).  Such a mesh works with gbem_assemble, gbem_factor,
  * gbem_solve and gbem_capacitance; refinement, batches and
  * gbem_mesh_panels' rectangle arrays return GBEM_ERR_STATE.  GBEM_ERR_MESH
  * for non-finite coordinates or zero area. */

@@ -12,13 +12,15 @@
 //  * triangles sharing a vertex or a side: the exact potential of one
 //    triangle (edge-by-edge closed form) integrated over the other with a
 //    tanh-sinh rule in both coordinates of its collapsed map (39 x 39
-//    points), whose sides all lie on the unit square's boundary, where the
-//    rule converges fast despite the potential's singular derivatives there;
+//    points; 25 x 25 in mixed mode), whose sides all lie on the unit
+//    square's boundary, where the rule converges fast despite the
+//    potential's singular derivatives there;
 //  * centroid distance below 3 diameters: the exact potential over the four
 //    midpoint children of the other triangle, collapsed Gauss-Legendre of
-//    order 8 on each;
+//    order 8 on each (one order-6 rule in mixed mode);
 //  * farther: the collapsed Gauss-Legendre product rule of order 3..6 on
-//    both triangles (calibrated to about 1e-11 relative).
+//    both triangles (calibrated to about 1e-11 relative), in FP32 with FP64
+//    outer sums in mixed mode (about 1e-7).
 // The mixed precision stores each entry as a float pair and its FP32 copy,
 // as the rectangle assembly does.
 #include <cmath>
@@ -34,9 +36,9 @@ constexpr int kMaxGl = 8;
 constexpr int kTsMax = 40;
 __constant__ double c_tgx[kMaxGl + 1][kMaxGl];   // Gauss-Legendre nodes on [0, 1]
 __constant__ double c_tgw[kMaxGl + 1][kMaxGl];
-__constant__ double c_tsx[kTsMax];                // tanh-sinh nodes on [0, 1]
-__constant__ double c_tsw[kTsMax];
-__constant__ int c_tsn;
+__constant__ double c_tsx[2][kTsMax];             // tanh-sinh nodes on [0, 1]: step 1/6, 1/4
+__constant__ double c_tsw[2][kTsMax];
+__constant__ int c_tsn[2];
 
 struct Tri {
     double v[3][3];
@@ -141,24 +143,25 @@ __device__ double tri_self(const Tri& T, double area)
 }
 
 // int over triangle (a, b, c) of the potential of F, by the collapsed map
-// y = a + xi ((b - a) + eta (c - b)) with Gauss-Legendre of order m (ts =
-// false) or the tanh-sinh rule (ts = true) in both coordinates.
-__device__ double outer_rule(const double* a, const double* b, const double* c, const TriFrame& F, int m, bool ts)
+// y = a + xi ((b - a) + eta (c - b)) with Gauss-Legendre of order m (ts < 0)
+// or tanh-sinh rule ts (0: step 1/6, 1: step 1/4) in both coordinates.
+__device__ double outer_rule(const double* a, const double* b, const double* c, const TriFrame& F, int m, int ts)
 {
     double ab[3], bc[3], cr[3];
     sub3(b, a, ab);
     sub3(c, b, bc);
     cross3(ab, bc, cr);
     const double j2 = sqrt(dot3(cr, cr));
-    const int n = ts ? c_tsn : m;
+    const bool t = ts >= 0;
+    const int n = t ? c_tsn[ts] : m;
     double s = 0.0;
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
-        const double xi = ts ? c_tsx[i] : c_tgx[m][i], wx = ts ? c_tsw[i] : c_tgw[m][i];
+        const double xi = t ? c_tsx[ts][i] : c_tgx[m][i], wx = t ? c_tsw[ts][i] : c_tgw[m][i];
         double row = 0.0;
 #pragma unroll 1
         for (int k = 0; k < n; ++k) {
-            const double eta = ts ? c_tsx[k] : c_tgx[m][k], we = ts ? c_tsw[k] : c_tgw[m][k];
+            const double eta = t ? c_tsx[ts][k] : c_tgx[m][k], we = t ? c_tsw[ts][k] : c_tgw[m][k];
             double y[3];
             for (int d = 0; d < 3; ++d) y[d] = a[d] + xi * (ab[d] + eta * bc[d]);
             row += we * tri_potential(F, y);
@@ -166,6 +169,59 @@ __device__ double outer_rule(const double* a, const double* b, const double* c, 
         s += wx * xi * row;
     }
     return s * j2;
+}
+
+__device__ __forceinline__ float mufu_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The same product rule in FP32 (mixed mode): node offsets from the FP64
+// vertex difference, FP32 inner sums, FP64 outer sum; about 1e-7 relative.
+__device__ double far_rule_f32(const Tri& A, const Tri& B, int n)
+{
+    float ab1[3], bc1[3], ab2[3], bc2[3], d0[3];
+    double cr[3], e1[3], e2[3];
+    for (int d = 0; d < 3; ++d) {
+        ab1[d] = (float)(A.v[1][d] - A.v[0][d]);
+        bc1[d] = (float)(A.v[2][d] - A.v[1][d]);
+        ab2[d] = (float)(B.v[1][d] - B.v[0][d]);
+        bc2[d] = (float)(B.v[2][d] - B.v[1][d]);
+        d0[d] = (float)(A.v[0][d] - B.v[0][d]);
+    }
+    sub3(A.v[1], A.v[0], e1);
+    sub3(A.v[2], A.v[1], e2);
+    cross3(e1, e2, cr);
+    const double j1 = sqrt(dot3(cr, cr));
+    sub3(B.v[1], B.v[0], e1);
+    sub3(B.v[2], B.v[1], e2);
+    cross3(e1, e2, cr);
+    const double j2 = sqrt(dot3(cr, cr));
+    double s = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i)
+#pragma unroll 1
+        for (int k = 0; k < n; ++k) {
+            const float xi = (float)c_tgx[n][i], xk = (float)c_tgx[n][k];
+            float x[3];
+            for (int d = 0; d < 3; ++d) x[d] = d0[d] + xi * (ab1[d] + xk * bc1[d]);
+            float t = 0.0f;
+#pragma unroll 1
+            for (int p = 0; p < n; ++p) {
+                const float xp = (float)c_tgx[n][p], wp = (float)(c_tgw[n][p] * c_tgx[n][p]);
+#pragma unroll 1
+                for (int q = 0; q < n; ++q) {
+                    const float xq = (float)c_tgx[n][q];
+                    float r[3];
+                    for (int d = 0; d < 3; ++d) r[d] = x[d] - xp * (ab2[d] + xq * bc2[d]);
+                    t = fmaf(wp * (float)c_tgw[n][q], mufu_rsqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), t);
+                }
+            }
+            s += c_tgw[n][i] * c_tgw[n][k] * c_tgx[n][i] * (double)t;
+        }
+    return s * j1 * j2;
 }
 
 // Collapsed Gauss-Legendre product rule of order n on both triangles.
@@ -235,24 +291,28 @@ __device__ int tri_class(const Tri& A, const Tri& B, bool same)
     return r >= 40.0 ? 3 : r >= 10.0 ? 4 : r >= 4.0 ? 5 : 6;
 }
 
+template <bool MIXED>
 __device__ double tri_pair(const Tri& A, const Tri& B, int cls, double aa, double ab)
 {
     if (cls == 0) return tri_self(A, aa);
-    if (cls >= 3) return far_rule(A, B, cls);
+    if (cls >= 3) return MIXED ? far_rule_f32(A, B, cls) : far_rule(A, B, cls);
     // the smaller triangle carries the outer rule (the integral is symmetric)
     const Tri& O = aa <= ab ? A : B;
     const Tri& I = aa <= ab ? B : A;
     TriFrame F;
     tri_frame(I, F);
-    if (cls == 1) return outer_rule(O.v[0], O.v[1], O.v[2], F, 0, true);
+    // mixed mode: the coarser tanh-sinh rule (about 1e-10) and one order-6
+    // rule for near pairs (about 1e-8), both far below its FP32 far field
+    if (cls == 1) return outer_rule(O.v[0], O.v[1], O.v[2], F, 0, MIXED ? 1 : 0);
+    if (MIXED) return outer_rule(O.v[0], O.v[1], O.v[2], F, 6, -1);
     double m01[3], m12[3], m20[3];
     for (int d = 0; d < 3; ++d) {
         m01[d] = 0.5 * (O.v[0][d] + O.v[1][d]);
         m12[d] = 0.5 * (O.v[1][d] + O.v[2][d]);
         m20[d] = 0.5 * (O.v[2][d] + O.v[0][d]);
     }
-    return outer_rule(O.v[0], m01, m20, F, 8, false) + outer_rule(m01, O.v[1], m12, F, 8, false) +
-           outer_rule(m20, m12, O.v[2], F, 8, false) + outer_rule(m01, m12, m20, F, 8, false);
+    return outer_rule(O.v[0], m01, m20, F, 8, -1) + outer_rule(m01, O.v[1], m12, F, 8, -1) +
+           outer_rule(m20, m12, O.v[2], F, 8, -1) + outer_rule(m01, m12, m20, F, 8, -1);
 }
 
 template <bool MIXED>
@@ -306,7 +366,7 @@ __global__ void __launch_bounds__(256) assemble_tri(const double* __restrict__ t
         const int li = e & 31, lj = e >> 5;
         const int i = TI * kTriTile + li, j = TJ * kTriTile + lj;
         const double ai = sa[li], aj = sa[kTriTile + lj];
-        const double v = tri_pair(st[li], st[kTriTile + lj], cls_s[e], ai, aj) / (4.0 * kPi * ai * aj);
+        const double v = tri_pair<MIXED>(st[li], st[kTriTile + lj], cls_s[e], ai, aj) / (4.0 * kPi * ai * aj);
         const size_t at = (size_t)i + (size_t)j * np;
         if constexpr (MIXED) {
             const float h = __double2float_rn(v);
@@ -322,9 +382,9 @@ __global__ void __launch_bounds__(256) assemble_tri(const double* __restrict__ t
 
 cudaError_t tri_tables_upload(cudaStream_t s)
 {
-    static double gx[kMaxGl + 1][kMaxGl], gw[kMaxGl + 1][kMaxGl], tx[kTsMax], tw[kTsMax];
-    static int tn = 0;
-    if (tn == 0) {
+    static double gx[kMaxGl + 1][kMaxGl], gw[kMaxGl + 1][kMaxGl], tx[2][kTsMax], tw[2][kTsMax];
+    static int tn[2] = {0, 0};
+    if (tn[0] == 0) {
         for (int m = 2; m <= kMaxGl; ++m) {
             double x[kMaxGl], w[kMaxGl];
             gl_nodes(m, x, w);
@@ -333,23 +393,26 @@ cudaError_t tri_tables_upload(cudaStream_t s)
                 gw[m][i] = 0.5 * w[i];
             }
         }
-        // tanh-sinh on [0, 1], step 1/6, |t| <= 3.2: x = 1/(1 + exp(-pi sinh t)),
-        // each node formed from its nearer end
-        const double h = 1.0 / 6.0, hp = 0.5 * 3.14159265358979323846;
-        const int k = (int)(3.2 / h);
-        for (int i = -k; i <= k && tn < kTsMax; ++i) {
-            const double t = i * h, sh = hp * std::sinh(t), ch = std::cosh(sh);
-            const double d = 1.0 / (1.0 + std::exp(2.0 * std::fabs(sh)));
-            tx[tn] = i < 0 ? d : (i > 0 ? 1.0 - d : 0.5);
-            tw[tn] = h * 0.5 * hp * std::cosh(t) / (ch * ch);
-            ++tn;
+        // tanh-sinh on [0, 1], steps 1/6 and 1/4, |t| <= 3.2:
+        // x = 1/(1 + exp(-pi sinh t)), each node formed from its nearer end
+        const double hp = 0.5 * 3.14159265358979323846;
+        for (int r = 0; r < 2; ++r) {
+            const double h = r == 0 ? 1.0 / 6.0 : 0.25;
+            const int k = (int)(3.2 / h);
+            for (int i = -k; i <= k && tn[r] < kTsMax; ++i) {
+                const double t = i * h, sh = hp * std::sinh(t), ch = std::cosh(sh);
+                const double d = 1.0 / (1.0 + std::exp(2.0 * std::fabs(sh)));
+                tx[r][tn[r]] = i < 0 ? d : (i > 0 ? 1.0 - d : 0.5);
+                tw[r][tn[r]] = h * 0.5 * hp * std::cosh(t) / (ch * ch);
+                ++tn[r];
+            }
         }
     }
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tgx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tgw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tsx, tx, sizeof(tx), 0, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tsw, tw, sizeof(tw), 0, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tsn, &tn, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tsn, tn, sizeof(tn), 0, cudaMemcpyHostToDevice, s);
     return e;
 }
 

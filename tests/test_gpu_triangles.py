@@ -49,6 +49,8 @@ def test_entries_and_capacitance_match_oracle(ctx):
     assert np.abs(C - C_ref).max() <= 1e-9 * np.abs(C_ref).max()
     mat.close()
     mat = mesh.assemble(gbem.GBEM_MIXED)
+    Am = mat.download()   # float pairs hi + lo: FP64 closed forms near, FP32 far rules
+    assert np.all(np.abs(Am - A_ref) <= 1e-6 * scale)
     Cm, resid = gbem.gbem_capacitance(mesh, mat, 1.0)
     assert resid <= 1e-10
     assert np.abs(Cm - C_ref).max() <= 1e-6 * np.abs(C_ref).max()
