@@ -25,6 +25,10 @@ It implements, plainly and slowly, every step of the extraction:
 
 Units: lengths in micrometres, so A is in 1/um and X in um; the capacitance in
 farads is eps0 * eps_r * 1e-6 * X.
+
+Two sibling modules extend it: ``dielectric`` (several dielectrics, Sec. 4:
+double-layer entries, the per-layer system, LU) and ``triangles`` (flat
+triangle panels).
 """
 from __future__ import annotations
 
