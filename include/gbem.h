@@ -534,6 +534,16 @@ typedef struct {
     int32_t face_bc[6];
     double h;        /* largest cell edge on conductors */
     double h_outer;  /* largest cell edge on faces and interfaces (0: h) */
+    /* graded != 0: the paper's partition for the main net main_conductor
+     * instead of uniform cells (h and h_outer then cap the panel edges):
+     * conductor faces by the rule of Sec. 3.3 (as gbem_mesh_graded: |I| <= p4
+     * within p5 of the main net, p4 p3 (d/p5)^3 beyond, p4 = p1 on faces
+     * that look toward the main net and p1 p2 on the others), enclosure faces
+     * by the same rule with p4 = p1 (Sec. 4 keeps it for the outer boundary),
+     * interfaces by the rule of Sec. 4 (p4 p3 (d/p5)^2 beyond, p4 = p1). */
+    int32_t graded;
+    int32_t main_conductor;
+    double p1, p2, p3, p5;
 } gbem_stack;
 
 typedef struct gbem_stack_s gbem_stack_t;

@@ -123,17 +123,80 @@ def _cells(lo, hi, h):
     return O.divide(lo, hi, h)
 
 
-def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0):
+def _graded_cells(k, plane, a0, b0, a1, b1, p4, p3, p5, power, hmax, mains):
+    """Rectangles of one face under the paper's partition: bisect the longer
+    edge (the first on a tie), first half first, until |I| <= p4 within p5 of
+    the main net and |I| <= p4 p3 (d / p5)**power beyond, and both edges <= hmax
+    (d the distance to the nearest box of the main net)."""
+    out = []
+
+    def dist(c0, c1, c2, c3):
+        lo = [0.0] * 3
+        hi = [0.0] * 3
+        p, q = [x for x in range(3) if x != k]
+        lo[k] = hi[k] = plane
+        lo[p], hi[p], lo[q], hi[q] = c0, c1, c2, c3
+        best = math.inf
+        for blo, bhi in mains:
+            s2 = sum(max(0.0, blo[d] - hi[d], lo[d] - bhi[d]) ** 2 for d in range(3))
+            best = min(best, math.sqrt(s2))
+        return best
+
+    def split(c0, c1, c2, c3):
+        d = dist(c0, c1, c2, c3)
+        limit = p4 if d < p5 else p4 * p3 * (d / p5) ** power
+        e0, e1 = c1 - c0, c3 - c2
+        if not (e0 * e1 > limit or (hmax > 0.0 and max(e0, e1) > hmax)):
+            out.append((c0, c1, c2, c3))
+            return
+        if e0 >= e1:
+            m = 0.5 * (c0 + c1)
+            split(c0, m, c2, c3)
+            split(m, c1, c2, c3)
+        else:
+            m = 0.5 * (c2 + c3)
+            split(c0, c1, c2, m)
+            split(c0, c1, m, c3)
+
+    split(a0, b0, a1, b1)
+    return out
+
+
+def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0, graded=None):
     """Panels of a layered stack.  Conductor boxes (disjoint, each strictly
     inside one layer and the enclosure) are cut as mesh_boxes cuts them (edge
     cells ceil(L / h)); enclosure faces and interfaces with cells of at most
     h_outer (h when 0).  Returns a dict of arrays: axis, geo (c, lo0, hi0,
     lo1, hi1), kind, cond (conductor id, GROUND, NEUMANN or INTERFACE),
     region_a, region_b (-1 unless an interface: region_a the layer below),
-    sign (the outward normal of region_a is sign * e_axis)."""
+    sign (the outward normal of region_a is sign * e_axis).
+
+    graded = (main, p1, p2, p3, p5) meshes by the paper's partition for the
+    main net `main` instead: conductor faces by the rule of Sec. 3.3 (|I| <=
+    p4 near the main net, p4 p3 (d/p5)^3 beyond; p4 = p1 on faces that look
+    toward the main net, p1 p2 on those that look away), the enclosure's
+    faces by the same rule with p4 = p1, the interfaces by the rule of Sec. 4
+    (p4 p3 (d/p5)^2 beyond, p4 = p1); h and h_outer then cap the panel
+    edges."""
     h_out = h_outer if h_outer > 0.0 else h
     R = len(stack.eps)
     rows = []   # (axis, geo, kind, cond, ra, rb, sign)
+    if graded is not None:
+        main, p1, p2, p3, p5 = graded
+        mains = [([float(v) for v in lo], [float(v) for v in hi]) for lo, hi, c in boxes if int(c) == int(main)]
+        if not mains:
+            raise ValueError("no box of the main net")
+        mlo = [min(b[0][d] for b in mains) for d in range(3)]
+        mhi = [max(b[1][d] for b in mains) for d in range(3)]
+
+    def cells2(k, plane, a0, b0, a1, b1, hcap, rule, toward=True):
+        """The face's cells: a uniform grid, or the paper's partition."""
+        if graded is None:
+            cp, cq = _cells(a0, b0, hcap), _cells(a1, b1, hcap)
+            return [(cp[i], cp[i + 1], cq[j], cq[j + 1]) for i in range(len(cp) - 1) for j in range(len(cq) - 1)]
+        p4 = p1 if toward else p1 * p2
+        return _graded_cells(k, plane, a0, b0, a1, b1, p4, p3, p5, 3 if rule == "conductor" else 2, hcap, mains)
+
     for lo, hi, c in boxes:
         lo = [float(v) for v in lo]
         hi = [float(v) for v in hi]
@@ -146,12 +209,12 @@ def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0):
         a = layer[0]
         for k in range(3):
             p, q = [x for x in range(3) if x != k]
-            cp, cq = _cells(lo[p], hi[p], h), _cells(lo[q], hi[q], h)
-            for plane, sgn in ((lo[k], 1), (hi[k], -1)):
-                for i in range(len(cp) - 1):
-                    for j in range(len(cq) - 1):
-                        rows.append((k, (plane, cp[i], cp[i + 1], cq[j], cq[j + 1]), KIND_CONDUCTOR,
-                                     int(c), a, -1, sgn))
+            for plane, sgn, side in ((lo[k], 1, 0), (hi[k], -1, 1)):
+                toward = True
+                if graded is not None:
+                    toward = int(c) == int(main) or (mhi[k] > plane if side == 1 else mlo[k] < plane)
+                for g0, g1, g2, g3 in cells2(k, plane, lo[p], hi[p], lo[q], hi[q], h, "conductor", toward):
+                    rows.append((k, (plane, g0, g1, g2, g3), KIND_CONDUCTOR, int(c), a, -1, sgn))
     for k in range(3):
         p, q = [x for x in range(3) if x != k]
         for s in (0, 1):
@@ -160,25 +223,19 @@ def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0):
             bc = stack.face_bc[2 * k + s]
             if k == 2:
                 a = R - 1 if s else 0
-                cp, cq = _cells(stack.lo[p], stack.hi[p], h_out), _cells(stack.lo[q], stack.hi[q], h_out)
-                for i in range(len(cp) - 1):
-                    for j in range(len(cq) - 1):
-                        rows.append((k, (plane, cp[i], cp[i + 1], cq[j], cq[j + 1]), KIND_FACE, bc, a, -1, sgn))
+                for g0, g1, g2, g3 in cells2(k, plane, stack.lo[p], stack.hi[p], stack.lo[q], stack.hi[q], h_out,
+                                             "conductor"):
+                    rows.append((k, (plane, g0, g1, g2, g3), KIND_FACE, bc, a, -1, sgn))
             else:
                 # q == 2 for k in {0, 1}: the face is cut at every layer plane
-                cp = _cells(stack.lo[p], stack.hi[p], h_out)
                 for a in range(R):
-                    cq = _cells(stack.z[a], stack.z[a + 1], h_out)
-                    for i in range(len(cp) - 1):
-                        for j in range(len(cq) - 1):
-                            rows.append((k, (plane, cp[i], cp[i + 1], cq[j], cq[j + 1]), KIND_FACE, bc, a, -1,
-                                         sgn))
+                    for g0, g1, g2, g3 in cells2(k, plane, stack.lo[p], stack.hi[p], stack.z[a], stack.z[a + 1],
+                                                 h_out, "conductor"):
+                        rows.append((k, (plane, g0, g1, g2, g3), KIND_FACE, bc, a, -1, sgn))
     for a in range(1, R):
-        cp, cq = _cells(stack.lo[0], stack.hi[0], h_out), _cells(stack.lo[1], stack.hi[1], h_out)
-        for i in range(len(cp) - 1):
-            for j in range(len(cq) - 1):
-                rows.append((2, (stack.z[a], cp[i], cp[i + 1], cq[j], cq[j + 1]), KIND_INTERFACE, INTERFACE,
-                             a - 1, a, 1))
+        for g0, g1, g2, g3 in cells2(2, stack.z[a], stack.lo[0], stack.hi[0], stack.lo[1], stack.hi[1], h_out,
+                                     "interface"):
+            rows.append((2, (stack.z[a], g0, g1, g2, g3), KIND_INTERFACE, INTERFACE, a - 1, a, 1))
     return {
         "axis": np.array([r[0] for r in rows], dtype=np.int32),
         "geo": np.array([r[1] for r in rows], dtype=np.float64).reshape(-1, 5),

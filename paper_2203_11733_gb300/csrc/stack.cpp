@@ -61,6 +61,11 @@ void cells(double lo, double hi, double h, std::vector<double>& out)
 
 struct Mesher {
     gbem_stack_s* S;
+    // the paper's partition (graded): the main net's boxes and parameters
+    bool graded = false;
+    std::vector<gbem_box> mains;
+    double mlo[3] = {0, 0, 0}, mhi[3] = {0, 0, 0};
+    double p1 = 0, p2 = 0, p3 = 0, p5 = 0;
     void add(int k, double c, double a0, double b0, double a1, double b1, int kind, int cond, int ra, int rb,
              int sign)
     {
@@ -72,6 +77,69 @@ struct Mesher {
         S->ra.push_back(ra);
         S->rb.push_back(rb);
         S->sign.push_back((int8_t)sign);
+    }
+    double main_distance(int k, double c, double l0, double h0, double l1, double h1) const
+    {
+        const int pa = k == 0 ? 1 : 0, qa = k == 2 ? 1 : 2;
+        double lo[3], hi[3];
+        lo[k] = hi[k] = c;
+        lo[pa] = l0;
+        hi[pa] = h0;
+        lo[qa] = l1;
+        hi[qa] = h1;
+        double best = 1e300;
+        for (const gbem_box& B : mains) {
+            double d2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double g = std::max(0.0, std::max(B.lo[d] - hi[d], lo[d] - B.hi[d]));
+                d2 += g * g;
+            }
+            best = std::min(best, std::sqrt(d2));
+        }
+        return best;
+    }
+    // the paper's partition of one face: bisect the longer edge (the first
+    // on a tie), first half first, until |I| <= p4 within p5 of the main net
+    // and p4 p3 (d/p5)^power beyond, and both edges <= hcap
+    void graded_face(int k, double c, double a0, double b0, double a1, double b1, double hcap, double p4, int power,
+                     int kind, int cond, int ra, int rb, int sign)
+    {
+        struct Piece {
+            double l0, h0, l1, h1;
+        };
+        std::vector<Piece> st{Piece{a0, b0, a1, b1}};
+        while (!st.empty()) {
+            const Piece r = st.back();
+            st.pop_back();
+            const double d = main_distance(k, c, r.l0, r.h0, r.l1, r.h1);
+            double limit = p4;
+            if (d >= p5) {
+                const double t = d / p5;
+                limit = p4 * p3 * (power == 3 ? t * t * t : t * t);
+            }
+            const double e0 = r.h0 - r.l0, e1 = r.h1 - r.l1;
+            if (!(e0 * e1 > limit || (hcap > 0.0 && std::max(e0, e1) > hcap))) {
+                add(k, c, r.l0, r.h0, r.l1, r.h1, kind, cond, ra, rb, sign);
+                continue;
+            }
+            if (e0 >= e1) {
+                const double m = 0.5 * (r.l0 + r.h0);
+                st.push_back(Piece{m, r.h0, r.l1, r.h1});
+                st.push_back(Piece{r.l0, m, r.l1, r.h1});
+            } else {
+                const double m = 0.5 * (r.l1 + r.h1);
+                st.push_back(Piece{r.l0, r.h0, m, r.h1});
+                st.push_back(Piece{r.l0, r.h0, r.l1, m});
+            }
+        }
+    }
+    // the face's panels: the uniform grid, or the paper's partition (rule 3:
+    // conductors and the enclosure, 2: interfaces)
+    void face(int k, double c, double a0, double b0, double a1, double b1, double h, int power, bool toward, int kind,
+              int cond, int ra, int rb, int sign)
+    {
+        if (graded) graded_face(k, c, a0, b0, a1, b1, h, toward ? p1 : p1 * p2, power, kind, cond, ra, rb, sign);
+        else grid(k, c, a0, b0, a1, b1, h, kind, cond, ra, rb, sign);
     }
     // every cell of the tensor grid of [a0,b0] x [a1,b1]
     void grid(int k, double c, double a0, double b0, double a1, double b1, double h, int kind, int cond, int ra,
@@ -106,6 +174,29 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
     if (nbox < 0 || (nbox > 0 && !boxes)) return err = "boxes", GBEM_ERR_ARG;
     const double h_out = st->h_outer > 0.0 ? st->h_outer : st->h;
     Mesher m{S};
+    if (st->graded) {
+        if (!(st->p1 > 0.0) || !(st->p2 >= 1.0) || !(st->p3 > 0.0) || !(st->p5 > 0.0) || !std::isfinite(st->p1) ||
+            !std::isfinite(st->p2) || !std::isfinite(st->p3) || !std::isfinite(st->p5))
+            return err = "graded stacks need p1 > 0, p2 >= 1, p3 > 0, p5 > 0", GBEM_ERR_ARG;
+        m.graded = true;
+        m.p1 = st->p1;
+        m.p2 = st->p2;
+        m.p3 = st->p3;
+        m.p5 = st->p5;
+        for (int d = 0; d < 3; ++d) {
+            m.mlo[d] = 1e300;
+            m.mhi[d] = -1e300;
+        }
+        for (int b = 0; b < nbox; ++b)
+            if (boxes[b].conductor == st->main_conductor) {
+                m.mains.push_back(boxes[b]);
+                for (int d = 0; d < 3; ++d) {
+                    m.mlo[d] = std::min(m.mlo[d], boxes[b].lo[d]);
+                    m.mhi[d] = std::max(m.mhi[d], boxes[b].hi[d]);
+                }
+            }
+        if (m.mains.empty()) return err = "no box of the main conductor", GBEM_ERR_ARG;
+    }
     for (int b = 0; b < nbox; ++b) {
         const gbem_box& B = boxes[b];
         if (B.conductor < 0) return err = "conductor ids must be >= 0", GBEM_ERR_ARG;
@@ -126,9 +217,14 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
         }
         for (int k = 0; k < 3; ++k) {
             const int p = k == 0 ? 1 : 0, q = k == 2 ? 1 : 2;
-            // the region lies outside the box: its outward normal points into it
-            m.grid(k, B.lo[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 0, B.conductor, layer, -1, 1);
-            m.grid(k, B.hi[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 0, B.conductor, layer, -1, -1);
+            // the region lies outside the box: its outward normal points into
+            // it; a face looks toward the main net when some of the net lies
+            // beyond its plane on the conductor's outward side
+            const bool is_main = B.conductor == st->main_conductor;
+            m.face(k, B.lo[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 3, is_main || m.mlo[k] < B.lo[k], 0,
+                   B.conductor, layer, -1, 1);
+            m.face(k, B.hi[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 3, is_main || m.mhi[k] > B.hi[k], 0,
+                   B.conductor, layer, -1, -1);
         }
     }
     for (int k = 0; k < 3; ++k) {
@@ -137,16 +233,18 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
             const double plane = s ? st->hi[k] : st->lo[k];
             const int bc = st->face_bc[2 * k + s], sign = s ? 1 : -1;
             if (k == 2) {
-                m.grid(k, plane, st->lo[p], st->hi[p], st->lo[q], st->hi[q], h_out, 1, bc, s ? R - 1 : 0, -1, sign);
+                m.face(k, plane, st->lo[p], st->hi[p], st->lo[q], st->hi[q], h_out, 3, true, 1, bc, s ? R - 1 : 0, -1,
+                       sign);
             } else {
                 // q == 2: the face is cut at every layer plane
                 for (int a = 0; a < R; ++a)
-                    m.grid(k, plane, st->lo[p], st->hi[p], st->z[a], st->z[a + 1], h_out, 1, bc, a, -1, sign);
+                    m.face(k, plane, st->lo[p], st->hi[p], st->z[a], st->z[a + 1], h_out, 3, true, 1, bc, a, -1, sign);
             }
         }
     }
     for (int a = 1; a < R; ++a)
-        m.grid(2, st->z[a], st->lo[0], st->hi[0], st->lo[1], st->hi[1], h_out, 2, GBEM_PANEL_INTERFACE, a - 1, a, 1);
+        m.face(2, st->z[a], st->lo[0], st->hi[0], st->lo[1], st->hi[1], h_out, 2, true, 2, GBEM_PANEL_INTERFACE, a - 1, a,
+               1);
     S->eps.assign(st->eps_r, st->eps_r + R);
     S->R = R;
     S->n = (int)S->axis.size();

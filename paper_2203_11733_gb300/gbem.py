@@ -506,13 +506,18 @@ FACE_GROUND, FACE_NEUMANN, PANEL_INTERFACE = -1, -2, -3
 class _Stack(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("n_layers", ctypes.c_int32),
                 ("z", ctypes.c_double * (MAX_LAYERS + 1)), ("eps_r", ctypes.c_double * MAX_LAYERS),
-                ("face_bc", ctypes.c_int32 * 6), ("h", ctypes.c_double), ("h_outer", ctypes.c_double)]
+                ("face_bc", ctypes.c_int32 * 6), ("h", ctypes.c_double), ("h_outer", ctypes.c_double),
+                ("graded", ctypes.c_int32), ("main_conductor", ctypes.c_int32), ("p1", ctypes.c_double),
+                ("p2", ctypes.c_double), ("p3", ctypes.c_double), ("p5", ctypes.c_double)]
 
 
 class Stack:
     """A layered dielectric stack and its system (gbem_stack_*, Sec. 4)."""
 
-    def __init__(self, ctx: Context, lo, hi, z, eps_r, face_bc, boxes, h: float, h_outer: float = 0.0):
+    def __init__(self, ctx: Context, lo, hi, z, eps_r, face_bc, boxes, h: float, h_outer: float = 0.0,
+                 graded=None):
+        """graded = (main conductor id, p1, p2, p3, p5): the paper's partition
+        for that main net instead of uniform cells."""
         p = _Stack()
         p.lo[:] = [float(v) for v in lo]
         p.hi[:] = [float(v) for v in hi]
@@ -525,6 +530,10 @@ class Stack:
             p.eps_r[a] = float(v)
         p.face_bc[:] = [int(v) for v in face_bc]
         p.h, p.h_outer = float(h), float(h_outer)
+        if graded is not None:
+            p.graded = 1
+            p.main_conductor = int(graded[0])
+            p.p1, p.p2, p.p3, p.p5 = (float(v) for v in graded[1:])
         self.ctx, self.h = ctx, None
         self.eps_r = [float(v) for v in eps_r]
         arr = _boxes(boxes) if boxes else None

@@ -74,3 +74,41 @@ def test_stack_guards(lib):
     assert e.value.status == -9
     S.close()
     ctx.close()
+
+
+def test_graded_stack_matches_oracle_and_bounds(lib):
+    """The paper's partition on a stack (Sec. 3.3 for conductors and the
+    enclosure, Sec. 4 for interfaces): the library and the oracle build the
+    same panels, and every panel meets its bound."""
+    lo, hi, z, eps, bc = [-8, -8, 0], [8, 8, 4], [0, 1.5, 2.5, 4], [3.9, 2.5, 7.0], [D.NEUMANN] * 4 + [D.GROUND] * 2
+    boxes = [([-1.5, -0.25, 1.75], [1.5, 0.25, 2.25], 0), ([-1.5, 0.75, 1.75], [1.5, 1.25, 2.25], 1),
+             ([3.0, -3.0, 0.4], [3.5, 3.0, 0.9], 2)]
+    main, p1, p2, p3, p5 = 0, 0.1, 4.0, 1.0, 1.0
+    ctx = _ctx()
+    S = gbem.Stack(ctx, lo, hi, z, eps, bc, boxes, 0.5, 4.0, graded=(main, p1, p2, p3, p5))
+    got = S.panels()
+    ref = D.mesh_stack(D.Stack(lo, hi, z, eps, bc), boxes, 0.5, 4.0, graded=(main, p1, p2, p3, p5))
+    for k in ("axis", "kind", "cond", "region_a", "region_b", "sign"):
+        assert np.array_equal(got[k].astype(np.int64), ref[k].astype(np.int64)), k
+    assert np.array_equal(got["geo"], ref["geo"])
+    # bounds: distance to the main net's box, area limit by kind
+    mlo, mhi = np.array(boxes[0][0], float), np.array(boxes[0][1], float)
+    g, ax = ref["geo"], ref["axis"]
+    for i in range(len(ax)):
+        k = ax[i]
+        p, q = [x for x in range(3) if x != k]
+        plo, phi = np.zeros(3), np.zeros(3)
+        plo[k] = phi[k] = g[i, 0]
+        plo[p], phi[p], plo[q], phi[q] = g[i, 1], g[i, 2], g[i, 3], g[i, 4]
+        d = np.linalg.norm(np.maximum(0.0, np.maximum(mlo - phi, plo - mhi)))
+        area = (g[i, 2] - g[i, 1]) * (g[i, 4] - g[i, 3])
+        power = 2 if ref["kind"][i] == D.KIND_INTERFACE else 3
+        limit_far = p1 * p2 * p3 * max(1.0, d / p5) ** power   # the looser p4 of faces looking away
+        assert area <= (p1 * p2 if d < p5 else limit_far) * (1 + 1e-12)
+        assert max(g[i, 2] - g[i, 1], g[i, 4] - g[i, 3]) <= (0.5 if ref["kind"][i] == D.KIND_CONDUCTOR else 4.0) + 1e-12
+    # the grading coarsens with distance: interface panels far from the net are larger
+    itf = ref["kind"] == D.KIND_INTERFACE
+    areas = (g[itf, 2] - g[itf, 1]) * (g[itf, 4] - g[itf, 3])
+    assert areas.max() > 20 * areas.min()
+    S.close()
+    ctx.close()
