@@ -12,14 +12,18 @@
 // -eps_lower/eps_upper times it).  Known potentials (conductors at 1 V for
 // their right-hand side) move to the right-hand sides.
 //
-// Entries are FP64: exact corner sums of closed forms (near_field.cuh) for
-// near pairs, tensor Gauss-Legendre of both kernels at shared nodes for far
-// pairs.  The matrix is not symmetric (Sec. 4), so it is factored by a
-// right-looking blocked LU with partial pivoting (blocks of 64 columns): one
-// CTA factors the panel (sub-panels of 8 columns, rank-8 updates between
-// them), the row interchanges are applied to the other columns, a triangular
-// solve forms the panel's block row of U, and a tiled FP64 update applies
-// the panel to the trailing matrix.  No kernel here waits on another CTA.
+// Entries: exact corner sums of closed forms (near_field.cuh) for near
+// pairs in FP64, tensor Gauss-Legendre of both kernels at shared nodes for
+// far pairs (FP64, or FP32 with FP64 outer sums in mixed mode).  The matrix
+// is not symmetric (Sec. 4), so it is factored by a right-looking blocked LU
+// with partial pivoting (blocks of 64 columns): the panel is factored by one
+// CTA (sub-panels of 8 columns, rank-8 updates between them) or, in FP32, by
+// a thread-block cluster holding its rows in distributed shared memory; the
+// row interchanges are applied to the other columns as one composed move, a
+// triangular solve forms the panel's block row of U, and tiled updates apply
+// the panel to the trailing matrix (in FP32 with one panel of lookahead on a
+// second stream).  The solve refines against the FP64 system.  Apart from
+// the cluster barriers of the panel, no kernel here waits on another CTA.
 #include <cooperative_groups.h>
 #include <cstdio>
 
