@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=24,
                     help="whole matrix rows the all-core oracle evaluates for the CPU baseline")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch512", "serving", "partition", "unit_rates", "stack", "sphere"],
+                    choices=["headline", "batch512", "serving", "partition", "unit_rates", "stack", "sphere",
+                             "stack_partition"],
                     help="headline: the three-layer bus (and the 2x2 bus as secondary); "
                          "batch512 / serving: the batched and served forms; unit_rates: the "
                          "arithmetic-unit rates that bound the assembly, nothing else; stack: the "
@@ -1076,6 +1077,48 @@ def run_sphere(args):
     dist_stop(world)
 
 
+def run_stack_partition(args):
+    """Panels for accuracy on a layered stack (Sec. 3.3 and Sec. 4): net 0's
+    column of C in FP64 from uniform meshes and from the paper's partition for
+    net 0, against the partition at p1 = 0.025.  Two 3 x 0.5 x 0.5 um wires
+    0.5 um apart in the middle of three layers (eps_r 3.9 / 2.5 / 7.0) of a
+    16 x 16 x 4 um enclosure, grounded top and bottom, insulating sides.  One
+    JSON line."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2203_11733_gb300 import build as B
+    from paper_2203_11733_gb300 import gbem
+    B.build()
+    ctx = gbem.Context(0)
+    lo, hi, z, eps = [-8, -8, 0], [8, 8, 4], [0, 1.5, 2.5, 4], [3.9, 2.5, 7.0]
+    bc = [gbem.FACE_NEUMANN] * 4 + [gbem.FACE_GROUND] * 2
+    boxes = [([-1.5, -0.25, 1.75], [1.5, 0.25, 2.25], 0), ([-1.5, 0.75, 1.75], [1.5, 1.25, 2.25], 1)]
+
+    def column(h, h_outer, graded=None):
+        S = gbem.Stack(ctx, lo, hi, z, eps, bc, boxes, h, h_outer, graded=graded)
+        try:
+            S.assemble(gbem.GBEM_FP64)
+            C, _ = S.capacitance()
+            return S.n, np.asarray(C)[:, 0]
+        finally:
+            S.close()
+
+    n_ref, ref = column(0.25, 8.0, (0, 0.025, 4.0, 1.0, 1.0))
+    rows = []
+    for label, kw in (("uniform h=0.5 h_outer=4", (0.5, 4.0, None)), ("uniform h=0.25 h_outer=2", (0.25, 2.0, None)),
+                      ("uniform h=0.25 h_outer=1", (0.25, 1.0, None)),
+                      ("partition p1=0.25", (0.5, 8.0, (0, 0.25, 4.0, 1.0, 1.0))),
+                      ("partition p1=0.1", (0.5, 8.0, (0, 0.1, 4.0, 1.0, 1.0))),
+                      ("partition p1=0.05", (0.5, 8.0, (0, 0.05, 4.0, 1.0, 1.0)))):
+        n, c = column(*kw)
+        rows.append({"mesh": label, "panels": n, "err_C00": float(abs(c[0] / ref[0] - 1.0)),
+                     "err_C10": float(abs(c[1] / ref[1] - 1.0))})
+    print(json.dumps({"workload": "stack_partition", "reference_panels": n_ref, "C00_aF": float(ref[0] * 1e18),
+                      "C10_aF": float(ref[1] * 1e18), "rows": rows}))
+    ctx.close()
+
+
 def run_batch(args):
     """512 independent 2-6 bar structures (N log-uniform in [200, 3000]):
     the autotuned batch (groups of structures whose graphs run concurrently,
@@ -1479,6 +1522,8 @@ def main():
         run_stack(args)
     elif args.workload == "sphere":
         run_sphere(args)
+    elif args.workload == "stack_partition":
+        run_stack_partition(args)
     else:
         run_ours(args)
 
