@@ -492,9 +492,11 @@ void gbem_matrix_destroy(gbem_matrix_t* mat);
  * Several dielectrics (Sec. 4).  A layered stack: the box enclosure
  * [lo, hi] (um) cut by the planes z = z[1] < ... < z[n_layers-1] into
  * n_layers horizontal layers (z[0] = lo[2], z[n_layers] = hi[2]) of relative
- * permittivity eps_r[a], with disjoint cuboid conductors, each strictly
- * inside one layer and the enclosure (no box touches another, a layer plane
- * or the enclosure).  face_bc[2k + s] sets the enclosure face normal to axis
+ * permittivity eps_r[a], with disjoint cuboid conductors strictly inside the
+ * enclosure (no box touches another or the enclosure; a box's bottom and top
+ * lie off the layer planes).  A box may cross layer planes, as a via does:
+ * its side faces are cut where they cross, and each interface is cut along
+ * the footprints of the boxes that cross it and holed there.  face_bc[2k + s] sets the enclosure face normal to axis
  * k at lo[k] (s = 0) or hi[k] (s = 1): GBEM_FACE_GROUND (u = 0),
  * GBEM_FACE_NEUMANN (insulating, du/dn = 0) or a conductor id >= 0 (the
  * face is an electrode held at that conductor's potential).
@@ -549,8 +551,8 @@ typedef struct {
 typedef struct gbem_stack_s gbem_stack_t;
 
 /* Mesh a stack and lay out its system (host); on a device context also
- * upload the geometry.  GBEM_ERR_MESH for boxes outside a layer or the
- * enclosure, touching boxes, or no conductor; GBEM_ERR_ARG for malformed
+ * upload the geometry.  GBEM_ERR_MESH for boxes outside the enclosure or with
+ * a bottom or top on a layer plane, touching boxes, or no conductor; GBEM_ERR_ARG for malformed
  * parameters or more than 32768 equations. */
 gbem_status gbem_stack_mesh(gbem_ctx* ctx, const gbem_stack* stack, const gbem_box* boxes, int nbox,
                             gbem_stack_t** out);

@@ -163,10 +163,13 @@ def _graded_cells(k, plane, a0, b0, a1, b1, p4, p3, p5, power, hmax, mains):
 
 
 def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0, graded=None):
-    """Panels of a layered stack.  Conductor boxes (disjoint, each strictly
-    inside one layer and the enclosure) are cut as mesh_boxes cuts them (edge
-    cells ceil(L / h)); enclosure faces and interfaces with cells of at most
-    h_outer (h when 0).  Returns a dict of arrays: axis, geo (c, lo0, hi0,
+    """Panels of a layered stack.  Conductor boxes (disjoint, strictly inside
+    the enclosure, their bottom and top off the layer planes; a box may cross
+    layer planes, as a via does) are cut as mesh_boxes cuts them (edge cells
+    ceil(L / h)), their side faces also where they cross a layer plane;
+    enclosure faces and interfaces with cells of at most h_outer (h when 0),
+    interfaces cut along the footprints of the boxes that cross them and
+    holed there.  Returns a dict of arrays: axis, geo (c, lo0, hi0,
     lo1, hi1), kind, cond (conductor id, GROUND, NEUMANN or INTERFACE),
     region_a, region_b (-1 unless an interface: region_a the layer below),
     sign (the outward normal of region_a is sign * e_axis).
@@ -197,24 +200,36 @@ def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0, graded=None)
         p4 = p1 if toward else p1 * p2
         return _graded_cells(k, plane, a0, b0, a1, b1, p4, p3, p5, 3 if rule == "conductor" else 2, hcap, mains)
 
+    def layer_of(zz):
+        return [a for a in range(R) if stack.z[a] < zz < stack.z[a + 1]][0]
+
+    fboxes = []
     for lo, hi, c in boxes:
         lo = [float(v) for v in lo]
         hi = [float(v) for v in hi]
         if int(c) < 0:
             raise ValueError("conductor ids must be >= 0")
-        layer = [a for a in range(R) if stack.z[a] < lo[2] and hi[2] < stack.z[a + 1]]
-        inside = all(stack.lo[d] < lo[d] and hi[d] < stack.hi[d] for d in range(3))
-        if len(layer) != 1 or not inside:
-            raise ValueError("every box must lie strictly inside one layer and the enclosure")
-        a = layer[0]
+        inside = all(stack.lo[d] < lo[d] < hi[d] < stack.hi[d] for d in range(3))
+        on_plane = any(v in stack.z for v in (lo[2], hi[2]))
+        if not inside or on_plane:
+            raise ValueError("every box must lie strictly inside the enclosure, its bottom and top off the "
+                             "layer planes")
+        fboxes.append((lo, hi, int(c)))
+        spans = [a for a in range(R) if stack.z[a] < hi[2] and lo[2] < stack.z[a + 1]]
         for k in range(3):
             p, q = [x for x in range(3) if x != k]
             for plane, sgn, side in ((lo[k], 1, 0), (hi[k], -1, 1)):
                 toward = True
                 if graded is not None:
                     toward = int(c) == int(main) or (mhi[k] > plane if side == 1 else mlo[k] < plane)
-                for g0, g1, g2, g3 in cells2(k, plane, lo[p], hi[p], lo[q], hi[q], h, "conductor", toward):
-                    rows.append((k, (plane, g0, g1, g2, g3), KIND_CONDUCTOR, int(c), a, -1, sgn))
+                if k == 2:
+                    pieces = [(layer_of(plane), lo[q], hi[q])]
+                else:
+                    # q == 2: a side face is cut where it crosses a layer plane
+                    pieces = [(a, max(lo[2], stack.z[a]), min(hi[2], stack.z[a + 1])) for a in spans]
+                for a, q0, q1 in pieces:
+                    for g0, g1, g2, g3 in cells2(k, plane, lo[p], hi[p], q0, q1, h, "conductor", toward):
+                        rows.append((k, (plane, g0, g1, g2, g3), KIND_CONDUCTOR, int(c), a, -1, sgn))
     for k in range(3):
         p, q = [x for x in range(3) if x != k]
         for s in (0, 1):
@@ -233,9 +248,19 @@ def mesh_stack(stack: Stack, boxes, h: float, h_outer: float = 0.0, graded=None)
                                                  h_out, "conductor"):
                         rows.append((k, (plane, g0, g1, g2, g3), KIND_FACE, bc, a, -1, sgn))
     for a in range(1, R):
-        for g0, g1, g2, g3 in cells2(2, stack.z[a], stack.lo[0], stack.hi[0], stack.lo[1], stack.hi[1], h_out,
-                                     "interface"):
-            rows.append((2, (stack.z[a], g0, g1, g2, g3), KIND_INTERFACE, INTERFACE, a - 1, a, 1))
+        za = stack.z[a]
+        holes = [(lo, hi) for lo, hi, c in fboxes if lo[2] < za < hi[2]]
+        # the interface is cut along the footprints of the conductors that
+        # cross it; cells inside a footprint are holes
+        bx = sorted({stack.lo[0], stack.hi[0]} | {v for lo, hi in holes for v in (lo[0], hi[0])})
+        by = sorted({stack.lo[1], stack.hi[1]} | {v for lo, hi in holes for v in (lo[1], hi[1])})
+        for i in range(len(bx) - 1):
+            for j in range(len(by) - 1):
+                cx, cy = 0.5 * (bx[i] + bx[i + 1]), 0.5 * (by[j] + by[j + 1])
+                if any(lo[0] < cx < hi[0] and lo[1] < cy < hi[1] for lo, hi in holes):
+                    continue
+                for g0, g1, g2, g3 in cells2(2, za, bx[i], bx[i + 1], by[j], by[j + 1], h_out, "interface"):
+                    rows.append((2, (za, g0, g1, g2, g3), KIND_INTERFACE, INTERFACE, a - 1, a, 1))
     return {
         "axis": np.array([r[0] for r in rows], dtype=np.int32),
         "geo": np.array([r[1] for r in rows], dtype=np.float64).reshape(-1, 5),

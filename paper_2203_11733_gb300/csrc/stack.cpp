@@ -197,19 +197,19 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
             }
         if (m.mains.empty()) return err = "no box of the main conductor", GBEM_ERR_ARG;
     }
+    auto layer_of = [&](double zz) {
+        for (int a = 0; a < R; ++a)
+            if (st->z[a] < zz && zz < st->z[a + 1]) return a;
+        return -1;
+    };
     for (int b = 0; b < nbox; ++b) {
         const gbem_box& B = boxes[b];
         if (B.conductor < 0) return err = "conductor ids must be >= 0", GBEM_ERR_ARG;
-        int layer = -1, count = 0;
-        for (int a = 0; a < R; ++a)
-            if (st->z[a] < B.lo[2] && B.hi[2] < st->z[a + 1]) {
-                layer = a;
-                ++count;
-            }
         bool inside = true;
-        for (int d = 0; d < 3; ++d) inside = inside && st->lo[d] < B.lo[d] && B.hi[d] < st->hi[d] && B.lo[d] < B.hi[d];
-        if (count != 1 || !inside)
-            return err = "every box must lie strictly inside one layer and the enclosure", GBEM_ERR_MESH;
+        for (int d = 0; d < 3; ++d) inside = inside && st->lo[d] < B.lo[d] && B.lo[d] < B.hi[d] && B.hi[d] < st->hi[d];
+        if (!inside || layer_of(B.lo[2]) < 0 || layer_of(B.hi[2]) < 0)
+            return err = "every box must lie strictly inside the enclosure, its bottom and top off the layer planes",
+                   GBEM_ERR_MESH;
         for (int c = 0; c < b; ++c) {
             bool apart = false;
             for (int d = 0; d < 3; ++d) apart = apart || boxes[c].hi[d] < B.lo[d] || B.hi[d] < boxes[c].lo[d];
@@ -221,10 +221,21 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
             // it; a face looks toward the main net when some of the net lies
             // beyond its plane on the conductor's outward side
             const bool is_main = B.conductor == st->main_conductor;
-            m.face(k, B.lo[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 3, is_main || m.mlo[k] < B.lo[k], 0,
-                   B.conductor, layer, -1, 1);
-            m.face(k, B.hi[k], B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 3, is_main || m.mhi[k] > B.hi[k], 0,
-                   B.conductor, layer, -1, -1);
+            for (int side = 0; side < 2; ++side) {
+                const double plane = side ? B.hi[k] : B.lo[k];
+                const bool toward = is_main || (side ? m.mhi[k] > plane : m.mlo[k] < plane);
+                const int sign = side ? -1 : 1;
+                if (k == 2) {
+                    m.face(k, plane, B.lo[p], B.hi[p], B.lo[q], B.hi[q], st->h, 3, toward, 0, B.conductor,
+                           layer_of(plane), -1, sign);
+                } else {
+                    // q == 2: a side face is cut where it crosses a layer plane
+                    for (int a = 0; a < R; ++a)
+                        if (st->z[a] < B.hi[2] && B.lo[2] < st->z[a + 1])
+                            m.face(k, plane, B.lo[p], B.hi[p], std::max(B.lo[2], st->z[a]),
+                                   std::min(B.hi[2], st->z[a + 1]), st->h, 3, toward, 0, B.conductor, a, -1, sign);
+                }
+            }
         }
     }
     for (int k = 0; k < 3; ++k) {
@@ -242,9 +253,33 @@ gbem_status stack_build(const gbem_stack* st, const gbem_box* boxes, int nbox, g
             }
         }
     }
-    for (int a = 1; a < R; ++a)
-        m.face(2, st->z[a], st->lo[0], st->hi[0], st->lo[1], st->hi[1], h_out, 2, true, 2, GBEM_PANEL_INTERFACE, a - 1, a,
-               1);
+    for (int a = 1; a < R; ++a) {
+        // the interface is cut along the footprints of the boxes that cross
+        // it; cells inside a footprint are holes
+        const double za = st->z[a];
+        std::vector<const gbem_box*> holes;
+        for (int b = 0; b < nbox; ++b)
+            if (boxes[b].lo[2] < za && za < boxes[b].hi[2]) holes.push_back(&boxes[b]);
+        std::vector<double> bx{st->lo[0], st->hi[0]}, by{st->lo[1], st->hi[1]};
+        for (const gbem_box* B : holes) {
+            bx.push_back(B->lo[0]);
+            bx.push_back(B->hi[0]);
+            by.push_back(B->lo[1]);
+            by.push_back(B->hi[1]);
+        }
+        std::sort(bx.begin(), bx.end());
+        bx.erase(std::unique(bx.begin(), bx.end()), bx.end());
+        std::sort(by.begin(), by.end());
+        by.erase(std::unique(by.begin(), by.end()), by.end());
+        for (size_t i = 0; i + 1 < bx.size(); ++i)
+            for (size_t j = 0; j + 1 < by.size(); ++j) {
+                const double cx = 0.5 * (bx[i] + bx[i + 1]), cy = 0.5 * (by[j] + by[j + 1]);
+                bool hole = false;
+                for (const gbem_box* B : holes) hole = hole || (B->lo[0] < cx && cx < B->hi[0] && B->lo[1] < cy && cy < B->hi[1]);
+                if (hole) continue;
+                m.face(2, za, bx[i], bx[i + 1], by[j], by[j + 1], h_out, 2, true, 2, GBEM_PANEL_INTERFACE, a - 1, a, 1);
+            }
+    }
     S->eps.assign(st->eps_r, st->eps_r + R);
     S->R = R;
     S->n = (int)S->axis.size();

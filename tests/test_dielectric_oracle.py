@@ -121,6 +121,33 @@ def test_stack_mesh_layout_and_guards():
     assert area[m["kind"] == D.KIND_INTERFACE].sum() == pytest.approx(16.0)
     assert area[m["kind"] == D.KIND_FACE].sum() == pytest.approx(2 * 16.0 + 4 * 12.0)
     with pytest.raises(ValueError):
-        D.mesh_stack(st, [([1, 1, 1.0], [2, 2, 2.0], 0)], 0.5)   # crosses z = 1.5
+        D.mesh_stack(st, [([1, 1, 1.5], [2, 2, 2.0], 0)], 0.5)   # bottom on the plane z = 1.5
     with pytest.raises(ValueError):
         D.mesh_stack(st, [([0, 1, 0.5], [2, 2, 1.0], 0)], 0.5)   # touches the enclosure
+
+
+def test_via_through_an_interface():
+    """A conductor crossing a layer plane (a via): its side faces are cut at
+    the plane, the interface is holed along its footprint, every region's
+    boundary stays closed (Gauss's theorem per region, as above), and C keeps
+    the Maxwell pattern and near-symmetry."""
+    st = D.Stack([0, 0, 0], [4, 4, 3], [0, 1.5, 3], [1.0, 3.0], [D.GROUND] * 6)
+    boxes = [([1.5, 1.5, 0.8], [2.0, 2.0, 2.2], 0), ([0.5, 2.8, 0.5], [3.5, 3.3, 1.0], 1)]
+    m = D.mesh_stack(st, boxes, 0.5, 1.0)
+    ra, rb, sg, kind = m["region_a"], m["region_b"], m["sign"], m["kind"]
+    area = O.areas(m["geo"])
+    # the interface loses the via's footprint (0.25 um^2) and the via gains
+    # side panels in both layers
+    assert area[kind == D.KIND_INTERFACE].sum() == pytest.approx(16.0 - 0.25)
+    via = (m["cond"] == 0) & (m["axis"] != 2)
+    assert set(ra[via].tolist()) == {0, 1}
+    for a in range(2):
+        P = np.nonzero((ra == a) | (rb == a))[0]
+        I, J = np.repeat(P, len(P)), np.tile(P, len(P))
+        Dm = D.dlayer_entries(m["axis"], m["geo"], I, J).reshape(len(P), len(P))
+        s = np.where(ra[P] == a, sg[P], -sg[P])
+        assert np.abs(Dm @ s + 0.5 * area[P]).max() <= 1e-13 * area[P].max()
+    C, _ = D.capacitance(m, st.eps)
+    assert C[0, 0] > 0 and C[1, 1] > 0 and C[0, 1] < 0
+    assert abs(C[0, 1] - C[1, 0]) < 0.03 * abs(C[0, 1])
+

@@ -47,11 +47,39 @@ def test_stack_mesh_matches_oracle(lib, case):
     ctx.close()
 
 
+VIA_CASES = [
+    ([0, 0, 0], [4, 4, 3], [0, 1.5, 3], [1.0, 3.0], [D.GROUND] * 6,
+     [([1.5, 1.5, 0.8], [2.0, 2.0, 2.2], 0), ([0.5, 2.8, 0.5], [3.5, 3.3, 1.0], 1)], 0.5, 1.0, None),
+    ([-3, -2, 0], [3, 2, 2.5], [0, 0.7, 1.6, 2.5], [3.9, 2.2, 7.0], [D.NEUMANN] * 4 + [D.GROUND, D.GROUND],
+     [([-0.3, -0.3, 0.3], [0.3, 0.3, 2.2], 4), ([1.0, -1.5, 0.9], [2.5, -1.0, 1.3], 2)], 0.3, 0.8, None),
+    ([-3, -2, 0], [3, 2, 2.5], [0, 0.7, 1.6, 2.5], [3.9, 2.2, 7.0], [D.NEUMANN] * 4 + [D.GROUND, D.GROUND],
+     [([-0.3, -0.3, 0.3], [0.3, 0.3, 2.2], 4), ([1.0, -1.5, 0.9], [2.5, -1.0, 1.3], 2)], 0.3, 0.8,
+     (4, 0.05, 4.0, 1.0, 0.5)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(VIA_CASES)))
+def test_vias_match_oracle(lib, case):
+    """Conductors crossing layer planes: the same panels in the library and
+    the oracle, uniform and graded."""
+    lo, hi, z, eps, bc, boxes, h, ho, graded = VIA_CASES[case]
+    ctx = _ctx()
+    S = gbem.Stack(ctx, lo, hi, z, eps, bc, boxes, h, ho, graded=graded)
+    got = S.panels()
+    ref = D.mesh_stack(D.Stack(lo, hi, z, eps, bc), boxes, h, ho, graded=graded)
+    for k in ("axis", "kind", "cond", "region_a", "region_b", "sign"):
+        assert np.array_equal(got[k].astype(np.int64), ref[k].astype(np.int64)), k
+    assert np.array_equal(got["geo"], ref["geo"])
+    assert S.n_eq == len(D.layout(ref)[0])
+    S.close()
+    ctx.close()
+
+
 def test_stack_guards(lib):
     ctx = _ctx()
     lo, hi, z, eps, bc = [0, 0, 0], [4, 4, 3], [0, 1.5, 3], [1.0, 3.0], [D.GROUND] * 6
     bad_boxes = [
-        [([1, 1, 1.0], [2, 2, 2.0], 0)],                              # crosses a layer plane
+        [([1, 1, 1.5], [2, 2, 2.0], 0)],                              # bottom on a layer plane
         [([0, 1, 0.5], [2, 2, 1.0], 0)],                              # touches the enclosure
         [([1, 1, 0.5], [2, 2, 1.0], 0), ([2, 1, 0.5], [3, 2, 1.0], 1)],  # boxes touch
     ]
