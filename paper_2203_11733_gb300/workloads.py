@@ -314,3 +314,56 @@ def icosphere(R: float = 1.0, level: int = 2, centre=(0.0, 0.0, 0.0)):
         tris = np.concatenate([np.stack([a, ab, ca], 1), np.stack([ab, b, bc], 1), np.stack([ca, bc, c], 1),
                                np.stack([ab, bc, ca], 1)])
     return (R * tris + np.asarray(centre, dtype=np.float64)).reshape(-1, 9)
+
+
+def trapezoid_bar(x0: float, x1: float, w_bottom: float, w_top: float, z0: float, z1: float,
+                  n_len: int = 8, n_w: int = 3, n_h: int = 3, y0: float = 0.0):
+    """Flat triangles on the closed surface of a straight wire along x whose
+    cross-section is a trapezoid (bottom width w_bottom at z0, top width w_top
+    at z1, centred on y0), as etched interconnect is.  Every face is a grid of
+    quadrilaterals (n_len along the wire, n_w across, n_h up the sides) cut
+    into two triangles; vertices shared by faces are the same numbers, so
+    touching triangles share them exactly.  Returns float64[n, 9]."""
+    import numpy as np
+    canon = {}
+
+    def vert(x, y, z):
+        key = (round(x, 12), round(y, 12), round(z, 12))
+        return canon.setdefault(key, (float(x), float(y), float(z)))
+
+    def lerp(a, b, t, n):
+        return b if t == n else a + (b - a) * t / n
+
+    def section(s, t):
+        """Point (y, z) of the cross-section at width fraction s/n_w of the
+        level t/n_h."""
+        z = lerp(z0, z1, t, n_h)
+        w = lerp(w_bottom, w_top, t, n_h)
+        return lerp(y0 - 0.5 * w, y0 + 0.5 * w, s, n_w), z
+
+    tris = []
+
+    def quad(a, b, c, d):   # counter-clockwise seen from outside
+        tris.append(a + b + c)
+        tris.append(a + c + d)
+
+    xs = [lerp(x0, x1, i, n_len) for i in range(n_len + 1)]
+    # the four long faces, each a strip along x: bottom, right side, top, left side
+    ring = ([section(s, 0) for s in range(n_w + 1)] + [section(n_w, t) for t in range(1, n_h + 1)] +
+            [section(s, n_h) for s in range(n_w - 1, -1, -1)] + [section(0, t) for t in range(n_h - 1, 0, -1)])
+    m = len(ring)
+    for i in range(n_len):
+        for r in range(m):
+            (ya, za), (yb, zb) = ring[r], ring[(r + 1) % m]
+            quad(vert(xs[i], ya, za), vert(xs[i], yb, zb), vert(xs[i + 1], yb, zb), vert(xs[i + 1], ya, za))
+    # the two end caps: the trapezoid's grid
+    for x, flip in ((x0, True), (x1, False)):
+        for t in range(n_h):
+            for s in range(n_w):
+                (ya, za), (yb, zb) = section(s, t), section(s + 1, t)
+                (yc, zc), (yd, zd) = section(s + 1, t + 1), section(s, t + 1)
+                p = [vert(x, ya, za), vert(x, yb, zb), vert(x, yc, zc), vert(x, yd, zd)]
+                if flip:
+                    p = p[::-1]
+                quad(*p)
+    return np.array(tris, dtype=np.float64)

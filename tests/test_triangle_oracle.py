@@ -1,8 +1,10 @@
 """Pins of the flat-triangle oracle against facts outside it: brute-force
 quadrature of a triangle's potential, rectangles cut into triangles (the
 rectangle oracle and its closed forms are pinned on their own), the published
-closed form of a triangle's self-integral, scaling and translation, and the
-capacitance of a sphere approached from below by inscribed icospheres."""
+closed form of a triangle's self-integral, scaling and translation, the
+capacitance of a sphere approached from below by inscribed icospheres, the
+variational bound under a refinement from rectangles to triangles, and a
+trapezoid wire between the cuboids of its two widths."""
 import math
 
 import numpy as np
@@ -93,3 +95,42 @@ def test_icosphere_capacitance_rises_toward_sphere():
         C = T.tri_capacitance(tris, np.zeros(len(tris), np.int32), 1.0)
         vals.append(C[0, 0] / (4 * math.pi * O.EPS0 * 1e-6))
     assert vals[0] < vals[1] < 1.0 and vals[1] > 0.95
+
+
+def _split(axis, geo):
+    """Each axis-aligned rectangle cut along a diagonal into two triangles."""
+    out = []
+    for k, (c, a0, b0, a1, b1) in zip(axis, geo):
+        p, q = [x for x in range(3) if x != k]
+        corners = []
+        for u, v in ((a0, a1), (b0, a1), (b0, b1), (a0, b1)):
+            x = [0.0] * 3
+            x[k], x[p], x[q] = c, u, v
+            corners.append(x)
+        out.append(corners[0] + corners[1] + corners[2])
+        out.append(corners[0] + corners[2] + corners[3])
+    return np.array(out)
+
+
+def test_triangles_refine_rectangles():
+    """Cutting every rectangle of a mesh into two triangles enlarges the
+    Galerkin space, so the capacitance can only rise (variational bound), and
+    only by the discretisation error."""
+    a, g, c = O.mesh_boxes([([0, 0, 0], [2.0, 0.5, 0.25], 0)], 0.25)
+    C_rect = O.capacitance(a, g, c, 1.0)[0, 0]
+    tris = _split(a, g)
+    C_tri = T.tri_capacitance(tris, np.zeros(len(tris), np.int32), 1.0)[0, 0]
+    assert C_rect * (1 - 1e-12) <= C_tri < C_rect * 1.02
+
+
+def test_trapezoid_wire_between_its_cuboids():
+    """A wire of trapezoidal cross-section (the paper stacks cuboids for such
+    shapes, Sec. 3.3; here flat triangles describe it exactly) has a
+    capacitance between those of the cuboids of its top and bottom widths."""
+    tris = W.trapezoid_bar(0.0, 2.0, 0.5, 0.25, 0.0, 0.25, n_len=8, n_w=2, n_h=2)
+    C_trap = T.tri_capacitance(tris, np.zeros(len(tris), np.int32), 1.0)[0, 0]
+    caps = []
+    for w in (0.25, 0.5):
+        a, g, c = O.mesh_boxes([([0, -w / 2, 0], [2.0, w / 2, 0.25], 0)], 0.125)
+        caps.append(O.capacitance(a, g, c, 1.0)[0, 0])
+    assert caps[0] < C_trap < caps[1]
