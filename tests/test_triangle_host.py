@@ -53,3 +53,16 @@ def test_icosphere_is_inscribed_and_closed():
             key = tuple(sorted((tuple(np.round(t[a], 12)), tuple(np.round(t[b], 12)))))
             edges[key] = edges.get(key, 0) + 1
     assert set(edges.values()) == {2}
+
+
+def test_trapezoid_bar_is_closed_and_outward():
+    tris = W.trapezoid_bar(0.0, 4.0, 1.0, 0.6, 0.0, 0.5, n_len=8, n_w=3, n_h=2).reshape(-1, 3, 3)
+    edges = {}
+    for t in tris:
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            key = (tuple(t[a]), tuple(t[b]))
+            edges[key] = edges.get(key, 0) + 1
+    # every directed edge once, its reverse once: closed and consistently oriented
+    assert all(v == 1 and edges.get((b, a), 0) == 1 for (a, b), v in edges.items())
+    volume = sum(np.dot(t[0], np.cross(t[1] - t[0], t[2] - t[0])) / 6.0 for t in tris)
+    assert volume == pytest.approx(4.0 * 0.5 * (1.0 + 0.6) / 2.0, rel=1e-12)
