@@ -100,6 +100,15 @@ def test_stack_guards(lib):
     with pytest.raises(gbem.GbemError) as e:   # a host context cannot assemble
         S.assemble(gbem.GBEM_FP64, stream=0)
     assert e.value.status == -9
+    with pytest.raises(gbem.GbemError) as e:   # nothing assembled to download
+        S.system()
+    assert e.value.status == -8
+    with pytest.raises(gbem.GbemError) as e:   # no device to solve on
+        S.capacitance(stream=0)
+    assert e.value.status == -9
+    with pytest.raises(gbem.GbemError) as e:   # a graded stack needs its main conductor
+        gbem.Stack(ctx, lo, hi, z, eps, bc, [([1, 1, 0.5], [2, 3, 1], 0)], 0.5, graded=(5, 0.1, 4.0, 1.0, 1.0))
+    assert e.value.status == -1
     S.close()
     ctx.close()
 
